@@ -1,0 +1,326 @@
+"""CPU oracle of SA-AMG with the 1Norm / OffLmp / Cnstrnt / Sprsfy adaptations.
+
+TEST INFRASTRUCTURE ONLY: the reference that the CUDA path is checked against.  Only the
+tests, the smoke check and the benchmark's CPU-baseline / reference arm may import this
+package.  It wraps `libsa_oracle.so` (plain single-threaded FP64 C, `sa_oracle.c`) through
+ctypes and converts to and from numpy arrays.  It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "sa_oracle.c")
+LIB = os.path.join(HERE, "libsa_oracle.so")
+
+OK, ERR_INVALID_ARG, ERR_OOM, ERR_ZERO_DIAG, ERR_EIGEN, ERR_COARSE_NOT_SPD, ERR_NOT_CONVERGED, ERR_UNSUPPORTED = \
+    0, 1, 2, 4, 5, 6, 7, 9
+ONENORM, OFFLMP, SPRSFY, CNSTRNT = 1, 2, 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (no FMA contraction, so every product and sum rounds as written)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(
+            os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "sa_oracle.h"))):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Params(C.Structure):
+    _fields_ = [("theta", C.c_double), ("variants", C.c_uint), ("tau", C.c_double), ("sigma", C.c_double),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("power_iters", C.c_int),
+                ("max_coarse", C.c_int), ("max_levels", C.c_int), ("pt_unit", C.c_int),
+                ("onenorm_power", C.c_int), ("seed", C.c_uint64), ("lambda_override", C.c_double),
+                ("max_iter", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("relres_true", C.c_double), ("levels", C.c_int),
+                ("op_complexity", C.c_double)]
+
+
+class _CSR(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rp", C.POINTER(C.c_int64)),
+                ("ci", C.POINTER(C.c_int32)), ("v", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        vp = C.c_void_p
+        L.oc_params_default.argtypes = [C.POINTER(Params)]
+        L.oc_strength.argtypes = [C.c_int64, vp, vp, vp, C.c_double, vp]
+        L.oc_filter.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_int, C.c_double, C.POINTER(C.POINTER(_CSR)), vp]
+        L.oc_mis2_aggregate.argtypes = [C.c_int64, vp, vp, vp, C.c_uint64, C.c_int, vp, vp]
+        L.oc_mis2_aggregate.restype = C.c_int64
+        L.oc_priority.argtypes = [C.c_uint64, C.c_int, C.c_int64]
+        L.oc_priority.restype = C.c_uint64
+        L.oc_sprsfy_mark.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_int64, vp]
+        L.oc_constrain_row.argtypes = [C.c_int64, vp, C.c_int64, C.c_double]
+        L.oc_spgemm.argtypes = [C.POINTER(_CSR), C.POINTER(_CSR), C.c_int64, C.POINTER(C.POINTER(_CSR))]
+        L.oc_transpose.argtypes = [C.POINTER(_CSR), C.c_int64, C.POINTER(C.POINTER(_CSR))]
+        L.oc_power_lambda.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_int, C.c_uint64]
+        L.oc_power_lambda.restype = C.c_double
+        L.oc_power_stream_seed.argtypes = [C.c_uint64, C.c_int, C.c_int]
+        L.oc_power_stream_seed.restype = C.c_uint64
+        L.oc_cholesky.argtypes = [C.c_int64, vp, vp]
+        L.oc_csr_free.argtypes = [C.POINTER(_CSR)]
+        L.oc_setup.argtypes = [C.c_int64, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
+        L.oc_prolongator_only.argtypes = [C.c_int64, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
+        L.oc_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Info)]
+        L.oc_pcg_plain.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(Info)]
+        L.oc_vcycle.argtypes = [vp, vp, vp]
+        L.oc_free.argtypes = [vp]
+        L.oc_nlevels.argtypes = [vp]
+        L.oc_level_get.argtypes = [vp, C.c_int, C.c_int, vp, C.POINTER(C.c_int64)]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _arrs(A):
+    rp = np.ascontiguousarray(A.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    v = np.ascontiguousarray(A.val, dtype=np.float64)
+    return rp, ci, v
+
+
+def _wrap(rp, ci, v, n):
+    return _CSR(n, int(rp[-1]), rp.ctypes.data_as(C.POINTER(C.c_int64)), ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                v.ctypes.data_as(C.POINTER(C.c_double)))
+
+
+def _take(cp):
+    c = cp.contents
+    n, nnz = c.n, c.nnz
+    rp = np.ctypeslib.as_array(c.rp, shape=(n + 1,)).copy()
+    ci = np.ctypeslib.as_array(c.ci, shape=(max(nnz, 1),))[:nnz].copy()
+    v = np.ctypeslib.as_array(c.v, shape=(max(nnz, 1),))[:nnz].copy()
+    lib().oc_csr_free(cp)
+    return rp, ci, v
+
+
+def params(**kw) -> Params:
+    p = Params()
+    lib().oc_params_default(C.byref(p))
+    for k, val in kw.items():
+        if k == "variants" and not isinstance(val, int):
+            m = 0
+            for s in val:
+                m |= {"1norm": ONENORM, "offlmp": OFFLMP, "sprsfy": SPRSFY, "cnstrnt": CNSTRNT}[s.lower()]
+            val = m
+        setattr(p, k, val)
+    return p
+
+
+@dataclass
+class SimpleCSR:
+    n: int
+    row_ptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+    def to_dense(self, ncol=None):
+        ncol = self.n if ncol is None else ncol
+        d = np.zeros((self.n, ncol))
+        rows = np.repeat(np.arange(self.n), np.diff(self.row_ptr))
+        d[rows, self.col] = self.val
+        return d
+
+
+# ---------------------------------------------------------------- single steps
+
+def strength(A, theta: float) -> np.ndarray:
+    rp, ci, v = _arrs(A)
+    out = np.zeros(len(ci), dtype=np.uint8)
+    lib().oc_strength(A.n, _p(rp), _p(ci), _p(v), theta, _p(out))
+    return out
+
+
+def filtered(A, removed: np.ndarray, offlmp: bool = False, tau: float = 1.1):
+    rp, ci, v = _arrs(A)
+    rem = np.ascontiguousarray(removed, dtype=np.uint8)
+    flag = np.zeros(max(A.n, 1), dtype=np.uint8)
+    out = C.POINTER(_CSR)()
+    st = lib().oc_filter(A.n, _p(rp), _p(ci), _p(v), _p(rem), int(offlmp), tau, C.byref(out), _p(flag))
+    assert st == 0
+    r, c, val = _take(out)
+    return SimpleCSR(A.n, r, c, val), flag[:A.n]
+
+
+def aggregate(A, strong: np.ndarray, seed: int = 0, level: int = 0):
+    rp, ci, _ = _arrs(A)
+    s = np.ascontiguousarray(strong, dtype=np.uint8)
+    agg = np.zeros(max(A.n, 1), dtype=np.int32)
+    root = np.zeros(max(A.n, 1), dtype=np.uint8)
+    nagg = lib().oc_mis2_aggregate(A.n, _p(rp), _p(ci), _p(s), seed, level, _p(agg), _p(root))
+    return agg[:A.n], root[:A.n], int(nagg)
+
+
+def priority(seed: int, level: int, i: int) -> int:
+    return int(lib().oc_priority(seed, level, i))
+
+
+def sprsfy_mark(A, strong, agg, root, nagg, removed):
+    rp, ci, _ = _arrs(A)
+    rem = np.ascontiguousarray(removed, dtype=np.uint8).copy()
+    npr = lib().oc_sprsfy_mark(A.n, _p(rp), _p(ci), _p(np.ascontiguousarray(strong, dtype=np.uint8)),
+                               _p(np.ascontiguousarray(agg, dtype=np.int32)),
+                               _p(np.ascontiguousarray(root, dtype=np.uint8)), nagg, _p(rem))
+    return rem, int(npr)
+
+
+def constrain_row(p, ptent_pos: int, ptent_val: float = 1.0):
+    a = np.ascontiguousarray(p, dtype=np.float64).copy()
+    code = lib().oc_constrain_row(len(a), _p(a), ptent_pos, ptent_val)
+    return a, int(code)
+
+
+def spgemm(A, B, ncolB: int) -> SimpleCSR:
+    ra, ca, va = _arrs(A)
+    rb, cb, vb = _arrs(B)
+    wa, wb = _wrap(ra, ca, va, A.n), _wrap(rb, cb, vb, B.n)
+    out = C.POINTER(_CSR)()
+    st = lib().oc_spgemm(C.byref(wa), C.byref(wb), ncolB, C.byref(out))
+    assert st == 0
+    return SimpleCSR(A.n, *_take(out))
+
+
+def transpose(A, ncol: int) -> SimpleCSR:
+    ra, ca, va = _arrs(A)
+    wa = _wrap(ra, ca, va, A.n)
+    out = C.POINTER(_CSR)()
+    st = lib().oc_transpose(C.byref(wa), ncol, C.byref(out))
+    assert st == 0
+    return SimpleCSR(ncol, *_take(out))
+
+
+def power_lambda(A, D, sweeps: int, stream_seed: int) -> float:
+    rp, ci, v = _arrs(A)
+    d = np.ascontiguousarray(D, dtype=np.float64)
+    return float(lib().oc_power_lambda(A.n, _p(rp), _p(ci), _p(v), _p(d), sweeps, stream_seed))
+
+
+def power_stream_seed(seed: int, level: int, purpose: int) -> int:
+    return int(lib().oc_power_stream_seed(seed, level, purpose))
+
+
+def cholesky(a: np.ndarray):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    n = a.shape[0]
+    l = np.zeros_like(a)
+    st = lib().oc_cholesky(n, _p(a), _p(l))
+    return l, int(st)
+
+
+def pcg_plain(A, b, tol: float, max_iter: int):
+    rp, ci, v = _arrs(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(max(A.n, 1))
+    info = Info()
+    lib().oc_pcg_plain(A.n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, max_iter, C.byref(info))
+    return x[:A.n], info
+
+
+# ---------------------------------------------------------------- the whole method
+
+_WHAT = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
+         "removed": (4, np.uint8), "lumpflag": (5, np.uint8), "Abar.rp": (6, np.int64), "Abar.ci": (7, np.int32),
+         "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
+         "P.ci": (12, np.int32), "P.v": (13, np.float64), "R.rp": (14, np.int64), "R.ci": (15, np.int32),
+         "R.v": (16, np.float64), "Dsm": (17, np.float64), "scalars": (18, np.float64), "B": (19, np.float64),
+         "cflag": (20, np.uint8), "chol": (21, np.float64)}
+
+
+class Hierarchy:
+    """An oracle hierarchy; `level(l)` returns its arrays as numpy copies."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().oc_free(self._h)
+            self._h = None
+
+    @property
+    def nlevels(self) -> int:
+        return int(lib().oc_nlevels(self._h))
+
+    def get(self, level: int, what: str) -> np.ndarray:
+        code, dt = _WHAT[what]
+        ln = C.c_int64(0)
+        st = lib().oc_level_get(self._h, level, code, None, C.byref(ln))
+        assert st == 0
+        out = np.zeros(max(ln.value, 1), dtype=dt)
+        lib().oc_level_get(self._h, level, code, _p(out), C.byref(ln))
+        return out[:ln.value]
+
+    def level(self, l: int) -> dict:
+        d = {k: self.get(l, k) for k in _WHAT}
+        n = len(d["A.rp"]) - 1
+        d["A"] = SimpleCSR(n, d["A.rp"], d["A.ci"], d["A.v"])
+        if len(d["Abar.rp"]):
+            d["Abar"] = SimpleCSR(n, d["Abar.rp"], d["Abar.ci"], d["Abar.v"])
+            d["P"] = SimpleCSR(n, d["P.rp"], d["P.ci"], d["P.v"])
+            d["R"] = SimpleCSR(len(d["R.rp"]) - 1, d["R.rp"], d["R.ci"], d["R.v"])
+            sc = d["scalars"]
+            d["lambda_bar"], d["omega"], d["lambda_cheb"], d["nagg"] = float(sc[0]), float(sc[1]), float(sc[2]), \
+                int(sc[3])
+        return d
+
+    def solve(self, b, tol: float = 1e-8):
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(max(self.n, 1))
+        info = Info()
+        st = lib().oc_solve(self._h, _p(b), _p(x), tol, C.byref(info))
+        return x[:self.n], info, int(st)
+
+    def vcycle(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        u = np.zeros(max(self.n, 1))
+        lib().oc_vcycle(self._h, _p(f), _p(u))
+        return u[:self.n]
+
+
+def setup(A, nullspace=None, **kw):
+    """Returns (Hierarchy or None, status)."""
+    rp, ci, v = _arrs(A)
+    ns = None if nullspace is None else np.ascontiguousarray(nullspace, dtype=np.float64)
+    p = params(**kw)
+    h = C.c_void_p()
+    st = lib().oc_setup(A.n, _p(rp), _p(ci), _p(v), _p(ns), C.byref(p), C.byref(h))
+    if st != 0:
+        return None, int(st)
+    return Hierarchy(h, A.n), 0
+
+
+def prolongator_only(A, nullspace=None, **kw):
+    rp, ci, v = _arrs(A)
+    ns = None if nullspace is None else np.ascontiguousarray(nullspace, dtype=np.float64)
+    p = params(**kw)
+    h = C.c_void_p()
+    st = lib().oc_prolongator_only(A.n, _p(rp), _p(ci), _p(v), _p(ns), C.byref(p), C.byref(h))
+    if st != 0:
+        return None, int(st)
+    return Hierarchy(h, A.n), 0

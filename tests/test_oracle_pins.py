@@ -1,0 +1,674 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a worked example the
+paper prints (tests/golden/), a closed form, an invariant stated by a definition, a
+special case that reduces to a textbook or library routine, or brute force on tiny inputs.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2103_10476_gb300 import problems as P
+from tests.helpers import csr_from_dense, graph_csr, periodic_5pt, rows_of
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    out = {}
+    for line in open(os.path.join(GOLD, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        parts = line.split()
+        out[parts[0]] = parts[1:]
+    return out
+
+
+# ------------------------------------------------------------------ inputs
+
+def test_splitmix64_published_outputs():
+    # first outputs of SplitMix64 from state 0 (Steele, Lea, Flood 2014; Vigna's reference code)
+    z = P.splitmix64_stream(0, 3)
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_q1_stencil_matches_paper_worked_example():
+    g = _golden("q1_stretched_stencil.txt")
+    hz = np.sqrt(7.0) / 2.0
+    A = P.q1_matrix(np.ones(6), np.ones(6), np.full(6, hz))
+    row = P.dirichlet_stencil_row(A, 2, 2, 2)
+    scaled = {k: v * 36.0 * hz for k, v in row.items()}
+    cls = {
+        "diagonal": [k for k in scaled if k == (0, 0, 0)],
+        "corner": [k for k in scaled if all(abs(c) == 1 for c in k)],
+        "xz_or_yz_face": [k for k in scaled if abs(k[2]) == 1 and sum(abs(c) for c in k) == 2],
+        "z_edge": [k for k in scaled if k[0] == 0 and k[1] == 0 and abs(k[2]) == 1],
+        "xy_face": [k for k in scaled if k[2] == 0 and abs(k[0]) == 1 and abs(k[1]) == 1],
+        "x_or_y_edge": [k for k in scaled if k[2] == 0 and abs(k[0]) + abs(k[1]) == 1],
+    }
+    for name, (count, _formula, value) in g.items():
+        assert len(cls[name]) == int(count), name
+        for k in cls[name]:
+            assert scaled[k] == pytest.approx(float(value), abs=1e-12), name
+    # the closed forms in h_z at another spacing
+    for hz in (0.5, 1.0, 3.0):
+        A = P.q1_matrix(np.ones(6), np.ones(6), np.full(6, hz))
+        row = {k: v * 36 * hz for k, v in P.dirichlet_stencil_row(A, 2, 2, 2).items()}
+        assert row[(0, 0, 0)] == pytest.approx(32 + 64 * hz ** 2)
+        assert row[(1, 1, 1)] == pytest.approx(-1 - 2 * hz ** 2)
+        assert row[(1, 0, 1)] == pytest.approx(-4 - 2 * hz ** 2)
+        assert row[(0, 0, 1)] == pytest.approx(16 * hz ** 2 - 16, abs=1e-12)
+        assert row[(1, 1, 0)] == pytest.approx(2 - 8 * hz ** 2)
+        assert row[(1, 0, 0)] == pytest.approx(8 - 8 * hz ** 2, abs=1e-12)
+
+
+def test_generator_symmetric_and_neumann_rows_sum_to_zero():
+    A = P.random_coefficient_cube(7, 5)
+    S = A.to_scipy()
+    assert (S - S.T).count_nonzero() == 0 or abs(S - S.T).max() == 0.0
+    assert A.nnz == (3 * 7 - 2) ** 3
+    N = P.neumann_box(4, 5, 3, hz=2.5)
+    assert np.abs(N.to_dense().sum(1)).max() < 1e-13
+
+
+# ------------------------------------------------------------------ strength, Eq. (7)
+
+def test_strength_special_cases(oracle_lib):
+    O = oracle_lib
+    A = P.laplace_cube(5)
+    s0 = O.strength(A, 0.0)
+    offd = A.col != rows_of(A)
+    assert np.all(s0[offd] == 1) and np.all(s0[~offd] == 0)
+    # SPD: every 2x2 principal minor is positive, so |a_ij| < sqrt(a_ii a_jj) and theta = 1
+    # leaves nothing strong
+    s1 = O.strength(P.random_coefficient_cube(5, 1), 1.0)
+    assert s1.sum() == 0
+
+
+def test_strength_on_paper_stencil(oracle_lib):
+    # h_z = sqrt(7)/2: scaled stencil 144 | -4.5 -7.5 12 -12 -6 (every interior row has the
+    # same diagonal).  theta = 0.05 -> threshold 7.2: strong are -7.5 (8), 12 (2), -12 (4).
+    hz = np.sqrt(7.0) / 2.0
+    A = P.q1_matrix(np.ones(8), np.ones(8), np.full(8, hz))
+    s = oracle_lib.strength(A, 0.05)
+    nx = A.meta["grid"][0]
+    r = 3 + nx * (3 + nx * 3)
+    assert s[A.row_ptr[r]:A.row_ptr[r + 1]].sum() == 14
+    # theta = 0.08 -> threshold 11.52: strong are 12 (2) and -12 (4)
+    s = oracle_lib.strength(A, 0.08)
+    assert s[A.row_ptr[r]:A.row_ptr[r + 1]].sum() == 6
+
+
+# ------------------------------------------------------------------ filtered matrix, Eq. (6)
+
+def test_filter_preserves_row_sums_and_theta0_identity(oracle_lib):
+    O = oracle_lib
+    A = P.random_coefficient_cube(6, 3)
+    for theta in (0.0, 0.02, 0.1):
+        s = O.strength(A, theta)
+        removed = ((A.col != rows_of(A)) & (s == 0)).astype(np.uint8)
+        Ab, _ = O.filtered(A, removed, offlmp=False)
+        ra = np.add.reduceat(A.val, A.row_ptr[:-1])
+        rb = np.add.reduceat(Ab.val, Ab.row_ptr[:-1])
+        assert np.allclose(ra, rb, rtol=0, atol=1e-14 * np.abs(A.val).max())
+        if theta == 0.0:
+            assert np.array_equal(Ab.col, A.col) and np.array_equal(Ab.val, A.val)
+
+
+def test_filter_negative_diagonal_example(oracle_lib):
+    # §1.2: for h_z > sqrt(7)/2 the positive z-edge entry is the largest off-diagonal; keeping
+    # only it and lumping every other entry gives a negative filtered diagonal (rows sum to 0).
+    hz = 2.0
+    A = P.neumann_box(6, 6, 6, hz=hz)
+    r = 2 + 6 * (2 + 6 * 2)
+    b, e = A.row_ptr[r], A.row_ptr[r + 1]
+    v = A.val[b:e]
+    offd = A.col[b:e] != r
+    keep = offd & (v == v[offd].max())
+    assert keep.sum() == 2 and v[keep][0] > 0
+    removed = np.zeros(A.nnz, dtype=np.uint8)
+    removed[b:e] = (offd & ~keep)
+    Ab, _ = oracle_lib.filtered(A, removed)
+    dr = Ab.val[(Ab.col == r) & (rows_of(Ab) == r)][0]
+    assert dr < 0
+    assert dr == pytest.approx(-2 * v[keep][0], rel=1e-12)   # row sum zero
+
+
+# ------------------------------------------------------------------ OffLmp, Algorithm 2
+
+def _ddom(v, col, i):
+    d = v[col == i][0]
+    return np.abs(v[col != i]).sum() / abs(d)
+
+
+def _row_csr(vals, diag_pos=0):
+    """One-row-of-interest matrix: row 0 has the given entries (columns 0..m-1)."""
+    m = len(vals)
+    d = np.eye(m) * 10.0
+    d[0, :] = vals
+    return csr_from_dense(d, keep_zeros_pattern=np.ones((m, m), bool) & (np.arange(m)[None, :] >= 0) & (
+        np.arange(m)[:, None] == 0) | np.eye(m, dtype=bool))
+
+
+def test_offlmp_branches_hand_computed(oracle_lib):
+    O = oracle_lib
+    # r = +1 > 0: all to the diagonal
+    A = _row_csr([10.0, -3.0, 1.0, -4.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[2] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    assert fl[0] == 0 and Ab.val[0] == 11.0
+    # r = -1, kappa+ = 2 (entry 2): K+ absorbs it, delta = -1/2 -> 2 * 0.5 = 1
+    A = _row_csr([10.0, -1.0, 2.0, -4.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    assert fl[0] == 1
+    assert list(Ab.val[:3]) == [10.0, 1.0, -4.0]
+    # r = -3, kappa+ = 1: K+ zeroed, rhat = -2, K- = {-4}: N = 4 + 2 = 6 <= a_ii = 10 -> r* = 2
+    A = _row_csr([10.0, -3.0, 1.0, -4.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    assert fl[0] == 2
+    assert list(Ab.val[:3]) == [8.0, 0.0, -4.0]
+    # N > a_ii, feasible: a_ii = 2, kept K- = {-1}, removed -2 -> r = -2, rhat = -2, N = 3,
+    # D(A_i) = 3/2, t = 1.65; N <= t a_ii = 3.3; r* = (3.3 - 3)/(0.65) = 0.4615...
+    A = _row_csr([2.0, -2.0, -1.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    rstar = (1.1 * 1.5 * 2.0 - 3.0) / (1.1 * 1.5 - 1.0)
+    assert fl[0] == 2
+    assert Ab.val[0] == pytest.approx(2.0 - rstar, rel=1e-14)
+    assert Ab.val[1] == pytest.approx(-1.0 * (1 + (-2.0 + rstar) / -1.0), rel=1e-14)
+    # the growth bound is met with equality
+    assert _ddom(Ab.val[:2], Ab.col[:2], 0) == pytest.approx(1.1 * 1.5, rel=1e-12)
+    # N > t a_ii (possible only for tau < 1: N never exceeds D(A_i) a_ii): no feasible share,
+    # r* = 0, all of rhat to K-.  D(A_i) = 5.1, tau = 0.5 -> t a_ii = 2.55 < N = 5.1
+    A = _row_csr([1.0, -0.1, -5.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True, tau=0.5)
+    assert fl[0] == 2 and Ab.val[0] == 1.0 and Ab.val[1] == pytest.approx(-5.1)
+    # K- empty, K+ non-empty: spread over K+ (entry becomes negative)
+    A = _row_csr([10.0, -3.0, 1.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    assert fl[0] == 3 and Ab.val[1] == pytest.approx(-2.0)
+    # nothing kept: row left alone, flagged
+    A = _row_csr([10.0, -3.0])
+    rem = np.zeros(A.nnz, np.uint8); rem[1] = 1
+    Ab, fl = O.filtered(A, rem, offlmp=True)
+    assert fl[0] == 4 and Ab.val[0] == 10.0
+
+
+def test_offlmp_rstar_matches_brute_force_scan(oracle_lib):
+    """The closed-form diagonal share equals the largest feasible share found by scanning."""
+    rng = np.random.default_rng(7)
+    for trial in range(60):
+        m = 6
+        aii = rng.uniform(0.5, 3.0)
+        vals = np.concatenate([[aii], -rng.uniform(0.05, 2.0, m - 1)])
+        vals[rng.integers(1, m)] *= -1.0     # one positive entry
+        rem = np.zeros(m, np.uint8)
+        rem[1 + rng.choice(m - 1, size=2, replace=False)] = 1
+        A = _row_csr(list(vals))
+        remA = np.zeros(A.nnz, np.uint8); remA[:m] = rem
+        Ab, fl = oracle_lib.filtered(A, remA, offlmp=True)
+        if fl[0] != 2:
+            continue
+        # scan r in [0, |rhat|]
+        keep = (rem == 0) & (np.arange(m) > 0)
+        r = vals[rem == 1].sum()
+        kp = vals[keep & (vals > 0)].sum()
+        km = vals[keep & (vals < 0)].sum()
+        rhat = r + kp
+        t = 1.1 * np.abs(vals[1:]).sum() / aii
+        grid = np.linspace(0, -rhat, 20001)
+        grid = grid[grid < aii]
+        dd = (-km - rhat - grid) / (aii - grid)
+        feas = grid[dd <= t * (1 + 1e-12)]
+        best = feas.max() if len(feas) else grid[np.argmin(dd)]
+        rstar = aii - Ab.val[0]
+        assert rstar == pytest.approx(best, abs=(-rhat) / 20000 * 1.01 + 1e-12)
+        # row sum preserved
+        assert Ab.val[:Ab.row_ptr[1]].sum() == pytest.approx(vals.sum(), abs=1e-12)
+    del trial
+
+
+def test_offlmp_invariants_on_stretched_mesh(oracle_lib):
+    O = oracle_lib
+    A = P.stretched_box(8, 1.4)
+    s = O.strength(A, 0.02)
+    removed = ((A.col != rows_of(A)) & (s == 0)).astype(np.uint8)
+    Ab, fl = O.filtered(A, removed, offlmp=True, tau=1.1)
+    ra = np.add.reduceat(A.val, A.row_ptr[:-1])
+    rb = np.add.reduceat(Ab.val, Ab.row_ptr[:-1])
+    ok = fl != 4
+    assert np.allclose(ra[ok], rb[ok], atol=1e-13 * np.abs(A.val).max())
+    # growth bound where the diagonal-share branch found a feasible share
+    for i in np.nonzero(fl == 0)[0][:200]:
+        b, e = Ab.row_ptr[i], Ab.row_ptr[i + 1]
+        ba, ea = A.row_ptr[i], A.row_ptr[i + 1]
+        assert _ddom(Ab.val[b:e], Ab.col[b:e], i) <= _ddom(A.val[ba:ea], A.col[ba:ea], i) + 1e-12
+
+
+def test_offlmp_zero_sum_negative_rows_keep_ddom_one(oracle_lib):
+    # §2.3: D(A_i) = 1 for zero-sum rows with only negative off-diagonals, and lumping keeps 1
+    A = graph_csr(5, [(0, 1), (0, 2), (0, 3), (0, 4), (1, 2)], weights=[1, 2, 0.01, 0.02, 1], diag=0.0)
+    d = A.to_dense()
+    np.fill_diagonal(d, -d.sum(1))
+    A = csr_from_dense(d)
+    s = oracle_lib.strength(A, 0.1)
+    removed = ((A.col != rows_of(A)) & (s == 0)).astype(np.uint8)
+    assert removed.sum() > 0
+    Ab, fl = oracle_lib.filtered(A, removed, offlmp=True)
+    assert _ddom(A.val[:A.row_ptr[1]], A.col[:A.row_ptr[1]], 0) == pytest.approx(1.0)
+    assert _ddom(Ab.val[:Ab.row_ptr[1]], Ab.col[:Ab.row_ptr[1]], 0) == pytest.approx(1.0)
+
+
+# ------------------------------------------------------------------ aggregation
+
+def _dist2_adjacency(A, strong):
+    rows = rows_of(A)
+    G = sp.csr_matrix((np.ones(int(strong.sum())), (rows[strong == 1], A.col[strong == 1])), shape=(A.n, A.n))
+    G2 = (G + G @ G).tocsr()
+    G2.data[:] = 1
+    G2.setdiag(0)
+    G2.eliminate_zeros()
+    return G, G2
+
+
+def _lexfirst_mis_rounds(G2, keys):
+    """Round form of the greedy MIS: in each round every undecided vertex whose key is the
+    largest among its undecided distance-2 neighbours enters; their neighbours leave."""
+    n = G2.shape[0]
+    state = np.zeros(n, np.int8)   # 0 undecided, 1 in, -1 out
+    while (state == 0).any():
+        und = state == 0
+        best = np.zeros(n, dtype=bool)
+        for v in np.nonzero(und)[0]:
+            nb = G2.indices[G2.indptr[v]:G2.indptr[v + 1]]
+            nb = nb[und[nb]]
+            best[v] = (len(nb) == 0) or keys[v] > keys[nb].max()
+        state[best] = 1
+        for v in np.nonzero(best)[0]:
+            nb = G2.indices[G2.indptr[v]:G2.indptr[v + 1]]
+            state[nb[state[nb] == 0]] = -1
+    return state == 1
+
+
+@pytest.mark.parametrize("case", ["laplace", "stretched", "random"])
+def test_aggregation_roots_are_lexfirst_distance2_mis(oracle_lib, case):
+    O = oracle_lib
+    A = {"laplace": P.laplace_cube(6), "stretched": P.stretched_box(6, 1.5),
+         "random": P.random_coefficient_cube(6, 4)}[case]
+    theta = 0.0 if case == "laplace" else 0.05
+    strong = O.strength(A, theta)
+    for seed, level in ((0, 0), (12345, 2)):
+        agg, root, nagg = O.aggregate(A, strong, seed, level)
+        G, G2 = _dist2_adjacency(A, strong)
+        keys = np.array([O.priority(seed, level, i) for i in range(A.n)], dtype=np.uint64)
+        assert len(set(keys.tolist())) == A.n
+        expect = _lexfirst_mis_rounds(G2, keys)
+        assert np.array_equal(root.astype(bool), expect)
+        # independence at distance >= 3 and maximality
+        R = np.nonzero(root)[0]
+        assert G2[R][:, R].nnz == 0
+        covered = np.asarray((G2[:, R].sum(1) > 0)).ravel() | root.astype(bool)
+        assert covered.all()
+        # partition; aggregates numbered by increasing root index; each root in its aggregate
+        assert nagg == len(R) and agg.min() == 0 and agg.max() == nagg - 1
+        assert np.array_equal(agg[R], np.arange(nagg))
+        # neighbours of a root join a root (the adjacent one of largest priority)
+        Gd = G.tocsr()
+        for v in range(A.n):
+            if root[v]:
+                continue
+            nb = Gd.indices[Gd.indptr[v]:Gd.indptr[v + 1]]
+            rn = nb[root[nb] == 1]
+            if len(rn):
+                assert agg[v] == agg[rn[np.argmax(keys[rn])]]
+            else:
+                # distance-2 vertices join through a neighbour adjacent to a root
+                assert any(agg[u] == agg[v] for u in nb)
+
+
+def test_aggregation_isolated_vertices_are_singletons(oracle_lib):
+    A = csr_from_dense(np.diag([1.0, 2.0, 3.0]))
+    agg, root, nagg = oracle_lib.aggregate(A, oracle_lib.strength(A, 0.0))
+    assert nagg == 3 and root.all() and list(agg) == [0, 1, 2]
+
+
+# ------------------------------------------------------------------ tentative and smoothed prolongator
+
+def test_tentative_prolongator_orthonormal_and_reproduces_nullspace(oracle_lib):
+    A = P.random_coefficient_cube(6, 9)
+    B = 1.0 + np.arange(A.n) % 7 * 0.25
+    h, st = oracle_lib.prolongator_only(A, B, theta=0.02, variants=0, lambda_override=1e300)
+    assert st == 0
+    lv = h.level(0)
+    agg, nagg = lv["agg"], lv["nagg"]
+    Bc = np.zeros(nagg)
+    np.add.at(Bc, agg, B ** 2)
+    Bc = np.sqrt(Bc)
+    Pt = sp.csr_matrix((B / Bc[agg], (np.arange(A.n), agg)), shape=(A.n, nagg))
+    assert abs((Pt.T @ Pt - sp.eye(nagg)).toarray()).max() < 1e-14
+    assert np.allclose(Pt @ Bc, B, rtol=1e-15, atol=0)
+    # with omega -> 0 (huge lambda) the smoothed P equals Pt
+    Pd = lv["P"].to_dense(nagg)
+    assert abs(Pd - Pt.toarray()).max() < 1e-15
+
+
+@pytest.mark.parametrize("variants", [0, 1, 2, 3, 4, 8, 15])
+def test_smoothed_prolongator_equals_dense_product(oracle_lib, variants):
+    A = P.stretched_box(5, 1.6)
+    h, st = oracle_lib.prolongator_only(A, None, theta=0.02, variants=variants, pt_unit=1)
+    assert st == 0
+    lv = h.level(0)
+    nagg = lv["nagg"]
+    Ab = lv["Abar"].to_dense()
+    Pt = np.zeros((A.n, nagg)); Pt[np.arange(A.n), lv["agg"]] = 1.0
+    Pd = (np.eye(A.n) - lv["omega"] * np.diag(1.0 / lv["Dsm"]) @ Ab) @ Pt
+    Po = lv["P"].to_dense(nagg)
+    if variants & 8:
+        # Algorithm 3 changes rows; the others must equal the product
+        touched = lv["cflag"] != 0
+        clipped = np.abs(Po - Pd).max(1) > 1e-12
+        rows_ok = ~clipped | touched | ((Pd < 0) | (Pd > 1)).any(1)
+        assert rows_ok.all()
+        assert (Po >= -1e-15).all() and (Po <= 1 + 1e-15).all()
+    else:
+        assert np.abs(Po - Pd).max() <= 1e-14 * max(1.0, np.abs(Pd).max())
+    # pattern: the aggregates of the columns of Abar's rows
+    for i in range(0, A.n, 7):
+        b, e = lv["Abar"].row_ptr[i], lv["Abar"].row_ptr[i + 1]
+        want = np.unique(lv["agg"][lv["Abar"].col[b:e]])
+        got = lv["P"].col[lv["P"].row_ptr[i]:lv["P"].row_ptr[i + 1]]
+        assert np.array_equal(want, got)
+
+
+def test_smoothed_prolongator_interpolates_constant_where_row_sum_zero(oracle_lib):
+    # With B = 1, unit Pt: P 1 = 1 - omega D^-1 (Abar 1) and Abar keeps A's row sums, so
+    # P 1 = 1 on every row where A's row sum is zero (§1.1)
+    A = P.neumann_box(6, 5, 4, hz=1.7)
+    h, st = oracle_lib.prolongator_only(A, None, theta=0.03, variants=0, pt_unit=1)
+    lv = h.level(0)
+    Psum = np.add.reduceat(lv["P"].val, lv["P"].row_ptr[:-1])
+    assert np.abs(Psum - 1.0).max() < 1e-12
+
+
+def test_1norm_equals_traditional_on_circulant(oracle_lib):
+    g = _golden("circulant_5pt.txt")
+    A = periodic_5pt(6)
+    hT, st = oracle_lib.prolongator_only(A, None, theta=0.0, variants=0, pt_unit=1,
+                                         lambda_override=float(g["lambda_bar"][0]))
+    h1, st1 = oracle_lib.prolongator_only(A, None, theta=0.0, variants=1, pt_unit=1)
+    assert st == 0 and st1 == 0
+    lt, l1 = hT.level(0), h1.level(0)
+    assert np.all(lt["Dsm"] == float(g["Dbar"][0]))
+    assert np.all(l1["Dsm"] == float(g["Dtilde"][0]))
+    assert l1["lambda_bar"] == float(g["lambda_tilde"][0])
+    assert np.array_equal(lt["P"].col, l1["P"].col)
+    assert np.abs(lt["P"].val - l1["P"].val).max() < 1e-14
+    # Gershgorin (§2.1): the power-method estimate of lambda(Dtilde^-1 Abar) is at most 1
+    lam = oracle_lib.power_lambda(A, l1["Dsm"], 30, 99)
+    assert lam <= 1.0 + 1e-12 and lam > 0.9
+
+
+def test_diagonal_filtered_matrix_root_values(oracle_lib):
+    g = _golden("diagonal_filtered.txt")
+    A = csr_from_dense(np.diag([2.0, 3.0, 5.0]))
+    h, _ = oracle_lib.prolongator_only(A, None, variants=0, pt_unit=1, lambda_override=1.0)
+    assert np.allclose(h.level(0)["P"].val, float(g["unsafeguarded_root_value"][0]), rtol=1e-15)
+    h, _ = oracle_lib.prolongator_only(A, None, variants=1, pt_unit=1)
+    assert np.allclose(h.level(0)["P"].val, float(g["safeguarded_root_value"][0]), rtol=1e-15)
+
+
+def test_1norm_root_value_closed_form(oracle_lib):
+    # §2.2: when every neighbour of row i lies in one aggregate, P_ij = 1 - (4/3) s_i / Dtilde_ii
+    d = np.array([[3.0, -1.0, 0.0], [-1.0, 2.0, -1.0], [0.0, -1.0, 2.5]])
+    A = csr_from_dense(d)
+    h, st = oracle_lib.prolongator_only(A, None, theta=0.0, variants=1, pt_unit=1)
+    lv = h.level(0)
+    assert lv["nagg"] == 1
+    s = d.sum(1)
+    Dt = np.maximum(np.abs(d).sum(1), 2 * s)
+    assert np.allclose(lv["P"].val, 1 - (4.0 / 3.0) * s / Dt, rtol=1e-15)
+
+
+# ------------------------------------------------------------------ Algorithm 3
+
+def test_constrain_row_cases(oracle_lib):
+    O = oracle_lib
+    # infeasible: negative row sum -> tentative row
+    p, c = O.constrain_row([0.2, -0.5, 0.1], 0, 1.0)
+    assert c == 2 and list(p) == [1.0, 0.0, 0.0]
+    # zero row sum -> zero row
+    p, c = O.constrain_row([0.5, -0.5, 0.0], 1, 1.0)
+    assert c == 1 and not p.any()
+    # row sum above the number of nonzeros -> tentative row
+    p, c = O.constrain_row([1.5, 1.2, 0.0], 1, 1.0)
+    assert c == 2 and list(p) == [0.0, 1.0, 0.0]
+    # hand-worked: [1.5, .25, -.25]: pin 1.5 -> 1 and -.25 -> 0, remainder .25 to entry 1
+    p, c = O.constrain_row([1.5, 0.25, -0.25], 0, 1.0)
+    assert c == 0 and list(p) == [1.0, 0.5, 0.0]
+    # already feasible rows are untouched
+    p, c = O.constrain_row([0.3, 0.7, 0.0, 1.0], 0, 1.0)
+    assert c == 0 and list(p) == [0.3, 0.7, 0.0, 1.0]
+
+
+def test_constrain_row_invariants_random(oracle_lib):
+    rng = np.random.default_rng(3)
+    for _ in range(500):
+        m = int(rng.integers(1, 12))
+        p0 = rng.normal(0.4, 0.6, m)
+        p0[rng.random(m) < 0.2] = 0.0
+        p, c = oracle_lib.constrain_row(p0, 0, 1.0)
+        if c == 0:
+            assert (p >= 0).all() and (p <= 1).all()
+            assert p.sum() == pytest.approx(p0.sum(), abs=1e-12)
+            assert np.all((p0 == 0) <= (p == 0))       # pattern does not grow
+        elif c == 2:
+            # infeasible (up front, or the working set emptied): the tentative row
+            assert p[0] == 1.0 and not p[1:].any()
+        else:
+            assert p0.sum() == 0.0 and not p.any()
+
+
+# ------------------------------------------------------------------ §2.5 sparsification
+
+def _two_columns(extra_links):
+    # a_top=0, a_mid=1, a_bot=2, b_top=3, b_mid=4, b_bot=5; strong vertical links, weak
+    # horizontal links a_k - b_k, and strong extra horizontal links
+    n = 6
+    d = np.zeros((n, n))
+    for (u, v) in ((0, 1), (1, 2), (3, 4), (4, 5)):
+        d[u, v] = d[v, u] = -1.0
+    for k in range(3):
+        d[k, 3 + k] = d[3 + k, k] = -0.001
+    for (u, v) in extra_links:
+        d[u, v] = d[v, u] = -1.0
+    np.fill_diagonal(d, 4.0)
+    return csr_from_dense(d)
+
+
+def _seed_for_roots(O, A, strong, want):
+    for seed in range(500):
+        agg, root, nagg = O.aggregate(A, strong, seed, 0)
+        if set(np.nonzero(root)[0]) == want:
+            return seed, agg, root, nagg
+    raise AssertionError("no seed gives the wanted roots")
+
+
+def test_sprsfy_prunes_lone_strong_link(oracle_lib):
+    O = oracle_lib
+    A = _two_columns([(2, 5)])
+    strong = O.strength(A, 0.1)
+    seed, agg, root, nagg = _seed_for_roots(O, A, strong, {1, 4})
+    removed = ((A.col != rows_of(A)) & (strong == 0)).astype(np.uint8)
+    rem2, npr = O.sprsfy_mark(A, strong, agg, root, nagg, removed)
+    rows = rows_of(A)
+    newly = (rem2 == 1) & (removed == 0)
+    pairs = {(int(rows[e]), int(A.col[e])) for e in np.nonzero(newly)[0]}
+    assert pairs == {(2, 5), (5, 2)}
+    # two strong links into the same aggregate: kept
+    A = _two_columns([(2, 5), (0, 3)])
+    strong = O.strength(A, 0.1)
+    seed, agg, root, nagg = _seed_for_roots(O, A, strong, {1, 4})
+    removed = ((A.col != rows_of(A)) & (strong == 0)).astype(np.uint8)
+    rem2, npr = O.sprsfy_mark(A, strong, agg, root, nagg, removed)
+    assert np.array_equal(rem2, removed) and npr == 0
+
+
+def test_sprsfy_invariants(oracle_lib):
+    A = P.stretched_box(7, 1.5)
+    for variants in (4, 6):
+        h0, _ = oracle_lib.prolongator_only(A, None, theta=0.05, variants=variants & ~4)
+        h1, _ = oracle_lib.prolongator_only(A, None, theta=0.05, variants=variants)
+        l0, l1 = h0.level(0), h1.level(0)
+        assert np.array_equal(l0["agg"], l1["agg"])           # aggregates unchanged
+        Ab = l1["Abar"]
+        S = sp.csr_matrix((np.ones(Ab.nnz), Ab.col, Ab.row_ptr), shape=(A.n, A.n))
+        assert (S != S.T).nnz == 0                              # structurally symmetric
+        assert l1["Abar"].nnz <= l0["Abar"].nnz
+        ra = np.add.reduceat(A.val, A.row_ptr[:-1])
+        rb = np.add.reduceat(Ab.val, Ab.row_ptr[:-1])
+        ok = l1["lumpflag"] != 4
+        assert np.allclose(ra[ok], rb[ok], atol=1e-13 * np.abs(A.val).max())
+
+
+# ------------------------------------------------------------------ products, Galerkin, solve
+
+def test_spgemm_and_transpose_match_scipy(oracle_lib):
+    A = P.random_coefficient_cube(5, 11)
+    S = A.to_scipy()
+    C = oracle_lib.spgemm(A, A, A.n)
+    ref = (S @ S).tocsr(); ref.sort_indices()
+    assert np.array_equal(C.row_ptr, ref.indptr) and np.array_equal(C.col, ref.indices)
+    assert np.abs(C.val - ref.data).max() <= 1e-13 * np.abs(ref.data).max()
+    rect = sp.random(40, 13, density=0.2, random_state=1, format="csr")
+    from paper_2103_10476_gb300.problems import CSR
+    Rc = CSR(40, rect.indptr.astype(np.int64), rect.indices.astype(np.int32), rect.data)
+    T = oracle_lib.transpose(Rc, 13)
+    tr = rect.T.tocsr(); tr.sort_indices()
+    assert np.array_equal(T.row_ptr, tr.indptr) and np.array_equal(T.col, tr.indices)
+    assert np.array_equal(T.val, tr.data)
+
+
+@pytest.mark.parametrize("variants", [0, 3, 4, 8])
+def test_galerkin_symmetric_and_equals_dense(oracle_lib, variants):
+    A = P.stretched_box(6, 1.4)
+    h, st = oracle_lib.setup(A, theta=0.02, variants=variants, max_coarse=10)
+    assert st == 0 and h.nlevels >= 2
+    for l in range(h.nlevels - 1):
+        lv, nx = h.level(l), h.level(l + 1)
+        Ad, Pd = lv["A"].to_dense(), lv["P"].to_dense(lv["nagg"])
+        Ac = nx["A"].to_dense()
+        ref = Pd.T @ Ad @ Pd
+        assert np.abs(Ac - ref).max() <= 1e-12 * np.abs(ref).max()
+        S = sp.csr_matrix((np.ones(nx["A"].nnz), nx["A"].col, nx["A"].row_ptr), shape=Ac.shape)
+        assert (S != S.T).nnz == 0
+        assert np.abs(Ac - Ac.T).max() <= 1e-13 * np.abs(Ac).max()
+        # R is the transpose of P
+        assert np.array_equal(lv["R"].to_dense(lv["A"].n), Pd.T)
+
+
+def test_galerkin_annihilates_constant_on_neumann(oracle_lib):
+    A = P.neumann_box(9, 8, 7, hz=1.3)
+    h, st = oracle_lib.setup(A, theta=0.0, variants=0, pt_unit=1, max_coarse=20, max_levels=2)
+    # the coarsest (singular) factorisation fails; read level 1 through prolongator + product
+    hp, _ = oracle_lib.prolongator_only(A, None, theta=0.0, variants=0, pt_unit=1)
+    lv = hp.level(0)
+    Pd = lv["P"].to_dense(lv["nagg"])
+    Ac = Pd.T @ A.to_dense() @ Pd
+    assert np.abs(Ac.sum(1)).max() <= 1e-12 * np.abs(Ac).max()
+    assert st == 6   # the singular coarse operator is reported, not factorised
+    # the oracle's own product agrees
+    AP = oracle_lib.spgemm(A, lv["P"], lv["nagg"])
+    Ac2 = oracle_lib.spgemm(lv["R"], AP, lv["nagg"]).to_dense()
+    assert np.abs(Ac2.sum(1)).max() <= 1e-12 * np.abs(Ac2).max()
+
+
+def test_cholesky_matches_numpy(oracle_lib):
+    rng = np.random.default_rng(0)
+    M = rng.normal(size=(30, 30))
+    a = M @ M.T + 30 * np.eye(30)
+    l, st = oracle_lib.cholesky(a)
+    assert st == 0 and np.abs(l - np.linalg.cholesky(a)).max() < 1e-12
+    a[5, 5] = -1.0
+    _, st = oracle_lib.cholesky(a)
+    assert st == 6
+
+
+def test_cg_without_preconditioner_is_textbook_cg(oracle_lib):
+    A = P.laplace_cube(6)
+    b = P.rhs_uniform(A.n, 3)
+    Ad = A.to_dense()
+    for k in (1, 3, 7):
+        x, info = oracle_lib.pcg_plain(A, b, 1e-30, k)
+        # textbook CG (Hestenes-Stiefel) in dense arithmetic
+        xr = np.zeros(A.n); r = b.copy(); p = r.copy(); rr = r @ r
+        for _ in range(k):
+            q = Ad @ p; a = rr / (p @ q); xr += a * p; r -= a * q
+            rr2 = r @ r; p = r + (rr2 / rr) * p; rr = rr2
+        assert np.abs(x - xr).max() <= 1e-12 * np.abs(xr).max()
+
+
+@pytest.mark.parametrize("variants", [0, 1, 2, 8])
+def test_pcg_anorm_error_decreases(oracle_lib, variants):
+    A = P.stretched_box(7, 1.3)
+    b = P.rhs_uniform(A.n, 1)
+    h, st = oracle_lib.setup(A, theta=0.02, variants=variants, max_coarse=20)
+    assert st == 0
+    xs = np.linalg.solve(A.to_dense(), b)
+    Ad = A.to_dense()
+    errs = []
+    _, info, _ = h.solve(b, 1e-10)
+    for k in range(1, info.iters + 1):
+        hk, _ = oracle_lib.setup(A, theta=0.02, variants=variants, max_coarse=20, max_iter=k)
+        x, _, _ = hk.solve(b, 1e-10)
+        e = x - xs
+        errs.append(np.sqrt(e @ Ad @ e))
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+    assert errs[-1] / np.sqrt(xs @ Ad @ xs) < 1e-8
+
+
+def test_vcycle_is_symmetric_positive_definite(oracle_lib):
+    A = P.random_coefficient_cube(8, 6)
+    h, st = oracle_lib.setup(A, theta=0.02, variants=3, max_coarse=30)
+    assert st == 0 and h.nlevels >= 2
+    rng = np.random.default_rng(1)
+    v, w = rng.normal(size=A.n), rng.normal(size=A.n)
+    Mv, Mw = h.vcycle(v), h.vcycle(w)
+    assert w @ Mv == pytest.approx(v @ Mw, rel=1e-10)
+    assert v @ Mv > 0 and w @ Mw > 0
+
+
+def test_single_level_hierarchy_solves_in_one_iteration(oracle_lib):
+    A = P.laplace_cube(6)
+    b = P.rhs_uniform(A.n, 0)
+    h, st = oracle_lib.setup(A, max_coarse=500)
+    assert st == 0 and h.nlevels == 1
+    x, info, st = h.solve(b, 1e-8)
+    assert st == 0 and info.iters == 1 and info.relres_true < 1e-12
+
+
+def test_power_method_dominant_eigenvalue(oracle_lib):
+    # D = I, A with eigenvalues {10, 1, ..., 1}: ten sweeps reach 10 to ~1e-18 relative
+    n = 50
+    rng = np.random.default_rng(2)
+    Q, _ = np.linalg.qr(rng.normal(size=(n, n)))
+    lam = np.ones(n); lam[0] = 10.0
+    a = (Q * lam) @ Q.T
+    A = csr_from_dense(a)
+    est = oracle_lib.power_lambda(A, np.ones(n), 10, 5)
+    assert est == pytest.approx(10.0, rel=1e-12)
+
+
+def test_dropping_breaks_traditional_sa_but_not_1norm_or_offlmp(oracle_lib):
+    # §1.2 / §3.1: magnitude-based dropping on stretched hexahedra can leave filtered diagonals
+    # that are zero or negative, which breaks the traditional smoothing step (reported as a
+    # status, not a crash); the 1-norm diagonal and the alternative lumping avoid it.
+    A = P.stretched_box(10, 1.1)
+    st = {v: oracle_lib.setup(A, theta=0.2, variants=v)[1] for v in (0, 1, 2)}
+    assert st[0] in (4, 5)
+    assert st[1] == 0 and st[2] == 0
