@@ -1,0 +1,406 @@
+"""Benchmark: SA-AMG hierarchy setup + PCG solve to 1e-8 relative residual on one GB300.
+
+Workload (default): Q1 finite-element Laplacian on a 64^3-node box mesh whose z spacing
+grows by 1.1 per element layer (aspect ratios 1 to ~1:446), strength threshold 0.02, right-
+hand side uniform in [-1, 1) (seed 1); one step = setup + solve for each of the five methods
+{traditional SA, 1Norm, OffLmp, Sprsfy, Cnstrnt} in FP64.  Synthetic inputs stand in for the
+paper's meshes (which are not available).
+
+Prints one JSON line (rank 0): solves/s over the timed steps (inputs resident in HBM), the
+end-to-end number through the C ABI with host buffers, the roofline of the dominant timed
+kernel class, the oracle timed on the host cores, and the SM clocks sampled during the
+timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload stretched64|randcoef128|laplace20] [--precision fp64|mixed]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SA-AMG setup+PCG solve s to 1e-8 rel-res, FP64 vs mixed; solves/s; p99 latency"
+TOL = 1e-8
+VARIANT_SETS = {
+    "stretched64": [("traditional", 0), ("1norm", 1), ("offlmp", 2), ("sprsfy", 4), ("cnstrnt", 8)],
+    "randcoef128": [("1norm+offlmp", 3)],
+    "laplace20": [("traditional", 0)],
+}
+L2_BYTES = 129 * 1024 * 1024
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(name: str):
+    from paper_2103_10476_gb300 import problems as P
+    if name == "stretched64":
+        A, b, cfg = P.workload_stretched64()
+        theta = 0.02
+    elif name == "randcoef128":
+        A, b, cfg = P.workload_randcoef128()
+        theta = 0.02
+    elif name == "laplace20":
+        A, b, cfg = P.workload_laplace20()
+        theta = 0.0
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return A, b, theta
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9], parts[3]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for nm, flag in zip(names, r[2]):
+                if flag.lower() in ("active", "1", "yes"):
+                    seen.add(nm)
+        sm = sorted(r[0] for r in rows)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows), "reasons": sorted(seen),
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2103_10476_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kclass_name: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(workload, {}).get(kclass_name)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------------------ CPU baseline / reference arm
+
+def oracle_sample(A, b, theta, variants, budget_s: float):
+    """Times the oracle (as it stands) on whole setup+solve runs of the workload's methods,
+    cycling through them until about budget_s seconds have passed.  Returns (solves, seconds,
+    description)."""
+    import oracle
+    oracle.build()
+    done = 0
+    t0 = time.perf_counter()
+    names = []
+    k = 0
+    while True:
+        name, v = variants[k % len(variants)]
+        h, st = oracle.setup(A, theta=theta, variants=v)
+        if h is not None:
+            h.solve(b, TOL)
+            del h
+        done += 1
+        names.append(name)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (el / done) * (done + 1) > 2.5 * budget_s:
+            break
+    return done, time.perf_counter() - t0, names
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    A, b, theta = make_workload(args.workload)
+    variants = VARIANT_SETS[args.workload]
+    # the oracle keeps no state between runs, so warm-up steps are not run (bounds the wall time)
+    budget = float(os.environ.get("REF_STEP_BUDGET_S", "4"))
+    solves = 0
+    secs = 0.0
+    per = []
+    for k in range(args.steps):
+        n, s, names = oracle_sample(A, b, theta, variants[k % len(variants):] + variants[:k % len(variants)], budget)
+        solves += n
+        secs += s
+        per.append(s / n)
+    value = solves / secs
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{solves} oracle setup+solve runs of the workload's methods, "
+                                   f"each step about {budget:.0f} s, single thread, host has {os.cpu_count()} cores"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": 1000 * statistics.median(per), "p99_ms": 1000 * max(per),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    desc = {
+        "stretched64": "Q1 FE Laplacian, 64^3 interior nodes, z spacing x1.1 per layer, theta=0.02; "
+                       "5 methods (traditional, 1Norm, OffLmp, Sprsfy, Cnstrnt) per step",
+        "randcoef128": "Q1 FE diffusion, 128^3 interior nodes, coefficient 10^U(-3,3), theta=0.02, 1Norm+OffLmp",
+        "laplace20": "Q1 FE Laplacian, 20^3 interior nodes, theta=0",
+    }[args.workload]
+    return {"workload": args.workload, "description": desc, "precision": args.precision, "tol": TOL,
+            "rhs": "uniform[-1,1) SplitMix64", "l2": "flushed (256 MiB write) before every timed step",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------------------ our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stretched64", choices=sorted(VARIANT_SETS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    world, rank, local = dist_init()
+
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2103_10476_gb300 import amg
+
+    A, b, theta = make_workload(args.workload)
+    variants = VARIANT_SETS[args.workload]
+    prec = amg.AMG_MIXED if args.precision == "mixed" else amg.AMG_FP64
+    stream = torch.cuda.current_stream()
+    params = [amg.amg_params_default(theta=theta, variants=v, precision=prec, cuda_stream=stream.cuda_stream)
+              for _, v in variants]
+    # device-resident inputs
+    rp_d = torch.from_numpy(A.row_ptr).cuda()
+    ci_d = torch.from_numpy(A.col).cuda()
+    v_d = torch.from_numpy(A.val).cuda()
+    b_d = torch.from_numpy(b).cuda()
+    x_d = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    arg_d = amg.csr_arg(A.n, rp_d, ci_d, v_d)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    per_solve_ms = []
+    iters = {}
+    statuses = {}
+
+    def step(record=False):
+        for (name, _), p in zip(variants, params):
+            t0 = time.perf_counter()
+            h, st = amg.amg_setup_status(arg_d, None, p)
+            if h is None:
+                statuses[name] = amg.amg_status_string(st)
+                continue
+            info = amg.amg_solve(h, b_d, x_d, TOL)
+            amg.amg_free(h)
+            if record:
+                per_solve_ms.append(1000 * (time.perf_counter() - t0))
+                iters[name] = info.iters
+                statuses[name] = amg.amg_status_string(info.status)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = amg.amg_launch_count()
+    amg.amg_profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev0[k].record(stream)
+            step(record=True)
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    launches = amg.amg_launch_count() - launches0
+    prof = {k: amg.amg_profile_read(k) for k in (amg.KC_PCG_SPMV, amg.KC_VCYCLE_SPMV, amg.KC_SPGEMM)}
+    amg.amg_profile_enable(False)
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
+    total_ms = max_over_ranks(world, sum(step_ms))
+    solves_per_step = len(variants)
+    value = solves_per_step * args.steps * world / (total_ms / 1000.0)
+
+    # end to end through the C ABI with host buffers (host -> device copy of the matrix and the
+    # right-hand side inside every step, device -> host copy of the solution)
+    arg_h = amg.csr_arg(A.n, A.row_ptr, A.col, A.val)
+    b_h = torch.from_numpy(b).pin_memory()
+    x_h = torch.zeros(A.n, dtype=torch.float64).pin_memory()
+    rp_h = torch.from_numpy(A.row_ptr).pin_memory()
+    ci_h = torch.from_numpy(A.col).pin_memory()
+    val_h = torch.from_numpy(A.val).pin_memory()
+    arg_h = amg.csr_arg(A.n, rp_h, ci_h, val_h)
+    e2e_steps = max(1, args.steps // 2)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        for p in params:
+            h, st = amg.amg_setup_status(arg_h, None, p)
+            if h is None:
+                continue
+            amg.amg_solve(h, b_h, x_h, TOL)
+            amg.amg_free(h)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te
+    e2e_value = solves_per_step * e2e_steps * world / max_over_ranks(world, te)
+    h2d = solves_per_step * (8 * (A.n + 1) + 12 * A.nnz + 8 * A.n)
+    d2h = solves_per_step * 8 * A.n
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant timed kernel class
+    peak, peak_src = measured_peaks()
+    names = {amg.KC_PCG_SPMV: "pcg_spmv_fp64", amg.KC_VCYCLE_SPMV: "vcycle_fine_spmv", amg.KC_SPGEMM: "galerkin_spgemm"}
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_l, ms_l, by_l = prof[dom]
+    achieved = (by_l / (ms_l / 1000.0)) / 1e9 if ms_l > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "launches": n_l,
+                "avg_launch_us": 1000.0 * ms_l / max(n_l, 1), "bytes_per_launch": by_l / max(n_l, 1),
+                "traffic": ncu_traffic(names[dom], args.workload),
+                "classes": {names[k]: {"launches": prof[k][0], "ms": prof[k][1],
+                                       "GBps": (prof[k][2] / (prof[k][1] / 1000.0) / 1e9) if prof[k][1] > 0 else None}
+                            for k in prof}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_s, secs, done = oracle_sample(A, b, theta, variants, args.cpu_budget)
+        cpu = {"value": n_s / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_s} whole setup+solve runs ({', '.join(done)}) of the same workload, single-threaded C "
+                         f"oracle, {secs:.1f} s; host has {os.cpu_count()} cores"}
+
+    lat = sorted(per_solve_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == amg.AMG_FP64 else "f64+f32", "data": "synthetic",
+        "config": workload_config(args),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "p50_ms": lat[len(lat) // 2] if lat else None,
+        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+        "iters": iters, "status": statuses, "wall_s": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

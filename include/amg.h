@@ -1,0 +1,185 @@
+/*
+ * amg.h -- C ABI of the GB300 (sm_103a) smoothed-aggregation AMG library.
+ *
+ * The library builds a smoothed-aggregation multigrid hierarchy for a sparse symmetric
+ * positive definite matrix and solves A x = b with conjugate gradients preconditioned by
+ * one V-cycle per iteration.  It follows Hu, Siefert and Tuminaro, "Smooth Aggregation for
+ * Difficult Stretched Mesh and Coefficient Variation Problems" (arXiv:2103.10476):
+ *   - the problem A_1 u_1 = f_1 and the V-cycle: §1.1, Eq. (1) and Algorithm 1;
+ *   - Galerkin coarse operators A_{l+1} = P_l^T A_l P_l: §1.1, Eq. (2);
+ *   - smoothed prolongator P = (I - omega D^-1 Abar) Pt, omega = 4 / (3 lambda): Eq. (3);
+ *   - aggregates (Eq. 4), tentative prolongator from the near-null space (Eq. 5),
+ *     filtered matrix (Eq. 6) and the strength test |a_ij| >= theta sqrt(a_ii a_jj) (Eq. 7);
+ *   - the four adaptations, each switchable: 1Norm (§2.1-§2.2, Eq. 9-11), OffLmp (§2.3,
+ *     Algorithm 2), Cnstrnt (§2.4, Algorithm 3) and Sprsfy (§2.5);
+ *   - Chebyshev smoothing on [lambda/10, lambda] with lambda from ten power-method sweeps,
+ *     and a direct solve on the coarsest level (§3.1).
+ *
+ * Every step runs in this library's CUDA kernels on the current device.  All functions
+ * return an amg_status_t; no C++ exception crosses the ABI.  A handle is not thread-safe:
+ * calls on one handle must not overlap.  Different handles are independent.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_ERR_INVALID_ARG = 1,    /* bad pointer, size, parameter or matrix structure          */
+    AMG_ERR_OOM = 2,            /* device allocation failed                                   */
+    AMG_ERR_CUDA = 3,           /* a CUDA runtime call failed (see amg_last_error)            */
+    AMG_ERR_ZERO_DIAG = 4,      /* a zero diagonal in the filtered or level matrix            */
+    AMG_ERR_EIGEN = 5,          /* eigenvalue estimate <= 0 or not finite (§3.1's failure)    */
+    AMG_ERR_COARSE_NOT_SPD = 6, /* Cholesky pivot <= 0 on the coarsest level                  */
+    AMG_ERR_NOT_CONVERGED = 7,  /* PCG reached max_iter; x holds the last iterate             */
+    AMG_ERR_BUDGET = 8,         /* a memory budget would be exceeded                          */
+    AMG_ERR_UNSUPPORTED = 9,    /* size beyond the library's limits                           */
+    AMG_ERR_INTERNAL = 10       /* a kernel reported an internal limit (e.g. hash overflow)   */
+} amg_status_t;
+
+/* adaptation bits (0 = traditional smoothed aggregation) */
+enum { AMG_VAR_1NORM = 1, AMG_VAR_OFFLMP = 2, AMG_VAR_SPRSFY = 4, AMG_VAR_CNSTRNT = 8 };
+/* arithmetic of the hierarchy and V-cycle: FP64 throughout, or FP32 levels and V-cycle
+ * inside an FP64 conjugate-gradient iteration (outer residual, dot products, eigenvalue
+ * estimates and the coarsest factorisation stay FP64) */
+enum { AMG_FP64 = 0, AMG_MIXED = 1 };
+/* tentative-prolongator columns: divided by the 2-norm of the near-null space on the
+ * aggregate (orthonormal), or Eq. (5) as printed (unit) */
+enum { AMG_PT_ORTHONORMAL = 0, AMG_PT_UNIT = 1 };
+/* eigenvalue used with the 1-norm diagonal: the bound 1 (§2.1) or the power method */
+enum { AMG_LAMBDA_ONE = 0, AMG_LAMBDA_POWER = 1 };
+
+/* Square CSR matrix.  row_ptr has n+1 entries (row_ptr[0] = 0), columns are sorted
+ * ascending within each row with no duplicates, and every row stores its diagonal.
+ * on_device = 1: the three arrays are device pointers; 0: host pointers.  The library
+ * copies the matrix; the caller keeps ownership of these arrays. */
+typedef struct {
+    int64_t n, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    int on_device;
+} amg_csr_t;
+
+typedef struct {
+    double theta;        /* strength threshold of Eq. (7), in [0, 1]; 0 keeps every entry   */
+    unsigned variants;   /* AMG_VAR_* bits                                                   */
+    double tau;          /* OffLmp growth factor (1.1)                                       */
+    double sigma;        /* 1Norm safeguard minimum root value (1/3)                         */
+    int cheb_degree;     /* Chebyshev degree (2)                                             */
+    double cheb_ratio;   /* Chebyshev interval [lambda/ratio, lambda] (10)                   */
+    int power_iters;     /* power-method sweeps (10)                                         */
+    int max_coarse;      /* stop coarsening at or below this size (500)                      */
+    int max_levels;      /* (10)                                                             */
+    int precision;       /* AMG_FP64 or AMG_MIXED                                            */
+    int pt_scaling;      /* AMG_PT_ORTHONORMAL or AMG_PT_UNIT                                */
+    int onenorm_lambda;  /* AMG_LAMBDA_ONE or AMG_LAMBDA_POWER                               */
+    int max_iter;        /* PCG iteration limit (1000)                                       */
+    uint64_t seed;       /* aggregation priorities and power-method start vectors (0)        */
+    double lambda_override; /* > 0: prolongator-smoothing eigenvalue on every level (tests)  */
+    void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream         */
+} amg_params_t;
+
+typedef struct {
+    int iters;           /* PCG iterations (matrix-vector products with A)                   */
+    int status;          /* amg_status_t of the call                                         */
+    double relres_true;  /* ||b - A x|| / ||b|| recomputed in FP64 at exit                    */
+    double setup_ms;     /* wall time of amg_setup                                           */
+    double solve_ms;     /* wall time of this amg_solve                                      */
+    int levels;
+    double op_complexity;/* sum of nnz(A_l) / nnz(A_1)                                       */
+} amg_info_t;
+
+typedef struct amg_hierarchy *amg_handle_t;
+
+/* Defaults listed above. */
+void amg_params_default(amg_params_t *p);
+
+/* Builds the hierarchy (Eq. 2-7 and §2 per level, then the coarsest factorisation).
+ * nullspace: n values on the host or the device, or NULL for the constant vector.
+ * On success *out owns all device memory of the hierarchy until amg_free.  On failure *out
+ * is NULL and nothing is leaked.  Synchronises the stream before returning. */
+amg_status_t amg_setup(const amg_csr_t *A, const double *nullspace, const amg_params_t *p,
+                       amg_handle_t *out);
+
+/* Solves A x = b from x = 0 by PCG with one V-cycle (Algorithm 1) per iteration, until
+ * ||r|| / ||b|| <= tol on the recurrence residual and on the recomputed true residual.
+ * b and x: n doubles each, host or device (any pointer CUDA can address); they may not
+ * alias.  info may be NULL.  Returns AMG_ERR_NOT_CONVERGED (x = last iterate) at max_iter.
+ * Synchronises the stream before returning. */
+amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, amg_info_t *info);
+
+/* Releases every resource of the handle; NULL is accepted. */
+amg_status_t amg_free(amg_handle_t h);
+
+/* Number of levels. */
+amg_status_t amg_num_levels(amg_handle_t h, int *levels);
+
+/* Size of level l: rows, stored entries of A_l, and the number of aggregates formed on it
+ * (0 on the coarsest level). */
+amg_status_t amg_level_info(amg_handle_t h, int level, int64_t *n, int64_t *nnz, int64_t *nagg);
+
+/* Introspection for parity tests: copies one array of level l to caller-allocated HOST
+ * memory.  amg_export_count gives the element count first.  Element types: row pointers
+ * int64, columns and aggregate ids int32, values and diagonals double, flags uint8.
+ * AMG_EX_SCALARS gives 4 doubles: lambda (smoothing), omega, lambda (Chebyshev), nagg. */
+enum {
+    AMG_EX_A_ROWPTR = 0, AMG_EX_A_COL = 1, AMG_EX_A_VAL = 2, AMG_EX_STRONG = 3, AMG_EX_REMOVED = 4,
+    AMG_EX_LUMPFLAG = 5, AMG_EX_ABAR_ROWPTR = 6, AMG_EX_ABAR_COL = 7, AMG_EX_ABAR_VAL = 8,
+    AMG_EX_AGG = 9, AMG_EX_ROOT = 10, AMG_EX_P_ROWPTR = 11, AMG_EX_P_COL = 12, AMG_EX_P_VAL = 13,
+    AMG_EX_R_ROWPTR = 14, AMG_EX_R_COL = 15, AMG_EX_R_VAL = 16, AMG_EX_DSMOOTH = 17,
+    AMG_EX_SCALARS = 18, AMG_EX_NULLSPACE = 19, AMG_EX_CFLAG = 20
+};
+amg_status_t amg_export_count(amg_handle_t h, int level, int what, int64_t *count);
+amg_status_t amg_export(amg_handle_t h, int level, int what, void *dst_host);
+
+/* One V-cycle z = M^-1 r (Algorithm 1 from z = 0), in the hierarchy's precision.
+ * r and z: n doubles, host or device.  Used to test the preconditioner on its own. */
+amg_status_t amg_vcycle(amg_handle_t h, const double *r, double *z);
+
+/* Sparse product C = A B on the device (the two-phase hash kernel used for Eq. (2)).
+ * A: m x k, B: k x ncolB, both device CSR with sorted columns.  C is allocated by the
+ * library (device memory, int64 row pointers); release it with amg_csr_release.
+ * Each c_ij is summed over ascending k starting from zero, with every product rounded
+ * separately (no fused multiply-add). */
+typedef struct {
+    int64_t nrow, ncol, nnz;
+    int64_t *row_ptr;
+    int32_t *col;
+    double *val;
+} amg_dcsr_t;
+amg_status_t amg_spgemm(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB,
+                        void *cuda_stream, amg_dcsr_t *C);
+amg_status_t amg_csr_release(amg_dcsr_t *C);
+/* Copies a library-allocated device CSR to caller-allocated host arrays (nrow+1, nnz, nnz). */
+amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *col, double *val);
+
+/* Measurement hooks (no counterpart in the paper).
+ * amg_launch_count: kernels launched by this library since it was loaded (all threads).
+ * amg_profile_enable(1) resets the totals and starts recording CUDA events around the
+ * launches of these kernel classes (on the stream they run on); (0) stops.
+ *   0: the finest-level FP64 SpMV of the PCG iteration (q = A p with p.q),
+ *   1: the finest-level SpMVs of the V-cycle (Chebyshev steps and residual),
+ *   2: the sparse products of the Galerkin step (both phases, per product),
+ *   3: reserved.
+ * amg_profile_read returns, for one class, the number of timed launches, their summed
+ * device time in ms and the summed algorithmic bytes (each stored matrix entry, row pointer
+ * and vector element counted once per launch). */
+int64_t amg_launch_count(void);
+amg_status_t amg_profile_enable(int on);
+amg_status_t amg_profile_read(int kclass, int64_t *launches, double *total_ms, double *total_bytes);
+
+/* Text of a status code, and of the last CUDA error seen by this thread. */
+const char *amg_status_string(amg_status_t s);
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -719,7 +719,7 @@ static int csr_copy(oc_csr *dst, int64_t n, const int64_t *rp, const int32_t *ci
  *  -> filtered matrix (Eq. 6 or Algorithm 2) -> diagonal (Dbar, or Dtilde of Eq. 9 with the
  *  safeguard of Eq. 10-11) -> lambda (power method, or 1 with 1Norm) -> omega = 4/(3 lambda)
  *  -> P = (I - omega D^-1 Abar) Pt (Eq. 3) -> [Algorithm 3 per row] -> column scaling. */
-static int build_prolongator(oc_hier *h, int L)
+static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
 {
     struct oc_level *lv = &h->lev[L];
     const oc_params *p = &h->p;
@@ -742,6 +742,8 @@ static int build_prolongator(oc_hier *h, int L)
     int64_t nagg = oc_mis2_aggregate(n, A->rp, A->ci, lv->strong, p->seed, L, lv->agg, lv->root);
     if (nagg < 0) return OC_ERR_INVALID_ARG;
     lv->nagg = nagg;
+    /* a level whose aggregation does not reduce its size is the coarsest: no prolongator */
+    if (stop_if_not_coarsened && (nagg == n || nagg == 0)) return OC_OK;
 
     /* tentative prolongator, Eq. (5) with B in place of the constant; the orthonormal form
      * divides each column by the 2-norm of B on its aggregate (summed in ascending index) */
@@ -878,7 +880,7 @@ int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, c
     for (;;) {
         struct oc_level *lv = &h->lev[L];
         if (lv->A.n <= p->max_coarse || L + 1 >= p->max_levels || L + 1 >= OC_MAX_LEVELS) break;
-        st = build_prolongator(h, L);
+        st = build_prolongator(h, L, 1);
         if (st) { oc_free(h); return st; }
         if (lv->nagg == lv->A.n || lv->nagg == 0) break;   /* no coarsening: this is the coarsest */
         /* Galerkin product, Eq. (2), with the original A */
@@ -1057,7 +1059,7 @@ int oc_prolongator_only(int64_t n, const int64_t *rp, const int32_t *ci, const d
     if (st) { oc_free(h); return st; }
     h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     for (int64_t i = 0; i < n; ++i) h->lev[0].B[i] = nullspace ? nullspace[i] : 1.0;
-    st = build_prolongator(h, 0);
+    st = build_prolongator(h, 0, 0);
     if (st) { oc_free(h); return st; }
     *out = h;
     return OC_OK;

@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/amg.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA); pointers are passed through unchanged and
+all arithmetic runs in libamg_gb300.so.  There is no fallback: if the library is missing
+or fails to load, the import of this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+AMG_OK, AMG_ERR_INVALID_ARG, AMG_ERR_OOM, AMG_ERR_CUDA, AMG_ERR_ZERO_DIAG, AMG_ERR_EIGEN, \
+    AMG_ERR_COARSE_NOT_SPD, AMG_ERR_NOT_CONVERGED, AMG_ERR_BUDGET, AMG_ERR_UNSUPPORTED, AMG_ERR_INTERNAL = range(11)
+AMG_VAR_1NORM, AMG_VAR_OFFLMP, AMG_VAR_SPRSFY, AMG_VAR_CNSTRNT = 1, 2, 4, 8
+AMG_FP64, AMG_MIXED = 0, 1
+AMG_PT_ORTHONORMAL, AMG_PT_UNIT = 0, 1
+AMG_LAMBDA_ONE, AMG_LAMBDA_POWER = 0, 1
+EXPORTS = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
+           "removed": (4, np.uint8), "lumpflag": (5, np.uint8), "Abar.rp": (6, np.int64), "Abar.ci": (7, np.int32),
+           "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
+           "P.ci": (12, np.int32), "P.v": (13, np.float64), "R.rp": (14, np.int64), "R.ci": (15, np.int32),
+           "R.v": (16, np.float64), "Dsm": (17, np.float64), "scalars": (18, np.float64), "B": (19, np.float64),
+           "cflag": (20, np.uint8)}
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+class amg_csr_t(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int)]
+
+
+class amg_params_t(C.Structure):
+    _fields_ = [("theta", C.c_double), ("variants", C.c_uint), ("tau", C.c_double), ("sigma", C.c_double),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("power_iters", C.c_int),
+                ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
+                ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
+                ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p)]
+
+
+class amg_info_t(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("relres_true", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double), ("levels", C.c_int), ("op_complexity", C.c_double)]
+
+
+class amg_dcsr_t(C.Structure):
+    _fields_ = [("nrow", C.c_int64), ("ncol", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_2103_10476_gb300.build.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp, st = C.c_void_p, C.c_int
+    sig = {
+        "amg_params_default": (None, [C.POINTER(amg_params_t)]),
+        "amg_setup": (st, [C.POINTER(amg_csr_t), vp, C.POINTER(amg_params_t), C.POINTER(vp)]),
+        "amg_solve": (st, [vp, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
+        "amg_free": (st, [vp]),
+        "amg_num_levels": (st, [vp, C.POINTER(C.c_int)]),
+        "amg_level_info": (st, [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "amg_export_count": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
+        "amg_export": (st, [vp, C.c_int, C.c_int, vp]),
+        "amg_vcycle": (st, [vp, vp, vp]),
+        "amg_spgemm": (st, [C.POINTER(amg_csr_t), C.c_int64, C.POINTER(amg_csr_t), C.c_int64, vp,
+                            C.POINTER(amg_dcsr_t)]),
+        "amg_csr_release": (st, [C.POINTER(amg_dcsr_t)]),
+        "amg_dcsr_download": (st, [C.POINTER(amg_dcsr_t), vp, vp, vp]),
+        "amg_launch_count": (C.c_int64, []),
+        "amg_profile_enable": (st, [C.c_int]),
+        "amg_profile_read": (st, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "amg_status_string": (C.c_char_p, [st]),
+        "amg_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (must be contiguous)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(status: int, where: str):
+    if status != AMG_OK:
+        raise AmgError(status, where, lib.amg_last_error().decode(errors="replace"))
+
+
+def csr_arg(n: int, row_ptr, col, val) -> amg_csr_t:
+    rp, d0 = _ptr(row_ptr)
+    ci, d1 = _ptr(col)
+    v, d2 = _ptr(val)
+    if len({d0, d1, d2}) != 1:
+        raise ValueError("row_ptr, col and val must live on the same side")
+    nnz = int(row_ptr[-1])
+    return amg_csr_t(n, nnz, rp, ci, v, d0)
+
+
+def amg_params_default(**overrides) -> amg_params_t:
+    p = amg_params_t()
+    lib.amg_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def amg_setup(A: amg_csr_t, nullspace=None, params: amg_params_t | None = None):
+    """Returns the handle (a c_void_p); raises AmgError with the library status on failure."""
+    p = params if params is not None else amg_params_default()
+    h = C.c_void_p()
+    ns, _ = _ptr(nullspace)
+    _check(lib.amg_setup(C.byref(A), ns, C.byref(p), C.byref(h)), "amg_setup")
+    return h
+
+
+def amg_setup_status(A: amg_csr_t, nullspace=None, params: amg_params_t | None = None):
+    """(handle or None, status) without raising."""
+    p = params if params is not None else amg_params_default()
+    h = C.c_void_p()
+    ns, _ = _ptr(nullspace)
+    s = lib.amg_setup(C.byref(A), ns, C.byref(p), C.byref(h))
+    return (h if s == AMG_OK else None), s
+
+
+def amg_solve(h, b, x, tol: float) -> amg_info_t:
+    """Solves into x; returns the info struct (info.status holds NOT_CONVERGED if so)."""
+    info = amg_info_t()
+    pb, _ = _ptr(b)
+    px, _ = _ptr(x)
+    s = lib.amg_solve(h, pb, px, tol, C.byref(info))
+    if s not in (AMG_OK, AMG_ERR_NOT_CONVERGED):
+        _check(s, "amg_solve")
+    info.status = s
+    return info
+
+
+def amg_free(h):
+    _check(lib.amg_free(h), "amg_free")
+
+
+def amg_num_levels(h) -> int:
+    n = C.c_int()
+    _check(lib.amg_num_levels(h, C.byref(n)), "amg_num_levels")
+    return n.value
+
+
+def amg_level_info(h, level: int):
+    n, nnz, nagg = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib.amg_level_info(h, level, C.byref(n), C.byref(nnz), C.byref(nagg)), "amg_level_info")
+    return n.value, nnz.value, nagg.value
+
+
+def amg_export(h, level: int, what: str) -> np.ndarray:
+    code, dt = EXPORTS[what]
+    cnt = C.c_int64()
+    _check(lib.amg_export_count(h, level, code, C.byref(cnt)), "amg_export_count")
+    out = np.zeros(max(cnt.value, 1), dtype=dt)
+    if cnt.value:
+        _check(lib.amg_export(h, level, code, out.ctypes.data), "amg_export")
+    return out[:cnt.value]
+
+
+def amg_vcycle(h, r, z):
+    pr, _ = _ptr(r)
+    pz, _ = _ptr(z)
+    _check(lib.amg_vcycle(h, pr, pz), "amg_vcycle")
+
+
+def amg_spgemm(A: amg_csr_t, ncolA: int, B: amg_csr_t, ncolB: int, stream=None):
+    """C = A B on the device; returns host numpy (row_ptr, col, val)."""
+    Cm = amg_dcsr_t()
+    _check(lib.amg_spgemm(C.byref(A), ncolA, C.byref(B), ncolB, stream, C.byref(Cm)), "amg_spgemm")
+    nrow, nnz = Cm.nrow, Cm.nnz
+    try:
+        rp = np.zeros(nrow + 1, dtype=np.int64)
+        ci = np.zeros(max(nnz, 1), dtype=np.int32)
+        v = np.zeros(max(nnz, 1), dtype=np.float64)
+        _check(lib.amg_dcsr_download(C.byref(Cm), rp.ctypes.data, ci.ctypes.data, v.ctypes.data), "amg_dcsr_download")
+    finally:
+        lib.amg_csr_release(C.byref(Cm))
+    return rp, ci[:nnz], v[:nnz]
+
+
+KC_PCG_SPMV, KC_VCYCLE_SPMV, KC_SPGEMM = 0, 1, 2
+
+
+def amg_launch_count() -> int:
+    return int(lib.amg_launch_count())
+
+
+def amg_profile_enable(on: bool):
+    _check(lib.amg_profile_enable(int(bool(on))), "amg_profile_enable")
+
+
+def amg_profile_read(kclass: int):
+    """(launches, total_ms, total_bytes) of one timed kernel class."""
+    n, ms, by = C.c_int64(), C.c_double(), C.c_double()
+    _check(lib.amg_profile_read(kclass, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
+    return n.value, ms.value, by.value
+
+
+def amg_status_string(s: int) -> str:
+    return lib.amg_status_string(s).decode()
+
+
+def amg_last_error() -> str:
+    return lib.amg_last_error().decode(errors="replace")

@@ -1,0 +1,170 @@
+// amg_internal.cuh -- internal declarations shared by the library's CUDA translation units.
+//
+// Layout in device memory: CSR with int32 row pointers (nnz < 2^31 per matrix), int32
+// sorted columns and double values (plus float copies of the level operators in mixed
+// precision).  Vectors are dense arrays of double or float.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "amg.h"
+
+namespace amgk {
+
+// Kernel-launch counter (every launch site calls note_launch) and per-class kernel timing
+// with CUDA events for roofline reports.
+void note_launch();
+long long launch_count();
+enum KernelClass { KC_PCG_SPMV = 0, KC_VCYCLE_SPMV = 1, KC_SPGEMM = 2, KC_SETUP_SPMV = 3, KC_COUNT = 4 };
+bool profiling_enabled();
+void profile_enable(bool on);
+void profile_read(int cls, long long *launches, double *ms, double *bytes);
+struct ProfScope {
+    ProfScope(int cls, cudaStream_t s, double bytes);
+    ~ProfScope();
+    int cls;
+    cudaStream_t s;
+    double bytes;
+    cudaEvent_t start = nullptr;
+};
+
+constexpr int kWarp = 32;
+constexpr int kReduceBlocks = 304;        // fixed grid of the deterministic reductions (2 x 152 SMs)
+constexpr int kReduceThreads = 256;
+
+struct DevCsr {
+    int n = 0;          // rows
+    int ncol = 0;       // columns
+    int64_t nnz = 0;
+    int *rp = nullptr;  // n + 1
+    int *ci = nullptr;  // nnz
+    double *v = nullptr;
+};
+
+// --------------------------------------------------------------------------------- util.cu
+// out[0..n] = exclusive scan of in[0..n-1]; out[n] = total.  in and out may alias.
+cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
+// grid-size helper: enough blocks of `threads` to cover `work` items, capped
+int grid_for(int64_t work, int threads, int cap = 1 << 30);
+cudaError_t fill_int(int *p, int value, int64_t n, cudaStream_t s);
+cudaError_t fill_double(double *p, double value, int64_t n, cudaStream_t s);
+cudaError_t convert_rowptr_to64(const int *rp32, int64_t *rp64, int n1, cudaStream_t s);
+cudaError_t convert_rowptr_to32(const int64_t *rp64, int *rp32, int n1, int *bad, cudaStream_t s);
+cudaError_t convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+
+// Deterministic reductions: stage 1 writes kReduceBlocks partial sums, stage 2 sums them in
+// a fixed order into *out.
+cudaError_t dot(const double *x, const double *y, int n, double *partial, double *out, cudaStream_t s);
+cudaError_t reduce_partials(const double *partial, int count, double *out, cudaStream_t s);
+cudaError_t dot_partial(const double *x, const double *y, int n, double *partial, cudaStream_t s);
+
+// --------------------------------------------------------------------------------- setup.cu
+// Index of each row's diagonal entry (-1 if absent) and its value.
+cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t s);
+// Eq. (7): strong[e], removed[e] (= weak off-diagonal) and kept-entry counts per row.
+cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
+                     int *kept, cudaStream_t s);
+// Strong graph (strong off-diagonals only) as CSR: rp from a scan of counts.
+cudaError_t strong_graph_counts(const DevCsr &A, const uint8_t *strong, int *cnt, cudaStream_t s);
+cudaError_t strong_graph_fill(const DevCsr &A, const uint8_t *strong, const int *grp, int *gci, cudaStream_t s);
+// Aggregation on the strong graph; writes agg, root and the aggregate count (device int).
+// Returns cudaErrorUnknown-free status; *status_flag set by kernels on internal failure.
+struct AggWork {
+    unsigned long long *t0, *t1;   // n tuples each
+    int *rootof, *join1;           // n each
+    int *counter;                  // 2 ints, device
+};
+cudaError_t aggregate_mis2(int n, const int *grp, const int *gci, uint64_t seed, int level, AggWork w, int *agg,
+                           uint8_t *root, int *nagg_host, int *rounds_host, cudaStream_t s);
+// Members of each aggregate in ascending order: mstart (nagg+1), members (n).
+cudaError_t aggregate_members(int n, int nagg, const int *agg, int *mstart, int *members, int *fill,
+                              cudaStream_t s);
+// Per aggregate: nrm = sqrt(sum of B^2 over members, ascending); bad > 0 if a norm is 0.
+cudaError_t aggregate_norms(int nagg, const int *mstart, const int *members, const double *B, double *nrm,
+                            int *bad, cudaStream_t s);
+// §2.5: mark pruned strong links (then their transposes) in `removed`, update kept counts.
+cudaError_t sprsfy(const DevCsr &A, const uint8_t *strong, const int *agg, const uint8_t *root, int nagg,
+                   const int *mstart, const int *members, uint8_t *drop, uint8_t *removed, int *kept,
+                   cudaStream_t s);
+// Filtered matrix (Eq. 6 or Algorithm 2) into Abar (rp from a scan of kept), plus the
+// smoothing diagonal (Dbar, or Dtilde of Eq. 9-11) and the per-row lumping outcome.
+cudaError_t filter(const DevCsr &A, const uint8_t *removed, int offlmp, double tau, int onenorm, double sigma,
+                   DevCsr &Abar, double *Dsm, uint8_t *lumpflag, int *zero_diag, cudaStream_t s);
+// Smoothed prolongator (unit basis), pattern counts then fill.
+cudaError_t smooth_counts(const DevCsr &Abar, const int *agg, int *cnt, cudaStream_t s);
+cudaError_t smooth_fill(const DevCsr &Abar, const int *agg, const double *B, const double *Dsm,
+                        const double *omega_dev, DevCsr &P, cudaStream_t s);
+// Algorithm 3 on each row of P (unit basis).
+cudaError_t constrain(DevCsr &P, const int *agg, const double *B, uint8_t *cflag, cudaStream_t s);
+// Column scaling P_ic /= nrm_c.
+cudaError_t scale_columns(DevCsr &P, const double *nrm, cudaStream_t s);
+// Transpose (rows of the result sorted).
+cudaError_t transpose_counts(const DevCsr &P, int *cnt, cudaStream_t s);
+cudaError_t transpose_fill(const DevCsr &P, DevCsr &R, int *fill, cudaStream_t s);
+// Power method on D^-1 A (Rayleigh quotient of the last sweep), result on the device.
+cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t stream_seed, double *x,
+                         double *y, double *partial, double *scal, double *lambda_dev, cudaStream_t s);
+uint64_t power_stream_seed(uint64_t seed, int level, int purpose);
+cudaError_t omega_from_lambda(const double *lambda_dev, double *omega_dev, cudaStream_t s);
+cudaError_t invert_diag(const double *d, double *inv, float *invf, int n, int *zero, cudaStream_t s);
+
+// --------------------------------------------------------------------------------- spgemm.cu
+// C = A B, allocating C's arrays with cudaMalloc.  On failure C is left empty.
+cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s);
+
+// --------------------------------------------------------------------------------- coarse.cu
+// Dense SPD inverse of the coarsest operator via Cholesky (FP64).  info = 0 or pivot row+1.
+cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s);
+
+// --------------------------------------------------------------------------------- solve.cu
+struct LevelView {      // what the solve needs of one level, in working precision T
+    int n = 0, nc = 0;
+    const int *arp = nullptr, *aci = nullptr;
+    const void *av = nullptr;               // A values (T)
+    const int *prp = nullptr, *pci = nullptr;
+    const void *pv = nullptr;               // P values (T)
+    const int *rrp = nullptr, *rci = nullptr;
+    const void *rv = nullptr;               // R values (T)
+    const void *invdiag = nullptr;          // T
+    double lambda = 0.0;                    // Chebyshev lambda_max
+    int64_t nnz_a = 0;                      // stored entries of A
+    int lanes_a = 8, lanes_p = 8, lanes_r = 8;
+    void *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *d = nullptr;   // T work vectors
+};
+struct SolveCtx {
+    int nlev = 0;
+    LevelView lev[32];
+    int coarse_n = 0;
+    const double *coarse_inv = nullptr;     // dense n x n FP64
+    double *coarse_tmp_in = nullptr, *coarse_tmp_out = nullptr;
+    int cheb_degree = 2;
+    double cheb_ratio = 10.0;
+    int mixed = 0;
+};
+// z = V-cycle(r) from z = 0 on the finest level (r, z double on the device).
+cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s);
+
+// PCG building blocks (FP64, deterministic reductions; scalars live on the device)
+struct PcgScalars {     // device
+    double rz, pq, alpha, beta, rr, bb, tmp;
+};
+cudaError_t spmv_dot(const DevCsr &A, int lanes, const double *p, double *q, double *partial, cudaStream_t s);
+cudaError_t spmv_d(const DevCsr &A, int lanes, const double *x, double *y, cudaStream_t s);
+cudaError_t residual_d(const DevCsr &A, int lanes, const double *b, const double *x, double *r, cudaStream_t s);
+cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, const PcgScalars *sc,
+                          double *partial, cudaStream_t s);
+cudaError_t pcg_update_p(int n, double *p, const double *z, const PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_alpha(const double *partial, PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_beta(const double *partial, PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_store(const double *partial, double *dst, cudaStream_t s);
+int pick_lanes(double avg_row);
+
+}  // namespace amgk
+
+// error plumbing shared by the host code
+#define AMG_CUDA_TRY(expr)                          \
+    do {                                            \
+        cudaError_t _e = (expr);                    \
+        if (_e != cudaSuccess) return _e;           \
+    } while (0)

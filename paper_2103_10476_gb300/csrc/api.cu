@@ -1,0 +1,859 @@
+// api.cu -- the C ABI: hierarchy setup (per level: strength, aggregation, tentative
+// prolongator, optional pruning, filtering, smoothing diagonal and damping, smoothed
+// prolongator, optional constraints, transpose, Galerkin product, Chebyshev eigenvalue; then
+// the coarsest factorisation) and the preconditioned conjugate-gradient solve.
+//
+// Host code only orchestrates: every arithmetic step runs in the kernels of setup.cu,
+// spgemm.cu, coarse.cu, solve.cu and util.cu.  The host reads back sizes (to allocate),
+// eigenvalue estimates (to set omega and the Chebyshev interval) and the residual norm (to
+// stop PCG).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amg_internal.cuh"
+
+using namespace amgk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Level {
+    DevCsr A;                 // level operator
+    double *diag = nullptr;   // diag(A)
+    uint8_t *strong = nullptr, *removed = nullptr, *lumpflag = nullptr, *cflag = nullptr;
+    DevCsr Abar;
+    int *agg = nullptr;
+    uint8_t *root = nullptr;
+    int nagg = 0;
+    double *B = nullptr, *nrm = nullptr, *Dsm = nullptr;
+    double lambda_bar = 0.0, omega = 0.0, lambda_cheb = 0.0;
+    DevCsr P, R;
+    double *invdiag = nullptr;
+    float *invdiag_f = nullptr, *Af = nullptr, *Pf = nullptr, *Rf = nullptr;
+    void *vf = nullptr, *vx = nullptr, *vx2 = nullptr, *vr = nullptr, *vd = nullptr;   // solve vectors
+    int lanes_a = 16, lanes_p = 8, lanes_r = 16;
+};
+
+}  // namespace
+
+struct amg_hierarchy {
+    amg_params_t p;
+    cudaStream_t s = nullptr;
+    int nlev = 0;
+    Level lev[32];
+    std::vector<void *> allocs;
+    double *coarse_inv = nullptr;
+    // solve workspace (FP64, finest level)
+    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
+    double *partial = nullptr;
+    PcgScalars *sc = nullptr;
+    SolveCtx ctx;
+    double setup_ms = 0.0;
+    int64_t fine_nnz = 0;
+};
+
+namespace {
+
+amg_status_t fail_cuda(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();   // clear a sticky-free error so later calls start clean
+    if (e == cudaErrorMemoryAllocation) return AMG_ERR_OOM;
+    return AMG_ERR_CUDA;
+}
+
+#define CK(expr)                                                          \
+    do {                                                                  \
+        cudaError_t _e = (expr);                                          \
+        if (_e != cudaSuccess) { st = fail_cuda(_e, #expr); goto done; }  \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(amg_hierarchy *h, T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e == cudaSuccess) h->allocs.push_back((void *)*p);
+    return e;
+}
+
+void own(amg_hierarchy *h, const DevCsr &c)
+{
+    if (c.rp) h->allocs.push_back(c.rp);
+    if (c.ci) h->allocs.push_back(c.ci);
+    if (c.v) h->allocs.push_back(c.v);
+}
+
+void release_all(amg_hierarchy *h)
+{
+    if (h->s) cudaStreamSynchronize(h->s);
+    else cudaDeviceSynchronize();
+    for (void *p : h->allocs) cudaFree(p);
+    h->allocs.clear();
+}
+
+__global__ void validate_kernel(int n, const int *rp, const int *ci, int *bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int has = 0, prev = -1;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int c = ci[e];
+        if (c < 0 || c >= n || c <= prev) { atomicAdd(bad, 1); return; }
+        prev = c;
+        has |= (c == i);
+    }
+    if (!has) atomicAdd(bad, 1);
+}
+
+__global__ void ones_kernel(int n, double *b)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = 1.0;
+}
+
+// stored bytes of a device CSR (int32 row pointers and columns, double values)
+double csr_bytes(const DevCsr &c) { return 12.0 * (double)c.nnz + 4.0 * (c.n + 1); }
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// one level of the hierarchy; *coarsest = 1 if the level cannot be coarsened further
+amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
+{
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const amg_params_t &p = h->p;
+    Level &lv = h->lev[L];
+    DevCsr &A = lv.A;
+    const int n = A.n;
+    int *kept = nullptr, *grp = nullptr, *gci = nullptr, *mstart = nullptr, *members = nullptr, *fill = nullptr;
+    int *flags = nullptr;
+    unsigned long long *t0 = nullptr, *t1 = nullptr;
+    int *rootof = nullptr, *join1 = nullptr;
+    uint8_t *drop = nullptr;
+    double *px = nullptr, *py = nullptr, *scal = nullptr;
+    DevCsr AP, Ac;
+    int hflags[4] = {0, 0, 0, 0};
+    int nagg = 0, rounds = 0, nnz_g = 0, nnz_bar = 0, nnz_p = 0, ovf = 0;
+    *coarsest = 0;
+
+    CK(dalloc(h, &lv.strong, (size_t)A.nnz));
+    CK(dalloc(h, &lv.removed, (size_t)A.nnz));
+    CK(cudaMalloc(&kept, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMalloc(&flags, sizeof(int) * 4));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
+    // Eq. (7)
+    CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
+    // strong graph
+    CK(cudaMalloc(&grp, sizeof(int) * (size_t)(n + 1)));
+    CK(strong_graph_counts(A, lv.strong, grp, s));
+    CK(scan_exclusive(grp, grp, n, s));
+    CK(cudaMemcpyAsync(&nnz_g, grp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMalloc(&gci, sizeof(int) * (size_t)(nnz_g > 0 ? nnz_g : 1)));
+    CK(strong_graph_fill(A, lv.strong, grp, gci, s));
+    // aggregation
+    CK(dalloc(h, &lv.agg, (size_t)n));
+    CK(dalloc(h, &lv.root, (size_t)n));
+    CK(cudaMalloc(&t0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1)));
+    CK(cudaMalloc(&t1, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1)));
+    CK(cudaMalloc(&rootof, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMalloc(&join1, sizeof(int) * (size_t)(n + 1)));
+    {
+        AggWork w{t0, t1, rootof, join1, flags + 2};
+        cudaError_t e = aggregate_mis2(n, grp, gci, p.seed, L, w, lv.agg, lv.root, &nagg, &rounds, s);
+        if (e == cudaErrorInvalidValue) { g_last_error = "aggregation left a vertex unassigned"; st = AMG_ERR_INTERNAL; goto done; }
+        CK(e);
+    }
+    lv.nagg = nagg;
+    if (nagg == n || nagg == 0) { *coarsest = 1; goto done; }
+    // members and tentative-prolongator column norms
+    CK(cudaMalloc(&mstart, sizeof(int) * (size_t)(nagg + 1)));
+    CK(cudaMalloc(&members, sizeof(int) * (size_t)n));
+    CK(cudaMalloc(&fill, sizeof(int) * (size_t)(nagg + 1)));
+    CK(aggregate_members(n, nagg, lv.agg, mstart, members, fill, s));
+    CK(dalloc(h, &lv.nrm, (size_t)nagg));
+    CK(aggregate_norms(nagg, mstart, members, lv.B, lv.nrm, flags + 0, s));
+    // §2.5
+    if (p.variants & AMG_VAR_SPRSFY) {
+        CK(cudaMalloc(&drop, (size_t)(A.nnz > 0 ? A.nnz : 1)));
+        CK(sprsfy(A, lv.strong, lv.agg, lv.root, nagg, mstart, members, drop, lv.removed, kept, s));
+    }
+    // filtered matrix and smoothing diagonal
+    lv.Abar.n = n;
+    lv.Abar.ncol = n;
+    CK(dalloc(h, &lv.Abar.rp, (size_t)n + 1));
+    CK(scan_exclusive(kept, lv.Abar.rp, n, s));
+    CK(cudaMemcpyAsync(&nnz_bar, lv.Abar.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hflags[0]) { g_last_error = "near-null space is zero on an aggregate"; st = AMG_ERR_INVALID_ARG; goto done; }
+    lv.Abar.nnz = nnz_bar;
+    CK(dalloc(h, &lv.Abar.ci, (size_t)nnz_bar));
+    CK(dalloc(h, &lv.Abar.v, (size_t)nnz_bar));
+    CK(dalloc(h, &lv.Dsm, (size_t)n));
+    CK(dalloc(h, &lv.lumpflag, (size_t)n));
+    CK(filter(A, lv.removed, (p.variants & AMG_VAR_OFFLMP) ? 1 : 0, p.tau, (p.variants & AMG_VAR_1NORM) ? 1 : 0,
+              p.sigma, lv.Abar, lv.Dsm, lv.lumpflag, flags + 1, s));
+    CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(p.variants & AMG_VAR_1NORM) && hflags[1]) {
+        g_last_error = "zero diagonal in the filtered matrix";
+        st = AMG_ERR_ZERO_DIAG;
+        goto done;
+    }
+    // eigenvalue of Dsm^-1 Abar and omega = 4 / (3 lambda), Eq. (3)
+    CK(cudaMalloc(&px, sizeof(double) * (size_t)n));
+    CK(cudaMalloc(&py, sizeof(double) * (size_t)n));
+    CK(cudaMalloc(&scal, sizeof(double) * (kReduceBlocks + 8)));
+    if (p.lambda_override > 0.0) {
+        lv.lambda_bar = p.lambda_override;
+    } else if ((p.variants & AMG_VAR_1NORM) && p.onenorm_lambda == AMG_LAMBDA_ONE) {
+        lv.lambda_bar = 1.0;
+    } else {
+        CK(power_lambda(lv.Abar, lv.Dsm, p.power_iters, power_stream_seed(p.seed, L, 1), px, py, scal + 8, scal,
+                        scal + 1, s));
+        CK(cudaMemcpyAsync(&lv.lambda_bar, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (!(lv.lambda_bar > 0.0) || !std::isfinite(lv.lambda_bar)) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "eigenvalue estimate %.17g on level %d", lv.lambda_bar, L);
+        g_last_error = buf;
+        st = AMG_ERR_EIGEN;
+        goto done;
+    }
+    lv.omega = 4.0 / (3.0 * lv.lambda_bar);
+    CK(cudaMemcpyAsync(scal + 2, &lv.omega, sizeof(double), cudaMemcpyHostToDevice, s));
+    // smoothed prolongator (unit basis), Algorithm 3, column scaling
+    lv.P.n = n;
+    lv.P.ncol = nagg;
+    CK(dalloc(h, &lv.P.rp, (size_t)n + 1));
+    CK(smooth_counts(lv.Abar, lv.agg, lv.P.rp, s));
+    CK(scan_exclusive(lv.P.rp, lv.P.rp, n, s));
+    CK(cudaMemcpyAsync(&nnz_p, lv.P.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    lv.P.nnz = nnz_p;
+    CK(dalloc(h, &lv.P.ci, (size_t)nnz_p));
+    CK(dalloc(h, &lv.P.v, (size_t)nnz_p));
+    CK(smooth_fill(lv.Abar, lv.agg, lv.B, lv.Dsm, scal + 2, lv.P, s));
+    CK(dalloc(h, &lv.cflag, (size_t)n));
+    CK(cudaMemsetAsync(lv.cflag, 0, (size_t)n, s));
+    if (p.variants & AMG_VAR_CNSTRNT) CK(constrain(lv.P, lv.agg, lv.B, lv.cflag, s));
+    if (p.pt_scaling == AMG_PT_ORTHONORMAL) CK(scale_columns(lv.P, lv.nrm, s));
+    // R = P^T
+    lv.R.n = nagg;
+    lv.R.ncol = n;
+    lv.R.nnz = nnz_p;
+    CK(dalloc(h, &lv.R.rp, (size_t)nagg + 1));
+    CK(dalloc(h, &lv.R.ci, (size_t)nnz_p));
+    CK(dalloc(h, &lv.R.v, (size_t)nnz_p));
+    CK(transpose_counts(lv.P, lv.R.rp, s));
+    CK(scan_exclusive(lv.R.rp, lv.R.rp, nagg, s));
+    CK(transpose_fill(lv.P, lv.R, fill, s));
+    // Galerkin product with the original A, Eq. (2)
+    {
+        cudaError_t e;
+        {
+            ProfScope ps(KC_SPGEMM, s, 0.0);
+            e = spgemm(A, lv.P, AP, &ovf, s);
+            ps.bytes = csr_bytes(A) + csr_bytes(lv.P) + csr_bytes(AP);
+        }
+        if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow in A*P"; st = AMG_ERR_INTERNAL; goto done; }
+        CK(e);
+        {
+            ProfScope ps(KC_SPGEMM, s, 0.0);
+            e = spgemm(lv.R, AP, Ac, &ovf, s);
+            ps.bytes = csr_bytes(lv.R) + csr_bytes(AP) + csr_bytes(Ac);
+        }
+        if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow in R*(AP)"; st = AMG_ERR_INTERNAL; goto done; }
+        CK(e);
+    }
+    // Chebyshev smoother: lambda_max(D^-1 A_L) and D^-1
+    CK(dalloc(h, &lv.invdiag, (size_t)n));
+    if (p.precision == AMG_MIXED) CK(dalloc(h, &lv.invdiag_f, (size_t)n));
+    CK(invert_diag(lv.diag, lv.invdiag, lv.invdiag_f, n, flags + 3, s));
+    CK(power_lambda(A, lv.diag, p.power_iters, power_stream_seed(p.seed, L, 2), px, py, scal + 8, scal, scal + 1, s));
+    CK(cudaMemcpyAsync(&lv.lambda_cheb, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hflags[3]) { g_last_error = "zero diagonal in a level operator"; st = AMG_ERR_ZERO_DIAG; goto done; }
+    if (!(lv.lambda_cheb > 0.0) || !std::isfinite(lv.lambda_cheb)) {
+        g_last_error = "Chebyshev eigenvalue estimate not positive";
+        st = AMG_ERR_EIGEN;
+        goto done;
+    }
+    // next level
+    {
+        Level &nx = h->lev[L + 1];
+        nx.A = Ac;
+        own(h, Ac);
+        Ac = DevCsr();
+        CK(dalloc(h, &nx.B, (size_t)nagg));
+        if (p.pt_scaling == AMG_PT_ORTHONORMAL)
+            CK(cudaMemcpyAsync(nx.B, lv.nrm, sizeof(double) * (size_t)nagg, cudaMemcpyDeviceToDevice, s));
+        else if (nagg > 0) {
+            ones_kernel<<<grid_for(nagg, 256), 256, 0, s>>>(nagg, nx.B); note_launch();
+        }
+        CK(cudaGetLastError());
+    }
+done:
+    cudaStreamSynchronize(s);
+    cudaFree(kept); cudaFree(grp); cudaFree(gci); cudaFree(mstart); cudaFree(members); cudaFree(fill);
+    cudaFree(flags); cudaFree(t0); cudaFree(t1); cudaFree(rootof); cudaFree(join1); cudaFree(drop);
+    cudaFree(px); cudaFree(py); cudaFree(scal);
+    cudaFree(AP.rp); cudaFree(AP.ci); cudaFree(AP.v);
+    cudaFree(Ac.rp); cudaFree(Ac.ci); cudaFree(Ac.v);
+    return st;
+}
+
+amg_status_t prepare_solve(amg_hierarchy *h)
+{
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const bool mixed = h->p.precision == AMG_MIXED;
+    const size_t ts = mixed ? sizeof(float) : sizeof(double);
+    const int n0 = h->lev[0].A.n;
+    SolveCtx &c = h->ctx;
+    c = SolveCtx();
+    c.nlev = h->nlev;
+    c.cheb_degree = h->p.cheb_degree;
+    c.cheb_ratio = h->p.cheb_ratio;
+    c.mixed = mixed ? 1 : 0;
+    for (int L = 0; L < h->nlev; ++L) {
+        Level &lv = h->lev[L];
+        const int n = lv.A.n;
+        const bool last = (L == h->nlev - 1);
+        CK(dalloc(h, (char **)&lv.vf, (size_t)n * ts));
+        CK(dalloc(h, (char **)&lv.vx, (size_t)n * ts));
+        LevelView &v = c.lev[L];
+        v.n = n;
+        v.f = lv.vf;
+        v.x = lv.vx;
+        if (!last) {
+            CK(dalloc(h, (char **)&lv.vx2, (size_t)n * ts));
+            CK(dalloc(h, (char **)&lv.vr, (size_t)n * ts));
+            CK(dalloc(h, (char **)&lv.vd, (size_t)n * ts));
+            v.x2 = lv.vx2;
+            v.r = lv.vr;
+            v.d = lv.vd;
+            v.nc = lv.nagg;
+            v.arp = lv.A.rp; v.aci = lv.A.ci;
+            v.prp = lv.P.rp; v.pci = lv.P.ci;
+            v.rrp = lv.R.rp; v.rci = lv.R.ci;
+            v.lambda = lv.lambda_cheb;
+            v.nnz_a = lv.A.nnz;
+            lv.lanes_a = pick_lanes(n ? (double)lv.A.nnz / n : 1.0);
+            lv.lanes_p = pick_lanes(n ? (double)lv.P.nnz / n : 1.0);
+            lv.lanes_r = pick_lanes(lv.nagg ? (double)lv.R.nnz / lv.nagg : 1.0);
+            v.lanes_a = lv.lanes_a; v.lanes_p = lv.lanes_p; v.lanes_r = lv.lanes_r;
+            if (mixed) {
+                CK(dalloc(h, &lv.Af, (size_t)lv.A.nnz));
+                CK(dalloc(h, &lv.Pf, (size_t)lv.P.nnz));
+                CK(dalloc(h, &lv.Rf, (size_t)lv.R.nnz));
+                CK(convert_d2f(lv.A.v, lv.Af, lv.A.nnz, s));
+                CK(convert_d2f(lv.P.v, lv.Pf, lv.P.nnz, s));
+                CK(convert_d2f(lv.R.v, lv.Rf, lv.R.nnz, s));
+                v.av = lv.Af; v.pv = lv.Pf; v.rv = lv.Rf; v.invdiag = lv.invdiag_f;
+            } else {
+                v.av = lv.A.v; v.pv = lv.P.v; v.rv = lv.R.v; v.invdiag = lv.invdiag;
+            }
+        }
+    }
+    c.coarse_n = h->lev[h->nlev - 1].A.n;
+    c.coarse_inv = h->coarse_inv;
+    // PCG vectors
+    CK(dalloc(h, &h->b, (size_t)n0));
+    CK(dalloc(h, &h->x, (size_t)n0));
+    CK(dalloc(h, &h->r, (size_t)n0));
+    CK(dalloc(h, &h->z, (size_t)n0));
+    CK(dalloc(h, &h->pv, (size_t)n0));
+    CK(dalloc(h, &h->q, (size_t)n0));
+    CK(dalloc(h, &h->t, (size_t)n0));
+    CK(dalloc(h, &h->partial, (size_t)kReduceBlocks));
+    CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
+done:
+    return st;
+}
+
+}  // namespace
+
+// ====================================================================================== ABI
+
+extern "C" {
+
+void amg_params_default(amg_params_t *p)
+{
+    if (!p) return;
+    p->theta = 0.0;
+    p->variants = 0;
+    p->tau = 1.1;
+    p->sigma = 1.0 / 3.0;
+    p->cheb_degree = 2;
+    p->cheb_ratio = 10.0;
+    p->power_iters = 10;
+    p->max_coarse = 500;
+    p->max_levels = 10;
+    p->precision = AMG_FP64;
+    p->pt_scaling = AMG_PT_ORTHONORMAL;
+    p->onenorm_lambda = AMG_LAMBDA_ONE;
+    p->max_iter = 1000;
+    p->seed = 0;
+    p->lambda_override = 0.0;
+    p->cuda_stream = nullptr;
+}
+
+const char *amg_status_string(amg_status_t s)
+{
+    switch (s) {
+    case AMG_OK: return "ok";
+    case AMG_ERR_INVALID_ARG: return "invalid argument";
+    case AMG_ERR_OOM: return "out of device memory";
+    case AMG_ERR_CUDA: return "CUDA error";
+    case AMG_ERR_ZERO_DIAG: return "zero diagonal";
+    case AMG_ERR_EIGEN: return "eigenvalue estimate not positive";
+    case AMG_ERR_COARSE_NOT_SPD: return "coarsest operator not positive definite";
+    case AMG_ERR_NOT_CONVERGED: return "not converged";
+    case AMG_ERR_BUDGET: return "memory budget exceeded";
+    case AMG_ERR_UNSUPPORTED: return "unsupported size";
+    case AMG_ERR_INTERNAL: return "internal limit";
+    }
+    return "unknown status";
+}
+
+const char *amg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t amg_launch_count(void) { return (int64_t)launch_count(); }
+
+amg_status_t amg_profile_enable(int on)
+{
+    profile_enable(on != 0);
+    return AMG_OK;
+}
+
+amg_status_t amg_profile_read(int kclass, int64_t *launches, double *total_ms, double *total_bytes)
+{
+    if (kclass < 0 || kclass >= KC_COUNT || !launches || !total_ms || !total_bytes) return AMG_ERR_INVALID_ARG;
+    long long l = 0;
+    profile_read(kclass, &l, total_ms, total_bytes);
+    *launches = l;
+    return AMG_OK;
+}
+
+amg_status_t amg_free(amg_handle_t h)
+{
+    if (!h) return AMG_OK;
+    release_all(h);
+    delete h;
+    return AMG_OK;
+}
+
+amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_params_t *pin, amg_handle_t *out)
+{
+    if (!out) return AMG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!Ain || !pin) return AMG_ERR_INVALID_ARG;
+    if (Ain->n < 0 || Ain->nnz < 0 || (Ain->n > 0 && (!Ain->row_ptr || !Ain->col || !Ain->val)))
+        return AMG_ERR_INVALID_ARG;
+    if (Ain->n > 0x7ffffffe || Ain->nnz > 0x7ffffffe) {
+        g_last_error = "matrix too large for 32-bit indices";
+        return AMG_ERR_UNSUPPORTED;
+    }
+    const amg_params_t &p = *pin;
+    if (!(p.theta >= 0.0 && p.theta <= 1.0) || p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || p.power_iters < 1 ||
+        p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0)) {
+        g_last_error = "parameter out of range";
+        return AMG_ERR_INVALID_ARG;
+    }
+    const double t_start = now_ms();
+    amg_hierarchy *h = new amg_hierarchy();
+    h->p = p;
+    h->s = (cudaStream_t)p.cuda_stream;
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const int n = (int)Ain->n;
+    const int nnz = (int)Ain->nnz;
+    int *bad = nullptr;
+    int hbad = 0;
+    int64_t *rp64 = nullptr;
+    const int maxL = p.max_levels < 32 ? p.max_levels : 32;
+    int L = 0;
+    int coarse_info = 0;
+    double *cwork = nullptr;
+    {
+        Level &l0 = h->lev[0];
+        l0.A.n = n;
+        l0.A.ncol = n;
+        l0.A.nnz = nnz;
+        CK(dalloc(h, &l0.A.rp, (size_t)n + 1));
+        CK(dalloc(h, &l0.A.ci, (size_t)nnz));
+        CK(dalloc(h, &l0.A.v, (size_t)nnz));
+        CK(cudaMalloc(&bad, sizeof(int)));
+        CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+        CK(cudaMalloc(&rp64, sizeof(int64_t) * ((size_t)n + 1)));
+        CK(cudaMemcpyAsync(rp64, Ain->row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDefault, s));
+        CK(convert_rowptr_to32(rp64, l0.A.rp, n + 1, bad, s));
+        if (nnz > 0) {
+            CK(cudaMemcpyAsync(l0.A.ci, Ain->col, sizeof(int) * (size_t)nnz, cudaMemcpyDefault, s));
+            CK(cudaMemcpyAsync(l0.A.v, Ain->val, sizeof(double) * (size_t)nnz, cudaMemcpyDefault, s));
+        }
+        CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int64_t last = 0;
+        if (n > 0) CK(cudaMemcpy(&last, rp64 + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (hbad || last != nnz) { g_last_error = "row pointer not monotone or not matching nnz"; st = AMG_ERR_INVALID_ARG; goto done; }
+        if (n > 0) {
+            validate_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.A.rp, l0.A.ci, bad); note_launch();
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (hbad) { g_last_error = "columns unsorted, out of range, duplicated, or a missing diagonal"; st = AMG_ERR_INVALID_ARG; goto done; }
+        }
+        CK(dalloc(h, &l0.B, (size_t)n));
+        if (nullspace) CK(cudaMemcpyAsync(l0.B, nullspace, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+        else if (n > 0) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
+        CK(cudaGetLastError());
+        h->fine_nnz = nnz;
+    }
+    // levels
+    for (L = 0;; ++L) {
+        Level &lv = h->lev[L];
+        CK(dalloc(h, &lv.diag, (size_t)lv.A.n));
+        CK(diag_extract(lv.A, nullptr, lv.diag, s));
+        if (lv.A.n <= p.max_coarse || L + 1 >= maxL) break;
+        int coarsest = 0;
+        st = build_level(h, L, &coarsest);
+        if (st != AMG_OK) goto done;
+        if (coarsest) break;
+    }
+    h->nlev = L + 1;
+    // coarsest level: dense inverse through the Cholesky factor
+    {
+        Level &cl = h->lev[L];
+        const int nc = cl.A.n;
+        if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
+        CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
+        CK(cudaMalloc(&cwork, sizeof(double) * ((size_t)nc * nc > 0 ? (size_t)nc * nc : 1)));
+        CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s));
+        CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (coarse_info) { g_last_error = "coarsest operator not positive definite"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
+    }
+    st = prepare_solve(h);
+    if (st == AMG_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail_cuda(e, "setup");
+    }
+done:
+    cudaFree(bad);
+    cudaFree(rp64);
+    cudaFree(cwork);
+    if (st != AMG_OK) {
+        amg_free(h);
+        return st;
+    }
+    h->setup_ms = now_ms() - t_start;
+    *out = h;
+    return AMG_OK;
+}
+
+amg_status_t amg_num_levels(amg_handle_t h, int *levels)
+{
+    if (!h || !levels) return AMG_ERR_INVALID_ARG;
+    *levels = h->nlev;
+    return AMG_OK;
+}
+
+amg_status_t amg_level_info(amg_handle_t h, int level, int64_t *n, int64_t *nnz, int64_t *nagg)
+{
+    if (!h || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
+    const Level &lv = h->lev[level];
+    if (n) *n = lv.A.n;
+    if (nnz) *nnz = lv.A.nnz;
+    if (nagg) *nagg = (level == h->nlev - 1) ? 0 : lv.nagg;
+    return AMG_OK;
+}
+
+amg_status_t amg_vcycle(amg_handle_t h, const double *r, double *z)
+{
+    if (!h || (!r && h->lev[0].A.n) || (!z && h->lev[0].A.n)) return AMG_ERR_INVALID_ARG;
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const int n = h->lev[0].A.n;
+    if (n == 0) return AMG_OK;
+    CK(cudaMemcpyAsync(h->r, r, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(vcycle(h->ctx, h->r, h->z, s));
+    CK(cudaMemcpyAsync(z, h->z, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+done:
+    return st;
+}
+
+amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, amg_info_t *info)
+{
+    if (!h) return AMG_ERR_INVALID_ARG;
+    const int n = h->lev[0].A.n;
+    if (n > 0 && (!b || !x)) return AMG_ERR_INVALID_ARG;
+    if (!(tol >= 0.0)) return AMG_ERR_INVALID_ARG;
+    const double t0 = now_ms();
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const DevCsr &A = h->lev[0].A;
+    const int lanes = pick_lanes(n ? (double)A.nnz / n : 1.0);
+    int it = 0;
+    double bb = 0.0, rr = 0.0, relres = 0.0, nb = 0.0;
+    amg_status_t result = AMG_OK;
+    if (n == 0) goto finish;
+    CK(cudaMemcpyAsync(h->b, b, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)n, s));
+    CK(cudaMemcpyAsync(h->r, h->b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(dot(h->b, h->b, n, h->partial, &h->sc->bb, s));
+    CK(cudaMemcpyAsync(&bb, &h->sc->bb, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    nb = std::sqrt(bb);
+    if (nb == 0.0) goto finish;
+    CK(vcycle(h->ctx, h->r, h->z, s));
+    CK(cudaMemcpyAsync(h->pv, h->z, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(dot(h->r, h->z, n, h->partial, &h->sc->rz, s));
+    result = AMG_ERR_NOT_CONVERGED;
+    while (it < h->p.max_iter) {
+        {
+            ProfScope ps(KC_PCG_SPMV, s, 12.0 * (double)A.nnz + 20.0 * n + 4.0);
+            CK(spmv_dot(A, lanes, h->pv, h->q, h->partial, s));
+        }
+        CK(pcg_alpha(h->partial, h->sc, s));
+        CK(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, s));
+        CK(pcg_store(h->partial, &h->sc->rr, s));
+        ++it;
+        CK(cudaMemcpyAsync(&rr, &h->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (std::sqrt(rr) / nb <= tol) {
+            CK(residual_d(A, lanes, h->b, h->x, h->t, s));
+            CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
+            double tt = 0.0;
+            CK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (std::sqrt(tt) / nb <= tol) { result = AMG_OK; break; }
+            CK(cudaMemcpyAsync(h->r, h->t, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+        }
+        CK(vcycle(h->ctx, h->r, h->z, s));
+        CK(dot_partial(h->r, h->z, n, h->partial, s));
+        CK(pcg_beta(h->partial, h->sc, s));
+        CK(pcg_update_p(n, h->pv, h->z, h->sc, s));
+    }
+finish:
+    if (n > 0) {
+        CK(residual_d(A, lanes, h->b, h->x, h->t, s));
+        CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
+        double tt = 0.0;
+        CK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(x, h->x, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+        CK(cudaStreamSynchronize(s));
+        relres = nb > 0.0 ? std::sqrt(tt) / nb : 0.0;
+    }
+    st = result;
+done:
+    if (info) {
+        info->iters = it;
+        info->status = st;
+        info->relres_true = relres;
+        info->setup_ms = h->setup_ms;
+        info->solve_ms = now_ms() - t0;
+        info->levels = h->nlev;
+        double tot = 0.0;
+        for (int L = 0; L < h->nlev; ++L) tot += (double)h->lev[L].A.nnz;
+        info->op_complexity = h->fine_nnz > 0 ? tot / (double)h->fine_nnz : 0.0;
+    }
+    return st;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct ExportSrc {
+    const void *ptr = nullptr;
+    int64_t count = 0;
+    int kind = 0;     // 0 raw bytes of elem size, 1 int32 row pointer widened to int64
+    size_t elem = 1;
+};
+
+ExportSrc export_src(const amg_hierarchy *h, int level, int what)
+{
+    ExportSrc e;
+    const Level &lv = h->lev[level];
+    const bool last = level == h->nlev - 1;
+    auto rowptr = [&](const DevCsr &c, int rows) {
+        ExportSrc r;
+        if (!c.rp) return r;
+        r.ptr = c.rp; r.count = rows + 1; r.kind = 1; r.elem = 8;
+        return r;
+    };
+    auto arr = [&](const void *p, int64_t cnt, size_t el) {
+        ExportSrc r;
+        if (!p) return r;
+        r.ptr = p; r.count = cnt; r.elem = el;
+        return r;
+    };
+    switch (what) {
+    case AMG_EX_A_ROWPTR: return rowptr(lv.A, lv.A.n);
+    case AMG_EX_A_COL: return arr(lv.A.ci, lv.A.nnz, 4);
+    case AMG_EX_A_VAL: return arr(lv.A.v, lv.A.nnz, 8);
+    case AMG_EX_NULLSPACE: return arr(lv.B, lv.A.n, 8);
+    default: break;
+    }
+    if (last) return e;
+    switch (what) {
+    case AMG_EX_STRONG: return arr(lv.strong, lv.A.nnz, 1);
+    case AMG_EX_REMOVED: return arr(lv.removed, lv.A.nnz, 1);
+    case AMG_EX_LUMPFLAG: return arr(lv.lumpflag, lv.A.n, 1);
+    case AMG_EX_ABAR_ROWPTR: return rowptr(lv.Abar, lv.Abar.n);
+    case AMG_EX_ABAR_COL: return arr(lv.Abar.ci, lv.Abar.nnz, 4);
+    case AMG_EX_ABAR_VAL: return arr(lv.Abar.v, lv.Abar.nnz, 8);
+    case AMG_EX_AGG: return arr(lv.agg, lv.A.n, 4);
+    case AMG_EX_ROOT: return arr(lv.root, lv.A.n, 1);
+    case AMG_EX_P_ROWPTR: return rowptr(lv.P, lv.P.n);
+    case AMG_EX_P_COL: return arr(lv.P.ci, lv.P.nnz, 4);
+    case AMG_EX_P_VAL: return arr(lv.P.v, lv.P.nnz, 8);
+    case AMG_EX_R_ROWPTR: return rowptr(lv.R, lv.R.n);
+    case AMG_EX_R_COL: return arr(lv.R.ci, lv.R.nnz, 4);
+    case AMG_EX_R_VAL: return arr(lv.R.v, lv.R.nnz, 8);
+    case AMG_EX_DSMOOTH: return arr(lv.Dsm, lv.A.n, 8);
+    case AMG_EX_CFLAG: return arr(lv.cflag, lv.A.n, 1);
+    case AMG_EX_SCALARS: e.count = 4; e.elem = 8; e.kind = 2; return e;
+    default: return e;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+amg_status_t amg_export_count(amg_handle_t h, int level, int what, int64_t *count)
+{
+    if (!h || !count || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
+    if (what < 0 || what > AMG_EX_CFLAG) return AMG_ERR_INVALID_ARG;
+    *count = export_src(h, level, what).count;
+    return AMG_OK;
+}
+
+amg_status_t amg_export(amg_handle_t h, int level, int what, void *dst)
+{
+    if (!h || !dst || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
+    if (what < 0 || what > AMG_EX_CFLAG) return AMG_ERR_INVALID_ARG;
+    ExportSrc e = export_src(h, level, what);
+    if (e.count == 0) return AMG_OK;
+    const Level &lv = h->lev[level];
+    if (e.kind == 2) {
+        double sc[4] = {lv.lambda_bar, lv.omega, lv.lambda_cheb, (double)lv.nagg};
+        std::memcpy(dst, sc, sizeof sc);
+        return AMG_OK;
+    }
+    cudaError_t err;
+    if (e.kind == 1) {
+        std::vector<int> tmp((size_t)e.count);
+        err = cudaMemcpy(tmp.data(), e.ptr, sizeof(int) * (size_t)e.count, cudaMemcpyDeviceToHost);
+        if (err != cudaSuccess) return fail_cuda(err, "amg_export");
+        int64_t *o = (int64_t *)dst;
+        for (int64_t i = 0; i < e.count; ++i) o[i] = tmp[(size_t)i];
+        return AMG_OK;
+    }
+    err = cudaMemcpy(dst, e.ptr, e.elem * (size_t)e.count, cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return fail_cuda(err, "amg_export");
+    return AMG_OK;
+}
+
+amg_status_t amg_csr_release(amg_dcsr_t *C)
+{
+    if (!C) return AMG_OK;
+    cudaFree(C->row_ptr);
+    cudaFree(C->col);
+    cudaFree(C->val);
+    C->row_ptr = nullptr; C->col = nullptr; C->val = nullptr;
+    C->nrow = C->ncol = C->nnz = 0;
+    return AMG_OK;
+}
+
+amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *col, double *val)
+{
+    if (!C || !row_ptr || (C->nnz > 0 && (!col || !val))) return AMG_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpy(row_ptr, C->row_ptr, sizeof(int64_t) * (size_t)(C->nrow + 1), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && C->nnz > 0) e = cudaMemcpy(col, C->col, sizeof(int32_t) * (size_t)C->nnz, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && C->nnz > 0) e = cudaMemcpy(val, C->val, sizeof(double) * (size_t)C->nnz, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? AMG_OK : fail_cuda(e, "amg_dcsr_download");
+}
+
+amg_status_t amg_spgemm(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB, void *stream,
+                        amg_dcsr_t *C)
+{
+    if (!A || !B || !C) return AMG_ERR_INVALID_ARG;
+    *C = amg_dcsr_t{0, 0, 0, nullptr, nullptr, nullptr};
+    if (A->n < 0 || B->n < 0 || ncolA != B->n || ncolB < 0 || A->n > 0x7ffffffe || B->n > 0x7ffffffe ||
+        A->nnz > 0x7ffffffe || B->nnz > 0x7ffffffe || ncolB > 0x7ffffffe)
+        return AMG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    amg_status_t st = AMG_OK;
+    DevCsr dA, dB, dC;
+    int64_t *rp64 = nullptr;
+    int *bad = nullptr;
+    int ovf = 0, hbad = 0;
+    const amg_csr_t *src[2] = {A, B};
+    DevCsr *dst[2] = {&dA, &dB};
+    CK(cudaMalloc(&bad, sizeof(int)));
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    for (int t = 0; t < 2; ++t) {
+        const amg_csr_t *m = src[t];
+        DevCsr *d = dst[t];
+        d->n = (int)m->n;
+        d->ncol = t == 0 ? (int)ncolA : (int)ncolB;
+        d->nnz = m->nnz;
+        CK(cudaMalloc(&d->rp, sizeof(int) * (size_t)(m->n + 1)));
+        CK(cudaMalloc(&d->ci, sizeof(int) * (size_t)(m->nnz > 0 ? m->nnz : 1)));
+        CK(cudaMalloc(&d->v, sizeof(double) * (size_t)(m->nnz > 0 ? m->nnz : 1)));
+        CK(cudaMalloc(&rp64, sizeof(int64_t) * (size_t)(m->n + 1)));
+        CK(cudaMemcpyAsync(rp64, m->row_ptr, sizeof(int64_t) * (size_t)(m->n + 1), cudaMemcpyDefault, s));
+        CK(convert_rowptr_to32(rp64, d->rp, (int)m->n + 1, bad, s));
+        if (m->nnz > 0) {
+            CK(cudaMemcpyAsync(d->ci, m->col, sizeof(int) * (size_t)m->nnz, cudaMemcpyDefault, s));
+            CK(cudaMemcpyAsync(d->v, m->val, sizeof(double) * (size_t)m->nnz, cudaMemcpyDefault, s));
+        }
+        CK(cudaStreamSynchronize(s));
+        cudaFree(rp64);
+        rp64 = nullptr;
+    }
+    CK(cudaMemcpy(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (hbad) { st = AMG_ERR_INVALID_ARG; goto done; }
+    {
+        cudaError_t e = spgemm(dA, dB, dC, &ovf, s);
+        if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow"; st = AMG_ERR_INTERNAL; goto done; }
+        CK(e);
+    }
+    CK(cudaMalloc(&C->row_ptr, sizeof(int64_t) * (size_t)(dC.n + 1)));
+    CK(convert_rowptr_to64(dC.rp, C->row_ptr, dC.n + 1, s));
+    CK(cudaStreamSynchronize(s));
+    C->nrow = dC.n;
+    C->ncol = ncolB;
+    C->nnz = dC.nnz;
+    C->col = dC.ci;
+    C->val = dC.v;
+    dC.ci = nullptr;
+    dC.v = nullptr;
+done:
+    cudaFree(bad); cudaFree(rp64);
+    cudaFree(dA.rp); cudaFree(dA.ci); cudaFree(dA.v);
+    cudaFree(dB.rp); cudaFree(dB.ci); cudaFree(dB.v);
+    cudaFree(dC.rp); cudaFree(dC.ci); cudaFree(dC.v);
+    if (st != AMG_OK) amg_csr_release(C);
+    return st;
+}
+
+}  // extern "C"

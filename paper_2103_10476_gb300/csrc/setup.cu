@@ -1,0 +1,981 @@
+// setup.cu -- hierarchy-setup kernels: strength of connection, filtering and lumping,
+// aggregation, tentative and smoothed prolongator with the four adaptations, transpose and
+// eigenvalue estimates.
+//
+// Compiled with --fmad=false: every product and sum is rounded as written, and every
+// per-row sum runs in ascending column order, so the values match a sequential evaluation
+// of the same formulas bit for bit (decisions taken on them are then identical too).
+#include <math.h>
+
+#include "amg_internal.cuh"
+
+namespace amgk {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ------------------------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t splitmix_mix(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Aggregation priority: top 30 bits of the SplitMix64 finaliser of seed ^ (level << 40) ^ i,
+// then the index; distinct for distinct i.
+__device__ __forceinline__ uint64_t agg_priority(uint64_t seed, int level, int i)
+{
+    uint64_t h = splitmix_mix(seed ^ ((uint64_t)level << 40) ^ (uint64_t)(uint32_t)i);
+    return ((h >> 34) << 32) | (uint64_t)(uint32_t)i;
+}
+
+// Sequential (ascending-lane) sum of one warp-wide chunk added to acc; every lane returns
+// the same value.  Lanes that contribute nothing pass +0.0 (which leaves the sum unchanged).
+__device__ __forceinline__ double warp_seq_sum(double acc, double x)
+{
+#pragma unroll
+    for (int t = 0; t < 32; ++t) acc = acc + __shfl_sync(kFull, x, t);
+    return acc;
+}
+
+// ------------------------------------------------------------------------------------ diagonal
+__global__ void diag_kernel(int n, const int *rp, const int *ci, const double *v, int *pos, double *d)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int lo = rp[i], hi = rp[i + 1] - 1, found = -1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int c = ci[mid];
+        if (c == i) { found = mid; break; }
+        if (c < i) lo = mid + 1; else hi = mid - 1;
+    }
+    if (pos) pos[i] = found;
+    if (d) d[i] = found >= 0 ? v[found] : 0.0;
+}
+
+cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    diag_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, diagpos, d); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ strength, Eq. (7)
+// One warp per row.  theta = 0 makes every stored off-diagonal strong (the filtered matrix is
+// then A); otherwise |a_ij| >= theta * sqrt(a_ii * a_jj) with each operation rounded, and a
+// negative product (sqrt = NaN) makes the entry weak.
+__global__ void strength_kernel(int n, const int *rp, const int *ci, const double *v, const double *d,
+                                double theta, uint8_t *strong, uint8_t *removed, int *kept)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int b = rp[i], e_end = rp[i + 1];
+    const double di = d[i];
+    int nkept = 0;
+    for (int base = b; base < e_end; base += 32) {
+        int e = base + lane;
+        bool rem = false;
+        if (e < e_end) {
+            int j = ci[e];
+            bool s = false;
+            if (j != i) {
+                if (theta == 0.0) {
+                    s = true;
+                } else {
+                    double prod = __dmul_rn(di, d[j]);
+                    double thr = __dmul_rn(theta, __dsqrt_rn(prod));
+                    s = fabs(v[e]) >= thr;
+                }
+                rem = !s;
+            }
+            strong[e] = s ? 1 : 0;
+            removed[e] = rem ? 1 : 0;
+        }
+        unsigned keep = __ballot_sync(kFull, e < e_end && !rem);
+        nkept += __popc(keep);
+    }
+    if (lane == 0) kept[i] = nkept;
+}
+
+cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
+                     int *kept, cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    strength_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, theta, strong,
+                                                                     removed, kept); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ strong graph
+__global__ void sg_count_kernel(int n, const int *rp, const uint8_t *strong, int *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    int c = 0;
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) c += strong[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
+    if (lane == 0) cnt[i] = c;
+}
+
+__global__ void sg_fill_kernel(int n, const int *rp, const int *ci, const uint8_t *strong, const int *grp,
+                               int *gci)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    int out = grp[i];
+    for (int base = rp[i]; base < rp[i + 1]; base += 32) {
+        int e = base + lane;
+        bool s = e < rp[i + 1] && strong[e];
+        unsigned m = __ballot_sync(kFull, s);
+        if (s) gci[out + __popc(m & ((1u << lane) - 1u))] = ci[e];
+        out += __popc(m);
+    }
+}
+
+cudaError_t strong_graph_counts(const DevCsr &A, const uint8_t *strong, int *cnt, cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    sg_count_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, strong, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t strong_graph_fill(const DevCsr &A, const uint8_t *strong, const int *grp, int *gci, cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    sg_fill_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, strong, grp, gci); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ aggregation
+// Roots: the greedy maximal independent set of the distance-2 strong graph in decreasing
+// priority.  Computed by synchronous rounds on 64-bit tuples (state << 62 | priority) with
+// state OUT = 0 < UNDECIDED = 1 < ROOT = 2: two rounds of max-propagation over the strong
+// graph give each vertex the largest tuple within distance 2; an undecided vertex whose own
+// tuple is that maximum becomes a root, one that sees a root becomes OUT.  A vertex joins
+// only when every higher-priority vertex within distance 2 is OUT, and leaves only next to a
+// root, so the result is the sequential greedy set.
+constexpr unsigned long long kStUndec = 1ULL << 62;
+constexpr unsigned long long kStRoot = 2ULL << 62;
+constexpr unsigned long long kPrioMask = (1ULL << 62) - 1ULL;
+
+__global__ void mis_init_kernel(int n, uint64_t seed, int level, unsigned long long *t0)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t0[i] = kStUndec | agg_priority(seed, level, i);
+}
+
+// one sub-warp of 8 lanes per vertex (no early exit: the shuffles use the full warp)
+__global__ void mis_max_kernel(int n, const int *grp, const int *gci, const unsigned long long *in,
+                               unsigned long long *out)
+{
+    const int sub = threadIdx.x & 7;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool valid = i < n;
+    unsigned long long m = (valid && sub == 0) ? in[i] : 0ULL;
+    if (valid) {
+        for (int e = grp[i] + sub; e < grp[i + 1]; e += 8) {
+            unsigned long long t = in[gci[e]];
+            m = t > m ? t : m;
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(kFull, m, o, 8);
+        m = t > m ? t : m;
+    }
+    if (valid && sub == 0) out[i] = m;
+}
+
+__global__ void mis_decide_kernel(int n, const int *grp, const int *gci, const unsigned long long *t1,
+                                  unsigned long long *t0, int *undecided)
+{
+    const int sub = threadIdx.x & 7;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const bool valid = i < n;
+    int und = 0;
+    unsigned long long m = (valid && sub == 0) ? t1[i] : 0ULL;
+    if (valid) {
+        for (int e = grp[i] + sub; e < grp[i + 1]; e += 8) {
+            unsigned long long t = t1[gci[e]];
+            m = t > m ? t : m;
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        unsigned long long t = __shfl_down_sync(kFull, m, o, 8);
+        m = t > m ? t : m;
+    }
+    if (valid && sub == 0) {
+        unsigned long long own = t0[i];
+        if ((own >> 62) == 1ULL) {
+            if (m == own) t0[i] = kStRoot | (own & kPrioMask);
+            else if ((m >> 62) == 2ULL) t0[i] = own & kPrioMask;
+            else und = 1;
+        }
+    }
+    // block-level count of still-undecided vertices
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    if (und) atomicAdd(&cnt, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && cnt) atomicAdd(undecided, cnt);
+}
+
+__global__ void mis_roots_kernel(int n, const unsigned long long *t0, uint8_t *root, int *rootflag_int)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = (t0[i] >> 62) == 2ULL;
+    root[i] = (uint8_t)r;
+    rootflag_int[i] = r;
+}
+
+// Join 1: a non-root adjacent to roots joins the adjacent root of largest priority.
+__global__ void join1_kernel(int n, const int *grp, const int *gci, const uint8_t *root, uint64_t seed, int level,
+                             int *join1)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (root[i]) { join1[i] = i; return; }
+    int best = -1;
+    uint64_t bk = 0;
+    for (int e = grp[i]; e < grp[i + 1]; ++e) {
+        int u = gci[e];
+        if (root[u]) {
+            uint64_t k = agg_priority(seed, level, u);
+            if (best < 0 || k > bk) { best = u; bk = k; }
+        }
+    }
+    join1[i] = best;
+}
+
+// Join 2: a vertex not yet assigned joins through the step-1 neighbour whose root has the
+// largest priority (reads only step-1 results).
+__global__ void join2_kernel(int n, const int *grp, const int *gci, const uint8_t *root, const int *join1,
+                             uint64_t seed, int level, int *rootof)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = join1[i];
+    if (r < 0) {
+        uint64_t bk = 0;
+        for (int e = grp[i]; e < grp[i + 1]; ++e) {
+            int u = gci[e];
+            int ru = join1[u];
+            if (!root[u] && ru >= 0) {
+                uint64_t k = agg_priority(seed, level, ru);
+                if (r < 0 || k > bk) { r = ru; bk = k; }
+            }
+        }
+    }
+    rootof[i] = r;
+}
+
+__global__ void agg_ids_kernel(int n, const int *rootof, const int *rootid, int *agg, int *bad)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int r = rootof[i];
+    if (r < 0) { agg[i] = -1; atomicAdd(bad, 1); }
+    else agg[i] = rootid[r];
+}
+
+cudaError_t aggregate_mis2(int n, const int *grp, const int *gci, uint64_t seed, int level, AggWork w, int *agg,
+                           uint8_t *root, int *nagg_host, int *rounds_host, cudaStream_t s)
+{
+    *nagg_host = 0;
+    *rounds_host = 0;
+    if (n == 0) return cudaSuccess;
+    const int tb = 256;
+    mis_init_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, seed, level, w.t0); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    int h_und = 1, rounds = 0;
+    while (h_und > 0) {
+        if (rounds >= 10000) return cudaErrorLaunchFailure;   // cannot happen: each round decides >= 1 vertex
+        AMG_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+        mis_max_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t0, w.t1); note_launch();
+        mis_decide_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t1, w.t0, w.counter); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        AMG_CUDA_TRY(cudaMemcpyAsync(&h_und, w.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        ++rounds;
+    }
+    *rounds_host = rounds;
+    // root flags and ids (exclusive scan of root flags -> aggregate numbers by increasing root index)
+    int *rootid = w.rootof;           // n+1 ints of scratch (rootof reused below after ids)
+    mis_roots_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, w.t0, root, rootid); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(scan_exclusive(rootid, rootid, n, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(nagg_host, rootid + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    join1_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, grp, gci, root, seed, level, w.join1); note_launch();
+    // agg[] temporarily holds the root of each vertex
+    join2_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, grp, gci, root, w.join1, seed, level, agg); note_launch();
+    AMG_CUDA_TRY(cudaMemsetAsync(w.counter + 1, 0, sizeof(int), s));
+    // agg_ids reads rootof (in agg) and writes agg: use join1 as the staging copy
+    AMG_CUDA_TRY(cudaMemcpyAsync(w.join1, agg, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    agg_ids_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, w.join1, rootid, agg, w.counter + 1); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    int bad = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&bad, w.counter + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------ aggregate members
+__global__ void member_count_kernel(int n, const int *agg, int *cnt)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void member_scatter_kernel(int n, const int *agg, const int *mstart, int *fill, int *tmp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        int a = agg[i];
+        int p = mstart[a] + atomicAdd(&fill[a], 1);
+        tmp[p] = i;
+    }
+}
+// one warp per aggregate: place each member at its rank (members are distinct)
+__global__ void member_sort_kernel(int nagg, const int *mstart, const int *tmp, int *members)
+{
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (a >= nagg) return;
+    const int b = mstart[a], m = mstart[a + 1] - b;
+    for (int t = lane; t < m; t += 32) {
+        int v = tmp[b + t], rank = 0;
+        for (int u = 0; u < m; ++u) rank += tmp[b + u] < v;
+        members[b + rank] = v;
+    }
+}
+
+cudaError_t aggregate_members(int n, int nagg, const int *agg, int *mstart, int *members, int *fill, cudaStream_t s)
+{
+    AMG_CUDA_TRY(cudaMemsetAsync(mstart, 0, sizeof(int) * (size_t)(nagg + 1), s));
+    if (n == 0) return cudaSuccess;
+    member_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, agg, mstart); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(scan_exclusive(mstart, mstart, nagg, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)nagg, s));
+    int *tmp = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&tmp, sizeof(int) * (size_t)n, s));
+    member_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, agg, mstart, fill, tmp); note_launch();
+    member_sort_kernel<<<grid_for((int64_t)nagg * 32, 256), 256, 0, s>>>(nagg, mstart, tmp, members); note_launch();
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaFreeAsync(tmp, s);
+    return e != cudaSuccess ? e : e2;
+}
+
+// sum of B^2 over members in ascending order, then sqrt
+__global__ void agg_norm_kernel(int nagg, const int *mstart, const int *members, const double *B, double *nrm,
+                                int *bad)
+{
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nagg) return;
+    double ss = 0.0;
+    for (int t = mstart[a]; t < mstart[a + 1]; ++t) {
+        double b = B[members[t]];
+        ss = ss + b * b;
+    }
+    if (!(ss > 0.0)) atomicAdd(bad, 1);
+    nrm[a] = __dsqrt_rn(ss);
+}
+
+cudaError_t aggregate_norms(int nagg, const int *mstart, const int *members, const double *B, double *nrm,
+                            int *bad, cudaStream_t s)
+{
+    if (nagg == 0) return cudaSuccess;
+    agg_norm_kernel<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, mstart, members, B, nrm, bad); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ §2.5 sparsification
+// One warp per aggregate a with root rho.  For each distinct aggregate c != a reached by a
+// weak entry of rho's row and holding no strong neighbour of rho, count the strong links
+// from a's non-root members into c; a single link is marked for dropping.
+__global__ void sprsfy_kernel(int nagg, const int *rp, const int *ci, const uint8_t *strong, const int *agg,
+                              const int *mstart, const int *members, const uint8_t *root, uint8_t *drop)
+{
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (a >= nagg) return;
+    const int mb = mstart[a], me = mstart[a + 1];
+    // the root of aggregate a
+    int rho = -1;
+    for (int t = mb + lane; t < me; t += 32)
+        if (root[members[t]]) rho = members[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rho = max(rho, __shfl_xor_sync(kFull, rho, o));
+    if (rho < 0) return;
+    const int rb = rp[rho], re = rp[rho + 1];
+    for (int e = rb; e < re; ++e) {
+        int j = ci[e];
+        if (j == rho || strong[e]) continue;
+        int c = agg[j];
+        if (c == a) continue;
+        // first weak entry of rho's row reaching c, and no strong neighbour of rho in c
+        int skip = 0;
+        for (int f = rb + lane; f < re; f += 32) {
+            int jf = ci[f];
+            if (jf == rho) continue;
+            if (agg[jf] != c) continue;
+            if (strong[f]) skip = 1;
+            else if (f < e) skip = 1;
+        }
+        if (__any_sync(kFull, skip)) continue;
+        int cnt = 0, link = -1;
+        for (int t = mb + lane; t < me; t += 32) {
+            int v = members[t];
+            if (v == rho) continue;
+            for (int f = rp[v]; f < rp[v + 1]; ++f) {
+                int w = ci[f];
+                if (w != v && strong[f] && agg[w] == c) { ++cnt; link = f; }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt += __shfl_xor_sync(kFull, cnt, o);
+            link = max(link, __shfl_xor_sync(kFull, link, o));
+        }
+        if (cnt == 1 && lane == 0) drop[link] = 1;
+    }
+}
+
+// removed |= drop on (v, w) and on (w, v); kept counts recomputed afterwards
+__global__ void sprsfy_symm_kernel(int n, const int *rp, const int *ci, const uint8_t *drop, uint8_t *removed)
+{
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    for (int e = rp[v]; e < rp[v + 1]; ++e) {
+        if (!drop[e]) continue;
+        removed[e] = 1;
+        int w = ci[e];
+        int lo = rp[w], hi = rp[w + 1] - 1;
+        while (lo <= hi) {
+            int mid = (lo + hi) >> 1;
+            int c = ci[mid];
+            if (c == v) { removed[mid] = 1; break; }
+            if (c < v) lo = mid + 1; else hi = mid - 1;
+        }
+    }
+}
+
+__global__ void kept_count_kernel(int n, const int *rp, const int *ci, const uint8_t *removed, int *kept)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int k = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) k += (ci[e] == i) || !removed[e];
+    kept[i] = k;
+}
+
+cudaError_t sprsfy(const DevCsr &A, const uint8_t *strong, const int *agg, const uint8_t *root, int nagg,
+                   const int *mstart, const int *members, uint8_t *drop, uint8_t *removed, int *kept,
+                   cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    AMG_CUDA_TRY(cudaMemsetAsync(drop, 0, (size_t)A.nnz, s));
+    sprsfy_kernel<<<grid_for((int64_t)nagg * 32, 128), 128, 0, s>>>(nagg, A.rp, A.ci, strong, agg, mstart,
+                                                                     members, root, drop); note_launch();
+    sprsfy_symm_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, drop, removed); note_launch();
+    kept_count_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, A.rp, A.ci, removed, kept); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ filtered matrix
+// One warp per row.  Standard (Eq. 6): removed entries summed in ascending column order and
+// added to a_ii.  OffLmp: Algorithm 2 with these readings -- r = 0 takes the diagonal branch;
+// D(A_i) counts every off-diagonal of A; a_ii <= 0 falls back to Eq. (6); with K- empty all of
+// r goes to K+ if K+ is not empty, else the row is left unlumped; the diagonal share is the
+// largest r in [0, |rhat|] keeping (N - r)/(a_ii - r) <= t (N = -kappa- - rhat,
+// t = tau D(A_i)): |rhat| if N <= a_ii, min(|rhat|, (t a_ii - N)/(t - 1)) if a_ii < N <= t a_ii,
+// and 0 if N > t a_ii.
+// The smoothing diagonal: Dbar_ii, or (1Norm) Dtilde_ii = sum_j |Abar_ij| raised to
+// 4 s_i / (3 (1 - sigma)) (2 s_i for sigma = 1/3) and set to 1 for an all-zero row (Eq. 9-11).
+enum { LUMP_DIAG = 0, LUMP_KPLUS = 1, LUMP_DIAG_KMINUS = 2, LUMP_KPLUS_NEG = 3, LUMP_SKIPPED = 4,
+       LUMP_FALLBACK = 5 };
+
+__global__ void filter_kernel(int n, const int *rp, const int *ci, const double *v, const uint8_t *removed,
+                              int offlmp, double tau, int onenorm, double sigma, const int *brp, int *bci,
+                              double *bv, double *Dsm, uint8_t *lumpflag, int *zero_diag)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int b = rp[i], e_end = rp[i + 1];
+    // pass 1: row sums in ascending order
+    double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
+    int nkp = 0, nkm = 0, has_diag = 0;
+    for (int base = b; base < e_end; base += 32) {
+        int e = base + lane;
+        double x = 0.0, xp = 0.0, xm = 0.0, xa = 0.0;
+        int isd = 0;
+        if (e < e_end) {
+            int j = ci[e];
+            double val = v[e];
+            if (j == i) { isd = 1; }
+            else {
+                xa = fabs(val);
+                if (removed[e]) x = val;
+                else if (val > 0.0) xp = val;
+                else if (val < 0.0) xm = val;
+            }
+        }
+        r = warp_seq_sum(r, x);
+        if (offlmp) {
+            kp = warp_seq_sum(kp, xp);
+            km = warp_seq_sum(km, xm);
+            offabs = warp_seq_sum(offabs, xa);
+            nkp += __popc(__ballot_sync(kFull, xp > 0.0));
+            nkm += __popc(__ballot_sync(kFull, xm < 0.0));
+        }
+        unsigned dm = __ballot_sync(kFull, isd);
+        if (dm) {
+            int src = __ffs(dm) - 1;
+            aii = __shfl_sync(kFull, e < e_end ? v[e < e_end ? e : b] : 0.0, src);
+            has_diag = 1;
+        }
+    }
+    // decide the row's outcome (every lane computes the same)
+    int flag = LUMP_DIAG;
+    double new_diag = aii + r;     // Eq. (6)
+    double fplus = 1.0, fminus = 1.0;
+    bool zero_plus = false;
+    if (offlmp) {
+        if (!(aii > 0.0)) {
+            flag = LUMP_FALLBACK;
+        } else if (r >= 0.0) {
+            flag = LUMP_DIAG;
+        } else if (fabs(r) <= kp) {
+            flag = LUMP_KPLUS;
+            new_diag = aii;
+            fplus = 1.0 + r / kp;
+        } else if (nkm == 0) {
+            new_diag = aii;
+            if (nkp > 0) {
+                flag = LUMP_KPLUS_NEG;
+                fplus = 1.0 + r / kp;
+            } else {
+                flag = LUMP_SKIPPED;
+            }
+        } else {
+            flag = LUMP_DIAG_KMINUS;
+            zero_plus = true;
+            double rhat = r + kp;
+            double t_bound = tau * (offabs / fabs(aii));
+            double N = -km - rhat;
+            double mag = -rhat;
+            double rstar;
+            if (N <= aii) {
+                rstar = mag;
+            } else if (N <= t_bound * aii) {
+                double rmax = (t_bound * aii - N) / (t_bound - 1.0);
+                rstar = rmax < mag ? rmax : mag;
+            } else {
+                rstar = 0.0;
+            }
+            new_diag = aii - rstar;
+            fminus = 1.0 + (rhat + rstar) / km;
+        }
+    }
+    // pass 2: write the kept entries, and the 1-norm sums over them in ascending order
+    int out = brp[i];
+    double dsum = 0.0, ssum = 0.0;
+    for (int base = b; base < e_end; base += 32) {
+        int e = base + lane;
+        bool keep = false;
+        double nv = 0.0;
+        int j = -1;
+        if (e < e_end) {
+            j = ci[e];
+            double val = v[e];
+            if (j == i) {
+                keep = true;
+                nv = new_diag;
+            } else if (!removed[e]) {
+                keep = true;
+                nv = val;
+                if (offlmp && flag != LUMP_FALLBACK) {
+                    if (val > 0.0) {
+                        if (zero_plus) nv = 0.0;
+                        else if (flag == LUMP_KPLUS || flag == LUMP_KPLUS_NEG) nv = val * fplus;
+                    } else if (val < 0.0 && flag == LUMP_DIAG_KMINUS) {
+                        nv = val * fminus;
+                    }
+                }
+            }
+        }
+        unsigned m = __ballot_sync(kFull, keep);
+        if (keep) {
+            int p = out + __popc(m & ((1u << lane) - 1u));
+            bci[p] = j;
+            bv[p] = nv;
+        }
+        out += __popc(m);
+        if (onenorm) {
+            dsum = warp_seq_sum(dsum, keep ? fabs(nv) : 0.0);
+            ssum = warp_seq_sum(ssum, keep ? nv : 0.0);
+        }
+    }
+    if (lane == 0) {
+        lumpflag[i] = (uint8_t)flag;
+        double dd;
+        if (onenorm) {
+            double f = (sigma == 1.0 / 3.0) ? 2.0 : 4.0 / (3.0 * (1.0 - sigma));
+            dd = dsum;
+            if (dd == 0.0) dd = 1.0;
+            if (dd < f * ssum) dd = f * ssum;
+        } else {
+            dd = has_diag ? new_diag : 0.0;
+            if (dd == 0.0) atomicAdd(zero_diag, 1);
+        }
+        Dsm[i] = dd;
+    }
+}
+
+cudaError_t filter(const DevCsr &A, const uint8_t *removed, int offlmp, double tau, int onenorm, double sigma,
+                   DevCsr &Abar, double *Dsm, uint8_t *lumpflag, int *zero_diag, cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    filter_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, removed, offlmp, tau,
+                                                                   onenorm, sigma, Abar.rp, Abar.ci, Abar.v, Dsm,
+                                                                   lumpflag, zero_diag); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ smoothed prolongator
+// Row i of P = (I - omega D^-1 Abar) Pt has the aggregates of Abar's row-i columns, sorted;
+// (Abar Pt)_ic sums Abar_ik B_k over those k (ascending) with agg(k) = c.
+__global__ void smooth_count_kernel(int n, const int *rp, const int *ci, const int *agg, int *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int b = rp[i], m = rp[i + 1] - b;
+    int distinct = 0;
+    for (int t = lane; t < m; t += 32) {
+        int c = agg[ci[b + t]];
+        bool first = true;
+        for (int u = 0; u < t; ++u)
+            if (agg[ci[b + u]] == c) { first = false; break; }
+        distinct += first;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) distinct += __shfl_down_sync(kFull, distinct, o);
+    if (lane == 0) cnt[i] = distinct;
+}
+
+__global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const double *v, const int *agg,
+                                   const double *B, const double *Dsm, const double *omega_dev, const int *prp,
+                                   int *pci, double *pv)
+{
+    const int lane = threadIdx.x & 31;
+    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= n) return;
+    const int b = rp[i], m = rp[i + 1] - b;
+    const double scale = *omega_dev / Dsm[i];
+    const int ai = agg[i];
+    const double bi = B[i];
+    for (int t = lane; t < m; t += 32) {
+        int c = agg[ci[b + t]];
+        bool first = true;
+        for (int u = 0; u < t; ++u)
+            if (agg[ci[b + u]] == c) { first = false; break; }
+        if (!first) continue;
+        // rank among distinct columns, and the ordered sum
+        int rank = 0;
+        double acc = 0.0;
+        for (int u = 0; u < m; ++u) {
+            int k = ci[b + u];
+            int cu = agg[k];
+            if (cu == c) {
+                acc = acc + v[b + u] * B[k];
+            } else if (cu < c) {
+                bool fu = true;
+                for (int w = 0; w < u; ++w)
+                    if (agg[ci[b + w]] == cu) { fu = false; break; }
+                rank += fu;
+            }
+        }
+        double pt = (c == ai) ? bi : 0.0;
+        int p = prp[i] + rank;
+        pci[p] = c;
+        pv[p] = pt - scale * acc;
+    }
+}
+
+cudaError_t smooth_counts(const DevCsr &Abar, const int *agg, int *cnt, cudaStream_t s)
+{
+    if (Abar.n == 0) return cudaSuccess;
+    smooth_count_kernel<<<grid_for((int64_t)Abar.n * 32, 256), 256, 0, s>>>(Abar.n, Abar.rp, Abar.ci, agg, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t smooth_fill(const DevCsr &Abar, const int *agg, const double *B, const double *Dsm,
+                        const double *omega_dev, DevCsr &P, cudaStream_t s)
+{
+    if (Abar.n == 0) return cudaSuccess;
+    smooth_fill_kernel<<<grid_for((int64_t)Abar.n * 32, 256), 256, 0, s>>>(Abar.n, Abar.rp, Abar.ci, Abar.v, agg, B,
+                                                                           Dsm, omega_dev, P.rp, P.ci, P.v); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ Algorithm 3
+// One thread per row of the unit-basis P.  The working set w starts as the nonzero entries
+// (inw, one byte per stored entry); each pass pins the smallest entry if negative and then
+// the largest if above one (ties to the lowest position) and shares the pinned excess
+// equally over w; the loop runs while any entry is below 0 or above 1, at most m + 1 passes.
+// A negative row sum, a row sum above |w|, or w emptying with a nonzero excess give the
+// tentative row; a zero row sum gives the zero row.
+// Outcome: 0 kept or clipped, 1 zero row, 2 tentative row.
+__global__ void constrain_kernel(int n, const int *rp, const int *ci, double *pv, const int *agg, const double *B,
+                                 uint8_t *inw_all, uint8_t *cflag)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = rp[i], m = rp[i + 1] - b;
+    double *p = pv + b;
+    uint8_t *inw = inw_all + b;
+    double s = 0.0;
+    int nw = 0;
+    for (int k = 0; k < m; ++k) {
+        s = s + p[k];
+        inw[k] = p[k] != 0.0;
+        nw += inw[k];
+    }
+    int outcome = 0;
+    if (s < 0.0 || s > (double)nw) {
+        outcome = 2;
+    } else if (s == 0.0) {
+        for (int k = 0; k < m; ++k) p[k] = 0.0;
+        cflag[i] = 1;
+        return;
+    } else {
+        for (int pass = 0; pass <= m; ++pass) {
+            int kmin = 0, kmax = 0;
+            for (int k = 1; k < m; ++k) {
+                if (p[k] < p[kmin]) kmin = k;
+                if (p[k] > p[kmax]) kmax = k;
+            }
+            if (!(p[kmin] < 0.0 || p[kmax] > 1.0)) break;
+            double delta = 0.0;
+            if (p[kmin] < 0.0) {
+                delta = delta + p[kmin];
+                p[kmin] = 0.0;
+                if (inw[kmin]) { inw[kmin] = 0; --nw; }
+            }
+            if (p[kmax] > 1.0) {
+                delta = delta + (p[kmax] - 1.0);
+                p[kmax] = 1.0;
+                if (inw[kmax]) { inw[kmax] = 0; --nw; }
+            }
+            if (nw == 0) {
+                if (delta != 0.0) outcome = 2;
+                break;
+            }
+            double share = delta / (double)nw;
+            for (int k = 0; k < m; ++k)
+                if (inw[k]) p[k] = p[k] + share;
+        }
+    }
+    if (outcome == 2) {
+        for (int k = 0; k < m; ++k) p[k] = (ci[b + k] == agg[i]) ? B[i] : 0.0;
+    }
+    cflag[i] = (uint8_t)outcome;
+}
+
+cudaError_t constrain(DevCsr &P, const int *agg, const double *B, uint8_t *cflag, cudaStream_t s)
+{
+    if (P.n == 0) return cudaSuccess;
+    uint8_t *inw = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&inw, (size_t)(P.nnz > 0 ? P.nnz : 1), s));
+    constrain_kernel<<<grid_for(P.n, 128), 128, 0, s>>>(P.n, P.rp, P.ci, P.v, agg, B, inw, cflag); note_launch();
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaFreeAsync(inw, s);
+    return e != cudaSuccess ? e : e2;
+}
+
+__global__ void scale_columns_kernel(int64_t nnz, const int *ci, double *v, const double *nrm)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        v[e] = v[e] / nrm[ci[e]];
+}
+
+cudaError_t scale_columns(DevCsr &P, const double *nrm, cudaStream_t s)
+{
+    if (P.nnz == 0) return cudaSuccess;
+    scale_columns_kernel<<<grid_for(P.nnz, 256, 8192), 256, 0, s>>>(P.nnz, P.ci, P.v, nrm); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ transpose
+__global__ void tr_count_kernel(int64_t nnz, const int *ci, int *cnt)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[e]], 1);
+}
+__global__ void tr_scatter_kernel(int n, const int *rp, const int *ci, const double *v, const int *trp, int *fill,
+                                  int *tci, double *tv)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        int c = ci[e];
+        int p = trp[c] + atomicAdd(&fill[c], 1);
+        tci[p] = i;
+        tv[p] = v[e];
+    }
+}
+// one warp per row of the transpose: each entry goes to its rank (row indices are distinct)
+__global__ void tr_sort_kernel(int nrow, const int *trp, const int *tci, const double *tv, int *oci, double *ov)
+{
+    const int lane = threadIdx.x & 31;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= nrow) return;
+    const int b = trp[r], m = trp[r + 1] - b;
+    for (int t = lane; t < m; t += 32) {
+        int key = tci[b + t], rank = 0;
+        for (int u = 0; u < m; ++u) rank += tci[b + u] < key;
+        oci[b + rank] = key;
+        ov[b + rank] = tv[b + t];
+    }
+}
+
+cudaError_t transpose_counts(const DevCsr &P, int *cnt, cudaStream_t s)
+{
+    AMG_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(P.ncol + 1), s));
+    if (P.nnz == 0) return cudaSuccess;
+    tr_count_kernel<<<grid_for(P.nnz, 256, 8192), 256, 0, s>>>(P.nnz, P.ci, cnt); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_fill(const DevCsr &P, DevCsr &R, int *fill, cudaStream_t s)
+{
+    if (P.nnz == 0) return cudaSuccess;
+    AMG_CUDA_TRY(cudaMemsetAsync(fill, 0, sizeof(int) * (size_t)R.n, s));
+    int *tci = nullptr;
+    double *tv = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&tci, sizeof(int) * (size_t)P.nnz, s));
+    cudaError_t e = cudaMallocAsync(&tv, sizeof(double) * (size_t)P.nnz, s);
+    if (e == cudaSuccess) {
+        tr_scatter_kernel<<<grid_for(P.n, 256), 256, 0, s>>>(P.n, P.rp, P.ci, P.v, R.rp, fill, tci, tv); note_launch();
+        tr_sort_kernel<<<grid_for((int64_t)R.n * 32, 256), 256, 0, s>>>(R.n, R.rp, tci, tv, R.ci, R.v); note_launch();
+        e = cudaGetLastError();
+        cudaError_t e2 = cudaFreeAsync(tv, s);
+        if (e == cudaSuccess) e = e2;
+    }
+    cudaError_t e3 = cudaFreeAsync(tci, s);
+    return e != cudaSuccess ? e : e3;
+}
+
+// ------------------------------------------------------------------------------------ power method
+// x0_i = 2 u_i - 1, u_i the i-th output of the SplitMix64 stream started at stream_seed;
+// x = x0 / ||x0||; each sweep y = D^-1 A x, lambda = x . y; between sweeps x = y / ||y||.
+uint64_t power_stream_seed(uint64_t seed, int level, int purpose)
+{
+    return seed ^ ((uint64_t)(level + 1) << 48) ^ ((uint64_t)purpose << 56);
+}
+
+__global__ void power_init_kernel(int n, uint64_t s0, double *x)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t z = splitmix_mix(s0 + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL);
+    double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    x[i] = 2.0 * u - 1.0;
+}
+
+// y = (A x) / D with the partial sums of x . y (one warp per row, fixed grid)
+__global__ void __launch_bounds__(kReduceThreads) power_spmv_kernel(int n, const int *rp, const int *ci,
+                                                                    const double *v, const double *D,
+                                                                    const double *x, double *y, double *partial)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps_total = kReduceBlocks * (kReduceThreads / 32);
+    double acc_dot = 0.0;
+    for (int i = (blockIdx.x * kReduceThreads + threadIdx.x) >> 5; i < n; i += warps_total) {
+        double sum = 0.0;
+        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) sum = sum + v[e] * x[ci[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum = sum + __shfl_xor_sync(kFull, sum, o);
+        double yi = sum / D[i];
+        if (lane == 0) {
+            y[i] = yi;
+            acc_dot = acc_dot + x[i] * yi;
+        }
+    }
+    __shared__ double sh[kReduceThreads / 32];
+    if (lane == 0) sh[threadIdx.x >> 5] = acc_dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) t = t + sh[w];
+        partial[blockIdx.x] = t;
+    }
+}
+
+__global__ void scale_by_norm_kernel(int n, const double *src, double *dst, const double *sq)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] / __dsqrt_rn(*sq);
+}
+
+cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t stream_seed, double *x, double *y,
+                         double *partial, double *scal, double *lambda_dev, cudaStream_t s)
+{
+    const int n = A.n;
+    if (n == 0) return cudaMemsetAsync(lambda_dev, 0, sizeof(double), s);
+    power_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, stream_seed, x); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(dot(x, x, n, partial, scal, s));
+    scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, x, scal); note_launch();
+    for (int k = 0; k < sweeps; ++k) {
+        power_spmv_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, A.rp, A.ci, A.v, D, x, y, partial); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        AMG_CUDA_TRY(reduce_partials(partial, kReduceBlocks, lambda_dev, s));
+        if (k + 1 < sweeps) {
+            AMG_CUDA_TRY(dot(y, y, n, partial, scal, s));
+            scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, y, x, scal); note_launch();
+        }
+    }
+    return cudaGetLastError();
+}
+
+__global__ void omega_kernel(const double *lambda, double *omega)
+{
+    *omega = 4.0 / (3.0 * *lambda);
+}
+
+cudaError_t omega_from_lambda(const double *lambda_dev, double *omega_dev, cudaStream_t s)
+{
+    omega_kernel<<<1, 1, 0, s>>>(lambda_dev, omega_dev); note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void invert_diag_kernel(const double *d, double *inv, float *invf, int n, int *zero)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double di = d[i];
+    if (di == 0.0) atomicAdd(zero, 1);
+    double r = 1.0 / di;
+    inv[i] = r;
+    if (invf) invf[i] = (float)r;
+}
+
+cudaError_t invert_diag(const double *d, double *inv, float *invf, int n, int *zero, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    invert_diag_kernel<<<grid_for(n, 256), 256, 0, s>>>(d, inv, invf, n, zero); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace amgk

@@ -1,0 +1,446 @@
+// spgemm.cu -- two-phase (symbolic count, numeric fill) hash SpGEMM C = A B, one warp per
+// row of A, hash tables in shared memory (global memory for rows whose table does not fit).
+//
+// Numeric order: for each row, the warp walks A's row in ascending k and, for one k at a
+// time, its lanes add a_ik * b_kj into the distinct slots of B's row k; the slots of one k
+// never collide, so every c_ij is the sum over ascending k starting from 0 of separately
+// rounded products (compiled with --fmad=false), independent of the hash layout.
+//
+// Rows are binned by table size so each launch uses one size: the symbolic phase by an
+// upper bound (min(products, columns)), the numeric phase by the exact count.
+#include <stdio.h>
+
+#include "amg_internal.cuh"
+
+namespace amgk {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kMinTable = 32;
+constexpr int kMaxSharedSym = 8192;     // symbolic: 4 bytes per slot
+constexpr int kMaxSharedNum = 4096;     // numeric: 12 bytes per slot
+constexpr int kNumBins = 10;            // 32 .. 8192 and the global bin
+constexpr int kGlobalBin = kNumBins - 1;
+constexpr int kSmemBudget = 96 * 1024;
+
+__device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
+
+// Insert key j into keys[0..S); returns the slot, and whether it was new.  Bounded probing.
+__device__ __forceinline__ int hash_insert(int *keys, int S, int j, bool &fresh, int *overflow)
+{
+    unsigned slot = hash_col(j) & (unsigned)(S - 1);
+    fresh = false;
+    for (int probe = 0; probe < S; ++probe) {
+        int cur = keys[slot];
+        if (cur == j) return (int)slot;
+        if (cur == -1) {
+            int old = atomicCAS(&keys[slot], -1, j);
+            if (old == -1) { fresh = true; return (int)slot; }
+            if (old == j) return (int)slot;
+        }
+        slot = (slot + 1) & (unsigned)(S - 1);
+    }
+    atomicAdd(overflow, 1);
+    return -1;
+}
+
+__device__ __forceinline__ int bin_of_table(int S)
+{
+    int b = 0;
+    while ((kMinTable << b) < S) ++b;
+    return b;
+}
+
+__device__ __forceinline__ int table_for(int64_t need)
+{
+    int S = kMinTable;
+    while ((int64_t)S < 2 * need && S < (1 << 28)) S <<= 1;
+    return S;
+}
+
+// ------------------------------------------------------------------------------------ bounds and bins
+__global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
+                          int *tsize)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t ub = 0;
+    for (int e = arp[i]; e < arp[i + 1]; ++e) {
+        int k = aci[e];
+        ub += brp[k + 1] - brp[k];
+    }
+    int64_t need = ub < ncolB ? ub : ncolB;
+    int S = table_for(need);
+    int b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
+    bin[i] = b;
+    tsize[i] = S;
+    atomicAdd(&binCount[b], 1);
+}
+
+__global__ void exact_bin_kernel(int n, const int *crp, int *bin, int *binCount, int *tsize)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t cnt = crp[i + 1] - crp[i];
+    int S = table_for(cnt);
+    int b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
+    bin[i] = b;
+    tsize[i] = S;
+    atomicAdd(&binCount[b], 1);
+}
+
+__global__ void bin_scatter_kernel(int n, const int *bin, const int *binStart, int *binFill, int *perm)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int b = bin[i];
+    perm[binStart[b] + atomicAdd(&binFill[b], 1)] = i;
+}
+
+// global-bin table offsets: tsize of listed rows, scanned on the host side of the launch
+__global__ void gather_tsize_kernel(int cnt, const int *rows, const int *tsize, int *out)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < cnt) out[t] = tsize[rows[t]];
+}
+
+// ------------------------------------------------------------------------------------ symbolic
+__device__ void symbolic_row(int i, const int *arp, const int *aci, const int *brp, const int *bci, int *keys, int S,
+                             int *ccnt, int *overflow)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < S; t += 32) keys[t] = -1;
+    __syncwarp();
+    int mine = 0;
+    for (int e = arp[i]; e < arp[i + 1]; ++e) {
+        int k = aci[e];
+        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
+            bool fresh;
+            hash_insert(keys, S, bci[f], fresh, overflow);
+            mine += fresh;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFullMask, mine, o);
+    if (lane == 0) ccnt[i] = mine;
+    __syncwarp();
+}
+
+template <int S>
+__global__ void symbolic_shared_kernel(int cnt, const int *rows, const int *arp, const int *aci, const int *brp,
+                                       const int *bci, int *ccnt, int *overflow)
+{
+    extern __shared__ int smem_keys[];
+    const int w = threadIdx.x >> 5;
+    const int row_slot = blockIdx.x * (blockDim.x >> 5) + w;
+    if (row_slot >= cnt) return;
+    symbolic_row(rows[row_slot], arp, aci, brp, bci, smem_keys + w * S, S, ccnt, overflow);
+}
+
+__global__ void symbolic_global_kernel(int cnt, const int *rows, const int *toff, const int *tsize, int *gkeys,
+                                       const int *arp, const int *aci, const int *brp, const int *bci, int *ccnt,
+                                       int *overflow)
+{
+    const int row_slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row_slot >= cnt) return;
+    int i = rows[row_slot];
+    symbolic_row(i, arp, aci, brp, bci, gkeys + toff[row_slot], tsize[i], ccnt, overflow);
+}
+
+// ------------------------------------------------------------------------------------ numeric
+__device__ void numeric_row(int i, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
+                            const double *bv, int *keys, double *vals, int S, const int *crp, int *cci, double *cv,
+                            int *overflow)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < S; t += 32) { keys[t] = -1; vals[t] = 0.0; }
+    __syncwarp();
+    for (int e = arp[i]; e < arp[i + 1]; ++e) {
+        const int k = aci[e];
+        const double a = av[e];
+        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
+            bool fresh;
+            int slot = hash_insert(keys, S, bci[f], fresh, overflow);
+            if (slot >= 0) vals[slot] = vals[slot] + a * bv[f];
+        }
+        __syncwarp();
+    }
+    // compact occupied slots to the front, in slot order
+    int base = 0;
+    for (int t0 = 0; t0 < S; t0 += 32) {
+        int t = t0 + lane;
+        int key = keys[t];
+        double val = vals[t];
+        bool occ = key != -1;
+        unsigned m = __ballot_sync(kFullMask, occ);
+        __syncwarp();
+        if (occ) {
+            int p = base + __popc(m & ((1u << lane) - 1u));
+            keys[p] = key;
+            vals[p] = val;
+        }
+        base += __popc(m);
+        __syncwarp();
+    }
+    const int cnt = base;
+    const int out = crp[i];
+    if (cnt != crp[i + 1] - out) {
+        if (lane == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    if (cnt <= 512) {
+        // each entry to its rank (columns are distinct)
+        for (int t = lane; t < cnt; t += 32) {
+            int key = keys[t], rank = 0;
+            for (int u = 0; u < cnt; ++u) rank += keys[u] < key;
+            cci[out + rank] = key;
+            cv[out + rank] = vals[t];
+        }
+        return;
+    }
+    // bitonic sort of the first P2 slots (padding keys above every column)
+    int P2 = 1;
+    while (P2 < cnt) P2 <<= 1;
+    for (int t = cnt + lane; t < P2; t += 32) { keys[t] = 0x7fffffff; vals[t] = 0.0; }
+    __syncwarp();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < P2; t += 32) {
+                int ixj = t ^ jj;
+                if (ixj > t) {
+                    bool asc = (t & kk) == 0;
+                    int a = keys[t], b = keys[ixj];
+                    if ((a > b) == asc) {
+                        keys[t] = b; keys[ixj] = a;
+                        double va = vals[t];
+                        vals[t] = vals[ixj]; vals[ixj] = va;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (int t = lane; t < cnt; t += 32) {
+        cci[out + t] = keys[t];
+        cv[out + t] = vals[t];
+    }
+}
+
+template <int S>
+__global__ void numeric_shared_kernel(int cnt, const int *rows, const int *arp, const int *aci, const double *av,
+                                      const int *brp, const int *bci, const double *bv, const int *crp, int *cci,
+                                      double *cv, int *overflow)
+{
+    extern __shared__ double smem_num[];
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    double *vals = smem_num + w * S;
+    int *keys = reinterpret_cast<int *>(smem_num + warps * S) + w * S;
+    const int row_slot = blockIdx.x * warps + w;
+    if (row_slot >= cnt) return;
+    numeric_row(rows[row_slot], arp, aci, av, brp, bci, bv, keys, vals, S, crp, cci, cv, overflow);
+}
+
+__global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff, const int *tsize, int *gkeys,
+                                      double *gvals, const int *arp, const int *aci, const double *av, const int *brp,
+                                      const int *bci, const double *bv, const int *crp, int *cci, double *cv,
+                                      int *overflow)
+{
+    const int row_slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row_slot >= cnt) return;
+    int i = rows[row_slot];
+    numeric_row(i, arp, aci, av, brp, bci, bv, gkeys + toff[row_slot], gvals + toff[row_slot], tsize[i], crp, cci, cv,
+                overflow);
+}
+
+// ------------------------------------------------------------------------------------ host side
+namespace {
+
+struct Bins {
+    int count[kNumBins] = {0};
+    int start[kNumBins + 1] = {0};
+};
+
+cudaError_t make_bins(int n, int *d_bin, int *d_binCount, int *d_binFill, int *d_binStart, int *d_perm, Bins &hb,
+                      cudaStream_t s)
+{
+    AMG_CUDA_TRY(cudaMemcpyAsync(hb.count, d_binCount, sizeof(int) * kNumBins, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    hb.start[0] = 0;
+    for (int b = 0; b < kNumBins; ++b) hb.start[b + 1] = hb.start[b] + hb.count[b];
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_binStart, hb.start, sizeof(int) * (kNumBins + 1), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(d_binFill, 0, sizeof(int) * kNumBins, s));
+    if (n > 0) {
+        bin_scatter_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, d_bin, d_binStart, d_binFill, d_perm);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_symbolic(int cnt, const int *rows, const DevCsr &A, const DevCsr &B, int *ccnt, int *ovf,
+                            cudaStream_t s)
+{
+    int warps = kSmemBudget / (S * 4);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    size_t smem = (size_t)warps * S * 4;
+    AMG_CUDA_TRY(cudaFuncSetAttribute(symbolic_shared_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    symbolic_shared_kernel<S><<<(cnt + warps - 1) / warps, warps * 32, smem, s>>>(cnt, rows, A.rp, A.ci, B.rp, B.ci,
+                                                                                 ccnt, ovf); note_launch();
+    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_numeric(int cnt, const int *rows, const DevCsr &A, const DevCsr &B, DevCsr &C, int *ovf,
+                           cudaStream_t s)
+{
+    int warps = kSmemBudget / (S * 12);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    size_t smem = (size_t)warps * S * 12;
+    AMG_CUDA_TRY(cudaFuncSetAttribute(numeric_shared_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    numeric_shared_kernel<S><<<(cnt + warps - 1) / warps, warps * 32, smem, s>>>(cnt, rows, A.rp, A.ci, A.v, B.rp,
+                                                                                B.ci, B.v, C.rp, C.ci, C.v, ovf); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t symbolic_bin(int b, int cnt, const int *rows, const DevCsr &A, const DevCsr &B, int *ccnt, int *ovf,
+                         cudaStream_t s)
+{
+    switch (b) {
+    case 0: return launch_symbolic<32>(cnt, rows, A, B, ccnt, ovf, s);
+    case 1: return launch_symbolic<64>(cnt, rows, A, B, ccnt, ovf, s);
+    case 2: return launch_symbolic<128>(cnt, rows, A, B, ccnt, ovf, s);
+    case 3: return launch_symbolic<256>(cnt, rows, A, B, ccnt, ovf, s);
+    case 4: return launch_symbolic<512>(cnt, rows, A, B, ccnt, ovf, s);
+    case 5: return launch_symbolic<1024>(cnt, rows, A, B, ccnt, ovf, s);
+    case 6: return launch_symbolic<2048>(cnt, rows, A, B, ccnt, ovf, s);
+    case 7: return launch_symbolic<4096>(cnt, rows, A, B, ccnt, ovf, s);
+    case 8: return launch_symbolic<8192>(cnt, rows, A, B, ccnt, ovf, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t numeric_bin(int b, int cnt, const int *rows, const DevCsr &A, const DevCsr &B, DevCsr &C, int *ovf,
+                        cudaStream_t s)
+{
+    switch (b) {
+    case 0: return launch_numeric<32>(cnt, rows, A, B, C, ovf, s);
+    case 1: return launch_numeric<64>(cnt, rows, A, B, C, ovf, s);
+    case 2: return launch_numeric<128>(cnt, rows, A, B, C, ovf, s);
+    case 3: return launch_numeric<256>(cnt, rows, A, B, C, ovf, s);
+    case 4: return launch_numeric<512>(cnt, rows, A, B, C, ovf, s);
+    case 5: return launch_numeric<1024>(cnt, rows, A, B, C, ovf, s);
+    case 6: return launch_numeric<2048>(cnt, rows, A, B, C, ovf, s);
+    case 7: return launch_numeric<4096>(cnt, rows, A, B, C, ovf, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// table offsets (int) for the rows of the global bin; returns total slots
+cudaError_t global_tables(int cnt, const int *rows, const int *tsize, int **toff, int64_t *total, cudaStream_t s)
+{
+    AMG_CUDA_TRY(cudaMallocAsync(toff, sizeof(int) * (size_t)(cnt + 1), s));
+    gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, tsize, *toff); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(scan_exclusive(*toff, *toff, cnt, s));
+    int h = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&h, *toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *total = h;
+    // the int offsets must not wrap
+    if (h < 0) return cudaErrorMemoryAllocation;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s)
+{
+    *overflow_host = 0;
+    C = DevCsr();
+    C.n = A.n;
+    C.ncol = B.ncol;
+    const int n = A.n;
+    AMG_CUDA_TRY(cudaMalloc(&C.rp, sizeof(int) * (size_t)(n + 1)));
+    if (n == 0) {
+        AMG_CUDA_TRY(cudaMemsetAsync(C.rp, 0, sizeof(int), s));
+        return cudaSuccess;
+    }
+    int *work = nullptr;   // bin[n] tsize[n] perm[n] binCount binFill binStart overflow
+    const size_t nwork = (size_t)3 * n + 3 * (kNumBins + 1) + 1;
+    AMG_CUDA_TRY(cudaMallocAsync(&work, sizeof(int) * nwork, s));
+    int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
+    int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
+    int *d_ovf = d_binStart + kNumBins + 1;
+    cudaError_t e = cudaSuccess;
+    int *gkeys = nullptr, *toff = nullptr;
+    double *gvals = nullptr;
+    Bins hb;
+    do {
+        if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
+        if ((e = cudaMemsetAsync(d_ovf, 0, sizeof(int), s))) break;
+        ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize); note_launch();
+        if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
+        // symbolic
+        for (int b = 0; b < kGlobalBin && !e; ++b)
+            if (hb.count[b]) e = symbolic_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, d_ovf, s);
+        if (e) break;
+        if (hb.count[kGlobalBin]) {
+            int cnt = hb.count[kGlobalBin];
+            const int *rows = d_perm + hb.start[kGlobalBin];
+            int64_t total = 0;
+            if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
+            if ((e = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) break;
+            symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
+                cnt, rows, toff, d_tsize, gkeys, A.rp, A.ci, B.rp, B.ci, C.rp, d_ovf); note_launch();
+            if ((e = cudaGetLastError())) break;
+            cudaFreeAsync(gkeys, s); gkeys = nullptr;
+            cudaFreeAsync(toff, s); toff = nullptr;
+        }
+        if ((e = scan_exclusive(C.rp, C.rp, n, s))) break;
+        int nnz = 0;
+        if ((e = cudaMemcpyAsync(&nnz, C.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaMemcpyAsync(overflow_host, d_ovf, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaStreamSynchronize(s))) break;
+        if (*overflow_host || nnz < 0) { e = cudaErrorInvalidValue; break; }
+        C.nnz = nnz;
+        if ((e = cudaMalloc(&C.ci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)))) break;
+        if ((e = cudaMalloc(&C.v, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)))) break;
+        // numeric, binned by the exact row counts
+        if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
+        exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
+        if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
+        for (int b = 0; b < kGlobalBin && !e; ++b)
+            if (hb.count[b]) e = numeric_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C, d_ovf, s);
+        if (e) break;
+        if (hb.count[kGlobalBin]) {
+            int cnt = hb.count[kGlobalBin];
+            const int *rows = d_perm + hb.start[kGlobalBin];
+            int64_t total = 0;
+            if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
+            if ((e = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) break;
+            if ((e = cudaMallocAsync(&gvals, sizeof(double) * (size_t)total, s))) break;
+            numeric_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
+                cnt, rows, toff, d_tsize, gkeys, gvals, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v, d_ovf); note_launch();
+            if ((e = cudaGetLastError())) break;
+        }
+        if ((e = cudaMemcpyAsync(overflow_host, d_ovf, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaStreamSynchronize(s))) break;
+        if (*overflow_host) e = cudaErrorInvalidValue;
+    } while (0);
+    if (gkeys) cudaFreeAsync(gkeys, s);
+    if (gvals) cudaFreeAsync(gvals, s);
+    if (toff) cudaFreeAsync(toff, s);
+    cudaFreeAsync(work, s);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        cudaFree(C.rp); cudaFree(C.ci); cudaFree(C.v);
+        C.rp = nullptr; C.ci = nullptr; C.v = nullptr; C.nnz = 0;
+    }
+    return e;
+}
+
+}  // namespace amgk

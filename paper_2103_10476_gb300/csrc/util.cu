@@ -1,0 +1,305 @@
+// util.cu -- scans, fills, conversions, deterministic reductions, and the launch counter and
+// event-based kernel timing used for roofline reports.
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "amg_internal.cuh"
+
+namespace amgk {
+
+// ------------------------------------------------------------------------------------ counters
+namespace {
+std::atomic<long long> g_launches{0};
+std::atomic<bool> g_prof_on{false};
+std::mutex g_prof_mu;
+struct ProfRecord {
+    int cls;
+    cudaEvent_t start, stop;
+    double bytes;
+};
+std::vector<ProfRecord> g_pending;
+std::vector<cudaEvent_t> g_pool;
+long long g_prof_launches[KC_COUNT];
+double g_prof_ms[KC_COUNT], g_prof_bytes[KC_COUNT];
+
+cudaEvent_t take_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void drain_locked()
+{
+    for (auto &r : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.stop) == cudaSuccess && cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+            g_prof_launches[r.cls] += 1;
+            g_prof_ms[r.cls] += ms;
+            g_prof_bytes[r.cls] += r.bytes;
+        }
+        g_pool.push_back(r.start);
+        g_pool.push_back(r.stop);
+    }
+    g_pending.clear();
+}
+}  // namespace
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+bool profiling_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
+
+ProfScope::ProfScope(int c, cudaStream_t st, double b) : cls(c), s(st), bytes(b)
+{
+    if (!profiling_enabled() || c < 0 || c >= KC_COUNT) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    start = take_event();
+    if (start) cudaEventRecord(start, s);
+}
+
+ProfScope::~ProfScope()
+{
+    if (!start) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEvent_t stop = take_event();
+    if (!stop) { g_pool.push_back(start); return; }
+    cudaEventRecord(stop, s);
+    g_pending.push_back(ProfRecord{cls, start, stop, bytes});
+    if (g_pending.size() > 4096) drain_locked();
+}
+
+void profile_enable(bool on)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_locked();
+    for (int k = 0; k < KC_COUNT; ++k) { g_prof_launches[k] = 0; g_prof_ms[k] = 0.0; g_prof_bytes[k] = 0.0; }
+    g_prof_on.store(on);
+}
+
+void profile_read(int cls, long long *launches, double *ms, double *bytes)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    drain_locked();
+    *launches = g_prof_launches[cls];
+    *ms = g_prof_ms[cls];
+    *bytes = g_prof_bytes[cls];
+}
+
+int grid_for(int64_t work, int threads, int cap)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// ------------------------------------------------------------------------------------ scan
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of one tile; tile total to sums[blockIdx.x]; the last block also stores the
+// running total at out[n] (before the cross-tile offsets are added).
+__global__ void scan_tile_kernel(const int *in, int *out, int n, int *sums)
+{
+    __shared__ int warp_tot[kScanThreads / kWarp];
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int run = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int idx = base + k;
+        int x = idx < n ? in[idx] : 0;
+        v[k] = run;
+        run += x;
+    }
+    // inclusive scan of per-thread totals across the block
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int t = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+    }
+    if (lane == 31) warp_tot[wid] = t;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < kScanThreads / kWarp ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < kScanThreads / kWarp) warp_tot[lane] = w;
+    }
+    __syncthreads();
+    int excl = t - run + (wid > 0 ? warp_tot[wid - 1] : 0);
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        int idx = base + k;
+        if (idx < n) out[idx] = v[k] + excl;
+    }
+    if (threadIdx.x == kScanThreads - 1) {
+        sums[blockIdx.x] = excl + run;
+        if (blockIdx.x == gridDim.x - 1) out[n] = excl + run;
+    }
+}
+
+__global__ void scan_add_kernel(int *out, int n, const int *offs)
+{
+    const int b = blockIdx.x;
+    if (b == 0) return;
+    const int add = offs[b];
+    const int base = b * kScanTile;
+    for (int k = threadIdx.x; k < kScanTile; k += blockDim.x) {
+        int idx = base + k;
+        if (idx < n) out[idx] += add;
+    }
+    if (b == gridDim.x - 1 && threadIdx.x == 0) out[n] += add;
+}
+
+cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t s)
+{
+    if (n <= 0) {
+        return cudaMemsetAsync(out, 0, sizeof(int), s);
+    }
+    int tiles = (n + kScanTile - 1) / kScanTile;
+    int *sums = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&sums, sizeof(int) * (size_t)(tiles + 1), s));
+    scan_tile_kernel<<<tiles, kScanThreads, 0, s>>>(in, out, n, sums); note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && tiles > 1) {
+        e = scan_exclusive(sums, sums, tiles, s);
+        if (e == cudaSuccess) {
+            scan_add_kernel<<<tiles, kScanThreads, 0, s>>>(out, n, sums); note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    cudaError_t e2 = cudaFreeAsync(sums, s);
+    return e != cudaSuccess ? e : e2;
+}
+
+// ------------------------------------------------------------------------------------ fills
+__global__ void fill_int_kernel(int *p, int v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void fill_double_kernel(double *p, double v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+cudaError_t fill_int(int *p, int value, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_int_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(p, value, n); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t fill_double(double *p, double value, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    fill_double_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(p, value, n); note_launch();
+    return cudaGetLastError();
+}
+
+__global__ void rp_to64_kernel(const int *a, int64_t *b, int n1)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) b[i] = a[i];
+}
+__global__ void rp_to32_kernel(const int64_t *a, int *b, int n1, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += gridDim.x * blockDim.x) {
+        int64_t v = a[i];
+        if (v < 0 || v > 0x7fffffffLL || (i > 0 && a[i - 1] > v)) atomicAdd(bad, 1);
+        b[i] = (int)v;
+    }
+}
+__global__ void d2f_kernel(const double *a, float *b, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+cudaError_t convert_rowptr_to64(const int *rp32, int64_t *rp64, int n1, cudaStream_t s)
+{
+    rp_to64_kernel<<<grid_for(n1, 256, 4096), 256, 0, s>>>(rp32, rp64, n1); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t convert_rowptr_to32(const int64_t *rp64, int *rp32, int n1, int *bad, cudaStream_t s)
+{
+    rp_to32_kernel<<<grid_for(n1, 256, 4096), 256, 0, s>>>(rp64, rp32, n1, bad); note_launch();
+    return cudaGetLastError();
+}
+cudaError_t convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    d2f_kernel<<<grid_for(n, 256, 8192), 256, 0, s>>>(in, out, n); note_launch();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ reductions
+// Fixed grid, fixed per-thread stride order, fixed tree: bitwise reproducible.
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sh[kReduceThreads / kWarp];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < kReduceThreads / kWarp ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;   // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kReduceThreads) dot_kernel(const double *x, const double *y, int n,
+                                                            double *partial)
+{
+    double acc = 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
+        acc += x[i] * y[i];
+    double t = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kReduceThreads) reduce_partials_kernel(const double *partial, int count,
+                                                                        double *out)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += kReduceThreads) acc += partial[i];
+    double t = block_sum(acc);
+    if (threadIdx.x == 0) *out = t;
+}
+
+cudaError_t dot(const double *x, const double *y, int n, double *partial, double *out, cudaStream_t s)
+{
+    dot_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, y, n, partial); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    reduce_partials_kernel<<<1, kReduceThreads, 0, s>>>(partial, kReduceBlocks, out); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t dot_partial(const double *x, const double *y, int n, double *partial, cudaStream_t s)
+{
+    dot_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(x, y, n, partial); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_partials(const double *partial, int count, double *out, cudaStream_t s)
+{
+    reduce_partials_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, out); note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace amgk

@@ -1,0 +1,115 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI and compare
+it with the oracle on the same seeded inputs.
+
+Tolerances (FP64 path):
+  * integer structures (strength masks, removal masks, lumping outcomes, aggregates, roots,
+    the patterns of the filtered matrix, P, R and every coarse A): bit-exact;
+  * hierarchy values: max |gpu - oracle| <= VAL_TOL * max |oracle| per array;
+  * eigenvalue estimates: relative VAL_TOL (1Norm's lambda = 1 and overrides are exact);
+  * PCG: identical iteration counts, solutions within SOL_TOL relative (2-norm).
+"""
+import numpy as np
+
+VAL_TOL = 1e-12
+SOL_TOL = 1e-9
+
+
+def gpu_params(amg, **kw):
+    variants = kw.pop("variants", 0)
+    if not isinstance(variants, int):
+        m = 0
+        for s in variants:
+            m |= {"1norm": 1, "offlmp": 2, "sprsfy": 4, "cnstrnt": 8}[s]
+        variants = m
+    pt_unit = kw.pop("pt_unit", 0)
+    onenorm_power = kw.pop("onenorm_power", 0)
+    p = amg.amg_params_default(variants=variants, pt_scaling=pt_unit, onenorm_lambda=onenorm_power, **kw)
+    return p
+
+
+def gpu_setup(A, nullspace=None, **kw):
+    from paper_2103_10476_gb300 import amg
+    p = gpu_params(amg, **kw)
+    arg = amg.csr_arg(A.n, np.ascontiguousarray(A.row_ptr, dtype=np.int64), np.ascontiguousarray(A.col, np.int32),
+                      np.ascontiguousarray(A.val, np.float64))
+    ns = None if nullspace is None else np.ascontiguousarray(nullspace, dtype=np.float64)
+    return amg.amg_setup_status(arg, ns, p)
+
+
+def iterations_agree(oracle_lib, A, kw, b, tol, k_gpu, k_oracle):
+    """PCG iteration counts must agree exactly.  The one exception is a borderline stop: if
+    the oracle's own true relative residual at the smaller of the two counts is already
+    within a factor 2 of the tolerance, rounding differences (FMA, summation order) can move
+    the stop by an iteration or two; then |difference| <= 2 is accepted."""
+    if k_gpu == k_oracle:
+        return True
+    if abs(k_gpu - k_oracle) > 2:
+        return False
+    k = min(k_gpu, k_oracle)
+    hk, st = oracle_lib.setup(A, max_iter=k, **kw)
+    _, info, _ = hk.solve(b, tol)
+    return info.relres_true <= 2.0 * tol
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if b.size == 0:
+        return 0.0
+    scale = np.abs(b).max()
+    if scale == 0:
+        return float(np.abs(a).max())
+    return float(np.abs(a - b).max() / scale)
+
+
+def compare_hierarchies(h, oh, check_values=True):
+    """Level-by-level comparison; returns a list of (level, what, detail) mismatches."""
+    from paper_2103_10476_gb300 import amg
+    bad = []
+    nl = amg.amg_num_levels(h)
+    if nl != oh.nlevels:
+        return [(-1, "nlevels", (nl, oh.nlevels))]
+    exact = ["A.rp", "A.ci", "strong", "removed", "lumpflag", "Abar.rp", "Abar.ci", "agg", "root", "P.rp", "P.ci",
+             "R.rp", "R.ci"]
+    values = ["A.v", "Abar.v", "P.v", "R.v", "Dsm", "B"]
+    for l in range(nl):
+        last = l == nl - 1
+        for w in exact:
+            if last and w not in ("A.rp", "A.ci"):
+                continue
+            g, o = amg.amg_export(h, l, w), oh.get(l, w)
+            if g.shape != o.shape or not np.array_equal(g, o):
+                nd = int((g != o).sum()) if g.shape == o.shape else -1
+                bad.append((l, w, f"mismatch ({nd} entries; shapes {g.shape} {o.shape})"))
+        if not last:
+            # Algorithm 3's outcome per row: exact, except where the row's input values differ in
+            # the last bits (the eigenvalue estimate behind omega is a parallel reduction) and a
+            # rounding-level remainder decides the outcome; the row's values must still agree
+            gc, oc = amg.amg_export(h, l, "cflag"), oh.get(l, "cflag")
+            if not np.array_equal(gc, oc):
+                gp, op = amg.amg_export(h, l, "P.v"), oh.get(l, "P.v")
+                rp = oh.get(l, "P.rp")
+                scale = max(np.abs(op).max(), 1e-300)
+                for i in np.nonzero(gc != oc)[0]:
+                    a, b = rp[i], rp[i + 1]
+                    if not np.abs(gp[a:b] - op[a:b]).max(initial=0.0) <= VAL_TOL * scale:
+                        bad.append((l, "cflag", f"row {i}: outcome {gc[i]} vs {oc[i]} with differing values"))
+                        break
+        if not check_values:
+            continue
+        for w in values:
+            if last and w not in ("A.v", "B"):
+                continue
+            g, o = amg.amg_export(h, l, w), oh.get(l, w)
+            if g.shape != o.shape:
+                bad.append((l, w, f"shape {g.shape} vs {o.shape}"))
+                continue
+            e = rel_err(g, o)
+            if not e <= VAL_TOL:
+                bad.append((l, w, f"rel err {e:.3e}"))
+        if not last:
+            gs, os_ = amg.amg_export(h, l, "scalars"), oh.get(l, "scalars")
+            for k, name in enumerate(("lambda_bar", "omega", "lambda_cheb", "nagg")):
+                if not abs(gs[k] - os_[k]) <= VAL_TOL * abs(os_[k]):
+                    bad.append((l, name, f"{gs[k]!r} vs {os_[k]!r}"))
+    return bad

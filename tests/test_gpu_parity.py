@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on seeded inputs."""
+import numpy as np
+import pytest
+
+from paper_2103_10476_gb300 import problems as P
+from tests.gpu_common import SOL_TOL, compare_hierarchies, gpu_setup, iterations_agree, rel_err
+from tests.helpers import csr_from_dense
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2103_10476_gb300 import build
+    build.build()
+    from paper_2103_10476_gb300 import amg as m
+    return m
+
+
+def _solve_both(amg, oracle_lib, A, b, tol=1e-8, **kw):
+    h, st = gpu_setup(A, **kw)
+    oh, ost = oracle_lib.setup(A, **kw)
+    assert st == ost, (st, ost, amg.amg_last_error())
+    if st != 0:
+        return None
+    bad = compare_hierarchies(h, oh)
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, tol)
+    xo, oinfo, ostat = oh.solve(b, tol)
+    amg.amg_free(h)
+    return bad, info, x, oinfo, xo, ostat
+
+
+# ---------------------------------------------------------------- whole method, small and ragged sizes
+
+CASES = [
+    ("laplace20", lambda: P.laplace_cube(20), dict(theta=0.0)),
+    ("laplace13", lambda: P.laplace_cube(13), dict(theta=0.0, max_coarse=20)),
+    ("stretched17", lambda: P.stretched_box(17, 1.1), dict(theta=0.02, max_coarse=40)),
+    ("random11", lambda: P.random_coefficient_cube(11, 2), dict(theta=0.02, max_coarse=30)),
+]
+VARIANTS = [0, 1, 2, 4, 8, 3, 15, 12]
+
+
+@pytest.mark.parametrize("variants", VARIANTS)
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_hierarchy_and_solve_match_oracle(amg, oracle_lib, name, make, kw, variants):
+    A = make()
+    b = P.rhs_uniform(A.n, 7)
+    out = _solve_both(amg, oracle_lib, A, b, variants=variants, **kw)
+    if out is None:
+        return   # same failure status on both sides (e.g. the traditional method's zero diagonal)
+    bad, info, x, oinfo, xo, ostat = out
+    assert not bad, bad[:8]
+    assert info.status == ostat
+    assert iterations_agree(oracle_lib, A, dict(variants=variants, **kw), b, 1e-8, info.iters, oinfo.iters), \
+        (info.iters, oinfo.iters)
+    if info.iters == oinfo.iters:
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= SOL_TOL
+    assert info.relres_true <= 1e-8
+
+
+@pytest.mark.parametrize("pt_unit", [0, 1])
+def test_bit_exact_values_when_lambda_is_fixed(amg, oracle_lib, pt_unit):
+    # with lambda fixed (1Norm's bound) the whole setup is evaluated in the same order on both
+    # sides, so every hierarchy value agrees to the last bit
+    A = P.stretched_box(15, 1.15)
+    h, st = gpu_setup(A, theta=0.02, variants=3, pt_unit=pt_unit, max_coarse=30)
+    oh, ost = oracle_lib.setup(A, theta=0.02, variants=3, pt_unit=pt_unit, max_coarse=30)
+    assert st == 0 and ost == 0
+    for l in range(amg.amg_num_levels(h) - 1):
+        for w in ("Abar.v", "Dsm", "P.v", "R.v"):
+            assert np.array_equal(amg.amg_export(h, l, w), oh.get(l, w)), (l, w)
+        assert np.array_equal(amg.amg_export(h, l + 1, "A.v"), oh.get(l + 1, "A.v")), l
+    amg.amg_free(h)
+
+
+def test_unit_and_orthonormal_give_same_iterations(amg):
+    A = P.random_coefficient_cube(12, 5)
+    b = P.rhs_uniform(A.n, 3)
+    its = []
+    for pt in (0, 1):
+        h, st = gpu_setup(A, theta=0.02, variants=1, pt_unit=pt, max_coarse=30)
+        x = np.zeros(A.n)
+        its.append(amg.amg_solve(h, b, x, 1e-8).iters)
+        amg.amg_free(h)
+    assert abs(its[0] - its[1]) <= 1
+
+
+def test_device_pointers_and_host_pointers_agree(amg):
+    import torch
+    A = P.stretched_box(12, 1.2)
+    b = P.rhs_uniform(A.n, 5)
+    h, st = gpu_setup(A, theta=0.02, variants=2, max_coarse=30)
+    x_host = np.zeros(A.n)
+    i1 = amg.amg_solve(h, b, x_host, 1e-8)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    i2 = amg.amg_solve(h, bd, xd, 1e-8)
+    torch.cuda.synchronize()
+    assert i1.iters == i2.iters
+    assert np.array_equal(xd.cpu().numpy(), x_host)   # deterministic: bitwise identical
+    amg.amg_free(h)
+    # the matrix itself from device memory
+    rp = torch.from_numpy(A.row_ptr).cuda()
+    ci = torch.from_numpy(A.col).cuda()
+    v = torch.from_numpy(A.val).cuda()
+    arg = amg.csr_arg(A.n, rp, ci, v)
+    assert arg.on_device == 1
+    h2 = amg.amg_setup(arg, None, amg.amg_params_default(theta=0.02, variants=2, max_coarse=30))
+    x2 = np.zeros(A.n)
+    amg.amg_solve(h2, b, x2, 1e-8)
+    assert np.array_equal(x2, x_host)
+    amg.amg_free(h2)
+
+
+def test_runs_are_bitwise_reproducible(amg):
+    A = P.random_coefficient_cube(14, 8)
+    b = P.rhs_uniform(A.n, 1)
+    xs = []
+    for _ in range(2):
+        h, st = gpu_setup(A, theta=0.02, variants=2, max_coarse=40)
+        assert st == 0
+        x = np.zeros(A.n)
+        amg.amg_solve(h, b, x, 1e-8)
+        xs.append(x)
+        amg.amg_free(h)
+    assert np.array_equal(xs[0], xs[1])
+
+
+# ---------------------------------------------------------------- SpGEMM on its own
+
+@pytest.mark.parametrize("seed,m,k,ncol,dens", [(0, 1, 1, 1, 1.0), (1, 37, 53, 29, 0.1), (2, 300, 200, 1000, 0.05),
+                                                (3, 64, 64, 7000, 0.9), (4, 500, 40, 5, 0.3)])
+def test_spgemm_matches_oracle_bitwise(amg, oracle_lib, seed, m, k, ncol, dens):
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    Am = sp.random(m, k, density=dens, random_state=rng, format="csr")
+    Bm = sp.random(k, ncol, density=dens, random_state=rng, format="csr")
+    Am.sort_indices(); Bm.sort_indices()
+    from paper_2103_10476_gb300.problems import CSR
+    Ac = CSR(m, Am.indptr.astype(np.int64), Am.indices.astype(np.int32), Am.data.astype(np.float64))
+    Bc = CSR(k, Bm.indptr.astype(np.int64), Bm.indices.astype(np.int32), Bm.data.astype(np.float64))
+    rp, ci, v = amg.amg_spgemm(amg.csr_arg(m, Ac.row_ptr, Ac.col, Ac.val), k,
+                               amg.csr_arg(k, Bc.row_ptr, Bc.col, Bc.val), ncol)
+    Co = oracle_lib.spgemm(Ac, Bc, ncol)
+    assert np.array_equal(rp, Co.row_ptr) and np.array_equal(ci, Co.col)
+    assert np.array_equal(v, Co.val)
+
+
+def test_spgemm_long_rows_use_global_tables(amg, oracle_lib):
+    # a dense-ish row block whose products exceed the shared-memory tables
+    import scipy.sparse as sp
+    rng = np.random.default_rng(9)
+    Am = sp.random(8, 400, density=0.9, random_state=rng, format="csr")
+    Bm = sp.random(400, 20000, density=0.05, random_state=rng, format="csr")
+    from paper_2103_10476_gb300.problems import CSR
+    Ac = CSR(8, Am.indptr.astype(np.int64), Am.indices.astype(np.int32), Am.data)
+    Bc = CSR(400, Bm.indptr.astype(np.int64), Bm.indices.astype(np.int32), Bm.data)
+    rp, ci, v = amg.amg_spgemm(amg.csr_arg(8, Ac.row_ptr, Ac.col, Ac.val), 400,
+                               amg.csr_arg(400, Bc.row_ptr, Bc.col, Bc.val), 20000)
+    Co = oracle_lib.spgemm(Ac, Bc, 20000)
+    assert np.array_equal(ci, Co.col) and np.array_equal(v, Co.val)
+
+
+# ---------------------------------------------------------------- degenerate cases
+
+def test_single_level_one_iteration(amg):
+    A = P.laplace_cube(6)
+    b = P.rhs_uniform(A.n, 0)
+    h, st = gpu_setup(A)
+    assert st == 0 and amg.amg_num_levels(h) == 1
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, 1e-8)
+    assert info.status == 0 and info.iters == 1 and info.relres_true < 1e-12
+    amg.amg_free(h)
+
+
+def test_zero_rhs_and_empty_matrix(amg):
+    A = P.laplace_cube(10)
+    h, st = gpu_setup(A, max_coarse=20)
+    x = np.ones(A.n)
+    info = amg.amg_solve(h, np.zeros(A.n), x, 1e-8)
+    assert info.status == 0 and info.iters == 0 and not x.any()
+    amg.amg_free(h)
+    E = csr_from_dense(np.zeros((0, 0)))
+    h, st = gpu_setup(E)
+    assert st == 0
+    info = amg.amg_solve(h, np.zeros(1), np.zeros(1), 1e-8)
+    assert info.iters == 0
+    amg.amg_free(h)
+
+
+def test_error_statuses_match_oracle(amg, oracle_lib):
+    # traditional SA with large coefficient jumps: a row whose off-diagonals are all weak is
+    # lumped to its row sum, zero for an interior row (zero filtered diagonal, §1.2)
+    A = P.random_coefficient_cube(14, 8)
+    h, st = gpu_setup(A, theta=0.02, variants=0, max_coarse=40)
+    _, ost = oracle_lib.setup(A, theta=0.02, variants=0, max_coarse=40)
+    assert st == ost == 4
+    # with no strong connection at all the level is not coarsened: a single (dense) level
+    A = P.stretched_box(10, 1.1)
+    h, st = gpu_setup(A, theta=0.2, variants=0)
+    oh, ost = oracle_lib.setup(A, theta=0.2, variants=0)
+    assert st == ost == 0 and amg.amg_num_levels(h) == oh.nlevels == 1
+    amg.amg_free(h)
+    # indefinite coarse operator
+    d = -np.eye(5) * 2.0
+    h, st = gpu_setup(csr_from_dense(d))
+    assert st == 6
+    # unsorted columns
+    A = P.laplace_cube(4)
+    A.col = A.col.copy()
+    A.col[[0, 1]] = A.col[[1, 0]]
+    h, st = gpu_setup(A)
+    assert st == 1
+
+
+def test_not_converged_returns_last_iterate(amg):
+    A = P.random_coefficient_cube(12, 1)
+    b = P.rhs_uniform(A.n, 2)
+    h, st = gpu_setup(A, theta=0.02, max_coarse=30, max_iter=3)
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, 1e-12)
+    assert info.status == 7 and info.iters == 3 and 0 < info.relres_true < 1
+    amg.amg_free(h)
+
+
+def test_mixed_precision_meets_tolerance(amg, oracle_lib):
+    A = P.random_coefficient_cube(16, 2)
+    b = P.rhs_uniform(A.n, 2)
+    h, st = gpu_setup(A, theta=0.02, variants=3, max_coarse=40, precision=1)
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, 1e-8)
+    oh, _ = oracle_lib.setup(A, theta=0.02, variants=3, max_coarse=40)
+    xo, oinfo, _ = oh.solve(b, 1e-8)
+    assert info.status == 0 and info.relres_true <= 1e-8
+    assert abs(info.iters - oinfo.iters) <= 1
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+    amg.amg_free(h)
