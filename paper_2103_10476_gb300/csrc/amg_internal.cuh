@@ -118,6 +118,15 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
 cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s);
 
 // --------------------------------------------------------------------------------- solve.cu
+// SpMV launch plan of one matrix: lanes per row and the shared-memory tile (entries; 0 = none)
+struct SpmvPlan {
+    int lpr = 2;
+    int cap = 0;
+};
+cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s);
+int spmv_partials_needed(int n);
+int *spmv_error_flag();
+int spmv_take_errors(cudaStream_t s);
 struct LevelView {      // what the solve needs of one level, in working precision T
     int n = 0, nc = 0;
     const int *arp = nullptr, *aci = nullptr;
@@ -129,7 +138,7 @@ struct LevelView {      // what the solve needs of one level, in working precisi
     const void *invdiag = nullptr;          // T
     double lambda = 0.0;                    // Chebyshev lambda_max
     int64_t nnz_a = 0;                      // stored entries of A
-    int lanes_a = 8, lanes_p = 8, lanes_r = 8;
+    SpmvPlan plan_a, plan_p, plan_r;
     void *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *d = nullptr;   // T work vectors
 };
 struct SolveCtx {
@@ -149,15 +158,19 @@ cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s
 struct PcgScalars {     // device
     double rz, pq, alpha, beta, rr, bb, tmp;
 };
-cudaError_t spmv_dot(const DevCsr &A, int lanes, const double *p, double *q, double *partial, cudaStream_t s);
-cudaError_t spmv_d(const DevCsr &A, int lanes, const double *x, double *y, cudaStream_t s);
-cudaError_t residual_d(const DevCsr &A, int lanes, const double *b, const double *x, double *r, cudaStream_t s);
+cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial, int *nparts,
+                     cudaStream_t s);
+cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
+                            double *partial, int *nparts, cudaStream_t s);
+cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
+cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
+                       cudaStream_t s);
 cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, const PcgScalars *sc,
                           double *partial, cudaStream_t s);
 cudaError_t pcg_update_p(int n, double *p, const double *z, const PcgScalars *sc, cudaStream_t s);
-cudaError_t pcg_alpha(const double *partial, PcgScalars *sc, cudaStream_t s);
-cudaError_t pcg_beta(const double *partial, PcgScalars *sc, cudaStream_t s);
-cudaError_t pcg_store(const double *partial, double *dst, cudaStream_t s);
+cudaError_t pcg_alpha(const double *partial, int count, PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_beta(const double *partial, int count, PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s);
 int pick_lanes(double avg_row);
 
 }  // namespace amgk

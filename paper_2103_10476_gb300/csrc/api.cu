@@ -36,7 +36,7 @@ struct Level {
     double *invdiag = nullptr;
     float *invdiag_f = nullptr, *Af = nullptr, *Pf = nullptr, *Rf = nullptr;
     void *vf = nullptr, *vx = nullptr, *vx2 = nullptr, *vr = nullptr, *vd = nullptr;   // solve vectors
-    int lanes_a = 16, lanes_p = 8, lanes_r = 16;
+    SpmvPlan plan_a, plan_p, plan_r;
 };
 
 }  // namespace
@@ -52,6 +52,7 @@ struct amg_hierarchy {
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
     double *partial = nullptr;
     PcgScalars *sc = nullptr;
+    SpmvPlan plan0;   // finest-level FP64 operator (PCG)
     SolveCtx ctx;
     double setup_ms = 0.0;
     int64_t fine_nnz = 0;
@@ -73,12 +74,12 @@ amg_status_t fail_cuda(cudaError_t e, const char *where)
         if (_e != cudaSuccess) { st = fail_cuda(_e, #expr); goto done; }  \
     } while (0)
 
+// every array carries 16 elements of padding: bulk copies widen ranges to 16-byte boundaries
 template <typename T>
 cudaError_t dalloc(amg_hierarchy *h, T **p, size_t count)
 {
     *p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    cudaError_t e = cudaMalloc((void **)p, (count + 16) * sizeof(T));
     if (e == cudaSuccess) h->allocs.push_back((void *)*p);
     return e;
 }
@@ -214,7 +215,11 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     // eigenvalue of Dsm^-1 Abar and omega = 4 / (3 lambda), Eq. (3)
     CK(cudaMalloc(&px, sizeof(double) * (size_t)n));
     CK(cudaMalloc(&py, sizeof(double) * (size_t)n));
-    CK(cudaMalloc(&scal, sizeof(double) * (kReduceBlocks + 8)));
+    {
+        // 8 scalars, then the partial sums of the power method's dot products
+        int np = spmv_partials_needed(n);
+        CK(cudaMalloc(&scal, sizeof(double) * (size_t)((np > kReduceBlocks ? np : kReduceBlocks) + 8)));
+    }
     if (p.lambda_override > 0.0) {
         lv.lambda_bar = p.lambda_override;
     } else if ((p.variants & AMG_VAR_1NORM) && p.onenorm_lambda == AMG_LAMBDA_ONE) {
@@ -352,10 +357,10 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             v.rrp = lv.R.rp; v.rci = lv.R.ci;
             v.lambda = lv.lambda_cheb;
             v.nnz_a = lv.A.nnz;
-            lv.lanes_a = pick_lanes(n ? (double)lv.A.nnz / n : 1.0);
-            lv.lanes_p = pick_lanes(n ? (double)lv.P.nnz / n : 1.0);
-            lv.lanes_r = pick_lanes(lv.nagg ? (double)lv.R.nnz / lv.nagg : 1.0);
-            v.lanes_a = lv.lanes_a; v.lanes_p = lv.lanes_p; v.lanes_r = lv.lanes_r;
+            CK(spmv_plan(lv.A.rp, n, lv.A.nnz, &lv.plan_a, s));
+            CK(spmv_plan(lv.P.rp, n, lv.P.nnz, &lv.plan_p, s));
+            CK(spmv_plan(lv.R.rp, lv.nagg, lv.R.nnz, &lv.plan_r, s));
+            v.plan_a = lv.plan_a; v.plan_p = lv.plan_p; v.plan_r = lv.plan_r;
             if (mixed) {
                 CK(dalloc(h, &lv.Af, (size_t)lv.A.nnz));
                 CK(dalloc(h, &lv.Pf, (size_t)lv.P.nnz));
@@ -379,7 +384,11 @@ amg_status_t prepare_solve(amg_hierarchy *h)
     CK(dalloc(h, &h->pv, (size_t)n0));
     CK(dalloc(h, &h->q, (size_t)n0));
     CK(dalloc(h, &h->t, (size_t)n0));
-    CK(dalloc(h, &h->partial, (size_t)kReduceBlocks));
+    {
+        int np = spmv_partials_needed(n0);
+        CK(dalloc(h, &h->partial, (size_t)(np > kReduceBlocks ? np : kReduceBlocks)));
+        if (n0 > 0) CK(spmv_plan(h->lev[0].A.rp, n0, h->lev[0].A.nnz, &h->plan0, s));
+    }
     CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
 done:
     return st;
@@ -552,6 +561,10 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
     if (st == AMG_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fail_cuda(e, "setup");
+        else if (spmv_take_errors(s) != 0) {
+            g_last_error = "a bulk copy into shared memory did not complete in time";
+            st = AMG_ERR_INTERNAL;
+        }
     }
 done:
     cudaFree(bad);
@@ -594,6 +607,10 @@ amg_status_t amg_vcycle(amg_handle_t h, const double *r, double *z)
     CK(vcycle(h->ctx, h->r, h->z, s));
     CK(cudaMemcpyAsync(z, h->z, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
     CK(cudaStreamSynchronize(s));
+    if (spmv_take_errors(s) != 0) {
+        g_last_error = "a bulk copy into shared memory did not complete in time";
+        st = AMG_ERR_INTERNAL;
+    }
 done:
     return st;
 }
@@ -608,7 +625,8 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     amg_status_t st = AMG_OK;
     cudaStream_t s = h->s;
     const DevCsr &A = h->lev[0].A;
-    const int lanes = pick_lanes(n ? (double)A.nnz / n : 1.0);
+    const SpmvPlan &plan = h->plan0;
+    int nparts = 0;
     int it = 0;
     double bb = 0.0, rr = 0.0, relres = 0.0, nb = 0.0;
     amg_status_t result = AMG_OK;
@@ -628,16 +646,16 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     while (it < h->p.max_iter) {
         {
             ProfScope ps(KC_PCG_SPMV, s, 12.0 * (double)A.nnz + 20.0 * n + 4.0);
-            CK(spmv_dot(A, lanes, h->pv, h->q, h->partial, s));
+            CK(spmv_dot(A, plan, h->pv, h->q, h->partial, &nparts, s));
         }
-        CK(pcg_alpha(h->partial, h->sc, s));
+        CK(pcg_alpha(h->partial, nparts, h->sc, s));
         CK(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, s));
-        CK(pcg_store(h->partial, &h->sc->rr, s));
+        CK(pcg_store(h->partial, kReduceBlocks, &h->sc->rr, s));
         ++it;
         CK(cudaMemcpyAsync(&rr, &h->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (std::sqrt(rr) / nb <= tol) {
-            CK(residual_d(A, lanes, h->b, h->x, h->t, s));
+            CK(residual_d(A, plan, h->b, h->x, h->t, s));
             CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
             double tt = 0.0;
             CK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -647,12 +665,12 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
         }
         CK(vcycle(h->ctx, h->r, h->z, s));
         CK(dot_partial(h->r, h->z, n, h->partial, s));
-        CK(pcg_beta(h->partial, h->sc, s));
+        CK(pcg_beta(h->partial, kReduceBlocks, h->sc, s));
         CK(pcg_update_p(n, h->pv, h->z, h->sc, s));
     }
 finish:
     if (n > 0) {
-        CK(residual_d(A, lanes, h->b, h->x, h->t, s));
+        CK(residual_d(A, plan, h->b, h->x, h->t, s));
         CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
         double tt = 0.0;
         CK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -661,6 +679,10 @@ finish:
         relres = nb > 0.0 ? std::sqrt(tt) / nb : 0.0;
     }
     st = result;
+    if (spmv_take_errors(s) != 0) {
+        g_last_error = "a bulk copy into shared memory did not complete in time";
+        st = AMG_ERR_INTERNAL;
+    }
 done:
     if (info) {
         info->iters = it;

@@ -893,35 +893,6 @@ __global__ void power_init_kernel(int n, uint64_t s0, double *x)
     x[i] = 2.0 * u - 1.0;
 }
 
-// y = (A x) / D with the partial sums of x . y (one warp per row, fixed grid)
-__global__ void __launch_bounds__(kReduceThreads) power_spmv_kernel(int n, const int *rp, const int *ci,
-                                                                    const double *v, const double *D,
-                                                                    const double *x, double *y, double *partial)
-{
-    const int lane = threadIdx.x & 31;
-    const int warps_total = kReduceBlocks * (kReduceThreads / 32);
-    double acc_dot = 0.0;
-    for (int i = (blockIdx.x * kReduceThreads + threadIdx.x) >> 5; i < n; i += warps_total) {
-        double sum = 0.0;
-        for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) sum = sum + v[e] * x[ci[e]];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sum = sum + __shfl_xor_sync(kFull, sum, o);
-        double yi = sum / D[i];
-        if (lane == 0) {
-            y[i] = yi;
-            acc_dot = acc_dot + x[i] * yi;
-        }
-    }
-    __shared__ double sh[kReduceThreads / 32];
-    if (lane == 0) sh[threadIdx.x >> 5] = acc_dot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) t = t + sh[w];
-        partial[blockIdx.x] = t;
-    }
-}
-
 __global__ void scale_by_norm_kernel(int n, const double *src, double *dst, const double *sq)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -937,10 +908,12 @@ cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t 
     AMG_CUDA_TRY(cudaGetLastError());
     AMG_CUDA_TRY(dot(x, x, n, partial, scal, s));
     scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, x, scal); note_launch();
+    SpmvPlan plan;
+    AMG_CUDA_TRY(spmv_plan(A.rp, n, A.nnz, &plan, s));
     for (int k = 0; k < sweeps; ++k) {
-        power_spmv_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, A.rp, A.ci, A.v, D, x, y, partial); note_launch();
-        AMG_CUDA_TRY(cudaGetLastError());
-        AMG_CUDA_TRY(reduce_partials(partial, kReduceBlocks, lambda_dev, s));
+        int nparts = 0;
+        AMG_CUDA_TRY(spmv_scaled_dot(A, plan, D, x, y, partial, &nparts, s));
+        AMG_CUDA_TRY(reduce_partials(partial, nparts, lambda_dev, s));
         if (k + 1 < sweeps) {
             AMG_CUDA_TRY(dot(y, y, n, partial, scal, s));
             scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, y, x, scal); note_launch();

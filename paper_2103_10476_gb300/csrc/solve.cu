@@ -1,152 +1,251 @@
 // solve.cu -- solve-phase kernels: CSR SpMV with fused epilogues (residual, Chebyshev step,
-// prolongation, dot product), the V-cycle of Algorithm 1 with degree-k Chebyshev smoothing,
+// prolongation, dot products), the V-cycle of Algorithm 1 with degree-k Chebyshev smoothing,
 // the coarsest-level dense solve and the PCG vector updates.
 //
-// SpMV layout: a group of LANES consecutive lanes per row (LANES in {4, 8, 16, 32}), lanes
-// stride over the row's entries (coalesced column/value loads), partial sums combined with
-// xor shuffles inside the group.  The working type T is double (FP64 path) or float (the
-// mixed path's V-cycle); accumulation is in T.
+// SpMV layout (one design for every level and both precisions): a block of 256 threads owns
+// 256/LPR consecutive rows, LPR lanes per row (LPR from the mean row length: 2 for the
+// 27-point fine operators, wider for the denser coarse operators).  One thread of the block
+// copies the block's contiguous range of values and column indices into shared memory with
+// two bulk asynchronous copies (cp.async.bulk + mbarrier), widened to 16-byte boundaries;
+// the lanes then walk their row from shared memory and gather x from global memory (L2).
+// Blocks whose range exceeds the shared tile read their rows directly from global memory.
+// Few lanes per row keep the cross-lane FP64 additions (issued on GB300's narrow FP64 pipe)
+// to log2(LPR) per row.  The working type T is double (FP64 path) or float (the mixed
+// path's V-cycle); accumulation is in T.  Partial dot products are per block, in a fixed
+// order, so every reduction is bitwise reproducible.
 #include "amg_internal.cuh"
+#include "tma.cuh"
 
 namespace amgk {
 
 constexpr unsigned kAll = 0xffffffffu;
+constexpr int kSpmvThreads = 256;
+constexpr int kMaxTile = 6144;            // entries staged per block at most
 
 enum SpmvMode {
     MODE_Y = 0,          // y = A x
     MODE_RESID = 1,      // y = f - A x
     MODE_CHEB = 2,       // r = f - A x; d = c1 d + c2 D^-1 r; y = x + d
     MODE_PROLONG = 3,    // y += A x
+    MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
+    MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
 };
 
-struct ChebArgs {
-    const void *f = nullptr;
-    const void *invdiag = nullptr;
-    void *d = nullptr;
-    double c1 = 0.0, c2 = 0.0;
-};
-
-template <typename T, int LANES, int MODE>
-__global__ void __launch_bounds__(256) spmv_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                                   const T *__restrict__ v, const T *__restrict__ x, T *y,
-                                                   const T *__restrict__ f, const T *__restrict__ invdiag, T *d,
-                                                   T c1, T c2)
+template <typename T>
+__host__ __device__ constexpr int tile_values_bytes(int cap)
 {
-    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int row = gtid / LANES;
-    const int sub = threadIdx.x & (LANES - 1);
+    return ((cap + 2 * (16 / (int)sizeof(T))) * (int)sizeof(T) + 127) / 128 * 128;
+}
+template <typename T>
+__host__ __device__ constexpr int tile_bytes(int cap)
+{
+    return cap > 0 ? tile_values_bytes<T>(cap) + (cap + 8) * 4 : 0;
+}
+
+template <typename T, int LPR, int MODE>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const int *__restrict__ rp,
+                                                                 const int *__restrict__ ci,
+                                                                 const T *__restrict__ v, const T *__restrict__ x,
+                                                                 T *y, const T *__restrict__ f,
+                                                                 const T *__restrict__ aux, T *d, T c1, T c2,
+                                                                 int cap, double *partial, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    constexpr int RPB = kSpmvThreads / LPR;
+    constexpr int VA = 16 / (int)sizeof(T);
+    const int r0 = blockIdx.x * RPB;
+    const int r1 = min(n, r0 + RPB);
+    const int k0 = rp[r0], k1 = rp[r1];
+    const int k0v = k0 & ~(VA - 1), k1v = (k1 + VA - 1) & ~(VA - 1);
+    const int k0i = k0 & ~3, k1i = (k1 + 3) & ~3;
+    const bool staged = cap > 0 && (k1v - k0v) <= cap + 2 * VA && (k1i - k0i) <= cap + 8 && k1 > k0;
+    T *sv = (T *)smem;
+    int *sc = (int *)(smem + tile_values_bytes<T>(cap));
+    if (staged) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned bv = (unsigned)((k1v - k0v) * (int)sizeof(T)), bi = (unsigned)((k1i - k0i) * 4);
+            mbar_expect_tx(&bar, bv + bi);
+            bulk_g2s(sv, v + k0v, bv, &bar);
+            bulk_g2s(sc, ci + k0i, bi, &bar);
+        }
+        const bool ok = mbar_wait_bounded(&bar, 0, err);
+        if (!__syncthreads_and(ok)) return;
+    }
+    const int row = r0 + threadIdx.x / LPR;
+    const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    if (row < n) {
+    if (row < r1) {
         const int b = rp[row], e = rp[row + 1];
-        for (int k = b + sub; k < e; k += LANES) sum += v[k] * x[ci[k]];
+        if (staged) {
+            for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
+        } else {
+            for (int k = b + lane; k < e; k += LPR) sum += v[k] * x[ci[k]];
+        }
     }
 #pragma unroll
-    for (int o = LANES / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LANES);
-    if (row < n && sub == 0) {
+    for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
+    double contrib = 0.0;
+    if (row < r1 && lane == 0) {
         if (MODE == MODE_Y) {
             y[row] = sum;
         } else if (MODE == MODE_RESID) {
             y[row] = f[row] - sum;
         } else if (MODE == MODE_CHEB) {
             T r = f[row] - sum;
-            T dn = c1 * d[row] + c2 * (invdiag[row] * r);
+            T dn = c1 * d[row] + c2 * (aux[row] * r);
             d[row] = dn;
             y[row] = x[row] + dn;
-        } else {
+        } else if (MODE == MODE_PROLONG) {
             y[row] += sum;
+        } else if (MODE == MODE_DOT) {
+            y[row] = sum;
+            contrib = (double)x[row] * (double)sum;
+        } else {
+            T yi = sum / aux[row];
+            y[row] = yi;
+            contrib = (double)x[row] * (double)yi;
+        }
+    }
+    if (MODE == MODE_DOT || MODE == MODE_SCALEDOT) {
+        __shared__ double sh[kSpmvThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(kAll, contrib, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = contrib;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kSpmvThreads / 32; ++w) t += sh[w];
+            partial[blockIdx.x] = t;
         }
     }
 }
 
-template <typename T, int MODE>
-cudaError_t spmv_launch_mode(int lanes, int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f,
-                             const T *invdiag, T *d, T c1, T c2, cudaStream_t s)
+int pick_lpr(double avg_row)
 {
-    if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = grid_for((int64_t)n * lanes, threads);
-    switch (lanes) {
-    case 4: spmv_kernel<T, 4, MODE><<<blocks, threads, 0, s>>>(n, rp, ci, v, x, y, f, invdiag, d, c1, c2); note_launch(); break;
-    case 8: spmv_kernel<T, 8, MODE><<<blocks, threads, 0, s>>>(n, rp, ci, v, x, y, f, invdiag, d, c1, c2); note_launch(); break;
-    case 16: spmv_kernel<T, 16, MODE><<<blocks, threads, 0, s>>>(n, rp, ci, v, x, y, f, invdiag, d, c1, c2); note_launch(); break;
-    default: spmv_kernel<T, 32, MODE><<<blocks, threads, 0, s>>>(n, rp, ci, v, x, y, f, invdiag, d, c1, c2); note_launch(); break;
-    }
-    return cudaGetLastError();
-}
-
-int pick_lanes(double avg_row)
-{
-    if (avg_row <= 6.0) return 4;
-    if (avg_row <= 12.0) return 8;
-    if (avg_row <= 40.0) return 16;
+    if (avg_row <= 40.0) return 2;
+    if (avg_row <= 80.0) return 4;
+    if (avg_row <= 160.0) return 8;
+    if (avg_row <= 320.0) return 16;
     return 32;
 }
 
-// ------------------------------------------------------------------------------------ FP64 entry points
-cudaError_t spmv_d(const DevCsr &A, int lanes, const double *x, double *y, cudaStream_t s)
+int pick_lanes(double avg_row) { return pick_lpr(avg_row); }
+
+int spmv_blocks(int n, int lpr) { return n > 0 ? (n + kSpmvThreads / lpr - 1) / (kSpmvThreads / lpr) : 0; }
+
+__global__ void span_max_kernel(int n, const int *rp, int rpb, int *out)
 {
-    return spmv_launch_mode<double, MODE_Y>(lanes, A.n, A.rp, A.ci, A.v, x, y, nullptr, nullptr, nullptr, 0.0, 0.0, s);
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    int r0 = b * rpb;
+    if (r0 >= n) return;
+    int r1 = min(n, r0 + rpb);
+    atomicMax(out, rp[r1] - rp[r0]);
 }
 
-cudaError_t residual_d(const DevCsr &A, int lanes, const double *b, const double *x, double *r, cudaStream_t s)
+cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s)
 {
-    return spmv_launch_mode<double, MODE_RESID>(lanes, A.n, A.rp, A.ci, A.v, x, r, b, nullptr, nullptr, 0.0, 0.0, s);
+    plan->lpr = pick_lpr(n ? (double)nnz / n : 1.0);
+    plan->cap = 0;
+    if (n == 0 || nnz == 0) return cudaSuccess;
+    int *d = nullptr, h = 0;
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int), s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
+    const int nb = spmv_blocks(n, plan->lpr);
+    if (e == cudaSuccess) {
+        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rp, kSpmvThreads / plan->lpr, d); note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    plan->cap = h + 8 < kMaxTile ? h + 8 : kMaxTile;
+    return e;
 }
 
-// q = A p with deterministic partial sums of p . q (fixed grid, fixed row-to-block mapping)
-template <int LANES>
-__global__ void __launch_bounds__(kReduceThreads) spmv_dot_kernel(int n, const int *__restrict__ rp,
-                                                                  const int *__restrict__ ci,
-                                                                  const double *__restrict__ v,
-                                                                  const double *__restrict__ p, double *q,
-                                                                  double *partial)
+static int *g_spmv_err = nullptr;   // device error flag of the bounded waits (allocated once)
+
+int *spmv_error_flag()
 {
-    const int sub = threadIdx.x & (LANES - 1);
-    const int groups_total = kReduceBlocks * (kReduceThreads / LANES);
-    double acc = 0.0;
-    // the trip count is uniform within a warp: it runs while any of its row groups has a row
-    for (int row = (blockIdx.x * kReduceThreads + threadIdx.x) / LANES; __any_sync(kAll, row < n);
-         row += groups_total) {
-        const bool valid = row < n;
-        double sum = 0.0;
-        if (valid) {
-            const int b = rp[row], e = rp[row + 1];
-            for (int k = b + sub; k < e; k += LANES) sum += v[k] * p[ci[k]];
-        }
-#pragma unroll
-        for (int o = LANES / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LANES);
-        if (valid && sub == 0) {
-            q[row] = sum;
-            acc += p[row] * sum;
-        }
+    if (!g_spmv_err) {
+        if (cudaMalloc(&g_spmv_err, sizeof(int)) != cudaSuccess) return nullptr;
+        cudaMemset(g_spmv_err, 0, sizeof(int));
     }
-    // block reduction in a fixed order
-    __shared__ double sh[kReduceThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kAll, acc, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kReduceThreads / 32; ++w) t += sh[w];
-        partial[blockIdx.x] = t;
-    }
+    return g_spmv_err;
 }
 
-cudaError_t spmv_dot(const DevCsr &A, int lanes, const double *p, double *q, double *partial, cudaStream_t s)
+// number of blocks whose bounded wait for a bulk copy ran out since the last call (resets it)
+int spmv_take_errors(cudaStream_t s)
 {
-    switch (lanes) {
-    case 4: spmv_dot_kernel<4><<<kReduceBlocks, kReduceThreads, 0, s>>>(A.n, A.rp, A.ci, A.v, p, q, partial); note_launch(); break;
-    case 8: spmv_dot_kernel<8><<<kReduceBlocks, kReduceThreads, 0, s>>>(A.n, A.rp, A.ci, A.v, p, q, partial); note_launch(); break;
-    case 16:
-        spmv_dot_kernel<16><<<kReduceBlocks, kReduceThreads, 0, s>>>(A.n, A.rp, A.ci, A.v, p, q, partial); note_launch();
-        break;
-    default:
-        spmv_dot_kernel<32><<<kReduceBlocks, kReduceThreads, 0, s>>>(A.n, A.rp, A.ci, A.v, p, q, partial); note_launch();
-        break;
+    if (!g_spmv_err) return 0;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, g_spmv_err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    if (h) cudaMemsetAsync(g_spmv_err, 0, sizeof(int), s);
+    return h;
+}
+
+template <typename T, int LPR, int MODE>
+cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
+                        T *d, T c1, T c2, int cap, double *partial, cudaStream_t s)
+{
+    const int smem = tile_bytes<T>(cap);
+    static int configured = -1;
+    if (configured < smem) {
+        AMG_CUDA_TRY(cudaFuncSetAttribute(spmv_tile_kernel<T, LPR, MODE>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T>(kMaxTile)));
+        configured = tile_bytes<T>(kMaxTile);
     }
+    spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, spmv_error_flag()); note_launch();
     return cudaGetLastError();
 }
+
+template <typename T, int MODE>
+cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
+                      const T *f, const T *aux, T *d, T c1, T c2, double *partial, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    switch (pl.lpr) {
+    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    case 16: return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    default: return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    }
+}
+
+// ------------------------------------------------------------------------------------ FP64 entry points
+cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s)
+{
+    return spmv_mode<double, MODE_Y>(pl, A.n, A.rp, A.ci, A.v, x, y, nullptr, nullptr, nullptr, 0.0, 0.0, nullptr, s);
+}
+
+cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
+                       cudaStream_t s)
+{
+    return spmv_mode<double, MODE_RESID>(pl, A.n, A.rp, A.ci, A.v, x, r, b, nullptr, nullptr, 0.0, 0.0, nullptr, s);
+}
+
+cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial, int *nparts,
+                     cudaStream_t s)
+{
+    *nparts = spmv_blocks(A.n, pl.lpr);
+    return spmv_mode<double, MODE_DOT>(pl, A.n, A.rp, A.ci, A.v, p, q, nullptr, nullptr, nullptr, 0.0, 0.0, partial,
+                                       s);
+}
+
+cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
+                            double *partial, int *nparts, cudaStream_t s)
+{
+    *nparts = spmv_blocks(A.n, pl.lpr);
+    return spmv_mode<double, MODE_SCALEDOT>(pl, A.n, A.rp, A.ci, A.v, x, y, nullptr, D, nullptr, 0.0, 0.0, partial,
+                                            s);
+}
+
+int spmv_partials_needed(int n) { return spmv_blocks(n, 2) + 1; }
 
 // ------------------------------------------------------------------------------------ PCG vector updates
 __device__ __forceinline__ double block_sum_fixed(double v)
@@ -199,50 +298,53 @@ cudaError_t pcg_update_p(int n, double *p, const double *z, const PcgScalars *sc
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ double sum_partials(const double *partial)
+__device__ __forceinline__ double sum_partials(const double *partial, int count)
 {
     double acc = 0.0;
-    for (int i = threadIdx.x; i < kReduceBlocks; i += kReduceThreads) acc += partial[i];
+    for (int i = threadIdx.x; i < count; i += kReduceThreads) acc += partial[i];
     return block_sum_fixed(acc);
 }
 
 // pq = sum(partial); alpha = rz / pq
-__global__ void __launch_bounds__(kReduceThreads) pcg_alpha_kernel(const double *partial, PcgScalars *sc)
+__global__ void __launch_bounds__(kReduceThreads) pcg_alpha_kernel(const double *partial, int count,
+                                                                   PcgScalars *sc)
 {
-    double t = sum_partials(partial);
+    double t = sum_partials(partial, count);
     if (threadIdx.x == 0) {
         sc->pq = t;
         sc->alpha = sc->rz / t;
     }
 }
 // rz_new = sum(partial); beta = rz_new / rz; rz = rz_new
-__global__ void __launch_bounds__(kReduceThreads) pcg_beta_kernel(const double *partial, PcgScalars *sc)
+__global__ void __launch_bounds__(kReduceThreads) pcg_beta_kernel(const double *partial, int count,
+                                                                  PcgScalars *sc)
 {
-    double t = sum_partials(partial);
+    double t = sum_partials(partial, count);
     if (threadIdx.x == 0) {
         sc->beta = t / sc->rz;
         sc->rz = t;
     }
 }
-__global__ void __launch_bounds__(kReduceThreads) pcg_store_kernel(const double *partial, double *dst)
+__global__ void __launch_bounds__(kReduceThreads) pcg_store_kernel(const double *partial, int count,
+                                                                   double *dst)
 {
-    double t = sum_partials(partial);
+    double t = sum_partials(partial, count);
     if (threadIdx.x == 0) *dst = t;
 }
 
-cudaError_t pcg_alpha(const double *partial, PcgScalars *sc, cudaStream_t s)
+cudaError_t pcg_alpha(const double *partial, int count, PcgScalars *sc, cudaStream_t s)
 {
-    pcg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partial, sc); note_launch();
+    pcg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, sc); note_launch();
     return cudaGetLastError();
 }
-cudaError_t pcg_beta(const double *partial, PcgScalars *sc, cudaStream_t s)
+cudaError_t pcg_beta(const double *partial, int count, PcgScalars *sc, cudaStream_t s)
 {
-    pcg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partial, sc); note_launch();
+    pcg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, sc); note_launch();
     return cudaGetLastError();
 }
-cudaError_t pcg_store(const double *partial, double *dst, cudaStream_t s)
+cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s)
 {
-    pcg_store_kernel<<<1, kReduceThreads, 0, s>>>(partial, dst); note_launch();
+    pcg_store_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, dst); note_launch();
     return cudaGetLastError();
 }
 
@@ -324,16 +426,16 @@ cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, c
         AMG_CUDA_TRY(cudaGetLastError());
     } else {
         ProfScope ps(L == 0 ? KC_VCYCLE_SPMV : KC_COUNT, s, spmv_bytes<T>(lv, 6));
-        AMG_CUDA_TRY((spmv_launch_mode<T, MODE_CHEB>(lv.lanes_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)0,
-                                                     (T)(1.0 / cc.theta), s)));
+        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)0,
+                                              (T)(1.0 / cc.theta), nullptr, s)));
         T *t = x; x = x2; x2 = t;
     }
     for (int k = 1; k < c.cheb_degree; ++k) {
         double rho_new = 1.0 / (2.0 * cc.sigma1 - rho);
         double c1 = rho_new * rho, c2 = 2.0 * rho_new / cc.delta;
         ProfScope ps(L == 0 ? KC_VCYCLE_SPMV : KC_COUNT, s, spmv_bytes<T>(lv, 6));
-        AMG_CUDA_TRY((spmv_launch_mode<T, MODE_CHEB>(lv.lanes_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)c1,
-                                                     (T)c2, s)));
+        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)c1, (T)c2,
+                                              nullptr, s)));
         T *t = x; x = x2; x2 = t;
         rho = rho_new;
     }
@@ -358,16 +460,16 @@ cudaError_t vcycle_level(const SolveCtx &c, int L, T **out, cudaStream_t s)
     // r = f - A x ; f_c = R r
     {
     ProfScope ps(L == 0 ? KC_VCYCLE_SPMV : KC_COUNT, s, spmv_bytes<T>(lv, 3));
-    AMG_CUDA_TRY((spmv_launch_mode<T, MODE_RESID>(lv.lanes_a, lv.n, lv.arp, lv.aci, (const T *)lv.av, x, (T *)lv.r,
-                                                  (const T *)lv.f, nullptr, nullptr, (T)0, (T)0, s)));
+    AMG_CUDA_TRY((spmv_mode<T, MODE_RESID>(lv.plan_a, lv.n, lv.arp, lv.aci, (const T *)lv.av, x, (T *)lv.r,
+                                           (const T *)lv.f, nullptr, nullptr, (T)0, (T)0, nullptr, s)));
     }
-    AMG_CUDA_TRY((spmv_launch_mode<T, MODE_Y>(lv.lanes_r, cl.n, lv.rrp, lv.rci, (const T *)lv.rv, (const T *)lv.r,
-                                              (T *)cl.f, nullptr, nullptr, nullptr, (T)0, (T)0, s)));
+    AMG_CUDA_TRY((spmv_mode<T, MODE_Y>(lv.plan_r, cl.n, lv.rrp, lv.rci, (const T *)lv.rv, (const T *)lv.r, (T *)cl.f,
+                                       nullptr, nullptr, nullptr, (T)0, (T)0, nullptr, s)));
     T *xc = nullptr;
     AMG_CUDA_TRY(vcycle_level<T>(c, L + 1, &xc, s));
     // x += P x_c
-    AMG_CUDA_TRY((spmv_launch_mode<T, MODE_PROLONG>(lv.lanes_p, lv.n, lv.prp, lv.pci, (const T *)lv.pv, xc, x,
-                                                    nullptr, nullptr, nullptr, (T)0, (T)0, s)));
+    AMG_CUDA_TRY((spmv_mode<T, MODE_PROLONG>(lv.plan_p, lv.n, lv.prp, lv.pci, (const T *)lv.pv, xc, x, nullptr,
+                                             nullptr, nullptr, (T)0, (T)0, nullptr, s)));
     AMG_CUDA_TRY(chebyshev<T>(c, L, x, x2, false, s));
     *out = x;
     return cudaSuccess;

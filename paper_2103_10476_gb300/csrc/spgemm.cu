@@ -364,7 +364,7 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     C.n = A.n;
     C.ncol = B.ncol;
     const int n = A.n;
-    AMG_CUDA_TRY(cudaMalloc(&C.rp, sizeof(int) * (size_t)(n + 1)));
+    AMG_CUDA_TRY(cudaMalloc(&C.rp, sizeof(int) * ((size_t)n + 17)));
     if (n == 0) {
         AMG_CUDA_TRY(cudaMemsetAsync(C.rp, 0, sizeof(int), s));
         return cudaSuccess;
@@ -407,8 +407,9 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if ((e = cudaStreamSynchronize(s))) break;
         if (*overflow_host || nnz < 0) { e = cudaErrorInvalidValue; break; }
         C.nnz = nnz;
-        if ((e = cudaMalloc(&C.ci, sizeof(int) * (size_t)(nnz > 0 ? nnz : 1)))) break;
-        if ((e = cudaMalloc(&C.v, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1)))) break;
+        // 16 elements of padding: bulk copies of row ranges widen to 16-byte boundaries
+        if ((e = cudaMalloc(&C.ci, sizeof(int) * ((size_t)nnz + 16)))) break;
+        if ((e = cudaMalloc(&C.v, sizeof(double) * ((size_t)nnz + 16)))) break;
         // numeric, binned by the exact row counts
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
