@@ -160,6 +160,28 @@ amg_status_t amg_csr_release(amg_dcsr_t *C);
 /* Copies a library-allocated device CSR to caller-allocated host arrays (nrow+1, nnz, nnz). */
 amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *col, double *val);
 
+/* Allocation-free sparse product (the paper has no counterpart; it is a deployment aid).
+ * Same product and same summation order as amg_spgemm, for callers that must not allocate
+ * device memory themselves or through the libraries they call: a process that hands all of
+ * the GPU's memory to its own pool, or a serving loop with a fixed memory budget in which a
+ * cudaMalloc could fail, and a cudaFree would stall every stream on the device.
+ *   A (m x ncolA, ncolA = B's rows) and B (ncolA x ncolB): device CSR arrays (on_device = 1),
+ *   int64 row pointers, sorted int32 columns.  The caller provides the result arrays on the
+ *   device: C_row_ptr (m + 1 entries), C_col and C_val (capacity entries each).
+ *   *nnz_out (host) receives nnz(C).  If it exceeds capacity, nothing is written to C_col or
+ *   C_val and AMG_ERR_BUDGET is returned, so the caller can retry with larger arrays.
+ * Temporaries live in one 32 MiB array of device memory that is part of the library: every
+ * GPU that loads the library holds it until the process exits.  Limits: at most 1,000,000
+ * rows in A and in B, and the hash tables of very long rows must fit in what the row arrays
+ * leave of the 32 MiB; beyond them the call returns AMG_ERR_UNSUPPORTED (amg_last_error says
+ * which).  The first call on a device looks the array up (no allocation); make that first
+ * call before any stream capture.  All calls share the array: calls that may overlap on the
+ * GPU (different host threads, or streams without ordering between them) race and must be
+ * serialised by the caller.  Runs on `cuda_stream` and synchronises it before returning. */
+amg_status_t amg_spgemm_noalloc(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB,
+                                void *cuda_stream, int64_t *C_row_ptr, int32_t *C_col, double *C_val,
+                                int64_t capacity, int64_t *nnz_out);
+
 /* Measurement hooks (no counterpart in the paper).
  * amg_launch_count: kernels launched by this library since it was loaded (all threads).
  * amg_profile_enable(1) resets the totals and starts recording CUDA events around the

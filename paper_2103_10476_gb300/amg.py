@@ -77,6 +77,8 @@ def _load():
         "amg_spgemm": (st, [C.POINTER(amg_csr_t), C.c_int64, C.POINTER(amg_csr_t), C.c_int64, vp,
                             C.POINTER(amg_dcsr_t)]),
         "amg_csr_release": (st, [C.POINTER(amg_dcsr_t)]),
+        "amg_spgemm_noalloc": (st, [C.POINTER(amg_csr_t), C.c_int64, C.POINTER(amg_csr_t), C.c_int64, vp, vp, vp, vp,
+                                    C.c_int64, C.POINTER(C.c_int64)]),
         "amg_dcsr_download": (st, [C.POINTER(amg_dcsr_t), vp, vp, vp]),
         "amg_launch_count": (C.c_int64, []),
         "amg_profile_enable": (st, [C.c_int]),
@@ -225,6 +227,17 @@ def amg_profile_read(kclass: int):
     n, ms, by = C.c_int64(), C.c_double(), C.c_double()
     _check(lib.amg_profile_read(kclass, C.byref(n), C.byref(ms), C.byref(by)), "amg_profile_read")
     return n.value, ms.value, by.value
+
+
+def amg_spgemm_noalloc(A: amg_csr_t, ncolA: int, B: amg_csr_t, ncolB: int, C_row_ptr, C_col, C_val,
+                       capacity: int, stream=None):
+    """Allocation-free C = A B into caller-provided device arrays; returns (status, nnz(C))."""
+    nnz = C.c_int64()
+    prp, _ = _ptr(C_row_ptr)
+    pci, _ = _ptr(C_col)
+    pv, _ = _ptr(C_val)
+    s = lib.amg_spgemm_noalloc(C.byref(A), ncolA, C.byref(B), ncolB, stream, prp, pci, pv, capacity, C.byref(nnz))
+    return s, nnz.value
 
 
 def amg_status_string(s: int) -> str:

@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "amg.h"
 
 namespace amgk {
@@ -45,6 +47,9 @@ struct DevCsr {
 // --------------------------------------------------------------------------------- util.cu
 // out[0..n] = exclusive scan of in[0..n-1]; out[n] = total.  in and out may alias.
 cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t s);
+// the same with caller-provided workspace of scan_ws_ints(n) ints (allocates nothing)
+size_t scan_ws_ints(int n);
+cudaError_t scan_exclusive_ws(const int *in, int *out, int n, int *ws, cudaStream_t s);
 // grid-size helper: enough blocks of `threads` to cover `work` items, capped
 int grid_for(int64_t work, int threads, int cap = 1 << 30);
 cudaError_t fill_int(int *p, int value, int64_t n, cudaStream_t s);
@@ -112,6 +117,13 @@ cudaError_t invert_diag(const double *d, double *inv, float *invf, int n, int *z
 // --------------------------------------------------------------------------------- spgemm.cu
 // C = A B, allocating C's arrays with cudaMalloc.  On failure C is left empty.
 cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s);
+
+// Allocation-free C = A B on device arrays (int64 row pointers in and out), temporaries in a
+// fixed file-scope device array; see spgemm.cu.
+cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int nB,
+                           int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t *crp64,
+                           int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status, std::string *msg,
+                           cudaStream_t s);
 
 // --------------------------------------------------------------------------------- coarse.cu
 // Dense SPD inverse of the coarsest operator via Cholesky (FP64).  info = 0 or pivot row+1.

@@ -814,6 +814,36 @@ amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *c
     return e == cudaSuccess ? AMG_OK : fail_cuda(e, "amg_dcsr_download");
 }
 
+amg_status_t amg_spgemm_noalloc(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB, void *stream,
+                                int64_t *C_row_ptr, int32_t *C_col, double *C_val, int64_t capacity, int64_t *nnz_out)
+{
+    if (!A || !B || !C_row_ptr || !nnz_out || capacity < 0 || (capacity > 0 && (!C_col || !C_val)))
+        return AMG_ERR_INVALID_ARG;
+    *nnz_out = 0;
+    if (!A->on_device || !B->on_device) {
+        g_last_error = "amg_spgemm_noalloc: A and B must be device arrays";
+        return AMG_ERR_INVALID_ARG;
+    }
+    if (A->n < 0 || B->n < 0 || ncolA != B->n || ncolB < 0 || ncolB > 0x7ffffffe || A->nnz > 0x7ffffffe ||
+        B->nnz > 0x7ffffffe || A->n > 0x7ffffffe || B->n > 0x7ffffffe || (A->n > 0 && !A->row_ptr) ||
+        (B->n > 0 && !B->row_ptr))
+        return AMG_ERR_INVALID_ARG;
+    int code = 0;
+    std::string msg;
+    cudaError_t e = spgemm_noalloc((int)A->n, (int)ncolA, A->row_ptr, A->col, A->val, (int)B->n, (int)ncolB,
+                                   B->row_ptr, B->col, B->val, C_row_ptr, C_col, C_val, capacity, nnz_out, &code,
+                                   &msg, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e, "amg_spgemm_noalloc");
+    if (code) g_last_error = msg;
+    switch (code) {
+    case 0: return AMG_OK;
+    case 1: return AMG_ERR_UNSUPPORTED;
+    case 2: return AMG_ERR_BUDGET;
+    case 3: return AMG_ERR_INVALID_ARG;
+    default: return AMG_ERR_INTERNAL;
+    }
+}
+
 amg_status_t amg_spgemm(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB, void *stream,
                         amg_dcsr_t *C)
 {

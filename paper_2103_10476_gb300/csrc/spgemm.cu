@@ -8,7 +8,9 @@
 //
 // Rows are binned by table size so each launch uses one size: the symbolic phase by an
 // upper bound (min(products, columns)), the numeric phase by the exact count.
+#include <mutex>
 #include <stdio.h>
+#include <string>
 
 #include "amg_internal.cuh"
 
@@ -442,6 +444,178 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         C.rp = nullptr; C.ci = nullptr; C.v = nullptr; C.nnz = 0;
     }
     return e;
+}
+
+
+// ====================================================================================
+// Allocation-free variant of C = A B (used by amg_spgemm_noalloc).
+//
+// Every temporary of the product lives in one file-scope device array of fixed size instead
+// of memory from cudaMalloc: the int32 row pointers of A, B and C, the row bins, the scan
+// workspace and the hash tables of long rows.  The array belongs to every device that loads
+// this library and stays allocated until the process exits.  Its device address is looked up
+// once per device (cudaGetSymbolAddress) by the first call on that device.  All calls share
+// the array, so calls that overlap on the GPU (other host threads, or other streams without
+// ordering) race on it; the array keeps the previous call's contents, and everything that
+// must start at zero is cleared by the call itself.
+// ====================================================================================
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)32 << 20;      // 32 MiB
+constexpr int64_t kNoAllocMaxRows = 1000000;             // rows of A and of B, each
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[64] = {nullptr};
+
+struct Arena {
+    unsigned char *base = nullptr;
+    size_t size = 0, used = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        size_t off = (used + 255) & ~(size_t)255;
+        size_t bytes = count * sizeof(T);
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return reinterpret_cast<T *>(base + off);
+    }
+};
+
+}  // namespace
+
+// device address of the scratch array on the current device (looked up on first use)
+cudaError_t noalloc_scratch(void **ptr, size_t *bytes)
+{
+    int dev = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    *ptr = g_noalloc_addr[dev];
+    *bytes = kNoAllocBytes;
+    return cudaSuccess;
+}
+
+// status: 0 ok, 1 sizes beyond the scratch limits (msg set), 2 output capacity too small
+// (*nnz_out = required), 3 invalid row pointers, 4 hash overflow; CUDA errors returned as such
+cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int nB,
+                           int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t *crp64,
+                           int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status, std::string *msg,
+                           cudaStream_t s)
+{
+    *status = 0;
+    *nnz_out = 0;
+    if (nA > kNoAllocMaxRows || nB > kNoAllocMaxRows) {
+        *status = 1;
+        *msg = "amg_spgemm_noalloc: more than 1,000,000 rows in A or B";
+        return cudaSuccess;
+    }
+    void *base = nullptr;
+    size_t bytes = 0;
+    AMG_CUDA_TRY(noalloc_scratch(&base, &bytes));
+    Arena ar{(unsigned char *)base, bytes, 0};
+    const int n = nA;
+    int *arp = ar.take<int>((size_t)nA + 1);
+    int *brp = ar.take<int>((size_t)nB + 1);
+    int *crp = ar.take<int>((size_t)nA + 17);
+    int *work = ar.take<int>((size_t)3 * n + 3 * (kNumBins + 1) + 4);
+    int *scan_ws = ar.take<int>(scan_ws_ints(n + 1) + 16);
+    if (!arp || !brp || !crp || !work || !scan_ws) {
+        *status = 1;
+        *msg = "amg_spgemm_noalloc: row arrays do not fit in the 32 MiB scratch";
+        return cudaSuccess;
+    }
+    int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
+    int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
+    int *d_flags = d_binStart + kNumBins + 1;     // [0] bad row pointers, [1] hash overflow
+    AMG_CUDA_TRY(cudaMemsetAsync(d_flags, 0, 2 * sizeof(int), s));
+    AMG_CUDA_TRY(convert_rowptr_to32(arp64, arp, nA + 1, d_flags, s));
+    AMG_CUDA_TRY(convert_rowptr_to32(brp64, brp, nB + 1, d_flags, s));
+    DevCsr A, B, C;
+    A.n = nA; A.ncol = ncolA; A.rp = arp; A.ci = const_cast<int *>(aci); A.v = const_cast<double *>(av);
+    B.n = nB; B.ncol = ncolB; B.rp = brp; B.ci = const_cast<int *>(bci); B.v = const_cast<double *>(bv);
+    C.n = nA; C.ncol = ncolB; C.rp = crp; C.ci = cci; C.v = cv;
+    int hflags[2] = {0, 0};
+    Bins hb;
+    if (n == 0) {
+        AMG_CUDA_TRY(cudaMemsetAsync(crp64, 0, sizeof(int64_t), s));
+        return cudaStreamSynchronize(s);
+    }
+    // symbolic
+    AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
+    ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s));
+    if (hflags[0]) { *status = 3; *msg = "amg_spgemm_noalloc: row pointers not monotone"; return cudaSuccess; }
+    for (int b = 0; b < kGlobalBin; ++b)
+        if (hb.count[b]) AMG_CUDA_TRY(symbolic_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, d_flags + 1, s));
+    const size_t mark = ar.used;
+    if (hb.count[kGlobalBin]) {
+        int cnt = hb.count[kGlobalBin];
+        const int *rows = d_perm + hb.start[kGlobalBin];
+        int *toff = ar.take<int>((size_t)cnt + 1);
+        int *ws2 = ar.take<int>(scan_ws_ints(cnt + 1) + 16);
+        if (!toff || !ws2) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
+        gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, d_tsize, toff); note_launch();
+        AMG_CUDA_TRY(scan_exclusive_ws(toff, toff, cnt, ws2, s));
+        int total = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&total, toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        int *gkeys = total >= 0 ? ar.take<int>((size_t)total) : nullptr;
+        if (!gkeys) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
+        symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, gkeys, A.rp,
+                                                                               A.ci, B.rp, B.ci, C.rp, d_flags + 1); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
+    ar.used = mark;
+    AMG_CUDA_TRY(scan_exclusive_ws(C.rp, C.rp, n, scan_ws, s));
+    int nnz = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&nnz, C.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags[1]) { *status = 4; *msg = "amg_spgemm_noalloc: hash table overflow"; return cudaSuccess; }
+    *nnz_out = nnz;
+    if (nnz > capacity) { *status = 2; *msg = "amg_spgemm_noalloc: output capacity smaller than nnz(C)"; return cudaSuccess; }
+    C.nnz = nnz;
+    // numeric, binned by the exact row counts
+    AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
+    exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s));
+    for (int b = 0; b < kGlobalBin; ++b)
+        if (hb.count[b]) AMG_CUDA_TRY(numeric_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C, d_flags + 1, s));
+    if (hb.count[kGlobalBin]) {
+        int cnt = hb.count[kGlobalBin];
+        const int *rows = d_perm + hb.start[kGlobalBin];
+        int *toff = ar.take<int>((size_t)cnt + 1);
+        int *ws2 = ar.take<int>(scan_ws_ints(cnt + 1) + 16);
+        if (!toff || !ws2) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
+        gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, d_tsize, toff); note_launch();
+        AMG_CUDA_TRY(scan_exclusive_ws(toff, toff, cnt, ws2, s));
+        int total = 0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&total, toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        int *gkeys = total >= 0 ? ar.take<int>((size_t)total) : nullptr;
+        double *gvals = total >= 0 ? ar.take<double>((size_t)total) : nullptr;
+        if (!gkeys || !gvals) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
+        numeric_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, gkeys, gvals,
+                                                                              A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
+                                                                              C.ci, C.v, d_flags + 1); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
+    AMG_CUDA_TRY(convert_rowptr_to64(C.rp, crp64, n + 1, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags[1]) { *status = 4; *msg = "amg_spgemm_noalloc: hash table overflow"; }
+    return cudaSuccess;
 }
 
 }  // namespace amgk

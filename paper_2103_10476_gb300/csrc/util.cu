@@ -185,6 +185,35 @@ cudaError_t scan_exclusive(const int *in, int *out, int n, cudaStream_t s)
     return e != cudaSuccess ? e : e2;
 }
 
+// Same scan with caller-provided workspace for the tile sums (no allocation); ws must hold
+// scan_ws_ints(n) ints.
+size_t scan_ws_ints(int n)
+{
+    size_t total = 0;
+    while (n > 1) {
+        int tiles = (n + kScanTile - 1) / kScanTile;
+        total += (size_t)tiles + 1;
+        if (tiles <= 1) break;
+        n = tiles;
+    }
+    return total + 1;
+}
+
+cudaError_t scan_exclusive_ws(const int *in, int *out, int n, int *ws, cudaStream_t s)
+{
+    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
+    int tiles = (n + kScanTile - 1) / kScanTile;
+    int *sums = ws;
+    scan_tile_kernel<<<tiles, kScanThreads, 0, s>>>(in, out, n, sums); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    if (tiles > 1) {
+        AMG_CUDA_TRY(scan_exclusive_ws(sums, sums, tiles, ws + tiles + 1, s));
+        scan_add_kernel<<<tiles, kScanThreads, 0, s>>>(out, n, sums); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
 // ------------------------------------------------------------------------------------ fills
 __global__ void fill_int_kernel(int *p, int v, int64_t n)
 {
