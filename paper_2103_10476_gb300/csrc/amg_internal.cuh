@@ -168,7 +168,7 @@ cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s
 
 // PCG building blocks (FP64, deterministic reductions; scalars live on the device)
 struct PcgScalars {     // device
-    double rz, pq, alpha, beta, rr, bb, tmp;
+    double rz, rz_next, pq, alpha, beta, rr, bb, tmp;
 };
 cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial, int *nparts,
                      cudaStream_t s);
@@ -177,11 +177,10 @@ cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
 cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
                        cudaStream_t s);
-cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, const PcgScalars *sc,
-                          double *partial, cudaStream_t s);
-cudaError_t pcg_update_p(int n, double *p, const double *z, const PcgScalars *sc, cudaStream_t s);
-cudaError_t pcg_alpha(const double *partial, int count, PcgScalars *sc, cudaStream_t s);
-cudaError_t pcg_beta(const double *partial, int count, PcgScalars *sc, cudaStream_t s);
+cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, PcgScalars *sc,
+                          const double *pq_partial, int pq_count, double *rr_partial, cudaStream_t s);
+cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, const double *rz_partial, int count,
+                         cudaStream_t s);
 cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s);
 int pick_lanes(double avg_row);
 

@@ -50,7 +50,8 @@ struct amg_hierarchy {
     double *coarse_inv = nullptr;
     // solve workspace (FP64, finest level)
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
-    double *partial = nullptr;
+    double *partial = nullptr, *partial2 = nullptr;
+    double *rr_host = nullptr;   // pinned copy of the r . r partial sums
     PcgScalars *sc = nullptr;
     SpmvPlan plan0;   // finest-level FP64 operator (PCG)
     SolveCtx ctx;
@@ -74,12 +75,14 @@ amg_status_t fail_cuda(cudaError_t e, const char *where)
         if (_e != cudaSuccess) { st = fail_cuda(_e, #expr); goto done; }  \
     } while (0)
 
-// every array carries 16 elements of padding: bulk copies widen ranges to 16-byte boundaries
+// Device memory comes from the stream-ordered pool of the handle's stream (no device-wide
+// synchronisation per allocation or free; freed blocks are kept by the pool for reuse).
+// Every array carries 16 elements of padding: bulk copies widen ranges to 16-byte boundaries.
 template <typename T>
 cudaError_t dalloc(amg_hierarchy *h, T **p, size_t count)
 {
     *p = nullptr;
-    cudaError_t e = cudaMalloc((void **)p, (count + 16) * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void **)p, (count + 16) * sizeof(T), h->s);
     if (e == cudaSuccess) h->allocs.push_back((void *)*p);
     return e;
 }
@@ -93,10 +96,29 @@ void own(amg_hierarchy *h, const DevCsr &c)
 
 void release_all(amg_hierarchy *h)
 {
-    if (h->s) cudaStreamSynchronize(h->s);
-    else cudaDeviceSynchronize();
-    for (void *p : h->allocs) cudaFree(p);
+    for (void *p : h->allocs) cudaFreeAsync(p, h->s);
     h->allocs.clear();
+    cudaStreamSynchronize(h->s);
+}
+
+// keep freed memory in the device's default pool instead of returning it at every sync
+void keep_pool_memory()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    static bool done[64] = {false};
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+}
+
+void free_async(void *p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
 }
 
 __global__ void validate_kernel(int n, const int *rp, const int *ci, int *bad)
@@ -149,26 +171,26 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
 
     CK(dalloc(h, &lv.strong, (size_t)A.nnz));
     CK(dalloc(h, &lv.removed, (size_t)A.nnz));
-    CK(cudaMalloc(&kept, sizeof(int) * (size_t)(n + 1)));
-    CK(cudaMalloc(&flags, sizeof(int) * 4));
+    CK(cudaMallocAsync(&kept, sizeof(int) * (size_t)(n + 1), s));
+    CK(cudaMallocAsync(&flags, sizeof(int) * 4, s));
     CK(cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
     // Eq. (7)
     CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
     // strong graph
-    CK(cudaMalloc(&grp, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(n + 1), s));
     CK(strong_graph_counts(A, lv.strong, grp, s));
     CK(scan_exclusive(grp, grp, n, s));
     CK(cudaMemcpyAsync(&nnz_g, grp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    CK(cudaMalloc(&gci, sizeof(int) * (size_t)(nnz_g > 0 ? nnz_g : 1)));
+    CK(cudaMallocAsync(&gci, sizeof(int) * (size_t)(nnz_g > 0 ? nnz_g : 1), s));
     CK(strong_graph_fill(A, lv.strong, grp, gci, s));
     // aggregation
     CK(dalloc(h, &lv.agg, (size_t)n));
     CK(dalloc(h, &lv.root, (size_t)n));
-    CK(cudaMalloc(&t0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1)));
-    CK(cudaMalloc(&t1, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1)));
-    CK(cudaMalloc(&rootof, sizeof(int) * (size_t)(n + 1)));
-    CK(cudaMalloc(&join1, sizeof(int) * (size_t)(n + 1)));
+    CK(cudaMallocAsync(&t0, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s));
+    CK(cudaMallocAsync(&t1, sizeof(unsigned long long) * (size_t)(n > 0 ? n : 1), s));
+    CK(cudaMallocAsync(&rootof, sizeof(int) * (size_t)(n + 1), s));
+    CK(cudaMallocAsync(&join1, sizeof(int) * (size_t)(n + 1), s));
     {
         AggWork w{t0, t1, rootof, join1, flags + 2};
         cudaError_t e = aggregate_mis2(n, grp, gci, p.seed, L, w, lv.agg, lv.root, &nagg, &rounds, s);
@@ -178,15 +200,15 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     lv.nagg = nagg;
     if (nagg == n || nagg == 0) { *coarsest = 1; goto done; }
     // members and tentative-prolongator column norms
-    CK(cudaMalloc(&mstart, sizeof(int) * (size_t)(nagg + 1)));
-    CK(cudaMalloc(&members, sizeof(int) * (size_t)n));
-    CK(cudaMalloc(&fill, sizeof(int) * (size_t)(nagg + 1)));
+    CK(cudaMallocAsync(&mstart, sizeof(int) * (size_t)(nagg + 1), s));
+    CK(cudaMallocAsync(&members, sizeof(int) * (size_t)n, s));
+    CK(cudaMallocAsync(&fill, sizeof(int) * (size_t)(nagg + 1), s));
     CK(aggregate_members(n, nagg, lv.agg, mstart, members, fill, s));
     CK(dalloc(h, &lv.nrm, (size_t)nagg));
     CK(aggregate_norms(nagg, mstart, members, lv.B, lv.nrm, flags + 0, s));
     // §2.5
     if (p.variants & AMG_VAR_SPRSFY) {
-        CK(cudaMalloc(&drop, (size_t)(A.nnz > 0 ? A.nnz : 1)));
+        CK(cudaMallocAsync(&drop, (size_t)(A.nnz > 0 ? A.nnz : 1), s));
         CK(sprsfy(A, lv.strong, lv.agg, lv.root, nagg, mstart, members, drop, lv.removed, kept, s));
     }
     // filtered matrix and smoothing diagonal
@@ -213,12 +235,12 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         goto done;
     }
     // eigenvalue of Dsm^-1 Abar and omega = 4 / (3 lambda), Eq. (3)
-    CK(cudaMalloc(&px, sizeof(double) * (size_t)n));
-    CK(cudaMalloc(&py, sizeof(double) * (size_t)n));
+    CK(cudaMallocAsync(&px, sizeof(double) * (size_t)n, s));
+    CK(cudaMallocAsync(&py, sizeof(double) * (size_t)n, s));
     {
         // 8 scalars, then the partial sums of the power method's dot products
         int np = spmv_partials_needed(n);
-        CK(cudaMalloc(&scal, sizeof(double) * (size_t)((np > kReduceBlocks ? np : kReduceBlocks) + 8)));
+        CK(cudaMallocAsync(&scal, sizeof(double) * (size_t)((np > kReduceBlocks ? np : kReduceBlocks) + 8), s));
     }
     if (p.lambda_override > 0.0) {
         lv.lambda_bar = p.lambda_override;
@@ -312,12 +334,12 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         CK(cudaGetLastError());
     }
 done:
+    for (void *p : {(void *)kept, (void *)grp, (void *)gci, (void *)mstart, (void *)members, (void *)fill,
+                    (void *)flags, (void *)t0, (void *)t1, (void *)rootof, (void *)join1, (void *)drop, (void *)px,
+                    (void *)py, (void *)scal, (void *)AP.rp, (void *)AP.ci, (void *)AP.v, (void *)Ac.rp,
+                    (void *)Ac.ci, (void *)Ac.v})
+        free_async(p, s);
     cudaStreamSynchronize(s);
-    cudaFree(kept); cudaFree(grp); cudaFree(gci); cudaFree(mstart); cudaFree(members); cudaFree(fill);
-    cudaFree(flags); cudaFree(t0); cudaFree(t1); cudaFree(rootof); cudaFree(join1); cudaFree(drop);
-    cudaFree(px); cudaFree(py); cudaFree(scal);
-    cudaFree(AP.rp); cudaFree(AP.ci); cudaFree(AP.v);
-    cudaFree(Ac.rp); cudaFree(Ac.ci); cudaFree(Ac.v);
     return st;
 }
 
@@ -387,6 +409,8 @@ amg_status_t prepare_solve(amg_hierarchy *h)
     {
         int np = spmv_partials_needed(n0);
         CK(dalloc(h, &h->partial, (size_t)(np > kReduceBlocks ? np : kReduceBlocks)));
+        CK(dalloc(h, &h->partial2, (size_t)kReduceBlocks));
+        CK(cudaMallocHost(&h->rr_host, sizeof(double) * kReduceBlocks));
         if (n0 > 0) CK(spmv_plan(h->lev[0].A.rp, n0, h->lev[0].A.nnz, &h->plan0, s));
     }
     CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
@@ -462,6 +486,7 @@ amg_status_t amg_free(amg_handle_t h)
 {
     if (!h) return AMG_OK;
     release_all(h);
+    if (h->rr_host) cudaFreeHost(h->rr_host);
     delete h;
     return AMG_OK;
 }
@@ -484,6 +509,7 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         return AMG_ERR_INVALID_ARG;
     }
     const double t_start = now_ms();
+    keep_pool_memory();
     amg_hierarchy *h = new amg_hierarchy();
     h->p = p;
     h->s = (cudaStream_t)p.cuda_stream;
@@ -506,9 +532,9 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         CK(dalloc(h, &l0.A.rp, (size_t)n + 1));
         CK(dalloc(h, &l0.A.ci, (size_t)nnz));
         CK(dalloc(h, &l0.A.v, (size_t)nnz));
-        CK(cudaMalloc(&bad, sizeof(int)));
+        CK(cudaMallocAsync(&bad, sizeof(int), s));
         CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
-        CK(cudaMalloc(&rp64, sizeof(int64_t) * ((size_t)n + 1)));
+        CK(cudaMallocAsync(&rp64, sizeof(int64_t) * ((size_t)n + 1), s));
         CK(cudaMemcpyAsync(rp64, Ain->row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDefault, s));
         CK(convert_rowptr_to32(rp64, l0.A.rp, n + 1, bad, s));
         if (nnz > 0) {
@@ -551,7 +577,7 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         const int nc = cl.A.n;
         if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
         CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
-        CK(cudaMalloc(&cwork, sizeof(double) * ((size_t)nc * nc > 0 ? (size_t)nc * nc : 1)));
+        CK(cudaMallocAsync(&cwork, sizeof(double) * ((size_t)nc * nc > 0 ? (size_t)nc * nc : 1), s));
         CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s));
         CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -567,9 +593,9 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         }
     }
 done:
-    cudaFree(bad);
-    cudaFree(rp64);
-    cudaFree(cwork);
+    free_async(bad, s);
+    free_async(rp64, s);
+    free_async(cwork, s);
     if (st != AMG_OK) {
         amg_free(h);
         return st;
@@ -641,19 +667,19 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     if (nb == 0.0) goto finish;
     CK(vcycle(h->ctx, h->r, h->z, s));
     CK(cudaMemcpyAsync(h->pv, h->z, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    CK(dot(h->r, h->z, n, h->partial, &h->sc->rz, s));
+    CK(dot(h->r, h->z, n, h->partial, &h->sc->rz_next, s));
     result = AMG_ERR_NOT_CONVERGED;
     while (it < h->p.max_iter) {
         {
             ProfScope ps(KC_PCG_SPMV, s, 12.0 * (double)A.nnz + 20.0 * n + 4.0);
             CK(spmv_dot(A, plan, h->pv, h->q, h->partial, &nparts, s));
         }
-        CK(pcg_alpha(h->partial, nparts, h->sc, s));
-        CK(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, s));
-        CK(pcg_store(h->partial, kReduceBlocks, &h->sc->rr, s));
+        CK(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, nparts, h->partial2, s));
         ++it;
-        CK(cudaMemcpyAsync(&rr, &h->sc->rr, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(h->rr_host, h->partial2, sizeof(double) * kReduceBlocks, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        rr = 0.0;
+        for (int k = 0; k < kReduceBlocks; ++k) rr += h->rr_host[k];
         if (std::sqrt(rr) / nb <= tol) {
             CK(residual_d(A, plan, h->b, h->x, h->t, s));
             CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
@@ -665,8 +691,7 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
         }
         CK(vcycle(h->ctx, h->r, h->z, s));
         CK(dot_partial(h->r, h->z, n, h->partial, s));
-        CK(pcg_beta(h->partial, kReduceBlocks, h->sc, s));
-        CK(pcg_update_p(n, h->pv, h->z, h->sc, s));
+        CK(pcg_update_p(n, h->pv, h->z, h->sc, h->partial, kReduceBlocks, s));
     }
 finish:
     if (n > 0) {

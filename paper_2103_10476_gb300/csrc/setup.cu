@@ -29,15 +29,6 @@ __device__ __forceinline__ uint64_t agg_priority(uint64_t seed, int level, int i
     return ((h >> 34) << 32) | (uint64_t)(uint32_t)i;
 }
 
-// Sequential (ascending-lane) sum of one warp-wide chunk added to acc; every lane returns
-// the same value.  Lanes that contribute nothing pass +0.0 (which leaves the sum unchanged).
-__device__ __forceinline__ double warp_seq_sum(double acc, double x)
-{
-#pragma unroll
-    for (int t = 0; t < 32; ++t) acc = acc + __shfl_sync(kFull, x, t);
-    return acc;
-}
-
 // ------------------------------------------------------------------------------------ diagonal
 __global__ void diag_kernel(int n, const int *rp, const int *ci, const double *v, int *pos, double *d)
 {
@@ -503,48 +494,36 @@ cudaError_t sprsfy(const DevCsr &A, const uint8_t *strong, const int *agg, const
 enum { LUMP_DIAG = 0, LUMP_KPLUS = 1, LUMP_DIAG_KMINUS = 2, LUMP_KPLUS_NEG = 3, LUMP_SKIPPED = 4,
        LUMP_FALLBACK = 5 };
 
+// One thread per row: every sum runs sequentially in ascending column order (the per-row
+// FP64 work is a handful of additions per stored entry; GB300's FP64 pipe makes redundant
+// per-lane sums expensive).
 __global__ void filter_kernel(int n, const int *rp, const int *ci, const double *v, const uint8_t *removed,
                               int offlmp, double tau, int onenorm, double sigma, const int *brp, int *bci,
                               double *bv, double *Dsm, uint8_t *lumpflag, int *zero_diag)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int b = rp[i], e_end = rp[i + 1];
     // pass 1: row sums in ascending order
     double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
     int nkp = 0, nkm = 0, has_diag = 0;
-    for (int base = b; base < e_end; base += 32) {
-        int e = base + lane;
-        double x = 0.0, xp = 0.0, xm = 0.0, xa = 0.0;
-        int isd = 0;
-        if (e < e_end) {
-            int j = ci[e];
-            double val = v[e];
-            if (j == i) { isd = 1; }
-            else {
-                xa = fabs(val);
-                if (removed[e]) x = val;
-                else if (val > 0.0) xp = val;
-                else if (val < 0.0) xm = val;
-            }
-        }
-        r = warp_seq_sum(r, x);
-        if (offlmp) {
-            kp = warp_seq_sum(kp, xp);
-            km = warp_seq_sum(km, xm);
-            offabs = warp_seq_sum(offabs, xa);
-            nkp += __popc(__ballot_sync(kFull, xp > 0.0));
-            nkm += __popc(__ballot_sync(kFull, xm < 0.0));
-        }
-        unsigned dm = __ballot_sync(kFull, isd);
-        if (dm) {
-            int src = __ffs(dm) - 1;
-            aii = __shfl_sync(kFull, e < e_end ? v[e < e_end ? e : b] : 0.0, src);
+    for (int e = b; e < e_end; ++e) {
+        const int j = ci[e];
+        const double val = v[e];
+        if (j == i) {
+            aii = val;
             has_diag = 1;
+            continue;
+        }
+        if (offlmp) offabs = offabs + fabs(val);
+        if (removed[e]) {
+            r = r + val;
+        } else if (offlmp) {
+            if (val > 0.0) { kp = kp + val; ++nkp; }
+            else if (val < 0.0) { km = km + val; ++nkm; }
         }
     }
-    // decide the row's outcome (every lane computes the same)
+    // the row's outcome
     int flag = LUMP_DIAG;
     double new_diag = aii + r;     // Eq. (6)
     double fplus = 1.0, fminus = 1.0;
@@ -586,66 +565,55 @@ __global__ void filter_kernel(int n, const int *rp, const int *ci, const double 
             fminus = 1.0 + (rhat + rstar) / km;
         }
     }
-    // pass 2: write the kept entries, and the 1-norm sums over them in ascending order
+    // pass 2: the kept entries, and the 1-norm sums over them in ascending order
     int out = brp[i];
     double dsum = 0.0, ssum = 0.0;
-    for (int base = b; base < e_end; base += 32) {
-        int e = base + lane;
-        bool keep = false;
-        double nv = 0.0;
-        int j = -1;
-        if (e < e_end) {
-            j = ci[e];
-            double val = v[e];
-            if (j == i) {
-                keep = true;
-                nv = new_diag;
-            } else if (!removed[e]) {
-                keep = true;
-                nv = val;
-                if (offlmp && flag != LUMP_FALLBACK) {
-                    if (val > 0.0) {
-                        if (zero_plus) nv = 0.0;
-                        else if (flag == LUMP_KPLUS || flag == LUMP_KPLUS_NEG) nv = val * fplus;
-                    } else if (val < 0.0 && flag == LUMP_DIAG_KMINUS) {
-                        nv = val * fminus;
-                    }
+    for (int e = b; e < e_end; ++e) {
+        const int j = ci[e];
+        double nv;
+        if (j == i) {
+            nv = new_diag;
+        } else if (!removed[e]) {
+            const double val = v[e];
+            nv = val;
+            if (offlmp && flag != LUMP_FALLBACK) {
+                if (val > 0.0) {
+                    if (zero_plus) nv = 0.0;
+                    else if (flag == LUMP_KPLUS || flag == LUMP_KPLUS_NEG) nv = val * fplus;
+                } else if (val < 0.0 && flag == LUMP_DIAG_KMINUS) {
+                    nv = val * fminus;
                 }
             }
-        }
-        unsigned m = __ballot_sync(kFull, keep);
-        if (keep) {
-            int p = out + __popc(m & ((1u << lane) - 1u));
-            bci[p] = j;
-            bv[p] = nv;
-        }
-        out += __popc(m);
-        if (onenorm) {
-            dsum = warp_seq_sum(dsum, keep ? fabs(nv) : 0.0);
-            ssum = warp_seq_sum(ssum, keep ? nv : 0.0);
-        }
-    }
-    if (lane == 0) {
-        lumpflag[i] = (uint8_t)flag;
-        double dd;
-        if (onenorm) {
-            double f = (sigma == 1.0 / 3.0) ? 2.0 : 4.0 / (3.0 * (1.0 - sigma));
-            dd = dsum;
-            if (dd == 0.0) dd = 1.0;
-            if (dd < f * ssum) dd = f * ssum;
         } else {
-            dd = has_diag ? new_diag : 0.0;
-            if (dd == 0.0) atomicAdd(zero_diag, 1);
+            continue;
         }
-        Dsm[i] = dd;
+        bci[out] = j;
+        bv[out] = nv;
+        ++out;
+        if (onenorm) {
+            dsum = dsum + fabs(nv);
+            ssum = ssum + nv;
+        }
     }
+    lumpflag[i] = (uint8_t)flag;
+    double dd;
+    if (onenorm) {
+        double f = (sigma == 1.0 / 3.0) ? 2.0 : 4.0 / (3.0 * (1.0 - sigma));
+        dd = dsum;
+        if (dd == 0.0) dd = 1.0;
+        if (dd < f * ssum) dd = f * ssum;
+    } else {
+        dd = has_diag ? new_diag : 0.0;
+        if (dd == 0.0) atomicAdd(zero_diag, 1);
+    }
+    Dsm[i] = dd;
 }
 
 cudaError_t filter(const DevCsr &A, const uint8_t *removed, int offlmp, double tau, int onenorm, double sigma,
                    DevCsr &Abar, double *Dsm, uint8_t *lumpflag, int *zero_diag, cudaStream_t s)
 {
     if (A.n == 0) return cudaSuccess;
-    filter_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, removed, offlmp, tau,
+    filter_kernel<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rp, A.ci, A.v, removed, offlmp, tau,
                                                                    onenorm, sigma, Abar.rp, Abar.ci, Abar.v, Dsm,
                                                                    lumpflag, zero_diag); note_launch();
     return cudaGetLastError();
@@ -654,32 +622,83 @@ cudaError_t filter(const DevCsr &A, const uint8_t *removed, int offlmp, double t
 // ------------------------------------------------------------------------------------ smoothed prolongator
 // Row i of P = (I - omega D^-1 Abar) Pt has the aggregates of Abar's row-i columns, sorted;
 // (Abar Pt)_ic sums Abar_ik B_k over those k (ascending) with agg(k) = c.
+constexpr int kSmoothLocal = 64;    // distinct columns a thread keeps locally
+
+// distinct aggregates of the row's columns (thread per row; integer work only)
 __global__ void smooth_count_kernel(int n, const int *rp, const int *ci, const int *agg, int *cnt)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int b = rp[i], m = rp[i + 1] - b;
     int distinct = 0;
-    for (int t = lane; t < m; t += 32) {
-        int c = agg[ci[b + t]];
+    for (int t = 0; t < m; ++t) {
+        const int c = agg[ci[b + t]];
         bool first = true;
         for (int u = 0; u < t; ++u)
             if (agg[ci[b + u]] == c) { first = false; break; }
         distinct += first;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) distinct += __shfl_down_sync(kFull, distinct, o);
-    if (lane == 0) cnt[i] = distinct;
+    cnt[i] = distinct;
 }
 
+// Thread per row: the products Abar_ik B_k are added in ascending k into the slot of agg(k)
+// (a local list in first-seen order), then the list is sorted by column and written as
+// P_ic = Pt_ic - (omega / D_i) (Abar Pt)_ic.  Rows with more than kSmoothLocal distinct
+// columns are listed for the warp kernel below.
 __global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const double *v, const int *agg,
                                    const double *B, const double *Dsm, const double *omega_dev, const int *prp,
-                                   int *pci, double *pv)
+                                   int *pci, double *pv, int *wide_rows, int *nwide)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nd = prp[i + 1] - prp[i];
+    if (nd > kSmoothLocal) {
+        wide_rows[atomicAdd(nwide, 1)] = i;
+        return;
+    }
+    int cols[kSmoothLocal];
+    double acc[kSmoothLocal];
+    int cnt = 0;
+    const int b = rp[i], e = rp[i + 1];
+    for (int t = b; t < e; ++t) {
+        const int k = ci[t];
+        const int c = agg[k];
+        const double prod = v[t] * B[k];
+        int p = 0;
+        while (p < cnt && cols[p] != c) ++p;
+        if (p == cnt) { cols[cnt] = c; acc[cnt] = 0.0; ++cnt; }
+        acc[p] = acc[p] + prod;
+    }
+    // insertion sort by column
+    for (int a = 1; a < cnt; ++a) {
+        int c = cols[a];
+        double x = acc[a];
+        int q = a - 1;
+        while (q >= 0 && cols[q] > c) { cols[q + 1] = cols[q]; acc[q + 1] = acc[q]; --q; }
+        cols[q + 1] = c;
+        acc[q + 1] = x;
+    }
+    const double scale = *omega_dev / Dsm[i];
+    const int ai = agg[i];
+    const double bi = B[i];
+    const int o = prp[i];
+    for (int a = 0; a < cnt; ++a) {
+        const double pt = (cols[a] == ai) ? bi : 0.0;
+        pci[o + a] = cols[a];
+        pv[o + a] = pt - scale * acc[a];
+    }
+}
+
+// one warp per wide row (listed by smooth_fill_kernel): each distinct column's sum runs
+// sequentially over the row in ascending order
+__global__ void smooth_fill_wide_kernel(const int *rows, const int *nrows, const int *rp, const int *ci,
+                                        const double *v, const int *agg, const double *B, const double *Dsm,
+                                        const double *omega_dev, const int *prp, int *pci, double *pv)
 {
     const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
+    const int total = *nrows;
+    for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += (gridDim.x * blockDim.x) >> 5) {
+    const int i = rows[w];
     const int b = rp[i], m = rp[i + 1] - b;
     const double scale = *omega_dev / Dsm[i];
     const int ai = agg[i];
@@ -690,7 +709,6 @@ __global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const do
         for (int u = 0; u < t; ++u)
             if (agg[ci[b + u]] == c) { first = false; break; }
         if (!first) continue;
-        // rank among distinct columns, and the ordered sum
         int rank = 0;
         double acc = 0.0;
         for (int u = 0; u < m; ++u) {
@@ -700,8 +718,8 @@ __global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const do
                 acc = acc + v[b + u] * B[k];
             } else if (cu < c) {
                 bool fu = true;
-                for (int w = 0; w < u; ++w)
-                    if (agg[ci[b + w]] == cu) { fu = false; break; }
+                for (int q = 0; q < u; ++q)
+                    if (agg[ci[b + q]] == cu) { fu = false; break; }
                 rank += fu;
             }
         }
@@ -710,12 +728,13 @@ __global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const do
         pci[p] = c;
         pv[p] = pt - scale * acc;
     }
+    }
 }
 
 cudaError_t smooth_counts(const DevCsr &Abar, const int *agg, int *cnt, cudaStream_t s)
 {
     if (Abar.n == 0) return cudaSuccess;
-    smooth_count_kernel<<<grid_for((int64_t)Abar.n * 32, 256), 256, 0, s>>>(Abar.n, Abar.rp, Abar.ci, agg, cnt); note_launch();
+    smooth_count_kernel<<<grid_for(Abar.n, 128), 128, 0, s>>>(Abar.n, Abar.rp, Abar.ci, agg, cnt); note_launch();
     return cudaGetLastError();
 }
 
@@ -723,9 +742,20 @@ cudaError_t smooth_fill(const DevCsr &Abar, const int *agg, const double *B, con
                         const double *omega_dev, DevCsr &P, cudaStream_t s)
 {
     if (Abar.n == 0) return cudaSuccess;
-    smooth_fill_kernel<<<grid_for((int64_t)Abar.n * 32, 256), 256, 0, s>>>(Abar.n, Abar.rp, Abar.ci, Abar.v, agg, B,
-                                                                           Dsm, omega_dev, P.rp, P.ci, P.v); note_launch();
-    return cudaGetLastError();
+    int *wide = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&wide, sizeof(int) * ((size_t)Abar.n + 1), s));
+    int *nwide = wide + Abar.n;
+    cudaError_t e = cudaMemsetAsync(nwide, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        smooth_fill_kernel<<<grid_for(Abar.n, 128), 128, 0, s>>>(Abar.n, Abar.rp, Abar.ci, Abar.v, agg, B, Dsm,
+                                                                 omega_dev, P.rp, P.ci, P.v, wide, nwide); note_launch();
+        // the wide rows (normally none): one warp each, grid-stride over the list
+        smooth_fill_wide_kernel<<<grid_for((int64_t)Abar.n * 32, 256, 608), 256, 0, s>>>(
+            wide, nwide, Abar.rp, Abar.ci, Abar.v, agg, B, Dsm, omega_dev, P.rp, P.ci, P.v); note_launch();
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(wide, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 // ------------------------------------------------------------------------------------ Algorithm 3
@@ -893,10 +923,14 @@ __global__ void power_init_kernel(int n, uint64_t s0, double *x)
     x[i] = 2.0 * u - 1.0;
 }
 
+// dst = src / sqrt(*sq); the square root is taken once per block
 __global__ void scale_by_norm_kernel(int n, const double *src, double *dst, const double *sq)
 {
+    __shared__ double nrm;
+    if (threadIdx.x == 0) nrm = __dsqrt_rn(*sq);
+    __syncthreads();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i] / __dsqrt_rn(*sq);
+    if (i < n) dst[i] = src[i] / nrm;
 }
 
 cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t stream_seed, double *x, double *y,

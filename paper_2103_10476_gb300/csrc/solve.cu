@@ -261,12 +261,44 @@ __device__ __forceinline__ double block_sum_fixed(double v)
     return t;
 }
 
-// x += alpha p; r -= alpha q; partial sums of r . r
-__global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x, double *r, const double *p,
-                                                                const double *q, const PcgScalars *sc,
-                                                                double *partial)
+// Every block sums the same partials in the same fixed order, so every block holds the
+// same scalar and no separate scalar kernel (and launch) is needed.
+__device__ __forceinline__ double block_sum_all(double v)
 {
-    const double alpha = sc->alpha;
+    __shared__ double sh[kReduceThreads / 32];
+    __shared__ double total;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kAll, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) t += sh[w];
+        total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ double sum_partials_all(const double *partial, int count)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < count; i += kReduceThreads) acc += partial[i];
+    return block_sum_all(acc);
+}
+
+// alpha = rz / (p . q) from the SpMV's partial sums; x += alpha p; r -= alpha q; partial sums
+// of r . r (read back by the host for the stopping test)
+__global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x, double *r, const double *p,
+                                                                const double *q, PcgScalars *sc,
+                                                                const double *pq_partial, int pq_count,
+                                                                double *rr_partial)
+{
+    const double pq = sum_partials_all(pq_partial, pq_count);
+    const double alpha = sc->rz_next / pq;
+    // rz_next (this iteration's r . z) becomes rz, read by the next p update; this kernel
+    // reads only rz_next, so the write races with nothing
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->pq = pq; sc->alpha = alpha; sc->rz = sc->rz_next; }
     double acc = 0.0;
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
         x[i] += alpha * p[i];
@@ -274,57 +306,42 @@ __global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x
         r[i] = ri;
         acc += ri * ri;
     }
-    double t = block_sum_fixed(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    double t = block_sum_all(acc);
+    if (threadIdx.x == 0) rr_partial[blockIdx.x] = t;
 }
 
-cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, const PcgScalars *sc,
-                          double *partial, cudaStream_t s)
+cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, PcgScalars *sc,
+                          const double *pq_partial, int pq_count, double *rr_partial, cudaStream_t s)
 {
-    pcg_xr_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p, q, sc, partial); note_launch();
+    pcg_xr_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p, q, sc, pq_partial, pq_count, rr_partial); note_launch();
     return cudaGetLastError();
 }
 
-__global__ void pcg_p_kernel(int n, double *p, const double *z, const PcgScalars *sc)
+// rz' = r . z from partial sums; beta = rz' / rz; p = z + beta p.  The new value goes to a
+// second slot (rz_next) that the next alpha reads, so no block overwrites what another block
+// of the same kernel still reads.
+__global__ void __launch_bounds__(kReduceThreads) pcg_p_kernel(int n, double *p, const double *z, PcgScalars *sc,
+                                                               const double *rz_partial, int count)
 {
-    const double beta = sc->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
+    const double rz_new = sum_partials_all(rz_partial, count);
+    const double beta = rz_new / sc->rz;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
+        p[i] = z[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
 }
 
-cudaError_t pcg_update_p(int n, double *p, const double *z, const PcgScalars *sc, cudaStream_t s)
+cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, const double *rz_partial, int count,
+                         cudaStream_t s)
 {
-    if (n == 0) return cudaSuccess;
-    pcg_p_kernel<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, p, z, sc); note_launch();
+    pcg_p_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, z, sc, rz_partial, count); note_launch();
     return cudaGetLastError();
 }
 
 __device__ __forceinline__ double sum_partials(const double *partial, int count)
 {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < count; i += kReduceThreads) acc += partial[i];
-    return block_sum_fixed(acc);
+    return sum_partials_all(partial, count);
 }
 
-// pq = sum(partial); alpha = rz / pq
-__global__ void __launch_bounds__(kReduceThreads) pcg_alpha_kernel(const double *partial, int count,
-                                                                   PcgScalars *sc)
-{
-    double t = sum_partials(partial, count);
-    if (threadIdx.x == 0) {
-        sc->pq = t;
-        sc->alpha = sc->rz / t;
-    }
-}
-// rz_new = sum(partial); beta = rz_new / rz; rz = rz_new
-__global__ void __launch_bounds__(kReduceThreads) pcg_beta_kernel(const double *partial, int count,
-                                                                  PcgScalars *sc)
-{
-    double t = sum_partials(partial, count);
-    if (threadIdx.x == 0) {
-        sc->beta = t / sc->rz;
-        sc->rz = t;
-    }
-}
 __global__ void __launch_bounds__(kReduceThreads) pcg_store_kernel(const double *partial, int count,
                                                                    double *dst)
 {
@@ -332,16 +349,6 @@ __global__ void __launch_bounds__(kReduceThreads) pcg_store_kernel(const double 
     if (threadIdx.x == 0) *dst = t;
 }
 
-cudaError_t pcg_alpha(const double *partial, int count, PcgScalars *sc, cudaStream_t s)
-{
-    pcg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, sc); note_launch();
-    return cudaGetLastError();
-}
-cudaError_t pcg_beta(const double *partial, int count, PcgScalars *sc, cudaStream_t s)
-{
-    pcg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, sc); note_launch();
-    return cudaGetLastError();
-}
 cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s)
 {
     pcg_store_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, dst); note_launch();
@@ -412,7 +419,8 @@ ChebCoef cheb_coef(double lambda, double ratio)
 // Chebyshev smoothing of degree m on level L; x holds the iterate (x_is_zero: it is 0).
 // Returns the buffer that holds the result (x or x2).
 template <typename T>
-cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, cudaStream_t s)
+cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, cudaStream_t s,
+                      T *final_out = nullptr)
 {
     const LevelView &lv = c.lev[L];
     const ChebCoef cc = cheb_coef(lv.lambda, c.cheb_ratio);
@@ -426,16 +434,20 @@ cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, c
         AMG_CUDA_TRY(cudaGetLastError());
     } else {
         ProfScope ps(L == 0 ? KC_VCYCLE_SPMV : KC_COUNT, s, spmv_bytes<T>(lv, 6));
-        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)0,
+        T *dst = (final_out && c.cheb_degree == 1) ? final_out : x2;
+        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, dst, f, inv, d, (T)0,
                                               (T)(1.0 / cc.theta), nullptr, s)));
+        x2 = dst;
         T *t = x; x = x2; x2 = t;
     }
     for (int k = 1; k < c.cheb_degree; ++k) {
         double rho_new = 1.0 / (2.0 * cc.sigma1 - rho);
         double c1 = rho_new * rho, c2 = 2.0 * rho_new / cc.delta;
         ProfScope ps(L == 0 ? KC_VCYCLE_SPMV : KC_COUNT, s, spmv_bytes<T>(lv, 6));
-        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, x2, f, inv, d, (T)c1, (T)c2,
+        T *dst = (final_out && k == c.cheb_degree - 1) ? final_out : x2;
+        AMG_CUDA_TRY((spmv_mode<T, MODE_CHEB>(lv.plan_a, lv.n, lv.arp, lv.aci, av, x, dst, f, inv, d, (T)c1, (T)c2,
                                               nullptr, s)));
+        x2 = dst;
         T *t = x; x = x2; x2 = t;
         rho = rho_new;
     }
@@ -444,7 +456,7 @@ cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, c
 
 // Algorithm 1 from level L with x = 0; on return *out points at the level's solution buffer.
 template <typename T>
-cudaError_t vcycle_level(const SolveCtx &c, int L, T **out, cudaStream_t s)
+cudaError_t vcycle_level(const SolveCtx &c, int L, T **out, cudaStream_t s, T *final_out = nullptr)
 {
     const LevelView &lv = c.lev[L];
     T *x = (T *)lv.x, *x2 = (T *)lv.x2;
@@ -470,7 +482,7 @@ cudaError_t vcycle_level(const SolveCtx &c, int L, T **out, cudaStream_t s)
     // x += P x_c
     AMG_CUDA_TRY((spmv_mode<T, MODE_PROLONG>(lv.plan_p, lv.n, lv.prp, lv.pci, (const T *)lv.pv, xc, x, nullptr,
                                              nullptr, nullptr, (T)0, (T)0, nullptr, s)));
-    AMG_CUDA_TRY(chebyshev<T>(c, L, x, x2, false, s));
+    AMG_CUDA_TRY(chebyshev<T>(c, L, x, x2, false, s, final_out));
     *out = x;
     return cudaSuccess;
 }
@@ -486,7 +498,8 @@ cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s
         SolveCtx cc = c;
         cc.lev[0].f = (void *)r;
         double *out = nullptr;
-        AMG_CUDA_TRY(vcycle_level<double>(cc, 0, &out, s));
+        AMG_CUDA_TRY(vcycle_level<double>(cc, 0, &out, s, c.nlev > 1 ? z : nullptr));
+        if (out == z) return cudaSuccess;
         return cudaMemcpyAsync(z, out, sizeof(double) * (size_t)l0.n, cudaMemcpyDeviceToDevice, s);
     }
     d2t_kernel<float><<<grid_for(l0.n, 256, 8192), 256, 0, s>>>(l0.n, r, (float *)l0.f); note_launch();

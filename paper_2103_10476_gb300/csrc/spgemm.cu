@@ -106,6 +106,38 @@ __global__ void gather_tsize_kernel(int cnt, const int *rows, const int *tsize, 
 }
 
 // ------------------------------------------------------------------------------------ symbolic
+// The products of row i, a_ik b_kj for k ascending and j ascending within B's row k, are
+// enumerated 32 at a time: lane l of a batch holds product number base + l.  For a chunk of
+// up to 32 entries of A's row, each lane holds one entry and the running (inclusive) count
+// of B-row lengths; a product's entry is found by binary search over those counts.
+struct ProductBatch {
+    int j;          // column of the product (valid lanes)
+    double prod;    // a_ik * b_kj, rounded
+    bool valid;
+};
+
+template <bool WITH_VALUES>
+__device__ __forceinline__ ProductBatch product_at(int q, int total, int incl, int excl, int fb, double a,
+                                                   const int *bci, const double *bv)
+{
+    ProductBatch pb;
+    pb.valid = q < total;
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int step = 0; step < 5; ++step) {
+        int mid = (lo + hi) >> 1;
+        int v = __shfl_sync(kFullMask, incl, mid);
+        if (v > q) hi = mid; else lo = mid + 1;
+    }
+    const int owner = lo;
+    const int off = q - __shfl_sync(kFullMask, excl, owner);
+    const int f = __shfl_sync(kFullMask, fb, owner) + off;
+    const double ao = WITH_VALUES ? __shfl_sync(kFullMask, a, owner) : 0.0;
+    pb.j = pb.valid ? bci[f] : -1;
+    pb.prod = (WITH_VALUES && pb.valid) ? ao * bv[f] : 0.0;
+    return pb;
+}
+
 __device__ void symbolic_row(int i, const int *arp, const int *aci, const int *brp, const int *bci, int *keys, int S,
                              int *ccnt, int *overflow)
 {
@@ -113,12 +145,30 @@ __device__ void symbolic_row(int i, const int *arp, const int *aci, const int *b
     for (int t = lane; t < S; t += 32) keys[t] = -1;
     __syncwarp();
     int mine = 0;
-    for (int e = arp[i]; e < arp[i + 1]; ++e) {
-        int k = aci[e];
-        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
-            bool fresh;
-            hash_insert(keys, S, bci[f], fresh, overflow);
-            mine += fresh;
+    const int ae = arp[i + 1];
+    for (int eb = arp[i]; eb < ae; eb += 32) {
+        const int e = eb + lane;
+        int len = 0, fb = 0;
+        if (e < ae) {
+            const int k = aci[e];
+            fb = brp[k];
+            len = brp[k + 1] - fb;
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFullMask, incl, 31);
+        const int excl = incl - len;
+        for (int qb = 0; qb < total; qb += 32) {
+            ProductBatch pb = product_at<false>(qb + lane, total, incl, excl, fb, 0.0, bci, nullptr);
+            if (pb.valid) {
+                bool fresh;
+                hash_insert(keys, S, pb.j, fresh, overflow);
+                mine += fresh;
+            }
         }
     }
 #pragma unroll
@@ -156,15 +206,43 @@ __device__ void numeric_row(int i, const int *arp, const int *aci, const double 
     const int lane = threadIdx.x & 31;
     for (int t = lane; t < S; t += 32) { keys[t] = -1; vals[t] = 0.0; }
     __syncwarp();
-    for (int e = arp[i]; e < arp[i + 1]; ++e) {
-        const int k = aci[e];
-        const double a = av[e];
-        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) {
-            bool fresh;
-            int slot = hash_insert(keys, S, bci[f], fresh, overflow);
-            if (slot >= 0) vals[slot] = vals[slot] + a * bv[f];
+    const unsigned lt = (1u << lane) - 1u;
+    const int ae = arp[i + 1];
+    for (int eb = arp[i]; eb < ae; eb += 32) {
+        const int e = eb + lane;
+        int len = 0, fb = 0;
+        double a = 0.0;
+        if (e < ae) {
+            const int k = aci[e];
+            a = av[e];
+            fb = brp[k];
+            len = brp[k + 1] - fb;
         }
-        __syncwarp();
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFullMask, incl, 31);
+        const int excl = incl - len;
+        for (int qb = 0; qb < total; qb += 32) {
+            ProductBatch pb = product_at<true>(qb + lane, total, incl, excl, fb, a, bci, bv);
+            int slot = -1;
+            if (pb.valid) {
+                bool fresh;
+                slot = hash_insert(keys, S, pb.j, fresh, overflow);
+            }
+            // products of one column inside the batch are added in lane (= product) order
+            const bool act = pb.valid && slot >= 0;
+            const unsigned same = __match_any_sync(kFullMask, act ? slot : -1 - lane);
+            const unsigned rank = act ? (unsigned)__popc(same & lt) : 0u;
+            const unsigned maxrank = __reduce_max_sync(kFullMask, rank);
+            for (unsigned r = 0; r <= maxrank; ++r) {
+                if (act && rank == r) vals[slot] = vals[slot] + pb.prod;
+                __syncwarp();
+            }
+        }
     }
     // compact occupied slots to the front, in slot order
     int base = 0;
@@ -366,7 +444,7 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     C.n = A.n;
     C.ncol = B.ncol;
     const int n = A.n;
-    AMG_CUDA_TRY(cudaMalloc(&C.rp, sizeof(int) * ((size_t)n + 17)));
+    AMG_CUDA_TRY(cudaMallocAsync(&C.rp, sizeof(int) * ((size_t)n + 17), s));
     if (n == 0) {
         AMG_CUDA_TRY(cudaMemsetAsync(C.rp, 0, sizeof(int), s));
         return cudaSuccess;
@@ -410,8 +488,8 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if (*overflow_host || nnz < 0) { e = cudaErrorInvalidValue; break; }
         C.nnz = nnz;
         // 16 elements of padding: bulk copies of row ranges widen to 16-byte boundaries
-        if ((e = cudaMalloc(&C.ci, sizeof(int) * ((size_t)nnz + 16)))) break;
-        if ((e = cudaMalloc(&C.v, sizeof(double) * ((size_t)nnz + 16)))) break;
+        if ((e = cudaMallocAsync(&C.ci, sizeof(int) * ((size_t)nnz + 16), s))) break;
+        if ((e = cudaMallocAsync(&C.v, sizeof(double) * ((size_t)nnz + 16), s))) break;
         // numeric, binned by the exact row counts
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
@@ -440,7 +518,10 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     cudaFreeAsync(work, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
-        cudaFree(C.rp); cudaFree(C.ci); cudaFree(C.v);
+        if (C.rp) cudaFreeAsync(C.rp, s);
+        if (C.ci) cudaFreeAsync(C.ci, s);
+        if (C.v) cudaFreeAsync(C.v, s);
+        cudaStreamSynchronize(s);
         C.rp = nullptr; C.ci = nullptr; C.v = nullptr; C.nnz = 0;
     }
     return e;
