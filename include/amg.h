@@ -12,8 +12,9 @@
  *     filtered matrix (Eq. 6) and the strength test |a_ij| >= theta sqrt(a_ii a_jj) (Eq. 7);
  *   - the four adaptations, each switchable: 1Norm (§2.1-§2.2, Eq. 9-11), OffLmp (§2.3,
  *     Algorithm 2), Cnstrnt (§2.4, Algorithm 3) and Sprsfy (§2.5);
- *   - Chebyshev smoothing on [lambda/10, lambda] with lambda from ten power-method sweeps,
- *     and a direct solve on the coarsest level (§3.1).
+ *   - Chebyshev smoothing on [b lambda/10, b lambda] with lambda from ten power-method sweeps
+ *     (b = 1.1 by default: ten sweeps underestimate lambda_max), and a direct solve on the
+ *     coarsest level (§3.1).
  *
  * Every step runs in this library's CUDA kernels on the current device.  All functions
  * return an amg_status_t; no C++ exception crosses the ABI.  A handle is not thread-safe:
@@ -73,7 +74,8 @@ typedef struct {
     double tau;          /* OffLmp growth factor (1.1)                                       */
     double sigma;        /* 1Norm safeguard minimum root value (1/3)                         */
     int cheb_degree;     /* Chebyshev degree (2)                                             */
-    double cheb_ratio;   /* Chebyshev interval [lambda/ratio, lambda] (10)                   */
+    double cheb_ratio;   /* Chebyshev interval [b lambda/ratio, b lambda] (10)               */
+    double cheb_boost;   /* b: safety factor on the power-method estimate of lambda_max (1.1) */
     int power_iters;     /* power-method sweeps (10)                                         */
     int max_coarse;      /* stop coarsening at or below this size (500)                      */
     int max_levels;      /* (10)                                                             */

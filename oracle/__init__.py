@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     _fields_ = [("theta", C.c_double), ("variants", C.c_uint), ("tau", C.c_double), ("sigma", C.c_double),
-                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("power_iters", C.c_int),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
+                ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("pt_unit", C.c_int),
                 ("onenorm_power", C.c_int), ("seed", C.c_uint64), ("lambda_override", C.c_double),
                 ("max_iter", C.c_int)]

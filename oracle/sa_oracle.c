@@ -60,6 +60,7 @@ void oc_params_default(oc_params *p)
     p->sigma = 1.0 / 3.0;
     p->cheb_degree = 2;
     p->cheb_ratio = 10.0;
+    p->cheb_boost = 1.1;
     p->power_iters = 10;
     p->max_coarse = 500;
     p->max_levels = 10;
@@ -918,18 +919,21 @@ int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, c
 /* Solve: Chebyshev smoother, V-cycle (Algorithm 1) and preconditioned CG                    */
 /* ---------------------------------------------------------------------------------------- */
 
-/* Chebyshev polynomial of degree m in D^-1 A on [lambda/ratio, lambda], applied to
+/* Chebyshev polynomial of degree m in D^-1 A on [b lambda/ratio, b lambda], applied to
  * A x = f from the current x (three-term recurrence of Chebyshev acceleration as in
  * Saad, Iterative Methods for Sparse Linear Systems, 2nd ed., Algorithm 12.1):
  *   theta = (a+b)/2, delta = (b-a)/2, sigma1 = theta/delta, rho = 1/sigma1,
  *   d = D^-1 (f - A x) / theta, x += d;
  *   repeat m-1 times: rho' = 1/(2 sigma1 - rho), d = rho' rho d + (2 rho'/delta) D^-1 (f - A x),
  *                     x += d, rho = rho'. */
-static void chebyshev(const struct oc_level *lv, int degree, double ratio, const double *f, double *x,
+static void chebyshev(const struct oc_level *lv, int degree, double ratio, double boost, const double *f, double *x,
                       double *r, double *d)
 {
     int64_t n = lv->A.n;
-    double lmax = lv->lambda_cheb, lmin = lv->lambda_cheb / ratio;
+    /* Reading: ten power sweeps give a lower estimate of lambda_max(D^-1 A); the interval's
+     * upper end is the estimate times a safety factor b (1.1), so that the polynomial does not
+     * amplify the top of the spectrum (b = 1 is the estimate itself). */
+    double lmax = boost * lv->lambda_cheb, lmin = lmax / ratio;
     double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
     double sigma1 = theta / delta, rho = 1.0 / sigma1;
     spmv(n, lv->A.rp, lv->A.ci, lv->A.v, x, r);
@@ -963,14 +967,14 @@ static void vcycle_level(oc_hier *h, int L, const double *f, double *u)
     int64_t nc = lv->nagg;
     double *fc = (double *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(double));
     double *uc = (double *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
-    chebyshev(lv, h->p.cheb_degree, h->p.cheb_ratio, f, u, r, d);
+    chebyshev(lv, h->p.cheb_degree, h->p.cheb_ratio, h->p.cheb_boost, f, u, r, d);
     spmv(n, lv->A.rp, lv->A.ci, lv->A.v, u, r);
     for (int64_t i = 0; i < n; ++i) r[i] = f[i] - r[i];
     spmv(nc, lv->R.rp, lv->R.ci, lv->R.v, r, fc);
     vcycle_level(h, L + 1, fc, uc);
     spmv(n, lv->P.rp, lv->P.ci, lv->P.v, uc, r);
     for (int64_t i = 0; i < n; ++i) u[i] = u[i] + r[i];
-    chebyshev(lv, h->p.cheb_degree, h->p.cheb_ratio, f, u, r, d);
+    chebyshev(lv, h->p.cheb_degree, h->p.cheb_ratio, h->p.cheb_boost, f, u, r, d);
     free(r); free(d); free(fc); free(uc);
 }
 

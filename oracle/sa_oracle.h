@@ -44,7 +44,8 @@ typedef struct {
     double tau;            /* OffLmp growth factor (1.1 in §3.1) */
     double sigma;          /* 1Norm safeguard minimum root value (1/3 in §2.2) */
     int cheb_degree;       /* Chebyshev polynomial degree */
-    double cheb_ratio;     /* interval [lambda/ratio, lambda] */
+    double cheb_ratio;     /* interval [b lambda/ratio, b lambda] */
+    double cheb_boost;     /* b: safety factor on the power-method estimate (1.1) */
     int power_iters;       /* power-method sweeps (10 in §3.1) */
     int max_coarse;        /* coarsest level size */
     int max_levels;

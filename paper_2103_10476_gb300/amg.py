@@ -43,7 +43,8 @@ class amg_csr_t(C.Structure):
 
 class amg_params_t(C.Structure):
     _fields_ = [("theta", C.c_double), ("variants", C.c_uint), ("tau", C.c_double), ("sigma", C.c_double),
-                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("power_iters", C.c_int),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
+                ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p)]

@@ -161,6 +161,7 @@ struct SolveCtx {
     double *coarse_tmp_in = nullptr, *coarse_tmp_out = nullptr;
     int cheb_degree = 2;
     double cheb_ratio = 10.0;
+    double cheb_boost = 1.1;
     int mixed = 0;
 };
 // z = V-cycle(r) from z = 0 on the finest level (r, z double on the device).
@@ -182,6 +183,8 @@ cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const do
 cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, const double *rz_partial, int count,
                          cudaStream_t s);
 cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s);
+cudaError_t pcg_update_p_flexible(int n, double *p, const double *r, const double *z, const double *z_prev,
+                                  PcgScalars *sc, double *pa, double *pb, cudaStream_t s);
 int pick_lanes(double avg_row);
 
 }  // namespace amgk

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -50,6 +51,7 @@ struct amg_hierarchy {
     double *coarse_inv = nullptr;
     // solve workspace (FP64, finest level)
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
+    double *z_prev = nullptr;   // previous preconditioned residual (flexible update, mixed precision)
     double *partial = nullptr, *partial2 = nullptr;
     double *rr_host = nullptr;   // pinned copy of the r . r partial sums
     PcgScalars *sc = nullptr;
@@ -355,6 +357,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
     c.nlev = h->nlev;
     c.cheb_degree = h->p.cheb_degree;
     c.cheb_ratio = h->p.cheb_ratio;
+    c.cheb_boost = h->p.cheb_boost;
     c.mixed = mixed ? 1 : 0;
     for (int L = 0; L < h->nlev; ++L) {
         Level &lv = h->lev[L];
@@ -406,6 +409,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
     CK(dalloc(h, &h->pv, (size_t)n0));
     CK(dalloc(h, &h->q, (size_t)n0));
     CK(dalloc(h, &h->t, (size_t)n0));
+    if (mixed) CK(dalloc(h, &h->z_prev, (size_t)n0));
     {
         int np = spmv_partials_needed(n0);
         CK(dalloc(h, &h->partial, (size_t)(np > kReduceBlocks ? np : kReduceBlocks)));
@@ -433,6 +437,7 @@ void amg_params_default(amg_params_t *p)
     p->sigma = 1.0 / 3.0;
     p->cheb_degree = 2;
     p->cheb_ratio = 10.0;
+    p->cheb_boost = 1.1;
     p->power_iters = 10;
     p->max_coarse = 500;
     p->max_levels = 10;
@@ -503,7 +508,8 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         return AMG_ERR_UNSUPPORTED;
     }
     const amg_params_t &p = *pin;
-    if (!(p.theta >= 0.0 && p.theta <= 1.0) || p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || p.power_iters < 1 ||
+    if (!(p.theta >= 0.0 && p.theta <= 1.0) || p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0) ||
+        p.power_iters < 1 ||
         p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0)) {
         g_last_error = "parameter out of range";
         return AMG_ERR_INVALID_ARG;
@@ -689,9 +695,16 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
             if (std::sqrt(tt) / nb <= tol) { result = AMG_OK; break; }
             CK(cudaMemcpyAsync(h->r, h->t, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
         }
-        CK(vcycle(h->ctx, h->r, h->z, s));
-        CK(dot_partial(h->r, h->z, n, h->partial, s));
-        CK(pcg_update_p(n, h->pv, h->z, h->sc, h->partial, kReduceBlocks, s));
+        if (h->z_prev) {
+            // mixed precision: flexible update against the previous preconditioned residual
+            std::swap(h->z, h->z_prev);
+            CK(vcycle(h->ctx, h->r, h->z, s));
+            CK(pcg_update_p_flexible(n, h->pv, h->r, h->z, h->z_prev, h->sc, h->partial, h->partial2, s));
+        } else {
+            CK(vcycle(h->ctx, h->r, h->z, s));
+            CK(dot_partial(h->r, h->z, n, h->partial, s));
+            CK(pcg_update_p(n, h->pv, h->z, h->sc, h->partial, kReduceBlocks, s));
+        }
     }
 finish:
     if (n > 0) {

@@ -337,6 +337,44 @@ cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, cons
     return cudaGetLastError();
 }
 
+// Flexible (Polak-Ribiere) update for the mixed-precision preconditioner, whose FP32
+// rounding makes it symmetric only approximately: beta = (r'.z' - r'.z_prev) / (r.z).  In
+// exact arithmetic r'.z_prev = 0 and this is the update above.
+__global__ void __launch_bounds__(kReduceThreads) pcg_p_flex_kernel(int n, double *p, const double *z,
+                                                                    PcgScalars *sc, const double *rz_partial,
+                                                                    const double *rzp_partial, int count)
+{
+    const double rz_new = sum_partials_all(rz_partial, count);
+    const double rz_cross = sum_partials_all(rzp_partial, count);
+    const double beta = (rz_new - rz_cross) / sc->rz;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
+        p[i] = z[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
+}
+
+// partial sums of r . z and r . z_prev in one pass
+__global__ void __launch_bounds__(kReduceThreads) dot2_kernel(int n, const double *r, const double *z,
+                                                              const double *zp, double *pa, double *pb)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
+        const double ri = r[i];
+        a += ri * z[i];
+        b += ri * zp[i];
+    }
+    const double ta = block_sum_all(a);
+    const double tb = block_sum_all(b);
+    if (threadIdx.x == 0) { pa[blockIdx.x] = ta; pb[blockIdx.x] = tb; }
+}
+
+cudaError_t pcg_update_p_flexible(int n, double *p, const double *r, const double *z, const double *z_prev,
+                                  PcgScalars *sc, double *pa, double *pb, cudaStream_t s)
+{
+    dot2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, r, z, z_prev, pa, pb); note_launch();
+    pcg_p_flex_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, z, sc, pa, pb, kReduceBlocks); note_launch();
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ double sum_partials(const double *partial, int count)
 {
     return sum_partials_all(partial, count);
@@ -406,9 +444,10 @@ double spmv_bytes(const LevelView &lv, int vecs)
     return (double)(sizeof(T) + 4) * (double)lv.nnz_a + 4.0 * (lv.n + 1) + (double)vecs * sizeof(T) * lv.n;
 }
 
-ChebCoef cheb_coef(double lambda, double ratio)
+ChebCoef cheb_coef(double lambda, double ratio, double boost)
 {
-    double lmax = lambda, lmin = lambda / ratio;
+    // interval [b lambda / ratio, b lambda]: b lifts the power-method estimate (a lower bound)
+    double lmax = boost * lambda, lmin = lmax / ratio;
     ChebCoef c;
     c.theta = 0.5 * (lmax + lmin);
     c.delta = 0.5 * (lmax - lmin);
@@ -423,7 +462,7 @@ cudaError_t chebyshev(const SolveCtx &c, int L, T *&x, T *&x2, bool x_is_zero, c
                       T *final_out = nullptr)
 {
     const LevelView &lv = c.lev[L];
-    const ChebCoef cc = cheb_coef(lv.lambda, c.cheb_ratio);
+    const ChebCoef cc = cheb_coef(lv.lambda, c.cheb_ratio, c.cheb_boost);
     double rho = 1.0 / cc.sigma1;
     const T *f = (const T *)lv.f;
     const T *inv = (const T *)lv.invdiag;

@@ -229,6 +229,24 @@ def test_not_converged_returns_last_iterate(amg):
     amg.amg_free(h)
 
 
+@pytest.mark.parametrize("variants", [0, 1, 2, 4, 8])
+def test_mixed_precision_iterations_track_fp64(amg, oracle_lib, variants):
+    # FP32 hierarchy and V-cycle inside FP64 flexible PCG: same 1e-8 true residual, iteration
+    # count within one of the FP64 oracle's, solution within the accuracy the stop guarantees
+    A = P.stretched_box(28, 1.1)
+    b = P.rhs_uniform(A.n, 1)
+    h, st = gpu_setup(A, theta=0.02, variants=variants, max_coarse=60, precision=1)
+    oh, ost = oracle_lib.setup(A, theta=0.02, variants=variants, max_coarse=60)
+    assert st == 0 and ost == 0
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, 1e-8)
+    xo, oinfo, _ = oh.solve(b, 1e-8)
+    amg.amg_free(h)
+    assert info.status == 0 and info.relres_true <= 1e-8
+    assert abs(info.iters - oinfo.iters) <= 1, (info.iters, oinfo.iters)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) < 1e-6
+
+
 def test_mixed_precision_meets_tolerance(amg, oracle_lib):
     A = P.random_coefficient_cube(16, 2)
     b = P.rhs_uniform(A.n, 2)
