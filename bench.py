@@ -297,6 +297,7 @@ def main():
     ap.add_argument("--workload", default="stretched64", choices=sorted(VARIANT_SETS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision line beside the FP64 one")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--once", action="store_true",
                     help="one setup + solve (or --vcycles V-cycles) of one method, for profiler captures")
@@ -330,55 +331,75 @@ def main():
     arg_d = amg.csr_arg(A.n, rp_d, ci_d, v_d)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    per_solve_ms = []
-    iters = {}
-    statuses = {}
+    def timed(params_list, steps, warmup, profile):
+        """Warm-up, then `steps` timed steps (per-step CUDA events on the launching stream,
+        L2 flushed before each step outside the events).  Returns the step times and details."""
+        per_solve, iters, statuses = [], {}, {}
 
-    def step(record=False):
-        for (name, _), p in zip(variants, params):
-            t0 = time.perf_counter()
-            h, st = amg.amg_setup_status(arg_d, None, p)
-            if h is None:
-                statuses[name] = amg.amg_status_string(st)
-                continue
-            info = amg.amg_solve(h, b_d, x_d, TOL)
-            amg.amg_free(h)
-            if record:
-                per_solve_ms.append(1000 * (time.perf_counter() - t0))
-                iters[name] = info.iters
-                statuses[name] = amg.amg_status_string(info.status)
+        def step(record):
+            for (name, _), p in zip(variants, params_list):
+                t0 = time.perf_counter()
+                h, st = amg.amg_setup_status(arg_d, None, p)
+                if h is None:
+                    statuses[name] = amg.amg_status_string(st)
+                    continue
+                info = amg.amg_solve(h, b_d, x_d, TOL)
+                amg.amg_free(h)
+                if record:
+                    per_solve.append(1000 * (time.perf_counter() - t0))
+                    iters[name] = info.iters
+                    statuses[name] = amg.amg_status_string(info.status)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    launches0 = amg.amg_launch_count()
-    amg.amg_profile_enable(True)
-    barrier(world)
-    torch.cuda.synchronize()
-    t_wall = time.perf_counter()
-    with ClockSampler(local) as clk:
-        for k in range(args.steps):
+        for _ in range(warmup):
+            step(False)
+        torch.cuda.synchronize()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        launches0 = amg.amg_launch_count()
+        if profile:
+            amg.amg_profile_enable(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(steps):
             flush.zero_()
             ev0[k].record(stream)
-            step(record=True)
+            step(True)
             ev1[k].record(stream)
         torch.cuda.synchronize()
-    barrier(world)
+        barrier(world)
+        launches = amg.amg_launch_count() - launches0
+        prof = None
+        if profile:
+            prof = {kc: amg.amg_profile_read(kc) for kc in (amg.KC_PCG_SPMV, amg.KC_VCYCLE_SPMV, amg.KC_SPGEMM)}
+            amg.amg_profile_enable(False)
+        step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
+        return step_ms, per_solve, iters, statuses, launches, prof
+
+    t_wall = time.perf_counter()
+    with ClockSampler(local) as clk:
+        step_ms, per_solve_ms, iters, statuses, launches, prof = timed(params, args.steps, args.warmup, True)
     t_wall = time.perf_counter() - t_wall
-    launches = amg.amg_launch_count() - launches0
-    prof = {k: amg.amg_profile_read(k) for k in (amg.KC_PCG_SPMV, amg.KC_VCYCLE_SPMV, amg.KC_SPGEMM)}
-    amg.amg_profile_enable(False)
-    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(args.steps)]
     total_ms = max_over_ranks(world, sum(step_ms))
     solves_per_step = len(variants)
     value = solves_per_step * args.steps * world / (total_ms / 1000.0)
 
+    # the other precision, same workload and timing rules (reported beside the headline)
+    other = None
+    if args.precision == "fp64" and not args.no_mixed:
+        mparams = [amg.amg_params_default(theta=theta, variants=v, precision=amg.AMG_MIXED,
+                                          cuda_stream=stream.cuda_stream) for _, v in variants]
+        msteps = max(2, args.steps // 2)
+        m_ms, m_solve, m_iters, m_status, _, _ = timed(mparams, msteps, 1, False)
+        m_total = max_over_ranks(world, sum(m_ms))
+        mlat = sorted(m_solve)
+        other = {"precision": "mixed (FP32 hierarchy values and V-cycle, FP64 flexible PCG)",
+                 "value": solves_per_step * msteps * world / (m_total / 1000.0), "unit": "solves/s",
+                 "ms_per_step": m_total / msteps, "steps": msteps, "iters": m_iters, "status": m_status,
+                 "p50_ms": mlat[len(mlat) // 2] if mlat else None,
+                 "p99_ms": mlat[min(len(mlat) - 1, int(0.99 * len(mlat)))] if mlat else None}
+
     # end to end through the C ABI with host buffers (host -> device copy of the matrix and the
     # right-hand side inside every step, device -> host copy of the solution)
-    arg_h = amg.csr_arg(A.n, A.row_ptr, A.col, A.val)
     b_h = torch.from_numpy(b).pin_memory()
     x_h = torch.zeros(A.n, dtype=torch.float64).pin_memory()
     rp_h = torch.from_numpy(A.row_ptr).pin_memory()
@@ -439,6 +460,7 @@ def main():
         "p50_ms": lat[len(lat) // 2] if lat else None,
         "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
         "iters": iters, "status": statuses, "wall_s": t_wall,
+        "mixed": other,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -541,8 +541,9 @@ int oc_constrain_row(int64_t m, double *p, int64_t ptent_pos, double ptent_val)
 /* ---------------------------------------------------------------------------------------- */
 
 /* C = A B by rows (Gustavson): for each i, for k ascending in row i of A, for j in row k of B,
- * acc[j] += a_ik b_kj.  Every reachable (i, j) is stored, whatever its value; columns are
- * sorted.  Each c_ij is therefore summed in ascending k starting from 0. */
+ * acc[j] = fma(a_ik, b_kj, acc[j]) (one rounding per term).  Every reachable (i, j) is stored,
+ * whatever its value; columns are sorted.  Each c_ij is therefore accumulated in ascending k
+ * starting from 0. */
 int oc_spgemm(const oc_csr *A, const oc_csr *B, int64_t ncolB, oc_csr **out)
 {
     int64_t n = A->n;
@@ -578,7 +579,7 @@ int oc_spgemm(const oc_csr *A, const oc_csr *B, int64_t ncolB, oc_csr **out)
             for (int64_t f = B->rp[k]; f < B->rp[k + 1]; ++f) {
                 int64_t j = B->ci[f];
                 if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols[cnt++] = (int32_t)j; }
-                acc[j] = acc[j] + a * B->v[f];
+                acc[j] = fma(a, B->v[f], acc[j]);
             }
         }
         qsort(cols, (size_t)cnt, sizeof(int32_t), cmp_i32);

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "amg.h"
 
@@ -17,10 +18,23 @@ namespace amgk {
 // Kernel-launch counter (every launch site calls note_launch) and per-class kernel timing
 // with CUDA events for roofline reports.
 void note_launch();
+void note_launches(long long k);
 long long launch_count();
 enum KernelClass { KC_PCG_SPMV = 0, KC_VCYCLE_SPMV = 1, KC_SPGEMM = 2, KC_SETUP_SPMV = 3, KC_COUNT = 4 };
 bool profiling_enabled();
 void profile_enable(bool on);
+struct ProfRecord {
+    int cls;
+    cudaEvent_t start, stop;
+    double bytes;
+};
+using ProfList = std::vector<ProfRecord>;
+// timing scopes opened while a graph body is captured go to `list` (their events become
+// graph nodes); profile_account adds their elapsed times after each launch of the graph
+void profile_capture_begin(ProfList *list);
+void profile_capture_end();
+void profile_account(const ProfList &list);
+void profile_release(ProfList &list);
 void profile_read(int cls, long long *launches, double *ms, double *bytes);
 struct ProfScope {
     ProfScope(int cls, cudaStream_t s, double bytes);
@@ -169,22 +183,23 @@ cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s
 
 // PCG building blocks (FP64, deterministic reductions; scalars live on the device)
 struct PcgScalars {     // device
-    double rz, rz_next, pq, alpha, beta, rr, bb, tmp;
+    double rz, rz_next, rz_new, rz_cross, pq, alpha, beta, rr, bb, tmp;
 };
-cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial, int *nparts,
-                     cudaStream_t s);
+cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial,
+                     double *result, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
-                            double *partial, int *nparts, cudaStream_t s);
+                            double *partial, double *result, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
 cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
                        cudaStream_t s);
 cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const double *q, PcgScalars *sc,
                           const double *pq_partial, int pq_count, double *rr_partial, cudaStream_t s);
-cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, const double *rz_partial, int count,
-                         cudaStream_t s);
+int spmv_block_count(int n, const SpmvPlan &pl);
+// r . z (and r . z_prev when z_prev is not null: flexible update) then p = z + beta p
+cudaError_t pcg_update_p(int n, double *p, const double *r, const double *z, const double *z_prev, PcgScalars *sc,
+                         double *pa, double *pb, unsigned *counters, cudaStream_t s);
 cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_t s);
-cudaError_t pcg_update_p_flexible(int n, double *p, const double *r, const double *z, const double *z_prev,
-                                  PcgScalars *sc, double *pa, double *pb, cudaStream_t s);
+
 int pick_lanes(double avg_row);
 
 }  // namespace amgk

@@ -52,9 +52,19 @@ struct amg_hierarchy {
     // solve workspace (FP64, finest level)
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
     double *z_prev = nullptr;   // previous preconditioned residual (flexible update, mixed precision)
-    double *partial = nullptr, *partial2 = nullptr;
+    double *zb[2] = {nullptr, nullptr};   // the two z buffers (their roles alternate in mixed mode)
+    // one PCG iteration (V-cycle, p update, q = A p, x and r update, copy of the r.r partial
+    // sums to the host) as a CUDA graph; two graphs in mixed mode (z buffers alternate)
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    ProfList gprof[2];
+    int gprof_on[2] = {-1, -1};
+    long long gkernels[2] = {0, 0};   // kernels in each graph (added to the launch count per replay)
+    bool graph_failed = false;
+    double *partial = nullptr, *partial2 = nullptr, *partial3 = nullptr;
     double *rr_host = nullptr;   // pinned copy of the r . r partial sums
     PcgScalars *sc = nullptr;
+    unsigned *counters = nullptr;   // ticket counters of the fixed-order reductions (zero between uses)
     SpmvPlan plan0;   // finest-level FP64 operator (PCG)
     SolveCtx ctx;
     double setup_ms = 0.0;
@@ -409,17 +419,89 @@ amg_status_t prepare_solve(amg_hierarchy *h)
     CK(dalloc(h, &h->pv, (size_t)n0));
     CK(dalloc(h, &h->q, (size_t)n0));
     CK(dalloc(h, &h->t, (size_t)n0));
-    if (mixed) CK(dalloc(h, &h->z_prev, (size_t)n0));
+    h->zb[0] = h->z;
+    if (mixed) {
+        CK(dalloc(h, &h->z_prev, (size_t)n0));
+        h->zb[1] = h->z_prev;
+    }
+    CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
     {
         int np = spmv_partials_needed(n0);
         CK(dalloc(h, &h->partial, (size_t)(np > kReduceBlocks ? np : kReduceBlocks)));
         CK(dalloc(h, &h->partial2, (size_t)kReduceBlocks));
+        CK(dalloc(h, &h->partial3, (size_t)kReduceBlocks));
         CK(cudaMallocHost(&h->rr_host, sizeof(double) * kReduceBlocks));
         if (n0 > 0) CK(spmv_plan(h->lev[0].A.rp, n0, h->lev[0].A.nnz, &h->plan0, s));
     }
     CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
+    CK(dalloc(h, &h->counters, 8));
+    CK(cudaMemsetAsync(h->counters, 0, sizeof(unsigned) * 8, s));
 done:
     return st;
+}
+
+// ----------------------------------------------------------------------- PCG iteration pieces
+// tail: z = M^-1 r (V-cycle), then p = z + beta p;  head: q = A p with p.q, alpha, x and r
+// update, r.r partial sums copied to the host.  Parity selects the z buffer in mixed mode.
+cudaError_t pcg_tail(amg_hierarchy *h, int parity, cudaStream_t s)
+{
+    const int n = h->lev[0].A.n;
+    double *z = h->zb[h->zb[1] ? parity : 0];
+    double *zp = h->zb[1] ? h->zb[1 - parity] : nullptr;
+    AMG_CUDA_TRY(vcycle(h->ctx, h->r, z, s));
+    return pcg_update_p(n, h->pv, h->r, z, zp, h->sc, h->partial, h->partial3, h->counters, s);
+}
+
+cudaError_t pcg_head(amg_hierarchy *h, cudaStream_t s)
+{
+    const DevCsr &A = h->lev[0].A;
+    const int n = A.n;
+    {
+        ProfScope ps(KC_PCG_SPMV, s, 12.0 * (double)A.nnz + 20.0 * n + 4.0);
+        AMG_CUDA_TRY(spmv_dot(A, h->plan0, h->pv, h->q, h->partial, nullptr, nullptr, s));
+    }
+    AMG_CUDA_TRY(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, spmv_block_count(n, h->plan0),
+                               h->partial2, s));
+    return cudaMemcpyAsync(h->rr_host, h->partial2, sizeof(double) * kReduceBlocks, cudaMemcpyDeviceToHost, s);
+}
+
+// the graph of tail(parity) + head, captured on first use (and again when kernel timing is
+// switched on or off, so that its timing events are in the graph exactly when wanted)
+cudaGraphExec_t pcg_graph(amg_hierarchy *h, int parity)
+{
+    if (h->graph_failed) return nullptr;
+    const int want = profiling_enabled() ? 1 : 0;
+    if (h->gexec[parity] && h->gprof_on[parity] == want) return h->gexec[parity];
+    if (h->gexec[parity]) {
+        cudaGraphExecDestroy(h->gexec[parity]);
+        h->gexec[parity] = nullptr;
+        profile_release(h->gprof[parity]);
+    }
+    cudaGraph_t g = nullptr;
+    const long long launches_before = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (want) profile_capture_begin(&h->gprof[parity]);
+        cudaError_t e1 = pcg_tail(h, parity, h->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? pcg_head(h, h->cap) : e1;
+        profile_capture_end();
+        e = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->graph_failed = true;     // this handle runs the iterations eagerly from now on
+        h->gexec[parity] = nullptr;
+        profile_release(h->gprof[parity]);
+        return nullptr;
+    }
+    h->gprof_on[parity] = want;
+    // the capture itself launched nothing; its kernels run at every replay
+    h->gkernels[parity] = launch_count() - launches_before;
+    note_launches(-h->gkernels[parity]);
+    return h->gexec[parity];
 }
 
 }  // namespace
@@ -490,6 +572,11 @@ amg_status_t amg_profile_read(int kclass, int64_t *launches, double *total_ms, d
 amg_status_t amg_free(amg_handle_t h)
 {
     if (!h) return AMG_OK;
+    for (int k = 0; k < 2; ++k) {
+        if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+        profile_release(h->gprof[k]);
+    }
+    if (h->cap) cudaStreamDestroy(h->cap);
     release_all(h);
     if (h->rr_host) cudaFreeHost(h->rr_host);
     delete h;
@@ -658,7 +745,6 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     cudaStream_t s = h->s;
     const DevCsr &A = h->lev[0].A;
     const SpmvPlan &plan = h->plan0;
-    int nparts = 0;
     int it = 0;
     double bb = 0.0, rr = 0.0, relres = 0.0, nb = 0.0;
     amg_status_t result = AMG_OK;
@@ -671,18 +757,15 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     CK(cudaStreamSynchronize(s));
     nb = std::sqrt(bb);
     if (nb == 0.0) goto finish;
-    CK(vcycle(h->ctx, h->r, h->z, s));
-    CK(cudaMemcpyAsync(h->pv, h->z, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    CK(dot(h->r, h->z, n, h->partial, &h->sc->rz_next, s));
+    CK(vcycle(h->ctx, h->r, h->zb[0], s));
+    CK(cudaMemcpyAsync(h->pv, h->zb[0], sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    CK(dot(h->r, h->zb[0], n, h->partial, &h->sc->rz_next, s));
     result = AMG_ERR_NOT_CONVERGED;
-    while (it < h->p.max_iter) {
-        {
-            ProfScope ps(KC_PCG_SPMV, s, 12.0 * (double)A.nnz + 20.0 * n + 4.0);
-            CK(spmv_dot(A, plan, h->pv, h->q, h->partial, &nparts, s));
-        }
-        CK(pcg_update_xr(n, h->x, h->r, h->pv, h->q, h->sc, h->partial, nparts, h->partial2, s));
+    if (h->p.max_iter > 0) {
+        CK(pcg_head(h, s));
         ++it;
-        CK(cudaMemcpyAsync(h->rr_host, h->partial2, sizeof(double) * kReduceBlocks, cudaMemcpyDeviceToHost, s));
+    }
+    while (it > 0) {
         CK(cudaStreamSynchronize(s));
         rr = 0.0;
         for (int k = 0; k < kReduceBlocks; ++k) rr += h->rr_host[k];
@@ -695,16 +778,20 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
             if (std::sqrt(tt) / nb <= tol) { result = AMG_OK; break; }
             CK(cudaMemcpyAsync(h->r, h->t, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
         }
-        if (h->z_prev) {
-            // mixed precision: flexible update against the previous preconditioned residual
-            std::swap(h->z, h->z_prev);
-            CK(vcycle(h->ctx, h->r, h->z, s));
-            CK(pcg_update_p_flexible(n, h->pv, h->r, h->z, h->z_prev, h->sc, h->partial, h->partial2, s));
-        } else {
-            CK(vcycle(h->ctx, h->r, h->z, s));
-            CK(dot_partial(h->r, h->z, n, h->partial, s));
-            CK(pcg_update_p(n, h->pv, h->z, h->sc, h->partial, kReduceBlocks, s));
+        if (it >= h->p.max_iter) break;
+        const int parity = h->zb[1] ? (it & 1) : 0;
+        cudaGraphExec_t gx = pcg_graph(h, parity);
+        if (gx) {
+            CK(cudaGraphLaunch(gx, s));
+            note_launches(h->gkernels[parity]);
+            ++it;
+            CK(cudaStreamSynchronize(s));
+            profile_account(h->gprof[parity]);
+            continue;
         }
+        CK(pcg_tail(h, parity, s));
+        CK(pcg_head(h, s));
+        ++it;
     }
 finish:
     if (n > 0) {

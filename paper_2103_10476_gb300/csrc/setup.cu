@@ -641,7 +641,8 @@ __global__ void smooth_count_kernel(int n, const int *rp, const int *ci, const i
     cnt[i] = distinct;
 }
 
-// Thread per row: the products Abar_ik B_k are added in ascending k into the slot of agg(k)
+// Thread per row: the terms Abar_ik B_k are accumulated (one fused multiply-add each) in
+// ascending k into the slot of agg(k)
 // (a local list in first-seen order), then the list is sorted by column and written as
 // P_ic = Pt_ic - (omega / D_i) (Abar Pt)_ic.  Rows with more than kSmoothLocal distinct
 // columns are listed for the warp kernel below.
@@ -663,11 +664,10 @@ __global__ void smooth_fill_kernel(int n, const int *rp, const int *ci, const do
     for (int t = b; t < e; ++t) {
         const int k = ci[t];
         const int c = agg[k];
-        const double prod = v[t] * B[k];
         int p = 0;
         while (p < cnt && cols[p] != c) ++p;
         if (p == cnt) { cols[cnt] = c; acc[cnt] = 0.0; ++cnt; }
-        acc[p] = acc[p] + prod;
+        acc[p] = __fma_rn(v[t], B[k], acc[p]);
     }
     // insertion sort by column
     for (int a = 1; a < cnt; ++a) {
@@ -715,7 +715,7 @@ __global__ void smooth_fill_wide_kernel(const int *rows, const int *nrows, const
             int k = ci[b + u];
             int cu = agg[k];
             if (cu == c) {
-                acc = acc + v[b + u] * B[k];
+                acc = __fma_rn(v[b + u], B[k], acc);
             } else if (cu < c) {
                 bool fu = true;
                 for (int q = 0; q < u; ++q)
@@ -944,10 +944,11 @@ cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t 
     scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, x, scal); note_launch();
     SpmvPlan plan;
     AMG_CUDA_TRY(spmv_plan(A.rp, n, A.nnz, &plan, s));
+    // ticket counter of the SpMV's fixed-order reduction (scal[7], zero)
+    unsigned *counter = reinterpret_cast<unsigned *>(scal + 7);
+    AMG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(double), s));
     for (int k = 0; k < sweeps; ++k) {
-        int nparts = 0;
-        AMG_CUDA_TRY(spmv_scaled_dot(A, plan, D, x, y, partial, &nparts, s));
-        AMG_CUDA_TRY(reduce_partials(partial, nparts, lambda_dev, s));
+        AMG_CUDA_TRY(spmv_scaled_dot(A, plan, D, x, y, partial, lambda_dev, counter, s));
         if (k + 1 < sweeps) {
             AMG_CUDA_TRY(dot(y, y, n, partial, scal, s));
             scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, y, x, scal); note_launch();

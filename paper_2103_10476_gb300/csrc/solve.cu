@@ -42,13 +42,44 @@ __host__ __device__ constexpr int tile_bytes(int cap)
     return cap > 0 ? tile_values_bytes<T>(cap) + (cap + 8) * 4 : 0;
 }
 
+// Fixed-order completion of a two-stage sum: the block that arrives last (atomic ticket)
+// adds every block's partial in index order -- the same order whichever block is last -- and
+// stores the total; it then returns the ticket counter to zero for the next launch.
+__device__ __forceinline__ void last_block_total(const double *partial, int nblocks, unsigned *counter,
+                                                 double *result)
+{
+    __shared__ bool last;
+    __shared__ double wsum[32];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += ((volatile const double *)partial)[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kAll, acc, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        *result = t;
+        *counter = 0u;
+    }
+}
+
 template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const int *__restrict__ rp,
                                                                  const int *__restrict__ ci,
                                                                  const T *__restrict__ v, const T *__restrict__ x,
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
-                                                                 int cap, double *partial, int *err)
+                                                                 int cap, double *partial, double *result,
+                                                                 unsigned *counter, int *err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -62,6 +93,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     const bool staged = cap > 0 && (k1v - k0v) <= cap + 2 * VA && (k1i - k0i) <= cap + 8 && k1 > k0;
     T *sv = (T *)smem;
     int *sc = (int *)(smem + tile_values_bytes<T>(cap));
+    bool tile_ok = true;   // a bulk copy that did not arrive in time: no row is written
     if (staged) {
         if (threadIdx.x == 0) mbar_init(&bar, 1);
         __syncthreads();
@@ -71,13 +103,12 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             bulk_g2s(sv, v + k0v, bv, &bar);
             bulk_g2s(sc, ci + k0i, bi, &bar);
         }
-        const bool ok = mbar_wait_bounded(&bar, 0, err);
-        if (!__syncthreads_and(ok)) return;
+        tile_ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, err));
     }
     const int row = r0 + threadIdx.x / LPR;
     const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    if (row < r1) {
+    if (row < r1 && tile_ok) {
         const int b = rp[row], e = rp[row + 1];
         if (staged) {
             for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
@@ -88,7 +119,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
     double contrib = 0.0;
-    if (row < r1 && lane == 0) {
+    if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
         } else if (MODE == MODE_RESID) {
@@ -120,6 +151,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             for (int w = 0; w < kSpmvThreads / 32; ++w) t += sh[w];
             partial[blockIdx.x] = t;
         }
+        if (result) last_block_total(partial, gridDim.x, counter, result);
     }
 }
 
@@ -189,7 +221,8 @@ int spmv_take_errors(cudaStream_t s)
 
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
-                        T *d, T c1, T c2, int cap, double *partial, cudaStream_t s)
+                        T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
+                        cudaStream_t s)
 {
     const int smem = tile_bytes<T>(cap);
     static int configured = -1;
@@ -199,21 +232,24 @@ cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T
         configured = tile_bytes<T>(kMaxTile);
     }
     spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, spmv_error_flag()); note_launch();
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag()); note_launch();
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
-                      const T *f, const T *aux, T *d, T c1, T c2, double *partial, cudaStream_t s)
+                      const T *f, const T *aux, T *d, T c1, T c2, double *partial, cudaStream_t s,
+                      double *result = nullptr, unsigned *counter = nullptr)
 {
     if (n == 0) return cudaSuccess;
     switch (pl.lpr) {
-    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
-    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
-    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
-    case 16: return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
-    default: return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, s);
+    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 16:
+        return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    default:
+        return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
     }
 }
 
@@ -229,23 +265,24 @@ cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, con
     return spmv_mode<double, MODE_RESID>(pl, A.n, A.rp, A.ci, A.v, x, r, b, nullptr, nullptr, 0.0, 0.0, nullptr, s);
 }
 
-cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial, int *nparts,
-                     cudaStream_t s)
+// q = A p and p . q into *result (fixed-order two-stage sum)
+cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, double *q, double *partial,
+                     double *result, unsigned *counter, cudaStream_t s)
 {
-    *nparts = spmv_blocks(A.n, pl.lpr);
     return spmv_mode<double, MODE_DOT>(pl, A.n, A.rp, A.ci, A.v, p, q, nullptr, nullptr, nullptr, 0.0, 0.0, partial,
-                                       s);
+                                       s, result, counter);
 }
 
+// y = (A x) / D and x . y into *result
 cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
-                            double *partial, int *nparts, cudaStream_t s)
+                            double *partial, double *result, unsigned *counter, cudaStream_t s)
 {
-    *nparts = spmv_blocks(A.n, pl.lpr);
     return spmv_mode<double, MODE_SCALEDOT>(pl, A.n, A.rp, A.ci, A.v, x, y, nullptr, D, nullptr, 0.0, 0.0, partial,
-                                            s);
+                                            s, result, counter);
 }
 
 int spmv_partials_needed(int n) { return spmv_blocks(n, 2) + 1; }
+int spmv_block_count(int n, const SpmvPlan &pl) { return spmv_blocks(n, pl.lpr); }
 
 // ------------------------------------------------------------------------------------ PCG vector updates
 __device__ __forceinline__ double block_sum_fixed(double v)
@@ -287,18 +324,20 @@ __device__ __forceinline__ double sum_partials_all(const double *partial, int co
     return block_sum_all(acc);
 }
 
-// alpha = rz / (p . q) from the SpMV's partial sums; x += alpha p; r -= alpha q; partial sums
-// of r . r (read back by the host for the stopping test)
+// alpha = rz / (p . q); x += alpha p; r -= alpha q; partial sums of r . r (read back by the
+// host for the stopping test)
 __global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x, double *r, const double *p,
                                                                 const double *q, PcgScalars *sc,
                                                                 const double *pq_partial, int pq_count,
                                                                 double *rr_partial)
 {
+    // p . q from the SpMV's per-block partial sums, the same fixed order in every block
     const double pq = sum_partials_all(pq_partial, pq_count);
     const double alpha = sc->rz_next / pq;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->pq = pq;
     // rz_next (this iteration's r . z) becomes rz, read by the next p update; this kernel
     // reads only rz_next, so the write races with nothing
-    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->pq = pq; sc->alpha = alpha; sc->rz = sc->rz_next; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->alpha = alpha; sc->rz = sc->rz_next; }
     double acc = 0.0;
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
         x[i] += alpha * p[i];
@@ -317,61 +356,44 @@ cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const do
     return cudaGetLastError();
 }
 
-// rz' = r . z from partial sums; beta = rz' / rz; p = z + beta p.  The new value goes to a
-// second slot (rz_next) that the next alpha reads, so no block overwrites what another block
-// of the same kernel still reads.
-__global__ void __launch_bounds__(kReduceThreads) pcg_p_kernel(int n, double *p, const double *z, PcgScalars *sc,
-                                                               const double *rz_partial, int count)
-{
-    const double rz_new = sum_partials_all(rz_partial, count);
-    const double beta = rz_new / sc->rz;
-    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
-        p[i] = z[i] + beta * p[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
-}
-
-cudaError_t pcg_update_p(int n, double *p, const double *z, PcgScalars *sc, const double *rz_partial, int count,
-                         cudaStream_t s)
-{
-    pcg_p_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, z, sc, rz_partial, count); note_launch();
-    return cudaGetLastError();
-}
-
-// Flexible (Polak-Ribiere) update for the mixed-precision preconditioner, whose FP32
-// rounding makes it symmetric only approximately: beta = (r'.z' - r'.z_prev) / (r.z).  In
-// exact arithmetic r'.z_prev = 0 and this is the update above.
-__global__ void __launch_bounds__(kReduceThreads) pcg_p_flex_kernel(int n, double *p, const double *z,
-                                                                    PcgScalars *sc, const double *rz_partial,
-                                                                    const double *rzp_partial, int count)
-{
-    const double rz_new = sum_partials_all(rz_partial, count);
-    const double rz_cross = sum_partials_all(rzp_partial, count);
-    const double beta = (rz_new - rz_cross) / sc->rz;
-    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
-        p[i] = z[i] + beta * p[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
-}
-
-// partial sums of r . z and r . z_prev in one pass
-__global__ void __launch_bounds__(kReduceThreads) dot2_kernel(int n, const double *r, const double *z,
-                                                              const double *zp, double *pa, double *pb)
+// r . z (and r . z_prev for the flexible form) into scalars, fixed-order two-stage sums
+__global__ void __launch_bounds__(kReduceThreads) dot_rz_kernel(int n, const double *r, const double *z,
+                                                                const double *zp, double *pa, double *pb,
+                                                                PcgScalars *sc, unsigned *counters)
 {
     double a = 0.0, b = 0.0;
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
         const double ri = r[i];
         a += ri * z[i];
-        b += ri * zp[i];
+        if (zp) b += ri * zp[i];
     }
     const double ta = block_sum_all(a);
-    const double tb = block_sum_all(b);
-    if (threadIdx.x == 0) { pa[blockIdx.x] = ta; pb[blockIdx.x] = tb; }
+    if (threadIdx.x == 0) pa[blockIdx.x] = ta;
+    last_block_total(pa, gridDim.x, counters, &sc->rz_new);
+    if (zp) {
+        const double tb = block_sum_all(b);
+        if (threadIdx.x == 0) pb[blockIdx.x] = tb;
+        last_block_total(pb, gridDim.x, counters + 1, &sc->rz_cross);
+    }
 }
 
-cudaError_t pcg_update_p_flexible(int n, double *p, const double *r, const double *z, const double *z_prev,
-                                  PcgScalars *sc, double *pa, double *pb, cudaStream_t s)
+// beta = rz_new / rz (flexible: (rz_new - rz_cross) / rz); p = z + beta p.  rz_new goes to
+// rz_next, which the next alpha reads (no block overwrites what another still reads).
+__global__ void __launch_bounds__(kReduceThreads) pcg_p_kernel(int n, double *p, const double *z, PcgScalars *sc,
+                                                               int flexible)
 {
-    dot2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, r, z, z_prev, pa, pb); note_launch();
-    pcg_p_flex_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, z, sc, pa, pb, kReduceBlocks); note_launch();
+    const double rz_new = sc->rz_new;
+    const double beta = (flexible ? rz_new - sc->rz_cross : rz_new) / sc->rz;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
+        p[i] = z[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
+}
+
+cudaError_t pcg_update_p(int n, double *p, const double *r, const double *z, const double *z_prev, PcgScalars *sc,
+                         double *pa, double *pb, unsigned *counters, cudaStream_t s)
+{
+    dot_rz_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, r, z, z_prev, pa, pb, sc, counters); note_launch();
+    pcg_p_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, z, sc, z_prev ? 1 : 0); note_launch();
     return cudaGetLastError();
 }
 

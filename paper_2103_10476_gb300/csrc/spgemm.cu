@@ -1,10 +1,10 @@
 // spgemm.cu -- two-phase (symbolic count, numeric fill) hash SpGEMM C = A B, one warp per
 // row of A, hash tables in shared memory (global memory for rows whose table does not fit).
 //
-// Numeric order: for each row, the warp walks A's row in ascending k and, for one k at a
-// time, its lanes add a_ik * b_kj into the distinct slots of B's row k; the slots of one k
-// never collide, so every c_ij is the sum over ascending k starting from 0 of separately
-// rounded products (compiled with --fmad=false), independent of the hash layout.
+// Numeric order: the products of a row are taken 32 at a time in (k, j) order; the terms that
+// land in one slot are applied in that order, each as c = fma(a_ik, b_kj, c), so every c_ij is
+// accumulated over ascending k from 0 with one rounding per term, independent of the hash
+// layout (the same arithmetic as a sequential Gustavson product with fma).
 //
 // Rows are binned by table size so each launch uses one size: the symbolic phase by an
 // upper bound (min(products, columns)), the numeric phase by the exact count.
@@ -60,42 +60,68 @@ __device__ __forceinline__ int table_for(int64_t need)
 }
 
 // ------------------------------------------------------------------------------------ bounds and bins
+// per-block histogram of bins, one global atomic per (block, bin)
+__device__ __forceinline__ void bin_count_block(int b, bool valid, int *binCount)
+{
+    __shared__ int hist[kNumBins];
+    if (threadIdx.x < kNumBins) hist[threadIdx.x] = 0;
+    __syncthreads();
+    if (valid) atomicAdd(&hist[b], 1);
+    __syncthreads();
+    if (threadIdx.x < kNumBins && hist[threadIdx.x]) atomicAdd(&binCount[threadIdx.x], hist[threadIdx.x]);
+}
+
 __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
                           int *tsize)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t ub = 0;
-    for (int e = arp[i]; e < arp[i + 1]; ++e) {
-        int k = aci[e];
-        ub += brp[k + 1] - brp[k];
+    int b = 0;
+    if (i < n) {
+        int64_t ub = 0;
+        for (int e = arp[i]; e < arp[i + 1]; ++e) {
+            int k = aci[e];
+            ub += brp[k + 1] - brp[k];
+        }
+        int64_t need = ub < ncolB ? ub : ncolB;
+        int S = table_for(need);
+        b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
+        bin[i] = b;
+        tsize[i] = S;
     }
-    int64_t need = ub < ncolB ? ub : ncolB;
-    int S = table_for(need);
-    int b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
-    bin[i] = b;
-    tsize[i] = S;
-    atomicAdd(&binCount[b], 1);
+    bin_count_block(b, i < n, binCount);
 }
 
 __global__ void exact_bin_kernel(int n, const int *crp, int *bin, int *binCount, int *tsize)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int64_t cnt = crp[i + 1] - crp[i];
-    int S = table_for(cnt);
-    int b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
-    bin[i] = b;
-    tsize[i] = S;
-    atomicAdd(&binCount[b], 1);
+    int b = 0;
+    if (i < n) {
+        int64_t cnt = crp[i + 1] - crp[i];
+        int S = table_for(cnt);
+        b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
+        bin[i] = b;
+        tsize[i] = S;
+    }
+    bin_count_block(b, i < n, binCount);
 }
 
+// rows to their bin's segment: block-local ranks, one global atomic per (block, bin)
 __global__ void bin_scatter_kernel(int n, const int *bin, const int *binStart, int *binFill, int *perm)
 {
+    __shared__ int hist[kNumBins], base[kNumBins];
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int b = bin[i];
-    perm[binStart[b] + atomicAdd(&binFill[b], 1)] = i;
+    if (threadIdx.x < kNumBins) hist[threadIdx.x] = 0;
+    __syncthreads();
+    int b = 0, local = 0;
+    if (i < n) {
+        b = bin[i];
+        local = atomicAdd(&hist[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins && hist[threadIdx.x])
+        base[threadIdx.x] = binStart[threadIdx.x] + atomicAdd(&binFill[threadIdx.x], hist[threadIdx.x]);
+    __syncthreads();
+    if (i < n) perm[base[b] + local] = i;
 }
 
 // global-bin table offsets: tsize of listed rows, scanned on the host side of the launch
@@ -112,7 +138,7 @@ __global__ void gather_tsize_kernel(int cnt, const int *rows, const int *tsize, 
 // of B-row lengths; a product's entry is found by binary search over those counts.
 struct ProductBatch {
     int j;          // column of the product (valid lanes)
-    double prod;    // a_ik * b_kj, rounded
+    double a, b;    // a_ik and b_kj
     bool valid;
 };
 
@@ -134,7 +160,8 @@ __device__ __forceinline__ ProductBatch product_at(int q, int total, int incl, i
     const int f = __shfl_sync(kFullMask, fb, owner) + off;
     const double ao = WITH_VALUES ? __shfl_sync(kFullMask, a, owner) : 0.0;
     pb.j = pb.valid ? bci[f] : -1;
-    pb.prod = (WITH_VALUES && pb.valid) ? ao * bv[f] : 0.0;
+    pb.a = ao;
+    pb.b = (WITH_VALUES && pb.valid) ? bv[f] : 0.0;
     return pb;
 }
 
@@ -239,7 +266,7 @@ __device__ void numeric_row(int i, const int *arp, const int *aci, const double 
             const unsigned rank = act ? (unsigned)__popc(same & lt) : 0u;
             const unsigned maxrank = __reduce_max_sync(kFullMask, rank);
             for (unsigned r = 0; r <= maxrank; ++r) {
-                if (act && rank == r) vals[slot] = vals[slot] + pb.prod;
+                if (act && rank == r) vals[slot] = __fma_rn(pb.a, pb.b, vals[slot]);
                 __syncwarp();
             }
         }

@@ -13,12 +13,8 @@ namespace {
 std::atomic<long long> g_launches{0};
 std::atomic<bool> g_prof_on{false};
 std::mutex g_prof_mu;
-struct ProfRecord {
-    int cls;
-    cudaEvent_t start, stop;
-    double bytes;
-};
 std::vector<ProfRecord> g_pending;
+thread_local ProfList *t_capture = nullptr;   // set while a graph body is being captured
 std::vector<cudaEvent_t> g_pool;
 long long g_prof_launches[KC_COUNT];
 double g_prof_ms[KC_COUNT], g_prof_bytes[KC_COUNT];
@@ -43,6 +39,8 @@ void drain_locked()
             g_prof_launches[r.cls] += 1;
             g_prof_ms[r.cls] += ms;
             g_prof_bytes[r.cls] += r.bytes;
+        } else {
+            cudaGetLastError();
         }
         g_pool.push_back(r.start);
         g_pool.push_back(r.stop);
@@ -52,15 +50,19 @@ void drain_locked()
 }  // namespace
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 bool profiling_enabled() { return g_prof_on.load(std::memory_order_relaxed); }
 
 ProfScope::ProfScope(int c, cudaStream_t st, double b) : cls(c), s(st), bytes(b)
 {
-    if (!profiling_enabled() || c < 0 || c >= KC_COUNT) return;
+    if (c < 0 || c >= KC_COUNT) return;
+    if (!t_capture && !profiling_enabled()) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     start = take_event();
-    if (start) cudaEventRecord(start, s);
+    // inside a capture the record must be an external event node (a plain record would only
+    // mark a dependency inside the graph and never set the event)
+    if (start) cudaEventRecordWithFlags(start, s, t_capture ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 ProfScope::~ProfScope()
@@ -69,9 +71,42 @@ ProfScope::~ProfScope()
     std::lock_guard<std::mutex> lk(g_prof_mu);
     cudaEvent_t stop = take_event();
     if (!stop) { g_pool.push_back(start); return; }
-    cudaEventRecord(stop, s);
+    cudaEventRecordWithFlags(stop, s, t_capture ? cudaEventRecordExternal : cudaEventRecordDefault);
+    if (t_capture) {
+        // the events become nodes of the graph being captured; the owner accounts them after
+        // each launch of that graph
+        t_capture->push_back(ProfRecord{cls, start, stop, bytes});
+        return;
+    }
     g_pending.push_back(ProfRecord{cls, start, stop, bytes});
     if (g_pending.size() > 4096) drain_locked();
+}
+
+void profile_capture_begin(ProfList *list) { t_capture = list; }
+void profile_capture_end() { t_capture = nullptr; }
+
+// after a launch of a graph whose body recorded `list` has completed
+void profile_account(const ProfList &list)
+{
+    if (!profiling_enabled()) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (const auto &r : list) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.start, r.stop) == cudaSuccess) {
+            g_prof_launches[r.cls] += 1;
+            g_prof_ms[r.cls] += ms;
+            g_prof_bytes[r.cls] += r.bytes;
+        } else {
+            cudaGetLastError();   // a failed query must not surface as a later launch's error
+        }
+    }
+}
+
+void profile_release(ProfList &list)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto &r : list) { g_pool.push_back(r.start); g_pool.push_back(r.stop); }
+    list.clear();
 }
 
 void profile_enable(bool on)
