@@ -84,6 +84,15 @@ def _load():
         "amg_launch_count": (C.c_int64, []),
         "amg_profile_enable": (st, [C.c_int]),
         "amg_profile_read": (st, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "amg_setup_batch": (st, [C.c_int, C.POINTER(C.POINTER(amg_csr_t)), C.POINTER(vp), C.POINTER(amg_params_t),
+                                 C.c_int, C.POINTER(vp)]),
+        "amg_batch_create": (st, [C.c_int, C.POINTER(vp), vp, C.POINTER(vp)]),
+        "amg_batch_solve": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(amg_info_t)]),
+        "amg_batch_free": (st, [vp]),
+        "amg_solve_batch": (st, [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_double,
+                                 C.POINTER(amg_info_t)]),
+        "amg_batch_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
+                                C.POINTER(C.c_int64)]),
         "amg_status_string": (C.c_char_p, [st]),
         "amg_last_error": (C.c_char_p, []),
     }
@@ -239,6 +248,69 @@ def amg_spgemm_noalloc(A: amg_csr_t, ncolA: int, B: amg_csr_t, ncolB: int, C_row
     pv, _ = _ptr(C_val)
     s = lib.amg_spgemm_noalloc(C.byref(A), ncolA, C.byref(B), ncolB, stream, prp, pci, pv, capacity, C.byref(nnz))
     return s, nnz.value
+
+
+def _ptr_array(arrays):
+    out = (C.c_void_p * max(1, len(arrays)))()
+    for k, a in enumerate(arrays):
+        out[k] = _ptr(a)[0]
+    return out
+
+
+def amg_setup_batch(As, nullspaces=None, params: amg_params_t | None = None, threads: int = 0):
+    """List of handles, one per amg_csr_t in As (built concurrently); raises AmgError."""
+    p = params if params is not None else amg_params_default()
+    n = len(As)
+    arr = (C.POINTER(amg_csr_t) * max(1, n))()
+    for k, A in enumerate(As):
+        arr[k] = C.pointer(A)
+    ns = _ptr_array(nullspaces) if nullspaces is not None else None
+    out = (C.c_void_p * max(1, n))()
+    _check(lib.amg_setup_batch(n, arr, ns, C.byref(p), threads, out), "amg_setup_batch")
+    return [C.c_void_p(out[k]) for k in range(n)]
+
+
+def _handle_array(handles):
+    arr = (C.c_void_p * max(1, len(handles)))()
+    for k, h in enumerate(handles):
+        arr[k] = h.value if isinstance(h, C.c_void_p) else h
+    return arr
+
+
+def amg_batch_create(handles, stream=None):
+    bt = C.c_void_p()
+    _check(lib.amg_batch_create(len(handles), _handle_array(handles), stream, C.byref(bt)), "amg_batch_create")
+    return bt
+
+
+def amg_batch_solve(bt, bs, xs, tol: float):
+    """Solves every system into xs[k]; returns (status, list of amg_info_t)."""
+    n = len(bs)
+    infos = (amg_info_t * max(1, n))()
+    s = lib.amg_batch_solve(bt, _ptr_array(bs), _ptr_array(xs), tol, infos)
+    if s not in (AMG_OK, AMG_ERR_NOT_CONVERGED):
+        _check(s, "amg_batch_solve")
+    return s, [infos[k] for k in range(n)]
+
+
+def amg_batch_free(bt):
+    _check(lib.amg_batch_free(bt), "amg_batch_free")
+
+
+def amg_solve_batch(handles, bs, xs, tol: float):
+    n = len(handles)
+    infos = (amg_info_t * max(1, n))()
+    s = lib.amg_solve_batch(n, _handle_array(handles), _ptr_array(bs), _ptr_array(xs), tol, infos)
+    if s not in (AMG_OK, AMG_ERR_NOT_CONVERGED):
+        _check(s, "amg_solve_batch")
+    return s, [infos[k] for k in range(n)]
+
+
+def amg_batch_info(bt):
+    """(systems, levels, fine rows, kernels per replayed iteration)."""
+    c, L, rows, gk = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+    _check(lib.amg_batch_info(bt, C.byref(c), C.byref(L), C.byref(rows), C.byref(gk)), "amg_batch_info")
+    return c.value, L.value, rows.value, gk.value
 
 
 def amg_status_string(s: int) -> str:

@@ -24,6 +24,7 @@ SOURCES = {
     "coarse.cu": [],
     "solve.cu": [],
     "api.cu": [],
+    "batch.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

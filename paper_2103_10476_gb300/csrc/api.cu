@@ -7,6 +7,7 @@
 // spgemm.cu, coarse.cu, solve.cu and util.cu.  The host reads back sizes (to allocate),
 // eigenvalue estimates (to set omega and the Chebyshev interval) and the residual norm (to
 // stop PCG).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -16,6 +17,7 @@
 #include <vector>
 
 #include "amg_internal.cuh"
+#include "hierarchy.cuh"
 
 using namespace amgk;
 
@@ -23,55 +25,11 @@ namespace {
 
 thread_local std::string g_last_error;
 
-struct Level {
-    DevCsr A;                 // level operator
-    double *diag = nullptr;   // diag(A)
-    uint8_t *strong = nullptr, *removed = nullptr, *lumpflag = nullptr, *cflag = nullptr;
-    DevCsr Abar;
-    int *agg = nullptr;
-    uint8_t *root = nullptr;
-    int nagg = 0;
-    double *B = nullptr, *nrm = nullptr, *Dsm = nullptr;
-    double lambda_bar = 0.0, omega = 0.0, lambda_cheb = 0.0;
-    DevCsr P, R;
-    double *invdiag = nullptr;
-    float *invdiag_f = nullptr, *Af = nullptr, *Pf = nullptr, *Rf = nullptr;
-    void *vf = nullptr, *vx = nullptr, *vx2 = nullptr, *vr = nullptr, *vd = nullptr;   // solve vectors
-    SpmvPlan plan_a, plan_p, plan_r;
-};
-
 }  // namespace
 
-struct amg_hierarchy {
-    amg_params_t p;
-    cudaStream_t s = nullptr;
-    int nlev = 0;
-    Level lev[32];
-    std::vector<void *> allocs;
-    double *coarse_inv = nullptr;
-    // solve workspace (FP64, finest level)
-    double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
-    double *z_prev = nullptr;   // previous preconditioned residual (flexible update, mixed precision)
-    double *zb[2] = {nullptr, nullptr};   // the two z buffers (their roles alternate in mixed mode)
-    // one PCG iteration (V-cycle, p update, q = A p, x and r update, copy of the r.r partial
-    // sums to the host) as a CUDA graph; two graphs in mixed mode (z buffers alternate)
-    cudaStream_t cap = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    ProfList gprof[2];
-    int gprof_on[2] = {-1, -1};
-    long long gkernels[2] = {0, 0};   // kernels in each graph (added to the launch count per replay)
-    bool graph_failed = false;
-    double *partial = nullptr, *partial2 = nullptr, *partial3 = nullptr;
-    double *rr_host = nullptr;   // pinned copy of the r . r partial sums
-    PcgScalars *sc = nullptr;
-    unsigned *counters = nullptr;   // ticket counters of the fixed-order reductions (zero between uses)
-    SpmvPlan plan0;   // finest-level FP64 operator (PCG)
-    SolveCtx ctx;
-    double setup_ms = 0.0;
-    int64_t fine_nnz = 0;
-};
+namespace amgk {
 
-namespace {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
 
 amg_status_t fail_cuda(cudaError_t e, const char *where)
 {
@@ -80,6 +38,10 @@ amg_status_t fail_cuda(cudaError_t e, const char *where)
     if (e == cudaErrorMemoryAllocation) return AMG_ERR_OOM;
     return AMG_ERR_CUDA;
 }
+
+}  // namespace amgk
+
+namespace {
 
 #define CK(expr)                                                          \
     do {                                                                  \
@@ -118,14 +80,14 @@ void keep_pool_memory()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return;
-    static bool done[64] = {false};
-    if (dev < 0 || dev >= 64 || done[dev]) return;
+    static std::atomic<bool> done[64];   // setting the attribute twice is harmless
+    if (dev < 0 || dev >= 64 || done[dev].load()) return;
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
         uint64_t thr = UINT64_MAX;
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    done[dev] = true;
+    done[dev].store(true);
 }
 
 void free_async(void *p, cudaStream_t s)

@@ -13,6 +13,8 @@
 // to log2(LPR) per row.  The working type T is double (FP64 path) or float (the mixed
 // path's V-cycle); accumulation is in T.  Partial dot products are per block, in a fixed
 // order, so every reduction is bitwise reproducible.
+#include <mutex>
+
 #include "amg_internal.cuh"
 #include "tma.cuh"
 
@@ -29,6 +31,7 @@ enum SpmvMode {
     MODE_PROLONG = 3,    // y += A x
     MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
     MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
+    MODE_CHEB_SEG = 6,   // MODE_CHEB with c1, c2 of the row's system: coef[rowsys[i] * cstride + {0, 1}]
 };
 
 template <typename T>
@@ -79,7 +82,10 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
                                                                  int cap, double *partial, double *result,
-                                                                 unsigned *counter, int *err)
+                                                                 unsigned *counter, int *err,
+                                                                 const int *__restrict__ rowsys,
+                                                                 const double *__restrict__ coef, int cstride,
+                                                                 const int *__restrict__ active)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -87,6 +93,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     constexpr int VA = 16 / (int)sizeof(T);
     const int r0 = blockIdx.x * RPB;
     const int r1 = min(n, r0 + RPB);
+    const int row = r0 + threadIdx.x / LPR;
+    const int lane = threadIdx.x % LPR;
+    bool on = row < r1;
+    if (MODE != MODE_DOT && MODE != MODE_SCALEDOT && active) {
+        // batched operators: rows of systems that have stopped are skipped, and so is a block
+        // with no other row (before it stages anything)
+        on = on && active[rowsys[row]] != 0;
+        if (!__syncthreads_or(on)) return;
+    }
     const int k0 = rp[r0], k1 = rp[r1];
     const int k0v = k0 & ~(VA - 1), k1v = (k1 + VA - 1) & ~(VA - 1);
     const int k0i = k0 & ~3, k1i = (k1 + 3) & ~3;
@@ -105,10 +120,8 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         }
         tile_ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, err));
     }
-    const int row = r0 + threadIdx.x / LPR;
-    const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    if (row < r1 && tile_ok) {
+    if (on && tile_ok) {
         const int b = rp[row], e = rp[row + 1];
         if (staged) {
             for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
@@ -119,12 +132,17 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
     double contrib = 0.0;
-    if (row < r1 && lane == 0 && tile_ok) {
+    if (on && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
         } else if (MODE == MODE_RESID) {
             y[row] = f[row] - sum;
-        } else if (MODE == MODE_CHEB) {
+        } else if (MODE == MODE_CHEB || MODE == MODE_CHEB_SEG) {
+            if (MODE == MODE_CHEB_SEG) {
+                const double *cs = coef + (size_t)rowsys[row] * cstride;
+                c1 = (T)cs[0];
+                c2 = (T)cs[1];
+            }
             T r = f[row] - sum;
             T dn = c1 * d[row] + c2 * (aux[row] * r);
             d[row] = dn;
@@ -198,13 +216,14 @@ cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStr
 }
 
 static int *g_spmv_err = nullptr;   // device error flag of the bounded waits (allocated once)
+static std::once_flag g_spmv_err_once;
 
 int *spmv_error_flag()
 {
-    if (!g_spmv_err) {
-        if (cudaMalloc(&g_spmv_err, sizeof(int)) != cudaSuccess) return nullptr;
+    std::call_once(g_spmv_err_once, [] {
+        if (cudaMalloc(&g_spmv_err, sizeof(int)) != cudaSuccess) { g_spmv_err = nullptr; return; }
         cudaMemset(g_spmv_err, 0, sizeof(int));
-    }
+    });
     return g_spmv_err;
 }
 
@@ -222,36 +241,71 @@ int spmv_take_errors(cudaStream_t s)
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
-                        cudaStream_t s)
+                        const int *rowsys, const double *coef, int cstride, const int *active, cudaStream_t s)
 {
     const int smem = tile_bytes<T>(cap);
-    static int configured = -1;
-    if (configured < smem) {
-        AMG_CUDA_TRY(cudaFuncSetAttribute(spmv_tile_kernel<T, LPR, MODE>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T>(kMaxTile)));
-        configured = tile_bytes<T>(kMaxTile);
-    }
+    // the attribute is set once per instantiation (any thread may get here first)
+    static std::once_flag configured;
+    static cudaError_t cfg_err = cudaSuccess;
+    std::call_once(configured, [] {
+        cfg_err = cudaFuncSetAttribute(spmv_tile_kernel<T, LPR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       tile_bytes<T>(kMaxTile));
+    });
+    AMG_CUDA_TRY(cfg_err);
     spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag()); note_launch();
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), rowsys, coef,
+        cstride, active); note_launch();
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
                       const T *f, const T *aux, T *d, T c1, T c2, double *partial, cudaStream_t s,
-                      double *result = nullptr, unsigned *counter = nullptr)
+                      double *result = nullptr, unsigned *counter = nullptr, const int *rowsys = nullptr,
+                      const double *coef = nullptr, int cstride = 0, const int *active = nullptr)
 {
     if (n == 0) return cudaSuccess;
+#define AMG_TILE_CASE(L)                                                                                    \
+    return launch_tile<T, L, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, \
+                                   rowsys, coef, cstride, active, s)
     switch (pl.lpr) {
-    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    case 16:
-        return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    default:
-        return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 2: AMG_TILE_CASE(2);
+    case 4: AMG_TILE_CASE(4);
+    case 8: AMG_TILE_CASE(8);
+    case 16: AMG_TILE_CASE(16);
+    default: AMG_TILE_CASE(32);
+    }
+#undef AMG_TILE_CASE
+}
+
+// ------------------------------------------------------------------------------------ segmented (batch) form
+template <typename T>
+cudaError_t seg_spmv(int mode, const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
+                     const T *f, const T *invd, T *d, const int *rowsys, const double *coef, int cstride,
+                     const int *active, cudaStream_t s)
+{
+    switch (mode) {
+    case SEG_Y:
+        return spmv_mode<T, MODE_Y>(pl, n, rp, ci, v, x, y, nullptr, nullptr, nullptr, T(0), T(0), nullptr, s, nullptr,
+                                    nullptr, rowsys, nullptr, 0, active);
+    case SEG_RESID:
+        return spmv_mode<T, MODE_RESID>(pl, n, rp, ci, v, x, y, f, nullptr, nullptr, T(0), T(0), nullptr, s, nullptr,
+                                        nullptr, rowsys, nullptr, 0, active);
+    case SEG_PROLONG:
+        return spmv_mode<T, MODE_PROLONG>(pl, n, rp, ci, v, x, y, nullptr, nullptr, nullptr, T(0), T(0), nullptr, s,
+                                          nullptr, nullptr, rowsys, nullptr, 0, active);
+    case SEG_CHEB:
+        return spmv_mode<T, MODE_CHEB_SEG>(pl, n, rp, ci, v, x, y, f, invd, d, T(0), T(0), nullptr, s, nullptr,
+                                           nullptr, rowsys, coef, cstride, active);
+    default: return cudaErrorInvalidValue;
     }
 }
+template cudaError_t seg_spmv<double>(int, const SpmvPlan &, int, const int *, const int *, const double *,
+                                      const double *, double *, const double *, const double *, double *,
+                                      const int *, const double *, int, const int *, cudaStream_t);
+template cudaError_t seg_spmv<float>(int, const SpmvPlan &, int, const int *, const int *, const float *,
+                                     const float *, float *, const float *, const float *, float *, const int *,
+                                     const double *, int, const int *, cudaStream_t);
 
 // ------------------------------------------------------------------------------------ FP64 entry points
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s)
