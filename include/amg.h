@@ -193,27 +193,28 @@ amg_status_t amg_spgemm_noalloc(const amg_csr_t *A, int64_t ncolA, const amg_csr
  *   16), each on a stream of its own.  out[k] is an ordinary handle (amg_solve, amg_free
  *   work on it) bound to params->cuda_stream.  On failure every out[k] is NULL, nothing is
  *   leaked, and amg_last_error names the first failing system.
- * amg_batch_create: assembles the given hierarchies into one batch for amg_batch_solve.  All
- *   need the same precision and Chebyshev degree.  The batch holds its own copy of every
- *   level (the handles may be freed afterwards).  Layout: systems ordered by decreasing
- *   depth; per level, block-diagonal operators, prolongators and restrictions in int32 CSR
- *   and the concatenated dense coarsest inverses.  Runs on cuda_stream.  At most 65535
- *   systems, and fewer than 2^31 rows and entries per level.
+ * amg_batch_create: groups the given hierarchies for amg_batch_solve.  All need the same
+ *   precision and Chebyshev degree.  The batch refers to the hierarchies' own arrays (the
+ *   handles must outlive it) and allocates only vectors and work lists.  The same handle may
+ *   appear several times (one system per right-hand side).  tune = 1: lanes per matrix row
+ *   of each SpMV are chosen by timing the candidates at the first solve (results can then
+ *   differ in the last bits from another batch); 0: from the mean row length
+ *   (deterministic).  Runs on cuda_stream.  At most 2^31 rows per level over all systems.
  * amg_batch_solve: PCG with one V-cycle per iteration for every system at once; each system
  *   has its own scalars and stopping test (as amg_solve, tolerance tol) and stops
- *   independently.  b[k], x[k]: the caller's system k (the order given to
- *   amg_batch_create), n_k doubles, host or device.  infos (count entries, may be NULL)
- *   receive each system's iterations, status and true residual; solve_ms is the batch's
- *   wall time.  Returns AMG_OK when every system converged, else AMG_ERR_NOT_CONVERGED (or
- *   the error that stopped the batch).  One iteration of the whole batch is replayed as a
- *   CUDA graph.  Synchronises the stream before returning.
- * amg_solve_batch: amg_batch_create + amg_batch_solve + amg_batch_free on h[0]'s stream.
+ *   independently.  b[k], x[k]: system k (the order given to amg_batch_create), n_k doubles,
+ *   host or device.  infos (count entries, may be NULL) receive each system's iterations,
+ *   status and true residual; solve_ms is the batch's wall time.  Returns AMG_OK when every
+ *   system converged, else AMG_ERR_NOT_CONVERGED (or the error that stopped the batch).  One
+ *   iteration of the whole batch is replayed as a CUDA graph.  Synchronises the stream.
+ * amg_solve_batch: amg_batch_create (tune = 0) + amg_batch_solve + amg_batch_free on h[0]'s
+ *   stream.
  * amg_batch_info: systems, levels of the deepest system, fine rows, kernels per replayed
  *   iteration (0 before the first solve). */
 typedef struct amg_batch *amg_batch_t;
 amg_status_t amg_setup_batch(int count, const amg_csr_t *const *A, const double *const *nullspace,
                              const amg_params_t *params, int threads, amg_handle_t *out);
-amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_stream, amg_batch_t *out);
+amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_stream, int tune, amg_batch_t *out);
 amg_status_t amg_batch_solve(amg_batch_t batch, const double *const *b, double *const *x, double tol,
                              amg_info_t *infos);
 amg_status_t amg_batch_free(amg_batch_t batch);

@@ -86,7 +86,7 @@ def _load():
         "amg_profile_read": (st, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "amg_setup_batch": (st, [C.c_int, C.POINTER(C.POINTER(amg_csr_t)), C.POINTER(vp), C.POINTER(amg_params_t),
                                  C.c_int, C.POINTER(vp)]),
-        "amg_batch_create": (st, [C.c_int, C.POINTER(vp), vp, C.POINTER(vp)]),
+        "amg_batch_create": (st, [C.c_int, C.POINTER(vp), vp, C.c_int, C.POINTER(vp)]),
         "amg_batch_solve": (st, [vp, C.POINTER(vp), C.POINTER(vp), C.c_double, C.POINTER(amg_info_t)]),
         "amg_batch_free": (st, [vp]),
         "amg_solve_batch": (st, [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.c_double,
@@ -277,9 +277,10 @@ def _handle_array(handles):
     return arr
 
 
-def amg_batch_create(handles, stream=None):
+def amg_batch_create(handles, stream=None, tune: bool = False):
     bt = C.c_void_p()
-    _check(lib.amg_batch_create(len(handles), _handle_array(handles), stream, C.byref(bt)), "amg_batch_create")
+    _check(lib.amg_batch_create(len(handles), _handle_array(handles), stream, int(tune), C.byref(bt)),
+           "amg_batch_create")
     return bt
 
 

@@ -202,16 +202,6 @@ cudaError_t pcg_store(const double *partial, int count, double *dst, cudaStream_
 
 int pick_lanes(double avg_row);
 
-// SpMV over a block-diagonal (batched) operator: the same tile kernel, with the Chebyshev
-// step's c1, c2 taken per row from its system's entry of a coefficient table
-// (coef[rowsys[i] * cstride + {0, 1}], coef already offset to the step).  Rows whose system
-// has active[rowsys[i]] == 0 are skipped (nothing written); active may be null (all rows).
-enum SegMode { SEG_Y = 0, SEG_RESID = 1, SEG_PROLONG = 2, SEG_CHEB = 3 };
-template <typename T>
-cudaError_t seg_spmv(int mode, const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
-                     const T *f, const T *invd, T *d, const int *rowsys, const double *coef, int cstride,
-                     const int *active, cudaStream_t s);
-
 }  // namespace amgk
 
 // error plumbing shared by the host code

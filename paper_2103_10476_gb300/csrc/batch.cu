@@ -1,174 +1,161 @@
-// batch.cu -- many independent systems solved together: one set of kernel launches per
-// V-cycle step and PCG update for the whole batch (no counterpart in the paper, which solves
-// one system at a time; each system's arithmetic is that of §1.1, Algorithm 1 and §3.1).
+// batch.cu -- the segment-indexed engine (engine.cuh) and the batch ABI on top of it: many
+// independent systems solved together (no counterpart in the paper, which treats one system;
+// each member's arithmetic is that of §1.1, Algorithm 1 and §3.1, as in amg_solve).
 //
-// Layout.  Systems are ordered by decreasing number of levels, so the systems that have a
-// level L form a prefix of that order, and among them the ones for which L is not the
-// coarsest ("intermediate") form a prefix again.  Level L of the batch concatenates level L of
-// those systems: block-diagonal A_L and P_L over the intermediate rows, R_L onto all rows of
-// level L+1 (column indices shifted by each system's row offset), vectors over every system
-// that has level L, and the dense inverses of the systems whose coarsest level is L.  Every
-// smoother step, residual and transfer of the V-cycle is one SpMV launch over the whole batch
-// (the tile kernel of solve.cu; Chebyshev coefficients per row through a row -> system map);
-// the coarse solves are one launch with a block per system.
-//
-// PCG scalars are per system.  Every vector kernel runs over "chunks" (at most kChunkRows rows
-// of one system); a chunk's partial sum goes to its slot, and the last chunk of a system to
-// finish (atomic ticket) adds the system's partials in chunk order, so every per-system scalar
-// is bitwise reproducible.  One PCG iteration of the whole batch is replayed as a CUDA graph.
-// Systems that have converged (or reached max_iter) are masked out of the PCG updates; their
-// V-cycle rows are still computed.
+// Per-member state is a slot: its hierarchy, the offsets of its vectors in the arenas, its
+// PCG scalars and stopping test.  A member joins a running engine at the top of an
+// iteration: with x = 0, r = b, p = 0, z_prev = 0 and r.z "= 1", the next iteration's
+// p = z + beta p is p = z, i.e. exactly the first step of PCG, so starting and joining are
+// the same code path.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
-#include "hierarchy.cuh"
+#include "engine.cuh"
+#include "tma.cuh"
 
 namespace amgk {
 namespace {
 
-constexpr unsigned kBAll = 0xffffffffu;
-constexpr int kBThreads = 256;
-constexpr int kChunkRows = 4096;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kET = 256;            // threads per block of every engine kernel
+constexpr int kEngChunk = 4096;     // fine rows per PCG chunk
+constexpr int kEngMaxTile = 6144;   // shared-memory tile entries at most
+constexpr int kLprs[5] = {2, 4, 8, 16, 32};
+enum { SK_Y = 0, SK_RESID = 1, SK_CHEB = 2, SK_PROLONG = 3 };
 
-// ------------------------------------------------------------------------------------ gathers
-struct CsrSeg {          // one system's matrix moved into the batch matrix
-    const int *rp;
-    const int *ci;
-    const double *v;
-    int n;               // rows
-    int row_off;         // first row in the batch matrix
-    int nnz_off;         // first entry in the batch matrix
-    int col_shift;       // added to every column index
-    int sys;             // batch position (row -> system map)
-};
-struct VecSeg {
-    const void *src;
-    long long n;
-    long long off;
-};
-
-template <typename TV>
-__global__ void gather_csr_kernel(const CsrSeg *segs, int *rp, int *ci, TV *v, int *rowsys)
+// ------------------------------------------------------------------------------------ SpMV tiles
+// Persistent: block b takes tiles b, b + grid, ... of the list.  Each tile's values and
+// column indices are staged in shared memory by two bulk copies completed on one mbarrier
+// (its phase advances once per staged tile), then LPR lanes per row gather x.
+template <typename T, int LPR, int MODE>
+__global__ void __launch_bounds__(kET) segtile_kernel(const SegTile *__restrict__ tiles, const int *__restrict__ count,
+                                                      const SegOp *__restrict__ ops, const T *__restrict__ x, T *y,
+                                                      const T *__restrict__ f, T *d, int coef_idx, int cap, int *err)
 {
-    const CsrSeg sg = segs[blockIdx.y];
-    const int stride = gridDim.x * blockDim.x;
-    const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
-    for (int i = t0; i < sg.n; i += stride) {
-        rp[sg.row_off + i] = sg.rp[i] + sg.nnz_off;
-        if (rowsys) rowsys[sg.row_off + i] = sg.sys;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    constexpr int VA = 16 / (int)sizeof(T);
+    T *sv = (T *)smem;
+    int *sci = (int *)(smem + tile_values_bytes<T>(cap));
+    const int ntiles = *count;
+    if ((int)blockIdx.x >= ntiles) return;
+    if (cap > 0) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
     }
-    const int nnz = sg.n > 0 ? sg.rp[sg.n] : 0;
-    for (int e = t0; e < nnz; e += stride) {
-        ci[sg.nnz_off + e] = sg.ci[e] + sg.col_shift;
-        v[sg.nnz_off + e] = (TV)sg.v[e];
-    }
-}
-
-template <typename TS, typename TD>
-__global__ void gather_vec_kernel(const VecSeg *segs, TD *dst)
-{
-    const VecSeg sg = segs[blockIdx.y];
-    const TS *src = (const TS *)sg.src;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < sg.n;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[sg.off + i] = (TD)src[i];
-}
-
-__global__ void set_int_kernel(int *p, int value) { *p = value; }
-
-struct SysSeg {
-    int off, n, sys;     // rows [off, off + n) of a level belong to batch position sys
-};
-__global__ void fill_rowsys_kernel(const SysSeg *segs, int *rowsys)
-{
-    const SysSeg sg = segs[blockIdx.y];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < sg.n; i += gridDim.x * blockDim.x)
-        rowsys[sg.off + i] = sg.sys;
-}
-
-// ------------------------------------------------------------------------------------ V-cycle pieces
-// First Chebyshev step from x = 0 with the row's own 1/theta: d = D^-1 f / theta, x = d
-template <typename T>
-__global__ void bcheb_zero_kernel(int n, const T *f, const T *invd, const int *rowsys, const double *coef,
-                                  int cstride, const int *active, T *d, T *x)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        if (!active[rowsys[i]]) continue;
-        const T di = (invd[i] * f[i]) * (T)coef[(size_t)rowsys[i] * cstride];
-        d[i] = di;
-        x[i] = di;
-    }
-}
-
-struct CoarseSeg {
-    int off;             // first row in the level
-    int n;               // rows
-    int sys;             // batch position
-    long long inv_off;   // first entry of the system's n x n inverse
-};
-
-// dense coarse solves x = Ainv f, one block per system, one warp per row (FP64 accumulation)
-template <typename T>
-__global__ void bcoarse_kernel(const CoarseSeg *segs, const int *active, const double *inv, const T *f, T *x)
-{
-    const CoarseSeg sg = segs[blockIdx.x];
-    if (!active[sg.sys]) return;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const double *a = inv + sg.inv_off;
-    for (int i = w; i < sg.n; i += nw) {
-        double acc = 0.0;
-        for (int k = lane; k < sg.n; k += 32) acc += a[(size_t)i * sg.n + k] * (double)f[sg.off + k];
+    unsigned phase = 0;
+    const int lrow = threadIdx.x / LPR, lane = threadIdx.x % LPR;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const SegTile tl = tiles[t];
+        const SegOp op = ops[tl.slot];
+        const T *v = (const T *)op.v;
+        const int r0 = tl.row0, r1 = tl.row0 + tl.rows;
+        const int k0 = op.rp[r0], k1 = op.rp[r1];
+        const int k0v = k0 & ~(VA - 1), k1v = (k1 + VA - 1) & ~(VA - 1);
+        const int k0i = k0 & ~3, k1i = (k1 + 3) & ~3;
+        const bool staged = cap > 0 && (k1v - k0v) <= cap + 2 * VA && (k1i - k0i) <= cap + 8 && k1 > k0;
+        if (staged) {
+            if (threadIdx.x == 0) {
+                const unsigned bv = (unsigned)((k1v - k0v) * (int)sizeof(T)), bi = (unsigned)((k1i - k0i) * 4);
+                mbar_expect_tx(&bar, bv + bi);
+                bulk_g2s(sv, v + k0v, bv, &bar);
+                bulk_g2s(sci, op.ci + k0i, bi, &bar);
+            }
+            const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, phase & 1u, err));
+            ++phase;
+            if (!ok) return;    // error recorded; nothing more is written by this block
+        }
+        const int row = r0 + lrow;
+        const T *xs = x + op.xoff;
+        T sum = T(0);
+        if (row < r1) {
+            const int b = op.rp[row], e = op.rp[row + 1];
+            if (staged) {
+                for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * xs[sci[k - k0i]];
+            } else {
+                for (int k = b + lane; k < e; k += LPR) sum += v[k] * xs[op.ci[k]];
+            }
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kBAll, acc, o);
-        if (lane == 0) x[sg.off + i] = (T)acc;
+        for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o, LPR);
+        if (row < r1 && lane == 0) {
+            const int yi = op.yoff + row;
+            if (MODE == SK_Y) {
+                y[yi] = sum;
+            } else if (MODE == SK_RESID) {
+                y[yi] = f[yi] - sum;
+            } else if (MODE == SK_CHEB) {
+                const double *cs = op.coef + coef_idx;
+                const T c1 = (T)cs[0], c2 = (T)cs[1];
+                const T rr = f[yi] - sum;
+                const T dn = c1 * d[yi] + c2 * (((const T *)op.invd)[row] * rr);
+                d[yi] = dn;
+                y[yi] = x[yi] + dn;     // square operator: x is row-indexed at the same offset
+            } else {
+                y[yi] += sum;
+            }
+        }
+        __syncthreads();                // the next tile overwrites the shared tile
     }
 }
 
-template <typename A, typename B>
-__global__ void convert_kernel(int n, const A *in, B *out)
+// first Chebyshev step from x = 0 over the rows of the A tiles: d = D^-1 f / theta, x = d
+template <typename T>
+__global__ void __launch_bounds__(kET) segcheb0_kernel(const SegTile *tiles, const int *count, const SegOp *ops,
+                                                       const T *f, T *d, T *x)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (B)in[i];
+    const int ntiles = *count;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const SegTile tl = tiles[t];
+        const SegOp op = ops[tl.slot];
+        const T inv_theta = (T)op.coef[0];
+        const T *invd = (const T *)op.invd;
+        for (int i = threadIdx.x; i < tl.rows; i += kET) {
+            const int row = tl.row0 + i, yi = op.yoff + row;
+            const T di = (invd[row] * f[yi]) * inv_theta;
+            d[yi] = di;
+            x[yi] = di;
+        }
+    }
 }
-template <typename A, typename B>
-__global__ void convert_active_kernel(int n, const int *rowsys, const int *active, const A *in, B *out)
+
+// dense coarsest-level solves x = Ainv f, a block per slot, a warp per row (FP64 sums)
+template <typename T>
+__global__ void __launch_bounds__(kET) segcoarse_kernel(const SegCoarse *list, const int *count, const T *f, T *x)
 {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        if (active[rowsys[i]]) out[i] = (B)in[i];
+    const int n_items = *count;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
+        const SegCoarse c = list[t];
+        for (int i = w; i < c.n; i += kET / 32) {
+            double acc = 0.0;
+            for (int k = lane; k < c.n; k += 32) acc += c.inv[(size_t)i * c.n + k] * (double)f[c.off + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+            if (lane == 0) x[c.off + i] = (T)acc;
+        }
+    }
 }
 
-// ------------------------------------------------------------------------------------ PCG pieces
-struct Chunk {
-    int sys;             // batch position of the system
-    int begin, end;      // rows [begin, end) of the batch vectors
-    int first, count;    // the system's chunks are [first, first + count)
-};
-
-struct BScal {           // per system, on the device
-    double rz;           // r . z of the current search direction
-    double rz_new;       // r . z after the latest V-cycle
-    double cross;        // r . z_prev (flexible form)
-    double alpha;
-    double pq, rr, tt, bb;
-};
-
-// fixed-order block sum; every thread gets the total
+// ------------------------------------------------------------------------------------ PCG chunks
 __device__ __forceinline__ double block_total(double v)
 {
-    __shared__ double sh[kBThreads / 32];
+    __shared__ double sh[kET / 32];
     __shared__ double tot;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kBAll, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int k = 0; k < kBThreads / 32; ++k) t += sh[k];
+        for (int k = 0; k < kET / 32; ++k) t += sh[k];
         tot = t;
     }
     __syncthreads();
@@ -177,17 +164,17 @@ __device__ __forceinline__ double block_total(double v)
     return r;
 }
 
-// Stores this chunk's partial; the system's last chunk (ticket) returns true in every thread
-// of its block with *total = the system's sum in chunk order, and resets the ticket.
-__device__ __forceinline__ bool chunk_finish(const Chunk &c, double part, double *partial, unsigned *ticket,
+// Stores the chunk's partial at its id; the slot's last chunk to arrive (ticket) returns
+// true with *total = the slot's partials added in chunk order, and resets the ticket.
+__device__ __forceinline__ bool chunk_finish(const SegChunk &c, double part, double *partial, unsigned *ticket,
                                              double *total)
 {
     __shared__ bool last;
     __shared__ double tot;
     if (threadIdx.x == 0) {
-        partial[blockIdx.x] = part;
+        partial[c.id] = part;
         __threadfence();
-        last = atomicAdd(&ticket[c.sys], 1u) == (unsigned)c.count - 1u;
+        last = atomicAdd(&ticket[c.slot], 1u) == (unsigned)c.count - 1u;
     }
     __syncthreads();
     if (!last) return false;
@@ -196,613 +183,239 @@ __device__ __forceinline__ bool chunk_finish(const Chunk &c, double part, double
         double t = 0.0;
         for (int k = 0; k < c.count; ++k) t += ((volatile const double *)partial)[c.first + k];
         tot = t;
-        ticket[c.sys] = 0u;
+        ticket[c.slot] = 0u;
     }
     __syncthreads();
     *total = tot;
     return true;
 }
 
-// per-system sums over the chunks (systems with mask[sys] = 0 skipped; mask may be null):
-// which = 0: a.a -> bb;  1: a.a -> tt;  2: a.b -> rz_new, and p_copy = b
-__global__ void __launch_bounds__(kBThreads) bdot_kernel(const Chunk *chunks, const int *mask, const double *a,
-                                                        const double *b, double *p_copy, double *partial,
-                                                        unsigned *ticket, BScal *sc, int which)
+// start of a solve: x = 0, r = b, p = 0, z_prev = 0, r.z = 1
+__global__ void __launch_bounds__(kET) eng_init_kernel(const SegChunk *chunks, const int *count, const double *b,
+                                                       double *x, double *r, double *p, double *zp, EngScal *sc)
 {
-    const Chunk c = chunks[blockIdx.x];
-    if (mask && !mask[c.sys]) return;
-    double acc = 0.0;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += kBThreads) {
-        const double ai = a[i];
-        if (which == 2) {
-            const double bi = b[i];
-            acc += ai * bi;
-            if (p_copy) p_copy[i] = bi;
-        } else {
-            acc += ai * ai;
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
+            x[i] = 0.0;
+            r[i] = b[i];
+            p[i] = 0.0;
+            if (zp) zp[i] = 0.0;
+        }
+        if (threadIdx.x == 0 && c.id == c.first) sc[c.slot].rz = 1.0;
+    }
+}
+
+// a . a per slot: which = 0 -> bb, 1 -> tt
+__global__ void __launch_bounds__(kET) eng_norm_kernel(const SegChunk *chunks, const int *count, const double *a,
+                                                       double *partial, unsigned *ticket, EngScal *sc, int which)
+{
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        double acc = 0.0;
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) acc += a[i] * a[i];
+        acc = block_total(acc);
+        double tot;
+        if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
+            if (which == 0) sc[c.slot].bb = tot;
+            else sc[c.slot].tt = tot;
         }
     }
-    acc = block_total(acc);
-    double tot;
-    if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
-        if (which == 0) sc[c.sys].bb = tot;
-        else if (which == 1) sc[c.sys].tt = tot;
-        else sc[c.sys].rz_new = tot;
+}
+
+// p . q per slot; the slot's last chunk sets alpha = rz_new / (p . q) and rz = rz_new
+__global__ void __launch_bounds__(kET) eng_pq_kernel(const SegChunk *chunks, const int *count, const double *p,
+                                                     const double *q, double *partial, unsigned *ticket, EngScal *sc)
+{
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        double acc = 0.0;
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) acc += p[i] * q[i];
+        acc = block_total(acc);
+        double tot;
+        if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
+            EngScal &s = sc[c.slot];
+            s.pq = tot;
+            s.alpha = s.rz_new / tot;
+            s.rz = s.rz_new;
+        }
     }
 }
 
-// p . q per system; the last chunk sets alpha = rz_new / (p . q) and rz = rz_new
-__global__ void __launch_bounds__(kBThreads) bpq_kernel(const Chunk *chunks, const int *active, const double *p,
-                                                       const double *q, double *partial, unsigned *ticket, BScal *sc)
+// x += alpha p; r -= alpha q; r . r per slot into rr[slot]
+__global__ void __launch_bounds__(kET) eng_xr_kernel(const SegChunk *chunks, const int *count, const double *p,
+                                                     const double *q, double *x, double *r, double *partial,
+                                                     unsigned *ticket, EngScal *sc, double *rr)
 {
-    const Chunk c = chunks[blockIdx.x];
-    if (!active[c.sys]) return;
-    double acc = 0.0;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += kBThreads) acc += p[i] * q[i];
-    acc = block_total(acc);
-    double tot;
-    if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
-        BScal &s = sc[c.sys];
-        s.pq = tot;
-        s.alpha = s.rz_new / tot;
-        s.rz = s.rz_new;
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        const double alpha = sc[c.slot].alpha;
+        double acc = 0.0;
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
+            x[i] += alpha * p[i];
+            const double ri = r[i] - alpha * q[i];
+            r[i] = ri;
+            acc += ri * ri;
+        }
+        acc = block_total(acc);
+        double tot;
+        if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
+            sc[c.slot].rr = tot;
+            rr[c.slot] = tot;
+        }
     }
 }
 
-// x += alpha p; r -= alpha q; r . r per system into rr_out[sys]
-__global__ void __launch_bounds__(kBThreads) bxr_kernel(const Chunk *chunks, const int *active, const double *p,
-                                                       const double *q, double *x, double *r, double *partial,
-                                                       unsigned *ticket, BScal *sc, double *rr_out)
+// r . z -> rz_new and r . z_prev -> cross (flexible form) per slot
+__global__ void __launch_bounds__(kET) eng_rz_kernel(const SegChunk *chunks, const int *count, const double *r,
+                                                     const double *z, const double *zp, double *partial,
+                                                     double *partial2, unsigned *ticket, unsigned *ticket2,
+                                                     EngScal *sc)
 {
-    const Chunk c = chunks[blockIdx.x];
-    if (!active[c.sys]) return;
-    const double alpha = sc[c.sys].alpha;
-    double acc = 0.0;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += kBThreads) {
-        x[i] += alpha * p[i];
-        const double ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        acc += ri * ri;
-    }
-    acc = block_total(acc);
-    double tot;
-    if (chunk_finish(c, acc, partial, ticket, &tot) && threadIdx.x == 0) {
-        sc[c.sys].rr = tot;
-        rr_out[c.sys] = tot;
-    }
-}
-
-// r . z (and r . z_prev) per system
-__global__ void __launch_bounds__(kBThreads) brz_kernel(const Chunk *chunks, const int *active, const double *r,
-                                                       const double *z, const double *zp, double *partial,
-                                                       double *partial2, unsigned *ticket, unsigned *ticket2,
-                                                       BScal *sc)
-{
-    const Chunk c = chunks[blockIdx.x];
-    if (!active[c.sys]) return;
-    double a = 0.0, b = 0.0;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += kBThreads) {
-        const double ri = r[i];
-        a += ri * z[i];
-        if (zp) b += ri * zp[i];
-    }
-    a = block_total(a);
-    double tot;
-    if (chunk_finish(c, a, partial, ticket, &tot) && threadIdx.x == 0) sc[c.sys].rz_new = tot;
-    if (zp) {
-        b = block_total(b);
-        if (chunk_finish(c, b, partial2, ticket2, &tot) && threadIdx.x == 0) sc[c.sys].cross = tot;
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        double a = 0.0, b = 0.0;
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
+            const double ri = r[i];
+            a += ri * z[i];
+            if (zp) b += ri * zp[i];
+        }
+        a = block_total(a);
+        double tot;
+        if (chunk_finish(c, a, partial, ticket, &tot) && threadIdx.x == 0) sc[c.slot].rz_new = tot;
+        if (zp) {
+            b = block_total(b);
+            if (chunk_finish(c, b, partial2, ticket2, &tot) && threadIdx.x == 0) sc[c.slot].cross = tot;
+        }
     }
 }
 
 // beta = rz_new / rz (flexible: (rz_new - cross) / rz); p = z + beta p
-__global__ void __launch_bounds__(kBThreads) bp_kernel(const Chunk *chunks, const int *active, const double *z,
-                                                      double *p, const BScal *sc, int flexible)
+__global__ void __launch_bounds__(kET) eng_p_kernel(const SegChunk *chunks, const int *count, const double *z,
+                                                    double *p, const EngScal *sc, int flexible)
 {
-    const Chunk c = chunks[blockIdx.x];
-    if (!active[c.sys]) return;
-    const BScal s = sc[c.sys];
-    const double beta = (flexible ? s.rz_new - s.cross : s.rz_new) / s.rz;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += kBThreads) p[i] = z[i] + beta * p[i];
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        const EngScal s = sc[c.slot];
+        const double beta = (flexible ? s.rz_new - s.cross : s.rz_new) / s.rz;
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) p[i] = z[i] + beta * p[i];
+    }
 }
 
-// r = t on the systems whose flag is set (residual replacement)
-__global__ void bcopy_flagged_kernel(const Chunk *chunks, const int *flag, const double *t, double *r)
+__global__ void __launch_bounds__(kET) eng_copy_kernel(const SegChunk *chunks, const int *count, const double *src,
+                                                       double *dst)
 {
-    const Chunk c = chunks[blockIdx.x];
-    if (!flag[c.sys]) return;
-    for (int i = c.begin + threadIdx.x; i < c.end; i += blockDim.x) r[i] = t[i];
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) dst[i] = src[i];
+    }
 }
 
-}  // namespace
-
-// ------------------------------------------------------------------------------------ structure
-struct BLevel {
-    int nrows = 0, nint = 0;            // rows of all systems / of the intermediate prefix
-    int nsys = 0, nsys_int = 0;         // systems having this level / intermediate ones
-    int ncoarse = 0;                    // systems whose coarsest level this is
-    int *arp = nullptr, *aci = nullptr; // block-diagonal A over the intermediate rows
-    int *prp = nullptr, *pci = nullptr; // P: nint x (rows of level L+1)
-    int *rrp = nullptr, *rci = nullptr; // R: (rows of level L+1) x nint
-    void *av = nullptr, *pv = nullptr, *rv = nullptr, *invd = nullptr;   // working type
-    int64_t nnz_a = 0, nnz_p = 0, nnz_r = 0;
-    SpmvPlan plan_a, plan_p, plan_r;
-    int *rowsys = nullptr;              // batch position of each row's system (all rows)
-    double *coef = nullptr;             // nsys_int x cstride Chebyshev coefficients
-    CoarseSeg *ctable = nullptr;        // ncoarse entries
-    double *cinv = nullptr;             // concatenated dense inverses
-    void *f = nullptr, *x = nullptr, *x2 = nullptr, *r = nullptr, *d = nullptr;   // working type
-};
-
-}  // namespace amgk
-
-struct amg_batch {
-    int count = 0;
-    int nlev = 0;
-    int mixed = 0;
-    int degree = 2, cstride = 5;
-    cudaStream_t s = nullptr, cap = nullptr;
-    std::vector<void *> allocs;
-    std::vector<int> order;             // batch position -> caller's index
-    std::vector<int> nlev_sys, max_iter;
-    std::vector<int64_t> off0;          // fine-level row offsets (batch order), count + 1
-    std::vector<double> opc, setup_ms;
-    amgk::BLevel lev[32];
-    int total = 0;                      // fine rows of all systems
-    int64_t nnz0 = 0;
-    int *a0rp = nullptr, *a0ci = nullptr;
-    double *a0v = nullptr;              // all fine operators, FP64 (PCG)
-    amgk::SpmvPlan plan0;
-    int nchunks = 0;
-    amgk::Chunk *chunks = nullptr;
-    double *partial = nullptr, *partial2 = nullptr;
-    unsigned *ticket = nullptr, *ticket2 = nullptr;
-    int *active = nullptr, *flag = nullptr;
-    amgk::BScal *sc = nullptr;
-    double *b = nullptr, *x = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
-    double *zb[2] = {nullptr, nullptr};
-    double *rr_dev = nullptr;
-    double *rr_host = nullptr;          // pinned, count doubles
-    int *host_flags = nullptr;          // pinned, 2 x count ints (active, flag)
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    long long gkernels[2] = {0, 0};
-    bool graph_failed = false;
-};
-
-namespace amgk {
-namespace {
-
-#define CKB(expr)                                                         \
-    do {                                                                  \
-        cudaError_t _e = (expr);                                          \
-        if (_e != cudaSuccess) { st = fail_cuda(_e, #expr); goto done; }  \
-    } while (0)
-
-template <typename T>
-cudaError_t balloc(amg_batch *B, T **p, size_t count)
+template <typename A, typename B>
+__global__ void __launch_bounds__(kET) eng_convert_kernel(const SegChunk *chunks, const int *count, const A *src,
+                                                          B *dst)
 {
-    *p = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)p, (count + 16) * sizeof(T), B->s);
-    if (e == cudaSuccess) B->allocs.push_back((void *)*p);
-    return e;
+    const int n = *count;
+    for (int t = blockIdx.x; t < n; t += gridDim.x) {
+        const SegChunk c = chunks[t];
+        for (int i = c.begin + threadIdx.x; i < c.end; i += kET) dst[i] = (B)src[i];
+    }
 }
 
-template <typename T>
-cudaError_t upload(amg_batch *B, T **dev, const std::vector<T> &host)
+// ------------------------------------------------------------------------------------ lists
+// out = the items of `full` whose slot has mask[slot] != 0 (order of arrival: every item is
+// independent work, and every reduction is ordered by chunk id, not by list position)
+template <typename E>
+__global__ void compact_kernel(const E *full, int n, const int *mask, E *out, int *count)
 {
-    AMG_CUDA_TRY(balloc(B, dev, host.size()));
-    if (host.empty()) return cudaSuccess;
-    AMG_CUDA_TRY(cudaMemcpyAsync(*dev, host.data(), sizeof(T) * host.size(), cudaMemcpyHostToDevice, B->s));
-    return cudaStreamSynchronize(B->s);   // the host vector may go away after return
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const E e = full[i];
+        if (mask[e.slot]) out[atomicAdd(count, 1)] = e;
+    }
 }
 
-int gather_width(int64_t longest)
+// largest number of stored entries of one tile of the list
+__global__ void span_kernel(const SegTile *tiles, int n, const SegOp *ops, int *out)
 {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(64, (longest + kBThreads * 8 - 1) / (kBThreads * 8)));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SegTile t = tiles[i];
+        const SegOp op = ops[t.slot];
+        atomicMax(out, op.rp[t.row0 + t.rows] - op.rp[t.row0]);
+    }
 }
 
-// one launch gathering the listed matrices into a batch CSR (row pointer closed with nnz);
-// longest: the most rows or entries of one listed matrix
-cudaError_t gather_csr(amg_batch *B, const std::vector<CsrSeg> &segs, int64_t longest, int rows, int64_t nnz,
-                       int **rp, int **ci, void **v, bool to_float, int **rowsys)
+__global__ void set_count_kernel(int *count, int value) { *count = value; }
+
+// ------------------------------------------------------------------------------------ launch helpers
+// Persistent grid: as many blocks as can be resident at once (the occupancy of this
+// instantiation with this shared-memory tile), capped by `grid` (the list's length bound).
+template <typename T, int LPR, int MODE>
+cudaError_t seg_launch_lpr(const SegTile *tiles, const int *count, const SegOp *ops, const T *x, T *y, const T *f,
+                           T *d, int coef_idx, int cap, int grid, cudaStream_t s)
 {
-    cudaStream_t s = B->s;
-    AMG_CUDA_TRY(balloc(B, rp, (size_t)rows + 1));
-    AMG_CUDA_TRY(balloc(B, ci, (size_t)nnz));
-    if (to_float) AMG_CUDA_TRY(balloc(B, (float **)v, (size_t)nnz));
-    else AMG_CUDA_TRY(balloc(B, (double **)v, (size_t)nnz));
-    if (rowsys) AMG_CUDA_TRY(balloc(B, rowsys, (size_t)rows));
-    set_int_kernel<<<1, 1, 0, s>>>(*rp + rows, (int)nnz); note_launch();
-    AMG_CUDA_TRY(cudaGetLastError());
-    if (segs.empty()) return cudaSuccess;
-    CsrSeg *dsegs = nullptr;
-    AMG_CUDA_TRY(upload(B, &dsegs, segs));
-    const dim3 grid((unsigned)gather_width(longest), (unsigned)segs.size());
-    if (to_float)
-        gather_csr_kernel<float><<<grid, kBThreads, 0, s>>>(dsegs, *rp, *ci, (float *)*v, rowsys ? *rowsys : nullptr);
-    else
-        gather_csr_kernel<double><<<grid, kBThreads, 0, s>>>(dsegs, *rp, *ci, (double *)*v, rowsys ? *rowsys : nullptr);
-    note_launch();
+    static std::once_flag once;
+    static cudaError_t cfg = cudaSuccess;
+    static int sms = 0;
+    std::call_once(once, [] {
+        cfg = cudaFuncSetAttribute(segtile_kernel<T, LPR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   tile_bytes<T>(kEngMaxTile));
+        int dev = 0;
+        if (cfg == cudaSuccess) cfg = cudaGetDevice(&dev);
+        if (cfg == cudaSuccess) cfg = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    });
+    AMG_CUDA_TRY(cfg);
+    const int smem = tile_bytes<T>(cap);
+    int per_sm = 0;
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, segtile_kernel<T, LPR, MODE>, kET, smem));
+    const int g = std::max(1, std::min(grid, std::max(1, per_sm) * sms));
+    segtile_kernel<T, LPR, MODE><<<g, kET, smem, s>>>(tiles, count, ops, x, y, f, d, coef_idx, cap,
+                                                      spmv_error_flag()); note_launch();
     return cudaGetLastError();
 }
 
-template <typename TS, typename TD>
-cudaError_t gather_vec(amg_batch *B, const std::vector<VecSeg> &segs, TD *dst)
+template <typename T, int MODE>
+cudaError_t seg_launch(int lpr, const SegTile *tiles, const int *count, const SegOp *ops, const T *x, T *y,
+                       const T *f, T *d, int coef_idx, int cap, int grid, cudaStream_t s)
 {
-    if (segs.empty()) return cudaSuccess;
-    VecSeg *dsegs = nullptr;
-    AMG_CUDA_TRY(upload(B, &dsegs, segs));
-    long long longest = 1;
-    for (const VecSeg &g : segs) longest = std::max(longest, g.n);
-    const dim3 grid((unsigned)gather_width(longest), (unsigned)segs.size());
-    gather_vec_kernel<TS, TD><<<grid, kBThreads, 0, B->s>>>(dsegs, dst); note_launch();
-    return cudaGetLastError();
+    switch (lpr) {
+    case 2: return seg_launch_lpr<T, 2, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    case 4: return seg_launch_lpr<T, 4, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    case 8: return seg_launch_lpr<T, 8, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    case 16: return seg_launch_lpr<T, 16, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    default: return seg_launch_lpr<T, 32, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    }
 }
 
-// Chebyshev coefficients of one system on one level, the recurrence of solve.cu's smoother
-// on [b lambda / ratio, b lambda] (§3.1's Chebyshev smoothing): [1/theta, then (c1, c2) for
-// each step k of a pass that starts from a non-zero iterate (step 0: c1 = 0, c2 = 1/theta)]
-void cheb_table(double lambda, const amg_params_t &p, std::vector<double> &out)
+// Chebyshev coefficients of one level of one system, the recurrence of solve.cu's smoother on
+// [b lambda / ratio, b lambda] (§3.1's Chebyshev smoothing): [1/theta, then (c1, c2) for each
+// step k of a pass that starts from a non-zero iterate (step 0: c1 = 0, c2 = 1/theta)]
+void cheb_table(double lambda, const amg_params_t &p, double *out)
 {
     const double lmax = p.cheb_boost * lambda, lmin = lmax / p.cheb_ratio;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
-    out.push_back(1.0 / theta);
-    out.push_back(0.0);
-    out.push_back(1.0 / theta);
+    int k = 0;
+    out[k++] = 1.0 / theta;
+    out[k++] = 0.0;
+    out[k++] = 1.0 / theta;
     double rho = 1.0 / sigma1;
-    for (int k = 1; k < p.cheb_degree; ++k) {
+    for (int j = 1; j < p.cheb_degree; ++j) {
         const double rho_new = 1.0 / (2.0 * sigma1 - rho);
-        out.push_back(rho_new * rho);
-        out.push_back(2.0 * rho_new / delta);
+        out[k++] = rho_new * rho;
+        out[k++] = 2.0 * rho_new / delta;
         rho = rho_new;
     }
 }
 
-amg_status_t too_large()
+void cut_tiles(std::vector<SegTile> &out, int slot, int rows, int rpb)
 {
-    set_last_error("batch too large for 32-bit indices");
-    return AMG_ERR_UNSUPPORTED;
-}
-
-amg_status_t batch_assemble(amg_batch *Bt, const amg_handle_t *H, int C)
-{
-    amg_status_t st = AMG_OK;
-    cudaStream_t s = Bt->s;
-    const bool mixed = Bt->mixed != 0;
-    const size_t ts = mixed ? sizeof(float) : sizeof(double);
-    std::vector<std::vector<int64_t>> off;
-    Bt->count = C;
-    Bt->order.resize(C);
-    for (int i = 0; i < C; ++i) Bt->order[i] = i;
-    std::stable_sort(Bt->order.begin(), Bt->order.end(), [&](int a, int b) { return H[a]->nlev > H[b]->nlev; });
-    Bt->nlev = C ? H[Bt->order[0]]->nlev : 0;
-    Bt->nlev_sys.resize(C);
-    Bt->max_iter.resize(C);
-    Bt->opc.resize(C);
-    Bt->setup_ms.resize(C);
-    for (int k = 0; k < C; ++k) {
-        const amg_hierarchy *h = H[Bt->order[k]];
-        Bt->nlev_sys[k] = h->nlev;
-        Bt->max_iter[k] = h->p.max_iter;
-        Bt->setup_ms[k] = h->setup_ms;
-        double tot = 0.0;
-        for (int L = 0; L < h->nlev; ++L) tot += (double)h->lev[L].A.nnz;
-        Bt->opc[k] = h->fine_nnz ? tot / (double)h->fine_nnz : 0.0;
-    }
-    // row offsets and sizes per level (int32 indices throughout)
-    off.resize(Bt->nlev);
-    for (int L = 0; L < Bt->nlev; ++L) {
-        BLevel &bl = Bt->lev[L];
-        std::vector<int64_t> &o = off[L];
-        o.push_back(0);
-        int64_t nint = 0;
-        for (int k = 0; k < C; ++k) {
-            const amg_hierarchy *h = H[Bt->order[k]];
-            if (h->nlev <= L) break;
-            o.push_back(o.back() + h->lev[L].A.n);
-            bl.nsys++;
-            if (h->nlev > L + 1) { bl.nsys_int++; nint = o.back(); }
-        }
-        if (o.back() > 0x7ffffff0LL) return too_large();
-        bl.nrows = (int)o.back();
-        bl.nint = (int)nint;
-        bl.ncoarse = bl.nsys - bl.nsys_int;
-    }
-    Bt->off0 = C ? off[0] : std::vector<int64_t>(1, 0);
-    Bt->total = C ? Bt->lev[0].nrows : 0;
-    // ---- all fine operators (FP64) for the PCG; level 0 of the V-cycle uses its first rows
-    {
-        std::vector<CsrSeg> segs;
-        int64_t nnz = 0, longest = 1;
-        for (int k = 0; k < C; ++k) {
-            const DevCsr &A = H[Bt->order[k]]->lev[0].A;
-            segs.push_back(CsrSeg{A.rp, A.ci, A.v, A.n, (int)off[0][k], (int)nnz, (int)off[0][k], k});
-            nnz += A.nnz;
-            longest = std::max<int64_t>(longest, std::max<int64_t>(A.nnz, A.n));
-            if (nnz > 0x7ffffff0LL) return too_large();
-        }
-        Bt->nnz0 = nnz;
-        int *rowsys0 = nullptr;
-        CKB(gather_csr(Bt, segs, longest, Bt->total, nnz, &Bt->a0rp, &Bt->a0ci, (void **)&Bt->a0v, false, &rowsys0));
-        if (Bt->nlev > 0) {
-            BLevel &l0 = Bt->lev[0];
-            l0.arp = Bt->a0rp;
-            l0.aci = Bt->a0ci;
-            l0.rowsys = rowsys0;
-            int64_t nnz_int = 0;
-            for (int k = 0; k < l0.nsys_int; ++k) nnz_int += H[Bt->order[k]]->lev[0].A.nnz;
-            l0.nnz_a = nnz_int;
-            if (mixed) {
-                CKB(balloc(Bt, (float **)&l0.av, (size_t)nnz));
-                if (nnz) {
-                    convert_kernel<double, float><<<grid_for(nnz, 256, 16384), 256, 0, s>>>((int)nnz, Bt->a0v,
-                                                                                        (float *)l0.av); note_launch();
-                    CKB(cudaGetLastError());
-                }
-            } else {
-                l0.av = Bt->a0v;
-            }
-        }
-    }
-    // ---- per level: A (L >= 1), P, R, 1/diag, row map, Chebyshev tables, coarse inverses
-    for (int L = 0; L < Bt->nlev; ++L) {
-        BLevel &bl = Bt->lev[L];
-        if (L > 0 && bl.nint > 0) {
-            std::vector<CsrSeg> segs;
-            int64_t nnz = 0, longest = 1;
-            for (int k = 0; k < bl.nsys_int; ++k) {
-                const DevCsr &A = H[Bt->order[k]]->lev[L].A;
-                segs.push_back(CsrSeg{A.rp, A.ci, A.v, A.n, (int)off[L][k], (int)nnz, (int)off[L][k], k});
-                nnz += A.nnz;
-                longest = std::max<int64_t>(longest, std::max<int64_t>(A.nnz, A.n));
-            }
-            if (nnz > 0x7ffffff0LL) return too_large();
-            bl.nnz_a = nnz;
-            CKB(gather_csr(Bt, segs, longest, bl.nint, nnz, &bl.arp, &bl.aci, &bl.av, mixed, nullptr));
-        }
-        if (L > 0) {
-            std::vector<SysSeg> ss;
-            int longest = 1;
-            for (int k = 0; k < bl.nsys; ++k) {
-                ss.push_back(SysSeg{(int)off[L][k], (int)(off[L][k + 1] - off[L][k]), k});
-                longest = std::max(longest, ss.back().n);
-            }
-            CKB(balloc(Bt, &bl.rowsys, (size_t)bl.nrows));
-            SysSeg *dss = nullptr;
-            CKB(upload(Bt, &dss, ss));
-            fill_rowsys_kernel<<<dim3((unsigned)gather_width(longest), (unsigned)ss.size()), kBThreads, 0, s>>>(dss, bl.rowsys); note_launch();
-            CKB(cudaGetLastError());
-        }
-        if (bl.nint > 0) {
-            std::vector<CsrSeg> ps, rs;
-            std::vector<VecSeg> ds;
-            std::vector<double> coef;
-            int64_t np = 0, nr = 0, longest = 1;
-            for (int k = 0; k < bl.nsys_int; ++k) {
-                const amg_hierarchy *h = H[Bt->order[k]];
-                const Level &lv = h->lev[L];
-                ps.push_back(CsrSeg{lv.P.rp, lv.P.ci, lv.P.v, lv.P.n, (int)off[L][k], (int)np, (int)off[L + 1][k], k});
-                rs.push_back(CsrSeg{lv.R.rp, lv.R.ci, lv.R.v, lv.R.n, (int)off[L + 1][k], (int)nr, (int)off[L][k], k});
-                np += lv.P.nnz;
-                nr += lv.R.nnz;
-                longest = std::max<int64_t>(longest, std::max<int64_t>(lv.P.nnz, lv.P.n));
-                ds.push_back(VecSeg{mixed ? (const void *)lv.invdiag_f : (const void *)lv.invdiag, lv.A.n, off[L][k]});
-                cheb_table(lv.lambda_cheb, h->p, coef);
-            }
-            if (np > 0x7ffffff0LL) return too_large();
-            bl.nnz_p = np;
-            bl.nnz_r = nr;
-            CKB(gather_csr(Bt, ps, longest, bl.nint, np, &bl.prp, &bl.pci, &bl.pv, mixed, nullptr));
-            CKB(gather_csr(Bt, rs, longest, Bt->lev[L + 1].nrows, nr, &bl.rrp, &bl.rci, &bl.rv, mixed, nullptr));
-            if (mixed) {
-                CKB(balloc(Bt, (float **)&bl.invd, (size_t)bl.nint));
-                CKB((gather_vec<float, float>(Bt, ds, (float *)bl.invd)));
-            } else {
-                CKB(balloc(Bt, (double **)&bl.invd, (size_t)bl.nint));
-                CKB((gather_vec<double, double>(Bt, ds, (double *)bl.invd)));
-            }
-            CKB(upload(Bt, &bl.coef, coef));
-            CKB(spmv_plan(bl.arp, bl.nint, bl.nnz_a, &bl.plan_a, s));
-            CKB(spmv_plan(bl.prp, bl.nint, bl.nnz_p, &bl.plan_p, s));
-            CKB(spmv_plan(bl.rrp, Bt->lev[L + 1].nrows, bl.nnz_r, &bl.plan_r, s));
-        }
-        if (bl.ncoarse > 0) {
-            std::vector<CoarseSeg> cs;
-            std::vector<VecSeg> is;
-            long long ioff = 0;
-            for (int k = bl.nsys_int; k < bl.nsys; ++k) {
-                const amg_hierarchy *h = H[Bt->order[k]];
-                const int n = h->lev[L].A.n;
-                cs.push_back(CoarseSeg{(int)off[L][k], n, k, ioff});
-                is.push_back(VecSeg{h->coarse_inv, (long long)n * n, ioff});
-                ioff += (long long)n * n;
-            }
-            CKB(upload(Bt, &bl.ctable, cs));
-            CKB(balloc(Bt, &bl.cinv, (size_t)ioff));
-            CKB((gather_vec<double, double>(Bt, is, bl.cinv)));
-        }
-        // work vectors (x and x2 both hold all rows: the level's result may end in either)
-        const size_t nr = (size_t)bl.nrows, ni = (size_t)bl.nint;
-        CKB(balloc(Bt, (char **)&bl.f, nr * ts));
-        CKB(balloc(Bt, (char **)&bl.x, nr * ts));
-        if (ni > 0) {
-            CKB(balloc(Bt, (char **)&bl.x2, nr * ts));
-            CKB(balloc(Bt, (char **)&bl.r, ni * ts));
-            CKB(balloc(Bt, (char **)&bl.d, ni * ts));
-        }
-    }
-    // ---- PCG workspace
-    {
-        const size_t n = (size_t)Bt->total;
-        std::vector<Chunk> ch;
-        for (int k = 0; k < C; ++k) {
-            const int b0 = (int)Bt->off0[k], b1 = (int)Bt->off0[k + 1];
-            const int cnt = b1 > b0 ? (b1 - b0 + kChunkRows - 1) / kChunkRows : 0;
-            const int first = (int)ch.size();
-            for (int c = 0; c < cnt; ++c)
-                ch.push_back(Chunk{k, b0 + c * kChunkRows, std::min(b1, b0 + (c + 1) * kChunkRows), first, cnt});
-        }
-        Bt->nchunks = (int)ch.size();
-        CKB(upload(Bt, &Bt->chunks, ch));
-        CKB(balloc(Bt, &Bt->partial, ch.size()));
-        CKB(balloc(Bt, &Bt->partial2, ch.size()));
-        CKB(balloc(Bt, &Bt->ticket, (size_t)C));
-        CKB(balloc(Bt, &Bt->ticket2, (size_t)C));
-        CKB(cudaMemsetAsync(Bt->ticket, 0, sizeof(unsigned) * (size_t)C, s));
-        CKB(cudaMemsetAsync(Bt->ticket2, 0, sizeof(unsigned) * (size_t)C, s));
-        CKB(balloc(Bt, &Bt->active, (size_t)C));
-        CKB(balloc(Bt, &Bt->flag, (size_t)C));
-        CKB(balloc(Bt, (char **)&Bt->sc, sizeof(BScal) * (size_t)C));
-        CKB(balloc(Bt, &Bt->rr_dev, (size_t)C));
-        for (double **v : {&Bt->b, &Bt->x, &Bt->r, &Bt->pv, &Bt->q, &Bt->t, &Bt->zb[0]}) CKB(balloc(Bt, v, n));
-        if (mixed) CKB(balloc(Bt, &Bt->zb[1], n));
-        CKB(cudaMallocHost(&Bt->rr_host, sizeof(double) * (size_t)(C > 0 ? C : 1)));
-        CKB(cudaMallocHost(&Bt->host_flags, sizeof(int) * 2 * (size_t)(C > 0 ? C : 1)));
-        if (n > 0) CKB(spmv_plan(Bt->a0rp, Bt->total, Bt->nnz0, &Bt->plan0, s));
-    }
-    CKB(cudaStreamCreateWithFlags(&Bt->cap, cudaStreamNonBlocking));
-    CKB(cudaStreamSynchronize(s));
-done:
-    return st;
-}
-
-// V-cycle of the whole batch from level L with x = 0 (Algorithm 1 per system).  f: the
-// level's right-hand side; final_out (level 0 only, may be null): where the finest result
-// goes; *out: the buffer holding the result.
-template <typename T>
-cudaError_t bvcycle(amg_batch *Bt, int L, const T *f, T *final_out, T **out, cudaStream_t s)
-{
-    BLevel &lv = Bt->lev[L];
-    T *x = (T *)lv.x, *x2 = (T *)lv.x2;
-    // the systems whose coarsest level this is: dense solves into the buffer that holds the
-    // level's result (rows [nint, nrows) of it)
-    auto coarse = [&](T *dst) -> cudaError_t {
-        if (lv.ncoarse == 0) return cudaSuccess;
-        bcoarse_kernel<T><<<lv.ncoarse, kBThreads, 0, s>>>(lv.ctable, Bt->active, lv.cinv, f, dst); note_launch();
-        return cudaGetLastError();
-    };
-    if (lv.nint == 0) {
-        *out = final_out ? final_out : x;
-        return coarse(*out);
-    }
-    const int ni = lv.nint;
-    const T *av = (const T *)lv.av;
-    const T *inv = (const T *)lv.invd;
-    T *d = (T *)lv.d;
-    const int deg = Bt->degree, cs = Bt->cstride;
-    // pre-smoothing from x = 0
-    const int *act = Bt->active;
-    bcheb_zero_kernel<T><<<grid_for(ni, 256, 16384), 256, 0, s>>>(ni, f, inv, lv.rowsys, lv.coef, cs, act, d, x); note_launch();
-    AMG_CUDA_TRY(cudaGetLastError());
-    for (int k = 1; k < deg; ++k) {
-        AMG_CUDA_TRY(seg_spmv<T>(SEG_CHEB, lv.plan_a, ni, lv.arp, lv.aci, av, x, x2, f, inv, d, lv.rowsys,
-                                 lv.coef + 1 + 2 * k, cs, act, s));
-        std::swap(x, x2);
-    }
-    // r = f - A x; f_c = R r; recursion; x += P x_c
-    BLevel &cl = Bt->lev[L + 1];
-    AMG_CUDA_TRY(seg_spmv<T>(SEG_RESID, lv.plan_a, ni, lv.arp, lv.aci, av, x, (T *)lv.r, f, nullptr, nullptr,
-                             lv.rowsys, nullptr, 0, act, s));
-    AMG_CUDA_TRY(seg_spmv<T>(SEG_Y, lv.plan_r, cl.nrows, lv.rrp, lv.rci, (const T *)lv.rv, (const T *)lv.r,
-                             (T *)cl.f, nullptr, nullptr, nullptr, cl.rowsys, nullptr, 0, act, s));
-    T *xc = nullptr;
-    AMG_CUDA_TRY(bvcycle<T>(Bt, L + 1, (const T *)cl.f, nullptr, &xc, s));
-    AMG_CUDA_TRY(seg_spmv<T>(SEG_PROLONG, lv.plan_p, ni, lv.prp, lv.pci, (const T *)lv.pv, xc, x, nullptr, nullptr,
-                             nullptr, lv.rowsys, nullptr, 0, act, s));
-    // post-smoothing from the corrected x
-    for (int k = 0; k < deg; ++k) {
-        T *dst = (final_out && k == deg - 1) ? final_out : x2;
-        AMG_CUDA_TRY(seg_spmv<T>(SEG_CHEB, lv.plan_a, ni, lv.arp, lv.aci, av, x, dst, f, inv, d, lv.rowsys,
-                                 lv.coef + 1 + 2 * k, cs, act, s));
-        x2 = x;
-        x = dst;
-    }
-    *out = x;
-    return coarse(x);
-}
-
-// z = M^-1 r for every system of the batch (r, z: FP64 over all fine rows)
-cudaError_t bprecond(amg_batch *Bt, const double *r, double *z, cudaStream_t s)
-{
-    if (Bt->nlev == 0 || Bt->total == 0) return cudaSuccess;
-    const int n = Bt->total;
-    if (Bt->mixed) {
-        BLevel &l0 = Bt->lev[0];
-        convert_active_kernel<double, float><<<grid_for(n, 256, 16384), 256, 0, s>>>(n, l0.rowsys, Bt->active, r,
-                                                                                    (float *)l0.f); note_launch();
-        AMG_CUDA_TRY(cudaGetLastError());
-        float *out = nullptr;
-        AMG_CUDA_TRY(bvcycle<float>(Bt, 0, (const float *)l0.f, nullptr, &out, s));
-        convert_active_kernel<float, double><<<grid_for(n, 256, 16384), 256, 0, s>>>(n, l0.rowsys, Bt->active, out,
-                                                                                    z); note_launch();
-        return cudaGetLastError();
-    }
-    double *out = nullptr;
-    AMG_CUDA_TRY(bvcycle<double>(Bt, 0, r, z, &out, s));
-    if (out == z) return cudaSuccess;
-    return cudaMemcpyAsync(z, out, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s);
-}
-
-// head of an iteration: q = A p, alpha per system, x and r update, r . r to the host
-cudaError_t bhead(amg_batch *Bt, cudaStream_t s)
-{
-    const int nc = Bt->nchunks;
-    AMG_CUDA_TRY(seg_spmv<double>(SEG_Y, Bt->plan0, Bt->total, Bt->a0rp, Bt->a0ci, Bt->a0v, Bt->pv, Bt->q, nullptr,
-                                  nullptr, nullptr, Bt->lev[0].rowsys, nullptr, 0, Bt->active, s));
-    bpq_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->active, Bt->pv, Bt->q, Bt->partial, Bt->ticket, Bt->sc); note_launch();
-    bxr_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->active, Bt->pv, Bt->q, Bt->x, Bt->r, Bt->partial, Bt->ticket,
-                                        Bt->sc, Bt->rr_dev); note_launch();
-    AMG_CUDA_TRY(cudaGetLastError());
-    return cudaMemcpyAsync(Bt->rr_host, Bt->rr_dev, sizeof(double) * (size_t)Bt->count, cudaMemcpyDeviceToHost, s);
-}
-
-// tail of an iteration: z = M^-1 r, r . z (and r . z_prev), p = z + beta p
-cudaError_t btail(amg_batch *Bt, int parity, cudaStream_t s)
-{
-    const int nc = Bt->nchunks;
-    double *z = Bt->zb[Bt->zb[1] ? parity : 0];
-    double *zp = Bt->zb[1] ? Bt->zb[1 - parity] : nullptr;
-    AMG_CUDA_TRY(bprecond(Bt, Bt->r, z, s));
-    brz_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->active, Bt->r, z, zp, Bt->partial, Bt->partial2, Bt->ticket,
-                                        Bt->ticket2, Bt->sc); note_launch();
-    bp_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->active, z, Bt->pv, Bt->sc, zp ? 1 : 0); note_launch();
-    return cudaGetLastError();
-}
-
-cudaGraphExec_t bgraph(amg_batch *Bt, int parity)
-{
-    if (Bt->graph_failed) return nullptr;
-    if (Bt->gexec[parity]) return Bt->gexec[parity];
-    cudaGraph_t g = nullptr;
-    const long long before = launch_count();
-    cudaError_t e = cudaStreamBeginCapture(Bt->cap, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        cudaError_t e1 = btail(Bt, parity, Bt->cap);
-        cudaError_t e2 = e1 == cudaSuccess ? bhead(Bt, Bt->cap) : e1;
-        e = cudaStreamEndCapture(Bt->cap, &g);
-        if (e == cudaSuccess) e = e2;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&Bt->gexec[parity], g, 0);
-    if (g) cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        Bt->graph_failed = true;    // iterations run eagerly from now on
-        Bt->gexec[parity] = nullptr;
-        return nullptr;
-    }
-    Bt->gkernels[parity] = launch_count() - before;
-    note_launches(-Bt->gkernels[parity]);
-    return Bt->gexec[parity];
-}
-
-// t = b - A x and |t|^2 into sc[].tt for the systems in mask (null: all)
-cudaError_t btrue_residual(amg_batch *Bt, const int *mask, cudaStream_t s)
-{
-    AMG_CUDA_TRY(seg_spmv<double>(SEG_RESID, Bt->plan0, Bt->total, Bt->a0rp, Bt->a0ci, Bt->a0v, Bt->x, Bt->t, Bt->b,
-                                  nullptr, nullptr, Bt->lev[0].rowsys, nullptr, 0, mask, s));
-    bdot_kernel<<<Bt->nchunks, kBThreads, 0, s>>>(Bt->chunks, mask, Bt->t, nullptr, nullptr, Bt->partial, Bt->ticket,
-                                                  Bt->sc, 1); note_launch();
-    return cudaGetLastError();
+    for (int r = 0; r < rows; r += rpb) out.push_back(SegTile{slot, r, std::min(rpb, rows - r), 0});
 }
 
 double now_ms()
@@ -810,20 +423,743 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-void batch_release(amg_batch *Bt)
+// (re)allocates a list's device arrays when the host list outgrew them; *moved if it did
+template <typename E>
+cudaError_t upload_list(EngList<E> &l, std::vector<void *> &allocs, size_t &bytes, cudaStream_t s, bool *moved)
 {
-    for (int k = 0; k < 2; ++k)
-        if (Bt->gexec[k]) cudaGraphExecDestroy(Bt->gexec[k]);
-    if (Bt->cap) cudaStreamDestroy(Bt->cap);
-    for (void *p : Bt->allocs) cudaFreeAsync(p, Bt->s);
-    Bt->allocs.clear();
-    cudaStreamSynchronize(Bt->s);
-    if (Bt->rr_host) cudaFreeHost(Bt->rr_host);
-    if (Bt->host_flags) cudaFreeHost(Bt->host_flags);
+    l.nfull = (int)l.host.size();
+    if (!l.full || (size_t)l.nfull > l.capacity) {
+        // the old arrays stay in the owner's allocation list until it is destroyed
+        const size_t cap = std::max<size_t>(64, (size_t)l.nfull + l.nfull / 4);
+        for (E **p : {&l.full, &l.act, &l.flg}) {
+            AMG_CUDA_TRY(cudaMallocAsync((void **)p, sizeof(E) * (cap + 16), s));
+            allocs.push_back((void *)*p);
+            bytes += sizeof(E) * (cap + 16);
+        }
+        if (!l.count) {
+            AMG_CUDA_TRY(cudaMallocAsync((void **)&l.count, sizeof(int) * 16, s));
+            allocs.push_back((void *)l.count);
+            AMG_CUDA_TRY(cudaMemsetAsync(l.count, 0, sizeof(int) * 16, s));
+        }
+        l.capacity = cap;
+        *moved = true;
+    }
+    if (l.nfull > 0)
+        AMG_CUDA_TRY(cudaMemcpyAsync(l.full, l.host.data(), sizeof(E) * (size_t)l.nfull, cudaMemcpyHostToDevice, s));
+    return cudaSuccess;
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------------------------ Engine
+template <typename T>
+cudaError_t Engine::alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    const size_t bytes = (count + 16) * sizeof(T);
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, s_);
+    if (e == cudaSuccess) {
+        allocs_.push_back((void *)*p);
+        bytes_ += bytes;
+    }
+    return e;
+}
+
+Engine::~Engine()
+{
+    drop_graphs();
+    if (cap_) cudaStreamDestroy(cap_);
+    for (void *p : allocs_) cudaFreeAsync(p, s_);
+    cudaStreamSynchronize(s_);
+    if (rr_host_) cudaFreeHost(rr_host_);
+    if (hflags_) cudaFreeHost(hflags_);
+}
+
+void Engine::drop_graphs()
+{
+    for (int k = 0; k < 2; ++k) {
+        if (gexec_[k]) cudaGraphExecDestroy(gexec_[k]);
+        gexec_[k] = nullptr;
+    }
+}
+
+#define EK(expr)                                                           \
+    do {                                                                   \
+        cudaError_t _e = (expr);                                           \
+        if (_e != cudaSuccess) return fail_cuda(_e, #expr);                \
+    } while (0)
+
+amg_status_t Engine::init(const Config &c, cudaStream_t s)
+{
+    cfg_ = c;
+    s_ = s;
+    cstride_ = 1 + 2 * c.degree;
+    const int S = c.slots > 0 ? c.slots : 1;
+    const size_t ts = c.mixed ? sizeof(float) : sizeof(double);
+    const size_t n0 = (size_t)std::max<int64_t>(c.cap0, 1), nc = (size_t)std::max<int64_t>(c.capc, 1);
+    slots_.assign((size_t)S, Slot());
+    hA_.assign((size_t)kEngLevels * S, SegOp{});
+    hP_ = hA_;
+    hR_ = hA_;
+    h0_.assign((size_t)S, SegOp{});
+    hC_.assign((size_t)kEngLevels * S, SegCoarse{});
+    hcoef_.assign((size_t)S * kEngLevels * cstride_, 0.0);
+    free0_.assign(1, {0, c.cap0});
+    freec_.assign(1, {0, c.capc});
+    if (spmv_error_flag() == nullptr) return fail_cuda(cudaErrorMemoryAllocation, "engine init");
+    EK(alloc(&opA_, hA_.size()));
+    EK(alloc(&opP_, hA_.size()));
+    EK(alloc(&opR_, hA_.size()));
+    EK(alloc(&op0_, h0_.size()));
+    EK(alloc(&opC_, hC_.size()));
+    EK(alloc(&coef_, hcoef_.size()));
+    EK(alloc(&active_, (size_t)S));
+    EK(alloc(&flag_, (size_t)S));
+    EK(cudaMemsetAsync(active_, 0, sizeof(int) * S, s_));
+    EK(cudaMemsetAsync(flag_, 0, sizeof(int) * S, s_));
+    EK(alloc((char **)&sc_, sizeof(EngScal) * (size_t)S));
+    EK(cudaMemsetAsync(sc_, 0, sizeof(EngScal) * S, s_));
+    EK(alloc(&rr_dev_, (size_t)S));
+    EK(alloc(&ticket_, (size_t)S));
+    EK(alloc(&ticket2_, (size_t)S));
+    EK(cudaMemsetAsync(ticket_, 0, sizeof(unsigned) * S, s_));
+    EK(cudaMemsetAsync(ticket2_, 0, sizeof(unsigned) * S, s_));
+    EK(alloc(&caps_dev_, (size_t)(3 * kEngLevels + 1)));
+    EK(cudaMallocHost(&rr_host_, sizeof(double) * S));
+    EK(cudaMallocHost(&hflags_, sizeof(int) * 2 * S));
+    std::memset(hflags_, 0, sizeof(int) * 2 * S);
+    for (double **v : {&b_, &x_, &r_, &p_, &q_, &t_, &zb_[0]}) EK(alloc(v, n0));
+    if (c.mixed) EK(alloc(&zb_[1], n0));
+    for (void **v : {&x0_, &x20_, &r0_, &d0_}) EK(alloc((char **)v, n0 * ts));
+    for (void **v : {&fc_, &xc_, &x2c_, &rc_, &dc_}) EK(alloc((char **)v, nc * ts));
+    if (c.mixed) EK(alloc((char **)&f0_, n0 * ts));
+    EK(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    {
+        int dev = 0, sms = 0;
+        EK(cudaGetDevice(&dev));
+        EK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        grid_tiles_ = sms * 8;      // persistent grids of the elementwise and coarse kernels
+        grid_chunks_ = sms * 8;
+    }
+    EK(cudaStreamSynchronize(s_));
+    return AMG_OK;
+}
+
+int64_t Engine::arena_take(std::vector<std::pair<int64_t, int64_t>> &fl, int64_t n)
+{
+    if (n == 0) return 0;
+    for (size_t i = 0; i < fl.size(); ++i) {
+        if (fl[i].second >= n) {
+            const int64_t off = fl[i].first;
+            fl[i].first += n;
+            fl[i].second -= n;
+            if (fl[i].second == 0) fl.erase(fl.begin() + (long)i);
+            return off;
+        }
+    }
+    return -1;
+}
+
+void Engine::arena_give(std::vector<std::pair<int64_t, int64_t>> &fl, int64_t off, int64_t n)
+{
+    if (n == 0) return;
+    fl.push_back({off, n});
+    std::sort(fl.begin(), fl.end());
+    std::vector<std::pair<int64_t, int64_t>> m;
+    for (auto &h : fl) {
+        if (!m.empty() && m.back().first + m.back().second == h.first) m.back().second += h.second;
+        else m.push_back(h);
+    }
+    fl.swap(m);
+}
+
+int Engine::add(amg_hierarchy *h)
+{
+    if (!h || h->nlev < 1 || h->nlev > kEngLevels) return -1;
+    if ((h->p.precision == AMG_MIXED) != (cfg_.mixed != 0) || h->p.cheb_degree != cfg_.degree) return -1;
+    int k = -1;
+    for (int i = 0; i < (int)slots_.size(); ++i)
+        if (!slots_[i].used) { k = i; break; }
+    if (k < 0) return -1;
+    Slot sl;
+    sl.h = h;
+    sl.nlev = h->nlev;
+    sl.n0 = h->lev[0].A.n;
+    for (int L = 1; L < h->nlev; ++L) sl.csize += h->lev[L].A.n;
+    sl.o0 = arena_take(free0_, sl.n0);
+    if (sl.o0 < 0) return -1;
+    sl.oc = arena_take(freec_, sl.csize);
+    if (sl.oc < 0) {
+        arena_give(free0_, sl.o0, sl.n0);
+        return -1;
+    }
+    sl.off[0] = sl.o0;
+    int64_t o = sl.oc;
+    for (int L = 1; L < h->nlev; ++L) {
+        sl.off[L] = o;
+        o += h->lev[L].A.n;
+    }
+    sl.used = true;
+    const int S = (int)slots_.size();
+    const bool mixed = cfg_.mixed != 0;
+    for (int L = 0; L + 1 < h->nlev; ++L) {
+        const Level &lv = h->lev[L];
+        const size_t i = (size_t)L * S + k;
+        const size_t ci = ((size_t)k * kEngLevels + L) * cstride_;
+        cheb_table(lv.lambda_cheb, h->p, &hcoef_[ci]);
+        hA_[i] = SegOp{lv.A.rp, lv.A.ci, mixed ? (const void *)lv.Af : (const void *)lv.A.v,
+                       mixed ? (const void *)lv.invdiag_f : (const void *)lv.invdiag, coef_ + ci, (int)sl.off[L],
+                       (int)sl.off[L]};
+        hP_[i] = SegOp{lv.P.rp, lv.P.ci, mixed ? (const void *)lv.Pf : (const void *)lv.P.v, nullptr, nullptr,
+                       (int)sl.off[L + 1], (int)sl.off[L]};
+        hR_[i] = SegOp{lv.R.rp, lv.R.ci, mixed ? (const void *)lv.Rf : (const void *)lv.R.v, nullptr, nullptr,
+                       (int)sl.off[L], (int)sl.off[L + 1]};
+    }
+    {
+        const int L = h->nlev - 1;
+        hC_[(size_t)L * S + k] = SegCoarse{h->coarse_inv, h->lev[L].A.n, (int)sl.off[L], k, 0};
+    }
+    const Level &l0 = h->lev[0];
+    h0_[k] = SegOp{l0.A.rp, l0.A.ci, l0.A.v, nullptr, nullptr, (int)sl.o0, (int)sl.o0};
+    slots_[k] = sl;
+    members_changed_ = true;
+    return k;
+}
+
+void Engine::remove(int k)
+{
+    if (k < 0 || k >= (int)slots_.size() || !slots_[k].used) return;
+    Slot &sl = slots_[k];
+    arena_give(free0_, sl.o0, sl.n0);
+    arena_give(freec_, sl.oc, sl.csize);
+    if (sl.active) --live_;
+    sl = Slot();
+    members_changed_ = true;
+}
+
+void Engine::load(int k, const double *b, double tol, int max_iter)
+{
+    if (k < 0 || k >= (int)slots_.size() || !slots_[k].used) return;
+    Slot &sl = slots_[k];
+    sl.pending = true;
+    sl.b = b;
+    sl.tol = tol;
+    sl.max_iter = max_iter;
+}
+
+// host lists of every used slot, in slot order, with each list's current lanes per row
+void Engine::build_lists()
+{
+    for (int L = 0; L < kEngLevels; ++L) {
+        lA_[L].host.clear();
+        lP_[L].host.clear();
+        lR_[L].host.clear();
+        lC_[L].host.clear();
+    }
+    l0_.host.clear();
+    lch_.host.clear();
+    nlev_ = 0;
+    const size_t S = slots_.size();
+    for (int k = 0; k < (int)S; ++k) {
+        const Slot &sl = slots_[k];
+        if (!sl.used) continue;
+        const amg_hierarchy *h = sl.h;
+        nlev_ = std::max(nlev_, sl.nlev);
+        for (int L = 0; L + 1 < sl.nlev; ++L) {
+            cut_tiles(lA_[L].host, k, h->lev[L].A.n, kET / lA_[L].lpr);
+            cut_tiles(lP_[L].host, k, h->lev[L].A.n, kET / lP_[L].lpr);
+            cut_tiles(lR_[L].host, k, h->lev[L + 1].A.n, kET / lR_[L].lpr);
+        }
+        lC_[sl.nlev - 1].host.push_back(hC_[(size_t)(sl.nlev - 1) * S + k]);
+        cut_tiles(l0_.host, k, sl.n0, kET / l0_.lpr);
+        const int cnt = (sl.n0 + kEngChunk - 1) / kEngChunk;
+        const int first = (int)lch_.host.size();
+        for (int c = 0; c < cnt; ++c) {
+            const int b0 = (int)sl.o0 + c * kEngChunk;
+            lch_.host.push_back(SegChunk{k, b0, (int)std::min<int64_t>(sl.o0 + sl.n0, b0 + kEngChunk), first, cnt,
+                                         first + c});
+        }
+    }
+}
+
+cudaError_t Engine::upload_lists()
+{
+    bool moved = false;
+    for (int L = 0; L < kEngLevels; ++L) {
+        AMG_CUDA_TRY(upload_list(lA_[L], allocs_, bytes_, s_, &moved));
+        AMG_CUDA_TRY(upload_list(lP_[L], allocs_, bytes_, s_, &moved));
+        AMG_CUDA_TRY(upload_list(lR_[L], allocs_, bytes_, s_, &moved));
+        AMG_CUDA_TRY(upload_list(lC_[L], allocs_, bytes_, s_, &moved));
+    }
+    AMG_CUDA_TRY(upload_list(l0_, allocs_, bytes_, s_, &moved));
+    const size_t old_cap = lch_.capacity;
+    AMG_CUDA_TRY(upload_list(lch_, allocs_, bytes_, s_, &moved));
+    if (!partial_ || lch_.capacity != old_cap) {
+        // chunk partial sums follow the chunk list's capacity (indexed by chunk id)
+        AMG_CUDA_TRY(alloc(&partial_, lch_.capacity));
+        AMG_CUDA_TRY(alloc(&partial2_, lch_.capacity));
+        moved = true;
+    }
+    if (moved) drop_graphs();
+    return cudaStreamSynchronize(s_);   // the host vectors may change after return
+}
+
+cudaError_t Engine::compute_caps()
+{
+    const int S = (int)slots_.size();
+    AMG_CUDA_TRY(cudaMemsetAsync(caps_dev_, 0, sizeof(int) * (3 * kEngLevels + 1), s_));
+    auto span = [&](EngList<SegTile> &l, const SegOp *ops, int idx) -> cudaError_t {
+        if (l.nfull == 0) return cudaSuccess;
+        span_kernel<<<grid_for(l.nfull, 256, 4096), 256, 0, s_>>>(l.full, l.nfull, ops, caps_dev_ + idx); note_launch();
+        return cudaGetLastError();
+    };
+    for (int L = 0; L < nlev_; ++L) {
+        AMG_CUDA_TRY(span(lA_[L], opA_ + (size_t)L * S, 3 * L));
+        AMG_CUDA_TRY(span(lP_[L], opP_ + (size_t)L * S, 3 * L + 1));
+        AMG_CUDA_TRY(span(lR_[L], opR_ + (size_t)L * S, 3 * L + 2));
+    }
+    AMG_CUDA_TRY(span(l0_, op0_, 3 * kEngLevels));
+    int h[3 * kEngLevels + 1];
+    AMG_CUDA_TRY(cudaMemcpyAsync(h, caps_dev_, sizeof h, cudaMemcpyDeviceToHost, s_));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s_));
+    bool changed = false;
+    auto setcap = [&](EngList<SegTile> &l, int span_entries) {
+        const int c = span_entries > 0 ? std::min(kEngMaxTile, span_entries + 8) : 0;
+        if (c != l.cap) changed = true;
+        l.cap = c;
+    };
+    for (int L = 0; L < nlev_; ++L) {
+        setcap(lA_[L], h[3 * L]);
+        setcap(lP_[L], h[3 * L + 1]);
+        setcap(lR_[L], h[3 * L + 2]);
+    }
+    setcap(l0_, h[3 * kEngLevels]);
+    if (changed) drop_graphs();
+    return cudaSuccess;
+}
+
+// active = true: every list by the active mask; false: the fine lists by the flag mask
+cudaError_t Engine::compact(bool active)
+{
+    const int *mask = active ? active_ : flag_;
+    const int ci = active ? 0 : 1;
+    auto one = [&](auto &l) -> cudaError_t {
+        if (!l.count) return cudaSuccess;
+        AMG_CUDA_TRY(cudaMemsetAsync(l.count + ci, 0, sizeof(int), s_));
+        if (l.nfull == 0) return cudaSuccess;
+        compact_kernel<<<grid_for(l.nfull, 256, 2048), 256, 0, s_>>>(l.full, l.nfull, mask, active ? l.act : l.flg,
+                                                                     l.count + ci); note_launch();
+        return cudaGetLastError();
+    };
+    if (active) {
+        for (int L = 0; L < nlev_; ++L) {
+            AMG_CUDA_TRY(one(lA_[L]));
+            AMG_CUDA_TRY(one(lP_[L]));
+            AMG_CUDA_TRY(one(lR_[L]));
+            AMG_CUDA_TRY(one(lC_[L]));
+        }
+    }
+    AMG_CUDA_TRY(one(l0_));
+    AMG_CUDA_TRY(one(lch_));
+    return cudaSuccess;
+}
+
+cudaError_t Engine::push_flags(const std::vector<int> &v, int *dst)
+{
+    int *h = dst == active_ ? hflags_ : hflags_ + slots_.size();
+    for (size_t i = 0; i < v.size(); ++i) h[i] = v[i];
+    return cudaMemcpyAsync(dst, h, sizeof(int) * v.size(), cudaMemcpyHostToDevice, s_);
+}
+
+// Lanes per row of every tile list, chosen by timing each candidate on the current members
+// (y = A x into the list's own scratch vectors); the winners are kept.
+cudaError_t Engine::autotune()
+{
+    const int S = (int)slots_.size();
+    cudaEvent_t e0, e1;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    cudaError_t err = cudaSuccess;
+    build_lists();
+    const int nl = nlev_;
+    for (int li = 0; li <= 3 * nl && err == cudaSuccess; ++li) {
+        const bool fine = li == 3 * nl;
+        const int L = fine ? 0 : li / 3, kind = fine ? 3 : li % 3;
+        if (!fine && L + 1 >= nl) continue;
+        EngList<SegTile> &l = fine ? l0_ : (kind == 0 ? lA_[L] : (kind == 1 ? lP_[L] : lR_[L]));
+        const SegOp *ops = fine ? op0_ : (kind == 0 ? opA_ : (kind == 1 ? opP_ : opR_)) + (size_t)L * S;
+        double best = 1e300;
+        int best_lpr = l.lpr;
+        for (int lpr : kLprs) {
+            l.lpr = lpr;
+            build_lists();
+            if (l.host.empty()) break;
+            if ((err = upload_lists()) != cudaSuccess) break;
+            if ((err = compute_caps()) != cudaSuccess) break;
+            set_count_kernel<<<1, 1, 0, s_>>>(l.count + 2, l.nfull); note_launch();
+            // x: the level's (or, for P, the next level's) iterate; y: a scratch vector
+            const bool coarse_cols = kind == 1 || L > 0;
+            auto run = [&]() -> cudaError_t {
+                if (fine)
+                    return seg_launch<double, SK_Y>(lpr, l.full, l.count + 2, ops, x_, q_, nullptr, nullptr, 0, l.cap,
+                                                    1 << 30, s_);
+                void *xs = (kind == 2) ? (L == 0 ? r0_ : rc_) : (coarse_cols ? xc_ : x0_);
+                void *ys = (kind == 2) ? fc_ : (L == 0 ? x20_ : x2c_);
+                if (cfg_.mixed)
+                    return seg_launch<float, SK_Y>(lpr, l.full, l.count + 2, ops, (const float *)xs, (float *)ys,
+                                                   nullptr, nullptr, 0, l.cap, 1 << 30, s_);
+                return seg_launch<double, SK_Y>(lpr, l.full, l.count + 2, ops, (const double *)xs, (double *)ys,
+                                                nullptr, nullptr, 0, l.cap, 1 << 30, s_);
+            };
+            if ((err = run()) != cudaSuccess) break;
+            if ((err = cudaEventRecord(e0, s_)) != cudaSuccess) break;
+            for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run();
+            if (err != cudaSuccess || (err = cudaEventRecord(e1, s_)) != cudaSuccess) break;
+            if ((err = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float ms = 0.f;
+            if ((err = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+            if (ms < best) { best = ms; best_lpr = lpr; }
+        }
+        l.lpr = best_lpr;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err;
+}
+
+// lanes per row from each list's mean row length (deterministic; the autotuner's fallback)
+void Engine::heuristic_lanes()
+{
+    double rows[3][kEngLevels] = {}, nnz[3][kEngLevels] = {}, r0 = 0, z0 = 0;
+    for (const Slot &sl : slots_) {
+        if (!sl.used) continue;
+        const amg_hierarchy *h = sl.h;
+        r0 += h->lev[0].A.n;
+        z0 += (double)h->lev[0].A.nnz;
+        for (int L = 0; L + 1 < sl.nlev; ++L) {
+            const Level &lv = h->lev[L];
+            rows[0][L] += lv.A.n; nnz[0][L] += (double)lv.A.nnz;
+            rows[1][L] += lv.P.n; nnz[1][L] += (double)lv.P.nnz;
+            rows[2][L] += lv.R.n; nnz[2][L] += (double)lv.R.nnz;
+        }
+    }
+    auto pick = [](double z, double r) { return pick_lanes(r > 0 ? z / r : 1.0); };
+    l0_.lpr = pick(z0, r0);
+    for (int L = 0; L < kEngLevels; ++L) {
+        lA_[L].lpr = pick(nnz[0][L], rows[0][L]);
+        lP_[L].lpr = pick(nnz[1][L], rows[1][L]);
+        lR_[L].lpr = pick(nnz[2][L], rows[2][L]);
+    }
+}
+
+std::string Engine::describe() const
+{
+    std::string s = "fine:" + std::to_string(l0_.lpr);
+    for (int L = 0; L + 1 < nlev_; ++L)
+        s += " L" + std::to_string(L) + ":A" + std::to_string(lA_[L].lpr) + "/P" + std::to_string(lP_[L].lpr) + "/R" +
+             std::to_string(lR_[L].lpr);
+    return s;
+}
+
+amg_status_t Engine::commit()
+{
+    const int S = (int)slots_.size();
+    if (members_changed_) {
+        EK(cudaMemcpyAsync(opA_, hA_.data(), sizeof(SegOp) * hA_.size(), cudaMemcpyHostToDevice, s_));
+        EK(cudaMemcpyAsync(opP_, hP_.data(), sizeof(SegOp) * hP_.size(), cudaMemcpyHostToDevice, s_));
+        EK(cudaMemcpyAsync(opR_, hR_.data(), sizeof(SegOp) * hR_.size(), cudaMemcpyHostToDevice, s_));
+        EK(cudaMemcpyAsync(op0_, h0_.data(), sizeof(SegOp) * h0_.size(), cudaMemcpyHostToDevice, s_));
+        EK(cudaMemcpyAsync(opC_, hC_.data(), sizeof(SegCoarse) * hC_.size(), cudaMemcpyHostToDevice, s_));
+        EK(cudaMemcpyAsync(coef_, hcoef_.data(), sizeof(double) * hcoef_.size(), cudaMemcpyHostToDevice, s_));
+        const int old_nlev = nlev_;
+        build_lists();
+        if (!tuned_ && !l0_.host.empty()) {
+            if (cfg_.tune) EK(autotune());
+            else heuristic_lanes();
+            tuned_ = true;
+            build_lists();
+        }
+        EK(upload_lists());
+        EK(compute_caps());
+        if (old_nlev != nlev_) drop_graphs();
+        members_changed_ = false;
+    }
+    // solves to start
+    std::vector<int> flags((size_t)S, 0);
+    bool any = false;
+    for (int k = 0; k < S; ++k) {
+        Slot &sl = slots_[k];
+        if (!sl.used || !sl.pending) continue;
+        flags[k] = 1;
+        any = true;
+        if (sl.n0 > 0) EK(cudaMemcpyAsync(b_ + sl.o0, sl.b, sizeof(double) * (size_t)sl.n0, cudaMemcpyDefault, s_));
+        if (sl.active) {
+            sl.active = 0;
+            --live_;
+        }
+    }
+    if (!any) {
+        std::vector<int> act((size_t)S, 0);
+        for (int k = 0; k < S; ++k) act[k] = slots_[k].active;
+        EK(push_flags(act, active_));
+        EK(compact(true));
+        return AMG_OK;
+    }
+    EK(push_flags(flags, flag_));
+    EK(compact(false));
+    {
+        const int parity_next = cfg_.mixed ? (it_ & 1) : 0;
+        double *zp = cfg_.mixed ? zb_[1 - parity_next] : nullptr;
+        eng_init_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, x_, r_, p_, zp, sc_); note_launch();
+        eng_norm_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, partial_, ticket_, sc_, 0); note_launch();
+        EK(cudaGetLastError());
+    }
+    std::vector<EngScal> hs((size_t)S);
+    EK(cudaMemcpyAsync(hs.data(), sc_, sizeof(EngScal) * S, cudaMemcpyDeviceToHost, s_));
+    EK(cudaStreamSynchronize(s_));
+    std::vector<int> act((size_t)S, 0);
+    for (int k = 0; k < S; ++k) {
+        Slot &sl = slots_[k];
+        act[k] = sl.active;
+        if (!flags[k]) continue;
+        sl.pending = false;
+        sl.iters = 0;
+        sl.nb = sl.n0 > 0 ? std::sqrt(hs[k].bb) : 0.0;
+        sl.relres = 0.0;
+        sl.result = sl.nb == 0.0 ? AMG_OK : AMG_ERR_NOT_CONVERGED;
+        sl.active = sl.nb > 0.0 && sl.max_iter > 0 ? 1 : 0;
+        act[k] = sl.active;
+        live_ += sl.active;
+    }
+    EK(push_flags(act, active_));
+    EK(compact(true));
+    return AMG_OK;
+}
+
+template <typename T>
+cudaError_t Engine::vcycle(int L, const T *f, T *final_out, T **out, cudaStream_t s)
+{
+    const int S = (int)slots_.size();
+    T *x = (T *)(L == 0 ? x0_ : xc_), *x2 = (T *)(L == 0 ? x20_ : x2c_);
+    T *rv = (T *)(L == 0 ? r0_ : rc_), *d = (T *)(L == 0 ? d0_ : dc_);
+    auto coarse = [&](T *dst) -> cudaError_t {
+        if (lC_[L].nfull == 0) return cudaSuccess;
+        segcoarse_kernel<T><<<grid_tiles_, kET, 0, s>>>(lC_[L].act, lC_[L].count, f, dst); note_launch();
+        return cudaGetLastError();
+    };
+    if (L == nlev_ - 1) {
+        *out = final_out ? final_out : x;
+        return coarse(*out);
+    }
+    const SegOp *opA = opA_ + (size_t)L * S, *opP = opP_ + (size_t)L * S, *opR = opR_ + (size_t)L * S;
+    EngList<SegTile> &la = lA_[L], &lp = lP_[L], &lr = lR_[L];
+    const int deg = cfg_.degree;
+    segcheb0_kernel<T><<<grid_tiles_, kET, 0, s>>>(la.act, la.count, opA, f, d, x); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    for (int k = 1; k < deg; ++k) {
+        AMG_CUDA_TRY((seg_launch<T, SK_CHEB>(la.lpr, la.act, la.count, opA, x, x2, f, d, 1 + 2 * k, la.cap,
+                                             1 << 30, s)));
+        std::swap(x, x2);
+    }
+    T *fc = (T *)fc_;
+    AMG_CUDA_TRY((seg_launch<T, SK_RESID>(la.lpr, la.act, la.count, opA, x, rv, f, nullptr, 0, la.cap, 1 << 30, s)));
+    AMG_CUDA_TRY((seg_launch<T, SK_Y>(lr.lpr, lr.act, lr.count, opR, rv, fc, nullptr, nullptr, 0, lr.cap, grid_tiles_,
+                                      s)));
+    T *xcv = nullptr;
+    AMG_CUDA_TRY(vcycle<T>(L + 1, fc, nullptr, &xcv, s));
+    AMG_CUDA_TRY((seg_launch<T, SK_PROLONG>(lp.lpr, lp.act, lp.count, opP, xcv, x, nullptr, nullptr, 0, lp.cap,
+                                            1 << 30, s)));
+    for (int k = 0; k < deg; ++k) {
+        T *dst = (final_out && k == deg - 1) ? final_out : x2;
+        AMG_CUDA_TRY((seg_launch<T, SK_CHEB>(la.lpr, la.act, la.count, opA, x, dst, f, d, 1 + 2 * k, la.cap,
+                                             1 << 30, s)));
+        x2 = x;
+        x = dst;
+    }
+    *out = x;
+    return coarse(x);
+}
+
+cudaError_t Engine::tail(int parity, cudaStream_t s)
+{
+    double *z = zb_[cfg_.mixed ? parity : 0];
+    double *zp = cfg_.mixed ? zb_[1 - parity] : nullptr;
+    if (nlev_ > 0) {
+        if (cfg_.mixed) {
+            eng_convert_kernel<double, float><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, r_, (float *)f0_); note_launch();
+            AMG_CUDA_TRY(cudaGetLastError());
+            float *out = nullptr;
+            AMG_CUDA_TRY(vcycle<float>(0, (const float *)f0_, nullptr, &out, s));
+            eng_convert_kernel<float, double><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z); note_launch();
+            AMG_CUDA_TRY(cudaGetLastError());
+        } else {
+            double *out = nullptr;
+            AMG_CUDA_TRY(vcycle<double>(0, r_, z, &out, s));
+            if (out != z) {
+                eng_copy_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z); note_launch();
+                AMG_CUDA_TRY(cudaGetLastError());
+            }
+        }
+    }
+    eng_rz_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, r_, z, zp, partial_, partial2_, ticket_, ticket2_,
+                                               sc_); note_launch();
+    eng_p_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, z, p_, sc_, zp ? 1 : 0); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t Engine::head(cudaStream_t s)
+{
+    AMG_CUDA_TRY((seg_launch<double, SK_Y>(l0_.lpr, l0_.act, l0_.count, op0_, p_, q_, nullptr, nullptr, 0, l0_.cap,
+                                           1 << 30, s)));
+    eng_pq_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, partial_, ticket_, sc_); note_launch();
+    eng_xr_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, x_, r_, partial_, ticket_, sc_, rr_dev_); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    return cudaMemcpyAsync(rr_host_, rr_dev_, sizeof(double) * slots_.size(), cudaMemcpyDeviceToHost, s);
+}
+
+cudaError_t Engine::true_residual(cudaStream_t s)
+{
+    AMG_CUDA_TRY((seg_launch<double, SK_RESID>(l0_.lpr, l0_.flg, l0_.count + 1, op0_, x_, t_, b_, nullptr, 0, l0_.cap,
+                                               1 << 30, s)));
+    eng_norm_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.flg, lch_.count + 1, t_, partial_, ticket_, sc_, 1); note_launch();
+    return cudaGetLastError();
+}
+
+cudaGraphExec_t Engine::graph(int parity)
+{
+    if (graph_failed_) return nullptr;
+    if (gexec_[parity]) return gexec_[parity];
+    cudaGraph_t g = nullptr;
+    const long long before = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = tail(parity, cap_);
+        cudaError_t e2 = e1 == cudaSuccess ? head(cap_) : e1;
+        e = cudaStreamEndCapture(cap_, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec_[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        graph_failed_ = true;       // iterations run eagerly from now on
+        gexec_[parity] = nullptr;
+        return nullptr;
+    }
+    gkernels_[parity] = launch_count() - before;
+    note_launches(-gkernels_[parity]);
+    return gexec_[parity];
+}
+
+amg_status_t Engine::step(std::vector<int> *finished)
+{
+    if (finished) finished->clear();
+    if (live_ == 0) return AMG_OK;
+    const int S = (int)slots_.size();
+    const int parity = cfg_.mixed ? (it_ & 1) : 0;
+    cudaGraphExec_t gx = graph(parity);
+    if (gx) {
+        EK(cudaGraphLaunch(gx, s_));
+        note_launches(gkernels_[parity]);
+    } else {
+        EK(tail(parity, s_));
+        EK(head(s_));
+    }
+    ++it_;
+    for (auto &sl : slots_)
+        if (sl.used && sl.active) ++sl.iters;
+    EK(cudaStreamSynchronize(s_));
+    std::vector<int> flags((size_t)S, 0), act((size_t)S, 0);
+    std::vector<int> stopped;
+    bool any = false;
+    for (int k = 0; k < S; ++k) {
+        const Slot &sl = slots_[k];
+        act[k] = sl.active;
+        if (sl.active && std::sqrt(rr_host_[k]) / sl.nb <= sl.tol) { flags[k] = 1; any = true; }
+    }
+    std::vector<EngScal> hs((size_t)S);
+    if (any) {
+        // the recurrence says converged: check b - A x of those slots
+        EK(push_flags(flags, flag_));
+        EK(compact(false));
+        EK(true_residual(s_));
+        EK(cudaMemcpyAsync(hs.data(), sc_, sizeof(EngScal) * S, cudaMemcpyDeviceToHost, s_));
+        EK(cudaStreamSynchronize(s_));
+        bool replace = false;
+        for (int k = 0; k < S; ++k) {
+            if (!flags[k]) continue;
+            Slot &sl = slots_[k];
+            const double rel = std::sqrt(hs[k].tt) / sl.nb;
+            if (rel <= sl.tol) {
+                sl.active = 0;
+                act[k] = 0;
+                sl.result = AMG_OK;
+                sl.relres = rel;
+                flags[k] = 0;
+                stopped.push_back(k);
+            } else {
+                replace = true;     // flags[k] stays set: r = b - A x for this slot
+            }
+        }
+        if (replace) {
+            EK(push_flags(flags, flag_));
+            EK(compact(false));
+            eng_copy_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, t_, r_); note_launch();
+            EK(cudaGetLastError());
+        }
+    }
+    // iteration limits: stop, with the true residual of the last iterate
+    std::fill(flags.begin(), flags.end(), 0);
+    bool limit = false;
+    for (int k = 0; k < S; ++k) {
+        Slot &sl = slots_[k];
+        if (sl.active && sl.iters >= sl.max_iter) {
+            sl.active = 0;
+            act[k] = 0;
+            sl.result = AMG_ERR_NOT_CONVERGED;
+            flags[k] = 1;
+            limit = true;
+            stopped.push_back(k);
+        }
+    }
+    if (limit) {
+        EK(push_flags(flags, flag_));
+        EK(compact(false));
+        EK(true_residual(s_));
+        EK(cudaMemcpyAsync(hs.data(), sc_, sizeof(EngScal) * S, cudaMemcpyDeviceToHost, s_));
+        EK(cudaStreamSynchronize(s_));
+        for (int k = 0; k < S; ++k)
+            if (flags[k]) slots_[k].relres = std::sqrt(hs[k].tt) / slots_[k].nb;
+    }
+    if (!stopped.empty()) {
+        live_ -= (int)stopped.size();
+        EK(push_flags(act, active_));
+        EK(compact(true));
+        if (finished) *finished = stopped;
+    }
+    return AMG_OK;
+}
+
+amg_status_t Engine::download(int k, double *x)
+{
+    const Slot &sl = slots_[k];
+    if (sl.n0 == 0) return AMG_OK;
+    EK(cudaMemcpyAsync(x, x_ + sl.o0, sizeof(double) * (size_t)sl.n0, cudaMemcpyDefault, s_));
+    EK(cudaStreamSynchronize(s_));
+    return AMG_OK;
+}
+
+#undef EK
+
 }  // namespace amgk
+
+// ====================================================================================== batch ABI
+
+struct amg_batch {
+    amgk::Engine eng;
+    std::vector<int> slot;              // caller's index -> engine slot
+    std::vector<amg_hierarchy *> h;
+};
 
 using namespace amgk;
 
@@ -883,34 +1219,47 @@ amg_status_t amg_setup_batch(int count, const amg_csr_t *const *A, const double 
     return AMG_OK;
 }
 
-amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_stream, amg_batch_t *out)
+amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_stream, int tune, amg_batch_t *out)
 {
     if (!out) return AMG_ERR_INVALID_ARG;
     *out = nullptr;
     if (count < 0 || (count > 0 && !h)) return AMG_ERR_INVALID_ARG;
-    if (count > 65535) {
-        set_last_error("at most 65535 systems per batch");
-        return AMG_ERR_UNSUPPORTED;
-    }
     for (int k = 0; k < count; ++k) {
         if (!h[k]) return AMG_ERR_INVALID_ARG;
         if (h[k]->p.precision != h[0]->p.precision || h[k]->p.cheb_degree != h[0]->p.cheb_degree) {
             set_last_error("all systems of a batch need the same precision and Chebyshev degree");
             return AMG_ERR_INVALID_ARG;
         }
+        if (h[k]->nlev > kEngLevels) {
+            set_last_error("a hierarchy deeper than the batch engine's level limit");
+            return AMG_ERR_UNSUPPORTED;
+        }
+    }
+    Engine::Config cfg;
+    cfg.mixed = count > 0 && h[0]->p.precision == AMG_MIXED;
+    cfg.degree = count > 0 ? h[0]->p.cheb_degree : 2;
+    cfg.slots = count;
+    cfg.tune = tune != 0;
+    for (int k = 0; k < count; ++k) {
+        cfg.cap0 += h[k]->lev[0].A.n;
+        for (int L = 1; L < h[k]->nlev; ++L) cfg.capc += h[k]->lev[L].A.n;
+    }
+    if (cfg.cap0 > 0x7ffffff0LL || cfg.capc > 0x7ffffff0LL) {
+        set_last_error("batch too large for 32-bit vector offsets");
+        return AMG_ERR_UNSUPPORTED;
     }
     amg_batch *Bt = new amg_batch();
-    Bt->s = (cudaStream_t)cuda_stream;
-    Bt->mixed = count > 0 && h[0]->p.precision == AMG_MIXED;
-    Bt->degree = count > 0 ? h[0]->p.cheb_degree : 2;
-    Bt->cstride = 1 + 2 * Bt->degree;
-    amg_status_t st = batch_assemble(Bt, h, count);
-    if (st == AMG_OK) {
-        cudaError_t e = cudaStreamSynchronize(Bt->s);
-        if (e != cudaSuccess) st = fail_cuda(e, "amg_batch_create");
+    amg_status_t st = Bt->eng.init(cfg, (cudaStream_t)cuda_stream);
+    for (int k = 0; k < count && st == AMG_OK; ++k) {
+        const int s = Bt->eng.add(h[k]);
+        if (s < 0) {
+            set_last_error("batch engine has no room for a system");
+            st = AMG_ERR_INTERNAL;
+        }
+        Bt->slot.push_back(s);
+        Bt->h.push_back(h[k]);
     }
     if (st != AMG_OK) {
-        batch_release(Bt);
         delete Bt;
         return st;
     }
@@ -920,8 +1269,6 @@ amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_strea
 
 amg_status_t amg_batch_free(amg_batch_t Bt)
 {
-    if (!Bt) return AMG_OK;
-    batch_release(Bt);
     delete Bt;
     return AMG_OK;
 }
@@ -929,148 +1276,44 @@ amg_status_t amg_batch_free(amg_batch_t Bt)
 amg_status_t amg_batch_solve(amg_batch_t Bt, const double *const *b, double *const *x, double tol, amg_info_t *infos)
 {
     if (!Bt) return AMG_ERR_INVALID_ARG;
-    const int C = Bt->count;
+    const int C = (int)Bt->slot.size();
     if (C > 0 && (!b || !x)) return AMG_ERR_INVALID_ARG;
     if (!(tol >= 0.0)) return AMG_ERR_INVALID_ARG;
-    for (int k = 0; k < C; ++k) {
-        const int u = Bt->order[k];
-        if (Bt->off0[k + 1] > Bt->off0[k] && (!b[u] || !x[u])) return AMG_ERR_INVALID_ARG;
-    }
-    const double t0 = now_ms();
-    amg_status_t st = AMG_OK;
-    cudaStream_t s = Bt->s;
-    const size_t n = (size_t)Bt->total;
-    const int nc = Bt->nchunks;
-    std::vector<int> iters((size_t)C, 0);
-    std::vector<amg_status_t> result((size_t)C, AMG_ERR_NOT_CONVERGED);
-    std::vector<double> nb((size_t)C, 0.0), relres((size_t)C, 0.0);
-    std::vector<BScal> hs((size_t)C);
-    int *act = Bt->host_flags, *flg = Bt->host_flags + C;
-    const double *hrr = Bt->rr_host;
-    int it = 0, live = 0;
-    auto push_flags = [&](const int *src, int *dst) -> cudaError_t {
-        return cudaMemcpyAsync(dst, src, sizeof(int) * (size_t)C, cudaMemcpyHostToDevice, s);
-    };
-    auto pull_scalars = [&]() -> cudaError_t {
-        AMG_CUDA_TRY(cudaMemcpyAsync(hs.data(), Bt->sc, sizeof(BScal) * (size_t)C, cudaMemcpyDeviceToHost, s));
-        return cudaStreamSynchronize(s);
-    };
-    if (C == 0) goto finish;
-    CKB(cudaMemsetAsync(Bt->sc, 0, sizeof(BScal) * (size_t)C, s));
-    // right-hand sides into batch order
-    for (int k = 0; k < C; ++k) {
-        const size_t len = (size_t)(Bt->off0[k + 1] - Bt->off0[k]);
-        if (len) CKB(cudaMemcpyAsync(Bt->b + Bt->off0[k], b[Bt->order[k]], sizeof(double) * len, cudaMemcpyDefault, s));
-    }
-    if (n > 0) {
-        CKB(cudaMemsetAsync(Bt->x, 0, sizeof(double) * n, s));
-        CKB(cudaMemcpyAsync(Bt->r, Bt->b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        bdot_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, nullptr, Bt->b, nullptr, nullptr, Bt->partial, Bt->ticket,
-                                             Bt->sc, 0); note_launch();
-        CKB(cudaGetLastError());
-    }
-    CKB(pull_scalars());
-    for (int k = 0; k < C; ++k) {
-        nb[k] = std::sqrt(hs[k].bb);
-        act[k] = nb[k] > 0.0 && Bt->max_iter[k] > 0 ? 1 : 0;
-        flg[k] = 0;
-        if (nb[k] == 0.0) result[k] = AMG_OK;
-        live += act[k];
-    }
-    CKB(push_flags(act, Bt->active));
-    if (live == 0) goto finish;
-    // z = M^-1 r, p = z, r . z; then the first head
-    CKB(bprecond(Bt, Bt->r, Bt->zb[0], s));
-    bdot_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->active, Bt->r, Bt->zb[0], Bt->pv, Bt->partial, Bt->ticket,
-                                         Bt->sc, 2); note_launch();
-    CKB(cudaGetLastError());
-    CKB(bhead(Bt, s));
-    it = 1;
-    for (int k = 0; k < C; ++k) iters[k] += act[k];
-    for (;;) {
-        CKB(cudaStreamSynchronize(s));
-        bool any_flag = false, changed = false;
-        for (int k = 0; k < C; ++k) {
-            flg[k] = act[k] && std::sqrt(hrr[k]) / nb[k] <= tol ? 1 : 0;
-            any_flag |= flg[k] != 0;
-        }
-        if (any_flag) {
-            // the recursive residual says converged: check b - A x of those systems
-            CKB(push_flags(flg, Bt->flag));
-            CKB(btrue_residual(Bt, Bt->flag, s));
-            CKB(pull_scalars());
-            bool replace = false;
-            for (int k = 0; k < C; ++k) {
-                if (!flg[k]) continue;
-                if (std::sqrt(hs[k].tt) / nb[k] <= tol) {
-                    act[k] = 0;
-                    flg[k] = 0;
-                    result[k] = AMG_OK;
-                    changed = true;
-                } else {
-                    replace = true;     // flg[k] stays set: r = b - A x for this system
-                }
-            }
-            if (replace) {
-                CKB(push_flags(flg, Bt->flag));
-                bcopy_flagged_kernel<<<nc, kBThreads, 0, s>>>(Bt->chunks, Bt->flag, Bt->t, Bt->r); note_launch();
-                CKB(cudaGetLastError());
-            }
-        }
-        live = 0;
-        for (int k = 0; k < C; ++k) {
-            if (act[k] && iters[k] >= Bt->max_iter[k]) { act[k] = 0; changed = true; }
-            live += act[k];
-        }
-        if (live == 0) break;
-        if (changed) CKB(push_flags(act, Bt->active));
-        const int parity = Bt->zb[1] ? (it & 1) : 0;
-        cudaGraphExec_t gx = bgraph(Bt, parity);
-        if (gx) {
-            CKB(cudaGraphLaunch(gx, s));
-            note_launches(Bt->gkernels[parity]);
-        } else {
-            CKB(btail(Bt, parity, s));
-            CKB(bhead(Bt, s));
-        }
-        ++it;
-        for (int k = 0; k < C; ++k) iters[k] += act[k];
-    }
-finish:
-    if (C > 0 && n > 0) {
-        CKB(btrue_residual(Bt, nullptr, s));
-        for (int k = 0; k < C; ++k) {
-            const size_t len = (size_t)(Bt->off0[k + 1] - Bt->off0[k]);
-            if (len)
-                CKB(cudaMemcpyAsync(x[Bt->order[k]], Bt->x + Bt->off0[k], sizeof(double) * len, cudaMemcpyDefault, s));
-        }
-        CKB(pull_scalars());
-        for (int k = 0; k < C; ++k) relres[k] = nb[k] > 0.0 ? std::sqrt(hs[k].tt) / nb[k] : 0.0;
-    }
-    st = AMG_OK;
     for (int k = 0; k < C; ++k)
-        if (result[k] != AMG_OK) st = AMG_ERR_NOT_CONVERGED;
-    if (spmv_take_errors(s) != 0) {
-        set_last_error("a bulk copy into shared memory did not complete in time");
-        st = AMG_ERR_INTERNAL;
-        for (int k = 0; k < C; ++k) result[k] = AMG_ERR_INTERNAL;
+        if (Bt->eng.slot(Bt->slot[k]).n0 > 0 && (!b[k] || !x[k])) return AMG_ERR_INVALID_ARG;
+    const double t0 = now_ms();
+    Engine &E = Bt->eng;
+    for (int k = 0; k < C; ++k) E.load(Bt->slot[k], b[k], tol, Bt->h[k]->p.max_iter);
+    amg_status_t st = E.commit();
+    while (st == AMG_OK && E.live() > 0) st = E.step(nullptr);
+    for (int k = 0; k < C && st == AMG_OK; ++k) st = E.download(Bt->slot[k], x[k]);
+    amg_status_t overall = st;
+    if (st == AMG_OK) {
+        for (int k = 0; k < C; ++k)
+            if (E.slot(Bt->slot[k]).result != AMG_OK) overall = AMG_ERR_NOT_CONVERGED;
+        if (spmv_take_errors(nullptr) != 0) {
+            set_last_error("a bulk copy into shared memory did not complete in time");
+            overall = AMG_ERR_INTERNAL;
+        }
     }
-done:
     if (infos) {
         const double ms = now_ms() - t0;
-        const bool per_system = st == AMG_OK || st == AMG_ERR_NOT_CONVERGED || st == AMG_ERR_INTERNAL;
         for (int k = 0; k < C; ++k) {
-            amg_info_t &in = infos[Bt->order[k]];
-            in.iters = iters[k];
-            in.status = per_system ? result[k] : st;
-            in.relres_true = relres[k];
-            in.setup_ms = Bt->setup_ms[k];
+            const Engine::Slot &sl = E.slot(Bt->slot[k]);
+            const amg_hierarchy *h = Bt->h[k];
+            amg_info_t &in = infos[k];
+            in.iters = sl.iters;
+            in.status = (st == AMG_OK && overall != AMG_ERR_INTERNAL) ? sl.result : overall;
+            in.relres_true = sl.relres;
+            in.setup_ms = h->setup_ms;
             in.solve_ms = ms;
-            in.levels = Bt->nlev_sys[k];
-            in.op_complexity = Bt->opc[k];
+            in.levels = h->nlev;
+            double tot = 0.0;
+            for (int L = 0; L < h->nlev; ++L) tot += (double)h->lev[L].A.nnz;
+            in.op_complexity = h->fine_nnz > 0 ? tot / (double)h->fine_nnz : 0.0;
         }
     }
-    return st;
+    return overall;
 }
 
 amg_status_t amg_solve_batch(int count, const amg_handle_t *h, const double *const *b, double *const *x, double tol,
@@ -1080,7 +1323,7 @@ amg_status_t amg_solve_batch(int count, const amg_handle_t *h, const double *con
     for (int k = 0; k < count; ++k)
         if (!h[k]) return AMG_ERR_INVALID_ARG;
     amg_batch_t Bt = nullptr;
-    amg_status_t st = amg_batch_create(count, h, count > 0 ? h[0]->p.cuda_stream : nullptr, &Bt);
+    amg_status_t st = amg_batch_create(count, h, count > 0 ? h[0]->p.cuda_stream : nullptr, 0, &Bt);
     if (st != AMG_OK) return st;
     st = amg_batch_solve(Bt, b, x, tol, infos);
     amg_batch_free(Bt);
@@ -1090,10 +1333,12 @@ amg_status_t amg_solve_batch(int count, const amg_handle_t *h, const double *con
 amg_status_t amg_batch_info(amg_batch_t Bt, int *count, int *levels, int64_t *rows, int64_t *graph_kernels)
 {
     if (!Bt) return AMG_ERR_INVALID_ARG;
-    if (count) *count = Bt->count;
-    if (levels) *levels = Bt->nlev;
-    if (rows) *rows = Bt->total;
-    if (graph_kernels) *graph_kernels = Bt->gkernels[0];
+    int64_t tot = 0;
+    for (int k = 0; k < (int)Bt->slot.size(); ++k) tot += Bt->eng.slot(Bt->slot[k]).n0;
+    if (count) *count = (int)Bt->slot.size();
+    if (levels) *levels = Bt->eng.levels();
+    if (rows) *rows = tot;
+    if (graph_kernels) *graph_kernels = Bt->eng.kernels_per_iteration();
     return AMG_OK;
 }
 

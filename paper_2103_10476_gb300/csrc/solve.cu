@@ -31,19 +31,8 @@ enum SpmvMode {
     MODE_PROLONG = 3,    // y += A x
     MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
     MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
-    MODE_CHEB_SEG = 6,   // MODE_CHEB with c1, c2 of the row's system: coef[rowsys[i] * cstride + {0, 1}]
 };
 
-template <typename T>
-__host__ __device__ constexpr int tile_values_bytes(int cap)
-{
-    return ((cap + 2 * (16 / (int)sizeof(T))) * (int)sizeof(T) + 127) / 128 * 128;
-}
-template <typename T>
-__host__ __device__ constexpr int tile_bytes(int cap)
-{
-    return cap > 0 ? tile_values_bytes<T>(cap) + (cap + 8) * 4 : 0;
-}
 
 // Fixed-order completion of a two-stage sum: the block that arrives last (atomic ticket)
 // adds every block's partial in index order -- the same order whichever block is last -- and
@@ -82,10 +71,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
                                                                  int cap, double *partial, double *result,
-                                                                 unsigned *counter, int *err,
-                                                                 const int *__restrict__ rowsys,
-                                                                 const double *__restrict__ coef, int cstride,
-                                                                 const int *__restrict__ active)
+                                                                 unsigned *counter, int *err)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -93,15 +79,6 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     constexpr int VA = 16 / (int)sizeof(T);
     const int r0 = blockIdx.x * RPB;
     const int r1 = min(n, r0 + RPB);
-    const int row = r0 + threadIdx.x / LPR;
-    const int lane = threadIdx.x % LPR;
-    bool on = row < r1;
-    if (MODE != MODE_DOT && MODE != MODE_SCALEDOT && active) {
-        // batched operators: rows of systems that have stopped are skipped, and so is a block
-        // with no other row (before it stages anything)
-        on = on && active[rowsys[row]] != 0;
-        if (!__syncthreads_or(on)) return;
-    }
     const int k0 = rp[r0], k1 = rp[r1];
     const int k0v = k0 & ~(VA - 1), k1v = (k1 + VA - 1) & ~(VA - 1);
     const int k0i = k0 & ~3, k1i = (k1 + 3) & ~3;
@@ -120,8 +97,10 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         }
         tile_ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, err));
     }
+    const int row = r0 + threadIdx.x / LPR;
+    const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    if (on && tile_ok) {
+    if (row < r1 && tile_ok) {
         const int b = rp[row], e = rp[row + 1];
         if (staged) {
             for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
@@ -132,17 +111,12 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
     double contrib = 0.0;
-    if (on && lane == 0 && tile_ok) {
+    if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
         } else if (MODE == MODE_RESID) {
             y[row] = f[row] - sum;
-        } else if (MODE == MODE_CHEB || MODE == MODE_CHEB_SEG) {
-            if (MODE == MODE_CHEB_SEG) {
-                const double *cs = coef + (size_t)rowsys[row] * cstride;
-                c1 = (T)cs[0];
-                c2 = (T)cs[1];
-            }
+        } else if (MODE == MODE_CHEB) {
             T r = f[row] - sum;
             T dn = c1 * d[row] + c2 * (aux[row] * r);
             d[row] = dn;
@@ -241,7 +215,7 @@ int spmv_take_errors(cudaStream_t s)
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
-                        const int *rowsys, const double *coef, int cstride, const int *active, cudaStream_t s)
+                        cudaStream_t s)
 {
     const int smem = tile_bytes<T>(cap);
     // the attribute is set once per instantiation (any thread may get here first)
@@ -253,59 +227,26 @@ cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T
     });
     AMG_CUDA_TRY(cfg_err);
     spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), rowsys, coef,
-        cstride, active); note_launch();
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag()); note_launch();
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
                       const T *f, const T *aux, T *d, T c1, T c2, double *partial, cudaStream_t s,
-                      double *result = nullptr, unsigned *counter = nullptr, const int *rowsys = nullptr,
-                      const double *coef = nullptr, int cstride = 0, const int *active = nullptr)
+                      double *result = nullptr, unsigned *counter = nullptr)
 {
     if (n == 0) return cudaSuccess;
-#define AMG_TILE_CASE(L)                                                                                    \
-    return launch_tile<T, L, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, \
-                                   rowsys, coef, cstride, active, s)
     switch (pl.lpr) {
-    case 2: AMG_TILE_CASE(2);
-    case 4: AMG_TILE_CASE(4);
-    case 8: AMG_TILE_CASE(8);
-    case 16: AMG_TILE_CASE(16);
-    default: AMG_TILE_CASE(32);
-    }
-#undef AMG_TILE_CASE
-}
-
-// ------------------------------------------------------------------------------------ segmented (batch) form
-template <typename T>
-cudaError_t seg_spmv(int mode, const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y,
-                     const T *f, const T *invd, T *d, const int *rowsys, const double *coef, int cstride,
-                     const int *active, cudaStream_t s)
-{
-    switch (mode) {
-    case SEG_Y:
-        return spmv_mode<T, MODE_Y>(pl, n, rp, ci, v, x, y, nullptr, nullptr, nullptr, T(0), T(0), nullptr, s, nullptr,
-                                    nullptr, rowsys, nullptr, 0, active);
-    case SEG_RESID:
-        return spmv_mode<T, MODE_RESID>(pl, n, rp, ci, v, x, y, f, nullptr, nullptr, T(0), T(0), nullptr, s, nullptr,
-                                        nullptr, rowsys, nullptr, 0, active);
-    case SEG_PROLONG:
-        return spmv_mode<T, MODE_PROLONG>(pl, n, rp, ci, v, x, y, nullptr, nullptr, nullptr, T(0), T(0), nullptr, s,
-                                          nullptr, nullptr, rowsys, nullptr, 0, active);
-    case SEG_CHEB:
-        return spmv_mode<T, MODE_CHEB_SEG>(pl, n, rp, ci, v, x, y, f, invd, d, T(0), T(0), nullptr, s, nullptr,
-                                           nullptr, rowsys, coef, cstride, active);
-    default: return cudaErrorInvalidValue;
+    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 16:
+        return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    default:
+        return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
     }
 }
-template cudaError_t seg_spmv<double>(int, const SpmvPlan &, int, const int *, const int *, const double *,
-                                      const double *, double *, const double *, const double *, double *,
-                                      const int *, const double *, int, const int *, cudaStream_t);
-template cudaError_t seg_spmv<float>(int, const SpmvPlan &, int, const int *, const int *, const float *,
-                                     const float *, float *, const float *, const float *, float *, const int *,
-                                     const double *, int, const int *, cudaStream_t);
 
 // ------------------------------------------------------------------------------------ FP64 entry points
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s)

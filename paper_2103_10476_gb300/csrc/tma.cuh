@@ -14,6 +14,19 @@ namespace amgk {
 
 constexpr int kWaitSpins = 1 << 22;
 
+// Shared-memory tile of a CSR row range staged by two bulk copies: `cap` values of type T
+// (plus one 16-byte widening on each side) and cap + 8 column indices.
+template <typename T>
+__host__ __device__ constexpr int tile_values_bytes(int cap)
+{
+    return ((cap + 2 * (16 / (int)sizeof(T))) * (int)sizeof(T) + 127) / 128 * 128;
+}
+template <typename T>
+__host__ __device__ constexpr int tile_bytes(int cap)
+{
+    return cap > 0 ? tile_values_bytes<T>(cap) + (cap + 8) * 4 : 0;
+}
+
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)

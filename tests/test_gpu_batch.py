@@ -4,9 +4,9 @@ alone (amg_solve on the same hierarchy) and against the oracle.
 Every system of a batch runs its own PCG (own scalars, own stopping test) through shared
 launches, so a batched result must be the result of that system alone: the same iteration
 count (up to the borderline rule of the single-system parity tests, the summation order of
-the dot products differs) and a solution within SOL_TOL.  Within a batch, a system's rows
-are computed by the same lanes in the same order wherever the system sits, so reordering the
-systems of a batch changes nothing, bit for bit.
+the dot products differs) and a solution within SOL_TOL.  With lanes per row chosen from the
+mean row length (no timing), a system's rows are computed by the same lanes in the same order
+wherever the system sits, so reordering the systems of a batch changes nothing, bit for bit.
 """
 import numpy as np
 import pytest
@@ -159,3 +159,44 @@ def test_setup_batch_reports_failing_system(amg):
 def test_empty_batch(amg):
     st, infos = amg.amg_solve_batch([], [], [], 1e-8)
     assert st == 0 and infos == []
+
+
+def test_shared_hierarchy_many_right_hand_sides(amg):
+    # one hierarchy serving several right-hand sides (the batch refers to it, copies nothing)
+    systems = _systems()[:2]
+    hs = _setup(amg, systems, **KW)
+    A0, A1 = systems[0][0], systems[1][0]
+    bs = [P.rhs_uniform(A0.n, 11), P.rhs_uniform(A0.n, 12), systems[1][1], P.rhs_uniform(A0.n, 13)]
+    handles = [hs[0], hs[0], hs[1], hs[0]]
+    xs = [np.zeros(len(b)) for b in bs]
+    st, infos = amg.amg_solve_batch(handles, bs, xs, 1e-8)
+    assert st == 0
+    for h, b, x, info in zip(handles, bs, xs, infos):
+        xa = np.zeros(len(b))
+        ia = amg.amg_solve(h, b, xa, 1e-8)
+        assert info.status == 0 and abs(info.iters - ia.iters) <= 2
+        assert np.linalg.norm(x - xa) / np.linalg.norm(xa) <= SOL_TOL
+    for h in hs:
+        amg.amg_free(h)
+
+
+def test_tuned_batch_and_repeated_solves(amg):
+    # lanes per row picked by timing; a second solve with the same batch reuses its graphs
+    systems = _systems()
+    hs = _setup(amg, systems, precision=1, **KW)
+    bt = amg.amg_batch_create(hs, tune=True)
+    bs = [b for _, b in systems]
+    x1 = [np.zeros(A.n) for A, _ in systems]
+    x2 = [np.zeros(A.n) for A, _ in systems]
+    st1, i1 = amg.amg_batch_solve(bt, bs, x1, 1e-8)
+    st2, i2 = amg.amg_batch_solve(bt, bs, x2, 1e-8)
+    amg.amg_batch_free(bt)
+    assert st1 == 0 and st2 == 0
+    for k, (A, b) in enumerate(systems):
+        assert i1[k].iters == i2[k].iters and np.array_equal(x1[k], x2[k])
+        xa = np.zeros(A.n)
+        ia = amg.amg_solve(hs[k], b, xa, 1e-8)
+        assert abs(i1[k].iters - ia.iters) <= 1
+        assert np.linalg.norm(x1[k] - xa) / np.linalg.norm(xa) <= 1e-6
+    for h in hs:
+        amg.amg_free(h)
