@@ -41,7 +41,8 @@ typedef enum {
     AMG_ERR_NOT_CONVERGED = 7,  /* PCG reached max_iter; x holds the last iterate             */
     AMG_ERR_BUDGET = 8,         /* a memory budget would be exceeded                          */
     AMG_ERR_UNSUPPORTED = 9,    /* size beyond the library's limits                           */
-    AMG_ERR_INTERNAL = 10       /* a kernel reported an internal limit (e.g. hash overflow)   */
+    AMG_ERR_INTERNAL = 10,      /* a kernel reported an internal limit (e.g. hash overflow)   */
+    AMG_PENDING = 11            /* a served request is not finished yet (amg_server_poll)     */
 } amg_status_t;
 
 /* adaptation bits (0 = traditional smoothed aggregation) */
@@ -222,6 +223,64 @@ amg_status_t amg_solve_batch(int count, const amg_handle_t *h, const double *con
                              double tol, amg_info_t *infos);
 amg_status_t amg_batch_info(amg_batch_t batch, int *count, int *levels, int64_t *rows,
                             int64_t *graph_kernels);
+
+/* ---- Serving (no counterpart in the paper): a request loop that admits solves as they
+ * arrive and runs them with continuous batching on the batch engine.
+ *
+ * A request is an operator A (host or device CSR) with nrhs right-hand sides b (nrhs * n
+ * doubles, system k at b + k n) and the place for the solutions x (same layout).  The
+ * server hashes A's arrays; a request whose operator is resident reuses that hierarchy,
+ * otherwise one of the setup threads builds it (amg_setup with the server's parameters).
+ * Hierarchies stay resident after their requests finish and are evicted least recently used
+ * first when a new one would exceed hbm_budget_bytes (hierarchies plus the engine's vectors
+ * and lists).  Every right-hand side becomes one system of the engine as soon as its
+ * hierarchy is ready and the engine has room; each PCG iteration of the engine advances every
+ * system in flight, and a finished system's x is copied out and its place given to the next.
+ * A, b and x belong to the caller and must stay valid until the request is done.
+ *
+ * amg_server_config_default: hbm_budget_bytes 120 GB, 8 setup threads, 4096 systems and
+ *   2^28 fine rows in flight at most, tol 1e-8, tune 1, params = amg_params_default.
+ * amg_server_submit: queues a request; *ticket identifies it.  Never blocks on the GPU.
+ * amg_server_poll: AMG_PENDING while the request runs; then AMG_OK once, with *info filled
+ *   in (info->status holds the request's own outcome); the ticket is released then.
+ * amg_server_wait: blocks until the request is done, then as amg_server_poll.
+ * amg_server_stats: counters since creation.
+ * amg_server_destroy: finishes every request in flight, then releases everything. */
+typedef struct amg_server *amg_server_t;
+typedef struct {
+    size_t hbm_budget_bytes;
+    int setup_threads;
+    int max_systems;
+    int64_t max_rows;
+    double tol;
+    int tune;
+    amg_params_t params;
+} amg_server_config_t;
+typedef struct {
+    int status;          /* AMG_OK, AMG_ERR_NOT_CONVERGED (some right-hand side) or the setup error */
+    int nrhs;
+    int iters_max;       /* most PCG iterations over the right-hand sides                     */
+    int cache_hit;       /* 1: the hierarchy was resident when the request arrived            */
+    double relres_max;   /* largest true relative residual over the right-hand sides          */
+    double queue_ms;     /* submit -> the first right-hand side enters the engine             */
+    double setup_ms;     /* the hierarchy build this request waited for (0 on a hit)          */
+    double latency_ms;   /* submit -> every solution copied out                               */
+} amg_request_info_t;
+typedef struct {
+    int64_t submitted, completed, solves, cache_hits, cache_misses, evictions, failed;
+    int64_t iterations, commits;
+    double engine_busy_ms;
+    size_t bytes_hierarchies, bytes_engine;
+    int resident_hierarchies;
+} amg_server_stats_t;
+void amg_server_config_default(amg_server_config_t *cfg);
+amg_status_t amg_server_create(const amg_server_config_t *cfg, amg_server_t *out);
+amg_status_t amg_server_submit(amg_server_t srv, const amg_csr_t *A, int nrhs, const double *b, double *x,
+                               uint64_t *ticket);
+amg_status_t amg_server_poll(amg_server_t srv, uint64_t ticket, amg_request_info_t *info);
+amg_status_t amg_server_wait(amg_server_t srv, uint64_t ticket, amg_request_info_t *info);
+amg_status_t amg_server_stats(amg_server_t srv, amg_server_stats_t *stats);
+amg_status_t amg_server_destroy(amg_server_t srv);
 
 /* Measurement hooks (no counterpart in the paper).
  * amg_launch_count: kernels launched by this library since it was loaded (all threads).

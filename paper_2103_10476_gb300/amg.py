@@ -17,7 +17,8 @@ from . import build as _build
 LIB_PATH = _build.LIB
 
 AMG_OK, AMG_ERR_INVALID_ARG, AMG_ERR_OOM, AMG_ERR_CUDA, AMG_ERR_ZERO_DIAG, AMG_ERR_EIGEN, \
-    AMG_ERR_COARSE_NOT_SPD, AMG_ERR_NOT_CONVERGED, AMG_ERR_BUDGET, AMG_ERR_UNSUPPORTED, AMG_ERR_INTERNAL = range(11)
+    AMG_ERR_COARSE_NOT_SPD, AMG_ERR_NOT_CONVERGED, AMG_ERR_BUDGET, AMG_ERR_UNSUPPORTED, AMG_ERR_INTERNAL, \
+    AMG_PENDING = range(12)
 AMG_VAR_1NORM, AMG_VAR_OFFLMP, AMG_VAR_SPRSFY, AMG_VAR_CNSTRNT = 1, 2, 4, 8
 AMG_FP64, AMG_MIXED = 0, 1
 AMG_PT_ORTHONORMAL, AMG_PT_UNIT = 0, 1
@@ -60,6 +61,25 @@ class amg_dcsr_t(C.Structure):
                 ("col", C.c_void_p), ("val", C.c_void_p)]
 
 
+class amg_server_config_t(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("setup_threads", C.c_int), ("max_systems", C.c_int),
+                ("max_rows", C.c_int64), ("tol", C.c_double), ("tune", C.c_int), ("params", amg_params_t)]
+
+
+class amg_request_info_t(C.Structure):
+    _fields_ = [("status", C.c_int), ("nrhs", C.c_int), ("iters_max", C.c_int), ("cache_hit", C.c_int),
+                ("relres_max", C.c_double), ("queue_ms", C.c_double), ("setup_ms", C.c_double),
+                ("latency_ms", C.c_double)]
+
+
+class amg_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("solves", C.c_int64),
+                ("cache_hits", C.c_int64), ("cache_misses", C.c_int64), ("evictions", C.c_int64),
+                ("failed", C.c_int64), ("iterations", C.c_int64), ("commits", C.c_int64),
+                ("engine_busy_ms", C.c_double), ("bytes_hierarchies", C.c_size_t), ("bytes_engine", C.c_size_t),
+                ("resident_hierarchies", C.c_int)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is not built; run paper_2103_10476_gb300.build.build() first")
@@ -93,6 +113,13 @@ def _load():
                                  C.POINTER(amg_info_t)]),
         "amg_batch_info": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                 C.POINTER(C.c_int64)]),
+        "amg_server_config_default": (None, [C.POINTER(amg_server_config_t)]),
+        "amg_server_create": (st, [C.POINTER(amg_server_config_t), C.POINTER(vp)]),
+        "amg_server_submit": (st, [vp, C.POINTER(amg_csr_t), C.c_int, vp, vp, C.POINTER(C.c_uint64)]),
+        "amg_server_poll": (st, [vp, C.c_uint64, C.POINTER(amg_request_info_t)]),
+        "amg_server_wait": (st, [vp, C.c_uint64, C.POINTER(amg_request_info_t)]),
+        "amg_server_stats": (st, [vp, C.POINTER(amg_server_stats_t)]),
+        "amg_server_destroy": (st, [vp]),
         "amg_status_string": (C.c_char_p, [st]),
         "amg_last_error": (C.c_char_p, []),
     }
@@ -312,6 +339,57 @@ def amg_batch_info(bt):
     c, L, rows, gk = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
     _check(lib.amg_batch_info(bt, C.byref(c), C.byref(L), C.byref(rows), C.byref(gk)), "amg_batch_info")
     return c.value, L.value, rows.value, gk.value
+
+
+def amg_server_config_default(params: amg_params_t | None = None, **overrides) -> amg_server_config_t:
+    c = amg_server_config_t()
+    lib.amg_server_config_default(C.byref(c))
+    if params is not None:
+        c.params = params
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def amg_server_create(cfg: amg_server_config_t):
+    srv = C.c_void_p()
+    _check(lib.amg_server_create(C.byref(cfg), C.byref(srv)), "amg_server_create")
+    return srv
+
+
+def amg_server_submit(srv, A: amg_csr_t, nrhs: int, b, x) -> int:
+    """Queues a request; b and x (nrhs * n doubles) and A's arrays must outlive it."""
+    t = C.c_uint64()
+    pb, _ = _ptr(b)
+    px, _ = _ptr(x)
+    _check(lib.amg_server_submit(srv, C.byref(A), nrhs, pb, px, C.byref(t)), "amg_server_submit")
+    return t.value
+
+
+def amg_server_poll(srv, ticket: int):
+    """None while pending, else the request's amg_request_info_t."""
+    info = amg_request_info_t()
+    s = lib.amg_server_poll(srv, ticket, C.byref(info))
+    if s == AMG_PENDING:
+        return None
+    _check(s, "amg_server_poll")
+    return info
+
+
+def amg_server_wait(srv, ticket: int) -> amg_request_info_t:
+    info = amg_request_info_t()
+    _check(lib.amg_server_wait(srv, ticket, C.byref(info)), "amg_server_wait")
+    return info
+
+
+def amg_server_stats(srv) -> amg_server_stats_t:
+    st = amg_server_stats_t()
+    _check(lib.amg_server_stats(srv, C.byref(st)), "amg_server_stats")
+    return st
+
+
+def amg_server_destroy(srv):
+    _check(lib.amg_server_destroy(srv), "amg_server_destroy")
 
 
 def amg_status_string(s: int) -> str:

@@ -25,6 +25,7 @@ SOURCES = {
     "solve.cu": [],
     "api.cu": [],
     "batch.cu": [],
+    "server.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

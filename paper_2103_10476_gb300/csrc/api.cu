@@ -57,7 +57,10 @@ cudaError_t dalloc(amg_hierarchy *h, T **p, size_t count)
 {
     *p = nullptr;
     cudaError_t e = cudaMallocAsync((void **)p, (count + 16) * sizeof(T), h->s);
-    if (e == cudaSuccess) h->allocs.push_back((void *)*p);
+    if (e == cudaSuccess) {
+        h->allocs.push_back((void *)*p);
+        h->bytes += (count + 16) * sizeof(T);
+    }
     return e;
 }
 
@@ -66,6 +69,7 @@ void own(amg_hierarchy *h, const DevCsr &c)
     if (c.rp) h->allocs.push_back(c.rp);
     if (c.ci) h->allocs.push_back(c.ci);
     if (c.v) h->allocs.push_back(c.v);
+    h->bytes += 12 * ((size_t)c.nnz + 16) + 4 * ((size_t)c.n + 17);
 }
 
 void release_all(amg_hierarchy *h)
@@ -508,6 +512,7 @@ const char *amg_status_string(amg_status_t s)
     case AMG_ERR_BUDGET: return "memory budget exceeded";
     case AMG_ERR_UNSUPPORTED: return "unsupported size";
     case AMG_ERR_INTERNAL: return "internal limit";
+    case AMG_PENDING: return "pending";
     }
     return "unknown status";
 }

@@ -60,6 +60,7 @@ struct amg_hierarchy {
     SolveCtx ctx;
     double setup_ms = 0.0;
     int64_t fine_nnz = 0;
+    size_t bytes = 0;   // device memory held by the handle
 };
 
 
