@@ -288,6 +288,135 @@ def run_once(args):
     return 0
 
 
+def pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(q * len(v)))] if v else None
+
+
+def run_batched(args, amg, torch):
+    """512 independent systems (edge 8..40 nodes, half stretched, half 10^U(-2,2) coefficients,
+    seed 3), one hierarchy each, theta 0.02 with 1Norm + OffLmp; one step = amg_setup_batch of
+    all 512 (matrices resident on the device) + the batched PCG solve of all 512 to 1e-8.
+    Host wall time between device synchronisations (setup runs on one stream per host
+    thread).  Mixed precision (FP32 levels, FP64 PCG) and FP64."""
+    from paper_2103_10476_gb300 import problems as P
+    t0 = time.perf_counter()
+    systems = P.batched_systems(512, engine="c")
+    gen_s = time.perf_counter() - t0
+    dev = []
+    for A, b in systems:
+        dev.append((torch.from_numpy(A.row_ptr).cuda(), torch.from_numpy(A.col).cuda(),
+                    torch.from_numpy(A.val).cuda(), torch.from_numpy(b).cuda(),
+                    torch.zeros(A.n, dtype=torch.float64, device="cuda")))
+    args_d = [amg.csr_arg(A.n, rp, ci, v) for (A, _), (rp, ci, v, _, _) in zip(systems, dev)]
+    bs = [d[3] for d in dev]
+    xs = [d[4] for d in dev]
+    out = {"workload": "512 Q1 systems, edge U{8..40} nodes, half stretched z ratio U[1.05,1.2], half "
+                       "10^U(-2,2) coefficients, seed 3; theta 0.02, 1Norm+OffLmp",
+           "rows": sum(A.n for A, _ in systems), "nnz": sum(A.nnz for A, _ in systems), "generate_s": gen_s}
+    for prec_name, prec in (("mixed", amg.AMG_MIXED), ("fp64", amg.AMG_FP64)):
+        p = amg.amg_params_default(theta=0.02, variants=3, precision=prec)
+        steps = []
+        for k in range(1 + args.batch_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs = amg.amg_setup_batch(args_d, None, p)
+            t1 = time.perf_counter()
+            bt = amg.amg_batch_create(hs, tune=True)
+            st, infos = amg.amg_batch_solve(bt, bs, xs, TOL)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            gk = amg.amg_batch_info(bt)[3]
+            amg.amg_batch_free(bt)
+            for h in hs:
+                amg.amg_free(h)
+            if k > 0:   # the first step is the warm-up (graph capture, lane tuning, pool growth)
+                its = [i.iters for i in infos]
+                steps.append({"setup_ms": 1e3 * (t1 - t0), "solve_ms": 1e3 * (t2 - t1), "status": st,
+                              "iters_mean": sum(its) / len(its), "iters_max": max(its),
+                              "relres_max": max(i.relres_true for i in infos), "kernels_per_iteration": gk})
+        tot = sum(s_["setup_ms"] + s_["solve_ms"] for s_ in steps)
+        out[prec_name] = {"value": 512 * len(steps) / (tot / 1000.0), "unit": "solves/s",
+                          "ms_per_step": tot / len(steps), "steps": len(steps), "per_step": steps}
+    return out
+
+
+def run_serving(args, amg, seconds: float, precisions):
+    """The request stream of problems.serving_stream (Poisson 200 req/s, operators with edge
+    log-uniform 16..96 nodes, stretched or 10^U(-2,2) coefficients, 30% repeats, 1..8
+    right-hand sides, seed 4) over the first `seconds` of arrivals, served with a 120 GB HBM
+    budget.  Operators and right-hand sides are host arrays generated before the clock
+    starts; each request is submitted at its arrival time and its latency runs from submit
+    until its solutions are in host memory."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+    from paper_2103_10476_gb300 import problems as P
+    reqs, ops = P.serving_stream(seconds, rate=args.serve_rate)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        mats = list(ex.map(lambda o: P.make_operator(o, engine="c"), ops))
+
+        def rhs(r):
+            n = mats[r[1]].n
+            return np.concatenate([P.rhs_uniform(n, r[3] ^ (k << 20)) for k in range(r[2])])
+        bs = list(ex.map(rhs, reqs))
+    gen_s = time.perf_counter() - t0
+    csr = [amg.csr_arg(A.n, A.row_ptr, A.col, A.val) for A in mats]
+    out = {"workload": f"Poisson {args.serve_rate:g} req/s for {seconds:g} s of arrivals ({len(reqs)} requests, "
+                       f"{len(ops)} distinct operators, {sum(r[2] for r in reqs)} right-hand sides), edge "
+                       "log-uniform 16..96 nodes, stretched or 10^U(-2,2) coefficients, 30% repeats, 1..8 RHS, "
+                       "seed 4; theta 0.02 1Norm+OffLmp; 120 GB HBM budget",
+           "generate_s": gen_s, "rows_mean": float(np.mean([A.n for A in mats]))}
+    for prec_name in precisions:
+        prec = amg.AMG_MIXED if prec_name == "mixed" else amg.AMG_FP64
+        p = amg.amg_params_default(theta=0.02, variants=3, precision=prec)
+        cfg = amg.amg_server_config_default(p, hbm_budget_bytes=120 << 30, setup_threads=8, max_systems=8192,
+                                            max_rows=1 << 27, tol=TOL, tune=1)
+        srv = amg.amg_server_create(cfg)
+        xs = [np.empty_like(b) for b in bs]
+        for x in xs:
+            x.fill(0.0)     # written once by the CPU, so every page is populated
+        tickets = [None] * len(reqs)
+        infos = [None] * len(reqs)
+        submitted = threading.Event()
+
+        def collect():
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0005)
+                infos[i] = amg.amg_server_wait(srv, tickets[i])
+        th = threading.Thread(target=collect)
+        th.start()
+        start = time.perf_counter()
+        for i, r in enumerate(reqs):
+            dt = r[0] - (time.perf_counter() - start)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = amg.amg_server_submit(srv, csr[r[1]], r[2], bs[i], xs[i])
+        submitted.set()
+        th.join()
+        wall = time.perf_counter() - start
+        stats = amg.amg_server_stats(srv)
+        amg.amg_server_destroy(srv)
+        lat = [i.latency_ms for i in infos]
+        ok = sum(1 for i in infos if i.status == 0)
+        out[prec_name] = {
+            "solves_per_s": stats.solves / wall, "requests_per_s": len(reqs) / wall, "wall_s": wall,
+            "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "mean_ms": sum(lat) / len(lat),
+            "queue_p50_ms": pct([i.queue_ms for i in infos], 0.5),
+            "setup_p50_ms": pct([i.setup_ms for i in infos if not i.cache_hit], 0.5),
+            "ok": ok, "failed": len(infos) - ok, "relres_max": max(i.relres_max for i in infos),
+            "cache_hits": stats.cache_hits, "cache_misses": stats.cache_misses, "evictions": stats.evictions,
+            "engine_iterations": stats.iterations, "engine_busy_s": stats.engine_busy_ms / 1000.0,
+            "commits": stats.commits, "first_error": stats.first_error.decode(errors="replace") or None,
+            "statuses": sorted({amg.amg_status_string(i.status) for i in infos}),
+            "hbm_hierarchies_gb": stats.bytes_hierarchies / 2**30,
+            "hbm_engine_gb": stats.bytes_engine / 2**30}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,6 +432,12 @@ def main():
                     help="one setup + solve (or --vcycles V-cycles) of one method, for profiler captures")
     ap.add_argument("--method", default=None, help="with --once: which method of the workload (default: first)")
     ap.add_argument("--vcycles", type=int, default=0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched line")
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-fp64", action="store_true", help="serve the stream in FP64 as well as mixed")
     args = ap.parse_args()
     world, rank, local = dist_init()
 
@@ -422,6 +557,10 @@ def main():
     h2d = solves_per_step * (8 * (A.n + 1) + 12 * A.nnz + 8 * A.n)
     d2h = solves_per_step * 8 * A.n
 
+    batched = None if args.no_batched else run_batched(args, amg, torch)
+    serving = None if not args.serving else run_serving(args, amg, args.serve_seconds,
+                                                        ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
+
     if rank != 0:
         return 0
 
@@ -461,6 +600,8 @@ def main():
         "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
         "iters": iters, "status": statuses, "wall_s": t_wall,
         "mixed": other,
+        "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -272,6 +272,7 @@ typedef struct {
     double engine_busy_ms;
     size_t bytes_hierarchies, bytes_engine;
     int resident_hierarchies;
+    char first_error[256];   /* the first failure's message (empty if none)                   */
 } amg_server_stats_t;
 void amg_server_config_default(amg_server_config_t *cfg);
 amg_status_t amg_server_create(const amg_server_config_t *cfg, amg_server_t *out);

@@ -77,7 +77,7 @@ class amg_server_stats_t(C.Structure):
                 ("cache_hits", C.c_int64), ("cache_misses", C.c_int64), ("evictions", C.c_int64),
                 ("failed", C.c_int64), ("iterations", C.c_int64), ("commits", C.c_int64),
                 ("engine_busy_ms", C.c_double), ("bytes_hierarchies", C.c_size_t), ("bytes_engine", C.c_size_t),
-                ("resident_hierarchies", C.c_int)]
+                ("resident_hierarchies", C.c_int), ("first_error", C.c_char * 256)]
 
 
 def _load():

@@ -84,5 +84,23 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     return LIB
 
 
+GEN_SRC = os.path.join(PKG, "q1gen.c")
+GEN_LIB = os.path.join(PKG, "libq1gen.so")
+
+
+def build_generator(force: bool = False) -> str:
+    """The C input generator (q1gen.c): host code, built with the system C compiler."""
+    if not force and os.path.exists(GEN_LIB) and os.path.getmtime(GEN_LIB) >= os.path.getmtime(GEN_SRC):
+        return GEN_LIB
+    tmp = GEN_LIB + f".tmp{os.getpid()}"
+    cmd = [os.environ.get("CC", "gcc"), "-O2", "-ffp-contract=off", "-fPIC", "-shared", GEN_SRC, "-o", tmp]
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError("q1gen build failed:\n" + r.stdout.decode(errors="replace"))
+    os.replace(tmp, GEN_LIB)
+    return GEN_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_generator(force="--force" in sys.argv))

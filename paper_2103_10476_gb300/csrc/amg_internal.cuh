@@ -71,6 +71,12 @@ cudaError_t fill_double(double *p, double value, int64_t n, cudaStream_t s);
 cudaError_t convert_rowptr_to64(const int *rp32, int64_t *rp64, int n1, cudaStream_t s);
 cudaError_t convert_rowptr_to32(const int64_t *rp64, int *rp32, int n1, int *bad, cudaStream_t s);
 cudaError_t convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+// Copies between the device and memory the caller owns (host or device).  Host memory that
+// CUDA did not allocate or register moves through pinned bounce buffers of the calling
+// thread, so the GPU never reads or writes the caller's pageable pages itself.
+// copy_to_device returns once `src` may be reused; copy_to_host synchronises `s`.
+cudaError_t copy_to_device(void *dst, const void *src, size_t bytes, cudaStream_t s);
+cudaError_t copy_to_host(void *dst, const void *src, size_t bytes, cudaStream_t s);
 
 // Deterministic reductions: stage 1 writes kReduceBlocks partial sums, stage 2 sums them in
 // a fixed order into *out.

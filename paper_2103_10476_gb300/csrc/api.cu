@@ -472,6 +472,59 @@ cudaGraphExec_t pcg_graph(amg_hierarchy *h, int parity)
 
 }  // namespace
 
+// ------------------------------------------------------------------------------------ integrity check
+namespace {
+__global__ void csr_check_kernel(int n, int ncol, int64_t nnz, const int *rp, const int *ci, int *bad)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int b = rp[i], e = rp[i + 1];
+        if (b < 0 || e < b || e > nnz) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        for (int k = b; k < e; ++k)
+            if (ci[k] < 0 || ci[k] >= ncol) {
+                atomicAdd(bad, 1);
+                break;
+            }
+    }
+}
+
+}  // namespace
+
+int amgk::hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail)
+{
+    int *bad = nullptr;
+    if (cudaMallocAsync(&bad, sizeof(int), s) != cudaSuccess) return -1;
+    int total = 0;
+    auto one = [&](const DevCsr &c, int L, const char *what) -> bool {
+        if (c.n == 0) return true;
+        int head[2] = {0, 0};
+        int hb = 0;
+        if (cudaMemsetAsync(bad, 0, sizeof(int), s) != cudaSuccess) return false;
+        csr_check_kernel<<<grid_for(c.n, 256, 4096), 256, 0, s>>>(c.n, c.ncol, c.nnz, c.rp, c.ci, bad); note_launch();
+        if (cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+        if (cudaMemcpyAsync(&head[0], c.rp, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+        if (cudaMemcpyAsync(&head[1], c.rp + c.n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+        const int f = hb + (head[0] != 0) + (head[1] != (int)c.nnz);
+        if (f && total == 0 && detail)
+            *detail = std::string(what) + " of level " + std::to_string(L) + ": " + std::to_string(hb) +
+                      " bad rows, rp[0]=" + std::to_string(head[0]) + " rp[n]=" + std::to_string(head[1]) +
+                      " nnz=" + std::to_string(c.nnz);
+        total += f;
+        return true;
+    };
+    bool ok = true;
+    for (int L = 0; L < h->nlev && ok; ++L) {
+        ok = one(h->lev[L].A, L, "A");
+        if (ok && L + 1 < h->nlev) ok = one(h->lev[L].P, L, "P") && one(h->lev[L].R, L, "R");
+    }
+    cudaFreeAsync(bad, s);
+    cudaStreamSynchronize(s);
+    return ok ? total : -1;
+}
+
 // ====================================================================================== ABI
 
 extern "C" {
@@ -595,11 +648,11 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
         CK(cudaMallocAsync(&bad, sizeof(int), s));
         CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
         CK(cudaMallocAsync(&rp64, sizeof(int64_t) * ((size_t)n + 1), s));
-        CK(cudaMemcpyAsync(rp64, Ain->row_ptr, sizeof(int64_t) * ((size_t)n + 1), cudaMemcpyDefault, s));
+        CK(copy_to_device(rp64, Ain->row_ptr, sizeof(int64_t) * ((size_t)n + 1), s));
         CK(convert_rowptr_to32(rp64, l0.A.rp, n + 1, bad, s));
         if (nnz > 0) {
-            CK(cudaMemcpyAsync(l0.A.ci, Ain->col, sizeof(int) * (size_t)nnz, cudaMemcpyDefault, s));
-            CK(cudaMemcpyAsync(l0.A.v, Ain->val, sizeof(double) * (size_t)nnz, cudaMemcpyDefault, s));
+            CK(copy_to_device(l0.A.ci, Ain->col, sizeof(int) * (size_t)nnz, s));
+            CK(copy_to_device(l0.A.v, Ain->val, sizeof(double) * (size_t)nnz, s));
         }
         CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -614,7 +667,7 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
             if (hbad) { g_last_error = "columns unsorted, out of range, duplicated, or a missing diagonal"; st = AMG_ERR_INVALID_ARG; goto done; }
         }
         CK(dalloc(h, &l0.B, (size_t)n));
-        if (nullspace) CK(cudaMemcpyAsync(l0.B, nullspace, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+        if (nullspace) CK(copy_to_device(l0.B, nullspace, sizeof(double) * (size_t)n, s));
         else if (n > 0) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
         CK(cudaGetLastError());
         h->fine_nnz = nnz;
@@ -689,9 +742,9 @@ amg_status_t amg_vcycle(amg_handle_t h, const double *r, double *z)
     cudaStream_t s = h->s;
     const int n = h->lev[0].A.n;
     if (n == 0) return AMG_OK;
-    CK(cudaMemcpyAsync(h->r, r, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(copy_to_device(h->r, r, sizeof(double) * (size_t)n, s));
     CK(vcycle(h->ctx, h->r, h->z, s));
-    CK(cudaMemcpyAsync(z, h->z, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(copy_to_host(z, h->z, sizeof(double) * (size_t)n, s));
     CK(cudaStreamSynchronize(s));
     if (spmv_take_errors(s) != 0) {
         g_last_error = "a bulk copy into shared memory did not complete in time";
@@ -716,7 +769,7 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     double bb = 0.0, rr = 0.0, relres = 0.0, nb = 0.0;
     amg_status_t result = AMG_OK;
     if (n == 0) goto finish;
-    CK(cudaMemcpyAsync(h->b, b, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+    CK(copy_to_device(h->b, b, sizeof(double) * (size_t)n, s));
     CK(cudaMemsetAsync(h->x, 0, sizeof(double) * (size_t)n, s));
     CK(cudaMemcpyAsync(h->r, h->b, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, s));
     CK(dot(h->b, h->b, n, h->partial, &h->sc->bb, s));
@@ -766,7 +819,7 @@ finish:
         CK(dot(h->t, h->t, n, h->partial, &h->sc->tmp, s));
         double tt = 0.0;
         CK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(x, h->x, sizeof(double) * (size_t)n, cudaMemcpyDefault, s));
+        CK(copy_to_host(x, h->x, sizeof(double) * (size_t)n, s));
         CK(cudaStreamSynchronize(s));
         relres = nb > 0.0 ? std::sqrt(tt) / nb : 0.0;
     }
@@ -875,13 +928,13 @@ amg_status_t amg_export(amg_handle_t h, int level, int what, void *dst)
     cudaError_t err;
     if (e.kind == 1) {
         std::vector<int> tmp((size_t)e.count);
-        err = cudaMemcpy(tmp.data(), e.ptr, sizeof(int) * (size_t)e.count, cudaMemcpyDeviceToHost);
+        err = copy_to_host(tmp.data(), e.ptr, sizeof(int) * (size_t)e.count, nullptr);
         if (err != cudaSuccess) return fail_cuda(err, "amg_export");
         int64_t *o = (int64_t *)dst;
         for (int64_t i = 0; i < e.count; ++i) o[i] = tmp[(size_t)i];
         return AMG_OK;
     }
-    err = cudaMemcpy(dst, e.ptr, e.elem * (size_t)e.count, cudaMemcpyDeviceToHost);
+    err = copy_to_host(dst, e.ptr, e.elem * (size_t)e.count, nullptr);
     if (err != cudaSuccess) return fail_cuda(err, "amg_export");
     return AMG_OK;
 }
@@ -900,9 +953,9 @@ amg_status_t amg_csr_release(amg_dcsr_t *C)
 amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *col, double *val)
 {
     if (!C || !row_ptr || (C->nnz > 0 && (!col || !val))) return AMG_ERR_INVALID_ARG;
-    cudaError_t e = cudaMemcpy(row_ptr, C->row_ptr, sizeof(int64_t) * (size_t)(C->nrow + 1), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && C->nnz > 0) e = cudaMemcpy(col, C->col, sizeof(int32_t) * (size_t)C->nnz, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && C->nnz > 0) e = cudaMemcpy(val, C->val, sizeof(double) * (size_t)C->nnz, cudaMemcpyDeviceToHost);
+    cudaError_t e = copy_to_host(row_ptr, C->row_ptr, sizeof(int64_t) * (size_t)(C->nrow + 1), nullptr);
+    if (e == cudaSuccess && C->nnz > 0) e = copy_to_host(col, C->col, sizeof(int32_t) * (size_t)C->nnz, nullptr);
+    if (e == cudaSuccess && C->nnz > 0) e = copy_to_host(val, C->val, sizeof(double) * (size_t)C->nnz, nullptr);
     return e == cudaSuccess ? AMG_OK : fail_cuda(e, "amg_dcsr_download");
 }
 
@@ -964,11 +1017,11 @@ amg_status_t amg_spgemm(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, i
         CK(cudaMalloc(&d->ci, sizeof(int) * (size_t)(m->nnz > 0 ? m->nnz : 1)));
         CK(cudaMalloc(&d->v, sizeof(double) * (size_t)(m->nnz > 0 ? m->nnz : 1)));
         CK(cudaMalloc(&rp64, sizeof(int64_t) * (size_t)(m->n + 1)));
-        CK(cudaMemcpyAsync(rp64, m->row_ptr, sizeof(int64_t) * (size_t)(m->n + 1), cudaMemcpyDefault, s));
+        CK(copy_to_device(rp64, m->row_ptr, sizeof(int64_t) * (size_t)(m->n + 1), s));
         CK(convert_rowptr_to32(rp64, d->rp, (int)m->n + 1, bad, s));
         if (m->nnz > 0) {
-            CK(cudaMemcpyAsync(d->ci, m->col, sizeof(int) * (size_t)m->nnz, cudaMemcpyDefault, s));
-            CK(cudaMemcpyAsync(d->v, m->val, sizeof(double) * (size_t)m->nnz, cudaMemcpyDefault, s));
+            CK(copy_to_device(d->ci, m->col, sizeof(int) * (size_t)m->nnz, s));
+            CK(copy_to_device(d->v, m->val, sizeof(double) * (size_t)m->nnz, s));
         }
         CK(cudaStreamSynchronize(s));
         cudaFree(rp64);

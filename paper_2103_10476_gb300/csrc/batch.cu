@@ -34,10 +34,43 @@ enum { SK_Y = 0, SK_RESID = 1, SK_CHEB = 2, SK_PROLONG = 3 };
 // Persistent: block b takes tiles b, b + grid, ... of the list.  Each tile's values and
 // column indices are staged in shared memory by two bulk copies completed on one mbarrier
 // (its phase advances once per staged tile), then LPR lanes per row gather x.
+// records the first violation; every later one only counts
+__device__ void guard_hit(EngGuard *g, int kind, int slot, int where, const int *info = nullptr, int ninfo = 0)
+{
+    if (atomicAdd(&g->count, 1) == 0) {
+        g->kind = kind;
+        g->slot = slot;
+        g->where = where;
+        for (int k = 0; k < ninfo && k < 12; ++k) g->info[k] = info[k];
+    }
+}
+
+// the tile's rows, its entries and the vector ranges it touches all lie inside their arrays
+__device__ __forceinline__ bool tile_ok(const SegTile &tl, const SegOp &op, int nslots, int xcap, int ycap,
+                                        EngGuard *g)
+{
+    bool ok = tl.slot >= 0 && tl.slot < nslots && tl.row0 >= 0 && tl.rows > 0 && tl.row0 + tl.rows <= op.n &&
+              op.xoff >= 0 && op.yoff >= 0 && (int64_t)op.xoff + op.ncol <= xcap &&
+              (int64_t)op.yoff + op.n <= ycap;
+    int k0 = -1, k1 = -1;
+    if (ok) {
+        k0 = op.rp[tl.row0];
+        k1 = op.rp[tl.row0 + tl.rows];
+        ok = k0 >= 0 && k0 <= k1 && k1 <= op.nnz;
+    }
+    if (!ok && threadIdx.x == 0) {
+        const int info[12] = {tl.row0, tl.rows, op.n, op.ncol, op.nnz, k0, k1, op.xoff, op.yoff, xcap, ycap,
+                              op.rp ? op.rp[0] : -7};
+        guard_hit(g, 1, tl.slot, tl.row0, info, 12);
+    }
+    return ok;
+}
+
 template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(kET) segtile_kernel(const SegTile *__restrict__ tiles, const int *__restrict__ count,
                                                       const SegOp *__restrict__ ops, const T *__restrict__ x, T *y,
-                                                      const T *__restrict__ f, T *d, int coef_idx, int cap, int *err)
+                                                      const T *__restrict__ f, T *d, int coef_idx, int cap, int *err,
+                                                      int nslots, int xcap, int ycap, EngGuard *guard)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -54,7 +87,12 @@ __global__ void __launch_bounds__(kET) segtile_kernel(const SegTile *__restrict_
     const int lrow = threadIdx.x / LPR, lane = threadIdx.x % LPR;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const SegTile tl = tiles[t];
+        if (tl.slot < 0 || tl.slot >= nslots) {
+            if (threadIdx.x == 0) guard_hit(guard, 1, tl.slot, t);
+            continue;
+        }
         const SegOp op = ops[tl.slot];
+        if (!tile_ok(tl, op, nslots, xcap, ycap, guard)) continue;     // uniform over the block
         const T *v = (const T *)op.v;
         const int r0 = tl.row0, r1 = tl.row0 + tl.rows;
         const int k0 = op.rp[r0], k1 = op.rp[r1];
@@ -109,12 +147,20 @@ __global__ void __launch_bounds__(kET) segtile_kernel(const SegTile *__restrict_
 // first Chebyshev step from x = 0 over the rows of the A tiles: d = D^-1 f / theta, x = d
 template <typename T>
 __global__ void __launch_bounds__(kET) segcheb0_kernel(const SegTile *tiles, const int *count, const SegOp *ops,
-                                                       const T *f, T *d, T *x)
+                                                       const T *f, T *d, T *x, int nslots, int cap, EngGuard *guard)
 {
     const int ntiles = *count;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const SegTile tl = tiles[t];
+        if (tl.slot < 0 || tl.slot >= nslots) {
+            if (threadIdx.x == 0) guard_hit(guard, 2, tl.slot, t);
+            continue;
+        }
         const SegOp op = ops[tl.slot];
+        if (tl.row0 < 0 || tl.row0 + tl.rows > op.n || op.yoff < 0 || (int64_t)op.yoff + op.n > cap) {
+            if (threadIdx.x == 0) guard_hit(guard, 2, tl.slot, tl.row0);
+            continue;
+        }
         const T inv_theta = (T)op.coef[0];
         const T *invd = (const T *)op.invd;
         for (int i = threadIdx.x; i < tl.rows; i += kET) {
@@ -128,12 +174,17 @@ __global__ void __launch_bounds__(kET) segcheb0_kernel(const SegTile *tiles, con
 
 // dense coarsest-level solves x = Ainv f, a block per slot, a warp per row (FP64 sums)
 template <typename T>
-__global__ void __launch_bounds__(kET) segcoarse_kernel(const SegCoarse *list, const int *count, const T *f, T *x)
+__global__ void __launch_bounds__(kET) segcoarse_kernel(const SegCoarse *list, const int *count, const T *f, T *x,
+                                                        int nslots, int cap, EngGuard *guard)
 {
     const int n_items = *count;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
         const SegCoarse c = list[t];
+        if (c.slot < 0 || c.slot >= nslots || c.n < 0 || c.off < 0 || (int64_t)c.off + c.n > cap || !c.inv) {
+            if (threadIdx.x == 0) guard_hit(guard, 3, c.slot, c.off);
+            continue;
+        }
         for (int i = w; i < c.n; i += kET / 32) {
             double acc = 0.0;
             for (int k = lane; k < c.n; k += 32) acc += c.inv[(size_t)i * c.n + k] * (double)f[c.off + k];
@@ -190,13 +241,24 @@ __device__ __forceinline__ bool chunk_finish(const SegChunk &c, double part, dou
     return true;
 }
 
+// a chunk inside the fine arena and the slot table (uniform over the block)
+__device__ __forceinline__ bool chunk_ok(const SegChunk &c, int nslots, int cap, EngGuard *g)
+{
+    const bool ok = c.slot >= 0 && c.slot < nslots && c.begin >= 0 && c.begin <= c.end && c.end <= cap &&
+                    c.first >= 0 && c.id >= c.first && c.id < c.first + c.count;
+    if (!ok && threadIdx.x == 0) guard_hit(g, 4, c.slot, c.begin);
+    return ok;
+}
+
 // start of a solve: x = 0, r = b, p = 0, z_prev = 0, r.z = 1
 __global__ void __launch_bounds__(kET) eng_init_kernel(const SegChunk *chunks, const int *count, const double *b,
-                                                       double *x, double *r, double *p, double *zp, EngScal *sc)
+                                                       double *x, double *r, double *p, double *zp, EngScal *sc,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
             x[i] = 0.0;
             r[i] = b[i];
@@ -209,11 +271,13 @@ __global__ void __launch_bounds__(kET) eng_init_kernel(const SegChunk *chunks, c
 
 // a . a per slot: which = 0 -> bb, 1 -> tt
 __global__ void __launch_bounds__(kET) eng_norm_kernel(const SegChunk *chunks, const int *count, const double *a,
-                                                       double *partial, unsigned *ticket, EngScal *sc, int which)
+                                                       double *partial, unsigned *ticket, EngScal *sc, int which,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         double acc = 0.0;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) acc += a[i] * a[i];
         acc = block_total(acc);
@@ -227,11 +291,13 @@ __global__ void __launch_bounds__(kET) eng_norm_kernel(const SegChunk *chunks, c
 
 // p . q per slot; the slot's last chunk sets alpha = rz_new / (p . q) and rz = rz_new
 __global__ void __launch_bounds__(kET) eng_pq_kernel(const SegChunk *chunks, const int *count, const double *p,
-                                                     const double *q, double *partial, unsigned *ticket, EngScal *sc)
+                                                     const double *q, double *partial, unsigned *ticket, EngScal *sc,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         double acc = 0.0;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) acc += p[i] * q[i];
         acc = block_total(acc);
@@ -248,11 +314,13 @@ __global__ void __launch_bounds__(kET) eng_pq_kernel(const SegChunk *chunks, con
 // x += alpha p; r -= alpha q; r . r per slot into rr[slot]
 __global__ void __launch_bounds__(kET) eng_xr_kernel(const SegChunk *chunks, const int *count, const double *p,
                                                      const double *q, double *x, double *r, double *partial,
-                                                     unsigned *ticket, EngScal *sc, double *rr)
+                                                     unsigned *ticket, EngScal *sc, double *rr,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         const double alpha = sc[c.slot].alpha;
         double acc = 0.0;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
@@ -274,11 +342,13 @@ __global__ void __launch_bounds__(kET) eng_xr_kernel(const SegChunk *chunks, con
 __global__ void __launch_bounds__(kET) eng_rz_kernel(const SegChunk *chunks, const int *count, const double *r,
                                                      const double *z, const double *zp, double *partial,
                                                      double *partial2, unsigned *ticket, unsigned *ticket2,
-                                                     EngScal *sc)
+                                                     EngScal *sc,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         double a = 0.0, b = 0.0;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) {
             const double ri = r[i];
@@ -297,11 +367,13 @@ __global__ void __launch_bounds__(kET) eng_rz_kernel(const SegChunk *chunks, con
 
 // beta = rz_new / rz (flexible: (rz_new - cross) / rz); p = z + beta p
 __global__ void __launch_bounds__(kET) eng_p_kernel(const SegChunk *chunks, const int *count, const double *z,
-                                                    double *p, const EngScal *sc, int flexible)
+                                                    double *p, const EngScal *sc, int flexible,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         const EngScal s = sc[c.slot];
         const double beta = (flexible ? s.rz_new - s.cross : s.rz_new) / s.rz;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) p[i] = z[i] + beta * p[i];
@@ -309,22 +381,26 @@ __global__ void __launch_bounds__(kET) eng_p_kernel(const SegChunk *chunks, cons
 }
 
 __global__ void __launch_bounds__(kET) eng_copy_kernel(const SegChunk *chunks, const int *count, const double *src,
-                                                       double *dst)
+                                                       double *dst,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) dst[i] = src[i];
     }
 }
 
 template <typename A, typename B>
 __global__ void __launch_bounds__(kET) eng_convert_kernel(const SegChunk *chunks, const int *count, const A *src,
-                                                          B *dst)
+                                                          B *dst,
+        int nslots, int cap, EngGuard *guard)
 {
     const int n = *count;
     for (int t = blockIdx.x; t < n; t += gridDim.x) {
         const SegChunk c = chunks[t];
+        if (!chunk_ok(c, nslots, cap, guard)) continue;
         for (int i = c.begin + threadIdx.x; i < c.end; i += kET) dst[i] = (B)src[i];
     }
 }
@@ -358,7 +434,7 @@ __global__ void set_count_kernel(int *count, int value) { *count = value; }
 // instantiation with this shared-memory tile), capped by `grid` (the list's length bound).
 template <typename T, int LPR, int MODE>
 cudaError_t seg_launch_lpr(const SegTile *tiles, const int *count, const SegOp *ops, const T *x, T *y, const T *f,
-                           T *d, int coef_idx, int cap, int grid, cudaStream_t s)
+                           T *d, int coef_idx, int cap, int grid, const SegCtx &cx, cudaStream_t s)
 {
     static std::once_flag once;
     static cudaError_t cfg = cudaSuccess;
@@ -376,20 +452,20 @@ cudaError_t seg_launch_lpr(const SegTile *tiles, const int *count, const SegOp *
     AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, segtile_kernel<T, LPR, MODE>, kET, smem));
     const int g = std::max(1, std::min(grid, std::max(1, per_sm) * sms));
     segtile_kernel<T, LPR, MODE><<<g, kET, smem, s>>>(tiles, count, ops, x, y, f, d, coef_idx, cap,
-                                                      spmv_error_flag()); note_launch();
+                                                      spmv_error_flag(), cx.nslots, cx.xcap, cx.ycap, cx.guard); note_launch();
     return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 cudaError_t seg_launch(int lpr, const SegTile *tiles, const int *count, const SegOp *ops, const T *x, T *y,
-                       const T *f, T *d, int coef_idx, int cap, int grid, cudaStream_t s)
+                       const T *f, T *d, int coef_idx, int cap, int grid, const SegCtx &cx, cudaStream_t s)
 {
     switch (lpr) {
-    case 2: return seg_launch_lpr<T, 2, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
-    case 4: return seg_launch_lpr<T, 4, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
-    case 8: return seg_launch_lpr<T, 8, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
-    case 16: return seg_launch_lpr<T, 16, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
-    default: return seg_launch_lpr<T, 32, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, s);
+    case 2: return seg_launch_lpr<T, 2, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, cx, s);
+    case 4: return seg_launch_lpr<T, 4, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, cx, s);
+    case 8: return seg_launch_lpr<T, 8, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, cx, s);
+    case 16: return seg_launch_lpr<T, 16, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, cx, s);
+    default: return seg_launch_lpr<T, 32, MODE>(tiles, count, ops, x, y, f, d, coef_idx, cap, grid, cx, s);
     }
 }
 
@@ -473,6 +549,8 @@ Engine::~Engine()
     cudaStreamSynchronize(s_);
     if (rr_host_) cudaFreeHost(rr_host_);
     if (hflags_) cudaFreeHost(hflags_);
+    for (cudaEvent_t e : flag_ev_)
+        if (e) cudaEventDestroy(e);
 }
 
 void Engine::drop_graphs()
@@ -525,8 +603,11 @@ amg_status_t Engine::init(const Config &c, cudaStream_t s)
     EK(cudaMemsetAsync(ticket_, 0, sizeof(unsigned) * S, s_));
     EK(cudaMemsetAsync(ticket2_, 0, sizeof(unsigned) * S, s_));
     EK(alloc(&caps_dev_, (size_t)(3 * kEngLevels + 1)));
+    EK(alloc(&guard_, 1));
+    EK(cudaMemsetAsync(guard_, 0, sizeof(EngGuard), s_));
     EK(cudaMallocHost(&rr_host_, sizeof(double) * S));
     EK(cudaMallocHost(&hflags_, sizeof(int) * 2 * S));
+    for (cudaEvent_t &e : flag_ev_) EK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     std::memset(hflags_, 0, sizeof(int) * 2 * S);
     for (double **v : {&b_, &x_, &r_, &p_, &q_, &t_, &zb_[0]}) EK(alloc(v, n0));
     if (c.mixed) EK(alloc(&zb_[1], n0));
@@ -609,18 +690,19 @@ int Engine::add(amg_hierarchy *h)
         cheb_table(lv.lambda_cheb, h->p, &hcoef_[ci]);
         hA_[i] = SegOp{lv.A.rp, lv.A.ci, mixed ? (const void *)lv.Af : (const void *)lv.A.v,
                        mixed ? (const void *)lv.invdiag_f : (const void *)lv.invdiag, coef_ + ci, (int)sl.off[L],
-                       (int)sl.off[L]};
+                       (int)sl.off[L], lv.A.n, lv.A.n, (int)lv.A.nnz, 0};
         hP_[i] = SegOp{lv.P.rp, lv.P.ci, mixed ? (const void *)lv.Pf : (const void *)lv.P.v, nullptr, nullptr,
-                       (int)sl.off[L + 1], (int)sl.off[L]};
+                       (int)sl.off[L + 1], (int)sl.off[L], lv.P.n, lv.P.ncol, (int)lv.P.nnz, 0};
         hR_[i] = SegOp{lv.R.rp, lv.R.ci, mixed ? (const void *)lv.Rf : (const void *)lv.R.v, nullptr, nullptr,
-                       (int)sl.off[L], (int)sl.off[L + 1]};
+                       (int)sl.off[L], (int)sl.off[L + 1], lv.R.n, lv.R.ncol, (int)lv.R.nnz, 0};
     }
     {
         const int L = h->nlev - 1;
         hC_[(size_t)L * S + k] = SegCoarse{h->coarse_inv, h->lev[L].A.n, (int)sl.off[L], k, 0};
     }
     const Level &l0 = h->lev[0];
-    h0_[k] = SegOp{l0.A.rp, l0.A.ci, l0.A.v, nullptr, nullptr, (int)sl.o0, (int)sl.o0};
+    h0_[k] = SegOp{l0.A.rp, l0.A.ci, l0.A.v, nullptr, nullptr, (int)sl.o0, (int)sl.o0, l0.A.n, l0.A.n,
+                   (int)l0.A.nnz, 0};
     slots_[k] = sl;
     members_changed_ = true;
     return k;
@@ -766,9 +848,13 @@ cudaError_t Engine::compact(bool active)
 
 cudaError_t Engine::push_flags(const std::vector<int> &v, int *dst)
 {
-    int *h = dst == active_ ? hflags_ : hflags_ + slots_.size();
+    const int half = dst == active_ ? 0 : 1;
+    int *h = hflags_ + (half ? slots_.size() : 0);
+    // the previous upload from this half must have read it before it is rewritten
+    AMG_CUDA_TRY(cudaEventSynchronize(flag_ev_[half]));
     for (size_t i = 0; i < v.size(); ++i) h[i] = v[i];
-    return cudaMemcpyAsync(dst, h, sizeof(int) * v.size(), cudaMemcpyHostToDevice, s_);
+    AMG_CUDA_TRY(cudaMemcpyAsync(dst, h, sizeof(int) * v.size(), cudaMemcpyHostToDevice, s_));
+    return cudaEventRecord(flag_ev_[half], s_);
 }
 
 // Lanes per row of every tile list, chosen by timing each candidate on the current members
@@ -799,17 +885,18 @@ cudaError_t Engine::autotune()
             set_count_kernel<<<1, 1, 0, s_>>>(l.count + 2, l.nfull); note_launch();
             // x: the level's (or, for P, the next level's) iterate; y: a scratch vector
             const bool coarse_cols = kind == 1 || L > 0;
+            const SegCtx cx = fine ? ctx(0, 0) : ctx(kind == 1 || L > 0 ? 1 : 0, kind == 2 || L > 0 ? 1 : 0);
             auto run = [&]() -> cudaError_t {
                 if (fine)
                     return seg_launch<double, SK_Y>(lpr, l.full, l.count + 2, ops, x_, q_, nullptr, nullptr, 0, l.cap,
-                                                    1 << 30, s_);
+                                                    1 << 30, cx, s_);
                 void *xs = (kind == 2) ? (L == 0 ? r0_ : rc_) : (coarse_cols ? xc_ : x0_);
                 void *ys = (kind == 2) ? fc_ : (L == 0 ? x20_ : x2c_);
                 if (cfg_.mixed)
                     return seg_launch<float, SK_Y>(lpr, l.full, l.count + 2, ops, (const float *)xs, (float *)ys,
-                                                   nullptr, nullptr, 0, l.cap, 1 << 30, s_);
+                                                   nullptr, nullptr, 0, l.cap, 1 << 30, cx, s_);
                 return seg_launch<double, SK_Y>(lpr, l.full, l.count + 2, ops, (const double *)xs, (double *)ys,
-                                                nullptr, nullptr, 0, l.cap, 1 << 30, s_);
+                                                nullptr, nullptr, 0, l.cap, 1 << 30, cx, s_);
             };
             if ((err = run()) != cudaSuccess) break;
             if ((err = cudaEventRecord(e0, s_)) != cudaSuccess) break;
@@ -852,6 +939,34 @@ void Engine::heuristic_lanes()
     }
 }
 
+SegCtx Engine::ctx(int xl, int yl) const
+{
+    const int c0 = (int)std::max<int64_t>(cfg_.cap0, 1), cc = (int)std::max<int64_t>(cfg_.capc, 1);
+    return SegCtx{(int)slots_.size(), xl ? cc : c0, yl ? cc : c0, guard_};
+}
+
+std::string Engine::take_guard(int *slot)
+{
+    EngGuard g{};
+    if (cudaMemcpyAsync(&g, guard_, sizeof g, cudaMemcpyDeviceToHost, s_) != cudaSuccess ||
+        cudaStreamSynchronize(s_) != cudaSuccess)
+        return "guard unreadable";
+    if (g.count == 0) return std::string();
+    cudaMemsetAsync(guard_, 0, sizeof(EngGuard), s_);
+    static const char *kinds[] = {"?", "spmv tile", "chebyshev start", "coarse solve", "pcg chunk"};
+    if (slot) *slot = g.slot;
+    std::string info;
+    if (g.kind == 1) {
+        static const char *names[12] = {"row0", "rows", "n", "ncol", "nnz", "k0", "k1", "xoff", "yoff", "xcap",
+                                        "ycap", "rp0"};
+        for (int k = 0; k < 12; ++k) info += std::string(k ? " " : " (") + names[k] + "=" + std::to_string(g.info[k]);
+        info += ")";
+    }
+    return std::to_string(g.count) + " work items outside their arrays; first: " +
+           kinds[(g.kind >= 1 && g.kind <= 4) ? g.kind : 0] + " of slot " + std::to_string(g.slot) + " at " +
+           std::to_string(g.where) + info;
+}
+
 std::string Engine::describe() const
 {
     std::string s = "fine:" + std::to_string(l0_.lpr);
@@ -892,7 +1007,7 @@ amg_status_t Engine::commit()
         if (!sl.used || !sl.pending) continue;
         flags[k] = 1;
         any = true;
-        if (sl.n0 > 0) EK(cudaMemcpyAsync(b_ + sl.o0, sl.b, sizeof(double) * (size_t)sl.n0, cudaMemcpyDefault, s_));
+        if (sl.n0 > 0) EK(copy_to_device(b_ + sl.o0, sl.b, sizeof(double) * (size_t)sl.n0, s_));
         if (sl.active) {
             sl.active = 0;
             --live_;
@@ -910,13 +1025,23 @@ amg_status_t Engine::commit()
     {
         const int parity_next = cfg_.mixed ? (it_ & 1) : 0;
         double *zp = cfg_.mixed ? zb_[1 - parity_next] : nullptr;
-        eng_init_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, x_, r_, p_, zp, sc_); note_launch();
-        eng_norm_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, partial_, ticket_, sc_, 0); note_launch();
+        const SegCtx cx = ctx(0, 0);
+        eng_init_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, x_, r_, p_, zp, sc_, cx.nslots,
+                                                      cx.ycap, cx.guard); note_launch();
+        eng_norm_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, b_, partial_, ticket_, sc_, 0,
+                                                      cx.nslots, cx.ycap, cx.guard); note_launch();
         EK(cudaGetLastError());
     }
     std::vector<EngScal> hs((size_t)S);
     EK(cudaMemcpyAsync(hs.data(), sc_, sizeof(EngScal) * S, cudaMemcpyDeviceToHost, s_));
     EK(cudaStreamSynchronize(s_));
+    {
+        const std::string g = take_guard();
+        if (!g.empty()) {
+            set_last_error("engine guard: " + g);
+            return AMG_ERR_INTERNAL;
+        }
+    }
     std::vector<int> act((size_t)S, 0);
     for (int k = 0; k < S; ++k) {
         Slot &sl = slots_[k];
@@ -944,7 +1069,9 @@ cudaError_t Engine::vcycle(int L, const T *f, T *final_out, T **out, cudaStream_
     T *rv = (T *)(L == 0 ? r0_ : rc_), *d = (T *)(L == 0 ? d0_ : dc_);
     auto coarse = [&](T *dst) -> cudaError_t {
         if (lC_[L].nfull == 0) return cudaSuccess;
-        segcoarse_kernel<T><<<grid_tiles_, kET, 0, s>>>(lC_[L].act, lC_[L].count, f, dst); note_launch();
+        const SegCtx cx = ctx(L > 0, L > 0);
+        segcoarse_kernel<T><<<grid_tiles_, kET, 0, s>>>(lC_[L].act, lC_[L].count, f, dst, cx.nslots, cx.ycap,
+                                                        cx.guard); note_launch();
         return cudaGetLastError();
     };
     if (L == nlev_ - 1) {
@@ -954,25 +1081,27 @@ cudaError_t Engine::vcycle(int L, const T *f, T *final_out, T **out, cudaStream_
     const SegOp *opA = opA_ + (size_t)L * S, *opP = opP_ + (size_t)L * S, *opR = opR_ + (size_t)L * S;
     EngList<SegTile> &la = lA_[L], &lp = lP_[L], &lr = lR_[L];
     const int deg = cfg_.degree;
-    segcheb0_kernel<T><<<grid_tiles_, kET, 0, s>>>(la.act, la.count, opA, f, d, x); note_launch();
+    const SegCtx ca = ctx(L > 0, L > 0), cp = ctx(1, L > 0), cr = ctx(L > 0, 1);
+    segcheb0_kernel<T><<<grid_tiles_, kET, 0, s>>>(la.act, la.count, opA, f, d, x, ca.nslots, ca.ycap, ca.guard); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     for (int k = 1; k < deg; ++k) {
         AMG_CUDA_TRY((seg_launch<T, SK_CHEB>(la.lpr, la.act, la.count, opA, x, x2, f, d, 1 + 2 * k, la.cap,
-                                             1 << 30, s)));
+                                             1 << 30, ca, s)));
         std::swap(x, x2);
     }
     T *fc = (T *)fc_;
-    AMG_CUDA_TRY((seg_launch<T, SK_RESID>(la.lpr, la.act, la.count, opA, x, rv, f, nullptr, 0, la.cap, 1 << 30, s)));
+    AMG_CUDA_TRY((seg_launch<T, SK_RESID>(la.lpr, la.act, la.count, opA, x, rv, f, nullptr, 0, la.cap, 1 << 30, ca,
+                                          s)));
     AMG_CUDA_TRY((seg_launch<T, SK_Y>(lr.lpr, lr.act, lr.count, opR, rv, fc, nullptr, nullptr, 0, lr.cap, grid_tiles_,
-                                      s)));
+                                      cr, s)));
     T *xcv = nullptr;
     AMG_CUDA_TRY(vcycle<T>(L + 1, fc, nullptr, &xcv, s));
     AMG_CUDA_TRY((seg_launch<T, SK_PROLONG>(lp.lpr, lp.act, lp.count, opP, xcv, x, nullptr, nullptr, 0, lp.cap,
-                                            1 << 30, s)));
+                                            1 << 30, cp, s)));
     for (int k = 0; k < deg; ++k) {
         T *dst = (final_out && k == deg - 1) ? final_out : x2;
         AMG_CUDA_TRY((seg_launch<T, SK_CHEB>(la.lpr, la.act, la.count, opA, x, dst, f, d, 1 + 2 * k, la.cap,
-                                             1 << 30, s)));
+                                             1 << 30, ca, s)));
         x2 = x;
         x = dst;
     }
@@ -982,46 +1111,56 @@ cudaError_t Engine::vcycle(int L, const T *f, T *final_out, T **out, cudaStream_
 
 cudaError_t Engine::tail(int parity, cudaStream_t s)
 {
+    const SegCtx c0 = ctx(0, 0);
     double *z = zb_[cfg_.mixed ? parity : 0];
     double *zp = cfg_.mixed ? zb_[1 - parity] : nullptr;
     if (nlev_ > 0) {
         if (cfg_.mixed) {
-            eng_convert_kernel<double, float><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, r_, (float *)f0_); note_launch();
+            eng_convert_kernel<double, float><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, r_, (float *)f0_,
+                                                                          c0.nslots, c0.ycap, c0.guard); note_launch();
             AMG_CUDA_TRY(cudaGetLastError());
             float *out = nullptr;
             AMG_CUDA_TRY(vcycle<float>(0, (const float *)f0_, nullptr, &out, s));
-            eng_convert_kernel<float, double><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z); note_launch();
+            eng_convert_kernel<float, double><<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z, c0.nslots,
+                                                                          c0.ycap, c0.guard); note_launch();
             AMG_CUDA_TRY(cudaGetLastError());
         } else {
             double *out = nullptr;
             AMG_CUDA_TRY(vcycle<double>(0, r_, z, &out, s));
             if (out != z) {
-                eng_copy_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z); note_launch();
+                eng_copy_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, out, z, c0.nslots, c0.ycap,
+                                                             c0.guard); note_launch();
                 AMG_CUDA_TRY(cudaGetLastError());
             }
         }
     }
     eng_rz_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, r_, z, zp, partial_, partial2_, ticket_, ticket2_,
-                                               sc_); note_launch();
-    eng_p_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, z, p_, sc_, zp ? 1 : 0); note_launch();
+                                               sc_, c0.nslots, c0.ycap, c0.guard); note_launch();
+    eng_p_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, z, p_, sc_, zp ? 1 : 0, c0.nslots, c0.ycap,
+                                              c0.guard); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t Engine::head(cudaStream_t s)
 {
+    const SegCtx c0 = ctx(0, 0);
     AMG_CUDA_TRY((seg_launch<double, SK_Y>(l0_.lpr, l0_.act, l0_.count, op0_, p_, q_, nullptr, nullptr, 0, l0_.cap,
-                                           1 << 30, s)));
-    eng_pq_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, partial_, ticket_, sc_); note_launch();
-    eng_xr_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, x_, r_, partial_, ticket_, sc_, rr_dev_); note_launch();
+                                           1 << 30, c0, s)));
+    eng_pq_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, partial_, ticket_, sc_, c0.nslots, c0.ycap,
+                                               c0.guard); note_launch();
+    eng_xr_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.act, lch_.count, p_, q_, x_, r_, partial_, ticket_, sc_, rr_dev_,
+                                               c0.nslots, c0.ycap, c0.guard); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     return cudaMemcpyAsync(rr_host_, rr_dev_, sizeof(double) * slots_.size(), cudaMemcpyDeviceToHost, s);
 }
 
 cudaError_t Engine::true_residual(cudaStream_t s)
 {
+    const SegCtx c0 = ctx(0, 0);
     AMG_CUDA_TRY((seg_launch<double, SK_RESID>(l0_.lpr, l0_.flg, l0_.count + 1, op0_, x_, t_, b_, nullptr, 0, l0_.cap,
-                                               1 << 30, s)));
-    eng_norm_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.flg, lch_.count + 1, t_, partial_, ticket_, sc_, 1); note_launch();
+                                               1 << 30, c0, s)));
+    eng_norm_kernel<<<grid_chunks_, kET, 0, s>>>(lch_.flg, lch_.count + 1, t_, partial_, ticket_, sc_, 1, c0.nslots,
+                                                 c0.ycap, c0.guard); note_launch();
     return cudaGetLastError();
 }
 
@@ -1069,6 +1208,23 @@ amg_status_t Engine::step(std::vector<int> *finished)
     for (auto &sl : slots_)
         if (sl.used && sl.active) ++sl.iters;
     EK(cudaStreamSynchronize(s_));
+    {
+        int gslot = -1;
+        const std::string g = take_guard(&gslot);
+        if (!g.empty()) {
+            // is the slot's hierarchy itself still intact?
+            std::string what = "; hierarchy of the slot ";
+            if (gslot >= 0 && gslot < S && slots_[gslot].used) {
+                std::string detail;
+                const int f = hierarchy_check(slots_[gslot].h, s_, &detail);
+                what += f == 0 ? "intact" : (f < 0 ? "not checkable" : "damaged: " + detail);
+            } else {
+                what += "not in use";
+            }
+            set_last_error("engine guard: " + g + what);
+            return AMG_ERR_INTERNAL;
+        }
+    }
     std::vector<int> flags((size_t)S, 0), act((size_t)S, 0);
     std::vector<int> stopped;
     bool any = false;
@@ -1104,7 +1260,9 @@ amg_status_t Engine::step(std::vector<int> *finished)
         if (replace) {
             EK(push_flags(flags, flag_));
             EK(compact(false));
-            eng_copy_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, t_, r_); note_launch();
+            const SegCtx c0 = ctx(0, 0);
+            eng_copy_kernel<<<grid_chunks_, kET, 0, s_>>>(lch_.flg, lch_.count + 1, t_, r_, c0.nslots, c0.ycap,
+                                                          c0.guard); note_launch();
             EK(cudaGetLastError());
         }
     }
@@ -1144,8 +1302,7 @@ amg_status_t Engine::download(int k, double *x)
 {
     const Slot &sl = slots_[k];
     if (sl.n0 == 0) return AMG_OK;
-    EK(cudaMemcpyAsync(x, x_ + sl.o0, sizeof(double) * (size_t)sl.n0, cudaMemcpyDefault, s_));
-    EK(cudaStreamSynchronize(s_));
+    EK(copy_to_host(x, x_ + sl.o0, sizeof(double) * (size_t)sl.n0, s_));
     return AMG_OK;
 }
 

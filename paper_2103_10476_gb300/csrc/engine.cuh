@@ -31,6 +31,14 @@ struct SegOp {          // one slot's matrix on one level, with where its vector
     const void *invd;   // 1 / diag (A only), working type
     const double *coef; // Chebyshev coefficients of this slot and level (A only)
     int xoff, yoff;     // offsets of the column-indexed and row-indexed vectors
+    int n, ncol;        // rows and columns (checked against each tile and the vectors)
+    int nnz, pad;
+};
+// Guard of the engine's kernels: a work item that would reach outside its matrix or vector
+// arena is skipped and recorded here (count, then the first item's kind, slot, position).
+struct EngGuard {
+    int count, kind, slot, where;
+    int info[12];       // the first item's tile, matrix and vector figures
 };
 struct SegCoarse {      // dense solve of a slot whose coarsest level this is
     const double *inv;
@@ -41,6 +49,13 @@ struct SegChunk {       // at most kEngChunk fine rows of one slot (PCG vector k
 };
 struct EngScal {        // per-slot PCG scalars (device)
     double rz, rz_new, cross, alpha, pq, rr, tt, bb;
+};
+
+// what a launch needs for the guard checks: the slot count, the lengths of the arenas its
+// column-indexed and row-indexed vectors live in, and the guard record
+struct SegCtx {
+    int nslots, xcap, ycap;
+    EngGuard *guard;
 };
 
 // a list of work items: host copy, the full device list, and the lists compacted by the
@@ -97,6 +112,8 @@ public:
     long long kernels_per_iteration() const { return gkernels_[0]; }
     size_t bytes() const { return bytes_; }
     std::string describe() const;   // lanes per row chosen for each list
+    // a guard violation recorded since the last call (message), or empty; *slot = its slot
+    std::string take_guard(int *slot = nullptr);
 
 private:
     template <typename T>
@@ -115,6 +132,8 @@ private:
     cudaError_t true_residual(cudaStream_t s);   // t = b - A x, |t|^2 for the flagged slots
     cudaGraphExec_t graph(int parity);
     void drop_graphs();
+    // guard context of a launch whose vectors are in arena xl / yl (0 fine, 1 coarse levels)
+    SegCtx ctx(int xl, int yl) const;
     int64_t arena_take(std::vector<std::pair<int64_t, int64_t>> &free_list, int64_t n);
     void arena_give(std::vector<std::pair<int64_t, int64_t>> &free_list, int64_t off, int64_t n);
 
@@ -143,10 +162,12 @@ private:
     // masks and scalars
     int *active_ = nullptr, *flag_ = nullptr;
     int *hflags_ = nullptr;         // pinned: [0, slots) active, [slots, 2 slots) flag
+    cudaEvent_t flag_ev_[2] = {nullptr, nullptr};   // the last upload from each half of hflags_
     EngScal *sc_ = nullptr;
     double *partial_ = nullptr, *partial2_ = nullptr, *rr_dev_ = nullptr, *rr_host_ = nullptr;
     unsigned *ticket_ = nullptr, *ticket2_ = nullptr;
     int *caps_dev_ = nullptr;
+    EngGuard *guard_ = nullptr;     // device
     // arenas: level 0 (FP64 PCG vectors; working-type V-cycle vectors) and coarser levels
     double *b_ = nullptr, *x_ = nullptr, *r_ = nullptr, *p_ = nullptr, *q_ = nullptr, *t_ = nullptr;
     double *zb_[2] = {nullptr, nullptr};

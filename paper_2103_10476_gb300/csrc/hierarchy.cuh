@@ -68,4 +68,9 @@ namespace amgk {
 // status plumbing shared by the ABI files
 amg_status_t fail_cuda(cudaError_t e, const char *where);
 void set_last_error(const std::string &msg);
+// structural check of the operators a solve reads (A of every level, P and R of every level
+// but the coarsest): row pointers start at 0, do not decrease and end at nnz, columns lie in
+// range.  Returns the number of faults found (0: intact; -1: the check itself failed) and
+// names the first in *detail.  Synchronises s.
+int hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail);
 }  // namespace amgk

@@ -136,6 +136,7 @@ struct amg_server {
     size_t cache_bytes = 0;
     size_t eng_bytes = 0;           // the engine's device bytes (updated by the engine thread)
     double per_nnz = 64.0;          // admission estimate of hierarchy bytes per stored entry
+    std::string first_error;        // the first failure's message
     double per_nnz_seen = 0.0;
     bool stop = false, workers_done = false;
     amg_server_stats_t stats{};
@@ -147,6 +148,12 @@ struct amg_server {
 
 namespace amgk {
 namespace {
+
+// under the lock: the first failure's message is kept for amg_server_stats
+void note_error(amg_server *S, const std::string &msg)
+{
+    if (S->first_error.empty()) S->first_error = msg.empty() ? std::string("unknown") : msg;
+}
 
 // under the lock: a finished request is visible to poll/wait; its hierarchy becomes evictable
 void finish_request(amg_server *S, Request *r, amg_status_t status)
@@ -197,6 +204,7 @@ void worker_loop(amg_server *S)
         lk.lock();
         if (!err.empty()) {
             set_last_error("operator hash: " + err);
+            note_error(S, "operator hash: " + err);
             finish_request(S, r, AMG_ERR_CUDA);
             S->stats.failed++;
             continue;
@@ -238,6 +246,7 @@ void worker_loop(amg_server *S)
         }
         S->stats.cache_misses++;
         if (!fits) {
+            note_error(S, "a hierarchy larger than the HBM budget");
             finish_request(S, r, AMG_ERR_BUDGET);
             S->stats.failed++;
             continue;
@@ -257,7 +266,33 @@ void worker_loop(amg_server *S)
         const amg_status_t st = amg_setup(&r->A, nullptr, &p, &h);
         const double t1 = now_ms();
         const std::string msg = st == AMG_OK ? std::string() : std::string(amg_last_error());
+        // the new hierarchy's structure is checked before anything solves with it
+        amg_status_t st2 = st;
+        std::string chk;
+        if (st == AMG_OK) {
+            const int f = hierarchy_check(h, ws, &chk);
+            if (f != 0) {
+                st2 = AMG_ERR_INTERNAL;
+                chk = "setup produced an inconsistent hierarchy: " + (f < 0 ? std::string("check failed") : chk);
+                amg_free(h);
+                h = nullptr;
+            }
+        }
         lk.lock();
+        if (st2 != AMG_OK && st == AMG_OK) {
+            S->cache.erase(key);
+            S->cache_bytes -= e->bytes;
+            std::vector<Request *> all(e->waiters);
+            all.push_back(r);
+            for (Request *w : all) {
+                w->e = nullptr;
+                finish_request(S, w, st2);
+                S->stats.failed++;
+            }
+            note_error(S, chk);
+            delete e;
+            continue;
+        }
         if (st == AMG_OK) {
             // the engine's stream orders the eventual release after the engine's last use
             h->s = S->es;
@@ -291,6 +326,7 @@ void worker_loop(amg_server *S)
                 finish_request(S, w, st);
                 S->stats.failed++;
             }
+            note_error(S, std::string("setup: ") + amg_status_string(st) + ": " + msg);
             set_last_error(msg);
             delete e;
         }
@@ -321,6 +357,7 @@ void engine_loop(amg_server *S)
                 // a request that can never fit the engine fails at once
                 if (r->A.n > max_rows || r->nrhs > max_sys) {
                     set_last_error("request larger than the engine's capacity");
+                    note_error(S, "request larger than the engine's capacity");
                     finish_request(S, r, AMG_ERR_BUDGET);
                     S->stats.failed++;
                     continue;
@@ -367,7 +404,9 @@ void engine_loop(amg_server *S)
         }
         if (st != AMG_OK) {
             // the engine failed: every request in it fails; the engine starts over empty
+            const std::string msg = std::string("engine: ") + amg_status_string(st) + ": " + amg_last_error();
             std::lock_guard<std::mutex> g(S->mu);
+            note_error(S, msg);
             for (auto &kv : owner) {
                 Request *r = kv.second.first;
                 E.remove(kv.first);
@@ -536,6 +575,8 @@ amg_status_t amg_server_stats(amg_server_t S, amg_server_stats_t *out)
     *out = S->stats;
     out->bytes_hierarchies = S->cache_bytes;
     out->bytes_engine = S->eng_bytes;
+    std::memset(out->first_error, 0, sizeof out->first_error);
+    std::strncpy(out->first_error, S->first_error.c_str(), sizeof out->first_error - 1);
     int n = 0;
     for (auto &kv : S->cache) n += kv.second->state == 1;
     out->resident_hierarchies = n;

@@ -12,6 +12,8 @@
 #include <stdio.h>
 #include <string>
 
+#include <vector>
+
 #include "amg_internal.cuh"
 
 namespace amgk {
@@ -452,13 +454,15 @@ cudaError_t global_tables(int cnt, const int *rows, const int *tsize, int **toff
     AMG_CUDA_TRY(cudaMallocAsync(toff, sizeof(int) * (size_t)(cnt + 1), s));
     gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, tsize, *toff); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
-    AMG_CUDA_TRY(scan_exclusive(*toff, *toff, cnt, s));
-    int h = 0;
-    AMG_CUDA_TRY(cudaMemcpyAsync(&h, *toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // the int offsets must not wrap: the sizes are summed in 64 bits before the int scan
+    std::vector<int> sizes((size_t)cnt);
+    AMG_CUDA_TRY(cudaMemcpyAsync(sizes.data(), *toff, sizeof(int) * (size_t)cnt, cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    *total = h;
-    // the int offsets must not wrap
-    if (h < 0) return cudaErrorMemoryAllocation;
+    int64_t sum = 0;
+    for (int v : sizes) sum += v;
+    if (sum > 0x7fffffffLL) return cudaErrorMemoryAllocation;
+    AMG_CUDA_TRY(scan_exclusive(*toff, *toff, cnt, s));
+    *total = sum;
     return cudaSuccess;
 }
 

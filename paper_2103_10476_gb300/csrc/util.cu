@@ -1,6 +1,8 @@
 // util.cu -- scans, fills, conversions, deterministic reductions, and the launch counter and
 // event-based kernel timing used for roofline reports.
+#include <algorithm>
 #include <atomic>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -364,6 +366,100 @@ cudaError_t reduce_partials(const double *partial, int count, double *out, cudaS
 {
     reduce_partials_kernel<<<1, kReduceThreads, 0, s>>>(partial, count, out); note_launch();
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------ host copies
+// Memory the caller allocated with malloc / numpy (not allocated or registered by CUDA) is
+// never handed to the copy engines: it moves through two pinned bounce halves of this
+// thread, and the CPU alone reads or writes the caller's pages.  Device, managed and pinned
+// memory is copied directly.
+namespace {
+constexpr size_t kBounceHalf = (size_t)4 << 20;
+
+struct Bounce {
+    unsigned char *buf = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    ~Bounce()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (buf) cudaFreeHost(buf);
+    }
+};
+thread_local Bounce t_bounce;
+
+cudaError_t bounce_ready()
+{
+    Bounce &b = t_bounce;
+    if (b.buf) return cudaSuccess;
+    AMG_CUDA_TRY(cudaMallocHost((void **)&b.buf, 2 * kBounceHalf));
+    for (cudaEvent_t &e : b.ev) AMG_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return cudaSuccess;
+}
+
+bool caller_pageable(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered;
+}
+}  // namespace
+
+cudaError_t copy_to_device(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (!caller_pageable(src)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    AMG_CUDA_TRY(bounce_ready());
+    Bounce &b = t_bounce;
+    const unsigned char *in = (const unsigned char *)src;
+    unsigned char *out = (unsigned char *)dst;
+    bool used[2] = {false, false};
+    for (size_t off = 0, k = 0; off < bytes; off += kBounceHalf, ++k) {
+        const int h = (int)(k & 1);
+        const size_t n = std::min(kBounceHalf, bytes - off);
+        if (used[h]) AMG_CUDA_TRY(cudaEventSynchronize(b.ev[h]));   // the half's last copy is done
+        std::memcpy(b.buf + h * kBounceHalf, in + off, n);
+        AMG_CUDA_TRY(cudaMemcpyAsync(out + off, b.buf + h * kBounceHalf, n, cudaMemcpyHostToDevice, s));
+        AMG_CUDA_TRY(cudaEventRecord(b.ev[h], s));
+        used[h] = true;
+    }
+    // the halves are reused by this thread's next copy: wait for the last ones
+    for (int h = 0; h < 2; ++h)
+        if (used[h]) AMG_CUDA_TRY(cudaEventSynchronize(b.ev[h]));
+    return cudaSuccess;
+}
+
+cudaError_t copy_to_host(void *dst, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (!caller_pageable(dst)) {
+        AMG_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+        return cudaStreamSynchronize(s);
+    }
+    AMG_CUDA_TRY(bounce_ready());
+    Bounce &b = t_bounce;
+    const unsigned char *in = (const unsigned char *)src;
+    unsigned char *out = (unsigned char *)dst;
+    const size_t chunks = (bytes + kBounceHalf - 1) / kBounceHalf;
+    // chunk k lands in half k & 1; the CPU drains chunk k while chunk k + 1 is in flight
+    auto issue = [&](size_t k) -> cudaError_t {
+        const size_t off = k * kBounceHalf, n = std::min(kBounceHalf, bytes - off);
+        const int h = (int)(k & 1);
+        AMG_CUDA_TRY(cudaMemcpyAsync(b.buf + h * kBounceHalf, in + off, n, cudaMemcpyDeviceToHost, s));
+        return cudaEventRecord(b.ev[h], s);
+    };
+    AMG_CUDA_TRY(issue(0));
+    for (size_t k = 0; k < chunks; ++k) {
+        if (k + 1 < chunks) AMG_CUDA_TRY(issue(k + 1));
+        const int h = (int)(k & 1);
+        AMG_CUDA_TRY(cudaEventSynchronize(b.ev[h]));
+        const size_t off = k * kBounceHalf, n = std::min(kBounceHalf, bytes - off);
+        std::memcpy(out + off, b.buf + h * kBounceHalf, n);
+    }
+    return cudaStreamSynchronize(s);
 }
 
 }  // namespace amgk

@@ -117,16 +117,55 @@ def _axis_options(h: np.ndarray, dirichlet: bool):
     return nn, opts
 
 
-def q1_matrix(hx, hy, hz, coef=None, dirichlet: bool = True) -> CSR:
+_GEN = None
+
+
+def _gen_lib():
+    """The C assembly of q1gen.c (built on first use)."""
+    global _GEN
+    if _GEN is None:
+        import ctypes as C
+        from . import build as _build
+        L = C.CDLL(_build.build_generator())
+        L.q1_assemble.restype = C.c_int64
+        L.q1_assemble.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        _GEN = L
+    return _GEN
+
+
+def _q1_matrix_c(hx, hy, hz, coef, dirichlet: bool) -> CSR:
+    L = _gen_lib()
+    nex, ney, nez = len(hx), len(hy), len(hz)
+    nx, ny, nz = ((nex - 1, ney - 1, nez - 1) if dirichlet else (nex + 1, ney + 1, nez + 1))
+    n = max(nx, 0) * max(ny, 0) * max(nz, 0)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    col = np.empty(27 * n, dtype=np.int32)
+    val = np.empty(27 * n, dtype=np.float64)
+    c = None if coef is None else np.ascontiguousarray(coef, dtype=np.float64)
+    nnz = L.q1_assemble(nex, ney, nez, hx.ctypes.data, hy.ctypes.data, hz.ctypes.data,
+                        None if c is None else c.ctypes.data, int(dirichlet), rp.ctypes.data, col.ctypes.data,
+                        val.ctypes.data)
+    if nnz < 0:
+        raise MemoryError("q1_assemble")
+    return CSR(n, rp, col[:nnz], val[:nnz], meta={"grid": (nx, ny, nz)})
+
+
+def q1_matrix(hx, hy, hz, coef=None, dirichlet: bool = True, engine: str = "numpy") -> CSR:
     """Assemble the Q1 finite-element diffusion matrix on a tensor mesh.
+
+    engine "c" runs the same assembly (the same operations in the same order, so the same
+    bits) in q1gen.c, for large operators.
 
     hx, hy, hz: element sizes along each axis (lengths nex, ney, nez).
     coef: per-element coefficient, shape (nez, ney, nex) (element order
           e = ex + nex (ey + ney ez)), or None for 1.
     """
-    hx = np.asarray(hx, dtype=np.float64)
-    hy = np.asarray(hy, dtype=np.float64)
-    hz = np.asarray(hz, dtype=np.float64)
+    hx = np.ascontiguousarray(hx, dtype=np.float64)
+    hy = np.ascontiguousarray(hy, dtype=np.float64)
+    hz = np.ascontiguousarray(hz, dtype=np.float64)
+    if engine == "c":
+        return _q1_matrix_c(hx, hy, hz, coef, dirichlet)
     nx, ox = _axis_options(hx, dirichlet)
     ny, oy = _axis_options(hy, dirichlet)
     nz, oz = _axis_options(hz, dirichlet)
@@ -182,17 +221,17 @@ def laplace_cube(N: int) -> CSR:
     return A
 
 
-def stretched_box(N: int, ratio: float = 1.1) -> CSR:
+def stretched_box(N: int, ratio: float = 1.1, engine: str = "numpy") -> CSR:
     """N^3 interior nodes; unit spacing in x and y, z element layers h_z(k) = ratio^k,
     k = 0..N (the stretched-mesh setting of §1.2 and §3.2: aspect ratios 1 to ratio^N)."""
     hxy = np.ones(N + 1)
     hz = ratio ** np.arange(N + 1, dtype=np.float64)
-    A = q1_matrix(hxy, hxy, hz)
+    A = q1_matrix(hxy, hxy, hz, engine=engine)
     A.meta.update(family="stretched_box", N=N, ratio=ratio)
     return A
 
 
-def random_coefficient_cube(N: int, seed: int, decades: float = 3.0) -> CSR:
+def random_coefficient_cube(N: int, seed: int, decades: float = 3.0, engine: str = "numpy") -> CSR:
     """Unit cube, N^3 interior nodes, per-element coefficient 10^(2*decades*u - decades),
     u ~ U[0, 1) from SplitMix64(seed) in element order (the coefficient-variation setting
     of §3.3)."""
@@ -200,7 +239,7 @@ def random_coefficient_cube(N: int, seed: int, decades: float = 3.0) -> CSR:
     u = uniform01(seed, ne ** 3).reshape(ne, ne, ne)
     coef = 10.0 ** (2.0 * decades * u - decades)
     h = np.full(ne, 1.0 / ne)
-    A = q1_matrix(h, h, h, coef)
+    A = q1_matrix(h, h, h, coef, engine=engine)
     A.meta.update(family="random_coefficient_cube", N=N, seed=seed, decades=decades)
     return A
 
@@ -245,7 +284,7 @@ def workload_randcoef128(N: int = 128):
     return A, rhs_uniform(A.n, 2), dict(theta=0.02, variants=VARIANT_BITS["1norm"] | VARIANT_BITS["offlmp"])
 
 
-def batched_systems(count: int = 512, seed: int = 3, nmin: int = 8, nmax: int = 40):
+def batched_systems(count: int = 512, seed: int = 3, nmin: int = 8, nmax: int = 40, engine: str = "numpy"):
     """`count` independent systems with edge N ~ U{nmin..nmax}; the first half stretched
     (z ratio ~ U[1.05, 1.2]), the second half coefficient 10^U(-2,2).  System s draws from
     the SplitMix64 stream seed ^ (s+1) << 32."""
@@ -256,11 +295,54 @@ def batched_systems(count: int = 512, seed: int = 3, nmin: int = 8, nmax: int = 
         N = nmin + int(u[0] * (nmax - nmin + 1))
         if s < count // 2:
             ratio = 1.05 + 0.15 * float(u[1])
-            A = stretched_box(N, ratio)
+            A = stretched_box(N, ratio, engine=engine)
         else:
-            A = random_coefficient_cube(N, sub ^ 0xC0EF, 2.0)
+            A = random_coefficient_cube(N, sub ^ 0xC0EF, 2.0, engine=engine)
         out.append((A, rhs_uniform(A.n, sub ^ 0xB)))
     return out
+
+
+def serving_stream(duration_s: float = 60.0, rate: float = 200.0, seed: int = 4, nmin: int = 16, nmax: int = 96,
+                   repeat: float = 0.3, rhs_max: int = 8):
+    """A request stream for the server: Poisson arrivals at `rate` per second over
+    `duration_s`; each request after the first repeats an earlier operator (uniformly among
+    those seen) with probability `repeat`, otherwise it brings a new one: edge N log-uniform
+    in [nmin, nmax] nodes, half stretched boxes (z ratio U[1.05, 1.2]), half
+    random-coefficient cubes (10^U(-2, 2)); 1..rhs_max right-hand sides.  Request r draws
+    six uniforms from SplitMix64(seed) at offset 6 r.
+
+    Returns (requests, operators): requests are tuples (arrival_s, operator index, nrhs,
+    rhs seed); operators are tuples (family, N, parameter) for make_operator."""
+    reqs, ops = [], []
+    t = 0.0
+    r = 0
+    while True:
+        u = uniform01(seed, 6, start=6 * r)
+        t += -np.log1p(-float(u[0])) / rate
+        if t >= duration_s:
+            break
+        if ops and float(u[1]) < repeat:
+            k = min(int(float(u[2]) * len(ops)), len(ops) - 1)
+        else:
+            N = int(np.floor(nmin * (nmax / nmin) ** float(u[3])))
+            N = min(max(N, nmin), nmax)
+            if float(u[4]) < 0.5:
+                ops.append(("stretched", N, 1.05 + 0.15 * float(u[2])))
+            else:
+                ops.append(("randcoef", N, (seed << 40) ^ (len(ops) + 1)))
+            k = len(ops) - 1
+        nrhs = 1 + min(int(float(u[5]) * rhs_max), rhs_max - 1)
+        reqs.append((t, k, nrhs, (seed << 48) ^ (r + 1)))
+        r += 1
+    return reqs, ops
+
+
+def make_operator(op, engine: str = "c") -> CSR:
+    """The matrix of one serving_stream operator."""
+    family, N, param = op
+    if family == "stretched":
+        return stretched_box(N, param, engine=engine)
+    return random_coefficient_cube(N, param, 2.0, engine=engine)
 
 
 def dirichlet_stencil_row(A: CSR, i: int, j: int, k: int) -> dict:
@@ -279,6 +361,7 @@ def dirichlet_stencil_row(A: CSR, i: int, j: int, k: int) -> dict:
 __all__ = [
     "CSR", "splitmix64_stream", "uniform01", "rhs_uniform", "q1_matrix", "laplace_cube",
     "stretched_box", "random_coefficient_cube", "neumann_box", "workload_laplace20",
-    "workload_stretched64", "workload_randcoef128", "batched_systems", "VARIANT_BITS",
+    "workload_stretched64", "workload_randcoef128", "batched_systems", "serving_stream", "make_operator",
+    "VARIANT_BITS",
     "variants_mask", "dirichlet_stencil_row",
 ]
