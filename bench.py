@@ -154,12 +154,19 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash() -> str:
+# the sources each timed kernel class is compiled from (its kernels, launch code and headers)
+KERNEL_SOURCES = {
+    "vcycle_fine_spmv": ("solve.cu", "tma.cuh", "amg_internal.cuh"),
+    "pcg_spmv_fp64": ("solve.cu", "tma.cuh", "amg_internal.cuh"),
+    "galerkin_spgemm": ("spgemm.cu", "amg_internal.cuh"),
+}
+
+
+def kernel_source_hash(kclass_name: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_10476_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kclass_name]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -172,7 +179,7 @@ def ncu_traffic(kclass_name: str, workload: str):
     try:
         d = json.load(open(p))
         e = d.get(workload, {}).get(kclass_name)
-        if e and e.get("source_hash") == kernel_source_hash():
+        if e and e.get("source_hash") == kernel_source_hash(kclass_name):
             return float(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -301,7 +308,8 @@ def run_batched(args, amg, torch):
     thread).  Mixed precision (FP32 levels, FP64 PCG) and FP64."""
     from paper_2103_10476_gb300 import problems as P
     t0 = time.perf_counter()
-    systems = P.batched_systems(512, engine="c")
+    count = args.batch_count
+    systems = P.batched_systems(count, engine="c")
     gen_s = time.perf_counter() - t0
     dev = []
     for A, b in systems:
@@ -311,10 +319,13 @@ def run_batched(args, amg, torch):
     args_d = [amg.csr_arg(A.n, rp, ci, v) for (A, _), (rp, ci, v, _, _) in zip(systems, dev)]
     bs = [d[3] for d in dev]
     xs = [d[4] for d in dev]
-    out = {"workload": "512 Q1 systems, edge U{8..40} nodes, half stretched z ratio U[1.05,1.2], half "
+    out = {"workload": f"{count} Q1 systems, edge U{{8..40}} nodes, half stretched z ratio U[1.05,1.2], half "
                        "10^U(-2,2) coefficients, seed 3; theta 0.02, 1Norm+OffLmp",
            "rows": sum(A.n for A, _ in systems), "nnz": sum(A.nnz for A, _ in systems), "generate_s": gen_s}
-    for prec_name, prec in (("mixed", amg.AMG_MIXED), ("fp64", amg.AMG_FP64)):
+    precs = (("mixed", amg.AMG_MIXED), ("fp64", amg.AMG_FP64))
+    if args.batch_precision != "both":
+        precs = tuple(q for q in precs if q[0] == args.batch_precision)
+    for prec_name, prec in precs:
         p = amg.amg_params_default(theta=0.02, variants=3, precision=prec)
         steps = []
         for k in range(1 + args.batch_steps):
@@ -336,7 +347,7 @@ def run_batched(args, amg, torch):
                               "iters_mean": sum(its) / len(its), "iters_max": max(its),
                               "relres_max": max(i.relres_true for i in infos), "kernels_per_iteration": gk})
         tot = sum(s_["setup_ms"] + s_["solve_ms"] for s_ in steps)
-        out[prec_name] = {"value": 512 * len(steps) / (tot / 1000.0), "unit": "solves/s",
+        out[prec_name] = {"value": count * len(steps) / (tot / 1000.0), "unit": "solves/s",
                           "ms_per_step": tot / len(steps), "steps": len(steps), "per_step": steps}
     return out
 
@@ -434,6 +445,10 @@ def main():
     ap.add_argument("--vcycles", type=int, default=0)
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched line")
     ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--batch-count", type=int, default=512, help="systems of the batched line")
+    ap.add_argument("--batch-precision", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched line, printed alone (for profiler captures)")
     ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -445,6 +460,12 @@ def main():
         return run_reference(args, world, rank)
     if args.once:
         return run_once(args)
+    if args.batched_only:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2103_10476_gb300 import amg
+        print(json.dumps(run_batched(args, amg, torch)), flush=True)
+        return 0
 
     import numpy as np
     import torch

@@ -452,7 +452,7 @@ cudaError_t seg_launch_lpr(const SegTile *tiles, const int *count, const SegOp *
     AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, segtile_kernel<T, LPR, MODE>, kET, smem));
     const int g = std::max(1, std::min(grid, std::max(1, per_sm) * sms));
     segtile_kernel<T, LPR, MODE><<<g, kET, smem, s>>>(tiles, count, ops, x, y, f, d, coef_idx, cap,
-                                                      spmv_error_flag(), cx.nslots, cx.xcap, cx.ycap, cx.guard); note_launch();
+                                                      &cx.guard->waits, cx.nslots, cx.xcap, cx.ycap, cx.guard); note_launch();
     return cudaGetLastError();
 }
 
@@ -584,7 +584,6 @@ amg_status_t Engine::init(const Config &c, cudaStream_t s)
     hcoef_.assign((size_t)S * kEngLevels * cstride_, 0.0);
     free0_.assign(1, {0, c.cap0});
     freec_.assign(1, {0, c.capc});
-    if (spmv_error_flag() == nullptr) return fail_cuda(cudaErrorMemoryAllocation, "engine init");
     EK(alloc(&opA_, hA_.size()));
     EK(alloc(&opP_, hA_.size()));
     EK(alloc(&opR_, hA_.size()));
@@ -951,8 +950,10 @@ std::string Engine::take_guard(int *slot)
     if (cudaMemcpyAsync(&g, guard_, sizeof g, cudaMemcpyDeviceToHost, s_) != cudaSuccess ||
         cudaStreamSynchronize(s_) != cudaSuccess)
         return "guard unreadable";
-    if (g.count == 0) return std::string();
+    if (g.count == 0 && g.waits == 0) return std::string();
     cudaMemsetAsync(guard_, 0, sizeof(EngGuard), s_);
+    if (g.count == 0)
+        return std::to_string(g.waits) + " blocks gave up waiting for a bulk copy into shared memory";
     static const char *kinds[] = {"?", "spmv tile", "chebyshev start", "coarse solve", "pcg chunk"};
     if (slot) *slot = g.slot;
     std::string info;
@@ -997,6 +998,15 @@ amg_status_t Engine::commit()
         EK(upload_lists());
         EK(compute_caps());
         if (old_nlev != nlev_) drop_graphs();
+        // a graph launches the dense solves only of the levels that held coarsest levels when
+        // it was captured
+        unsigned cm = 0;
+        for (int L = 0; L < kEngLevels; ++L)
+            if (lC_[L].nfull > 0) cm |= 1u << L;
+        if (cm != coarse_mask_) {
+            drop_graphs();
+            coarse_mask_ = cm;
+        }
         members_changed_ = false;
     }
     // solves to start

@@ -39,6 +39,7 @@ struct SegOp {          // one slot's matrix on one level, with where its vector
 struct EngGuard {
     int count, kind, slot, where;
     int info[12];       // the first item's tile, matrix and vector figures
+    int waits;          // blocks whose bounded wait for a bulk copy ran out
 };
 struct SegCoarse {      // dense solve of a slot whose coarsest level this is
     const double *inv;
@@ -177,6 +178,7 @@ private:
     cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
     long long gkernels_[2] = {0, 0};
     bool graph_failed_ = false;
+    unsigned coarse_mask_ = 0;      // levels with coarsest-level solves in the captured graphs
     int grid_tiles_ = 0, grid_chunks_ = 0;
 };
 
