@@ -352,6 +352,65 @@ def run_batched(args, amg, torch):
     return out
 
 
+COMBOS = [(m, "+".join(n for b, n in ((1, "1Norm"), (2, "OffLmp"), (8, "Cnstrnt"), (4, "Sprsfy")) if m & b)
+           or "traditional") for m in range(16)]
+
+
+def run_study(args, amg, torch):
+    """§3.1's study on its stand-in: the randomly perturbed cube (ne^3 elements, z spacing 100x,
+    nodes moved by up to 20% of the spacing, seeds 5, 6, ...), strength from the distance
+    Laplacian (theta 0.025), coarsest level <= 1000 rows, PCG to 1e-10, all 16 combinations of
+    1Norm, OffLmp, Cnstrnt and Sprsfy.  Matrix, coordinates and right-hand side resident on
+    the device; each run is amg_setup_coords + amg_solve + amg_free, timed on the host
+    between device synchronisations."""
+    import numpy as np
+    from paper_2103_10476_gb300 import problems as P
+    seeds = list(range(5, 5 + args.study_seeds))
+    t0 = time.perf_counter()
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=len(seeds)) as ex:
+        meshes = list(ex.map(lambda s: P.perturbed_cube(args.study_ne, seed=s), seeds))
+    gen_s = time.perf_counter() - t0
+    rows = {name: {"iters": [], "fail": 0, "opc": []} for _, name in COMBOS}
+    ms = []
+    for A in meshes:
+        rp, ci, v = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A.row_ptr, A.col, A.val))
+        X = torch.from_numpy(np.ascontiguousarray(A.meta["coords"])).cuda()
+        b = torch.from_numpy(P.rhs_uniform(A.n, 1)).cuda()
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        arg = amg.csr_arg(A.n, rp, ci, v)
+        for k, (mask, name) in enumerate([(0, "warm-up")] + COMBOS):
+            p = amg.amg_params_default(theta=0.025, variants=mask, max_coarse=1000,
+                                       strength=amg.AMG_STRENGTH_DISTANCE)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            h = amg.C.c_void_p()
+            st = amg.lib.amg_setup_coords(amg.C.byref(arg), None, X.data_ptr(), 3, amg.C.byref(p), amg.C.byref(h))
+            info = None
+            if st == amg.AMG_OK:
+                info = amg.amg_solve(h, b, x, 1e-10)
+                amg.amg_free(h)
+            torch.cuda.synchronize()
+            if k == 0:
+                continue
+            ms.append(1e3 * (time.perf_counter() - t1))
+            r = rows[name]
+            if st != amg.AMG_OK or info.status != amg.AMG_OK:
+                r["fail"] += 1
+            else:
+                r["iters"].append(info.iters)
+                r["opc"].append(info.op_complexity)
+    table = {name: {"iters_mean": (sum(r["iters"]) / len(r["iters"])) if r["iters"] else None,
+                    "failures": r["fail"], "runs": len(seeds),
+                    "op_complexity": (sum(r["opc"]) / len(r["opc"])) if r["opc"] else None}
+             for name, r in rows.items()}
+    return {"workload": f"perturbed cube {args.study_ne}^3 elements ({meshes[0].n} unknowns), z spacing x100, "
+                        f"nodes moved up to 20% of the spacing, seeds {seeds[0]}..{seeds[-1]}; distance-Laplacian "
+                        "strength theta 0.025, coarsest <= 1000, PCG to 1e-10, 16 combinations",
+            "generate_s": gen_s, "runs": len(ms), "ms_per_run": sum(ms) / len(ms),
+            "solves_per_s": len(ms) / (sum(ms) / 1000.0), "combinations": table}
+
+
 def run_serving(args, amg, seconds: float, precisions):
     """The request stream of problems.serving_stream (Poisson 200 req/s, operators with edge
     log-uniform 16..96 nodes, stretched or 10^U(-2,2) coefficients, 30% repeats, 1..8
@@ -449,6 +508,10 @@ def main():
     ap.add_argument("--batch-precision", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched line, printed alone (for profiler captures)")
+    ap.add_argument("--no-study", action="store_true", help="skip the 16-combination perturbed-cube study line")
+    ap.add_argument("--study-ne", type=int, default=60, help="elements per direction of the study's cube")
+    ap.add_argument("--study-seeds", type=int, default=3, help="meshes (seeds) of the study")
+    ap.add_argument("--study-only", action="store_true", help="only the study line, printed alone")
     ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -460,6 +523,12 @@ def main():
         return run_reference(args, world, rank)
     if args.once:
         return run_once(args)
+    if args.study_only:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2103_10476_gb300 import amg
+        print(json.dumps(run_study(args, amg, torch)), flush=True)
+        return 0
     if args.batched_only:
         import torch
         torch.cuda.set_device(local)
@@ -579,6 +648,7 @@ def main():
     d2h = solves_per_step * 8 * A.n
 
     batched = None if args.no_batched else run_batched(args, amg, torch)
+    study = None if args.no_study else run_study(args, amg, torch)
     serving = None if not args.serving else run_serving(args, amg, args.serve_seconds,
                                                         ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
 
@@ -622,6 +692,7 @@ def main():
         "iters": iters, "status": statuses, "wall_s": t_wall,
         "mixed": other,
         "batched": batched,
+        "study": study,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

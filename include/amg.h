@@ -56,6 +56,11 @@ enum { AMG_FP64 = 0, AMG_MIXED = 1 };
 enum { AMG_PT_ORTHONORMAL = 0, AMG_PT_UNIT = 1 };
 /* eigenvalue used with the 1-norm diagonal: the bound 1 (§2.1) or the power method */
 enum { AMG_LAMBDA_ONE = 0, AMG_LAMBDA_POWER = 1 };
+/* Strength of connection (Eq. 7) evaluated on A_l itself, or on the distance Laplacian of
+ * §3.1: the pattern of A_l with off-diagonal -1 / |x_i - x_j| and a diagonal that makes each
+ * row sum to zero, from coordinates given to amg_setup_coords (level 0) and, on coarser
+ * levels, the mean coordinates of each aggregate's members. */
+enum { AMG_STRENGTH_MATRIX = 0, AMG_STRENGTH_DISTANCE = 1 };
 
 /* Square CSR matrix.  row_ptr has n+1 entries (row_ptr[0] = 0), columns are sorted
  * ascending within each row with no duplicates, and every row stores its diagonal.
@@ -87,6 +92,7 @@ typedef struct {
     uint64_t seed;       /* aggregation priorities and power-method start vectors (0)        */
     double lambda_override; /* > 0: prolongator-smoothing eigenvalue on every level (tests)  */
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream         */
+    int strength;        /* AMG_STRENGTH_MATRIX (Eq. 7 on A_l) or AMG_STRENGTH_DISTANCE       */
 } amg_params_t;
 
 typedef struct {
@@ -110,6 +116,15 @@ void amg_params_default(amg_params_t *p);
  * is NULL and nothing is leaked.  Synchronises the stream before returning. */
 amg_status_t amg_setup(const amg_csr_t *A, const double *nullspace, const amg_params_t *p,
                        amg_handle_t *out);
+
+/* amg_setup with coordinates of the rows (for AMG_STRENGTH_DISTANCE, §3.1): coords holds
+ * dim (1..3) doubles per row, row-major (x_0, y_0, z_0, x_1, ...), on the same side as A's
+ * arrays (host, or device when A->on_device).  The hierarchy keeps a copy of each level's
+ * coordinates.  With params->strength = AMG_STRENGTH_DISTANCE, coords NULL or dim outside
+ * 1..3 is AMG_ERR_INVALID_ARG, and so are two coupled rows at the same coordinates.
+ * amg_setup is this call with coords = NULL. */
+amg_status_t amg_setup_coords(const amg_csr_t *A, const double *nullspace, const double *coords, int dim,
+                              const amg_params_t *p, amg_handle_t *out);
 
 /* Solves A x = b from x = 0 by PCG with one V-cycle (Algorithm 1) per iteration, until
  * ||r|| / ||b|| <= tol on the recurrence residual and on the recomputed true residual.
@@ -137,7 +152,7 @@ enum {
     AMG_EX_LUMPFLAG = 5, AMG_EX_ABAR_ROWPTR = 6, AMG_EX_ABAR_COL = 7, AMG_EX_ABAR_VAL = 8,
     AMG_EX_AGG = 9, AMG_EX_ROOT = 10, AMG_EX_P_ROWPTR = 11, AMG_EX_P_COL = 12, AMG_EX_P_VAL = 13,
     AMG_EX_R_ROWPTR = 14, AMG_EX_R_COL = 15, AMG_EX_R_VAL = 16, AMG_EX_DSMOOTH = 17,
-    AMG_EX_SCALARS = 18, AMG_EX_NULLSPACE = 19, AMG_EX_CFLAG = 20
+    AMG_EX_SCALARS = 18, AMG_EX_NULLSPACE = 19, AMG_EX_CFLAG = 20, AMG_EX_COORDS = 21
 };
 amg_status_t amg_export_count(amg_handle_t h, int level, int what, int64_t *count);
 amg_status_t amg_export(amg_handle_t h, int level, int what, void *dst_host);

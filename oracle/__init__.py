@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("pt_unit", C.c_int),
                 ("onenorm_power", C.c_int), ("seed", C.c_uint64), ("lambda_override", C.c_double),
-                ("max_iter", C.c_int)]
+                ("max_iter", C.c_int), ("strength", C.c_int)]
 
 
 class Info(C.Structure):
@@ -80,6 +80,9 @@ def lib():
         L.oc_cholesky.argtypes = [C.c_int64, vp, vp]
         L.oc_csr_free.argtypes = [C.POINTER(_CSR)]
         L.oc_setup.argtypes = [C.c_int64, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
+        L.oc_setup_coords.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_int, C.POINTER(Params), C.POINTER(vp)]
+        L.oc_distance_laplacian.argtypes = [C.c_int64, vp, vp, vp, C.c_int, vp]
+        L.oc_coarse_coords.argtypes = [C.c_int64, vp, C.c_int64, vp, C.c_int, vp]
         L.oc_prolongator_only.argtypes = [C.c_int64, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
         L.oc_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Info)]
         L.oc_pcg_plain.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(Info)]
@@ -155,6 +158,26 @@ def strength(A, theta: float) -> np.ndarray:
     out = np.zeros(len(ci), dtype=np.uint8)
     lib().oc_strength(A.n, _p(rp), _p(ci), _p(v), theta, _p(out))
     return out
+
+
+def distance_laplacian(A, coords):
+    """Values of the distance Laplacian on A's pattern (§3.1); (values, status)."""
+    rp, ci, _ = _arrs(A)
+    X = np.ascontiguousarray(coords, dtype=np.float64)
+    dim = 1 if X.ndim == 1 else X.shape[1]
+    out = np.zeros(max(len(ci), 1))
+    st = lib().oc_distance_laplacian(A.n, _p(rp), _p(ci), _p(X), dim, _p(out))
+    return out[:len(ci)], int(st)
+
+
+def coarse_coords(agg, nagg: int, coords):
+    a = np.ascontiguousarray(agg, dtype=np.int32)
+    X = np.ascontiguousarray(coords, dtype=np.float64)
+    dim = 1 if X.ndim == 1 else X.shape[1]
+    out = np.zeros((max(nagg, 1), dim))
+    st = lib().oc_coarse_coords(len(a), _p(a), nagg, _p(X), dim, _p(out))
+    assert st == 0
+    return out[:nagg]
 
 
 def filtered(A, removed: np.ndarray, offlmp: bool = False, tau: float = 1.1):
@@ -249,7 +272,7 @@ _WHAT = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "
          "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
          "P.ci": (12, np.int32), "P.v": (13, np.float64), "R.rp": (14, np.int64), "R.ci": (15, np.int32),
          "R.v": (16, np.float64), "Dsm": (17, np.float64), "scalars": (18, np.float64), "B": (19, np.float64),
-         "cflag": (20, np.uint8), "chol": (21, np.float64)}
+         "cflag": (20, np.uint8), "chol": (21, np.float64), "coords": (22, np.float64)}
 
 
 class Hierarchy:
@@ -304,13 +327,19 @@ class Hierarchy:
         return u[:self.n]
 
 
-def setup(A, nullspace=None, **kw):
-    """Returns (Hierarchy or None, status)."""
+def setup(A, nullspace=None, coords=None, **kw):
+    """Returns (Hierarchy or None, status).  coords: (n, dim) coordinates of the rows, needed
+    with strength=1 (distance-Laplacian strength, §3.1)."""
     rp, ci, v = _arrs(A)
     ns = None if nullspace is None else np.ascontiguousarray(nullspace, dtype=np.float64)
     p = params(**kw)
     h = C.c_void_p()
-    st = lib().oc_setup(A.n, _p(rp), _p(ci), _p(v), _p(ns), C.byref(p), C.byref(h))
+    if coords is not None:
+        X = np.ascontiguousarray(coords, dtype=np.float64)
+        dim = 1 if X.ndim == 1 else X.shape[1]
+        st = lib().oc_setup_coords(A.n, _p(rp), _p(ci), _p(v), _p(ns), _p(X), dim, C.byref(p), C.byref(h))
+    else:
+        st = lib().oc_setup(A.n, _p(rp), _p(ci), _p(v), _p(ns), C.byref(p), C.byref(h))
     if st != 0:
         return None, int(st)
     return Hierarchy(h, A.n), 0

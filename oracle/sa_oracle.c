@@ -38,10 +38,12 @@ struct oc_level {
     oc_csr P, R;
     double lambda_cheb;   /* lambda_max(D^-1 A_l) for the Chebyshev smoother       */
     double *invdiag;      /* 1 / diag(A_l)                                         */
+    double *coords;       /* dim coordinates per row (distance-Laplacian strength)  */
 };
 
 struct oc_hier {
     int nlev;
+    int dim;              /* coordinates per row, 0 without coordinates */
     int prolongator_only; /* level 0 holds P but no coarser level was formed */
     struct oc_level lev[OC_MAX_LEVELS];
     double *chol;         /* dense lower Cholesky factor of the coarsest operator */
@@ -69,6 +71,7 @@ void oc_params_default(oc_params *p)
     p->seed = 0;
     p->lambda_override = 0.0;
     p->max_iter = 1000;
+    p->strength = 0;
 }
 
 static void csr_release(oc_csr *c)
@@ -153,6 +156,56 @@ void oc_strength(int64_t n, const int64_t *rp, const int32_t *ci, const double *
         }
     }
     free(d);
+}
+
+/* Distance Laplacian of §3.1: the pattern of A; off-diagonal L_ij = -1 / |x_i - x_j| (the
+ * reciprocal of the negative distance between the coordinates of rows i and j) and L_ii
+ * chosen so that the row sums to zero, L_ii = sum over j != i of 1 / |x_i - x_j| in ascending
+ * column order.  The distance is sqrt of the squared differences summed in coordinate order.
+ * Reading: stored zeros of A are part of the pattern and get a value too.  Returns
+ * OC_ERR_INVALID_ARG if two coupled rows have the same coordinates. */
+int oc_distance_laplacian(int64_t n, const int64_t *rp, const int32_t *ci, const double *coords, int dim,
+                          double *L)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double diag = 0.0;
+        int64_t dpos = -1;
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int32_t j = ci[e];
+            if (j == i) { dpos = e; continue; }
+            double d2 = 0.0;
+            for (int c = 0; c < dim; ++c) {
+                double dx = coords[i * dim + c] - coords[(int64_t)j * dim + c];
+                d2 = d2 + dx * dx;
+            }
+            double dist = sqrt(d2);
+            if (!(dist > 0.0)) return OC_ERR_INVALID_ARG;
+            double w = 1.0 / dist;
+            L[e] = -w;
+            diag = diag + w;
+        }
+        if (dpos >= 0) L[dpos] = diag;
+    }
+    return OC_OK;
+}
+
+/* Coordinates of the next level (Reading: the paper supplies coordinates for the finest
+ * level only; an aggregate's coordinates are the mean of its members', summed in ascending
+ * member index and divided by the member count). */
+int oc_coarse_coords(int64_t n, const int32_t *agg, int64_t nagg, const double *coords, int dim, double *out)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)(nagg > 0 ? nagg : 1), sizeof(int64_t));
+    if (!cnt) return OC_ERR_OOM;
+    for (int64_t k = 0; k < nagg * dim; ++k) out[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t a = agg[i];
+        for (int c = 0; c < dim; ++c) out[(int64_t)a * dim + c] = out[(int64_t)a * dim + c] + coords[i * dim + c];
+        cnt[a] += 1;
+    }
+    for (int64_t a = 0; a < nagg; ++a)
+        for (int c = 0; c < dim; ++c) out[a * dim + c] = out[a * dim + c] / (double)cnt[a];
+    free(cnt);
+    return OC_OK;
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -736,7 +789,18 @@ static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
     lv->root = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     if (!lv->strong || !lv->removed || !lv->lumpflag || !lv->agg || !lv->root) return OC_ERR_OOM;
 
-    oc_strength(n, A->rp, A->ci, A->v, p->theta, lv->strong);
+    if (p->strength == 1) {
+        /* §3.1: Eq. (7) evaluated on the distance Laplacian instead of A */
+        if (!lv->coords || h->dim < 1) return OC_ERR_INVALID_ARG;
+        double *Ld = (double *)malloc((size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+        if (!Ld) return OC_ERR_OOM;
+        st = oc_distance_laplacian(n, A->rp, A->ci, lv->coords, h->dim, Ld);
+        if (!st) oc_strength(n, A->rp, A->ci, Ld, p->theta, lv->strong);
+        free(Ld);
+        if (st) return st;
+    } else {
+        oc_strength(n, A->rp, A->ci, A->v, p->theta, lv->strong);
+    }
     for (int64_t i = 0; i < n; ++i)
         for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
             lv->removed[e] = (A->ci[e] != i && !lv->strong[e]) ? 1 : 0;
@@ -869,13 +933,26 @@ static int smoother_setup(oc_hier *h, int L)
 int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *nullspace,
              const oc_params *p, oc_hier **out)
 {
+    return oc_setup_coords(n, rp, ci, v, nullspace, NULL, 0, p, out);
+}
+
+int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *nullspace,
+                    const double *coords, int dim, const oc_params *p, oc_hier **out)
+{
     *out = NULL;
     if (n < 0 || !rp) return OC_ERR_INVALID_ARG;
+    if (p->strength == 1 && (!coords || dim < 1 || dim > 3)) return OC_ERR_INVALID_ARG;
     oc_hier *h = (oc_hier *)calloc(1, sizeof(oc_hier));
     if (!h) return OC_ERR_OOM;
     h->p = *p;
     int st = csr_copy(&h->lev[0].A, n, rp, ci, v);
     if (st) { oc_free(h); return st; }
+    if (coords && dim >= 1) {
+        h->dim = dim;
+        h->lev[0].coords = (double *)malloc((size_t)(n > 0 ? n * dim : 1) * sizeof(double));
+        if (!h->lev[0].coords) { oc_free(h); return OC_ERR_OOM; }
+        memcpy(h->lev[0].coords, coords, (size_t)(n * dim) * sizeof(double));
+    }
     h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     for (int64_t i = 0; i < n; ++i) h->lev[0].B[i] = nullspace ? nullspace[i] : 1.0;
     int L = 0;
@@ -898,6 +975,12 @@ int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, c
         free(Ac);
         nx->B = (double *)malloc((size_t)(lv->nagg > 0 ? lv->nagg : 1) * sizeof(double));
         for (int64_t a = 0; a < lv->nagg; ++a) nx->B[a] = p->pt_unit ? 1.0 : lv->nrm[a];
+        if (h->dim > 0) {
+            nx->coords = (double *)malloc((size_t)(lv->nagg > 0 ? lv->nagg * h->dim : 1) * sizeof(double));
+            if (!nx->coords) { oc_free(h); return OC_ERR_OOM; }
+            st = oc_coarse_coords(lv->A.n, lv->agg, lv->nagg, lv->coords, h->dim, nx->coords);
+            if (st) { oc_free(h); return st; }
+        }
         ++L;
     }
     h->nlev = L + 1;
@@ -1083,7 +1166,7 @@ void oc_free(oc_hier *h)
         struct oc_level *lv = &h->lev[L];
         csr_release(&lv->A); csr_release(&lv->Abar); csr_release(&lv->P); csr_release(&lv->R);
         free(lv->strong); free(lv->removed); free(lv->lumpflag); free(lv->agg); free(lv->root);
-        free(lv->B); free(lv->nrm); free(lv->Dsm); free(lv->cflag); free(lv->invdiag);
+        free(lv->B); free(lv->nrm); free(lv->Dsm); free(lv->cflag); free(lv->invdiag); free(lv->coords);
     }
     free(h->chol);
     free(h);
@@ -1097,7 +1180,8 @@ int oc_nlevels(const oc_hier *h) { return h ? h->nlev : 0; }
 
 /* what: 0 A.rp, 1 A.ci, 2 A.v, 3 strong, 4 removed, 5 lumpflag, 6 Abar.rp, 7 Abar.ci,
  * 8 Abar.v, 9 agg, 10 root, 11 P.rp, 12 P.ci, 13 P.v, 14 R.rp, 15 R.ci, 16 R.v, 17 Dsm,
- * 18 scalars [lambda_bar, omega, lambda_cheb, nagg], 19 B, 20 cflag, 21 Cholesky factor.
+ * 18 scalars [lambda_bar, omega, lambda_cheb, nagg], 19 B, 20 cflag, 21 Cholesky factor,
+ * 22 coordinates (n * dim).
  * Copies into dst when it is not NULL; *len receives the element count. */
 int oc_level_get(const oc_hier *h, int L, int what, void *dst, int64_t *len)
 {
@@ -1133,6 +1217,7 @@ int oc_level_get(const oc_hier *h, int L, int what, void *dst, int64_t *len)
     case 19: src = lv->B; es = 8; cnt = lv->A.n; break;
     case 20: src = lv->cflag; es = 1; cnt = last ? 0 : lv->A.n; break;
     case 21: src = h->chol; es = 8; cnt = last ? lv->A.n * lv->A.n : 0; break;
+    case 22: src = lv->coords; es = 8; cnt = lv->coords ? lv->A.n * h->dim : 0; break;
     default: return OC_ERR_INVALID_ARG;
     }
     if (len) *len = cnt;

@@ -54,6 +54,7 @@ typedef struct {
     uint64_t seed;         /* aggregation priorities and power-method start vectors */
     double lambda_override;/* > 0: use as the prolongator-smoothing eigenvalue on every level */
     int max_iter;          /* PCG iteration limit */
+    int strength;          /* 0: Eq. (7) on the matrix; 1: Eq. (7) on the distance Laplacian (§3.1) */
 } oc_params;
 
 typedef struct {
@@ -71,6 +72,9 @@ void oc_params_default(oc_params *p);
 /* single steps (used by the tests to pin each one) */
 void oc_strength(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, double theta,
                  uint8_t *strong);
+int oc_distance_laplacian(int64_t n, const int64_t *rp, const int32_t *ci, const double *coords, int dim,
+                          double *L);
+int oc_coarse_coords(int64_t n, const int32_t *agg, int64_t nagg, const double *coords, int dim, double *out);
 int oc_filter(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const uint8_t *removed,
               int offlmp, double tau, oc_csr **out, uint8_t *rowflag);
 int64_t oc_mis2_aggregate(int64_t n, const int64_t *rp, const int32_t *ci, const uint8_t *strong,
@@ -90,6 +94,8 @@ void oc_csr_free(oc_csr *c);
 /* the whole method */
 int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *nullspace,
              const oc_params *p, oc_hier **out);
+int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *nullspace,
+                    const double *coords, int dim, const oc_params *p, oc_hier **out);
 int oc_prolongator_only(int64_t n, const int64_t *rp, const int32_t *ci, const double *v,
                         const double *nullspace, const oc_params *p, oc_hier **out);
 int oc_solve(oc_hier *h, const double *b, double *x, double tol, oc_info *info);

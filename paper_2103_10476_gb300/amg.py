@@ -23,12 +23,13 @@ AMG_VAR_1NORM, AMG_VAR_OFFLMP, AMG_VAR_SPRSFY, AMG_VAR_CNSTRNT = 1, 2, 4, 8
 AMG_FP64, AMG_MIXED = 0, 1
 AMG_PT_ORTHONORMAL, AMG_PT_UNIT = 0, 1
 AMG_LAMBDA_ONE, AMG_LAMBDA_POWER = 0, 1
+AMG_STRENGTH_MATRIX, AMG_STRENGTH_DISTANCE = 0, 1
 EXPORTS = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
            "removed": (4, np.uint8), "lumpflag": (5, np.uint8), "Abar.rp": (6, np.int64), "Abar.ci": (7, np.int32),
            "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
            "P.ci": (12, np.int32), "P.v": (13, np.float64), "R.rp": (14, np.int64), "R.ci": (15, np.int32),
            "R.v": (16, np.float64), "Dsm": (17, np.float64), "scalars": (18, np.float64), "B": (19, np.float64),
-           "cflag": (20, np.uint8)}
+           "cflag": (20, np.uint8), "coords": (21, np.float64)}
 
 
 class AmgError(RuntimeError):
@@ -48,7 +49,7 @@ class amg_params_t(C.Structure):
                 ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
-                ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p)]
+                ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int)]
 
 
 class amg_info_t(C.Structure):
@@ -88,6 +89,7 @@ def _load():
     sig = {
         "amg_params_default": (None, [C.POINTER(amg_params_t)]),
         "amg_setup": (st, [C.POINTER(amg_csr_t), vp, C.POINTER(amg_params_t), C.POINTER(vp)]),
+        "amg_setup_coords": (st, [C.POINTER(amg_csr_t), vp, vp, C.c_int, C.POINTER(amg_params_t), C.POINTER(vp)]),
         "amg_solve": (st, [vp, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
         "amg_free": (st, [vp]),
         "amg_num_levels": (st, [vp, C.POINTER(C.c_int)]),
@@ -177,6 +179,18 @@ def amg_setup(A: amg_csr_t, nullspace=None, params: amg_params_t | None = None):
     h = C.c_void_p()
     ns, _ = _ptr(nullspace)
     _check(lib.amg_setup(C.byref(A), ns, C.byref(p), C.byref(h)), "amg_setup")
+    return h
+
+
+def amg_setup_coords(A: amg_csr_t, nullspace=None, coords=None, params: amg_params_t | None = None):
+    """amg_setup with row coordinates (n x dim array, host or device, same side as A), for the
+    distance-Laplacian strength; raises AmgError on failure."""
+    p = params if params is not None else amg_params_default()
+    h = C.c_void_p()
+    ns, _ = _ptr(nullspace)
+    xc, _ = _ptr(coords)
+    dim = 0 if coords is None else (1 if len(coords.shape) == 1 else int(coords.shape[1]))
+    _check(lib.amg_setup_coords(C.byref(A), ns, xc, dim, C.byref(p), C.byref(h)), "amg_setup_coords")
     return h
 
 

@@ -90,6 +90,13 @@ cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t 
 // Eq. (7): strong[e], removed[e] (= weak off-diagonal) and kept-entry counts per row.
 cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
                      int *kept, cudaStream_t s);
+// §3.1's distance Laplacian on A's pattern (L: one value per stored entry, Ld: its diagonal);
+// *bad counts coupled rows at zero distance
+cudaError_t distance_laplacian(const DevCsr &A, const double *X, int dim, double *L, double *Ld, int *bad,
+                               cudaStream_t s);
+// coordinates of the next level: the mean of each aggregate's members (ascending member order)
+cudaError_t coarse_coords(int nagg, const int *mstart, const int *members, const double *X, int dim, double *Xc,
+                          cudaStream_t s);
 // Strong graph (strong off-diagonals only) as CSR: rp from a scan of counts.
 cudaError_t strong_graph_counts(const DevCsr &A, const uint8_t *strong, int *cnt, cudaStream_t s);
 cudaError_t strong_graph_fill(const DevCsr &A, const uint8_t *strong, const int *grp, int *gci, cudaStream_t s);

@@ -141,19 +141,28 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     unsigned long long *t0 = nullptr, *t1 = nullptr;
     int *rootof = nullptr, *join1 = nullptr;
     uint8_t *drop = nullptr;
-    double *px = nullptr, *py = nullptr, *scal = nullptr;
+    double *px = nullptr, *py = nullptr, *scal = nullptr, *lvals = nullptr, *ldiag = nullptr;
     DevCsr AP, Ac;
-    int hflags[4] = {0, 0, 0, 0};
+    int hflags[5] = {0, 0, 0, 0, 0};
     int nagg = 0, rounds = 0, nnz_g = 0, nnz_bar = 0, nnz_p = 0, ovf = 0;
     *coarsest = 0;
 
     CK(dalloc(h, &lv.strong, (size_t)A.nnz));
     CK(dalloc(h, &lv.removed, (size_t)A.nnz));
     CK(cudaMallocAsync(&kept, sizeof(int) * (size_t)(n + 1), s));
-    CK(cudaMallocAsync(&flags, sizeof(int) * 4, s));
-    CK(cudaMemsetAsync(flags, 0, sizeof(int) * 4, s));
-    // Eq. (7)
-    CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
+    CK(cudaMallocAsync(&flags, sizeof(int) * 5, s));
+    CK(cudaMemsetAsync(flags, 0, sizeof(int) * 5, s));
+    // Eq. (7), on A or (§3.1) on the distance Laplacian of the level's coordinates
+    if (p.strength == AMG_STRENGTH_DISTANCE) {
+        CK(cudaMallocAsync(&lvals, sizeof(double) * (size_t)(A.nnz > 0 ? A.nnz : 1), s));
+        CK(cudaMallocAsync(&ldiag, sizeof(double) * (size_t)(n > 0 ? n : 1), s));
+        CK(distance_laplacian(A, lv.coords, h->dim, lvals, ldiag, flags + 4, s));
+        DevCsr Ld = A;
+        Ld.v = lvals;
+        CK(strength(Ld, ldiag, p.theta, lv.strong, lv.removed, kept, s));
+    } else {
+        CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
+    }
     // strong graph
     CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(n + 1), s));
     CK(strong_graph_counts(A, lv.strong, grp, s));
@@ -182,6 +191,11 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(cudaMallocAsync(&members, sizeof(int) * (size_t)n, s));
     CK(cudaMallocAsync(&fill, sizeof(int) * (size_t)(nagg + 1), s));
     CK(aggregate_members(n, nagg, lv.agg, mstart, members, fill, s));
+    if (lv.coords) {
+        Level &nx = h->lev[L + 1];
+        CK(dalloc(h, &nx.coords, (size_t)nagg * (size_t)h->dim));
+        CK(coarse_coords(nagg, mstart, members, lv.coords, h->dim, nx.coords, s));
+    }
     CK(dalloc(h, &lv.nrm, (size_t)nagg));
     CK(aggregate_norms(nagg, mstart, members, lv.B, lv.nrm, flags + 0, s));
     // §2.5
@@ -195,8 +209,9 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(dalloc(h, &lv.Abar.rp, (size_t)n + 1));
     CK(scan_exclusive(kept, lv.Abar.rp, n, s));
     CK(cudaMemcpyAsync(&nnz_bar, lv.Abar.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 5, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (hflags[4]) { g_last_error = "two coupled rows at the same coordinates"; st = AMG_ERR_INVALID_ARG; goto done; }
     if (hflags[0]) { g_last_error = "near-null space is zero on an aggregate"; st = AMG_ERR_INVALID_ARG; goto done; }
     lv.Abar.nnz = nnz_bar;
     CK(dalloc(h, &lv.Abar.ci, (size_t)nnz_bar));
@@ -315,7 +330,7 @@ done:
     for (void *p : {(void *)kept, (void *)grp, (void *)gci, (void *)mstart, (void *)members, (void *)fill,
                     (void *)flags, (void *)t0, (void *)t1, (void *)rootof, (void *)join1, (void *)drop, (void *)px,
                     (void *)py, (void *)scal, (void *)AP.rp, (void *)AP.ci, (void *)AP.v, (void *)Ac.rp,
-                    (void *)Ac.ci, (void *)Ac.v})
+                    (void *)Ac.ci, (void *)Ac.v, (void *)lvals, (void *)ldiag})
         free_async(p, s);
     cudaStreamSynchronize(s);
     return st;
@@ -549,6 +564,7 @@ void amg_params_default(amg_params_t *p)
     p->seed = 0;
     p->lambda_override = 0.0;
     p->cuda_stream = nullptr;
+    p->strength = AMG_STRENGTH_MATRIX;
 }
 
 const char *amg_status_string(amg_status_t s)
@@ -605,9 +621,27 @@ amg_status_t amg_free(amg_handle_t h)
 
 amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_params_t *pin, amg_handle_t *out)
 {
+    return amg_setup_coords(Ain, nullspace, nullptr, 0, pin, out);
+}
+
+amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, const double *coords, int dim,
+                              const amg_params_t *pin, amg_handle_t *out)
+{
     if (!out) return AMG_ERR_INVALID_ARG;
     *out = nullptr;
     if (!Ain || !pin) return AMG_ERR_INVALID_ARG;
+    if (pin->strength != AMG_STRENGTH_MATRIX && pin->strength != AMG_STRENGTH_DISTANCE) {
+        g_last_error = "unknown strength criterion";
+        return AMG_ERR_INVALID_ARG;
+    }
+    if (coords && (dim < 1 || dim > 3)) {
+        g_last_error = "coordinates need 1 to 3 values per row";
+        return AMG_ERR_INVALID_ARG;
+    }
+    if (pin->strength == AMG_STRENGTH_DISTANCE && !coords && Ain->n > 0) {
+        g_last_error = "the distance-Laplacian strength needs coordinates";
+        return AMG_ERR_INVALID_ARG;
+    }
     if (Ain->n < 0 || Ain->nnz < 0 || (Ain->n > 0 && (!Ain->row_ptr || !Ain->col || !Ain->val)))
         return AMG_ERR_INVALID_ARG;
     if (Ain->n > 0x7ffffffe || Ain->nnz > 0x7ffffffe) {
@@ -667,6 +701,11 @@ amg_status_t amg_setup(const amg_csr_t *Ain, const double *nullspace, const amg_
             if (hbad) { g_last_error = "columns unsorted, out of range, duplicated, or a missing diagonal"; st = AMG_ERR_INVALID_ARG; goto done; }
         }
         CK(dalloc(h, &l0.B, (size_t)n));
+        if (coords && n > 0) {
+            h->dim = dim;
+            CK(dalloc(h, &l0.coords, (size_t)n * (size_t)dim));
+            CK(copy_to_device(l0.coords, coords, sizeof(double) * (size_t)n * (size_t)dim, s));
+        }
         if (nullspace) CK(copy_to_device(l0.B, nullspace, sizeof(double) * (size_t)n, s));
         else if (n > 0) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
         CK(cudaGetLastError());
@@ -876,6 +915,7 @@ ExportSrc export_src(const amg_hierarchy *h, int level, int what)
     case AMG_EX_A_COL: return arr(lv.A.ci, lv.A.nnz, 4);
     case AMG_EX_A_VAL: return arr(lv.A.v, lv.A.nnz, 8);
     case AMG_EX_NULLSPACE: return arr(lv.B, lv.A.n, 8);
+    case AMG_EX_COORDS: return arr(lv.coords, (int64_t)lv.A.n * h->dim, 8);
     default: break;
     }
     if (last) return e;
@@ -908,7 +948,7 @@ extern "C" {
 amg_status_t amg_export_count(amg_handle_t h, int level, int what, int64_t *count)
 {
     if (!h || !count || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
-    if (what < 0 || what > AMG_EX_CFLAG) return AMG_ERR_INVALID_ARG;
+    if (what < 0 || what > AMG_EX_COORDS) return AMG_ERR_INVALID_ARG;
     *count = export_src(h, level, what).count;
     return AMG_OK;
 }
@@ -916,7 +956,7 @@ amg_status_t amg_export_count(amg_handle_t h, int level, int what, int64_t *coun
 amg_status_t amg_export(amg_handle_t h, int level, int what, void *dst)
 {
     if (!h || !dst || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
-    if (what < 0 || what > AMG_EX_CFLAG) return AMG_ERR_INVALID_ARG;
+    if (what < 0 || what > AMG_EX_COORDS) return AMG_ERR_INVALID_ARG;
     ExportSrc e = export_src(h, level, what);
     if (e.count == 0) return AMG_OK;
     const Level &lv = h->lev[level];

@@ -21,6 +21,7 @@ struct Level {
     double lambda_bar = 0.0, omega = 0.0, lambda_cheb = 0.0;
     DevCsr P, R;
     double *invdiag = nullptr;
+    double *coords = nullptr; // dim coordinates per row (distance-Laplacian strength)
     float *invdiag_f = nullptr, *Af = nullptr, *Pf = nullptr, *Rf = nullptr;
     void *vf = nullptr, *vx = nullptr, *vx2 = nullptr, *vr = nullptr, *vd = nullptr;   // solve vectors
     SpmvPlan plan_a, plan_p, plan_r;
@@ -37,6 +38,7 @@ struct amg_hierarchy {
     amg_params_t p;
     cudaStream_t s = nullptr;
     int nlev = 0;
+    int dim = 0;                // coordinates per row (0: none given)
     Level lev[32];
     std::vector<void *> allocs;
     double *coarse_inv = nullptr;

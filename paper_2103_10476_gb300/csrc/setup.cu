@@ -99,6 +99,68 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------ distance Laplacian, §3.1
+// Thread per row, entries in ascending column order: off the diagonal L_ij = -1 / |x_i - x_j|
+// (the distance from the squared coordinate differences summed in coordinate order), on it
+// the sum of the 1 / |x_i - x_j|, so every row sums to zero.  Each operation is rounded.
+__global__ void dlap_kernel(int n, const int *rp, const int *ci, const double *X, int dim, double *L, double *Ld,
+                            int *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double diag = 0.0;
+    int dpos = -1;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const int j = ci[e];
+        if (j == i) {
+            dpos = e;
+            continue;
+        }
+        double d2 = 0.0;
+        for (int c = 0; c < dim; ++c) {
+            const double dx = __dsub_rn(X[(size_t)i * dim + c], X[(size_t)j * dim + c]);
+            d2 = __dadd_rn(d2, __dmul_rn(dx, dx));
+        }
+        const double dist = __dsqrt_rn(d2);
+        if (!(dist > 0.0)) atomicAdd(bad, 1);
+        const double w = __ddiv_rn(1.0, dist);
+        L[e] = -w;
+        diag = __dadd_rn(diag, w);
+    }
+    if (dpos >= 0) L[dpos] = diag;
+    Ld[i] = diag;
+}
+
+cudaError_t distance_laplacian(const DevCsr &A, const double *X, int dim, double *L, double *Ld, int *bad,
+                               cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    dlap_kernel<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rp, A.ci, X, dim, L, Ld, bad); note_launch();
+    return cudaGetLastError();
+}
+
+// thread per aggregate: members in ascending order, sum then divide by the member count
+__global__ void coarse_coords_kernel(int nagg, const int *mstart, const int *members, const double *X, int dim,
+                                     double *Xc)
+{
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nagg) return;
+    const int b = mstart[a], e = mstart[a + 1];
+    for (int c = 0; c < dim; ++c) {
+        double sum = 0.0;
+        for (int t = b; t < e; ++t) sum = __dadd_rn(sum, X[(size_t)members[t] * dim + c]);
+        Xc[(size_t)a * dim + c] = __ddiv_rn(sum, (double)(e - b));
+    }
+}
+
+cudaError_t coarse_coords(int nagg, const int *mstart, const int *members, const double *X, int dim, double *Xc,
+                          cudaStream_t s)
+{
+    if (nagg == 0) return cudaSuccess;
+    coarse_coords_kernel<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, mstart, members, X, dim, Xc); note_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------ strong graph
 __global__ void sg_count_kernel(int n, const int *rp, const uint8_t *strong, int *cnt)
 {

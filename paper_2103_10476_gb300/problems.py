@@ -258,6 +258,167 @@ def neumann_box(nx: int, ny: int, nz: int, hx=1.0, hy=1.0, hz=1.0, coef=None) ->
 VARIANT_BITS = {"1norm": 1, "offlmp": 2, "sprsfy": 4, "cnstrnt": 8}
 
 
+# ------------------------------------------------------------------------------ general hexahedra
+# Q1 elements on a structured grid of arbitrary (non-inverted) trilinear hexahedra, for the
+# distance-Laplacian experiments of §3.1-§3.2 (a randomly perturbed cube and a triaxially
+# graded cube with a reaction term).  Element (i, j, k) has the 8 nodes (i + ax, j + ay,
+# k + az), a in {0,1}^3, local number ax + 2 ay + 4 az, reference coordinates 2a - 1.  Its
+# matrix is c_e * stiffness + r_e * mass, integrated with the 2 x 2 x 2 Gauss rule (points
+# +-1/sqrt(3), weights 1), which is exact for the mass and stiffness of axis-aligned boxes.
+# Entry (p, q) of the global matrix adds its element contributions in increasing element
+# number (e = i + nex (j + ney k)); each element's matrix is exactly symmetric, so the global
+# matrix is too.
+
+_GAUSS = 1.0 / np.sqrt(3.0)
+
+
+def _hex_element_matrices(Xe: np.ndarray, coef: np.ndarray, reaction: np.ndarray | None) -> np.ndarray:
+    """Xe: (E, 8, 3) node coordinates; coef, reaction: (E,).  Returns (E, 8, 8)."""
+    E = Xe.shape[0]
+    sgn = np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1] for a in range(8)],
+                   dtype=np.float64)
+    K = np.zeros((E, 8, 8))
+    M = np.zeros((E, 8, 8)) if reaction is not None else None
+    for gz in (-_GAUSS, _GAUSS):
+        for gy in (-_GAUSS, _GAUSS):
+            for gx in (-_GAUSS, _GAUSS):
+                g = np.array([gx, gy, gz])
+                f = 1.0 + sgn * g                       # (8, 3): 1 + xi_a xi per axis
+                N = f[:, 0] * f[:, 1] * f[:, 2] / 8.0   # shape functions
+                dN = np.empty((8, 3))                   # d N_a / d xi_q
+                dN[:, 0] = sgn[:, 0] * f[:, 1] * f[:, 2] / 8.0
+                dN[:, 1] = f[:, 0] * sgn[:, 1] * f[:, 2] / 8.0
+                dN[:, 2] = f[:, 0] * f[:, 1] * sgn[:, 2] / 8.0
+                # J[e, p, q] = sum_a X[e, a, p] dN[a, q]
+                J = np.zeros((E, 3, 3))
+                for a in range(8):
+                    J += Xe[:, a, :, None] * dN[a][None, None, :]
+                c00 = J[:, 1, 1] * J[:, 2, 2] - J[:, 1, 2] * J[:, 2, 1]
+                c01 = J[:, 1, 2] * J[:, 2, 0] - J[:, 1, 0] * J[:, 2, 2]
+                c02 = J[:, 1, 0] * J[:, 2, 1] - J[:, 1, 1] * J[:, 2, 0]
+                det = J[:, 0, 0] * c00 + J[:, 0, 1] * c01 + J[:, 0, 2] * c02
+                if np.any(det <= 0.0):
+                    raise ValueError("inverted or degenerate hexahedron")
+                inv = np.empty((E, 3, 3))           # inv = J^-1 (adjugate / det)
+                inv[:, 0, 0] = c00
+                inv[:, 1, 0] = c01
+                inv[:, 2, 0] = c02
+                inv[:, 0, 1] = J[:, 0, 2] * J[:, 2, 1] - J[:, 0, 1] * J[:, 2, 2]
+                inv[:, 1, 1] = J[:, 0, 0] * J[:, 2, 2] - J[:, 0, 2] * J[:, 2, 0]
+                inv[:, 2, 1] = J[:, 0, 1] * J[:, 2, 0] - J[:, 0, 0] * J[:, 2, 1]
+                inv[:, 0, 2] = J[:, 0, 1] * J[:, 1, 2] - J[:, 0, 2] * J[:, 1, 1]
+                inv[:, 1, 2] = J[:, 0, 2] * J[:, 1, 0] - J[:, 0, 0] * J[:, 1, 2]
+                inv[:, 2, 2] = J[:, 0, 0] * J[:, 1, 1] - J[:, 0, 1] * J[:, 1, 0]
+                inv /= det[:, None, None]
+                # physical gradients G[e, a, p] = sum_q dN[a, q] inv[e, q, p]
+                G = np.zeros((E, 8, 3))
+                for q in range(3):
+                    G += dN[None, :, q, None] * inv[:, None, q, :]
+                w = (det * coef)[:, None, None]
+                K += w * (G[:, :, None, 0] * G[:, None, :, 0] + G[:, :, None, 1] * G[:, None, :, 1]
+                          + G[:, :, None, 2] * G[:, None, :, 2])
+                if M is not None:
+                    M += (det * reaction)[:, None, None] * (N[:, None] * N[None, :])[None]
+    return K if M is None else K + M
+
+
+def hex_q1_matrix(X: np.ndarray, Y: np.ndarray, Z: np.ndarray, coef=None, reaction=None,
+                  dirichlet: bool = True) -> CSR:
+    """Q1 matrix of the structured hexahedral grid with node coordinates X, Y, Z (each of
+    shape (nez + 1, ney + 1, nex + 1), node (i, j, k) at [k, j, i]).  coef: per-element
+    diffusion (shape (nez, ney, nex) or None for 1); reaction: per-element coefficient of the
+    mass term (the 1/sigma of §3.2's reaction-diffusion equation) or None.  With Dirichlet
+    boundaries the boundary nodes are eliminated.  meta["coords"] holds the (n, 3)
+    coordinates of the unknowns, in unknown order."""
+    X, Y, Z = (np.ascontiguousarray(a, dtype=np.float64) for a in (X, Y, Z))
+    nz1, ny1, nx1 = X.shape
+    nex, ney, nez = nx1 - 1, ny1 - 1, nz1 - 1
+    E = nex * ney * nez
+    ei, ej, ek = np.meshgrid(np.arange(nex), np.arange(ney), np.arange(nez), indexing="xy")
+    # element order e = i + nex (j + ney k)
+    ei = np.transpose(ei, (2, 0, 1)).ravel()
+    ej = np.transpose(ej, (2, 0, 1)).ravel()
+    ek = np.transpose(ek, (2, 0, 1)).ravel()
+    nodes = np.empty((E, 8), dtype=np.int64)
+    Xe = np.empty((E, 8, 3))
+    for a in range(8):
+        ii, jj, kk = ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1)
+        nodes[:, a] = ii + nx1 * (jj + ny1 * kk)
+        Xe[:, a, 0] = X[kk, jj, ii]
+        Xe[:, a, 1] = Y[kk, jj, ii]
+        Xe[:, a, 2] = Z[kk, jj, ii]
+    c = np.ones(E) if coef is None else np.asarray(coef, dtype=np.float64).reshape(nez, ney, nex).ravel()
+    r = None if reaction is None else np.broadcast_to(np.asarray(reaction, dtype=np.float64),
+                                                      (nez, ney, nex)).ravel()
+    Ke = _hex_element_matrices(Xe, c, r)
+    # unknown numbering
+    if dirichlet:
+        inner = np.zeros((nz1, ny1, nx1), dtype=bool)
+        inner[1:-1, 1:-1, 1:-1] = True
+    else:
+        inner = np.ones((nz1, ny1, nx1), dtype=bool)
+    inner = inner.ravel()
+    num = np.full(inner.size, -1, dtype=np.int64)
+    num[inner] = np.arange(int(inner.sum()))
+    n = int(inner.sum())
+    rows = np.repeat(num[nodes], 8, axis=1).ravel()          # (E, 64): row of entry (a, b)
+    cols = np.tile(num[nodes], (1, 8)).ravel()
+    vals = Ke.reshape(E, 64).ravel()
+    keep = (rows >= 0) & (cols >= 0)
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    elem = np.repeat(np.arange(E), 64)[keep]
+    order = np.lexsort((elem, cols, rows))                    # by row, column, element
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    key = rows * n + cols
+    start = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    cnt = np.diff(np.r_[start, key.size])
+    acc = vals[start].copy()
+    for k in range(1, int(cnt.max()) if cnt.size else 1):   # contributions in element order
+        m = cnt > k
+        acc[m] = acc[m] + vals[start[m] + k]
+    urow = rows[start]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, urow + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    coords = np.stack([X.ravel()[inner], Y.ravel()[inner], Z.ravel()[inner]], axis=1)
+    return CSR(n, row_ptr, cols[start].astype(np.int32), acc,
+               meta={"grid": (nx1 - 2, ny1 - 2, nz1 - 2) if dirichlet else (nx1, ny1, nz1), "coords": coords})
+
+
+def perturbed_cube(ne: int = 60, seed: int = 5, amplitude: float = 0.2, zscale: float = 100.0) -> CSR:
+    """§3.1's randomly perturbed cube: the Laplacian on [0,1] x [0,1] x [0,zscale] with ne
+    elements per direction; every node of the uniform grid moves along each axis by
+    amplitude * u / ne (u uniform in [0, 1), SplitMix64 stream `seed`, three draws per node
+    in node order x, y, z) before z is scaled by zscale, so the z spacing is zscale times
+    the x and y spacing and the hexahedra are general trilinear ones."""
+    n1 = ne + 1
+    u = uniform01(seed, 3 * n1 ** 3).reshape(n1, n1, n1, 3)   # [k, j, i, axis]
+    g = np.arange(n1, dtype=np.float64) / ne
+    Z0, Y0, X0 = np.meshgrid(g, g, g, indexing="ij")
+    X = X0 + amplitude * u[..., 0] / ne
+    Y = Y0 + amplitude * u[..., 1] / ne
+    Z = (Z0 + amplitude * u[..., 2] / ne) * zscale
+    A = hex_q1_matrix(X, Y, Z)
+    A.meta.update(family="perturbed", ne=ne, seed=seed)
+    return A
+
+
+def graded_sizes(k: float, ne: int = 60) -> np.ndarray:
+    """Element sizes varying linearly from 0.1 to k/10 over ne elements (length 3(k+1)
+    for ne = 60), the grading of §3.2's triaxially stretched cube."""
+    return 0.1 + (k / 10.0 - 0.1) * np.arange(ne, dtype=np.float64) / (ne - 1)
+
+
+def graded_cube(kx: float, ky: float, kz: float, sigma: float, ne: int = 60) -> CSR:
+    """§3.2's triaxially stretched cube: sigma^-1 u - Laplace(u) on the tensor mesh with
+    graded_sizes(kx), (ky), (kz) along x, y, z (positive row sums from the reaction term)."""
+    ax = [np.r_[0.0, np.cumsum(graded_sizes(k, ne))] for k in (kx, ky, kz)]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    A = hex_q1_matrix(X, Y, Z, reaction=1.0 / sigma)
+    A.meta.update(family="graded", k=(kx, ky, kz), sigma=sigma, ne=ne)
+    return A
+
+
 def variants_mask(names) -> int:
     m = 0
     for s in names:
@@ -363,5 +524,6 @@ __all__ = [
     "stretched_box", "random_coefficient_cube", "neumann_box", "workload_laplace20",
     "workload_stretched64", "workload_randcoef128", "batched_systems", "serving_stream", "make_operator",
     "VARIANT_BITS",
-    "variants_mask", "dirichlet_stencil_row",
+    "variants_mask", "dirichlet_stencil_row", "hex_q1_matrix", "perturbed_cube", "graded_sizes",
+    "graded_cube",
 ]
