@@ -273,12 +273,25 @@ def run_once(args):
     v = torch.from_numpy(A.val).cuda()
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros_like(bd)
+    arg = amg.csr_arg(A.n, rp, ci, v)
+    phases = None
+    if args.trace:
+        # a warm-up setup, then one with every phase boundary synchronised and timed
+        for trace in (0, 1):
+            ht = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name],
+                                                                 precision=prec, trace=trace))
+            if trace:
+                levels = amg.amg_num_levels(ht)
+                phases = [{k: round(t, 3) for k, t in amg.amg_setup_trace(ht, l).items() if t > 0}
+                          for l in range(levels)]
+            amg.amg_free(ht)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = amg.amg_setup(amg.csr_arg(A.n, rp, ci, v), None,
-                      amg.amg_params_default(theta=theta, variants=variants[name], precision=prec))
+    h = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec))
     torch.cuda.synchronize()
     out = {"workload": args.workload, "method": name, "setup_ms": 1000 * (time.perf_counter() - t0)}
+    if phases is not None:
+        out["phases_ms"] = phases
     t0 = time.perf_counter()
     if args.vcycles:
         for _ in range(args.vcycles):
@@ -502,6 +515,7 @@ def main():
                     help="one setup + solve (or --vcycles V-cycles) of one method, for profiler captures")
     ap.add_argument("--method", default=None, help="with --once: which method of the workload (default: first)")
     ap.add_argument("--vcycles", type=int, default=0)
+    ap.add_argument("--trace", action="store_true", help="with --once: also report the setup's phase times")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched line")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-count", type=int, default=512, help="systems of the batched line")

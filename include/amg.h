@@ -93,6 +93,8 @@ typedef struct {
     double lambda_override; /* > 0: prolongator-smoothing eigenvalue on every level (tests)  */
     void *cuda_stream;   /* cudaStream_t to run on; NULL = the legacy default stream         */
     int strength;        /* AMG_STRENGTH_MATRIX (Eq. 7 on A_l) or AMG_STRENGTH_DISTANCE       */
+    int trace;           /* 1: time each setup phase (synchronises the stream at every phase  */
+                         /*    boundary; read with amg_setup_trace); 0: no tracing (default)   */
 } amg_params_t;
 
 typedef struct {
@@ -135,6 +137,24 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
 
 /* Releases every resource of the handle; NULL is accepted. */
 amg_status_t amg_free(amg_handle_t h);
+
+/* Setup phases timed when params.trace = 1 (wall milliseconds on the host, the stream
+ * synchronised at each boundary, so each phase includes its device work):
+ *   per level l that was coarsened: STRENGTH (Eq. 7 and the strong graph), AGGREGATE (distance-2
+ *   MIS and joins), FILTER (aggregate members, Sprsfy, the filtered matrix and its diagonal),
+ *   EIGEN (lambda-bar, omega), PROLONG (smoothed P, Cnstrnt, column scaling, R = P^T),
+ *   GALERKIN_AP and GALERKIN_RAP (the two products of Eq. 2), SMOOTHER (1/diag and the
+ *   Chebyshev eigenvalue);
+ *   level 0 only: INPUT (copy and validation of A) and PREPARE (solve vectors, FP32 copies);
+ *   the coarsest level only: COARSE (dense Cholesky factor and inverse). */
+enum {
+    AMG_PH_INPUT = 0, AMG_PH_STRENGTH = 1, AMG_PH_AGGREGATE = 2, AMG_PH_FILTER = 3, AMG_PH_EIGEN = 4,
+    AMG_PH_PROLONG = 5, AMG_PH_GALERKIN_AP = 6, AMG_PH_GALERKIN_RAP = 7, AMG_PH_SMOOTHER = 8,
+    AMG_PH_COARSE = 9, AMG_PH_PREPARE = 10, AMG_PH_COUNT = 11
+};
+/* ms[AMG_PH_COUNT] receives level l's phase times (0 where a phase did not run on that level,
+ * or without tracing). */
+amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms);
 
 /* Number of levels. */
 amg_status_t amg_num_levels(amg_handle_t h, int *levels);

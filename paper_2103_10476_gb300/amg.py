@@ -24,6 +24,8 @@ AMG_FP64, AMG_MIXED = 0, 1
 AMG_PT_ORTHONORMAL, AMG_PT_UNIT = 0, 1
 AMG_LAMBDA_ONE, AMG_LAMBDA_POWER = 0, 1
 AMG_STRENGTH_MATRIX, AMG_STRENGTH_DISTANCE = 0, 1
+PHASES = ("input", "strength", "aggregate", "filter", "eigen", "prolong", "galerkin_ap", "galerkin_rap",
+          "smoother", "coarse", "prepare")
 EXPORTS = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
            "removed": (4, np.uint8), "lumpflag": (5, np.uint8), "Abar.rp": (6, np.int64), "Abar.ci": (7, np.int32),
            "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
@@ -49,7 +51,8 @@ class amg_params_t(C.Structure):
                 ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
-                ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int)]
+                ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int),
+                ("trace", C.c_int)]
 
 
 class amg_info_t(C.Structure):
@@ -93,6 +96,7 @@ def _load():
         "amg_solve": (st, [vp, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
         "amg_free": (st, [vp]),
         "amg_num_levels": (st, [vp, C.POINTER(C.c_int)]),
+        "amg_setup_trace": (st, [vp, C.c_int, C.POINTER(C.c_double)]),
         "amg_level_info": (st, [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "amg_export_count": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
         "amg_export": (st, [vp, C.c_int, C.c_int, vp]),
@@ -239,6 +243,13 @@ def amg_export(h, level: int, what: str) -> np.ndarray:
     if cnt.value:
         _check(lib.amg_export(h, level, code, out.ctypes.data), "amg_export")
     return out[:cnt.value]
+
+
+def amg_setup_trace(h, level: int) -> dict:
+    """Setup phase times (ms) of one level of a hierarchy built with params.trace = 1."""
+    ms = (C.c_double * len(PHASES))()
+    _check(lib.amg_setup_trace(h, level, ms), "amg_setup_trace")
+    return {name: ms[k] for k, name in enumerate(PHASES)}
 
 
 def amg_vcycle(h, r, z):

@@ -154,6 +154,7 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
 
 // --------------------------------------------------------------------------------- coarse.cu
 // Dense SPD inverse of the coarsest operator via Cholesky (FP64).  info = 0 or pivot row+1.
+// work: 2 n^2 + n doubles.
 cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s);
 
 // --------------------------------------------------------------------------------- solve.cu

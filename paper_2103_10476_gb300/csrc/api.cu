@@ -127,6 +127,19 @@ double now_ms()
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+}  // namespace
+
+void amgk::trace_mark(amg_hierarchy *h, int level, int phase)
+{
+    if (!h->p.trace || level < 0 || level >= 32) return;
+    cudaStreamSynchronize(h->s);
+    const double t = now_ms();
+    h->phase_ms[level][phase] += t - h->phase_t;
+    h->phase_t = t;
+}
+
+namespace {
+
 // one level of the hierarchy; *coarsest = 1 if the level cannot be coarsened further
 amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
 {
@@ -171,6 +184,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(cudaStreamSynchronize(s));
     CK(cudaMallocAsync(&gci, sizeof(int) * (size_t)(nnz_g > 0 ? nnz_g : 1), s));
     CK(strong_graph_fill(A, lv.strong, grp, gci, s));
+    trace_mark(h, L, AMG_PH_STRENGTH);
     // aggregation
     CK(dalloc(h, &lv.agg, (size_t)n));
     CK(dalloc(h, &lv.root, (size_t)n));
@@ -185,6 +199,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         CK(e);
     }
     lv.nagg = nagg;
+    trace_mark(h, L, AMG_PH_AGGREGATE);
     if (nagg == n || nagg == 0) { *coarsest = 1; goto done; }
     // members and tentative-prolongator column norms
     CK(cudaMallocAsync(&mstart, sizeof(int) * (size_t)(nagg + 1), s));
@@ -227,6 +242,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         st = AMG_ERR_ZERO_DIAG;
         goto done;
     }
+    trace_mark(h, L, AMG_PH_FILTER);
     // eigenvalue of Dsm^-1 Abar and omega = 4 / (3 lambda), Eq. (3)
     CK(cudaMallocAsync(&px, sizeof(double) * (size_t)n, s));
     CK(cudaMallocAsync(&py, sizeof(double) * (size_t)n, s));
@@ -254,6 +270,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     }
     lv.omega = 4.0 / (3.0 * lv.lambda_bar);
     CK(cudaMemcpyAsync(scal + 2, &lv.omega, sizeof(double), cudaMemcpyHostToDevice, s));
+    trace_mark(h, L, AMG_PH_EIGEN);
     // smoothed prolongator (unit basis), Algorithm 3, column scaling
     lv.P.n = n;
     lv.P.ncol = nagg;
@@ -280,6 +297,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(transpose_counts(lv.P, lv.R.rp, s));
     CK(scan_exclusive(lv.R.rp, lv.R.rp, nagg, s));
     CK(transpose_fill(lv.P, lv.R, fill, s));
+    trace_mark(h, L, AMG_PH_PROLONG);
     // Galerkin product with the original A, Eq. (2)
     {
         cudaError_t e;
@@ -290,6 +308,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         }
         if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow in A*P"; st = AMG_ERR_INTERNAL; goto done; }
         CK(e);
+        trace_mark(h, L, AMG_PH_GALERKIN_AP);
         {
             ProfScope ps(KC_SPGEMM, s, 0.0);
             e = spgemm(lv.R, AP, Ac, &ovf, s);
@@ -297,6 +316,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         }
         if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow in R*(AP)"; st = AMG_ERR_INTERNAL; goto done; }
         CK(e);
+        trace_mark(h, L, AMG_PH_GALERKIN_RAP);
     }
     // Chebyshev smoother: lambda_max(D^-1 A_L) and D^-1
     CK(dalloc(h, &lv.invdiag, (size_t)n));
@@ -312,6 +332,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         st = AMG_ERR_EIGEN;
         goto done;
     }
+    trace_mark(h, L, AMG_PH_SMOOTHER);
     // next level
     {
         Level &nx = h->lev[L + 1];
@@ -565,6 +586,14 @@ void amg_params_default(amg_params_t *p)
     p->lambda_override = 0.0;
     p->cuda_stream = nullptr;
     p->strength = AMG_STRENGTH_MATRIX;
+    p->trace = 0;
+}
+
+amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms)
+{
+    if (!h || !ms || level < 0 || level >= h->nlev) return AMG_ERR_INVALID_ARG;
+    for (int k = 0; k < AMG_PH_COUNT; ++k) ms[k] = h->phase_ms[level][k];
+    return AMG_OK;
 }
 
 const char *amg_status_string(amg_status_t s)
@@ -659,6 +688,7 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
     keep_pool_memory();
     amg_hierarchy *h = new amg_hierarchy();
     h->p = p;
+    h->phase_t = t_start;
     h->s = (cudaStream_t)p.cuda_stream;
     amg_status_t st = AMG_OK;
     cudaStream_t s = h->s;
@@ -710,12 +740,14 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         else if (n > 0) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
         CK(cudaGetLastError());
         h->fine_nnz = nnz;
+        trace_mark(h, 0, AMG_PH_INPUT);
     }
     // levels
     for (L = 0;; ++L) {
         Level &lv = h->lev[L];
         CK(dalloc(h, &lv.diag, (size_t)lv.A.n));
         CK(diag_extract(lv.A, nullptr, lv.diag, s));
+        trace_mark(h, L, AMG_PH_STRENGTH);
         if (lv.A.n <= p.max_coarse || L + 1 >= maxL) break;
         int coarsest = 0;
         st = build_level(h, L, &coarsest);
@@ -729,13 +761,16 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         const int nc = cl.A.n;
         if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
         CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
-        CK(cudaMallocAsync(&cwork, sizeof(double) * ((size_t)nc * nc > 0 ? (size_t)nc * nc : 1), s));
+        // the factor, its transpose and the reciprocal diagonal
+        CK(cudaMallocAsync(&cwork, sizeof(double) * (2 * (size_t)nc * nc + (size_t)nc + 1), s));
         CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s));
         CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (coarse_info) { g_last_error = "coarsest operator not positive definite"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
+        trace_mark(h, L, AMG_PH_COARSE);
     }
     st = prepare_solve(h);
+    trace_mark(h, 0, AMG_PH_PREPARE);
     if (st == AMG_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fail_cuda(e, "setup");

@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(kET) segcheb0_kernel(const SegTile *tiles, con
     }
 }
 
-// dense coarsest-level solves x = Ainv f, a block per slot, a warp per row (FP64 sums)
+// dense coarsest-level solves x = Ainv f: a block per item (kCoarseRows rows of one slot's
+// solve), a warp per row (FP64 sums over the row in lane-strided order)
 template <typename T>
 __global__ void __launch_bounds__(kET) segcoarse_kernel(const SegCoarse *list, const int *count, const T *f, T *x,
                                                         int nslots, int cap, EngGuard *guard)
@@ -181,11 +182,13 @@ __global__ void __launch_bounds__(kET) segcoarse_kernel(const SegCoarse *list, c
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int t = blockIdx.x; t < n_items; t += gridDim.x) {
         const SegCoarse c = list[t];
-        if (c.slot < 0 || c.slot >= nslots || c.n < 0 || c.off < 0 || (int64_t)c.off + c.n > cap || !c.inv) {
+        if (c.slot < 0 || c.slot >= nslots || c.n < 0 || c.off < 0 || (int64_t)c.off + c.n > cap || !c.inv ||
+            c.row0 < 0 || c.row0 >= c.n) {
             if (threadIdx.x == 0) guard_hit(guard, 3, c.slot, c.off);
             continue;
         }
-        for (int i = w; i < c.n; i += kET / 32) {
+        const int r1 = min(c.n, c.row0 + kCoarseRows);
+        for (int i = c.row0 + w; i < r1; i += kET / 32) {
             double acc = 0.0;
             for (int k = lane; k < c.n; k += 32) acc += c.inv[(size_t)i * c.n + k] * (double)f[c.off + k];
 #pragma unroll
@@ -751,7 +754,10 @@ void Engine::build_lists()
             cut_tiles(lP_[L].host, k, h->lev[L].A.n, kET / lP_[L].lpr);
             cut_tiles(lR_[L].host, k, h->lev[L + 1].A.n, kET / lR_[L].lpr);
         }
-        lC_[sl.nlev - 1].host.push_back(hC_[(size_t)(sl.nlev - 1) * S + k]);
+        {
+            SegCoarse c = hC_[(size_t)(sl.nlev - 1) * S + k];
+            for (c.row0 = 0; c.row0 < c.n; c.row0 += kCoarseRows) lC_[sl.nlev - 1].host.push_back(c);
+        }
         cut_tiles(l0_.host, k, sl.n0, kET / l0_.lpr);
         const int cnt = (sl.n0 + kEngChunk - 1) / kEngChunk;
         const int first = (int)lch_.host.size();

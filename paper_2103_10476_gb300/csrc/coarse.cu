@@ -2,17 +2,33 @@
 // coarsest operator, then its explicit inverse, so that each V-cycle's coarse solve is one
 // dense matrix-vector product spread over many warps.
 //
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so the work is cut
+// so that no SM carries much more than its share and no step waits on a long chain of
+// dependent global-memory round trips.
+//
 // Factorisation: right-looking, 32-column panels.  Per panel one kernel factors the 32 x 32
-// diagonal block (every block redundantly, in shared memory) and solves its rows of the
-// panel; a second kernel updates the trailing lower triangle.  A pivot <= 0 stores its row
-// (1-based) in *info and the remaining kernels return without work.
+// diagonal block with a single warp in shared memory (every block redundantly, which is
+// cheaper than another launch) and then solves 32 rows of the panel below it, one row per
+// lane with the row held in registers; a second kernel updates the trailing lower triangle.
+// A pivot <= 0 stores its row (1-based) in *info and every later kernel returns at once.
+//
+// Inverse: X = L^-T L^-1, column j by one warp: L y = e_j forward and L^T x = y backward, both
+// in the axpy form (step i finishes y_i, then every lane updates the entries it owns with row
+// i of L^T resp. L, read contiguously), so a step's critical path is one multiply and one
+// shuffle.  Only x_i for i >= j is formed (the backward sweep stops at j); the strictly upper
+// part is written from the symmetry of X.
 #include <math.h>
+
+#include <algorithm>
+#include <mutex>
 
 #include "amg_internal.cuh"
 
 namespace amgk {
 
 constexpr int kPanel = 32;
+constexpr int kInvWarps = 4;                 // columns per block of the inverse (at most)
+constexpr int kInvSmem = 200 * 1024;         // dynamic shared memory cap of the inverse kernel
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
 {
@@ -21,56 +37,54 @@ __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const
     for (int e = rp[i]; e < rp[i + 1]; ++e) a[(size_t)i * n + ci[e]] = v[e];
 }
 
-// factor the diagonal block [j0, j0+b) in shared memory; rows j0+b+blockIdx.x*128+t solve
-// L_ib = A_ib L_bb^-T.  Block 0 writes the factored diagonal block back.
-__global__ void __launch_bounds__(128) panel_kernel(int n, int j0, double *a, int *info)
+// One warp per block.  Factors the diagonal block [j0, j0 + b) in shared memory (lane r owns
+// row r), then lane r solves row i = j0 + b + 32 blockIdx.x + r of the panel:
+// L_ib = A_ib L_bb^-T.  Block 0 writes the factored block back.
+__global__ void __launch_bounds__(32) panel_kernel(int n, int j0, double *a, int *info)
 {
-    __shared__ double L[kPanel][kPanel + 1];
+    __shared__ double Lb[kPanel][kPanel + 1];
     if (*info) return;
     const int b = min(kPanel, n - j0);
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-        int r = t / b, c = t % b;
-        L[r][c] = a[(size_t)(j0 + r) * n + j0 + c];
-    }
-    __syncthreads();
+    const int r = threadIdx.x;
+    if (r < b)
+        for (int c = 0; c < b; ++c) Lb[r][c] = a[(size_t)(j0 + r) * n + j0 + c];
+    __syncwarp();
     for (int j = 0; j < b; ++j) {
-        if (threadIdx.x == 0) {
-            double d = L[j][j];
-            if (!(d > 0.0)) {
-                if (blockIdx.x == 0) atomicCAS(info, 0, j0 + j + 1);
-                L[j][j] = 0.0;
-            } else {
-                L[j][j] = sqrt(d);
-            }
+        const double d = Lb[j][j];
+        if (!(d > 0.0)) {
+            if (blockIdx.x == 0 && r == 0) atomicCAS(info, 0, j0 + j + 1);
+            return;                                   // uniform over the warp
         }
-        __syncthreads();
-        if (L[j][j] == 0.0) return;
-        double ljj = L[j][j];
-        for (int i = j + 1 + threadIdx.x; i < b; i += blockDim.x) L[i][j] = L[i][j] / ljj;
-        __syncthreads();
-        for (int t = threadIdx.x; t < (b - j - 1) * (b - j - 1); t += blockDim.x) {
-            int i = j + 1 + t / (b - j - 1), k = j + 1 + t % (b - j - 1);
-            if (k <= i) L[i][k] -= L[i][j] * L[k][j];
+        const double ljj = sqrt(d);
+        __syncwarp();
+        if (r == j) Lb[j][j] = ljj;
+        if (r > j && r < b) Lb[r][j] = Lb[r][j] / ljj;
+        __syncwarp();
+        if (r > j && r < b) {
+            const double lrj = Lb[r][j];
+            for (int k = j + 1; k <= r; ++k) Lb[r][k] -= lrj * Lb[k][j];
         }
-        __syncthreads();
+        __syncwarp();
     }
-    if (blockIdx.x == 0) {
-        for (int t = threadIdx.x; t < b * b; t += blockDim.x) {
-            int r = t / b, c = t % b;
-            if (c <= r) a[(size_t)(j0 + r) * n + j0 + c] = L[r][c];
-        }
-    }
-    // rows below the block: forward substitution against L_bb
-    int i = j0 + b + blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && r < b)
+        for (int c = 0; c <= r; ++c) a[(size_t)(j0 + r) * n + j0 + c] = Lb[r][c];
+    const int i = j0 + b + blockIdx.x * kPanel + r;
     if (i >= n) return;
     double *row = a + (size_t)i * n + j0;
     double x[kPanel];
-    for (int c = 0; c < b; ++c) {
-        double s = row[c];
-        for (int k = 0; k < c; ++k) s -= x[k] * L[c][k];
-        x[c] = s / L[c][c];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c) {
+        if (c < b) {
+            double s = row[c];
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k)
+                if (k < c) s -= x[k] * Lb[c][k];
+            x[c] = s / Lb[c][c];
+        }
     }
-    for (int c = 0; c < b; ++c) row[c] = x[c];
+#pragma unroll
+    for (int c = 0; c < kPanel; ++c)
+        if (c < b) row[c] = x[c];
 }
 
 // trailing update of the lower triangle: a_ik -= sum_t L_it L_kt over the panel columns
@@ -84,71 +98,122 @@ __global__ void __launch_bounds__(256) trailing_kernel(int n, int j0, double *a,
     const int ti = blockIdx.y * 32, tk = blockIdx.x * 32;
     if (tk > ti) return;      // strictly upper tiles
     for (int t = threadIdx.x; t < 32 * b; t += blockDim.x) {
-        int r = t / b, c = t % b;
-        Li[r][c] = (ti + r < m) ? a[(size_t)(s0 + ti + r) * n + j0 + c] : 0.0;
-        Lk[r][c] = (tk + r < m) ? a[(size_t)(s0 + tk + r) * n + j0 + c] : 0.0;
+        int rr = t / b, c = t % b;
+        Li[rr][c] = (ti + rr < m) ? a[(size_t)(s0 + ti + rr) * n + j0 + c] : 0.0;
+        Lk[rr][c] = (tk + rr < m) ? a[(size_t)(s0 + tk + rr) * n + j0 + c] : 0.0;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-        int r = t / 32, c = t % 32;
-        int i = ti + r, k = tk + c;
+        int rr = t / 32, c = t % 32;
+        int i = ti + rr, k = tk + c;
         if (i >= m || k >= m || k > i) continue;
         double s = 0.0;
-        for (int q = 0; q < b; ++q) s += Li[r][q] * Lk[c][q];
+        for (int q = 0; q < b; ++q) s += Li[rr][q] * Lk[c][q];
         a[(size_t)(s0 + i) * n + s0 + k] -= s;
     }
 }
 
-// column j of A^-1 = L^-T L^-1 e_j, one warp per column, written as row j (A^-1 is symmetric)
-__global__ void inverse_kernel(int n, const double *L, double *inv, const int *info)
+// lt = L^T (upper) and rdiag = 1 / L_ii, from the factored lower triangle of a
+__global__ void transpose_lower_kernel(int n, const double *a, double *lt, double *rdiag, const int *info)
 {
     if (*info) return;
-    const int lane = threadIdx.x & 31;
-    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (j >= n) return;
-    double *y = inv + (size_t)j * n;
-    for (int i = lane; i < n; i += 32) y[i] = 0.0;
-    __syncwarp();
-    // forward: L y = e_j (y_i = 0 for i < j)
-    for (int i = j; i < n; ++i) {
-        double s = 0.0;
-        for (int k = j + lane; k < i; k += 32) s += L[(size_t)i * n + k] * y[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) y[i] = ((i == j ? 1.0 : 0.0) - s) / L[(size_t)i * n + i];
-        __syncwarp();
+    __shared__ double tile[32][33];
+    const int bi = blockIdx.y * 32, bk = blockIdx.x * 32;     // source tile rows bi.., cols bk..
+    if (bk > bi) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int y = ty; y < 32; y += 8) {
+        const int i = bi + y, k = bk + tx;
+        tile[y][tx] = (i < n && k < n && k <= i) ? a[(size_t)i * n + k] : 0.0;
     }
-    // backward: L^T x = y
-    for (int i = n - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < n; k += 32) s += L[(size_t)k * n + i] * y[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) y[i] = (y[i] - s) / L[(size_t)i * n + i];
-        __syncwarp();
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int k = bk + y, i = bi + tx;                   // lt[k][i] = a[i][k]
+        if (k < n && i < n && k <= i) lt[(size_t)k * n + i] = tile[tx][y];
+    }
+    if (bi == bk)
+        for (int y = threadIdx.x; y < 32; y += blockDim.x)
+            if (bi + y < n) rdiag[bi + y] = 1.0 / a[(size_t)(bi + y) * n + bi + y];
+}
+
+// One warp per column j.  Lane l owns y_k and x_k for k = j + l + 32 m (kept in the warp's
+// slice of shared memory).  Forward: y_i *= 1/L_ii, then y_k -= L^T_ik y_i for k > i.
+// Backward: x_i = y_i / L_ii, then y_k -= L_ik x_i for j <= k < i.  inv_ij = inv_ji = x_i.
+__global__ void __launch_bounds__(32 * kInvWarps) inverse_kernel(int n, const double *L, const double *Lt,
+                                                                  const double *rdiag, double *inv, const int *info)
+{
+    extern __shared__ double ys[];
+    if (*info) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int j = blockIdx.x * (int)(blockDim.x >> 5) + w;
+    if (j >= n) return;
+    double *y = ys + (size_t)w * n;
+    const int m = n - j;                               // entries j .. n-1, local index k - j
+    for (int t = lane; t < m; t += 32) y[t] = (t == 0) ? 1.0 : 0.0;
+    __syncwarp();
+    // forward: L y = e_j
+    for (int t = 0; t < m; ++t) {
+        const int i = j + t;
+        double yi = 0.0;
+        if ((t & 31) == lane) {
+            yi = y[t] * rdiag[i];
+            y[t] = yi;
+        }
+        yi = __shfl_sync(0xffffffffu, yi, t & 31);
+        const double *lrow = Lt + (size_t)i * n;       // row i of L^T: L_ki for k > i
+        for (int u = t + 1 + ((lane - t - 1) & 31); u < m; u += 32) y[u] -= lrow[j + u] * yi;
+    }
+    // backward: L^T x = y, rows n-1 down to j
+    for (int t = m - 1; t >= 0; --t) {
+        const int i = j + t;
+        double xi = 0.0;
+        if ((t & 31) == lane) {
+            xi = y[t] * rdiag[i];
+            y[t] = xi;
+        }
+        xi = __shfl_sync(0xffffffffu, xi, t & 31);
+        const double *lrow = L + (size_t)i * n;        // row i of L: L_ik for k < i
+        for (int u = lane; u < t; u += 32) y[u] -= lrow[j + u] * xi;
+    }
+    __syncwarp();
+    for (int t = lane; t < m; t += 32) {
+        inv[(size_t)(j + t) * n + j] = y[t];
+        inv[(size_t)j * n + j + t] = y[t];
     }
 }
 
 cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s)
 {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
+    });
+    AMG_CUDA_TRY(attr);
     const int n = A.n;
     AMG_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
     if (n == 0) return cudaSuccess;
+    // columns per block: as many as the shared-memory cap holds, at most kInvWarps
+    const int warps = (int)std::min<size_t>(kInvWarps, (size_t)kInvSmem / ((size_t)n * sizeof(double)));
+    if (warps < 1) return cudaErrorInvalidValue;
+    double *lt = work + (size_t)n * n, *rdiag = lt + (size_t)n * n;
     AMG_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(double) * (size_t)n * n, s));
     dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, work); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     for (int j0 = 0; j0 < n; j0 += kPanel) {
         const int b = min(kPanel, n - j0);
         const int rows_below = n - j0 - b;
-        const int pblocks = rows_below > 0 ? (rows_below + 127) / 128 : 1;
-        panel_kernel<<<pblocks, 128, 0, s>>>(n, j0, work, info_dev); note_launch();
+        const int pblocks = rows_below > 0 ? (rows_below + kPanel - 1) / kPanel : 1;
+        panel_kernel<<<pblocks, kPanel, 0, s>>>(n, j0, work, info_dev); note_launch();
         if (rows_below > 0) {
             int tiles = (rows_below + 31) / 32;
             trailing_kernel<<<dim3(tiles, tiles), 256, 0, s>>>(n, j0, work, info_dev); note_launch();
         }
         AMG_CUDA_TRY(cudaGetLastError());
     }
-    inverse_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, work, inv, info_dev); note_launch();
+    const int tb = (n + 31) / 32;
+    transpose_lower_kernel<<<dim3(tb, tb), 256, 0, s>>>(n, work, lt, rdiag, info_dev); note_launch();
+    const size_t smem = (size_t)warps * n * sizeof(double);
+    inverse_kernel<<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(n, work, lt, rdiag, inv, info_dev); note_launch();
     return cudaGetLastError();
 }
 

@@ -41,10 +41,11 @@ struct EngGuard {
     int info[12];       // the first item's tile, matrix and vector figures
     int waits;          // blocks whose bounded wait for a bulk copy ran out
 };
-struct SegCoarse {      // dense solve of a slot whose coarsest level this is
-    const double *inv;
-    int n, off, slot, pad;
+struct SegCoarse {      // rows [row0, row0 + kCoarseRows) of the dense solve of a slot whose
+    const double *inv;  // coarsest level this is (inverse: n x n, row-major)
+    int n, off, slot, row0;
 };
+constexpr int kCoarseRows = 32;    // rows of the coarse solve per work item
 struct SegChunk {       // at most kEngChunk fine rows of one slot (PCG vector kernels)
     int slot, begin, end, first, count, id;
 };

@@ -61,6 +61,8 @@ struct amg_hierarchy {
     SpmvPlan plan0;   // finest-level FP64 operator (PCG)
     SolveCtx ctx;
     double setup_ms = 0.0;
+    double phase_ms[32][AMG_PH_COUNT] = {};   // setup phases per level (params.trace)
+    double phase_t = 0.0;                     // end of the last traced phase
     int64_t fine_nnz = 0;
     size_t bytes = 0;   // device memory held by the handle
 };
@@ -75,4 +77,7 @@ void set_last_error(const std::string &msg);
 // range.  Returns the number of faults found (0: intact; -1: the check itself failed) and
 // names the first in *detail.  Synchronises s.
 int hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail);
+// with params.trace: synchronise the handle's stream and book the time since the last mark to
+// (level, phase)
+void trace_mark(amg_hierarchy *h, int level, int phase);
 }  // namespace amgk
