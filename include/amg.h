@@ -321,7 +321,9 @@ amg_status_t amg_server_destroy(amg_server_t srv);
 /* Measurement hooks (no counterpart in the paper).
  * amg_launch_count: kernels launched by this library since it was loaded (all threads).
  * amg_profile_enable(1) resets the totals and starts recording CUDA events around the
- * launches of these kernel classes (on the stream they run on); (0) stops.
+ * launches of these kernel classes (on the stream they run on); (2) resumes recording and
+ * keeps the totals; (0) stops (the totals stay readable).  A hierarchy whose iteration graph
+ * is captured while recording carries the events in that graph.
  *   0: the finest-level FP64 SpMV of the PCG iteration (q = A p with p.q),
  *   1: the finest-level SpMVs of the V-cycle (Chebyshev steps and residual),
  *   2: the sparse products of the Galerkin step (both phases, per product),

@@ -280,8 +280,9 @@ def amg_launch_count() -> int:
     return int(lib.amg_launch_count())
 
 
-def amg_profile_enable(on: bool):
-    _check(lib.amg_profile_enable(int(bool(on))), "amg_profile_enable")
+def amg_profile_enable(on):
+    """True/1: reset and record; 2: resume recording keeping the totals; False/0: stop."""
+    _check(lib.amg_profile_enable(int(on)), "amg_profile_enable")
 
 
 def amg_profile_read(kclass: int):

@@ -22,7 +22,7 @@ void note_launches(long long k);
 long long launch_count();
 enum KernelClass { KC_PCG_SPMV = 0, KC_VCYCLE_SPMV = 1, KC_SPGEMM = 2, KC_SETUP_SPMV = 3, KC_COUNT = 4 };
 bool profiling_enabled();
-void profile_enable(bool on);
+void profile_enable(int mode);   // 1 reset and record, 2 record (keep totals), 0 stop
 struct ProfRecord {
     int cls;
     cudaEvent_t start, stop;

@@ -621,7 +621,8 @@ int64_t amg_launch_count(void) { return (int64_t)launch_count(); }
 
 amg_status_t amg_profile_enable(int on)
 {
-    profile_enable(on != 0);
+    if (on < 0 || on > 2) return AMG_ERR_INVALID_ARG;
+    profile_enable(on);
     return AMG_OK;
 }
 

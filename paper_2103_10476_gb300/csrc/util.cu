@@ -111,12 +111,13 @@ void profile_release(ProfList &list)
     list.clear();
 }
 
-void profile_enable(bool on)
+void profile_enable(int mode)
 {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     drain_locked();
-    for (int k = 0; k < KC_COUNT; ++k) { g_prof_launches[k] = 0; g_prof_ms[k] = 0.0; g_prof_bytes[k] = 0.0; }
-    g_prof_on.store(on);
+    if (mode == 1)
+        for (int k = 0; k < KC_COUNT; ++k) { g_prof_launches[k] = 0; g_prof_ms[k] = 0.0; g_prof_bytes[k] = 0.0; }
+    g_prof_on.store(mode != 0);
 }
 
 void profile_read(int cls, long long *launches, double *ms, double *bytes)
