@@ -135,8 +135,9 @@ cudaError_t scale_columns(DevCsr &P, const double *nrm, cudaStream_t s);
 cudaError_t transpose_counts(const DevCsr &P, int *cnt, cudaStream_t s);
 cudaError_t transpose_fill(const DevCsr &P, DevCsr &R, int *fill, cudaStream_t s);
 // Power method on D^-1 A (Rayleigh quotient of the last sweep), result on the device.
-cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t stream_seed, double *x,
-                         double *y, double *partial, double *scal, double *lambda_dev, cudaStream_t s);
+struct SpmvPlan;
+cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D, int sweeps, uint64_t stream_seed,
+                         double *x, double *y, double *partial, double *scal, double *lambda_dev, cudaStream_t s);
 uint64_t power_stream_seed(uint64_t seed, int level, int purpose);
 cudaError_t omega_from_lambda(const double *lambda_dev, double *omega_dev, cudaStream_t s);
 cudaError_t invert_diag(const double *d, double *inv, float *invf, int n, int *zero, cudaStream_t s);
@@ -164,6 +165,8 @@ struct SpmvPlan {
     int cap = 0;
 };
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s);
+cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns, const int64_t *nnzs,
+                       cudaStream_t s);
 int spmv_partials_needed(int n);
 int *spmv_error_flag();
 int spmv_take_errors(cudaStream_t s);
@@ -203,6 +206,8 @@ cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, doubl
                      double *result, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
                             double *partial, double *result, unsigned *counter, cudaStream_t s);
+cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, const double *xx,
+                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
 cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
                        cudaStream_t s);

@@ -157,6 +157,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     double *px = nullptr, *py = nullptr, *scal = nullptr, *lvals = nullptr, *ldiag = nullptr;
     DevCsr AP, Ac;
     int hflags[5] = {0, 0, 0, 0, 0};
+    SpmvPlan plan_bar;
     int nagg = 0, rounds = 0, nnz_g = 0, nnz_bar = 0, nnz_p = 0, ovf = 0;
     *coarsest = 0;
 
@@ -248,15 +249,25 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(cudaMallocAsync(&py, sizeof(double) * (size_t)n, s));
     {
         // 8 scalars, then the partial sums of the power method's dot products
-        int np = spmv_partials_needed(n);
+        // the power method's two partial sums per SpMV block
+        int np = 2 * spmv_partials_needed(n);
         CK(cudaMallocAsync(&scal, sizeof(double) * (size_t)((np > kReduceBlocks ? np : kReduceBlocks) + 8), s));
+    }
+    // launch plans of the filtered matrix (λ̄ power method) and of A_l (λ* power method, and
+    // every V-cycle), with one synchronisation
+    {
+        SpmvPlan *pls[2] = {&plan_bar, &lv.plan_a};
+        const int *rps[2] = {lv.Abar.rp, A.rp};
+        const int ns[2] = {n, n};
+        const int64_t nz[2] = {lv.Abar.nnz, A.nnz};
+        CK(spmv_plans(2, pls, rps, ns, nz, s));
     }
     if (p.lambda_override > 0.0) {
         lv.lambda_bar = p.lambda_override;
     } else if ((p.variants & AMG_VAR_1NORM) && p.onenorm_lambda == AMG_LAMBDA_ONE) {
         lv.lambda_bar = 1.0;
     } else {
-        CK(power_lambda(lv.Abar, lv.Dsm, p.power_iters, power_stream_seed(p.seed, L, 1), px, py, scal + 8, scal,
+        CK(power_lambda(lv.Abar, plan_bar, lv.Dsm, p.power_iters, power_stream_seed(p.seed, L, 1), px, py, scal + 8, scal,
                         scal + 1, s));
         CK(cudaMemcpyAsync(&lv.lambda_bar, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -322,7 +333,8 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(dalloc(h, &lv.invdiag, (size_t)n));
     if (p.precision == AMG_MIXED) CK(dalloc(h, &lv.invdiag_f, (size_t)n));
     CK(invert_diag(lv.diag, lv.invdiag, lv.invdiag_f, n, flags + 3, s));
-    CK(power_lambda(A, lv.diag, p.power_iters, power_stream_seed(p.seed, L, 2), px, py, scal + 8, scal, scal + 1, s));
+    CK(power_lambda(A, lv.plan_a, lv.diag, p.power_iters, power_stream_seed(p.seed, L, 2), px, py, scal + 8, scal,
+                    scal + 1, s));
     CK(cudaMemcpyAsync(&lv.lambda_cheb, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -394,10 +406,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             v.rrp = lv.R.rp; v.rci = lv.R.ci;
             v.lambda = lv.lambda_cheb;
             v.nnz_a = lv.A.nnz;
-            CK(spmv_plan(lv.A.rp, n, lv.A.nnz, &lv.plan_a, s));
-            CK(spmv_plan(lv.P.rp, n, lv.P.nnz, &lv.plan_p, s));
-            CK(spmv_plan(lv.R.rp, lv.nagg, lv.R.nnz, &lv.plan_r, s));
-            v.plan_a = lv.plan_a; v.plan_p = lv.plan_p; v.plan_r = lv.plan_r;
+            // plan_a was made during setup; plan_p and plan_r below, all levels at once
             if (mixed) {
                 CK(dalloc(h, &lv.Af, (size_t)lv.A.nnz));
                 CK(dalloc(h, &lv.Pf, (size_t)lv.P.nnz));
@@ -433,7 +442,29 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         CK(dalloc(h, &h->partial2, (size_t)kReduceBlocks));
         CK(dalloc(h, &h->partial3, (size_t)kReduceBlocks));
         CK(cudaMallocHost(&h->rr_host, sizeof(double) * kReduceBlocks));
-        if (n0 > 0) CK(spmv_plan(h->lev[0].A.rp, n0, h->lev[0].A.nnz, &h->plan0, s));
+    }
+    // launch plans of every P and R (and of A_0 when level 0 is the coarsest), one sync
+    {
+        std::vector<SpmvPlan *> pls;
+        std::vector<const int *> rps;
+        std::vector<int> ns;
+        std::vector<int64_t> nz;
+        for (int L = 0; L + 1 < h->nlev; ++L) {
+            Level &lv = h->lev[L];
+            pls.push_back(&lv.plan_p); rps.push_back(lv.P.rp); ns.push_back(lv.A.n); nz.push_back(lv.P.nnz);
+            pls.push_back(&lv.plan_r); rps.push_back(lv.R.rp); ns.push_back(lv.nagg); nz.push_back(lv.R.nnz);
+        }
+        if (h->nlev == 1 && n0 > 0) {
+            pls.push_back(&h->plan0); rps.push_back(h->lev[0].A.rp); ns.push_back(n0); nz.push_back(h->lev[0].A.nnz);
+        }
+        CK(spmv_plans((int)pls.size(), pls.data(), rps.data(), ns.data(), nz.data(), s));
+        if (h->nlev > 1) h->plan0 = h->lev[0].plan_a;
+        for (int L = 0; L + 1 < h->nlev; ++L) {
+            Level &lv = h->lev[L];
+            c.lev[L].plan_a = lv.plan_a;
+            c.lev[L].plan_p = lv.plan_p;
+            c.lev[L].plan_r = lv.plan_r;
+        }
     }
     CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
     CK(dalloc(h, &h->counters, 8));

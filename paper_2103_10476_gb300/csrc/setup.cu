@@ -7,6 +7,8 @@
 // of the same formulas bit for bit (decisions taken on them are then identical too).
 #include <math.h>
 
+#include <utility>
+
 #include "amg_internal.cuh"
 
 namespace amgk {
@@ -348,16 +350,20 @@ cudaError_t aggregate_mis2(int n, const int *grp, const int *gci, uint64_t seed,
     const int tb = 256;
     mis_init_kernel<<<grid_for(n, tb), tb, 0, s>>>(n, seed, level, w.t0); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
+    // rounds go in pairs between looks at the undecided count (a round after the last decision
+    // changes nothing), which halves the host round trips
     int h_und = 1, rounds = 0;
     while (h_und > 0) {
         if (rounds >= 10000) return cudaErrorLaunchFailure;   // cannot happen: each round decides >= 1 vertex
-        AMG_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
-        mis_max_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t0, w.t1); note_launch();
-        mis_decide_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t1, w.t0, w.counter); note_launch();
+        for (int q = 0; q < 2; ++q) {
+            if (q == 1) AMG_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
+            mis_max_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t0, w.t1); note_launch();
+            mis_decide_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t1, w.t0, w.counter); note_launch();
+        }
         AMG_CUDA_TRY(cudaGetLastError());
         AMG_CUDA_TRY(cudaMemcpyAsync(&h_und, w.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        ++rounds;
+        rounds += 2;
     }
     *rounds_host = rounds;
     // root flags and ids (exclusive scan of root flags -> aggregate numbers by increasing root index)
@@ -985,36 +991,24 @@ __global__ void power_init_kernel(int n, uint64_t s0, double *x)
     x[i] = 2.0 * u - 1.0;
 }
 
-// dst = src / sqrt(*sq); the square root is taken once per block
-__global__ void scale_by_norm_kernel(int n, const double *src, double *dst, const double *sq)
-{
-    __shared__ double nrm;
-    if (threadIdx.x == 0) nrm = __dsqrt_rn(*sq);
-    __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = src[i] / nrm;
-}
-
-cudaError_t power_lambda(const DevCsr &A, const double *D, int sweeps, uint64_t stream_seed, double *x, double *y,
-                         double *partial, double *scal, double *lambda_dev, cudaStream_t s)
+cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D, int sweeps, uint64_t stream_seed,
+                         double *x, double *y, double *partial, double *scal, double *lambda_dev, cudaStream_t s)
 {
     const int n = A.n;
     if (n == 0) return cudaMemsetAsync(lambda_dev, 0, sizeof(double), s);
+    // x0 and x0 . x0; each sweep then works on the unnormalised iterate and its squared norm
+    // (scal[3], scal[4] alternate), which equals normalising before every sweep
     power_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, stream_seed, x); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
-    AMG_CUDA_TRY(dot(x, x, n, partial, scal, s));
-    scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, x, x, scal); note_launch();
-    SpmvPlan plan;
-    AMG_CUDA_TRY(spmv_plan(A.rp, n, A.nnz, &plan, s));
+    AMG_CUDA_TRY(dot(x, x, n, partial, scal + 3, s));
     // ticket counter of the SpMV's fixed-order reduction (scal[7], zero)
     unsigned *counter = reinterpret_cast<unsigned *>(scal + 7);
     AMG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(double), s));
+    double *a = x, *b = y;
     for (int k = 0; k < sweeps; ++k) {
-        AMG_CUDA_TRY(spmv_scaled_dot(A, plan, D, x, y, partial, lambda_dev, counter, s));
-        if (k + 1 < sweeps) {
-            AMG_CUDA_TRY(dot(y, y, n, partial, scal, s));
-            scale_by_norm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, y, x, scal); note_launch();
-        }
+        AMG_CUDA_TRY(spmv_power(A, plan, D, a, scal + 3 + (k & 1), b, scal + 4 - (k & 1), partial, lambda_dev,
+                                counter, s));
+        std::swap(a, b);
     }
     return cudaGetLastError();
 }

@@ -15,6 +15,8 @@
 // order, so every reduction is bitwise reproducible.
 #include <mutex>
 
+#include <vector>
+
 #include "amg_internal.cuh"
 #include "tma.cuh"
 
@@ -31,6 +33,8 @@ enum SpmvMode {
     MODE_PROLONG = 3,    // y += A x
     MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
     MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
+    MODE_POWER = 6,      // power-method sweep on an unnormalised x with q = f[0] = x . x:
+                         // y = (A x) / D / sqrt(q); result[0] = (x . y) / sqrt(q); d[0] = y . y
 };
 
 
@@ -60,6 +64,48 @@ __device__ __forceinline__ void last_block_total(const double *partial, int nblo
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
         *result = t;
+        *counter = 0u;
+    }
+}
+
+// Two fixed-order sums at once (partial[0, nblocks) and partial[nblocks, 2 nblocks)); the last
+// block stores *r1 = scale * (first total) and *r2 = second total.
+__device__ __forceinline__ void last_block_total2(const double *partial, int nblocks, unsigned *counter, double *r1,
+                                                  double *r2, double scale)
+{
+    __shared__ bool last;
+    __shared__ double w1[32], w2[32];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nblocks - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        a += ((volatile const double *)partial)[i];
+        b += ((volatile const double *)partial)[nblocks + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(kAll, a, o);
+        b += __shfl_down_sync(kAll, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        w1[threadIdx.x >> 5] = a;
+        w2[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t1 += w1[w];
+            t2 += w2[w];
+        }
+        *r1 = scale * t1;
+        *r2 = t2;
         *counter = 0u;
     }
 }
@@ -110,7 +156,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
-    double contrib = 0.0;
+    double contrib = 0.0, contrib2 = 0.0;
+    double rq = 0.0;                // MODE_POWER: 1 / sqrt(x . x)
+    if (MODE == MODE_POWER) rq = 1.0 / __dsqrt_rn((double)f[0]);
     if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
@@ -126,11 +174,39 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         } else if (MODE == MODE_DOT) {
             y[row] = sum;
             contrib = (double)x[row] * (double)sum;
-        } else {
+        } else if (MODE == MODE_SCALEDOT) {
             T yi = sum / aux[row];
             y[row] = yi;
             contrib = (double)x[row] * (double)yi;
+        } else {
+            const double yi = ((double)sum / (double)aux[row]) * rq;
+            y[row] = (T)yi;
+            contrib = (double)x[row] * yi;
+            contrib2 = yi * yi;
         }
+    }
+    if (MODE == MODE_POWER) {
+        __shared__ double sh1[kSpmvThreads / 32], sh2[kSpmvThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            contrib += __shfl_down_sync(kAll, contrib, o);
+            contrib2 += __shfl_down_sync(kAll, contrib2, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh1[threadIdx.x >> 5] = contrib;
+            sh2[threadIdx.x >> 5] = contrib2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int w = 0; w < kSpmvThreads / 32; ++w) {
+                t1 += sh1[w];
+                t2 += sh2[w];
+            }
+            partial[blockIdx.x] = t1;
+            partial[gridDim.x + blockIdx.x] = t2;
+        }
+        last_block_total2(partial, gridDim.x, counter, result, (double *)d, rq);
     }
     if (MODE == MODE_DOT || MODE == MODE_SCALEDOT) {
         __shared__ double sh[kSpmvThreads / 32];
@@ -167,6 +243,34 @@ __global__ void span_max_kernel(int n, const int *rp, int rpb, int *out)
     if (r0 >= n) return;
     int r1 = min(n, r0 + rpb);
     atomicMax(out, rp[r1] - rp[r0]);
+}
+
+// Plans of several matrices with one synchronisation: every span kernel is queued first,
+// then one copy of all maxima to the host.
+cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns, const int64_t *nnzs,
+                       cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    int *d = nullptr;
+    std::vector<int> h((size_t)count, 0);
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * (size_t)count, s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * (size_t)count, s);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        SpmvPlan *pl = plans[k];
+        const int n = ns[k];
+        pl->lpr = pick_lpr(n ? (double)nnzs[k] / n : 1.0);
+        pl->cap = 0;
+        if (n == 0 || nnzs[k] == 0) continue;
+        const int nb = spmv_blocks(n, pl->lpr);
+        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rps[k], kSpmvThreads / pl->lpr, d + k); note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int k = 0; k < count; ++k)
+        if (ns[k] > 0 && nnzs[k] > 0) plans[k]->cap = h[(size_t)k] + 8 < kMaxTile ? h[(size_t)k] + 8 : kMaxTile;
+    return e;
 }
 
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s)
@@ -274,6 +378,16 @@ cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D
 {
     return spmv_mode<double, MODE_SCALEDOT>(pl, A.n, A.rp, A.ci, A.v, x, y, nullptr, D, nullptr, 0.0, 0.0, partial,
                                             s, result, counter);
+}
+
+// one sweep of the power method on D^-1 A from the unnormalised x with *xx = x . x:
+// y = (D^-1 A x) / sqrt(xx), *lambda = (x . y) / sqrt(xx) (the Rayleigh quotient of the unit
+// vector), *yy = y . y.  partial holds 2 x the plan's blocks.
+cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, const double *xx,
+                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s)
+{
+    return spmv_mode<double, MODE_POWER>(pl, A.n, A.rp, A.ci, A.v, x, y, xx, D, yy, 0.0, 0.0, partial, s, lambda,
+                                         counter);
 }
 
 int spmv_partials_needed(int n) { return spmv_blocks(n, 2) + 1; }
