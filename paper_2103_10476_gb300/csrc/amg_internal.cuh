@@ -154,9 +154,11 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
                            cudaStream_t s);
 
 // --------------------------------------------------------------------------------- coarse.cu
-// Dense SPD inverse of the coarsest operator via Cholesky (FP64).  info = 0 or pivot row+1.
-// work: 2 n^2 + n doubles.
-cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s);
+// Dense SPD inverse of the coarsest operator in FP64 (FP32 Cholesky and inverse refined by
+// Newton-Schulz in FP64, or the FP64 factorisation when that does not converge).  info = 0
+// or the failing pivot row + 1.  work: coarse_work_bytes(n) bytes.
+size_t coarse_work_bytes(int n);
+cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_dev, cudaStream_t s);
 
 // --------------------------------------------------------------------------------- solve.cu
 // SpMV launch plan of one matrix: lanes per row and the shared-memory tile (entries; 0 = none)

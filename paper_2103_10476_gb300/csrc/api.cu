@@ -793,8 +793,7 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         const int nc = cl.A.n;
         if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
         CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
-        // the factor, its transpose and the reciprocal diagonal
-        CK(cudaMallocAsync(&cwork, sizeof(double) * (2 * (size_t)nc * nc + (size_t)nc + 1), s));
+        CK(cudaMallocAsync(&cwork, coarse_work_bytes(nc), s));
         CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s));
         CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

@@ -1,22 +1,28 @@
-// coarse.cu -- direct solve on the coarsest level (§3.1): dense FP64 Cholesky factor of the
-// coarsest operator, then its explicit inverse, so that each V-cycle's coarse solve is one
-// dense matrix-vector product spread over many warps.
+// coarse.cu -- direct solve on the coarsest level (§3.1): the explicit inverse of the coarsest
+// operator in FP64, so that each V-cycle's coarse solve is one dense matrix-vector product
+// spread over many warps.
 //
-// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU, so the work is cut
-// so that no SM carries much more than its share and no step waits on a long chain of
-// dependent global-memory round trips.
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU: a warp's FP64
+// instruction occupies a sub-partition's FP64 unit for tens of cycles, so a serial chain of
+// FP64 operations (a Cholesky panel, a triangular solve) is slow however few flops it has,
+// while independent FP64 work spread over every sub-partition runs at the full rate.  The
+// inverse is therefore formed in two stages:
+//   1. Cholesky factor and inverse in FP32 (the serial chains at the FP32 rate): X0.
+//   2. Newton-Schulz refinement in FP64, X <- X (2I - A X), as dense products with one output
+//      per thread.  The error E = max |I - A X| squares every step; the step taken with
+//      E < 1e-10 is the last (two steps from an FP32 inverse of a well-conditioned operator).
+// If the FP32 factorisation meets a pivot <= 0 (the operator is too ill-conditioned for FP32)
+// or the refinement does not bring E below 1e-6, the inverse is formed directly in FP64 by
+// the same factorisation and inverse kernels in double precision.
 //
-// Factorisation: right-looking, 32-column panels.  Per panel one kernel factors the 32 x 32
-// diagonal block with a single warp in shared memory (every block redundantly, which is
-// cheaper than another launch) and then solves 32 rows of the panel below it, one row per
-// lane with the row held in registers; a second kernel updates the trailing lower triangle.
-// A pivot <= 0 stores its row (1-based) in *info and every later kernel returns at once.
-//
-// Inverse: X = L^-T L^-1, column j by one warp: L y = e_j forward and L^T x = y backward, both
-// in the axpy form (step i finishes y_i, then every lane updates the entries it owns with row
-// i of L^T resp. L, read contiguously), so a step's critical path is one multiply and one
-// shuffle.  Only x_i for i >= j is formed (the backward sweep stops at j); the strictly upper
-// part is written from the symmetry of X.
+// Factorisation (either precision): right-looking, 32-column panels.  Per panel one kernel
+// factors the 32 x 32 diagonal block with a single warp in shared memory (every block
+// redundantly, cheaper than another launch) and then solves 32 rows of the panel below it,
+// one row per lane with the row in registers; a second kernel updates the trailing lower
+// triangle.  A pivot <= 0 stores its row (1-based) in *info and every later kernel returns.
+// Inverse: X = L^-T L^-1, column j by one warp in the axpy form (step i finishes y_i, then
+// every lane updates the entries it owns from a contiguous row of L^T resp. L); the backward
+// sweep stops at j and the strictly upper part is written from the symmetry of X.
 #include <math.h>
 
 #include <algorithm>
@@ -29,6 +35,8 @@ namespace amgk {
 constexpr int kPanel = 32;
 constexpr int kInvWarps = 4;                 // columns per block of the inverse (at most)
 constexpr int kInvSmem = 200 * 1024;         // dynamic shared memory cap of the inverse kernel
+constexpr int kNewtonSteps = 6;              // refinement steps at most
+constexpr int kGT = 32;                      // product tile
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
 {
@@ -37,12 +45,20 @@ __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const
     for (int e = rp[i]; e < rp[i + 1]; ++e) a[(size_t)i * n + ci[e]] = v[e];
 }
 
+template <typename A, typename B>
+__global__ void convert_dense_kernel(size_t count, const A *src, B *dst)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = (B)src[i];
+}
+
 // One warp per block.  Factors the diagonal block [j0, j0 + b) in shared memory (lane r owns
 // row r), then lane r solves row i = j0 + b + 32 blockIdx.x + r of the panel:
 // L_ib = A_ib L_bb^-T.  Block 0 writes the factored block back.
-__global__ void __launch_bounds__(32) panel_kernel(int n, int j0, double *a, int *info)
+template <typename T>
+__global__ void __launch_bounds__(32) panel_kernel(int n, int j0, T *a, int *info)
 {
-    __shared__ double Lb[kPanel][kPanel + 1];
+    __shared__ T Lb[kPanel][kPanel + 1];
     if (*info) return;
     const int b = min(kPanel, n - j0);
     const int r = threadIdx.x;
@@ -50,18 +66,18 @@ __global__ void __launch_bounds__(32) panel_kernel(int n, int j0, double *a, int
         for (int c = 0; c < b; ++c) Lb[r][c] = a[(size_t)(j0 + r) * n + j0 + c];
     __syncwarp();
     for (int j = 0; j < b; ++j) {
-        const double d = Lb[j][j];
-        if (!(d > 0.0)) {
+        const T d = Lb[j][j];
+        if (!(d > T(0))) {
             if (blockIdx.x == 0 && r == 0) atomicCAS(info, 0, j0 + j + 1);
             return;                                   // uniform over the warp
         }
-        const double ljj = sqrt(d);
+        const T ljj = sqrt(d);
         __syncwarp();
         if (r == j) Lb[j][j] = ljj;
         if (r > j && r < b) Lb[r][j] = Lb[r][j] / ljj;
         __syncwarp();
         if (r > j && r < b) {
-            const double lrj = Lb[r][j];
+            const T lrj = Lb[r][j];
             for (int k = j + 1; k <= r; ++k) Lb[r][k] -= lrj * Lb[k][j];
         }
         __syncwarp();
@@ -70,12 +86,12 @@ __global__ void __launch_bounds__(32) panel_kernel(int n, int j0, double *a, int
         for (int c = 0; c <= r; ++c) a[(size_t)(j0 + r) * n + j0 + c] = Lb[r][c];
     const int i = j0 + b + blockIdx.x * kPanel + r;
     if (i >= n) return;
-    double *row = a + (size_t)i * n + j0;
-    double x[kPanel];
+    T *row = a + (size_t)i * n + j0;
+    T x[kPanel];
 #pragma unroll
     for (int c = 0; c < kPanel; ++c) {
         if (c < b) {
-            double s = row[c];
+            T s = row[c];
 #pragma unroll
             for (int k = 0; k < kPanel; ++k)
                 if (k < c) s -= x[k] * Lb[c][k];
@@ -88,42 +104,44 @@ __global__ void __launch_bounds__(32) panel_kernel(int n, int j0, double *a, int
 }
 
 // trailing update of the lower triangle: a_ik -= sum_t L_it L_kt over the panel columns
-__global__ void __launch_bounds__(256) trailing_kernel(int n, int j0, double *a, const int *info)
+template <typename T>
+__global__ void __launch_bounds__(256) trailing_kernel(int n, int j0, T *a, const int *info)
 {
     if (*info) return;
     const int b = min(kPanel, n - j0);
     const int s0 = j0 + b;
     const int m = n - s0;
-    __shared__ double Li[32][kPanel + 1], Lk[32][kPanel + 1];
+    __shared__ T Li[32][kPanel + 1], Lk[32][kPanel + 1];
     const int ti = blockIdx.y * 32, tk = blockIdx.x * 32;
     if (tk > ti) return;      // strictly upper tiles
     for (int t = threadIdx.x; t < 32 * b; t += blockDim.x) {
         int rr = t / b, c = t % b;
-        Li[rr][c] = (ti + rr < m) ? a[(size_t)(s0 + ti + rr) * n + j0 + c] : 0.0;
-        Lk[rr][c] = (tk + rr < m) ? a[(size_t)(s0 + tk + rr) * n + j0 + c] : 0.0;
+        Li[rr][c] = (ti + rr < m) ? a[(size_t)(s0 + ti + rr) * n + j0 + c] : T(0);
+        Lk[rr][c] = (tk + rr < m) ? a[(size_t)(s0 + tk + rr) * n + j0 + c] : T(0);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         int rr = t / 32, c = t % 32;
         int i = ti + rr, k = tk + c;
         if (i >= m || k >= m || k > i) continue;
-        double s = 0.0;
+        T s = T(0);
         for (int q = 0; q < b; ++q) s += Li[rr][q] * Lk[c][q];
         a[(size_t)(s0 + i) * n + s0 + k] -= s;
     }
 }
 
 // lt = L^T (upper) and rdiag = 1 / L_ii, from the factored lower triangle of a
-__global__ void transpose_lower_kernel(int n, const double *a, double *lt, double *rdiag, const int *info)
+template <typename T>
+__global__ void transpose_lower_kernel(int n, const T *a, T *lt, T *rdiag, const int *info)
 {
     if (*info) return;
-    __shared__ double tile[32][33];
+    __shared__ T tile[32][33];
     const int bi = blockIdx.y * 32, bk = blockIdx.x * 32;     // source tile rows bi.., cols bk..
     if (bk > bi) return;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
     for (int y = ty; y < 32; y += 8) {
         const int i = bi + y, k = bk + tx;
-        tile[y][tx] = (i < n && k < n && k <= i) ? a[(size_t)i * n + k] : 0.0;
+        tile[y][tx] = (i < n && k < n && k <= i) ? a[(size_t)i * n + k] : T(0);
     }
     __syncthreads();
     for (int y = ty; y < 32; y += 8) {
@@ -132,46 +150,45 @@ __global__ void transpose_lower_kernel(int n, const double *a, double *lt, doubl
     }
     if (bi == bk)
         for (int y = threadIdx.x; y < 32; y += blockDim.x)
-            if (bi + y < n) rdiag[bi + y] = 1.0 / a[(size_t)(bi + y) * n + bi + y];
+            if (bi + y < n) rdiag[bi + y] = T(1) / a[(size_t)(bi + y) * n + bi + y];
 }
 
 // One warp per column j.  Lane l owns y_k and x_k for k = j + l + 32 m (kept in the warp's
 // slice of shared memory).  Forward: y_i *= 1/L_ii, then y_k -= L^T_ik y_i for k > i.
 // Backward: x_i = y_i / L_ii, then y_k -= L_ik x_i for j <= k < i.  inv_ij = inv_ji = x_i.
-__global__ void __launch_bounds__(32 * kInvWarps) inverse_kernel(int n, const double *L, const double *Lt,
-                                                                  const double *rdiag, double *inv, const int *info)
+template <typename T>
+__global__ void __launch_bounds__(32 * kInvWarps) inverse_kernel(int n, const T *L, const T *Lt, const T *rdiag,
+                                                                  T *inv, const int *info)
 {
-    extern __shared__ double ys[];
+    extern __shared__ __align__(16) unsigned char inv_smem[];
     if (*info) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int j = blockIdx.x * (int)(blockDim.x >> 5) + w;
     if (j >= n) return;
-    double *y = ys + (size_t)w * n;
+    T *y = (T *)inv_smem + (size_t)w * n;
     const int m = n - j;                               // entries j .. n-1, local index k - j
-    for (int t = lane; t < m; t += 32) y[t] = (t == 0) ? 1.0 : 0.0;
+    for (int t = lane; t < m; t += 32) y[t] = (t == 0) ? T(1) : T(0);
     __syncwarp();
-    // forward: L y = e_j
-    for (int t = 0; t < m; ++t) {
+    for (int t = 0; t < m; ++t) {                      // forward: L y = e_j
         const int i = j + t;
-        double yi = 0.0;
+        T yi = T(0);
         if ((t & 31) == lane) {
             yi = y[t] * rdiag[i];
             y[t] = yi;
         }
         yi = __shfl_sync(0xffffffffu, yi, t & 31);
-        const double *lrow = Lt + (size_t)i * n;       // row i of L^T: L_ki for k > i
+        const T *lrow = Lt + (size_t)i * n;            // row i of L^T: L_ki for k > i
         for (int u = t + 1 + ((lane - t - 1) & 31); u < m; u += 32) y[u] -= lrow[j + u] * yi;
     }
-    // backward: L^T x = y, rows n-1 down to j
-    for (int t = m - 1; t >= 0; --t) {
+    for (int t = m - 1; t >= 0; --t) {                 // backward: L^T x = y, rows n-1 .. j
         const int i = j + t;
-        double xi = 0.0;
+        T xi = T(0);
         if ((t & 31) == lane) {
             xi = y[t] * rdiag[i];
             y[t] = xi;
         }
         xi = __shfl_sync(0xffffffffu, xi, t & 31);
-        const double *lrow = L + (size_t)i * n;        // row i of L: L_ik for k < i
+        const T *lrow = L + (size_t)i * n;             // row i of L: L_ik for k < i
         for (int u = lane; u < t; u += 32) y[u] -= lrow[j + u] * xi;
     }
     __syncwarp();
@@ -181,40 +198,148 @@ __global__ void __launch_bounds__(32 * kInvWarps) inverse_kernel(int n, const do
     }
 }
 
-cudaError_t coarse_inverse(const DevCsr &A, double *work, double *inv, int *info_dev, cudaStream_t s)
+// ------------------------------------------------------------------------------------ refinement
+// Newton-Schulz state (device): [0] E of the previous step, [1] 1 once converged, [2] E of this
+// step (as the bits of a non-negative double, for atomicMax).
+struct NewtonState {
+    double e_prev;
+    int done, last;         // last: this step's update is the final one
+    unsigned long long e_bits;
+};
+
+// C = P Q (n x n, FP64), one output per thread, 32 x 32 tiles staged in shared memory.
+// MODE 0: C = P Q and state->e_bits = max |I - C| (the residual of X = Q against P = A);
+// MODE 1: C = 2 X - X R with X = P, R = Q (the Newton update), or C = X once converged.
+template <int MODE>
+__global__ void __launch_bounds__(kGT * kGT) newton_gemm_kernel(int n, const double *P, const double *Q, double *C,
+                                                                 NewtonState *state)
+{
+    __shared__ double Ps[kGT][kGT + 1], Qs[kGT][kGT + 1];
+    const int done = state->done || (MODE == 0 && state->last);
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = blockIdx.y * kGT + ty, col = blockIdx.x * kGT + tx;
+    if (done) {
+        if (MODE == 1 && row < n && col < n) C[(size_t)row * n + col] = P[(size_t)row * n + col];
+        return;
+    }
+    double acc = 0.0;
+    for (int k0 = 0; k0 < n; k0 += kGT) {
+        Ps[ty][tx] = (row < n && k0 + tx < n) ? P[(size_t)row * n + k0 + tx] : 0.0;
+        Qs[ty][tx] = (k0 + ty < n && col < n) ? Q[(size_t)(k0 + ty) * n + col] : 0.0;
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kGT; ++k) acc += Ps[ty][k] * Qs[k][tx];
+        __syncthreads();
+    }
+    if (row >= n || col >= n) return;
+    if (MODE == 0) {
+        C[(size_t)row * n + col] = acc;
+        const double e = fabs((row == col ? 1.0 : 0.0) - acc);
+        // non-negative doubles order as their bit patterns
+        atomicMax(&state->e_bits, (unsigned long long)__double_as_longlong(e));
+    } else {
+        C[(size_t)row * n + col] = 2.0 * P[(size_t)row * n + col] - acc;
+    }
+}
+
+// after a residual with error E: E < 1e-10 -> this update is the last (its error, about E^2,
+// is at rounding level); E >= 1 or E no longer halving -> stop without it (a step after the
+// last update only marks the end)
+__global__ void newton_check_kernel(NewtonState *state)
+{
+    if (state->done) return;
+    if (state->last) {
+        state->done = 1;
+        return;
+    }
+    const double e = __longlong_as_double((long long)state->e_bits);
+    if (e < 1e-10) state->last = 1;
+    else if (!(e < 1.0) || !(e < 0.5 * state->e_prev)) state->done = 1;
+    state->e_prev = e;
+    state->e_bits = 0ULL;
+}
+
+template <typename T>
+cudaError_t factor_and_invert(int n, T *a, T *lt, T *rdiag, T *inv, int *info, cudaStream_t s)
 {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
+        attr = cudaFuncSetAttribute(inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kInvSmem);
     });
     AMG_CUDA_TRY(attr);
-    const int n = A.n;
-    AMG_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
-    if (n == 0) return cudaSuccess;
-    // columns per block: as many as the shared-memory cap holds, at most kInvWarps
-    const int warps = (int)std::min<size_t>(kInvWarps, (size_t)kInvSmem / ((size_t)n * sizeof(double)));
+    const int warps = (int)std::min<size_t>(kInvWarps, (size_t)kInvSmem / ((size_t)n * sizeof(T)));
     if (warps < 1) return cudaErrorInvalidValue;
-    double *lt = work + (size_t)n * n, *rdiag = lt + (size_t)n * n;
-    AMG_CUDA_TRY(cudaMemsetAsync(work, 0, sizeof(double) * (size_t)n * n, s));
-    dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, work); note_launch();
-    AMG_CUDA_TRY(cudaGetLastError());
     for (int j0 = 0; j0 < n; j0 += kPanel) {
         const int b = min(kPanel, n - j0);
         const int rows_below = n - j0 - b;
         const int pblocks = rows_below > 0 ? (rows_below + kPanel - 1) / kPanel : 1;
-        panel_kernel<<<pblocks, kPanel, 0, s>>>(n, j0, work, info_dev); note_launch();
+        panel_kernel<T><<<pblocks, kPanel, 0, s>>>(n, j0, a, info); note_launch();
         if (rows_below > 0) {
             int tiles = (rows_below + 31) / 32;
-            trailing_kernel<<<dim3(tiles, tiles), 256, 0, s>>>(n, j0, work, info_dev); note_launch();
+            trailing_kernel<T><<<dim3(tiles, tiles), 256, 0, s>>>(n, j0, a, info); note_launch();
         }
         AMG_CUDA_TRY(cudaGetLastError());
     }
     const int tb = (n + 31) / 32;
-    transpose_lower_kernel<<<dim3(tb, tb), 256, 0, s>>>(n, work, lt, rdiag, info_dev); note_launch();
-    const size_t smem = (size_t)warps * n * sizeof(double);
-    inverse_kernel<<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(n, work, lt, rdiag, inv, info_dev); note_launch();
+    transpose_lower_kernel<T><<<dim3(tb, tb), 256, 0, s>>>(n, a, lt, rdiag, info); note_launch();
+    const size_t smem = (size_t)warps * n * sizeof(T);
+    inverse_kernel<T><<<(n + warps - 1) / warps, 32 * warps, smem, s>>>(n, a, lt, rdiag, inv, info); note_launch();
     return cudaGetLastError();
+}
+
+size_t coarse_work_bytes(int n)
+{
+    const size_t nn = (size_t)n * n;
+    return sizeof(double) * (4 * nn + n + 16) + sizeof(float) * (3 * nn + n + 16) + sizeof(NewtonState) + 256;
+}
+
+cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info_dev, cudaStream_t s)
+{
+    const int n = A.n;
+    AMG_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+    if (n == 0) return cudaSuccess;
+    const size_t nn = (size_t)n * n;
+    double *Ad = (double *)work_v, *X = Ad + nn, *Y = X + nn, *R = Y + nn, *rd = R + nn;
+    float *Af = (float *)(rd + n + 16), *Ltf = Af + nn, *rdf = Ltf + nn;
+    NewtonState *st = (NewtonState *)(((uintptr_t)(rdf + n + 16) + 15) & ~(uintptr_t)15);
+    const int cgrid = (int)std::min<size_t>((nn + 255) / 256, 4096);
+    AMG_CUDA_TRY(cudaMemsetAsync(Ad, 0, sizeof(double) * nn, s));
+    dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
+    convert_dense_kernel<double, float><<<cgrid, 256, 0, s>>>(nn, Ad, Af); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    // stage 1: FP32 factor and inverse (X0 in Y's memory, as floats)
+    float *Xf = (float *)Y;
+    AMG_CUDA_TRY(factor_and_invert<float>(n, Af, Ltf, rdf, Xf, info_dev, s));
+    int info = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    bool refined = false;
+    if (info == 0) {
+        // stage 2: Newton-Schulz in FP64 from X0
+        convert_dense_kernel<float, double><<<cgrid, 256, 0, s>>>(nn, Xf, X); note_launch();
+        NewtonState init{1e300, 0, 0, 0ULL};   // e_prev, done, last, e_bits
+        AMG_CUDA_TRY(cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+        const dim3 blk(kGT, kGT), grd((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
+        double *cur = X, *nxt = Y;
+        for (int k = 0; k < kNewtonSteps; ++k) {
+            newton_gemm_kernel<0><<<grd, blk, 0, s>>>(n, Ad, cur, R, st); note_launch();
+            newton_check_kernel<<<1, 1, 0, s>>>(st); note_launch();
+            newton_gemm_kernel<1><<<grd, blk, 0, s>>>(n, cur, R, nxt, st); note_launch();
+            std::swap(cur, nxt);
+        }
+        AMG_CUDA_TRY(cudaGetLastError());
+        NewtonState fin{};
+        AMG_CUDA_TRY(cudaMemcpyAsync(&fin, st, sizeof fin, cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaMemcpyAsync(inv, cur, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        // e_prev: the error of the last iterate checked; the one returned is at least as good
+        refined = fin.e_prev < 1e-6;
+    }
+    if (refined) return cudaSuccess;
+    // the direct FP64 path
+    AMG_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
+    return factor_and_invert<double>(n, Ad, X, rd, inv, info_dev, s);
 }
 
 }  // namespace amgk

@@ -179,6 +179,29 @@ def test_single_level_one_iteration(amg):
     amg.amg_free(h)
 
 
+@pytest.mark.parametrize("decades,N", [(2.0, 8), (12.0, 7)])
+def test_coarse_inverse_single_level(amg, decades, N):
+    # the whole matrix is the coarsest level: one PCG step with its dense inverse solves the
+    # system.  Moderate contrast takes the FP32 factorisation refined by Newton-Schulz in FP64;
+    # 10^12 contrast leaves FP32 without a usable factor and takes the direct FP64 path.
+    A = P.random_coefficient_cube(N, 5, decades)
+    b = P.rhs_uniform(A.n, 1)
+    h, st = gpu_setup(A, max_coarse=1000)
+    assert st == 0 and amg.amg_num_levels(h) == 1
+    x = np.zeros(A.n)
+    info = amg.amg_solve(h, b, x, 1e-10)
+    amg.amg_free(h)
+    assert info.status == 0 and info.relres_true <= 1e-10, (info.status, info.relres_true)
+    if decades <= 2.0:
+        # well conditioned: the inverse is exact to rounding, one step
+        xr = np.linalg.solve(A.to_dense(), b)
+        assert info.iters == 1 and np.linalg.norm(x - xr) / np.linalg.norm(xr) <= 1e-13
+    else:
+        # condition number ~1e14: the explicit inverse leaves a residual of order cond * eps,
+        # which the outer PCG removes in a few steps
+        assert info.iters <= 6, info.iters
+
+
 def test_zero_rhs_and_empty_matrix(amg):
     A = P.laplace_cube(10)
     h, st = gpu_setup(A, max_coarse=20)
