@@ -35,8 +35,8 @@ namespace amgk {
 constexpr int kPanel = 32;
 constexpr int kInvWarps = 4;                 // columns per block of the inverse (at most)
 constexpr int kInvSmem = 200 * 1024;         // dynamic shared memory cap of the inverse kernel
-constexpr int kNewtonSteps = 6;              // refinement steps at most
-constexpr int kGT = 32;                      // product tile
+constexpr int kNewtonSteps = 4;              // refinement steps at most (E0 up to ~1e-2 converges)
+constexpr int kGT = 16;                      // product tile: many blocks, so that every SM's FP64 units work
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
 {
@@ -171,25 +171,31 @@ __global__ void __launch_bounds__(32 * kInvWarps) inverse_kernel(int n, const T 
     __syncwarp();
     for (int t = 0; t < m; ++t) {                      // forward: L y = e_j
         const int i = j + t;
+        const T *lrow = Lt + (size_t)i * n;            // row i of L^T: L_ki for k > i
+        const int u0 = t + 1 + ((lane - t - 1) & 31);
+        // the row's first entry of this lane is requested before the chain's shuffle
+        const T l0 = u0 < m ? lrow[j + u0] : T(0);
         T yi = T(0);
         if ((t & 31) == lane) {
             yi = y[t] * rdiag[i];
             y[t] = yi;
         }
         yi = __shfl_sync(0xffffffffu, yi, t & 31);
-        const T *lrow = Lt + (size_t)i * n;            // row i of L^T: L_ki for k > i
-        for (int u = t + 1 + ((lane - t - 1) & 31); u < m; u += 32) y[u] -= lrow[j + u] * yi;
+        if (u0 < m) y[u0] -= l0 * yi;
+        for (int u = u0 + 32; u < m; u += 32) y[u] -= lrow[j + u] * yi;
     }
     for (int t = m - 1; t >= 0; --t) {                 // backward: L^T x = y, rows n-1 .. j
         const int i = j + t;
+        const T *lrow = L + (size_t)i * n;             // row i of L: L_ik for k < i
+        const T l0 = lane < t ? lrow[j + lane] : T(0);
         T xi = T(0);
         if ((t & 31) == lane) {
             xi = y[t] * rdiag[i];
             y[t] = xi;
         }
         xi = __shfl_sync(0xffffffffu, xi, t & 31);
-        const T *lrow = L + (size_t)i * n;             // row i of L: L_ik for k < i
-        for (int u = lane; u < t; u += 32) y[u] -= lrow[j + u] * xi;
+        if (lane < t) y[lane] -= l0 * xi;
+        for (int u = lane + 32; u < t; u += 32) y[u] -= lrow[j + u] * xi;
     }
     __syncwarp();
     for (int t = lane; t < m; t += 32) {
