@@ -365,6 +365,55 @@ def run_batched(args, amg, torch):
     return out
 
 
+def run_multi(args, amg, torch):
+    """§8(f) row 4: eight right-hand sides of the benchmark's stretched64 system (1Norm) solved
+    at once by amg_solve_multi against the same eight solved one after another by amg_solve on
+    the same hierarchy; matrix, right-hand sides and solutions resident on the device; solve
+    phase only (one setup shared), FP64 and mixed.  Host wall time between device
+    synchronisations; L2 flushed before each timed repetition."""
+    import numpy as np
+    from paper_2103_10476_gb300 import problems as P
+    A, b, _ = P.workload_stretched64()
+    k = 8
+    rp, ci, v = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A.row_ptr, A.col, A.val))
+    B = torch.from_numpy(np.stack([P.rhs_uniform(A.n, 200 + j) for j in range(k)])).cuda()
+    X = torch.zeros_like(B)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"stretched64, 1Norm, {k} right-hand sides (SplitMix64 seeds 200..207), one hierarchy; "
+                       "solve phase only, device-resident", "rhs": k}
+    for prec_name, prec in (("fp64", amg.AMG_FP64), ("mixed", amg.AMG_MIXED)):
+        p = amg.amg_params_default(theta=0.02, variants=1, precision=prec, cuda_stream=stream.cuda_stream)
+        h = amg.amg_setup(amg.csr_arg(A.n, rp, ci, v), None, p)
+        amg.amg_solve_multi(h, B, X, TOL)          # warm-up: work vectors, graphs
+        for j in range(k):
+            amg.amg_solve(h, B[j], X[j], TOL)
+        reps = 3
+        t_multi = t_single = 0.0
+        iters_multi = iters_single = None
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, infos = amg.amg_solve_multi(h, B, X, TOL)
+            torch.cuda.synchronize()
+            t_multi += time.perf_counter() - t0
+            iters_multi = [i.iters for i in infos]
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            its = []
+            for j in range(k):
+                its.append(amg.amg_solve(h, B[j], X[j], TOL).iters)
+            torch.cuda.synchronize()
+            t_single += time.perf_counter() - t0
+            iters_single = its
+        amg.amg_free(h)
+        out[prec_name] = {"multi_solves_per_s": k * reps / t_multi, "single_solves_per_s": k * reps / t_single,
+                          "speedup": t_single / t_multi, "iters_multi": iters_multi, "iters_single": iters_single}
+    return out
+
+
 COMBOS = [(m, "+".join(n for b, n in ((1, "1Norm"), (2, "OffLmp"), (8, "Cnstrnt"), (4, "Sprsfy")) if m & b)
            or "traditional") for m in range(16)]
 
@@ -526,6 +575,8 @@ def main():
     ap.add_argument("--study-ne", type=int, default=60, help="elements per direction of the study's cube")
     ap.add_argument("--study-seeds", type=int, default=3, help="meshes (seeds) of the study")
     ap.add_argument("--study-only", action="store_true", help="only the study line, printed alone")
+    ap.add_argument("--no-multi", action="store_true", help="skip the eight-right-hand-side line")
+    ap.add_argument("--multi-only", action="store_true", help="only the eight-right-hand-side line, printed alone")
     ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -537,6 +588,12 @@ def main():
         return run_reference(args, world, rank)
     if args.once:
         return run_once(args)
+    if args.multi_only:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2103_10476_gb300 import amg
+        print(json.dumps(run_multi(args, amg, torch)), flush=True)
+        return 0
     if args.study_only:
         import torch
         torch.cuda.set_device(local)
@@ -672,6 +729,7 @@ def main():
 
     batched = None if args.no_batched else run_batched(args, amg, torch)
     study = None if args.no_study else run_study(args, amg, torch)
+    multi = None if args.no_multi else run_multi(args, amg, torch)
     serving = None if not args.serving else run_serving(args, amg, args.serve_seconds,
                                                         ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
 
@@ -716,6 +774,7 @@ def main():
         "mixed": other,
         "batched": batched,
         "study": study,
+        "multi": multi,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

@@ -135,6 +135,16 @@ amg_status_t amg_setup_coords(const amg_csr_t *A, const double *nullspace, const
  * Synchronises the stream before returning. */
 amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, amg_info_t *info);
 
+/* Several right-hand sides of one system at once (no counterpart in the paper): k (1..8)
+ * columns, column j of B and X at B + j n and X + j n (host or device).  Each column is
+ * solved as amg_solve would solve it alone (PCG with one V-cycle per iteration from x = 0,
+ * its own scalars and stopping test, tolerance tol, the same true-residual check); every
+ * sparse product reads the matrix once for all columns.  infos (k entries, may be NULL)
+ * receive each column's iterations, status and true residual.  Returns AMG_OK when every
+ * column converged, else AMG_ERR_NOT_CONVERGED.  Work vectors for up to 8 columns are
+ * allocated with the hierarchy on first use.  Synchronises the stream. */
+amg_status_t amg_solve_multi(amg_handle_t h, int k, const double *B, double *X, double tol, amg_info_t *infos);
+
 /* Releases every resource of the handle; NULL is accepted. */
 amg_status_t amg_free(amg_handle_t h);
 

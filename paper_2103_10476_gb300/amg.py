@@ -94,6 +94,7 @@ def _load():
         "amg_setup": (st, [C.POINTER(amg_csr_t), vp, C.POINTER(amg_params_t), C.POINTER(vp)]),
         "amg_setup_coords": (st, [C.POINTER(amg_csr_t), vp, vp, C.c_int, C.POINTER(amg_params_t), C.POINTER(vp)]),
         "amg_solve": (st, [vp, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
+        "amg_solve_multi": (st, [vp, C.c_int, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
         "amg_free": (st, [vp]),
         "amg_num_levels": (st, [vp, C.POINTER(C.c_int)]),
         "amg_setup_trace": (st, [vp, C.c_int, C.POINTER(C.c_double)]),
@@ -217,6 +218,19 @@ def amg_solve(h, b, x, tol: float) -> amg_info_t:
         _check(s, "amg_solve")
     info.status = s
     return info
+
+
+def amg_solve_multi(h, B, X, tol: float):
+    """k right-hand sides at once: B, X of shape (k, n) (numpy or torch, row j = column j of
+    the C call).  Returns (status, [amg_info_t] * k)."""
+    k = int(B.shape[0])
+    infos = (amg_info_t * max(1, k))()
+    pb, _ = _ptr(B)
+    px, _ = _ptr(X)
+    s = lib.amg_solve_multi(h, k, pb, px, tol, infos)
+    if s not in (AMG_OK, AMG_ERR_NOT_CONVERGED):
+        _check(s, "amg_solve_multi")
+    return s, [infos[j] for j in range(k)]
 
 
 def amg_free(h):

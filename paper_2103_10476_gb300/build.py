@@ -22,6 +22,7 @@ SOURCES = {
     "setup.cu": ["--fmad=false"],
     "spgemm.cu": ["--fmad=false"],
     "coarse.cu": [],
+    "multi.cu": [],
     "solve.cu": [],
     "api.cu": [],
     "batch.cu": [],

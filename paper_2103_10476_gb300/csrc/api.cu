@@ -674,6 +674,7 @@ amg_status_t amg_free(amg_handle_t h)
         profile_release(h->gprof[k]);
     }
     if (h->cap) cudaStreamDestroy(h->cap);
+    multi_release(h);
     release_all(h);
     if (h->rr_host) cudaFreeHost(h->rr_host);
     delete h;

@@ -9,6 +9,8 @@
 
 namespace amgk {
 
+struct MultiWork;           // work vectors of amg_solve_multi (multi.cu)
+
 struct Level {
     DevCsr A;                 // level operator
     double *diag = nullptr;   // diag(A)
@@ -65,6 +67,7 @@ struct amg_hierarchy {
     double phase_t = 0.0;                     // end of the last traced phase
     int64_t fine_nnz = 0;
     size_t bytes = 0;   // device memory held by the handle
+    amgk::MultiWork *multi = nullptr;   // several right-hand sides at once (allocated on first use)
 };
 
 
@@ -80,4 +83,6 @@ int hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail)
 // with params.trace: synchronise the handle's stream and book the time since the last mark to
 // (level, phase)
 void trace_mark(amg_hierarchy *h, int level, int phase);
+// releases the host side of amg_solve_multi's work vectors (their device memory is in allocs)
+void multi_release(amg_hierarchy *h);
 }  // namespace amgk
