@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hierarchy.cuh"
@@ -149,7 +150,15 @@ cudaError_t spmm(const SpmvPlan &pl, int n, const int *rp, const int *ci, const 
     if (n == 0) return cudaSuccess;
     const int smem = tile_bytes<T>(pl.cap);
     auto go = [&](auto kern, int lpr) -> cudaError_t {
-        AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T>(kMaxTileM)));
+        // the shared-memory limit is raised once per instantiation (no API call inside a capture)
+        static std::once_flag once[5];
+        static cudaError_t cfg[5];
+        const int slot = lpr == 2 ? 0 : lpr == 4 ? 1 : lpr == 8 ? 2 : lpr == 16 ? 3 : 4;
+        std::call_once(once[slot], [&] {
+            cfg[slot] = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             tile_bytes<T>(kMaxTileM));
+        });
+        AMG_CUDA_TRY(cfg[slot]);
         const int blocks = (n + kMT / lpr - 1) / (kMT / lpr);
         kern<<<blocks, kMT, smem, s>>>(n, rp, ci, v, x, y, f, invd, d, c1, c2, pl.cap, partial, spmv_error_flag());
         note_launch();
@@ -376,6 +385,9 @@ struct MultiWork {
     int *mask = nullptr;
     double *host = nullptr;      // pinned: rr (K x kReduceBlocks), then per-column scalars
     int nparts = 0;              // partial slots per column of the products
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // one iteration (z parity in mixed precision)
+    long long gkernels[2] = {0, 0};
+    bool graph_failed = false;
 };
 
 namespace {
@@ -497,6 +509,69 @@ cudaError_t mvcycle(amg_hierarchy *h, MultiWork &w, const double *r, double *z, 
     return cudaGetLastError();
 }
 
+// q = A p with the per-column p . q, then x, r and the r . r partials (copied to the host)
+template <int K>
+cudaError_t mhead(amg_hierarchy *h, MultiWork &w, cudaStream_t s)
+{
+    const Level &l0 = h->lev[0];
+    const int n = l0.A.n;
+    AMG_CUDA_TRY((spmm<double, MM_DOT, K>(h->plan0, n, l0.A.rp, l0.A.ci, l0.A.v, w.p, w.q, nullptr, nullptr, nullptr,
+                                          0.0, 0.0, w.partial, s)));
+    mxr_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.xs, w.rs, w.p, w.q, w.sc, w.partial,
+                                                spmv_block_count(n, h->plan0), w.rr); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    return cudaMemcpyAsync(w.host, w.rr, sizeof(double) * (size_t)K * kReduceBlocks, cudaMemcpyDeviceToHost, s);
+}
+
+// z = M r, the per-column r . z (and r . z_prev), p = z + beta p
+template <int K>
+cudaError_t mtail(amg_hierarchy *h, MultiWork &w, int parity, cudaStream_t s)
+{
+    const int n = h->lev[0].A.n;
+    const bool flexible = h->ctx.mixed != 0;
+    double *z = w.zb[parity], *zp = flexible ? w.zb[1 - parity] : nullptr;
+    AMG_CUDA_TRY(mvcycle<K>(h, w, w.rs, z, s));
+    mrz_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.rs, z, zp, w.pa, w.pb); note_launch();
+    mp_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.p, z, w.sc, w.pa, w.pb, kReduceBlocks, zp ? 1 : 0); note_launch();
+    return cudaGetLastError();
+}
+
+// one iteration (tail, then head) as a CUDA graph, captured on first use
+template <int K>
+cudaGraphExec_t mgraph(amg_hierarchy *h, MultiWork &w, int parity)
+{
+    if (w.graph_failed || !h->cap) return nullptr;
+    if (w.gexec[parity]) return w.gexec[parity];
+    cudaGraph_t g = nullptr;
+    const long long before = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = mtail<K>(h, w, parity, h->cap);
+        cudaError_t e2 = e1 == cudaSuccess ? mhead<K>(h, w, h->cap) : e1;
+        e = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&w.gexec[parity], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w.graph_failed = true;      // iterations run eagerly from now on
+        w.gexec[parity] = nullptr;
+        return nullptr;
+    }
+    w.gkernels[parity] = launch_count() - before;
+    note_launches(-w.gkernels[parity]);
+    return w.gexec[parity];
+}
+
+void drop_multi_graphs(MultiWork &w)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (w.gexec[k]) cudaGraphExecDestroy(w.gexec[k]);
+        w.gexec[k] = nullptr;
+    }
+}
+
 #define MK(expr)                                                           \
     do {                                                                   \
         cudaError_t _e = (expr);                                           \
@@ -530,6 +605,7 @@ amg_status_t solve_k(amg_hierarchy *h, int k, const double *B, double *X, double
         if (w.K != 0) {
             // another width was used before: start over with fresh vectors (the old ones stay
             // with the hierarchy until it is freed)
+            drop_multi_graphs(w);
             if (w.host) cudaFreeHost(w.host);
             w = MultiWork();
         }
@@ -584,18 +660,8 @@ amg_status_t solve_k(amg_hierarchy *h, int k, const double *B, double *X, double
         if (flexible) MK(cudaMemsetAsync(w.zb[1], 0, sizeof(double) * nk, s));
         MK(cudaGetLastError());
     }
-    const int nbk = spmv_block_count(n, h->plan0);
-    auto head = [&]() -> amg_status_t {
-        MK((spmm<double, MM_DOT, K>(h->plan0, n, l0.A.rp, l0.A.ci, l0.A.v, w.p, w.q, nullptr, nullptr, nullptr, 0.0,
-                                    0.0, w.partial, s)));
-        mxr_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.xs, w.rs, w.p, w.q, w.sc, w.partial, nbk, w.rr); note_launch();
-        MK(cudaGetLastError());
-        MK(cudaMemcpyAsync(w.host, w.rr, sizeof(double) * (size_t)K * kReduceBlocks, cudaMemcpyDeviceToHost, s));
-        return AMG_OK;
-    };
     if (live > 0 && h->p.max_iter > 0) {
-        amg_status_t st = head();
-        if (st != AMG_OK) return st;
+        MK(mhead<K>(h, w, s));
         ++it;
     }
     while (live > 0 && it > 0) {
@@ -637,13 +703,14 @@ amg_status_t solve_k(amg_hierarchy *h, int k, const double *B, double *X, double
         }
         if (live == 0 || it >= h->p.max_iter) break;
         const int parity = flexible ? (it & 1) : 0;
-        double *z = w.zb[parity], *zp = flexible ? w.zb[1 - parity] : nullptr;
-        MK(mvcycle<K>(h, w, w.rs, z, s));
-        mrz_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.rs, z, zp, w.pa, w.pb); note_launch();
-        mp_kernel<K><<<kReduceBlocks, kMT, 0, s>>>(n, w.p, z, w.sc, w.pa, w.pb, kReduceBlocks, zp ? 1 : 0); note_launch();
-        MK(cudaGetLastError());
-        amg_status_t st = head();
-        if (st != AMG_OK) return st;
+        cudaGraphExec_t gx = mgraph<K>(h, w, parity);
+        if (gx) {
+            MK(cudaGraphLaunch(gx, s));
+            note_launches(w.gkernels[parity]);
+        } else {
+            MK(mtail<K>(h, w, parity, s));
+            MK(mhead<K>(h, w, s));
+        }
         ++it;
     }
     for (int c = 0; c < K; ++c)
@@ -689,6 +756,7 @@ amg_status_t solve_k(amg_hierarchy *h, int k, const double *B, double *X, double
 void multi_release(amg_hierarchy *h)
 {
     if (!h->multi) return;
+    drop_multi_graphs(*h->multi);
     if (h->multi->host) cudaFreeHost(h->multi->host);
     delete h->multi;
     h->multi = nullptr;
