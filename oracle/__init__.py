@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("pt_unit", C.c_int),
                 ("onenorm_power", C.c_int), ("seed", C.c_uint64), ("lambda_override", C.c_double),
-                ("max_iter", C.c_int), ("strength", C.c_int)]
+                ("max_iter", C.c_int), ("strength", C.c_int), ("krylov", C.c_int), ("restart", C.c_int)]
 
 
 class Info(C.Structure):
@@ -86,6 +86,9 @@ def lib():
         L.oc_prolongator_only.argtypes = [C.c_int64, vp, vp, vp, vp, C.POINTER(Params), C.POINTER(vp)]
         L.oc_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(Info)]
         L.oc_pcg_plain.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.POINTER(Info)]
+        L.oc_gmres_plain.argtypes = [C.c_int64, vp, vp, vp, vp, vp, C.c_double, C.c_int, C.c_int, C.POINTER(Info)]
+        L.oc_lu.argtypes = [C.c_int64, vp, vp]
+        L.oc_lu_solve.argtypes = [C.c_int64, vp, vp, vp, vp]
         L.oc_vcycle.argtypes = [vp, vp, vp]
         L.oc_free.argtypes = [vp]
         L.oc_nlevels.argtypes = [vp]
@@ -263,6 +266,27 @@ def pcg_plain(A, b, tol: float, max_iter: int):
     info = Info()
     lib().oc_pcg_plain(A.n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, max_iter, C.byref(info))
     return x[:A.n], info
+
+
+def gmres_plain(A, b, tol: float, restart: int = 30, max_iter: int = 1000):
+    rp, ci, v = _arrs(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(max(A.n, 1))
+    info = Info()
+    lib().oc_gmres_plain(A.n, _p(rp), _p(ci), _p(v), _p(b), _p(x), tol, restart, max_iter, C.byref(info))
+    return x[:A.n], info
+
+
+def lu_solve(a, b):
+    """Dense LU with partial pivoting, then the solve: (x, status)."""
+    a = np.ascontiguousarray(a, dtype=np.float64).copy()
+    n = a.shape[0]
+    piv = np.zeros(max(n, 1), dtype=np.int64)
+    st = lib().oc_lu(n, _p(a), _p(piv))
+    x = np.zeros(max(n, 1))
+    if st == 0:
+        lib().oc_lu_solve(n, _p(a), _p(piv), _p(np.ascontiguousarray(b, dtype=np.float64)), _p(x))
+    return x[:n], int(st)
 
 
 # ---------------------------------------------------------------- the whole method

@@ -47,6 +47,8 @@ struct oc_hier {
     int prolongator_only; /* level 0 holds P but no coarser level was formed */
     struct oc_level lev[OC_MAX_LEVELS];
     double *chol;         /* dense lower Cholesky factor of the coarsest operator */
+    double *lu;           /* nonsymmetric operators: dense LU factors (unit lower L) instead */
+    int64_t *piv;         /* and the row exchanged with row k at step k */
     oc_params p;
 };
 
@@ -72,6 +74,8 @@ void oc_params_default(oc_params *p)
     p->lambda_override = 0.0;
     p->max_iter = 1000;
     p->strength = 0;
+    p->krylov = 0;
+    p->restart = 30;
 }
 
 static void csr_release(oc_csr *c)
@@ -742,6 +746,50 @@ int oc_cholesky(int64_t n, const double *a, double *l)
     return OC_OK;
 }
 
+/* Dense LU with partial pivoting, in place (row-major): at step k the row with the largest
+ * |a_ik|, i >= k (the lowest such index on ties), is exchanged with row k; then the
+ * multipliers a_ik / a_kk and the update of the trailing rows.  A zero pivot: singular. */
+int oc_lu(int64_t n, double *a, int64_t *piv)
+{
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t p = k;
+        for (int64_t i = k + 1; i < n; ++i)
+            if (fabs(a[i * n + k]) > fabs(a[p * n + k])) p = i;
+        piv[k] = p;
+        if (p != k)
+            for (int64_t j = 0; j < n; ++j) {
+                double t = a[k * n + j];
+                a[k * n + j] = a[p * n + j];
+                a[p * n + j] = t;
+            }
+        double d = a[k * n + k];
+        if (d == 0.0) return OC_ERR_COARSE_NOT_SPD;
+        for (int64_t i = k + 1; i < n; ++i) {
+            double m = a[i * n + k] / d;
+            a[i * n + k] = m;
+            for (int64_t j = k + 1; j < n; ++j) a[i * n + j] = a[i * n + j] - m * a[k * n + j];
+        }
+    }
+    return OC_OK;
+}
+
+void oc_lu_solve(int64_t n, const double *lu, const int64_t *piv, const double *b, double *x)
+{
+    for (int64_t i = 0; i < n; ++i) x[i] = b[i];
+    for (int64_t k = 0; k < n; ++k)
+        if (piv[k] != k) { double t = x[k]; x[k] = x[piv[k]]; x[piv[k]] = t; }
+    for (int64_t i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int64_t k = 0; k < i; ++k) s = s - lu[i * n + k] * x[k];
+        x[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t k = i + 1; k < n; ++k) s = s - lu[i * n + k] * x[k];
+        x[i] = s / lu[i * n + i];
+    }
+}
+
 static void chol_solve(int64_t n, const double *l, const double *b, double *x)
 {
     for (int64_t i = 0; i < n; ++i) {
@@ -800,6 +848,22 @@ static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
         if (st) return st;
     } else {
         oc_strength(n, A->rp, A->ci, A->v, p->theta, lv->strong);
+    }
+    if (p->krylov == 1) {
+        /* Reading: for a nonsymmetric operator the connection i-j is strong when Eq. (7) holds
+         * for a_ij or for a_ji, so that the aggregation graph is undirected (symmetric
+         * operators give the same mask either way). */
+        uint8_t *own = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+        if (!own) return OC_ERR_OOM;
+        memcpy(own, lv->strong, (size_t)nnz);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e) {
+                int32_t j = A->ci[e];
+                if (j == i || own[e]) continue;
+                int64_t t = find_entry(A->rp, A->ci, j, (int32_t)i);
+                if (t >= 0 && own[t]) lv->strong[e] = 1;
+            }
+        free(own);
     }
     for (int64_t i = 0; i < n; ++i)
         for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
@@ -989,11 +1053,18 @@ int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
     int64_t nc = cl->A.n;
     if (nc > OC_MAX_DENSE) { oc_free(h); return OC_ERR_UNSUPPORTED; }
     double *dense = (double *)calloc((size_t)(nc * nc > 0 ? nc * nc : 1), sizeof(double));
-    h->chol = (double *)calloc((size_t)(nc * nc > 0 ? nc * nc : 1), sizeof(double));
     for (int64_t i = 0; i < nc; ++i)
         for (int64_t e = cl->A.rp[i]; e < cl->A.rp[i + 1]; ++e) dense[i * nc + cl->A.ci[e]] = cl->A.v[e];
-    st = oc_cholesky(nc, dense, h->chol);
-    free(dense);
+    if (p->krylov == 1) {
+        /* nonsymmetric: LU with partial pivoting */
+        h->lu = dense;
+        h->piv = (int64_t *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(int64_t));
+        st = h->piv ? oc_lu(nc, h->lu, h->piv) : OC_ERR_OOM;
+    } else {
+        h->chol = (double *)calloc((size_t)(nc * nc > 0 ? nc * nc : 1), sizeof(double));
+        st = oc_cholesky(nc, dense, h->chol);
+        free(dense);
+    }
     if (st) { oc_free(h); return st; }
     *out = h;
     return OC_OK;
@@ -1043,7 +1114,8 @@ static void vcycle_level(oc_hier *h, int L, const double *f, double *u)
     struct oc_level *lv = &h->lev[L];
     int64_t n = lv->A.n;
     if (L == h->nlev - 1) {
-        chol_solve(n, h->chol, f, u);
+        if (h->lu) oc_lu_solve(n, h->lu, h->piv, f, u);
+        else chol_solve(n, h->chol, f, u);
         return;
     }
     double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
@@ -1118,10 +1190,113 @@ done:
     return status;
 }
 
+/* Flexible GMRES(m) with right preconditioning (Saad, SIAM J. Sci. Comput. 14, 1993), from
+ * x = 0: per cycle r = b - A x, v_0 = r / |r|; per step z_j = M v_j (one V-cycle), w = A z_j,
+ * classical Gram-Schmidt against v_0..v_j done twice (h = V^T w, w -= V h, each product and
+ * sum in ascending index), v_{j+1} = w / |w|; Givens rotations keep the Hessenberg matrix
+ * triangular and |g_{j+1}| is the residual norm of the minimiser.  When |g_{j+1}| <= tol |b|,
+ * at the cycle's end or at the iteration limit: y from the triangular system, x += Z y, and
+ * the true residual decides (stop, or restart from x).  The iteration count is the number of
+ * products with A inside the Arnoldi steps.  h NULL: no preconditioner (z_j = v_j). */
+static int fgmres(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, oc_hier *h, const double *b,
+                  double *x, double tol, int m, int max_iter, oc_info *info)
+{
+    if (m < 1) m = 1;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    double *V = (double *)calloc(nn * (size_t)(m + 1), sizeof(double));
+    double *Z = (double *)calloc(nn * (size_t)m, sizeof(double));
+    double *w = (double *)malloc(nn * sizeof(double));
+    double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));   /* H[i * m + j] */
+    double *g = (double *)calloc((size_t)(m + 1), sizeof(double));
+    double *cs = (double *)calloc((size_t)m, sizeof(double)), *sn = (double *)calloc((size_t)m, sizeof(double));
+    double *hv = (double *)calloc((size_t)(m + 1), sizeof(double)), *y = (double *)calloc((size_t)m, sizeof(double));
+    memset(x, 0, nn * sizeof(double));
+    double nb = sqrt(dot(n, b, b));
+    int it = 0, status = OC_OK;
+    double relres = 0.0;
+    if (nb == 0.0) goto done;
+    status = OC_ERR_NOT_CONVERGED;
+    while (it < max_iter) {
+        spmv(n, rp, ci, v, x, w);
+        for (int64_t i = 0; i < n; ++i) w[i] = b[i] - w[i];
+        double beta = sqrt(dot(n, w, w));
+        if (beta / nb <= tol) { status = OC_OK; break; }
+        for (int64_t i = 0; i < n; ++i) V[i] = w[i] / beta;
+        memset(g, 0, (size_t)(m + 1) * sizeof(double));
+        g[0] = beta;
+        int j = 0, stop = 0;
+        for (; j < m && it < max_iter; ++j) {
+            double *vj = V + (size_t)j * nn, *zj = Z + (size_t)j * nn;
+            if (h) oc_vcycle(h, vj, zj); else memcpy(zj, vj, nn * sizeof(double));
+            spmv(n, rp, ci, v, zj, w);
+            ++it;
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = 0.0;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i = 0; i <= j; ++i) hv[i] = dot(n, V + (size_t)i * nn, w);
+                for (int64_t e = 0; e < n; ++e) {
+                    double t = w[e];
+                    for (int i = 0; i <= j; ++i) t = t - hv[i] * V[(size_t)i * nn + e];
+                    w[e] = t;
+                }
+                for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = H[(size_t)i * m + j] + hv[i];
+            }
+            double hn = sqrt(dot(n, w, w));
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0)
+                for (int64_t e = 0; e < n; ++e) V[(size_t)(j + 1) * nn + e] = w[e] / hn;
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+            double r = sqrt(a * a + c * c);
+            cs[j] = a / r;
+            sn[j] = c / r;
+            H[(size_t)j * m + j] = r;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            if (fabs(g[j + 1]) / nb <= tol || hn == 0.0) { stop = 1; ++j; break; }
+        }
+        /* y = H(0:j, 0:j)^-1 g(0:j); x += Z y */
+        for (int i = j - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int k = i + 1; k < j; ++k) s = s - H[(size_t)i * m + k] * y[k];
+            y[i] = s / H[(size_t)i * m + i];
+        }
+        for (int64_t e = 0; e < n; ++e) {
+            double t = x[e];
+            for (int k = 0; k < j; ++k) t = t + y[k] * Z[(size_t)k * nn + e];
+            x[e] = t;
+        }
+        if (stop || it >= max_iter) {
+            spmv(n, rp, ci, v, x, w);
+            for (int64_t i = 0; i < n; ++i) w[i] = b[i] - w[i];
+            if (sqrt(dot(n, w, w)) / nb <= tol) { status = OC_OK; break; }
+        }
+    }
+done:
+    spmv(n, rp, ci, v, x, w);
+    for (int64_t i = 0; i < n; ++i) w[i] = b[i] - w[i];
+    relres = nb == 0.0 ? 0.0 : sqrt(dot(n, w, w)) / nb;
+    if (info) { info->iters = it; info->status = status; info->relres_true = relres; }
+    free(V); free(Z); free(w); free(H); free(g); free(cs); free(sn); free(hv); free(y);
+    return status;
+}
+
+int oc_gmres_plain(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                   double tol, int restart, int max_iter, oc_info *info)
+{
+    return fgmres(n, rp, ci, v, NULL, b, x, tol, restart, max_iter, info);
+}
+
 int oc_solve(oc_hier *h, const double *b, double *x, double tol, oc_info *info)
 {
     oc_csr *A = &h->lev[0].A;
-    int st = pcg(A->n, A->rp, A->ci, A->v, h, b, x, tol, h->p.max_iter, info);
+    int st = h->p.krylov == 1
+                 ? fgmres(A->n, A->rp, A->ci, A->v, h, b, x, tol, h->p.restart, h->p.max_iter, info)
+                 : pcg(A->n, A->rp, A->ci, A->v, h, b, x, tol, h->p.max_iter, info);
     if (info) {
         info->levels = h->nlev;
         double tot = 0.0;
@@ -1169,6 +1344,8 @@ void oc_free(oc_hier *h)
         free(lv->B); free(lv->nrm); free(lv->Dsm); free(lv->cflag); free(lv->invdiag); free(lv->coords);
     }
     free(h->chol);
+    free(h->lu);
+    free(h->piv);
     free(h);
 }
 

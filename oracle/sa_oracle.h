@@ -55,6 +55,8 @@ typedef struct {
     double lambda_override;/* > 0: use as the prolongator-smoothing eigenvalue on every level */
     int max_iter;          /* PCG iteration limit */
     int strength;          /* 0: Eq. (7) on the matrix; 1: Eq. (7) on the distance Laplacian (§3.1) */
+    int krylov;            /* 0: PCG (symmetric operators); 1: flexible GMRES (nonsymmetric operators) */
+    int restart;           /* GMRES restart length */
 } oc_params;
 
 typedef struct {
@@ -89,6 +91,10 @@ double oc_power_lambda(int64_t n, const int64_t *rp, const int32_t *ci, const do
                        int sweeps, uint64_t stream_seed);
 uint64_t oc_power_stream_seed(uint64_t seed, int level, int purpose);
 int oc_cholesky(int64_t n, const double *a, double *l);
+int oc_lu(int64_t n, double *a, int64_t *piv);
+void oc_lu_solve(int64_t n, const double *lu, const int64_t *piv, const double *b, double *x);
+int oc_gmres_plain(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
+                   double tol, int restart, int max_iter, oc_info *info);
 void oc_csr_free(oc_csr *c);
 
 /* the whole method */

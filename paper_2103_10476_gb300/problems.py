@@ -272,9 +272,13 @@ VARIANT_BITS = {"1norm": 1, "offlmp": 2, "sprsfy": 4, "cnstrnt": 8}
 _GAUSS = 1.0 / np.sqrt(3.0)
 
 
-def _hex_element_matrices(Xe: np.ndarray, coef: np.ndarray, reaction: np.ndarray | None) -> np.ndarray:
-    """Xe: (E, 8, 3) node coordinates; coef, reaction: (E,).  Returns (E, 8, 8)."""
+def _hex_element_matrices(Xe: np.ndarray, coef: np.ndarray, reaction: np.ndarray | None,
+                          velocity=None) -> np.ndarray:
+    """Xe: (E, 8, 3) node coordinates; coef, reaction: (E,); velocity: constant 3-vector of the
+    convection term sum over Gauss points of N_a (v . grad N_b) (nonsymmetric), or None.
+    Returns (E, 8, 8)."""
     E = Xe.shape[0]
+    vel = None if velocity is None else np.asarray(velocity, dtype=np.float64)
     sgn = np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1] for a in range(8)],
                    dtype=np.float64)
     K = np.zeros((E, 8, 8))
@@ -319,11 +323,14 @@ def _hex_element_matrices(Xe: np.ndarray, coef: np.ndarray, reaction: np.ndarray
                           + G[:, :, None, 2] * G[:, None, :, 2])
                 if M is not None:
                     M += (det * reaction)[:, None, None] * (N[:, None] * N[None, :])[None]
+                if vel is not None:
+                    vg = G[:, :, 0] * vel[0] + G[:, :, 1] * vel[1] + G[:, :, 2] * vel[2]    # (E, 8): v . grad N_b
+                    K += det[:, None, None] * (N[None, :, None] * vg[:, None, :])
     return K if M is None else K + M
 
 
 def hex_q1_matrix(X: np.ndarray, Y: np.ndarray, Z: np.ndarray, coef=None, reaction=None,
-                  dirichlet: bool = True) -> CSR:
+                  dirichlet: bool = True, velocity=None) -> CSR:
     """Q1 matrix of the structured hexahedral grid with node coordinates X, Y, Z (each of
     shape (nez + 1, ney + 1, nex + 1), node (i, j, k) at [k, j, i]).  coef: per-element
     diffusion (shape (nez, ney, nex) or None for 1); reaction: per-element coefficient of the
@@ -350,7 +357,7 @@ def hex_q1_matrix(X: np.ndarray, Y: np.ndarray, Z: np.ndarray, coef=None, reacti
     c = np.ones(E) if coef is None else np.asarray(coef, dtype=np.float64).reshape(nez, ney, nex).ravel()
     r = None if reaction is None else np.broadcast_to(np.asarray(reaction, dtype=np.float64),
                                                       (nez, ney, nex)).ravel()
-    Ke = _hex_element_matrices(Xe, c, r)
+    Ke = _hex_element_matrices(Xe, c, r, velocity)
     # unknown numbering
     if dirichlet:
         inner = np.zeros((nz1, ny1, nx1), dtype=bool)
@@ -416,6 +423,19 @@ def graded_cube(kx: float, ky: float, kz: float, sigma: float, ne: int = 60) -> 
     Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
     A = hex_q1_matrix(X, Y, Z, reaction=1.0 / sigma)
     A.meta.update(family="graded", k=(kx, ky, kz), sigma=sigma, ne=ne)
+    return A
+
+
+def convection_diffusion_box(N: int, velocity=(1.0, 0.5, 0.25), ratio: float = 1.1) -> CSR:
+    """A nonsymmetric stand-in (§3's wind pressure system is solved by GMRES): -Laplace(u) +
+    v . grad(u) with constant velocity v, Galerkin Q1 on the stretched box of `stretched_box`
+    (unit x and y spacing, z spacing ratio^k), N^3 interior nodes, Dirichlet boundaries.  The
+    element Peclet number |v| h / 2 is below 1 on the unit-spaced axes."""
+    ax = np.arange(N + 2, dtype=np.float64)
+    az = np.r_[0.0, np.cumsum(ratio ** np.arange(N + 1, dtype=np.float64))]
+    Z, Y, X = np.meshgrid(az, ax, ax, indexing="ij")
+    A = hex_q1_matrix(X, Y, Z, velocity=velocity)
+    A.meta.update(family="convection", velocity=tuple(velocity), ratio=ratio)
     return A
 
 
@@ -525,5 +545,5 @@ __all__ = [
     "workload_stretched64", "workload_randcoef128", "batched_systems", "serving_stream", "make_operator",
     "VARIANT_BITS",
     "variants_mask", "dirichlet_stencil_row", "hex_q1_matrix", "perturbed_cube", "graded_sizes",
-    "graded_cube",
+    "graded_cube", "convection_diffusion_box",
 ]
