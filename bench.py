@@ -414,6 +414,48 @@ def run_multi(args, amg, torch):
     return out
 
 
+def run_gmres(args, amg, torch):
+    """§8(f) row 3: the nonsymmetric stand-in for §3's pressure system (convection-diffusion,
+    64^3 interior nodes, 6.86M entries) with the symmetrised strength mask, the general
+    coarsest inverse and flexible GMRES(30) to 1e-8, one V-cycle per step; matrix, right-hand
+    side and solution resident on the device; one step = amg_setup + amg_solve + amg_free, host
+    wall time between device synchronisations, L2 flushed before each; FP64 and mixed."""
+    import numpy as np
+    from paper_2103_10476_gb300 import problems as P
+    A, b, kw = P.workload_convdiff64()
+    rp, ci, v = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A.row_ptr, A.col, A.val))
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    arg = amg.csr_arg(A.n, rp, ci, v)
+    out = {"workload": "convection-diffusion 64^3 interior nodes (velocity (0.16,0.08,0.04), unit x/y spacing, "
+                       "z ratio 1.05), theta 0.02, 1Norm+OffLmp, symmetrised strength, GMRES(30) to 1e-8, "
+                       "RHS seed 1; setup+solve per step, device-resident",
+           "rows": A.n, "nnz": A.nnz}
+    for prec_name, prec in (("fp64", amg.AMG_FP64), ("mixed", amg.AMG_MIXED)):
+        p = amg.amg_params_default(precision=prec, cuda_stream=stream.cuda_stream, **kw)
+        steps = []
+        for k in range(1 + 3):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = amg.amg_setup(arg, None, p)
+            t1 = time.perf_counter()
+            info = amg.amg_solve(h, bd, xd, TOL)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            amg.amg_free(h)
+            if k > 0:
+                steps.append({"setup_ms": 1e3 * (t1 - t0), "solve_ms": 1e3 * (t2 - t1), "iters": info.iters,
+                              "status": info.status, "relres": info.relres_true, "levels": info.levels})
+        tot = sum(s_["setup_ms"] + s_["solve_ms"] for s_ in steps)
+        its = steps[-1]["iters"]
+        out[prec_name] = {"solves_per_s": len(steps) / (tot / 1000.0), "ms_per_step": tot / len(steps),
+                          "solve_ms_per_iteration": steps[-1]["solve_ms"] / max(its, 1), "per_step": steps}
+    return out
+
+
 COMBOS = [(m, "+".join(n for b, n in ((1, "1Norm"), (2, "OffLmp"), (8, "Cnstrnt"), (4, "Sprsfy")) if m & b)
            or "traditional") for m in range(16)]
 
@@ -577,6 +619,8 @@ def main():
     ap.add_argument("--study-only", action="store_true", help="only the study line, printed alone")
     ap.add_argument("--no-multi", action="store_true", help="skip the eight-right-hand-side line")
     ap.add_argument("--multi-only", action="store_true", help="only the eight-right-hand-side line, printed alone")
+    ap.add_argument("--no-gmres", action="store_true", help="skip the nonsymmetric (GMRES) line")
+    ap.add_argument("--gmres-only", action="store_true", help="only the nonsymmetric (GMRES) line, printed alone")
     ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -593,6 +637,12 @@ def main():
         torch.cuda.set_device(local)
         from paper_2103_10476_gb300 import amg
         print(json.dumps(run_multi(args, amg, torch)), flush=True)
+        return 0
+    if args.gmres_only:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2103_10476_gb300 import amg
+        print(json.dumps(run_gmres(args, amg, torch)), flush=True)
         return 0
     if args.study_only:
         import torch
@@ -730,6 +780,7 @@ def main():
     batched = None if args.no_batched else run_batched(args, amg, torch)
     study = None if args.no_study else run_study(args, amg, torch)
     multi = None if args.no_multi else run_multi(args, amg, torch)
+    gmres = None if args.no_gmres else run_gmres(args, amg, torch)
     serving = None if not args.serving else run_serving(args, amg, args.serve_seconds,
                                                         ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
 
@@ -775,6 +826,7 @@ def main():
         "batched": batched,
         "study": study,
         "multi": multi,
+        "gmres": gmres,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

@@ -38,9 +38,9 @@ typedef enum {
     AMG_ERR_ZERO_DIAG = 4,      /* a zero diagonal in the filtered or level matrix            */
     AMG_ERR_EIGEN = 5,          /* eigenvalue estimate <= 0 or not finite (§3.1's failure)    */
     AMG_ERR_COARSE_NOT_SPD = 6, /* Cholesky pivot <= 0 on the coarsest level                  */
-    AMG_ERR_NOT_CONVERGED = 7,  /* PCG reached max_iter; x holds the last iterate             */
+    AMG_ERR_NOT_CONVERGED = 7,  /* max_iter reached; x holds the last iterate                 */
     AMG_ERR_BUDGET = 8,         /* a memory budget would be exceeded                          */
-    AMG_ERR_UNSUPPORTED = 9,    /* size beyond the library's limits                           */
+    AMG_ERR_UNSUPPORTED = 9,    /* size beyond the library's limits, or a mode it lacks       */
     AMG_ERR_INTERNAL = 10,      /* a kernel reported an internal limit (e.g. hash overflow)   */
     AMG_PENDING = 11            /* a served request is not finished yet (amg_server_poll)     */
 } amg_status_t;
@@ -61,6 +61,13 @@ enum { AMG_LAMBDA_ONE = 0, AMG_LAMBDA_POWER = 1 };
  * row sum to zero, from coordinates given to amg_setup_coords (level 0) and, on coarser
  * levels, the mean coordinates of each aggregate's members. */
 enum { AMG_STRENGTH_MATRIX = 0, AMG_STRENGTH_DISTANCE = 1 };
+/* Outer Krylov method of amg_solve.  CG for symmetric positive definite operators (§1.1,
+ * §3.1); flexible GMRES(restart) with the V-cycle as right preconditioner for nonsymmetric
+ * ones (§3's wind pressure system is solved by GMRES preconditioned with smoothed
+ * aggregation).  With GMRES the setup treats the operator as nonsymmetric: a connection is
+ * strong when Eq. (7) holds for a_ij or for a_ji (the aggregation graph is undirected), and
+ * the coarsest inverse makes no use of symmetry. */
+enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
 
 /* Square CSR matrix.  row_ptr has n+1 entries (row_ptr[0] = 0), columns are sorted
  * ascending within each row with no duplicates, and every row stores its diagonal.
@@ -95,6 +102,8 @@ typedef struct {
     int strength;        /* AMG_STRENGTH_MATRIX (Eq. 7 on A_l) or AMG_STRENGTH_DISTANCE       */
     int trace;           /* 1: time each setup phase (synchronises the stream at every phase  */
                          /*    boundary; read with amg_setup_trace); 0: no tracing (default)   */
+    int krylov;          /* AMG_KRYLOV_CG (symmetric operators) or AMG_KRYLOV_GMRES            */
+    int restart;         /* GMRES restart length (30)                                         */
 } amg_params_t;
 
 typedef struct {
@@ -127,6 +136,14 @@ amg_status_t amg_setup(const amg_csr_t *A, const double *nullspace, const amg_pa
  * amg_setup is this call with coords = NULL. */
 amg_status_t amg_setup_coords(const amg_csr_t *A, const double *nullspace, const double *coords, int dim,
                               const amg_params_t *p, amg_handle_t *out);
+
+/* With params.krylov = AMG_KRYLOV_GMRES, amg_solve runs flexible GMRES(restart) instead:
+ * per step one V-cycle z_j = M v_j and one product A z_j, classical Gram-Schmidt done twice,
+ * Givens rotations; it stops when the minimiser's residual norm is <= tol ||b|| and the
+ * recomputed true residual agrees (else it restarts from the current x).  info->iters counts
+ * the products with A inside the Arnoldi steps.  Work vectors (2 restart + 2 of them) are
+ * allocated with the hierarchy on the first such solve.  amg_solve_multi and the batch engine
+ * run PCG only: they return AMG_ERR_UNSUPPORTED for such a handle. */
 
 /* Solves A x = b from x = 0 by PCG with one V-cycle (Algorithm 1) per iteration, until
  * ||r|| / ||b|| <= tol on the recurrence residual and on the recomputed true residual.

@@ -23,6 +23,7 @@ SOURCES = {
     "spgemm.cu": ["--fmad=false"],
     "coarse.cu": [],
     "multi.cu": [],
+    "gmres.cu": [],
     "solve.cu": [],
     "api.cu": [],
     "batch.cu": [],

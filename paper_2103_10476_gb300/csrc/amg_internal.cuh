@@ -90,6 +90,9 @@ cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t 
 // Eq. (7): strong[e], removed[e] (= weak off-diagonal) and kept-entry counts per row.
 cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
                      int *kept, cudaStream_t s);
+// nonsymmetric operators: strong[e] = own[e] or own[transpose of e]; removed and kept follow
+cudaError_t symmetrize_strength(const DevCsr &A, const uint8_t *own, uint8_t *strong, uint8_t *removed, int *kept,
+                                cudaStream_t s);
 // §3.1's distance Laplacian on A's pattern (L: one value per stored entry, Ld: its diagonal);
 // *bad counts coupled rows at zero distance
 cudaError_t distance_laplacian(const DevCsr &A, const double *X, int dim, double *L, double *Ld, int *bad,
@@ -158,7 +161,10 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
 // Newton-Schulz in FP64, or the FP64 factorisation when that does not converge).  info = 0
 // or the failing pivot row + 1.  work: coarse_work_bytes(n) bytes.
 size_t coarse_work_bytes(int n);
-cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_dev, cudaStream_t s);
+// general: the operator may be nonsymmetric (Newton-Schulz from the scaled transpose; info =
+// -1 when that does not converge)
+cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_dev, cudaStream_t s,
+                           bool general = false);
 
 // --------------------------------------------------------------------------------- solve.cu
 // SpMV launch plan of one matrix: lanes per row and the shared-memory tile (entries; 0 = none)

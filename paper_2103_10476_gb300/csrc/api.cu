@@ -155,6 +155,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     int *rootof = nullptr, *join1 = nullptr;
     uint8_t *drop = nullptr;
     double *px = nullptr, *py = nullptr, *scal = nullptr, *lvals = nullptr, *ldiag = nullptr;
+    uint8_t *own_mask = nullptr;
     DevCsr AP, Ac;
     int hflags[5] = {0, 0, 0, 0, 0};
     SpmvPlan plan_bar;
@@ -176,6 +177,12 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         CK(strength(Ld, ldiag, p.theta, lv.strong, lv.removed, kept, s));
     } else {
         CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
+    }
+    if (p.krylov == AMG_KRYLOV_GMRES) {
+        // nonsymmetric operator: i-j strong when either direction passes Eq. (7)
+        CK(cudaMallocAsync(&own_mask, (size_t)(A.nnz > 0 ? A.nnz : 1), s));
+        CK(cudaMemcpyAsync(own_mask, lv.strong, (size_t)A.nnz, cudaMemcpyDeviceToDevice, s));
+        CK(symmetrize_strength(A, own_mask, lv.strong, lv.removed, kept, s));
     }
     // strong graph
     CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(n + 1), s));
@@ -363,7 +370,7 @@ done:
     for (void *p : {(void *)kept, (void *)grp, (void *)gci, (void *)mstart, (void *)members, (void *)fill,
                     (void *)flags, (void *)t0, (void *)t1, (void *)rootof, (void *)join1, (void *)drop, (void *)px,
                     (void *)py, (void *)scal, (void *)AP.rp, (void *)AP.ci, (void *)AP.v, (void *)Ac.rp,
-                    (void *)Ac.ci, (void *)Ac.v, (void *)lvals, (void *)ldiag})
+                    (void *)Ac.ci, (void *)Ac.v, (void *)lvals, (void *)ldiag, (void *)own_mask})
         free_async(p, s);
     cudaStreamSynchronize(s);
     return st;
@@ -618,6 +625,8 @@ void amg_params_default(amg_params_t *p)
     p->cuda_stream = nullptr;
     p->strength = AMG_STRENGTH_MATRIX;
     p->trace = 0;
+    p->krylov = AMG_KRYLOV_CG;
+    p->restart = 30;
 }
 
 amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms)
@@ -675,6 +684,7 @@ amg_status_t amg_free(amg_handle_t h)
     }
     if (h->cap) cudaStreamDestroy(h->cap);
     multi_release(h);
+    gmres_release(h);
     release_all(h);
     if (h->rr_host) cudaFreeHost(h->rr_host);
     delete h;
@@ -713,7 +723,9 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
     const amg_params_t &p = *pin;
     if (!(p.theta >= 0.0 && p.theta <= 1.0) || p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0) ||
         p.power_iters < 1 ||
-        p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0)) {
+        p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0) ||
+        (p.krylov != AMG_KRYLOV_CG && p.krylov != AMG_KRYLOV_GMRES) ||
+        (p.krylov == AMG_KRYLOV_GMRES && (p.restart < 1 || p.restart > 512))) {
         g_last_error = "parameter out of range";
         return AMG_ERR_INVALID_ARG;
     }
@@ -795,9 +807,10 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
         CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
         CK(cudaMallocAsync(&cwork, coarse_work_bytes(nc), s));
-        CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s));
+        CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s, p.krylov == AMG_KRYLOV_GMRES));
         CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        if (coarse_info < 0) { g_last_error = "coarsest operator singular or too ill-conditioned for its inverse"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
         if (coarse_info) { g_last_error = "coarsest operator not positive definite"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
         trace_mark(h, L, AMG_PH_COARSE);
     }
@@ -866,6 +879,7 @@ amg_status_t amg_solve(amg_handle_t h, const double *b, double *x, double tol, a
     const int n = h->lev[0].A.n;
     if (n > 0 && (!b || !x)) return AMG_ERR_INVALID_ARG;
     if (!(tol >= 0.0)) return AMG_ERR_INVALID_ARG;
+    if (h->p.krylov == AMG_KRYLOV_GMRES) return fgmres_solve(h, b, x, tol, info);
     const double t0 = now_ms();
     amg_status_t st = AMG_OK;
     cudaStream_t s = h->s;

@@ -1403,6 +1403,10 @@ amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_strea
             set_last_error("all systems of a batch need the same precision and Chebyshev degree");
             return AMG_ERR_INVALID_ARG;
         }
+        if (h[k]->p.krylov != AMG_KRYLOV_CG) {
+            set_last_error("the batch engine runs PCG only");
+            return AMG_ERR_UNSUPPORTED;
+        }
         if (h[k]->nlev > kEngLevels) {
             set_last_error("a hierarchy deeper than the batch engine's level limit");
             return AMG_ERR_UNSUPPORTED;

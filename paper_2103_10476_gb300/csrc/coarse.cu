@@ -14,6 +14,9 @@
 // If the FP32 factorisation meets a pivot <= 0 (the operator is too ill-conditioned for FP32)
 // or the refinement does not bring E below 1e-6, the inverse is formed directly in FP64 by
 // the same factorisation and inverse kernels in double precision.
+// A nonsymmetric coarsest operator (GMRES outer iteration) has no Cholesky factor: its
+// inverse starts from X0 = A^T / (||A||_1 ||A||_inf), for which ||I - A X0||_2 < 1 whenever A
+// is nonsingular, and takes Newton-Schulz steps in FP32 until E < 1e-4, then in FP64.
 //
 // Factorisation (either precision): right-looking, 32-column panels.  Per panel one kernel
 // factors the 32 x 32 diagonal block with a single warp in shared memory (every block
@@ -36,6 +39,8 @@ constexpr int kPanel = 32;
 constexpr int kInvWarps = 4;                 // columns per block of the inverse (at most)
 constexpr int kInvSmem = 200 * 1024;         // dynamic shared memory cap of the inverse kernel
 constexpr int kNewtonSteps = 4;              // refinement steps at most (E0 up to ~1e-2 converges)
+constexpr int kGeneral32 = 64;               // nonsymmetric operators: FP32 steps from the scaled transpose
+constexpr int kGeneral64 = 8;                //   and FP64 steps after them
 constexpr int kGT = 16;                      // product tile: many blocks, so that every SM's FP64 units work
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
@@ -216,11 +221,11 @@ struct NewtonState {
 // C = P Q (n x n, FP64), one output per thread, 32 x 32 tiles staged in shared memory.
 // MODE 0: C = P Q and state->e_bits = max |I - C| (the residual of X = Q against P = A);
 // MODE 1: C = 2 X - X R with X = P, R = Q (the Newton update), or C = X once converged.
-template <int MODE>
-__global__ void __launch_bounds__(kGT * kGT) newton_gemm_kernel(int n, const double *P, const double *Q, double *C,
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kGT * kGT) newton_gemm_kernel(int n, const T *P, const T *Q, T *C,
                                                                  NewtonState *state)
 {
-    __shared__ double Ps[kGT][kGT + 1], Qs[kGT][kGT + 1];
+    __shared__ T Ps[kGT][kGT + 1], Qs[kGT][kGT + 1];
     const int done = state->done || (MODE == 0 && state->last);
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int row = blockIdx.y * kGT + ty, col = blockIdx.x * kGT + tx;
@@ -228,10 +233,10 @@ __global__ void __launch_bounds__(kGT * kGT) newton_gemm_kernel(int n, const dou
         if (MODE == 1 && row < n && col < n) C[(size_t)row * n + col] = P[(size_t)row * n + col];
         return;
     }
-    double acc = 0.0;
+    T acc = T(0);
     for (int k0 = 0; k0 < n; k0 += kGT) {
-        Ps[ty][tx] = (row < n && k0 + tx < n) ? P[(size_t)row * n + k0 + tx] : 0.0;
-        Qs[ty][tx] = (k0 + ty < n && col < n) ? Q[(size_t)(k0 + ty) * n + col] : 0.0;
+        Ps[ty][tx] = (row < n && k0 + tx < n) ? P[(size_t)row * n + k0 + tx] : T(0);
+        Qs[ty][tx] = (k0 + ty < n && col < n) ? Q[(size_t)(k0 + ty) * n + col] : T(0);
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < kGT; ++k) acc += Ps[ty][k] * Qs[k][tx];
@@ -240,11 +245,45 @@ __global__ void __launch_bounds__(kGT * kGT) newton_gemm_kernel(int n, const dou
     if (row >= n || col >= n) return;
     if (MODE == 0) {
         C[(size_t)row * n + col] = acc;
-        const double e = fabs((row == col ? 1.0 : 0.0) - acc);
+        const double e = fabs((row == col ? 1.0 : 0.0) - (double)acc);
         // non-negative doubles order as their bit patterns
         atomicMax(&state->e_bits, (unsigned long long)__double_as_longlong(e));
     } else {
-        C[(size_t)row * n + col] = 2.0 * P[(size_t)row * n + col] - acc;
+        C[(size_t)row * n + col] = T(2) * P[(size_t)row * n + col] - acc;
+    }
+}
+
+// FP32 stage of the general inverse: done once E < 1e-4 (the FP64 steps take it from there)
+__global__ void newton32_check_kernel(NewtonState *state)
+{
+    if (state->done) return;
+    const double e = __longlong_as_double((long long)state->e_bits);
+    if (e < 1e-4) state->done = 1;
+    state->e_prev = e;
+    state->e_bits = 0ULL;
+}
+
+// out[0] = max row sum of |a_ij|, out[1] = max column sum (as bit patterns of non-negative doubles)
+__global__ void abs_sums_kernel(int n, const double *a, unsigned long long *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double r = 0.0, c = 0.0;
+    for (int k = 0; k < n; ++k) {
+        r += fabs(a[(size_t)t * n + k]);
+        c += fabs(a[(size_t)k * n + t]);
+    }
+    atomicMax(&out[0], (unsigned long long)__double_as_longlong(r));
+    atomicMax(&out[1], (unsigned long long)__double_as_longlong(c));
+}
+
+// X0 = A^T / (||A||_1 ||A||_inf) in FP32: ||I - A X0||_2 < 1 for every nonsingular A
+__global__ void transpose_seed_kernel(int n, const double *a, const unsigned long long *sums, float *x)
+{
+    const double scale = 1.0 / (__longlong_as_double((long long)sums[0]) * __longlong_as_double((long long)sums[1]));
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / n, j = e % n;
+        x[e] = (float)(a[j * n + i] * scale);
     }
 }
 
@@ -297,10 +336,33 @@ cudaError_t factor_and_invert(int n, T *a, T *lt, T *rdiag, T *inv, int *info, c
 size_t coarse_work_bytes(int n)
 {
     const size_t nn = (size_t)n * n;
-    return sizeof(double) * (4 * nn + n + 16) + sizeof(float) * (3 * nn + n + 16) + sizeof(NewtonState) + 256;
+    return sizeof(double) * (4 * nn + n + 16) + sizeof(float) * (3 * nn + n + 16) + 2 * sizeof(NewtonState) + 256;
 }
 
-cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info_dev, cudaStream_t s)
+// FP64 Newton-Schulz steps from X (in cur), at most `steps`; the result is in *out.  Returns
+// the error of the last iterate checked (the one returned is at least as good).
+cudaError_t newton64(int n, const double *Ad, double *cur, double *nxt, double *R, NewtonState *st, int steps,
+                     double **out, double *err, cudaStream_t s)
+{
+    NewtonState init{1e300, 0, 0, 0ULL};   // e_prev, done, last, e_bits
+    AMG_CUDA_TRY(cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+    const dim3 blk(kGT, kGT), grd((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
+    for (int k = 0; k < steps; ++k) {
+        newton_gemm_kernel<double, 0><<<grd, blk, 0, s>>>(n, Ad, cur, R, st); note_launch();
+        newton_check_kernel<<<1, 1, 0, s>>>(st); note_launch();
+        newton_gemm_kernel<double, 1><<<grd, blk, 0, s>>>(n, cur, R, nxt, st); note_launch();
+        std::swap(cur, nxt);
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+    NewtonState fin{};
+    AMG_CUDA_TRY(cudaMemcpyAsync(&fin, st, sizeof fin, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = cur;
+    *err = fin.e_prev;
+    return cudaSuccess;
+}
+
+cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info_dev, cudaStream_t s, bool general)
 {
     const int n = A.n;
     AMG_CUDA_TRY(cudaMemsetAsync(info_dev, 0, sizeof(int), s));
@@ -314,6 +376,34 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
     dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
     convert_dense_kernel<double, float><<<cgrid, 256, 0, s>>>(nn, Ad, Af); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
+    if (general) {
+        // a nonsymmetric operator: Newton-Schulz from the scaled transpose, first in FP32 until
+        // E < 1e-4 (at most kGeneral32 steps), then in FP64
+        float *Xf = (float *)Y, *Rf = (float *)Y + nn, *Xf2 = Ltf;
+        unsigned long long *sums = (unsigned long long *)(st + 1);
+        AMG_CUDA_TRY(cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), s));
+        abs_sums_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, Ad, sums); note_launch();
+        transpose_seed_kernel<<<cgrid, 256, 0, s>>>(n, Ad, sums, Xf); note_launch();
+        NewtonState init{1e300, 0, 0, 0ULL};
+        AMG_CUDA_TRY(cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s));
+        const dim3 blk(kGT, kGT), grd((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
+        float *cur = Xf, *nxt = Xf2;
+        for (int k = 0; k < kGeneral32; ++k) {
+            newton_gemm_kernel<float, 0><<<grd, blk, 0, s>>>(n, Af, cur, Rf, st); note_launch();
+            newton32_check_kernel<<<1, 1, 0, s>>>(st); note_launch();
+            newton_gemm_kernel<float, 1><<<grd, blk, 0, s>>>(n, cur, Rf, nxt, st); note_launch();
+            std::swap(cur, nxt);
+        }
+        convert_dense_kernel<float, double><<<cgrid, 256, 0, s>>>(nn, cur, X); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        double *res = nullptr, err = 0.0;
+        AMG_CUDA_TRY(newton64(n, Ad, X, R, (double *)Y, st, kGeneral64, &res, &err, s));
+        if (!(err < 1e-6)) {
+            const int bad = -1;        // singular, or too ill-conditioned for the iteration
+            return cudaMemcpy(info_dev, &bad, sizeof(int), cudaMemcpyHostToDevice);
+        }
+        return cudaMemcpyAsync(inv, res, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+    }
     // stage 1: FP32 factor and inverse (X0 in Y's memory, as floats)
     float *Xf = (float *)Y;
     AMG_CUDA_TRY(factor_and_invert<float>(n, Af, Ltf, rdf, Xf, info_dev, s));
@@ -324,23 +414,11 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
     if (info == 0) {
         // stage 2: Newton-Schulz in FP64 from X0
         convert_dense_kernel<float, double><<<cgrid, 256, 0, s>>>(nn, Xf, X); note_launch();
-        NewtonState init{1e300, 0, 0, 0ULL};   // e_prev, done, last, e_bits
-        AMG_CUDA_TRY(cudaMemcpyAsync(st, &init, sizeof init, cudaMemcpyHostToDevice, s));
-        const dim3 blk(kGT, kGT), grd((n + kGT - 1) / kGT, (n + kGT - 1) / kGT);
-        double *cur = X, *nxt = Y;
-        for (int k = 0; k < kNewtonSteps; ++k) {
-            newton_gemm_kernel<0><<<grd, blk, 0, s>>>(n, Ad, cur, R, st); note_launch();
-            newton_check_kernel<<<1, 1, 0, s>>>(st); note_launch();
-            newton_gemm_kernel<1><<<grd, blk, 0, s>>>(n, cur, R, nxt, st); note_launch();
-            std::swap(cur, nxt);
-        }
         AMG_CUDA_TRY(cudaGetLastError());
-        NewtonState fin{};
-        AMG_CUDA_TRY(cudaMemcpyAsync(&fin, st, sizeof fin, cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaMemcpyAsync(inv, cur, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        // e_prev: the error of the last iterate checked; the one returned is at least as good
-        refined = fin.e_prev < 1e-6;
+        double *res = nullptr, err = 0.0;
+        AMG_CUDA_TRY(newton64(n, Ad, X, Y, R, st, kNewtonSteps, &res, &err, s));
+        refined = err < 1e-6;
+        if (refined) AMG_CUDA_TRY(cudaMemcpyAsync(inv, res, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s));
     }
     if (refined) return cudaSuccess;
     // the direct FP64 path

@@ -10,6 +10,7 @@
 namespace amgk {
 
 struct MultiWork;           // work vectors of amg_solve_multi (multi.cu)
+struct GmresWork;           // Krylov basis and work vectors of flexible GMRES (gmres.cu)
 
 struct Level {
     DevCsr A;                 // level operator
@@ -68,6 +69,7 @@ struct amg_hierarchy {
     int64_t fine_nnz = 0;
     size_t bytes = 0;   // device memory held by the handle
     amgk::MultiWork *multi = nullptr;   // several right-hand sides at once (allocated on first use)
+    amgk::GmresWork *gmres = nullptr;   // flexible GMRES basis (allocated on the first GMRES solve)
 };
 
 
@@ -85,4 +87,9 @@ int hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail)
 void trace_mark(amg_hierarchy *h, int level, int phase);
 // releases the host side of amg_solve_multi's work vectors (their device memory is in allocs)
 void multi_release(amg_hierarchy *h);
+// flexible GMRES(params.restart) preconditioned by one V-cycle per step (amg_solve of a handle
+// set up with AMG_KRYLOV_GMRES); same arguments, results and info fields as amg_solve
+amg_status_t fgmres_solve(amg_hierarchy *h, const double *b, double *x, double tol, amg_info_t *info);
+// releases the host side of the GMRES work vectors (their device memory is in allocs)
+void gmres_release(amg_hierarchy *h);
 }  // namespace amgk

@@ -770,6 +770,10 @@ extern "C" amg_status_t amg_solve_multi(amg_handle_t h, int k, const double *B, 
                                         amg_info_t *infos)
 {
     if (!h || k < 0 || k > 8 || !(tol >= 0.0)) return AMG_ERR_INVALID_ARG;
+    if (h->p.krylov != AMG_KRYLOV_CG) {
+        set_last_error("several right-hand sides at once are solved by PCG only");
+        return AMG_ERR_UNSUPPORTED;
+    }
     if (k == 0) return AMG_OK;
     if (h->lev[0].A.n > 0 && (!B || !X)) return AMG_ERR_INVALID_ARG;
     if (k <= 2) return solve_k<2>(h, k, B, X, tol, infos);

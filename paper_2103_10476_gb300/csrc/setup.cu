@@ -101,6 +101,46 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------ nonsymmetric operators
+// Thread per row: entry (i, j) is strong when its own test or that of (j, i) (found by binary
+// search in row j) passed; removed and the kept count follow.
+__global__ void symmetrize_kernel(int n, const int *rp, const int *ci, const uint8_t *own, uint8_t *strong,
+                                  uint8_t *removed, int *kept)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int nk = 0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const int j = ci[e];
+        bool st = false;
+        if (j != i) {
+            st = own[e] != 0;
+            if (!st) {
+                int lo = rp[j], hi = rp[j + 1] - 1;
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int c = ci[mid];
+                    if (c == i) { st = own[mid] != 0; break; }
+                    if (c < i) lo = mid + 1; else hi = mid - 1;
+                }
+            }
+        }
+        strong[e] = st ? 1 : 0;
+        const bool rem = j != i && !st;
+        removed[e] = rem ? 1 : 0;
+        nk += rem ? 0 : 1;
+    }
+    kept[i] = nk;
+}
+
+cudaError_t symmetrize_strength(const DevCsr &A, const uint8_t *own, uint8_t *strong, uint8_t *removed, int *kept,
+                                cudaStream_t s)
+{
+    if (A.n == 0) return cudaSuccess;
+    symmetrize_kernel<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rp, A.ci, own, strong, removed, kept); note_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------ distance Laplacian, §3.1
 // Thread per row, entries in ascending column order: off the diagonal L_ij = -1 / |x_i - x_j|
 // (the distance from the squared coordinate differences summed in coordinate order), on it

@@ -465,6 +465,16 @@ def workload_randcoef128(N: int = 128):
     return A, rhs_uniform(A.n, 2), dict(theta=0.02, variants=VARIANT_BITS["1norm"] | VARIANT_BITS["offlmp"])
 
 
+def workload_convdiff64(N: int = 64):
+    """Nonsymmetric stand-in for §3's pressure system (solved there by GMRES with SA):
+    convection-diffusion with velocity (0.16, 0.08, 0.04) on the box with unit x and y spacing
+    and z ratio 1.05, 64^3 interior nodes (cell Peclet numbers |v_i| h_i / 2 below 0.5); theta = 0.02,
+    1Norm + OffLmp, GMRES(30); RHS seed 1."""
+    A = convection_diffusion_box(N, velocity=(0.16, 0.08, 0.04), ratio=1.05)
+    return A, rhs_uniform(A.n, 1), dict(theta=0.02, variants=VARIANT_BITS["1norm"] | VARIANT_BITS["offlmp"],
+                                        krylov=1, restart=30)
+
+
 def batched_systems(count: int = 512, seed: int = 3, nmin: int = 8, nmax: int = 40, engine: str = "numpy"):
     """`count` independent systems with edge N ~ U{nmin..nmax}; the first half stretched
     (z ratio ~ U[1.05, 1.2]), the second half coefficient 10^U(-2,2).  System s draws from
@@ -545,5 +555,5 @@ __all__ = [
     "workload_stretched64", "workload_randcoef128", "batched_systems", "serving_stream", "make_operator",
     "VARIANT_BITS",
     "variants_mask", "dirichlet_stencil_row", "hex_q1_matrix", "perturbed_cube", "graded_sizes",
-    "graded_cube", "convection_diffusion_box",
+    "graded_cube", "convection_diffusion_box", "workload_convdiff64",
 ]

@@ -1,10 +1,11 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py times (matrix,
 right-hand side and solution resident on the device, the solve on torch's current stream).
 
-stretched64 (262,144 unknowns, 6.86M entries; the five methods the benchmark steps through)
-and randcoef128 (2,097,152 unknowns, 55.7M entries; 1Norm + OffLmp, FP64 and mixed): the
-whole hierarchy against the oracle's (integer structures bit-exact, values within VAL_TOL),
-PCG iterations by the rule of the small-size tests, solutions within SOL_TOL, and the
+stretched64 (262,144 unknowns, 6.86M entries; the five methods the benchmark steps through),
+randcoef128 (2,097,152 unknowns, 55.7M entries; 1Norm + OffLmp, FP64 and mixed) and the
+nonsymmetric convdiff64 (262,144 unknowns; GMRES(30), FP64 and mixed): the whole hierarchy
+against the oracle's (integer structures bit-exact, values within VAL_TOL), PCG or GMRES
+iterations by the rule of the small-size tests, solutions within SOL_TOL, and the
 relative residual ||b - A x|| / ||b|| recomputed here on the host with scipy.
 """
 import numpy as np
@@ -92,3 +93,25 @@ def test_randcoef128_matches_oracle_fp64_and_mixed(amg, oracle_lib):
     assert infom.status == 0 and abs(infom.iters - oinfo.iters) <= 1, (infom.iters, oinfo.iters)
     assert _relres(A, xm, b) <= 1.01 * TOL
     assert np.linalg.norm(xm - xo) / np.linalg.norm(xo) <= 1e-6
+
+
+def test_convdiff64_gmres_matches_oracle_fp64_and_mixed(amg, oracle_lib):
+    # the nonsymmetric line of the benchmark: symmetrised strength, general coarsest inverse,
+    # flexible GMRES(30)
+    A, b, kw = P.workload_convdiff64()
+    h, info, x = _device_solve(amg, A, b, **kw)
+    oh, ost = oracle_lib.setup(A, **kw)
+    assert ost == 0
+    bad = compare_hierarchies(h, oh)
+    amg.amg_free(h)
+    assert not bad, bad[:8]
+    xo, oinfo, ostat = oh.solve(b, TOL)
+    assert info.status == 0 and ostat == 0
+    assert iterations_agree(oracle_lib, A, kw, b, TOL, info.iters, oinfo.iters), (info.iters, oinfo.iters)
+    if info.iters == oinfo.iters:
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= SOL_TOL
+    assert _relres(A, x, b) <= 1.01 * TOL
+    hm, infom, xm = _device_solve(amg, A, b, precision=amg.AMG_MIXED, **kw)
+    amg.amg_free(hm)
+    assert infom.status == 0 and abs(infom.iters - oinfo.iters) <= 2, (infom.iters, oinfo.iters)
+    assert _relres(A, xm, b) <= 1.01 * TOL
