@@ -398,10 +398,8 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
         AMG_CUDA_TRY(cudaGetLastError());
         double *res = nullptr, err = 0.0;
         AMG_CUDA_TRY(newton64(n, Ad, X, R, (double *)Y, st, kGeneral64, &res, &err, s));
-        if (!(err < 1e-6)) {
-            const int bad = -1;        // singular, or too ill-conditioned for the iteration
-            return cudaMemcpy(info_dev, &bad, sizeof(int), cudaMemcpyHostToDevice);
-        }
+        if (!(err < 1e-6))             // singular, or too ill-conditioned: info = -1 (all bits set)
+            return cudaMemsetAsync(info_dev, 0xFF, sizeof(int), s);
         return cudaMemcpyAsync(inv, res, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
     }
     // stage 1: FP32 factor and inverse (X0 in Y's memory, as floats)

@@ -5,10 +5,17 @@
 //
 // Per cycle r = b - A x, v_0 = r / |r|; per step z_j = M v_j (one V-cycle), w = A z_j,
 // classical Gram-Schmidt against v_0..v_j done twice (h = V^T w, then w -= V h), v_{j+1} =
-// w / |w|.  The Hessenberg column is copied to the host, where Givens rotations keep it
-// triangular and |g_{j+1}| is the minimiser's residual norm.  When that is <= tol |b|, at the
-// end of a cycle or at the iteration limit: y from the triangular system, x += Z y, and the
-// true residual decides (stop, or restart from x).  One synchronisation per step.
+// w / |w|.  The Hessenberg column goes to the host, where Givens rotations keep it triangular
+// and |g_{j+1}| is the minimiser's residual norm.  When that is <= tol |b|, at the end of a
+// cycle or at the iteration limit: y from the triangular system, x += Z y, and the true
+// residual decides (stop, or restart from x).
+//
+// Execution: step j (v_j = w / |w| from the norm left on the device, the V-cycle, A z_j, both
+// Gram-Schmidt passes, |w|^2, the copy of the column to pinned host memory) is one CUDA graph,
+// captured on first use and replayed in later cycles and solves.  Step j+1 is launched before
+// the host waits for step j, so the GPU does not idle while the host rotates the column; a
+// step launched past the stop is discarded (it writes only v_{j+1}, z_{j+1}, w and its own
+// column slot, none of which the update of x reads).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -20,11 +27,16 @@ namespace amgk {
 
 struct GmresWork {
     int m = 0, n = 0;
+    int slot = 0;                     // doubles per step slot: 2 (m+1) projections, then |w|^2
     double *V = nullptr, *Z = nullptr, *w = nullptr;   // V: (m+1) x n, Z: m x n
     double *partial = nullptr;        // kReduceBlocks x (m+1)
-    double *hd = nullptr;             // device: 2 (m+1) projections, then |w|^2, then spare
+    double *hd = nullptr;             // device: m step slots, then r.r of the cycle's start
     double *yd = nullptr;             // device copy of y
-    double *host = nullptr;           // pinned: 2 (m+2) values
+    double *host = nullptr;           // pinned: m step slots, r.r, then y (m values)
+    std::vector<cudaGraphExec_t> gx;  // step graphs (null until captured)
+    std::vector<long long> gk;        // kernels in each step graph
+    bool graph_failed = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -88,9 +100,12 @@ __global__ void gs_update_kernel(int n, const double *V, int nv, const double *h
     }
 }
 
-__global__ void scale_copy_kernel(int n, const double *w, double nrm, double *v)
+// v = w / sqrt(*nrm2) (v = 0 when the norm is 0: the step before broke down and the host stops)
+__global__ void scale_norm_kernel(int n, const double *w, const double *nrm2, double *v)
 {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) v[e] = w[e] / nrm;
+    const double nrm = sqrt(*nrm2);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        v[e] = nrm > 0.0 ? w[e] / nrm : 0.0;
 }
 
 // x += sum_k y_k Z_k (per entry, k ascending)
@@ -103,6 +118,17 @@ __global__ void xz_update_kernel(int n, const double *Z, int nk, const double *y
     }
 }
 
+void release_host_side(GmresWork *W)
+{
+    for (cudaGraphExec_t g : W->gx)
+        if (g) cudaGraphExecDestroy(g);
+    for (int k = 0; k < 2; ++k)
+        if (W->ev[k]) cudaEventDestroy(W->ev[k]);
+    if (W->host) cudaFreeHost(W->host);
+    delete W;
+}
+
+// device vectors (owned by the handle's allocation list), pinned host slots, two events
 cudaError_t gmres_alloc(amg_hierarchy *h, GmresWork &g, int m)
 {
     const int n = h->lev[0].A.n;
@@ -115,15 +141,96 @@ cudaError_t gmres_alloc(amg_hierarchy *h, GmresWork &g, int m)
         return e;
     };
     const size_t nn = (size_t)(n > 0 ? n : 1);
+    g.slot = 2 * (m + 1) + 1;
+    g.m = m;
+    g.n = n;
     AMG_CUDA_TRY(al((void **)&g.V, sizeof(double) * nn * (size_t)(m + 1)));
     AMG_CUDA_TRY(al((void **)&g.Z, sizeof(double) * nn * (size_t)m));
     AMG_CUDA_TRY(al((void **)&g.w, sizeof(double) * nn));
     AMG_CUDA_TRY(al((void **)&g.partial, sizeof(double) * (size_t)kReduceBlocks * (size_t)(m + 1)));
-    AMG_CUDA_TRY(al((void **)&g.hd, sizeof(double) * (size_t)(2 * (m + 1) + 4)));
+    AMG_CUDA_TRY(al((void **)&g.hd, sizeof(double) * ((size_t)m * g.slot + 1)));
     AMG_CUDA_TRY(al((void **)&g.yd, sizeof(double) * (size_t)(m + 1)));
-    AMG_CUDA_TRY(cudaMallocHost(&g.host, sizeof(double) * (size_t)(2 * (m + 1) + 4)));
-    g.m = m;
-    g.n = n;
+    AMG_CUDA_TRY(cudaMallocHost(&g.host, sizeof(double) * ((size_t)m * g.slot + 1 + (size_t)m)));
+    for (int k = 0; k < 2; ++k) AMG_CUDA_TRY(cudaEventCreateWithFlags(&g.ev[k], cudaEventDisableTiming));
+    g.gx.assign((size_t)m, nullptr);
+    g.gk.assign((size_t)m, 0);
+    return cudaSuccess;
+}
+
+// step j of a cycle, enqueued on st (the body of step graph j)
+cudaError_t step_body(amg_hierarchy *h, GmresWork &W, int j, cudaStream_t st)
+{
+    const int n = W.n, m = W.m;
+    const int gp = grid_for(n, 256, 8192);
+    double *vj = W.V + (size_t)j * n, *zj = W.Z + (size_t)j * n;
+    double *slot = W.hd + (size_t)j * W.slot;
+    const double *nrm2 = j == 0 ? W.hd + (size_t)m * W.slot : W.hd + (size_t)(j - 1) * W.slot + 2 * (m + 1);
+    scale_norm_kernel<<<gp, 256, 0, st>>>(n, W.w, nrm2, vj); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(vcycle(h->ctx, vj, zj, st));
+    AMG_CUDA_TRY(spmv_d(h->lev[0].A, h->plan0, zj, W.w, st));
+    const int nv = j + 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        double *hp = slot + (size_t)pass * (m + 1);
+        gs_dots_kernel<<<kReduceBlocks, kGT, 0, st>>>(n, W.V, nv, W.w, W.partial); note_launch();
+        gs_reduce_kernel<<<nv, kGT, 0, st>>>(W.partial, kReduceBlocks, hp); note_launch();
+        gs_update_kernel<<<gp, 256, 0, st>>>(n, W.V, nv, hp, W.w); note_launch();
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(dot(W.w, W.w, n, h->partial, slot + 2 * (m + 1), st));
+    return cudaMemcpyAsync(W.host + (size_t)j * W.slot, slot, sizeof(double) * (size_t)W.slot,
+                           cudaMemcpyDeviceToHost, st);
+}
+
+// the graph of step j (captured on first use); null when steps run eagerly
+cudaGraphExec_t step_graph(amg_hierarchy *h, GmresWork &W, int j)
+{
+    if (W.graph_failed || profiling_enabled()) return nullptr;
+    if (W.gx[(size_t)j]) return W.gx[(size_t)j];
+    cudaGraph_t g = nullptr;
+    const long long launches_before = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = step_body(h, W, j, h->cap);
+        e = cudaStreamEndCapture(h->cap, &g);
+        if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+    }
+    cudaGraphExec_t gx = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, g, 0);
+    if (g) cudaGraphDestroy(g);
+    const long long kernels = launch_count() - launches_before;
+    note_launches(-kernels);       // the capture itself launched nothing
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        W.graph_failed = true;     // this handle's steps run eagerly from now on
+        return nullptr;
+    }
+    W.gx[(size_t)j] = gx;
+    W.gk[(size_t)j] = kernels;
+    return gx;
+}
+
+cudaError_t launch_step(amg_hierarchy *h, GmresWork &W, int j, cudaStream_t s)
+{
+    cudaGraphExec_t gx = step_graph(h, W, j);
+    if (gx) {
+        AMG_CUDA_TRY(cudaGraphLaunch(gx, s));
+        note_launches(W.gk[(size_t)j]);
+    } else {
+        AMG_CUDA_TRY(step_body(h, W, j, s));
+    }
+    return cudaEventRecord(W.ev[j & 1], s);
+}
+
+// w = b - A x and |w|^2 (left on the device where step 0 reads it, and in *out); synchronises s
+cudaError_t true_residual2(amg_hierarchy *h, GmresWork &W, double *out, cudaStream_t s)
+{
+    double *dv = W.hd + (size_t)W.m * W.slot, *hv = W.host + (size_t)W.m * W.slot;
+    AMG_CUDA_TRY(residual_d(h->lev[0].A, h->plan0, h->b, h->x, W.w, s));
+    AMG_CUDA_TRY(dot(W.w, W.w, W.n, h->partial, dv, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(hv, dv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    *out = *hv;
     return cudaSuccess;
 }
 
@@ -138,8 +245,7 @@ cudaError_t gmres_alloc(amg_hierarchy *h, GmresWork &g, int m)
 void gmres_release(amg_hierarchy *h)
 {
     if (!h->gmres) return;
-    if (h->gmres->host) cudaFreeHost(h->gmres->host);
-    delete h->gmres;
+    release_host_side(h->gmres);
     h->gmres = nullptr;
 }
 
@@ -149,19 +255,22 @@ amg_status_t fgmres_solve(amg_hierarchy *h, const double *b, double *x, double t
     const int m = h->p.restart;
     const double t0 = now_ms_g();
     cudaStream_t s = h->s;
-    const DevCsr &A = h->lev[0].A;
     amg_status_t st = AMG_OK, result = AMG_OK;
     int it = 0;
     double nb = 0.0, relres = 0.0;
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), g((size_t)(m + 1), 0.0), cs((size_t)m, 0.0), sn((size_t)m, 0.0),
-        y((size_t)m, 0.0);
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), g((size_t)(m + 1), 0.0), cs((size_t)m, 0.0), sn((size_t)m, 0.0);
     const int gp = grid_for(n, 256, 8192);
-    if (!h->gmres) h->gmres = new GmresWork();
-    GmresWork &W = *h->gmres;
-    if (n > 0 && W.m != m) {
-        if (W.host) cudaFreeHost(W.host);
-        W = GmresWork();
-        GK(gmres_alloc(h, W, m));
+    GmresWork *W = h->gmres;
+    if (n > 0 && !W) {
+        W = new GmresWork();
+        const cudaError_t e = gmres_alloc(h, *W, m);
+        if (e != cudaSuccess) {
+            release_host_side(W);      // device memory stays on the handle's list
+            W = nullptr;
+            st = fail_cuda(e, "gmres_alloc");
+            goto done;
+        }
+        h->gmres = W;
     }
     if (n == 0) goto finish;
     GK(copy_to_device(h->b, b, sizeof(double) * (size_t)n, s));
@@ -176,41 +285,25 @@ amg_status_t fgmres_solve(amg_hierarchy *h, const double *b, double *x, double t
     if (nb == 0.0) goto finish;
     result = AMG_ERR_NOT_CONVERGED;
     while (it < h->p.max_iter) {
-        // r = b - A x, v_0 = r / |r|
-        GK(residual_d(A, h->plan0, h->b, h->x, W.w, s));
-        GK(dot(W.w, W.w, n, h->partial, &h->sc->tmp, s));
+        double *y = W->host + (size_t)m * W->slot + 1;
         double rr = 0.0;
-        GK(cudaMemcpyAsync(&rr, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
-        GK(cudaStreamSynchronize(s));
+        GK(true_residual2(h, *W, &rr, s));
         const double beta = std::sqrt(rr);
         if (beta / nb <= tol) { result = AMG_OK; break; }
-        scale_copy_kernel<<<gp, 256, 0, s>>>(n, W.w, beta, W.V); note_launch();
         std::fill(g.begin(), g.end(), 0.0);
         g[0] = beta;
         int j = 0;
         bool stop = false;
+        GK(launch_step(h, *W, 0, s));
         for (; j < m && it < h->p.max_iter; ++j) {
-            double *vj = W.V + (size_t)j * n, *zj = W.Z + (size_t)j * n;
-            GK(vcycle(h->ctx, vj, zj, s));
-            GK(spmv_d(A, h->plan0, zj, W.w, s));
+            // step j+1 is launched exactly when the loop will reach it, unless this step stops
+            if (j + 1 < m && it + 1 < h->p.max_iter) GK(launch_step(h, *W, j + 1, s));
+            GK(cudaEventSynchronize(W->ev[j & 1]));
             ++it;
-            const int nv = j + 1;
-            for (int pass = 0; pass < 2; ++pass) {
-                double *hp = W.hd + (size_t)pass * (m + 1);
-                gs_dots_kernel<<<kReduceBlocks, kGT, 0, s>>>(n, W.V, nv, W.w, W.partial); note_launch();
-                gs_reduce_kernel<<<nv, kGT, 0, s>>>(W.partial, kReduceBlocks, hp); note_launch();
-                gs_update_kernel<<<gp, 256, 0, s>>>(n, W.V, nv, hp, W.w); note_launch();
-            }
-            GK(cudaGetLastError());
-            GK(dot(W.w, W.w, n, h->partial, W.hd + 2 * (m + 1), s));
-            GK(cudaMemcpyAsync(W.host, W.hd, sizeof(double) * (size_t)(2 * (m + 1) + 1), cudaMemcpyDeviceToHost, s));
-            GK(cudaStreamSynchronize(s));
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = (0.0 + W.host[i]) + W.host[(m + 1) + i];
-            const double hn = std::sqrt(W.host[2 * (m + 1)]);
+            const double *col = W->host + (size_t)j * W->slot;
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = (0.0 + col[i]) + col[(m + 1) + i];
+            const double hn = std::sqrt(col[2 * (m + 1)]);
             H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) {
-                scale_copy_kernel<<<gp, 256, 0, s>>>(n, W.w, hn, W.V + (size_t)(j + 1) * n); note_launch();
-            }
             for (int i = 0; i < j; ++i) {
                 const double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
                 H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
@@ -237,25 +330,20 @@ amg_status_t fgmres_solve(amg_hierarchy *h, const double *b, double *x, double t
             y[i] = sum / H[(size_t)i * m + i];
         }
         if (j > 0) {
-            GK(cudaMemcpyAsync(W.yd, y.data(), sizeof(double) * (size_t)j, cudaMemcpyHostToDevice, s));
-            xz_update_kernel<<<gp, 256, 0, s>>>(n, W.Z, j, W.yd, h->x); note_launch();
+            GK(cudaMemcpyAsync(W->yd, y, sizeof(double) * (size_t)j, cudaMemcpyHostToDevice, s));
+            xz_update_kernel<<<gp, 256, 0, s>>>(n, W->Z, j, W->yd, h->x); note_launch();
             GK(cudaGetLastError());
         }
         if (stop || it >= h->p.max_iter) {
-            GK(residual_d(A, h->plan0, h->b, h->x, W.w, s));
-            GK(dot(W.w, W.w, n, h->partial, &h->sc->tmp, s));
             double tt = 0.0;
-            GK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
-            GK(cudaStreamSynchronize(s));
+            GK(true_residual2(h, *W, &tt, s));
             if (std::sqrt(tt) / nb <= tol) { result = AMG_OK; break; }
         }
     }
 finish:
     if (n > 0) {
-        GK(residual_d(A, h->plan0, h->b, h->x, W.w, s));
-        GK(dot(W.w, W.w, n, h->partial, &h->sc->tmp, s));
         double tt = 0.0;
-        GK(cudaMemcpyAsync(&tt, &h->sc->tmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GK(true_residual2(h, *W, &tt, s));
         GK(copy_to_host(x, h->x, sizeof(double) * (size_t)n, s));
         GK(cudaStreamSynchronize(s));
         relres = nb > 0.0 ? std::sqrt(tt) / nb : 0.0;

@@ -166,6 +166,30 @@ def test_gmres_device_buffers_and_repeat(amg):
     assert np.array_equal(x1.cpu().numpy(), xh)
 
 
+def test_gmres_graph_steps_equal_eager_steps(amg):
+    # each Arnoldi step is a CUDA graph launched one step ahead; with profiling on, the same
+    # steps run eagerly one after another: identical bits, iterations and launch counts
+    A = P.convection_diffusion_box(14)
+    b = P.rhs_uniform(A.n, 7)
+    h, st = _setup(amg, A, theta=0.05, variants=3, krylov=1, restart=8, max_coarse=40)
+    assert st == 0
+    xg, xe = np.zeros(A.n), np.zeros(A.n)
+    amg.amg_solve(h, b, xg, TOL)                 # captures the step graphs
+    c0 = amg.amg_launch_count()
+    ig = amg.amg_solve(h, b, xg, TOL)
+    c1 = amg.amg_launch_count()
+    amg.amg_profile_enable(1)
+    try:
+        ie = amg.amg_solve(h, b, xe, TOL)
+        c2 = amg.amg_launch_count()
+    finally:
+        amg.amg_profile_enable(0)
+    amg.amg_free(h)
+    assert ig.status == ie.status == 0 and ig.iters == ie.iters
+    assert np.array_equal(xg, xe)
+    assert c1 - c0 == c2 - c1 > 0
+
+
 def test_gmres_zero_rhs_and_unsupported_modes(amg):
     A = P.convection_diffusion_box(10)
     h, st = _setup(amg, A, theta=0.05, krylov=1, max_coarse=40)
