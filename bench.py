@@ -268,6 +268,7 @@ def run_once(args):
     variants = dict(VARIANT_SETS[args.workload])
     name = args.method or VARIANT_SETS[args.workload][0][0]
     prec = amg.AMG_MIXED if args.precision == "mixed" else amg.AMG_FP64
+    lay = {"auto": amg.AMG_LAYOUT_AUTO, "csr": amg.AMG_LAYOUT_CSR, "sell": amg.AMG_LAYOUT_SELL}[args.layout]
     rp = torch.from_numpy(A.row_ptr).cuda()
     ci = torch.from_numpy(A.col).cuda()
     v = torch.from_numpy(A.val).cuda()
@@ -279,7 +280,7 @@ def run_once(args):
         # a warm-up setup, then one with every phase boundary synchronised and timed
         for trace in (0, 1):
             ht = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name],
-                                                                 precision=prec, trace=trace))
+                                                                 precision=prec, trace=trace, spmv_layout=lay))
             if trace:
                 levels = amg.amg_num_levels(ht)
                 phases = [{k: round(t, 3) for k, t in amg.amg_setup_trace(ht, l).items() if t > 0}
@@ -287,9 +288,11 @@ def run_once(args):
             amg.amg_free(ht)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec))
+    h = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec,
+                                                       spmv_layout=lay))
     torch.cuda.synchronize()
-    out = {"workload": args.workload, "method": name, "setup_ms": 1000 * (time.perf_counter() - t0)}
+    out = {"workload": args.workload, "method": name, "layout": args.layout,
+           "setup_ms": 1000 * (time.perf_counter() - t0)}
     if phases is not None:
         out["phases_ms"] = phases
     t0 = time.perf_counter()
@@ -606,6 +609,8 @@ def main():
                     help="one setup + solve (or --vcycles V-cycles) of one method, for profiler captures")
     ap.add_argument("--method", default=None, help="with --once: which method of the workload (default: first)")
     ap.add_argument("--vcycles", type=int, default=0)
+    ap.add_argument("--layout", default="auto", choices=["auto", "csr", "sell"],
+                    help="with --once: storage of the solve's operator products (spmv_layout)")
     ap.add_argument("--trace", action="store_true", help="with --once: also report the setup's phase times")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-system batched line")
     ap.add_argument("--batch-steps", type=int, default=2)

@@ -68,6 +68,16 @@ enum { AMG_STRENGTH_MATRIX = 0, AMG_STRENGTH_DISTANCE = 1 };
  * strong when Eq. (7) holds for a_ij or for a_ji (the aggregation graph is undirected), and
  * the coarsest inverse makes no use of symmetry. */
 enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
+/* Storage read by the solve's products with the level operators (no counterpart in the paper).
+ * A sliced-ELL copy (slices of 32 rows, column-major inside a slice, padded to the slice's
+ * longest row; one lane per row with coalesced loads) may be kept beside CSR for a level whose
+ * rows average at most 40 entries and whose padding stays within an eighth of its entries.
+ * SELL: every such level.  AUTO: only those whose FP64 operator (12 bytes per entry) exceeds the
+ * L2 cache; smaller ones are read mostly from L2 by the CSR kernel's consecutive products,
+ * which is faster there.  CSR: never.  A row is summed in the order of the CSR kernel, so every
+ * layout gives identical results; a copy costs 12 bytes per stored entry (16 with AMG_MIXED)
+ * plus its padding. */
+enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_CSR = 1, AMG_LAYOUT_SELL = 2 };
 
 /* Square CSR matrix.  row_ptr has n+1 entries (row_ptr[0] = 0), columns are sorted
  * ascending within each row with no duplicates, and every row stores its diagonal.
@@ -104,6 +114,7 @@ typedef struct {
                          /*    boundary; read with amg_setup_trace); 0: no tracing (default)   */
     int krylov;          /* AMG_KRYLOV_CG (symmetric operators) or AMG_KRYLOV_GMRES            */
     int restart;         /* GMRES restart length (30)                                         */
+    int spmv_layout;     /* AMG_LAYOUT_AUTO (default), AMG_LAYOUT_CSR or AMG_LAYOUT_SELL       */
 } amg_params_t;
 
 typedef struct {

@@ -25,6 +25,7 @@ AMG_PT_ORTHONORMAL, AMG_PT_UNIT = 0, 1
 AMG_LAMBDA_ONE, AMG_LAMBDA_POWER = 0, 1
 AMG_STRENGTH_MATRIX, AMG_STRENGTH_DISTANCE = 0, 1
 AMG_KRYLOV_CG, AMG_KRYLOV_GMRES = 0, 1
+AMG_LAYOUT_AUTO, AMG_LAYOUT_CSR, AMG_LAYOUT_SELL = 0, 1, 2
 PHASES = ("input", "strength", "aggregate", "filter", "eigen", "prolong", "galerkin_ap", "galerkin_rap",
           "smoother", "coarse", "prepare")
 EXPORTS = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
@@ -53,7 +54,7 @@ class amg_params_t(C.Structure):
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int),
-                ("trace", C.c_int), ("krylov", C.c_int), ("restart", C.c_int)]
+                ("trace", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("spmv_layout", C.c_int)]
 
 
 class amg_info_t(C.Structure):

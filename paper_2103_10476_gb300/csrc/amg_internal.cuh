@@ -171,7 +171,22 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_d
 struct SpmvPlan {
     int lpr = 2;
     int cap = 0;
+    // sliced-ELL copy of the matrix read by the solve's products (solve.cu; ns = 0: none).
+    // Columns and the layout are shared by the FP64 and FP32 values.
+    int ns = 0;
+    const int *sp = nullptr, *sw = nullptr, *sci = nullptr;
+    const double *sv64 = nullptr;
+    const float *sv32 = nullptr;
 };
+// sliced ELL (slices of 32 rows): slices of an n-row matrix; widths sw[ns], offsets sp[ns+1]
+// and the entry count in 64 bits (*total64, device; the offsets hold only when it fits an
+// int); then columns and values
+int sell_slices(int n);
+cudaError_t sell_layout(int n, const int *rp, int *sw, int *sp, unsigned long long *total64, cudaStream_t s);
+cudaError_t sell_fill_d(int n, const int *rp, const int *ci, const double *v, int ns, const int *sp, const int *sw,
+                        int *sci, double *sv, cudaStream_t s);
+cudaError_t sell_fill_f(int n, const int *rp, const float *v, int ns, const int *sp, const int *sw, float *sv,
+                        cudaStream_t s);
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s);
 cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns, const int64_t *nnzs,
                        cudaStream_t s);

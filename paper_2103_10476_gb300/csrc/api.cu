@@ -464,7 +464,58 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         if (h->nlev == 1 && n0 > 0) {
             pls.push_back(&h->plan0); rps.push_back(h->lev[0].A.rp); ns.push_back(n0); nz.push_back(h->lev[0].A.nnz);
         }
+        // sliced-ELL copies of the level operators with short rows (their layout first; the
+        // entry counts reach the host with the plans' synchronisation)
+        // An operator that fits in L2 is read mostly from L2 by the CSR kernel's consecutive
+        // products; only larger ones, with short rows, get the copy.
+        std::vector<int> sell_levels;
+        unsigned long long *tot_host = (unsigned long long *)h->rr_host;
+        int dev = 0, l2 = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        for (int L = 0; L + 1 < h->nlev; ++L) {
+            Level &lv = h->lev[L];
+            const bool want = h->p.spmv_layout == AMG_LAYOUT_SELL ||
+                              (h->p.spmv_layout == AMG_LAYOUT_AUTO && 12.0 * (double)lv.A.nnz > (double)l2);
+            if (!want || lv.plan_a.lpr != 2 || lv.A.n == 0 || (int)sell_levels.size() >= kReduceBlocks) continue;
+            const int nsl = sell_slices(lv.A.n);
+            int *sw = nullptr, *sp = nullptr;
+            unsigned long long *t64 = nullptr;
+            CK(dalloc(h, &sw, (size_t)nsl));
+            CK(dalloc(h, &sp, (size_t)nsl + 1));
+            CK(dalloc(h, &t64, 1));
+            CK(sell_layout(lv.A.n, lv.A.rp, sw, sp, t64, s));
+            CK(cudaMemcpyAsync(tot_host + sell_levels.size(), t64, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+            lv.plan_a.sw = sw;
+            lv.plan_a.sp = sp;
+            sell_levels.push_back(L);
+        }
         CK(spmv_plans((int)pls.size(), pls.data(), rps.data(), ns.data(), nz.data(), s));
+        if (!sell_levels.empty()) CK(cudaStreamSynchronize(s));
+        for (size_t k = 0; k < sell_levels.size(); ++k) {
+            Level &lv = h->lev[sell_levels[k]];
+            SpmvPlan &pa = lv.plan_a;
+            // no copy when the offsets would overflow or the padding exceeds an eighth
+            if (tot_host[k] > (unsigned long long)INT32_MAX - 64 ||
+                tot_host[k] > (unsigned long long)lv.A.nnz + (unsigned long long)lv.A.nnz / 8)
+                continue;
+            pa.ns = sell_slices(lv.A.n);
+            const size_t total = (size_t)tot_host[k];
+            int *sci = nullptr;
+            CK(dalloc(h, &sci, total));
+            double *sv64 = nullptr;
+            if (!mixed || sell_levels[k] == 0) CK(dalloc(h, &sv64, total));   // FP64 products: PCG, FP64 V-cycle
+            CK(sell_fill_d(lv.A.n, lv.A.rp, lv.A.ci, lv.A.v, pa.ns, pa.sp, pa.sw, sci, sv64, s));
+            pa.sci = sci;
+            pa.sv64 = sv64;
+            if (mixed) {
+                float *sv32 = nullptr;
+                CK(dalloc(h, &sv32, total));
+                CK(sell_fill_f(lv.A.n, lv.A.rp, lv.Af, pa.ns, pa.sp, pa.sw, sv32, s));
+                pa.sv32 = sv32;
+            }
+        }
         if (h->nlev > 1) h->plan0 = h->lev[0].plan_a;
         for (int L = 0; L + 1 < h->nlev; ++L) {
             Level &lv = h->lev[L];
@@ -627,6 +678,7 @@ void amg_params_default(amg_params_t *p)
     p->trace = 0;
     p->krylov = AMG_KRYLOV_CG;
     p->restart = 30;
+    p->spmv_layout = AMG_LAYOUT_AUTO;
 }
 
 amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms)
@@ -725,7 +777,8 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         p.power_iters < 1 ||
         p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0) ||
         (p.krylov != AMG_KRYLOV_CG && p.krylov != AMG_KRYLOV_GMRES) ||
-        (p.krylov == AMG_KRYLOV_GMRES && (p.restart < 1 || p.restart > 512))) {
+        (p.krylov == AMG_KRYLOV_GMRES && (p.restart < 1 || p.restart > 512)) ||
+        (p.spmv_layout != AMG_LAYOUT_AUTO && p.spmv_layout != AMG_LAYOUT_CSR && p.spmv_layout != AMG_LAYOUT_SELL)) {
         g_last_error = "parameter out of range";
         return AMG_ERR_INVALID_ARG;
     }

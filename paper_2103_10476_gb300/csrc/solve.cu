@@ -157,8 +157,13 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
     double contrib = 0.0, contrib2 = 0.0;
-    double rq = 0.0;                // MODE_POWER: 1 / sqrt(x . x)
-    if (MODE == MODE_POWER) rq = 1.0 / __dsqrt_rn((double)f[0]);
+    double rq = 0.0;                // MODE_POWER: 1 / sqrt(x . x), formed once per block (a
+    if (MODE == MODE_POWER) {       // square root and a division are long FP64 sequences)
+        __shared__ double rq_s;
+        if (threadIdx.x == 0) rq_s = 1.0 / __dsqrt_rn((double)f[0]);
+        __syncthreads();
+        rq = rq_s;
+    }
     if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
@@ -316,6 +321,166 @@ int spmv_take_errors(cudaStream_t s)
     return h;
 }
 
+// ------------------------------------------------------------------------------------ sliced ELL
+// The solve's products with A on levels of short rows read a sliced-ELL copy of A: slices of
+// kSliceRows consecutive rows, each as wide as its longest row, stored column-major (entry k
+// of the slice's row t at sp[slice] + kSliceRows k + t).  Padding has value 0 and the row's own
+// column (the last row's for rows past n).  One lane per row, so the loads of values, columns
+// and x are coalesced across the warp.  A row is summed in two parts, entries 0, 2, 4, ... and
+// 1, 3, 5, ..., added at the end: the arithmetic of the CSR kernel with two lanes per row, so
+// both forms give the same bits (a padding entry adds an exact 0).
+constexpr int kSliceRows = 32;
+constexpr int kSellThreads = 256;
+
+__device__ __forceinline__ double ld_stream(const double *p)
+{
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ld_stream(const int *p)
+{
+    int v;
+    asm volatile("ld.global.nc.L1::no_allocate.s32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// MODE_Y, MODE_RESID, MODE_CHEB and MODE_DOT (partials only) as in spmv_tile_kernel.  MODE_DOT
+// writes the partials of the two-lanes-per-row CSR kernel: one per 128 rows (nparts), each
+// summed by the same shuffle tree and the same order of warps.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const int *__restrict__ sp,
+                                                                 const int *__restrict__ sw,
+                                                                 const int *__restrict__ sci,
+                                                                 const T *__restrict__ sv, const T *__restrict__ x,
+                                                                 T *y, const T *__restrict__ f,
+                                                                 const T *__restrict__ aux, T *d, T c1, T c2,
+                                                                 double *partial, int nparts)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slice = blockIdx.x * (kSellThreads / kSliceRows) + warp;
+    const int row = slice * kSliceRows + lane;
+    T sum = T(0);
+    if (slice * kSliceRows < n) {
+        const int base = sp[slice] + lane, w = sw[slice];
+        const T *vv = sv + base;
+        const int *cc = sci + base;
+        T s0 = T(0), s1 = T(0);
+        int k = 0;
+#pragma unroll 2
+        for (; k + 1 < w; k += 2) {
+            s0 += ld_stream(vv + kSliceRows * k) * x[ld_stream(cc + kSliceRows * k)];
+            s1 += ld_stream(vv + kSliceRows * (k + 1)) * x[ld_stream(cc + kSliceRows * (k + 1))];
+        }
+        if (k < w) s0 += ld_stream(vv + kSliceRows * k) * x[ld_stream(cc + kSliceRows * k)];
+        sum = s0 + s1;
+    }
+    double contrib = 0.0;
+    if (row < n) {
+        if (MODE == MODE_Y) {
+            y[row] = sum;
+        } else if (MODE == MODE_RESID) {
+            y[row] = f[row] - sum;
+        } else if (MODE == MODE_CHEB) {
+            T r = f[row] - sum;
+            T dn = c1 * d[row] + c2 * (aux[row] * r);
+            d[row] = dn;
+            y[row] = x[row] + dn;
+        } else {
+            y[row] = sum;
+            contrib = (double)x[row] * (double)sum;
+        }
+    }
+    if (MODE == MODE_DOT) {
+        // CSR block b covers rows 128 b .. 128 b + 127, its warp w rows 16 w .. 16 w + 15 with
+        // row j's term on lane 2 j; this block's rows are CSR blocks 2 blockIdx and 2 blockIdx + 1
+        __shared__ double con[kSellThreads];
+        __shared__ double wsum[2][kSellThreads / 32];
+        con[threadIdx.x] = contrib;
+        __syncthreads();
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            double v = (lane & 1) ? 0.0 : con[128 * hh + 16 * warp + (lane >> 1)];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kAll, v, o);
+            if (lane == 0) wsum[hh][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int part = 2 * blockIdx.x + threadIdx.x;
+            if (part < nparts) {
+                double t = 0.0;
+                for (int w = 0; w < kSellThreads / 32; ++w) t += wsum[threadIdx.x][w];
+                partial[part] = t;
+            }
+        }
+    }
+}
+
+// slice s: sw[s] = its width, size[s] = kSliceRows sw[s]; *total64 += size[s] (the int offsets
+// are used only when this 64-bit total fits an int)
+__global__ void sell_width_kernel(int n, const int *rp, int ns, int *sw, int *size, unsigned long long *total64)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= ns) return;
+    const int r0 = s * kSliceRows, r1 = min(n, r0 + kSliceRows);
+    int w = 0;
+    for (int r = r0; r < r1; ++r) w = max(w, rp[r + 1] - rp[r]);
+    sw[s] = w;
+    size[s] = kSliceRows * w;
+    atomicAdd(total64, (unsigned long long)kSliceRows * (unsigned long long)w);
+}
+
+// one thread per row slot of every slice: its columns (sci non-null) and values (sv non-null)
+template <typename T>
+__global__ void sell_fill_kernel(int n, const int *rp, const int *ci, const T *v, int ns, const int *sp,
+                                 const int *sw, int *sci, T *sv)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ns * kSliceRows) return;
+    const int s = t / kSliceRows, lane = t % kSliceRows;
+    const int w = sw[s], base = sp[s] + lane;
+    const int b = t < n ? rp[t] : 0, len = t < n ? rp[t + 1] - b : 0;
+    const int pad = t < n ? t : n - 1;
+    for (int k = 0; k < w; ++k) {
+        if (sci) sci[base + kSliceRows * k] = k < len ? ci[b + k] : pad;
+        if (sv) sv[base + kSliceRows * k] = k < len ? v[b + k] : T(0);
+    }
+}
+
+template <typename T>
+const T *sell_values(const SpmvPlan &pl);
+template <>
+const double *sell_values<double>(const SpmvPlan &pl) { return pl.sv64; }
+template <>
+const float *sell_values<float>(const SpmvPlan &pl) { return pl.sv32; }
+
+template <typename T, int MODE>
+cudaError_t launch_sell(const SpmvPlan &pl, int n, const T *sv, const T *x, T *y, const T *f, const T *aux, T *d,
+                        T c1, T c2, double *partial, cudaStream_t s)
+{
+    const int blocks = (pl.ns + kSellThreads / kSliceRows - 1) / (kSellThreads / kSliceRows);
+    spmv_sell_kernel<T, MODE><<<blocks, kSellThreads, 0, s>>>(n, pl.sp, pl.sw, pl.sci, sv, x, y, f, aux, d, c1, c2,
+                                                              partial, spmv_blocks(n, 2)); note_launch();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sell_fill_t(int n, const int *rp, const int *ci, const T *v, int ns, const int *sp, const int *sw,
+                        int *sci, T *sv, cudaStream_t s)
+{
+    if (ns == 0) return cudaSuccess;
+    const int64_t slots = (int64_t)ns * kSliceRows;
+    sell_fill_kernel<T><<<(int)((slots + 255) / 256), 256, 0, s>>>(n, rp, ci, v, ns, sp, sw, sci, sv); note_launch();
+    return cudaGetLastError();
+}
+
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
@@ -341,6 +506,11 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
                       double *result = nullptr, unsigned *counter = nullptr)
 {
     if (n == 0) return cudaSuccess;
+    if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr)) &&
+        pl.ns > 0 && pl.lpr == 2) {
+        const T *sv = sell_values<T>(pl);
+        if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s);
+    }
     switch (pl.lpr) {
     case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
     case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
@@ -391,6 +561,30 @@ cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, con
 }
 
 int spmv_partials_needed(int n) { return spmv_blocks(n, 2) + 1; }
+
+int sell_slices(int n) { return n > 0 ? (n + kSliceRows - 1) / kSliceRows : 0; }
+
+cudaError_t sell_layout(int n, const int *rp, int *sw, int *sp, unsigned long long *total64, cudaStream_t s)
+{
+    const int ns = sell_slices(n);
+    AMG_CUDA_TRY(cudaMemsetAsync(total64, 0, sizeof(unsigned long long), s));
+    if (ns == 0) return cudaMemsetAsync(sp, 0, sizeof(int), s);
+    sell_width_kernel<<<(ns + 255) / 256, 256, 0, s>>>(n, rp, ns, sw, sp, total64); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    return scan_exclusive(sp, sp, ns, s);
+}
+
+cudaError_t sell_fill_d(int n, const int *rp, const int *ci, const double *v, int ns, const int *sp, const int *sw,
+                        int *sci, double *sv, cudaStream_t s)
+{
+    return sell_fill_t<double>(n, rp, ci, v, ns, sp, sw, sci, sv, s);
+}
+
+cudaError_t sell_fill_f(int n, const int *rp, const float *v, int ns, const int *sp, const int *sw, float *sv,
+                        cudaStream_t s)
+{
+    return sell_fill_t<float>(n, rp, nullptr, v, ns, sp, sw, nullptr, sv, s);
+}
 int spmv_block_count(int n, const SpmvPlan &pl) { return spmv_blocks(n, pl.lpr); }
 
 // ------------------------------------------------------------------------------------ PCG vector updates
