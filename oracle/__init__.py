@@ -40,7 +40,8 @@ class Params(C.Structure):
                 ("power_iters", C.c_int),
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("pt_unit", C.c_int),
                 ("onenorm_power", C.c_int), ("seed", C.c_uint64), ("lambda_override", C.c_double),
-                ("max_iter", C.c_int), ("strength", C.c_int), ("krylov", C.c_int), ("restart", C.c_int)]
+                ("max_iter", C.c_int), ("strength", C.c_int), ("krylov", C.c_int), ("restart", C.c_int),
+                ("block_size", C.c_int), ("nullspace_dim", C.c_int)]
 
 
 class Info(C.Structure):
@@ -93,6 +94,10 @@ def lib():
         L.oc_free.argtypes = [vp]
         L.oc_nlevels.argtypes = [vp]
         L.oc_level_get.argtypes = [vp, C.c_int, C.c_int, vp, C.POINTER(C.c_int64)]
+        L.oc_node_graph.argtypes = [C.c_int64, vp, vp, C.c_int, vp]
+        L.oc_node_graph.restype = C.c_int64
+        L.oc_node_fill.argtypes = [C.c_int64, vp, vp, vp, C.c_int, C.c_double, vp, vp, vp, vp, vp]
+        L.oc_block_tentative.argtypes = [C.c_int64, C.c_int, C.c_int, vp, C.c_int64, vp, vp, vp]
     return _lib
 
 
@@ -289,6 +294,33 @@ def lu_solve(a, b):
     return x[:n], int(st)
 
 
+def node_strength(A, bs: int, theta: float):
+    """Block strength of a system with bs unknowns per node: (node row pointer, node columns,
+    block Frobenius norms, node strong flags, per-entry strong flags of A)."""
+    rp, ci, v = _arrs(A)
+    nn = A.n // bs
+    nrp = np.zeros(nn + 1, dtype=np.int64)
+    m = lib().oc_node_graph(A.n, _p(rp), _p(ci), bs, _p(nrp))
+    assert m >= 0
+    nci = np.zeros(max(m, 1), dtype=np.int32)
+    nF = np.zeros(max(m, 1))
+    ns = np.zeros(max(m, 1), dtype=np.uint8)
+    strong = np.zeros(max(A.nnz, 1), dtype=np.uint8)
+    st = lib().oc_node_fill(A.n, _p(rp), _p(ci), _p(v), bs, theta, _p(nrp), _p(nci), _p(nF), _p(ns), _p(strong))
+    assert st == 0
+    return nrp, nci[:m], nF[:m], ns[:m], strong[:A.nnz]
+
+
+def block_tentative(n: int, bs: int, k: int, node_agg, nagg: int, B):
+    """(Qv (n x k, row i = Pt's row i), Bc (k x nagg k), status) of the QR tentative prolongator."""
+    node_agg = np.ascontiguousarray(node_agg, dtype=np.int32)
+    B = np.ascontiguousarray(B, dtype=np.float64).reshape(-1)
+    Qv = np.zeros(max(n * k, 1))
+    Bc = np.zeros(max(nagg * k * k, 1))
+    st = lib().oc_block_tentative(n, bs, k, _p(node_agg), nagg, _p(B), _p(Qv), _p(Bc))
+    return Qv[:n * k].reshape(n, k), Bc[:nagg * k * k].reshape(k, nagg * k), int(st)
+
+
 # ---------------------------------------------------------------- the whole method
 
 _WHAT = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
@@ -296,7 +328,7 @@ _WHAT = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "
          "Abar.v": (8, np.float64), "agg": (9, np.int32), "root": (10, np.uint8), "P.rp": (11, np.int64),
          "P.ci": (12, np.int32), "P.v": (13, np.float64), "R.rp": (14, np.int64), "R.ci": (15, np.int32),
          "R.v": (16, np.float64), "Dsm": (17, np.float64), "scalars": (18, np.float64), "B": (19, np.float64),
-         "cflag": (20, np.uint8), "chol": (21, np.float64), "coords": (22, np.float64)}
+         "cflag": (20, np.uint8), "chol": (21, np.float64), "coords": (22, np.float64), "bsk": (23, np.float64)}
 
 
 class Hierarchy:

@@ -39,6 +39,8 @@ struct oc_level {
     double lambda_cheb;   /* lambda_max(D^-1 A_l) for the Chebyshev smoother       */
     double *invdiag;      /* 1 / diag(A_l)                                         */
     double *coords;       /* dim coordinates per row (distance-Laplacian strength)  */
+    int bs, k;            /* unknowns per node; near-null-space vectors (B is n x k) */
+    double *Bc;           /* systems: the coarse near-null space (nagg k x k)        */
 };
 
 struct oc_hier {
@@ -76,6 +78,8 @@ void oc_params_default(oc_params *p)
     p->strength = 0;
     p->krylov = 0;
     p->restart = 30;
+    p->block_size = 1;
+    p->nullspace_dim = 1;
 }
 
 static void csr_release(oc_csr *c)
@@ -217,6 +221,164 @@ int oc_coarse_coords(int64_t n, const int32_t *agg, int64_t nagg, const double *
 /* ---------------------------------------------------------------------------------------- */
 
 /* Diagonal-dominance measure of §2.3: sum_{j != i} |a_ij| / |a_ii|. */
+/* ---------------------------------------------------------------------------------------- */
+/* Systems of PDEs (the paper treats scalar PDEs and leaves systems to future work; the       */
+/* readings below extend its steps to bs unknowns per node, interleaved: unknown bs v + c is  */
+/* component c of node v, and k near-null-space vectors)                                      */
+/* ---------------------------------------------------------------------------------------- */
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* the nodes coupled to node I: node ids of every stored entry of its bs rows, sorted, without
+ * repeats; returns how many (written to out) */
+static int64_t node_row(const int64_t *rp, const int32_t *ci, int bs, int64_t I, int64_t *out)
+{
+    int64_t m = 0;
+    for (int64_t r = I * bs; r < (I + 1) * bs; ++r)
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e) out[m++] = ci[e] / bs;
+    qsort(out, (size_t)m, sizeof(int64_t), cmp_i64);
+    int64_t u = 0;
+    for (int64_t t = 0; t < m; ++t)
+        if (u == 0 || out[t] != out[u - 1]) out[u++] = out[t];
+    return u;
+}
+
+/* Node graph of the bs x bs blocks: row pointer nrp (n/bs + 1 entries); returns its entry
+ * count, -1 when n is not a multiple of bs. */
+int64_t oc_node_graph(int64_t n, const int64_t *rp, const int32_t *ci, int bs, int64_t *nrp)
+{
+    if (bs < 1 || n % bs) return -1;
+    int64_t nn = n / bs, maxrow = 0;
+    for (int64_t I = 0; I < nn; ++I) {
+        int64_t w = rp[(I + 1) * bs] - rp[I * bs];
+        if (w > maxrow) maxrow = w;
+    }
+    int64_t *tmp = (int64_t *)malloc((size_t)(maxrow > 0 ? maxrow : 1) * sizeof(int64_t));
+    if (!tmp) return -1;
+    nrp[0] = 0;
+    for (int64_t I = 0; I < nn; ++I) nrp[I + 1] = nrp[I] + node_row(rp, ci, bs, I, tmp);
+    free(tmp);
+    return nrp[nn];
+}
+
+/* Block strength.  F_IJ = Frobenius norm of the block coupling nodes I and J (squares summed
+ * over the block's rows in order, each row's entries in order, then the square root).
+ * Reading: Eq. (7) between nodes with F_IJ in place of |a_ij| and F_II, F_JJ in place of
+ * a_ii, a_jj: I != J is strong when F_IJ >= theta sqrt(F_II F_JJ) (for bs = 1 this is Eq. (7)
+ * itself, sqrt(a^2) being |a| exactly).  Per stored entry of A, strong[e] is the strength of
+ * its node pair, and an entry inside a node's own block (off the diagonal) counts as strong:
+ * it is never dropped from the filtered matrix. */
+int oc_node_fill(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs, double theta,
+                 const int64_t *nrp, int32_t *nci, double *nF, uint8_t *nstrong, uint8_t *strong)
+{
+    if (bs < 1 || n % bs) return OC_ERR_INVALID_ARG;
+    int64_t nn = n / bs, maxrow = 0;
+    for (int64_t I = 0; I < nn; ++I) {
+        int64_t w = rp[(I + 1) * bs] - rp[I * bs];
+        if (w > maxrow) maxrow = w;
+    }
+    int64_t *tmp = (int64_t *)malloc((size_t)(maxrow > 0 ? maxrow : 1) * sizeof(int64_t));
+    double *fd = (double *)calloc((size_t)(nn > 0 ? nn : 1), sizeof(double));
+    if (!tmp || !fd) { free(tmp); free(fd); return OC_ERR_OOM; }
+    for (int64_t I = 0; I < nn; ++I) {
+        int64_t m = node_row(rp, ci, bs, I, tmp);
+        for (int64_t t = 0; t < m; ++t) {
+            int64_t J = tmp[t];
+            double acc = 0.0;
+            for (int64_t r = I * bs; r < (I + 1) * bs; ++r)
+                for (int64_t e = rp[r]; e < rp[r + 1]; ++e)
+                    if (ci[e] / bs == J) acc = acc + v[e] * v[e];
+            nci[nrp[I] + t] = (int32_t)J;
+            nF[nrp[I] + t] = sqrt(acc);
+            if (J == I) fd[I] = nF[nrp[I] + t];
+        }
+    }
+    for (int64_t I = 0; I < nn; ++I)
+        for (int64_t t = nrp[I]; t < nrp[I + 1]; ++t) {
+            int64_t J = nci[t];
+            nstrong[t] = (J != I && nF[t] >= theta * sqrt(fd[I] * fd[J])) ? 1 : 0;
+        }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int64_t I = i / bs, J = ci[e] / bs;
+            if (I == J) { strong[e] = ci[e] != i; continue; }
+            uint8_t sflag = 0;
+            for (int64_t t = nrp[I]; t < nrp[I + 1]; ++t)
+                if (nci[t] == J) sflag = nstrong[t];
+            strong[e] = sflag;
+        }
+    free(tmp);
+    free(fd);
+    return OC_OK;
+}
+
+/* Tentative prolongator for k near-null-space vectors (B: k vectors of length n, one after
+ * another).  Aggregate a's rows are the unknowns of its nodes, nodes ascending and components
+ * ascending (m rows); its m x k block of B is factored B_a = Q_a R_a by modified Gram-Schmidt
+ * in column order (every inner product and norm summed over the rows in order), R_a upper
+ * triangular with a positive diagonal.  Row i of Pt holds Q_a's row at columns a k .. a k + k - 1
+ * (Qv[i k + j]); the coarse near-null space is R_a (Bc: k vectors of length nagg k, row
+ * a k + j of vector c = (R_a)_jc).  So Pt Bc = B and each aggregate's columns are orthonormal.
+ * Reading: a column whose norm after the projections falls to 1e-12 of its norm before them
+ * (the aggregate is too small to carry k independent vectors) fails with OC_ERR_UNSUPPORTED. */
+int oc_block_tentative(int64_t n, int bs, int k, const int32_t *node_agg, int64_t nagg, const double *B,
+                       double *Qv, double *Bc)
+{
+    if (bs < 1 || k < 1 || n % bs) return OC_ERR_INVALID_ARG;
+    int64_t nn = n / bs, nc = nagg * k;
+    int64_t *start = (int64_t *)calloc((size_t)(nagg + 1), sizeof(int64_t));
+    int64_t *members = (int64_t *)malloc((size_t)(nn > 0 ? nn : 1) * sizeof(int64_t));
+    int64_t *fillp = (int64_t *)calloc((size_t)(nagg + 1), sizeof(int64_t));
+    double *W = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)k * sizeof(double));
+    double *R = (double *)calloc((size_t)k * (size_t)k, sizeof(double));
+    int st = OC_OK;
+    if (!start || !members || !fillp || !W || !R) { st = OC_ERR_OOM; goto out; }
+    for (int64_t I = 0; I < nn; ++I) start[node_agg[I] + 1]++;
+    for (int64_t a = 0; a < nagg; ++a) start[a + 1] += start[a];
+    for (int64_t I = 0; I < nn; ++I) members[start[node_agg[I]] + fillp[node_agg[I]]++] = I;
+    for (int64_t e = 0; e < nc * k; ++e) Bc[e] = 0.0;
+    for (int64_t a = 0; a < nagg && st == OC_OK; ++a) {
+        int64_t m = (start[a + 1] - start[a]) * bs;
+        /* W[j m + t] = B restricted to the aggregate's rows */
+        for (int j = 0; j < k; ++j)
+            for (int64_t t = 0; t < m; ++t) {
+                int64_t i = members[start[a] + t / bs] * bs + t % bs;
+                W[j * m + t] = B[(int64_t)j * n + i];
+            }
+        for (int j = 0; j < k * k; ++j) R[j] = 0.0;
+        for (int j = 0; j < k; ++j) {
+            double before = 0.0;
+            for (int64_t t = 0; t < m; ++t) before = before + W[j * m + t] * W[j * m + t];
+            for (int l = 0; l < j; ++l) {
+                double r = 0.0;
+                for (int64_t t = 0; t < m; ++t) r = r + W[l * m + t] * W[j * m + t];
+                R[l * k + j] = r;
+                for (int64_t t = 0; t < m; ++t) W[j * m + t] = W[j * m + t] - r * W[l * m + t];
+            }
+            double s = 0.0;
+            for (int64_t t = 0; t < m; ++t) s = s + W[j * m + t] * W[j * m + t];
+            double rjj = sqrt(s);
+            if (!(rjj > 1e-12 * sqrt(before))) { st = OC_ERR_UNSUPPORTED; break; }
+            for (int64_t t = 0; t < m; ++t) W[j * m + t] = W[j * m + t] / rjj;
+            R[j * k + j] = rjj;
+        }
+        if (st) break;
+        for (int64_t t = 0; t < m; ++t) {
+            int64_t i = members[start[a] + t / bs] * bs + t % bs;
+            for (int j = 0; j < k; ++j) Qv[i * k + j] = W[j * m + t];
+        }
+        for (int c = 0; c < k; ++c)
+            for (int j = 0; j < k; ++j) Bc[(int64_t)c * nc + a * k + j] = R[j * k + c];
+    }
+out:
+    free(start); free(members); free(fillp); free(W); free(R);
+    return st;
+}
+
 static double ddom(const double *val, const int32_t *col, int64_t len, int64_t i, double aii)
 {
     double s = 0.0;
@@ -822,8 +984,11 @@ static int csr_copy(oc_csr *dst, int64_t n, const int64_t *rp, const int32_t *ci
  *  -> filtered matrix (Eq. 6 or Algorithm 2) -> diagonal (Dbar, or Dtilde of Eq. 9 with the
  *  safeguard of Eq. 10-11) -> lambda (power method, or 1 with 1Norm) -> omega = 4/(3 lambda)
  *  -> P = (I - omega D^-1 Abar) Pt (Eq. 3) -> [Algorithm 3 per row] -> column scaling. */
+static int build_prolongator_block(oc_hier *h, int L, int stop_if_not_coarsened);
+
 static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
 {
+    if (h->p.block_size > 1 || h->p.nullspace_dim > 1) return build_prolongator_block(h, L, stop_if_not_coarsened);
     struct oc_level *lv = &h->lev[L];
     const oc_params *p = &h->p;
     oc_csr *A = &lv->A;
@@ -975,6 +1140,107 @@ static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
     return OC_OK;
 }
 
+/* The same steps for a system of PDEs (variants off): block strength between nodes
+ * (oc_node_fill), MIS-2 aggregation of the node graph, the QR tentative prolongator
+ * (oc_block_tentative), the filtered matrix with the dropped entries lumped into the diagonal
+ * (Eq. 6), lambda of Dbar^-1 Abar, and P = Pt - omega Dbar^-1 (Abar Pt) (Eq. 3).  agg and root
+ * are per node; the coarse level has k unknowns per aggregate. */
+static int build_prolongator_block(oc_hier *h, int L, int stop_if_not_coarsened)
+{
+    struct oc_level *lv = &h->lev[L];
+    const oc_params *p = &h->p;
+    oc_csr *A = &lv->A;
+    int64_t n = A->n, nnz = A->nnz;
+    int bs = lv->bs, k = lv->k;
+    if (bs < 1 || k < 1 || n % bs) return OC_ERR_INVALID_ARG;
+    int64_t nn = n / bs;
+    int st;
+    lv->strong = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    lv->removed = (uint8_t *)malloc((size_t)(nnz > 0 ? nnz : 1));
+    lv->lumpflag = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    lv->agg = (int32_t *)malloc((size_t)(nn > 0 ? nn : 1) * sizeof(int32_t));
+    lv->root = (uint8_t *)malloc((size_t)(nn > 0 ? nn : 1));
+    int64_t *nrp = (int64_t *)malloc((size_t)(nn + 1) * sizeof(int64_t));
+    if (!lv->strong || !lv->removed || !lv->lumpflag || !lv->agg || !lv->root || !nrp) { free(nrp); return OC_ERR_OOM; }
+    int64_t nnzn = oc_node_graph(n, A->rp, A->ci, bs, nrp);
+    if (nnzn < 0) { free(nrp); return OC_ERR_INVALID_ARG; }
+    int32_t *nci = (int32_t *)malloc((size_t)(nnzn > 0 ? nnzn : 1) * sizeof(int32_t));
+    double *nF = (double *)malloc((size_t)(nnzn > 0 ? nnzn : 1) * sizeof(double));
+    uint8_t *nstrong = (uint8_t *)malloc((size_t)(nnzn > 0 ? nnzn : 1));
+    if (!nci || !nF || !nstrong) { free(nrp); free(nci); free(nF); free(nstrong); return OC_ERR_OOM; }
+    st = oc_node_fill(n, A->rp, A->ci, A->v, bs, p->theta, nrp, nci, nF, nstrong, lv->strong);
+    int64_t nagg = -1;
+    if (!st) nagg = oc_mis2_aggregate(nn, nrp, nci, nstrong, p->seed, L, lv->agg, lv->root);
+    free(nrp); free(nci); free(nF); free(nstrong);
+    if (st) return st;
+    if (nagg < 0) return OC_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
+            lv->removed[e] = (A->ci[e] != i && !lv->strong[e]) ? 1 : 0;
+    lv->nagg = nagg;
+    if (stop_if_not_coarsened && (nagg == 0 || nagg * k >= n)) return OC_OK;
+    int64_t nc = nagg * k;
+
+    double *Qv = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)k * sizeof(double));
+    lv->Bc = (double *)malloc((size_t)(nc > 0 ? nc : 1) * (size_t)k * sizeof(double));
+    if (!Qv || !lv->Bc) { free(Qv); return OC_ERR_OOM; }
+    st = oc_block_tentative(n, bs, k, lv->agg, nagg, lv->B, Qv, lv->Bc);
+    if (st) { free(Qv); return st; }
+
+    oc_csr *Ab = NULL;
+    st = oc_filter(n, A->rp, A->ci, A->v, lv->removed, 0, p->tau, &Ab, lv->lumpflag);
+    if (st) { free(Qv); return st; }
+    lv->Abar = *Ab;
+    free(Ab);
+    lv->Dsm = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t i = 0; i < n; ++i) {
+        double d = diag_of(lv->Abar.rp, lv->Abar.ci, lv->Abar.v, i);
+        if (d == 0.0) { free(Qv); return OC_ERR_ZERO_DIAG; }
+        lv->Dsm[i] = d;
+    }
+    if (p->lambda_override > 0.0)
+        lv->lambda_bar = p->lambda_override;
+    else
+        lv->lambda_bar = oc_power_lambda(n, lv->Abar.rp, lv->Abar.ci, lv->Abar.v, lv->Dsm, p->power_iters,
+                                         oc_power_stream_seed(p->seed, L, 1));
+    if (!(lv->lambda_bar > 0.0) || !isfinite(lv->lambda_bar)) { free(Qv); return OC_ERR_EIGEN; }
+    lv->omega = 4.0 / (3.0 * lv->lambda_bar);
+
+    /* P = Pt - omega Dbar^-1 (Abar Pt); Pt row i: columns agg(i) k .. agg(i) k + k - 1 */
+    oc_csr Pt;
+    if (csr_alloc(&Pt, n, n * k)) { free(Qv); return OC_ERR_OOM; }
+    for (int64_t i = 0; i < n; ++i) {
+        Pt.rp[i + 1] = (i + 1) * k;
+        for (int j = 0; j < k; ++j) {
+            Pt.ci[i * k + j] = (int32_t)(lv->agg[i / bs] * k + j);
+            Pt.v[i * k + j] = Qv[i * k + j];
+        }
+    }
+    oc_csr *AP = NULL;
+    st = oc_spgemm(&lv->Abar, &Pt, nc, &AP);
+    csr_release(&Pt);
+    if (st) { free(Qv); return st; }
+    for (int64_t i = 0; i < n; ++i) {
+        double scale = lv->omega / lv->Dsm[i];
+        int64_t c0 = (int64_t)lv->agg[i / bs] * k;
+        for (int64_t e = AP->rp[i]; e < AP->rp[i + 1]; ++e) {
+            int64_t c = AP->ci[e];
+            double pt = (c >= c0 && c < c0 + k) ? Qv[i * k + (c - c0)] : 0.0;
+            AP->v[e] = pt - scale * AP->v[e];
+        }
+    }
+    free(Qv);
+    lv->P = *AP;
+    free(AP);
+    lv->cflag = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    oc_csr *R = NULL;
+    st = oc_transpose(&lv->P, nc, &R);
+    if (st) return st;
+    lv->R = *R;
+    free(R);
+    return OC_OK;
+}
+
 /* Chebyshev eigenvalue and inverse diagonal of A_L */
 static int smoother_setup(oc_hier *h, int L)
 {
@@ -1006,6 +1272,10 @@ int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
     *out = NULL;
     if (n < 0 || !rp) return OC_ERR_INVALID_ARG;
     if (p->strength == 1 && (!coords || dim < 1 || dim > 3)) return OC_ERR_INVALID_ARG;
+    const int block = p->block_size > 1 || p->nullspace_dim > 1;
+    if (p->block_size < 1 || p->nullspace_dim < 1 || n % p->block_size) return OC_ERR_INVALID_ARG;
+    if (block && (p->variants || p->strength || (!nullspace && p->nullspace_dim != p->block_size)))
+        return p->variants || p->strength ? OC_ERR_UNSUPPORTED : OC_ERR_INVALID_ARG;
     oc_hier *h = (oc_hier *)calloc(1, sizeof(oc_hier));
     if (!h) return OC_ERR_OOM;
     h->p = *p;
@@ -1017,19 +1287,29 @@ int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
         if (!h->lev[0].coords) { oc_free(h); return OC_ERR_OOM; }
         memcpy(h->lev[0].coords, coords, (size_t)(n * dim) * sizeof(double));
     }
-    h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
-    for (int64_t i = 0; i < n; ++i) h->lev[0].B[i] = nullspace ? nullspace[i] : 1.0;
+    {
+        /* B: k vectors of length n one after another; without one given, the constant (scalar)
+         * or the constant of each component (k = bs) */
+        const int k = p->nullspace_dim, bs = p->block_size;
+        h->lev[0].bs = bs;
+        h->lev[0].k = k;
+        h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)k * sizeof(double));
+        if (!h->lev[0].B) { oc_free(h); return OC_ERR_OOM; }
+        for (int j = 0; j < k; ++j)
+            for (int64_t i = 0; i < n; ++i)
+                h->lev[0].B[(int64_t)j * n + i] = nullspace ? nullspace[(int64_t)j * n + i] : (i % bs == j ? 1.0 : 0.0);
+    }
     int L = 0;
     for (;;) {
         struct oc_level *lv = &h->lev[L];
         if (lv->A.n <= p->max_coarse || L + 1 >= p->max_levels || L + 1 >= OC_MAX_LEVELS) break;
         st = build_prolongator(h, L, 1);
         if (st) { oc_free(h); return st; }
-        if (lv->nagg == lv->A.n || lv->nagg == 0) break;   /* no coarsening: this is the coarsest */
+        if (lv->nagg * lv->k >= lv->A.n || lv->nagg == 0) break;   /* no coarsening: this is the coarsest */
         /* Galerkin product, Eq. (2), with the original A */
         oc_csr *AP = NULL, *Ac = NULL;
-        st = oc_spgemm(&lv->A, &lv->P, lv->nagg, &AP);
-        if (!st) st = oc_spgemm(&lv->R, AP, lv->nagg, &Ac);
+        st = oc_spgemm(&lv->A, &lv->P, lv->nagg * lv->k, &AP);
+        if (!st) st = oc_spgemm(&lv->R, AP, lv->nagg * lv->k, &Ac);
         oc_csr_free(AP);
         if (st) { oc_free(h); return st; }
         st = smoother_setup(h, L);
@@ -1037,8 +1317,15 @@ int oc_setup_coords(int64_t n, const int64_t *rp, const int32_t *ci, const doubl
         struct oc_level *nx = &h->lev[L + 1];
         nx->A = *Ac;
         free(Ac);
-        nx->B = (double *)malloc((size_t)(lv->nagg > 0 ? lv->nagg : 1) * sizeof(double));
-        for (int64_t a = 0; a < lv->nagg; ++a) nx->B[a] = p->pt_unit ? 1.0 : lv->nrm[a];
+        nx->bs = lv->k;
+        nx->k = lv->k;
+        if (block) {
+            nx->B = lv->Bc;
+            lv->Bc = NULL;
+        } else {
+            nx->B = (double *)malloc((size_t)(lv->nagg > 0 ? lv->nagg : 1) * sizeof(double));
+            for (int64_t a = 0; a < lv->nagg; ++a) nx->B[a] = p->pt_unit ? 1.0 : lv->nrm[a];
+        }
         if (h->dim > 0) {
             nx->coords = (double *)malloc((size_t)(lv->nagg > 0 ? lv->nagg * h->dim : 1) * sizeof(double));
             if (!nx->coords) { oc_free(h); return OC_ERR_OOM; }
@@ -1120,7 +1407,7 @@ static void vcycle_level(oc_hier *h, int L, const double *f, double *u)
     }
     double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
     double *d = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
-    int64_t nc = lv->nagg;
+    int64_t nc = lv->nagg * lv->k;     /* rows of the next level */
     double *fc = (double *)malloc((size_t)(nc > 0 ? nc : 1) * sizeof(double));
     double *uc = (double *)calloc((size_t)(nc > 0 ? nc : 1), sizeof(double));
     chebyshev(lv, h->p.cheb_degree, h->p.cheb_ratio, h->p.cheb_boost, f, u, r, d);
@@ -1320,8 +1607,18 @@ int oc_prolongator_only(int64_t n, const int64_t *rp, const int32_t *ci, const d
     h->prolongator_only = 1;
     int st = csr_copy(&h->lev[0].A, n, rp, ci, v);
     if (st) { oc_free(h); return st; }
-    h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
-    for (int64_t i = 0; i < n; ++i) h->lev[0].B[i] = nullspace ? nullspace[i] : 1.0;
+    {
+        /* B: k vectors of length n one after another; without one given, the constant (scalar)
+         * or the constant of each component (k = bs) */
+        const int k = p->nullspace_dim, bs = p->block_size;
+        h->lev[0].bs = bs;
+        h->lev[0].k = k;
+        h->lev[0].B = (double *)malloc((size_t)(n > 0 ? n : 1) * (size_t)k * sizeof(double));
+        if (!h->lev[0].B) { oc_free(h); return OC_ERR_OOM; }
+        for (int j = 0; j < k; ++j)
+            for (int64_t i = 0; i < n; ++i)
+                h->lev[0].B[(int64_t)j * n + i] = nullspace ? nullspace[(int64_t)j * n + i] : (i % bs == j ? 1.0 : 0.0);
+    }
     st = build_prolongator(h, 0, 0);
     if (st) { oc_free(h); return st; }
     *out = h;
@@ -1342,6 +1639,7 @@ void oc_free(oc_hier *h)
         csr_release(&lv->A); csr_release(&lv->Abar); csr_release(&lv->P); csr_release(&lv->R);
         free(lv->strong); free(lv->removed); free(lv->lumpflag); free(lv->agg); free(lv->root);
         free(lv->B); free(lv->nrm); free(lv->Dsm); free(lv->cflag); free(lv->invdiag); free(lv->coords);
+        free(lv->Bc);
     }
     free(h->chol);
     free(h->lu);
@@ -1358,7 +1656,7 @@ int oc_nlevels(const oc_hier *h) { return h ? h->nlev : 0; }
 /* what: 0 A.rp, 1 A.ci, 2 A.v, 3 strong, 4 removed, 5 lumpflag, 6 Abar.rp, 7 Abar.ci,
  * 8 Abar.v, 9 agg, 10 root, 11 P.rp, 12 P.ci, 13 P.v, 14 R.rp, 15 R.ci, 16 R.v, 17 Dsm,
  * 18 scalars [lambda_bar, omega, lambda_cheb, nagg], 19 B, 20 cflag, 21 Cholesky factor,
- * 22 coordinates (n * dim).
+ * 22 coordinates (n * dim), 23 [unknowns per node, near-null-space vectors].
  * Copies into dst when it is not NULL; *len receives the element count. */
 int oc_level_get(const oc_hier *h, int L, int what, void *dst, int64_t *len)
 {
@@ -1379,8 +1677,8 @@ int oc_level_get(const oc_hier *h, int L, int what, void *dst, int64_t *len)
     case 6: src = lv->Abar.rp; es = 8; cnt = last ? 0 : lv->Abar.n + 1; break;
     case 7: src = lv->Abar.ci; es = 4; cnt = last ? 0 : lv->Abar.nnz; break;
     case 8: src = lv->Abar.v; es = 8; cnt = last ? 0 : lv->Abar.nnz; break;
-    case 9: src = lv->agg; es = 4; cnt = last ? 0 : lv->A.n; break;
-    case 10: src = lv->root; es = 1; cnt = last ? 0 : lv->A.n; break;
+    case 9: src = lv->agg; es = 4; cnt = last ? 0 : lv->A.n / (lv->bs > 0 ? lv->bs : 1); break;
+    case 10: src = lv->root; es = 1; cnt = last ? 0 : lv->A.n / (lv->bs > 0 ? lv->bs : 1); break;
     case 11: src = lv->P.rp; es = 8; cnt = last ? 0 : lv->P.n + 1; break;
     case 12: src = lv->P.ci; es = 4; cnt = last ? 0 : lv->P.nnz; break;
     case 13: src = lv->P.v; es = 8; cnt = last ? 0 : lv->P.nnz; break;
@@ -1391,10 +1689,11 @@ int oc_level_get(const oc_hier *h, int L, int what, void *dst, int64_t *len)
     case 18:
         sc[0] = lv->lambda_bar; sc[1] = lv->omega; sc[2] = lv->lambda_cheb; sc[3] = (double)lv->nagg;
         src = sc; es = 8; cnt = 4; break;
-    case 19: src = lv->B; es = 8; cnt = lv->A.n; break;
+    case 19: src = lv->B; es = 8; cnt = lv->A.n * (lv->k > 0 ? lv->k : 1); break;
     case 20: src = lv->cflag; es = 1; cnt = last ? 0 : lv->A.n; break;
     case 21: src = h->chol; es = 8; cnt = last ? lv->A.n * lv->A.n : 0; break;
     case 22: src = lv->coords; es = 8; cnt = lv->coords ? lv->A.n * h->dim : 0; break;
+    case 23: sc[0] = lv->bs; sc[1] = lv->k; src = sc; es = 8; cnt = 2; break;
     default: return OC_ERR_INVALID_ARG;
     }
     if (len) *len = cnt;

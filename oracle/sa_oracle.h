@@ -57,6 +57,8 @@ typedef struct {
     int strength;          /* 0: Eq. (7) on the matrix; 1: Eq. (7) on the distance Laplacian (§3.1) */
     int krylov;            /* 0: PCG (symmetric operators); 1: flexible GMRES (nonsymmetric operators) */
     int restart;           /* GMRES restart length */
+    int block_size;        /* unknowns per node on the finest level (systems of PDEs; 1: scalar) */
+    int nullspace_dim;     /* near-null-space vectors k (coarse levels carry k unknowns per node) */
 } oc_params;
 
 typedef struct {
@@ -96,6 +98,12 @@ void oc_lu_solve(int64_t n, const double *lu, const int64_t *piv, const double *
 int oc_gmres_plain(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *b, double *x,
                    double tol, int restart, int max_iter, oc_info *info);
 void oc_csr_free(oc_csr *c);
+/* systems of PDEs: node graph of bs x bs blocks, block strength, per-aggregate QR */
+int64_t oc_node_graph(int64_t n, const int64_t *rp, const int32_t *ci, int bs, int64_t *nrp);
+int oc_node_fill(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, int bs, double theta,
+                 const int64_t *nrp, int32_t *nci, double *nF, uint8_t *nstrong, uint8_t *strong);
+int oc_block_tentative(int64_t n, int bs, int k, const int32_t *node_agg, int64_t nagg, const double *B,
+                       double *Qv, double *Bc);
 
 /* the whole method */
 int oc_setup(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *nullspace,

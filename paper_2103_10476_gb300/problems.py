@@ -392,6 +392,126 @@ def hex_q1_matrix(X: np.ndarray, Y: np.ndarray, Z: np.ndarray, coef=None, reacti
                meta={"grid": (nx1 - 2, ny1 - 2, nz1 - 2) if dirichlet else (nx1, ny1, nz1), "coords": coords})
 
 
+def _hex_elasticity_matrices(Xe: np.ndarray, lam: float, mu: float) -> np.ndarray:
+    """Xe: (E, 8, 3) node coordinates.  Isotropic linear elasticity with Lame parameters lam,
+    mu on trilinear hexahedra, 2x2x2 Gauss rule: entry (3a + p, 3b + q) of the (E, 24, 24)
+    element matrices is the sum over Gauss points of
+    det J (lam G_ap G_bq + mu G_aq G_bp + mu delta_pq grad N_a . grad N_b)."""
+    E = Xe.shape[0]
+    sgn = np.array([[2 * (a & 1) - 1, 2 * ((a >> 1) & 1) - 1, 2 * ((a >> 2) & 1) - 1] for a in range(8)],
+                   dtype=np.float64)
+    K = np.zeros((E, 8, 3, 8, 3))
+    for gz in (-_GAUSS, _GAUSS):
+        for gy in (-_GAUSS, _GAUSS):
+            for gx in (-_GAUSS, _GAUSS):
+                g = np.array([gx, gy, gz])
+                f = 1.0 + sgn * g
+                dN = np.empty((8, 3))
+                dN[:, 0] = sgn[:, 0] * f[:, 1] * f[:, 2] / 8.0
+                dN[:, 1] = f[:, 0] * sgn[:, 1] * f[:, 2] / 8.0
+                dN[:, 2] = f[:, 0] * f[:, 1] * sgn[:, 2] / 8.0
+                J = np.einsum("eap,aq->epq", Xe, dN)
+                det = np.linalg.det(J)
+                if np.any(det <= 0.0):
+                    raise ValueError("inverted or degenerate hexahedron")
+                inv = np.linalg.inv(J)
+                G = np.einsum("aq,eqp->eap", dN, inv)             # physical gradients
+                w = det[:, None, None, None, None]
+                lap = np.einsum("eap,ebp->eab", G, G)
+                K += w * (lam * np.einsum("eap,ebq->eapbq", G, G) + mu * np.einsum("eaq,ebp->eapbq", G, G)
+                          + mu * lap[:, :, None, :, None] * np.eye(3)[None, None, :, None, :])
+    return K.reshape(E, 24, 24)
+
+
+def elasticity_box(hx, hy, hz, E: float = 1.0, nu: float = 0.3, clamp: bool = True) -> CSR:
+    """3D linear elasticity on the tensor mesh with element sizes hx, hy, hz (Q1 hexahedra,
+    2x2x2 Gauss rule), three unknowns per node interleaved (unknown 3 v + c is displacement
+    component c of node v).  clamp: the nodes of the face x = 0 are fixed (eliminated), making
+    the operator positive definite; otherwise every node is kept (the six rigid-body motions
+    span the kernel).  meta: "coords" (per node), "block_size" 3, "rbm" (n x 6, column-major
+    as 6 vectors of length n: translations x, y, z, then rotations about the z, x and y axes
+    through the centroid of the kept nodes)."""
+    hx, hy, hz = (np.asarray(h, dtype=np.float64) for h in (hx, hy, hz))
+    ax = [np.r_[0.0, np.cumsum(h)] for h in (hx, hy, hz)]
+    nx1, ny1, nz1 = (len(a) for a in ax)
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    nex, ney, nez = nx1 - 1, ny1 - 1, nz1 - 1
+    ne = nex * ney * nez
+    ei, ej, ek = np.meshgrid(np.arange(nex), np.arange(ney), np.arange(nez), indexing="xy")
+    ei = np.transpose(ei, (2, 0, 1)).ravel()
+    ej = np.transpose(ej, (2, 0, 1)).ravel()
+    ek = np.transpose(ek, (2, 0, 1)).ravel()
+    nodes = np.empty((ne, 8), dtype=np.int64)
+    Xe = np.empty((ne, 8, 3))
+    for a in range(8):
+        ii, jj, kk = ei + (a & 1), ej + ((a >> 1) & 1), ek + ((a >> 2) & 1)
+        nodes[:, a] = ii + nx1 * (jj + ny1 * kk)
+        Xe[:, a, 0] = X[kk, jj, ii]
+        Xe[:, a, 1] = Y[kk, jj, ii]
+        Xe[:, a, 2] = Z[kk, jj, ii]
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    mu = E / (2.0 * (1.0 + nu))
+    Ke = _hex_elasticity_matrices(Xe, lam, mu)
+    keep_node = np.ones((nz1, ny1, nx1), dtype=bool)
+    if clamp:
+        keep_node[:, :, 0] = False
+    keep_node = keep_node.ravel()
+    num = np.full(keep_node.size, -1, dtype=np.int64)
+    num[keep_node] = np.arange(int(keep_node.sum()))
+    nn = int(keep_node.sum())
+    n = 3 * nn
+    dof = np.where(num[nodes][:, :, None] >= 0, 3 * num[nodes][:, :, None] + np.arange(3)[None, None, :], -1)
+    dof = dof.reshape(ne, 24)
+    rows = np.repeat(dof, 24, axis=1).ravel()
+    cols = np.tile(dof, (1, 24)).ravel()
+    vals = Ke.reshape(ne, 576).ravel()
+    keep = (rows >= 0) & (cols >= 0)
+    rows, cols, vals = rows[keep], cols[keep], vals[keep]
+    elem = np.repeat(np.arange(ne), 576)[keep]
+    order = np.lexsort((elem, cols, rows))                    # by row, column, element
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    key = rows * n + cols
+    start = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    cnt = np.diff(np.r_[start, key.size])
+    acc = vals[start].copy()
+    for k in range(1, int(cnt.max()) if cnt.size else 1):   # contributions in element order
+        m = cnt > k
+        acc[m] = acc[m] + vals[start[m] + k]
+    urow = rows[start]
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, urow + 1, 1)
+    row_ptr = np.cumsum(row_ptr)
+    coords = np.stack([X.ravel()[keep_node], Y.ravel()[keep_node], Z.ravel()[keep_node]], axis=1)
+    return CSR(n, row_ptr, cols[start].astype(np.int32), acc,
+               meta={"coords": coords, "block_size": 3, "rbm": rigid_body_modes(coords),
+                     "grid": (nx1, ny1, nz1), "family": "elasticity", "E": E, "nu": nu, "clamp": clamp})
+
+
+def rigid_body_modes(coords: np.ndarray) -> np.ndarray:
+    """The six rigid-body motions of nodes at coords (nn x 3) as 6 vectors of length 3 nn,
+    stored one after another (unknown 3 v + c = component c of node v): translations along
+    x, y, z, then rotations about the z, x and y axes through the centroid."""
+    nn = coords.shape[0]
+    c = coords - coords.mean(axis=0)
+    x, y, z = c[:, 0], c[:, 1], c[:, 2]
+    B = np.zeros((6, nn, 3))
+    for t in range(3):
+        B[t, :, t] = 1.0
+    B[3, :, 0], B[3, :, 1] = -y, x          # about z
+    B[4, :, 1], B[4, :, 2] = -z, y          # about x
+    B[5, :, 0], B[5, :, 2] = z, -x          # about y
+    return np.ascontiguousarray(B.reshape(6, 3 * nn))
+
+
+def workload_elasticity(N: int = 40):
+    """Cantilever-like elasticity block: N^3 unit elements, E = 1, nu = 0.3, face x = 0 clamped
+    (N (N+1)^2 nodes, three unknowns each); near-null space = the six rigid-body modes;
+    theta = 0.02, traditional SA; RHS seed 6."""
+    h = np.ones(N)
+    A = elasticity_box(h, h, h)
+    return A, rhs_uniform(A.n, 6), dict(theta=0.02, variants=0, block_size=3, nullspace_dim=6)
+
+
 def perturbed_cube(ne: int = 60, seed: int = 5, amplitude: float = 0.2, zscale: float = 100.0) -> CSR:
     """§3.1's randomly perturbed cube: the Laplacian on [0,1] x [0,1] x [0,zscale] with ne
     elements per direction; every node of the uniform grid moves along each axis by
@@ -555,5 +675,6 @@ __all__ = [
     "workload_stretched64", "workload_randcoef128", "batched_systems", "serving_stream", "make_operator",
     "VARIANT_BITS",
     "variants_mask", "dirichlet_stencil_row", "hex_q1_matrix", "perturbed_cube", "graded_sizes",
-    "graded_cube", "convection_diffusion_box", "workload_convdiff64",
+    "graded_cube", "convection_diffusion_box", "workload_convdiff64", "elasticity_box", "rigid_body_modes",
+    "workload_elasticity",
 ]
