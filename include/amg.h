@@ -78,6 +78,21 @@ enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
  * layout gives identical results; a copy costs 12 bytes per stored entry (16 with AMG_MIXED)
  * plus its padding. */
 enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_CSR = 1, AMG_LAYOUT_SELL = 2 };
+/* Systems of PDEs (block_size > 1 or nullspace_dim > 1; the paper treats scalar PDEs and leaves
+ * systems to future work).  Unknown bs v + c is component c of node v (n a multiple of bs).
+ * The near-null space passed to amg_setup is then nullspace_dim vectors of length n, one after
+ * another (NULL: the constant of each component, which needs nullspace_dim = block_size).
+ * Strength is decided between nodes: the Frobenius norm F_IJ of the bs x bs block coupling
+ * nodes I and J stands for |a_ij| in Eq. (7), F_II and F_JJ for a_ii and a_jj; entries inside
+ * a node's block are never dropped.  Aggregation is the distance-2 MIS of the strong node graph.
+ * Each aggregate's block of B (its nodes' unknowns, nodes and components ascending) is factored
+ * by modified Gram-Schmidt, B_a = Q_a R_a: the tentative prolongator holds Q_a and the coarse
+ * near-null space is R_a.  P = Pt - omega Dbar^-1 Abar Pt as for scalar problems.  The four
+ * adaptations (variants) and the distance strength are not defined for systems: a non-zero
+ * variants or AMG_STRENGTH_DISTANCE gives AMG_ERR_UNSUPPORTED, and so does an aggregate too
+ * small to carry k independent vectors (a column of its block left with norm <= 1e-12 of its
+ * norm before the projections).  amg_export's AMG_EX_AGG and AMG_EX_ROOT are then per node,
+ * AMG_EX_NULLSPACE holds the level's k vectors. */
 
 /* Square CSR matrix.  row_ptr has n+1 entries (row_ptr[0] = 0), columns are sorted
  * ascending within each row with no duplicates, and every row stores its diagonal.
@@ -115,6 +130,9 @@ typedef struct {
     int krylov;          /* AMG_KRYLOV_CG (symmetric operators) or AMG_KRYLOV_GMRES            */
     int restart;         /* GMRES restart length (30)                                         */
     int spmv_layout;     /* AMG_LAYOUT_AUTO (default), AMG_LAYOUT_CSR or AMG_LAYOUT_SELL       */
+    int block_size;      /* systems of PDEs: unknowns per node, interleaved (1: scalar; <= 16)  */
+    int nullspace_dim;   /* near-null-space vectors k (1; <= 8); coarse levels have k unknowns  */
+                         /*   per aggregate                                                   */
 } amg_params_t;
 
 typedef struct {

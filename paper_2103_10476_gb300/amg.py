@@ -54,7 +54,8 @@ class amg_params_t(C.Structure):
                 ("max_coarse", C.c_int), ("max_levels", C.c_int), ("precision", C.c_int), ("pt_scaling", C.c_int),
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int),
-                ("trace", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("spmv_layout", C.c_int)]
+                ("trace", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("spmv_layout", C.c_int),
+                ("block_size", C.c_int), ("nullspace_dim", C.c_int)]
 
 
 class amg_info_t(C.Structure):

@@ -21,6 +21,7 @@ SOURCES = {
     "util.cu": [],
     "setup.cu": ["--fmad=false"],
     "spgemm.cu": ["--fmad=false"],
+    "block.cu": ["--fmad=false"],
     "coarse.cu": [],
     "multi.cu": [],
     "gmres.cu": [],

@@ -145,6 +145,24 @@ uint64_t power_stream_seed(uint64_t seed, int level, int purpose);
 cudaError_t omega_from_lambda(const double *lambda_dev, double *omega_dev, cudaStream_t s);
 cudaError_t invert_diag(const double *d, double *inv, float *invf, int n, int *zero, cudaStream_t s);
 
+// --------------------------------------------------------------------------------- block.cu
+// systems of PDEs (bs unknowns per node, k near-null-space vectors): the node graph of bs x bs
+// blocks (counts, then columns, block Frobenius norms and each node's own norm), the block
+// strength, the per-entry masks of A, the QR tentative prolongator and P's combination
+int block_max_bs();
+int block_max_k();
+cudaError_t node_counts(const DevCsr &A, int bs, int *cnt, cudaStream_t s);
+cudaError_t node_fill(const DevCsr &A, int bs, const int *nrp, int *nci, double *nF, double *fdiag, cudaStream_t s);
+cudaError_t node_strength(int nn, const int *nrp, const int *nci, const double *nF, const double *fdiag, double theta,
+                          uint8_t *nstrong, cudaStream_t s);
+cudaError_t block_masks(const DevCsr &A, int bs, const int *nrp, const int *nci, const uint8_t *nstrong,
+                        uint8_t *strong, uint8_t *removed, int *kept, cudaStream_t s);
+cudaError_t block_tentative(int n, int bs, int k, int nagg, const int *mstart, const int *members, const double *B,
+                            double *W, double *Qv, double *Bc, int *bad, cudaStream_t s);
+cudaError_t block_pt(int n, int bs, int k, const int *agg, const double *Qv, DevCsr &Pt, cudaStream_t s);
+cudaError_t block_combine(int n, int bs, int k, const int *agg, const double *Qv, const double *Dsm,
+                          const double *omega, DevCsr &AP, cudaStream_t s);
+
 // --------------------------------------------------------------------------------- spgemm.cu
 // C = A B, allocating C's arrays with cudaMalloc.  On failure C is left empty.
 cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s);

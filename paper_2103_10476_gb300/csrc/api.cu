@@ -119,6 +119,14 @@ __global__ void ones_kernel(int n, double *b)
     if (i < n) b[i] = 1.0;
 }
 
+__global__ void component_ones_kernel(int n, int bs, int k, double *B)
+{
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * k) return;
+    const int j = (int)(t / n), i = (int)(t % n);
+    B[t] = (i % bs == j) ? 1.0 : 0.0;
+}
+
 // stored bytes of a device CSR (int32 row pointers and columns, double values)
 double csr_bytes(const DevCsr &c) { return 12.0 * (double)c.nnz + 4.0 * (c.n + 1); }
 
@@ -156,6 +164,10 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     uint8_t *drop = nullptr;
     double *px = nullptr, *py = nullptr, *scal = nullptr, *lvals = nullptr, *ldiag = nullptr;
     uint8_t *own_mask = nullptr;
+    int *nrp = nullptr, *nci = nullptr, *ptrp = nullptr, *ptci = nullptr;   // systems: node graph, Pt
+    double *nF = nullptr, *fdiag = nullptr, *W = nullptr, *Qv = nullptr, *ptv = nullptr;
+    uint8_t *nstrong = nullptr;
+    int nnz_n = 0;
     DevCsr AP, Ac;
     int hflags[5] = {0, 0, 0, 0, 0};
     SpmvPlan plan_bar;
@@ -167,6 +179,148 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(cudaMallocAsync(&kept, sizeof(int) * (size_t)(n + 1), s));
     CK(cudaMallocAsync(&flags, sizeof(int) * 5, s));
     CK(cudaMemsetAsync(flags, 0, sizeof(int) * 5, s));
+    if (h->block) {
+        // a system of PDEs: block strength between nodes, MIS-2 of the node graph, QR
+        // tentative prolongator, P = Pt - omega Dbar^-1 (Abar Pt)
+        const int bs = lv.bs, k = lv.k, nn = n / bs;
+        CK(cudaMallocAsync(&nrp, sizeof(int) * (size_t)(nn + 1), s));
+        CK(node_counts(A, bs, nrp, s));
+        CK(scan_exclusive(nrp, nrp, nn, s));
+        CK(cudaMemcpyAsync(&nnz_n, nrp + nn, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMallocAsync(&nci, sizeof(int) * (size_t)(nnz_n > 0 ? nnz_n : 1), s));
+        CK(cudaMallocAsync(&nF, sizeof(double) * (size_t)(nnz_n > 0 ? nnz_n : 1), s));
+        CK(cudaMallocAsync(&fdiag, sizeof(double) * (size_t)(nn > 0 ? nn : 1), s));
+        CK(cudaMallocAsync(&nstrong, (size_t)(nnz_n > 0 ? nnz_n : 1), s));
+        CK(node_fill(A, bs, nrp, nci, nF, fdiag, s));
+        CK(node_strength(nn, nrp, nci, nF, fdiag, p.theta, nstrong, s));
+        CK(block_masks(A, bs, nrp, nci, nstrong, lv.strong, lv.removed, kept, s));
+        DevCsr G;
+        G.n = nn;
+        G.ncol = nn;
+        G.nnz = nnz_n;
+        G.rp = nrp;
+        G.ci = nci;
+        CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(nn + 1), s));
+        CK(strong_graph_counts(G, nstrong, grp, s));
+        CK(scan_exclusive(grp, grp, nn, s));
+        CK(cudaMemcpyAsync(&nnz_g, grp + nn, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        CK(cudaMallocAsync(&gci, sizeof(int) * (size_t)(nnz_g > 0 ? nnz_g : 1), s));
+        CK(strong_graph_fill(G, nstrong, grp, gci, s));
+        trace_mark(h, L, AMG_PH_STRENGTH);
+        CK(dalloc(h, &lv.agg, (size_t)nn));
+        CK(dalloc(h, &lv.root, (size_t)nn));
+        CK(cudaMallocAsync(&t0, sizeof(unsigned long long) * (size_t)(nn > 0 ? nn : 1), s));
+        CK(cudaMallocAsync(&t1, sizeof(unsigned long long) * (size_t)(nn > 0 ? nn : 1), s));
+        CK(cudaMallocAsync(&rootof, sizeof(int) * (size_t)(nn + 1), s));
+        CK(cudaMallocAsync(&join1, sizeof(int) * (size_t)(nn + 1), s));
+        {
+            AggWork w{t0, t1, rootof, join1, flags + 2};
+            cudaError_t e = aggregate_mis2(nn, grp, gci, p.seed, L, w, lv.agg, lv.root, &nagg, &rounds, s);
+            if (e == cudaErrorInvalidValue) { g_last_error = "aggregation left a node unassigned"; st = AMG_ERR_INTERNAL; goto done; }
+            CK(e);
+        }
+        lv.nagg = nagg;
+        trace_mark(h, L, AMG_PH_AGGREGATE);
+        if (nagg == 0 || (int64_t)nagg * k >= (int64_t)n) { *coarsest = 1; goto done; }
+        const int nc = nagg * k;
+        CK(cudaMallocAsync(&mstart, sizeof(int) * (size_t)(nagg + 1), s));
+        CK(cudaMallocAsync(&members, sizeof(int) * (size_t)nn, s));
+        CK(cudaMallocAsync(&fill, sizeof(int) * (size_t)(nagg + 1), s));
+        CK(aggregate_members(nn, nagg, lv.agg, mstart, members, fill, s));
+        CK(cudaMallocAsync(&W, sizeof(double) * (size_t)n * (size_t)k, s));
+        CK(cudaMallocAsync(&Qv, sizeof(double) * (size_t)n * (size_t)k, s));
+        CK(dalloc(h, &lv.Bc, (size_t)nc * (size_t)k));
+        CK(block_tentative(n, bs, k, nagg, mstart, members, lv.B, W, Qv, lv.Bc, flags + 0, s));
+        // filtered matrix: dropped entries lumped into the diagonal (Eq. 6)
+        lv.Abar.n = n;
+        lv.Abar.ncol = n;
+        CK(dalloc(h, &lv.Abar.rp, (size_t)n + 1));
+        CK(scan_exclusive(kept, lv.Abar.rp, n, s));
+        CK(cudaMemcpyAsync(&nnz_bar, lv.Abar.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 5, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hflags[0]) {
+            g_last_error = "an aggregate too small to carry the near-null space";
+            st = AMG_ERR_UNSUPPORTED;
+            goto done;
+        }
+        lv.Abar.nnz = nnz_bar;
+        CK(dalloc(h, &lv.Abar.ci, (size_t)nnz_bar));
+        CK(dalloc(h, &lv.Abar.v, (size_t)nnz_bar));
+        CK(dalloc(h, &lv.Dsm, (size_t)n));
+        CK(dalloc(h, &lv.lumpflag, (size_t)n));
+        CK(filter(A, lv.removed, 0, p.tau, 0, p.sigma, lv.Abar, lv.Dsm, lv.lumpflag, flags + 1, s));
+        CK(cudaMemcpyAsync(hflags, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (hflags[1]) { g_last_error = "zero diagonal in the filtered matrix"; st = AMG_ERR_ZERO_DIAG; goto done; }
+        trace_mark(h, L, AMG_PH_FILTER);
+        CK(cudaMallocAsync(&px, sizeof(double) * (size_t)n, s));
+        CK(cudaMallocAsync(&py, sizeof(double) * (size_t)n, s));
+        {
+            int np = 2 * spmv_partials_needed(n);
+            CK(cudaMallocAsync(&scal, sizeof(double) * (size_t)((np > kReduceBlocks ? np : kReduceBlocks) + 8), s));
+        }
+        {
+            SpmvPlan *pls[2] = {&plan_bar, &lv.plan_a};
+            const int *rps[2] = {lv.Abar.rp, A.rp};
+            const int ns[2] = {n, n};
+            const int64_t nz[2] = {lv.Abar.nnz, A.nnz};
+            CK(spmv_plans(2, pls, rps, ns, nz, s));
+        }
+        if (p.lambda_override > 0.0) {
+            lv.lambda_bar = p.lambda_override;
+        } else {
+            CK(power_lambda(lv.Abar, plan_bar, lv.Dsm, p.power_iters, power_stream_seed(p.seed, L, 1), px, py,
+                            scal + 8, scal, scal + 1, s));
+            CK(cudaMemcpyAsync(&lv.lambda_bar, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        if (!(lv.lambda_bar > 0.0) || !std::isfinite(lv.lambda_bar)) {
+            g_last_error = "eigenvalue estimate not positive";
+            st = AMG_ERR_EIGEN;
+            goto done;
+        }
+        lv.omega = 4.0 / (3.0 * lv.lambda_bar);
+        CK(cudaMemcpyAsync(scal + 2, &lv.omega, sizeof(double), cudaMemcpyHostToDevice, s));
+        trace_mark(h, L, AMG_PH_EIGEN);
+        {
+            DevCsr Pt;
+            Pt.n = n;
+            Pt.ncol = nc;
+            Pt.nnz = (int64_t)n * k;
+            CK(cudaMallocAsync(&ptrp, sizeof(int) * ((size_t)n + 17), s));
+            CK(cudaMallocAsync(&ptci, sizeof(int) * ((size_t)n * k + 16), s));
+            CK(cudaMallocAsync(&ptv, sizeof(double) * ((size_t)n * k + 16), s));
+            Pt.rp = ptrp;
+            Pt.ci = ptci;
+            Pt.v = ptv;
+            CK(block_pt(n, bs, k, lv.agg, Qv, Pt, s));
+            cudaError_t e = spgemm(lv.Abar, Pt, lv.P, &ovf, s);
+            if (e == cudaErrorInvalidValue && ovf) { g_last_error = "hash table overflow in Abar*Pt"; st = AMG_ERR_INTERNAL; goto done; }
+            CK(e);
+            own(h, lv.P);
+            nnz_p = (int)lv.P.nnz;
+        }
+        CK(block_combine(n, bs, k, lv.agg, Qv, lv.Dsm, scal + 2, lv.P, s));
+        CK(dalloc(h, &lv.cflag, (size_t)n));
+        CK(cudaMemsetAsync(lv.cflag, 0, (size_t)n, s));
+        lv.R.n = nc;
+        lv.R.ncol = n;
+        lv.R.nnz = nnz_p;
+        CK(dalloc(h, &lv.R.rp, (size_t)nc + 1));
+        CK(dalloc(h, &lv.R.ci, (size_t)nnz_p));
+        CK(dalloc(h, &lv.R.v, (size_t)nnz_p));
+        CK(transpose_counts(lv.P, lv.R.rp, s));
+        CK(scan_exclusive(lv.R.rp, lv.R.rp, nc, s));
+        CK(cudaFreeAsync(fill, s));
+        fill = nullptr;
+        CK(cudaMallocAsync(&fill, sizeof(int) * (size_t)(nc + 1), s));
+        CK(transpose_fill(lv.P, lv.R, fill, s));
+        trace_mark(h, L, AMG_PH_PROLONG);
+        goto galerkin;
+    }
     // Eq. (7), on A or (§3.1) on the distance Laplacian of the level's coordinates
     if (p.strength == AMG_STRENGTH_DISTANCE) {
         CK(cudaMallocAsync(&lvals, sizeof(double) * (size_t)(A.nnz > 0 ? A.nnz : 1), s));
@@ -316,6 +470,7 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
     CK(scan_exclusive(lv.R.rp, lv.R.rp, nagg, s));
     CK(transpose_fill(lv.P, lv.R, fill, s));
     trace_mark(h, L, AMG_PH_PROLONG);
+galerkin:
     // Galerkin product with the original A, Eq. (2)
     {
         cudaError_t e;
@@ -358,11 +513,18 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         nx.A = Ac;
         own(h, Ac);
         Ac = DevCsr();
-        CK(dalloc(h, &nx.B, (size_t)nagg));
-        if (p.pt_scaling == AMG_PT_ORTHONORMAL)
-            CK(cudaMemcpyAsync(nx.B, lv.nrm, sizeof(double) * (size_t)nagg, cudaMemcpyDeviceToDevice, s));
-        else if (nagg > 0) {
-            ones_kernel<<<grid_for(nagg, 256), 256, 0, s>>>(nagg, nx.B); note_launch();
+        nx.bs = lv.k;
+        nx.k = lv.k;
+        if (h->block) {
+            nx.B = lv.Bc;           // R_a of every aggregate: k vectors of length nagg k
+            lv.Bc = nullptr;
+        } else {
+            CK(dalloc(h, &nx.B, (size_t)nagg));
+            if (p.pt_scaling == AMG_PT_ORTHONORMAL)
+                CK(cudaMemcpyAsync(nx.B, lv.nrm, sizeof(double) * (size_t)nagg, cudaMemcpyDeviceToDevice, s));
+            else if (nagg > 0) {
+                ones_kernel<<<grid_for(nagg, 256), 256, 0, s>>>(nagg, nx.B); note_launch();
+            }
         }
         CK(cudaGetLastError());
     }
@@ -370,7 +532,9 @@ done:
     for (void *p : {(void *)kept, (void *)grp, (void *)gci, (void *)mstart, (void *)members, (void *)fill,
                     (void *)flags, (void *)t0, (void *)t1, (void *)rootof, (void *)join1, (void *)drop, (void *)px,
                     (void *)py, (void *)scal, (void *)AP.rp, (void *)AP.ci, (void *)AP.v, (void *)Ac.rp,
-                    (void *)Ac.ci, (void *)Ac.v, (void *)lvals, (void *)ldiag, (void *)own_mask})
+                    (void *)Ac.ci, (void *)Ac.v, (void *)lvals, (void *)ldiag, (void *)own_mask, (void *)nrp,
+                    (void *)nci, (void *)nF, (void *)fdiag, (void *)nstrong, (void *)W, (void *)Qv, (void *)ptrp,
+                    (void *)ptci, (void *)ptv})
         free_async(p, s);
     cudaStreamSynchronize(s);
     return st;
@@ -407,7 +571,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             v.x2 = lv.vx2;
             v.r = lv.vr;
             v.d = lv.vd;
-            v.nc = lv.nagg;
+            v.nc = lv.R.n;
             v.arp = lv.A.rp; v.aci = lv.A.ci;
             v.prp = lv.P.rp; v.pci = lv.P.ci;
             v.rrp = lv.R.rp; v.rci = lv.R.ci;
@@ -459,7 +623,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         for (int L = 0; L + 1 < h->nlev; ++L) {
             Level &lv = h->lev[L];
             pls.push_back(&lv.plan_p); rps.push_back(lv.P.rp); ns.push_back(lv.A.n); nz.push_back(lv.P.nnz);
-            pls.push_back(&lv.plan_r); rps.push_back(lv.R.rp); ns.push_back(lv.nagg); nz.push_back(lv.R.nnz);
+            pls.push_back(&lv.plan_r); rps.push_back(lv.R.rp); ns.push_back(lv.R.n); nz.push_back(lv.R.nnz);
         }
         if (h->nlev == 1 && n0 > 0) {
             pls.push_back(&h->plan0); rps.push_back(h->lev[0].A.rp); ns.push_back(n0); nz.push_back(h->lev[0].A.nnz);
@@ -679,6 +843,8 @@ void amg_params_default(amg_params_t *p)
     p->krylov = AMG_KRYLOV_CG;
     p->restart = 30;
     p->spmv_layout = AMG_LAYOUT_AUTO;
+    p->block_size = 1;
+    p->nullspace_dim = 1;
 }
 
 amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms)
@@ -782,10 +948,21 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         g_last_error = "parameter out of range";
         return AMG_ERR_INVALID_ARG;
     }
+    const bool block = p.block_size > 1 || p.nullspace_dim > 1;
+    if (p.block_size < 1 || p.block_size > block_max_bs() || p.nullspace_dim < 1 || p.nullspace_dim > block_max_k() ||
+        Ain->n % p.block_size != 0 || (block && !nullspace && p.nullspace_dim != p.block_size)) {
+        g_last_error = "block size or near-null-space dimension out of range (or no vectors given for k != bs)";
+        return AMG_ERR_INVALID_ARG;
+    }
+    if (block && (p.variants != 0 || p.strength != AMG_STRENGTH_MATRIX)) {
+        g_last_error = "systems of PDEs: the adaptations and the distance strength are defined for scalar problems";
+        return AMG_ERR_UNSUPPORTED;
+    }
     const double t_start = now_ms();
     keep_pool_memory();
     amg_hierarchy *h = new amg_hierarchy();
     h->p = p;
+    h->block = block;
     h->phase_t = t_start;
     h->s = (cudaStream_t)p.cuda_stream;
     amg_status_t st = AMG_OK;
@@ -828,14 +1005,20 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
             CK(cudaStreamSynchronize(s));
             if (hbad) { g_last_error = "columns unsorted, out of range, duplicated, or a missing diagonal"; st = AMG_ERR_INVALID_ARG; goto done; }
         }
-        CK(dalloc(h, &l0.B, (size_t)n));
+        l0.bs = p.block_size;
+        l0.k = p.nullspace_dim;
+        CK(dalloc(h, &l0.B, (size_t)n * (size_t)l0.k));
         if (coords && n > 0) {
             h->dim = dim;
             CK(dalloc(h, &l0.coords, (size_t)n * (size_t)dim));
             CK(copy_to_device(l0.coords, coords, sizeof(double) * (size_t)n * (size_t)dim, s));
         }
-        if (nullspace) CK(copy_to_device(l0.B, nullspace, sizeof(double) * (size_t)n, s));
-        else if (n > 0) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
+        if (nullspace) CK(copy_to_device(l0.B, nullspace, sizeof(double) * (size_t)n * (size_t)l0.k, s));
+        else if (n > 0 && !block) { ones_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, l0.B); note_launch(); }
+        else if (n > 0) {
+            // the constant of each component: vector j is 1 on the unknowns of component j
+            component_ones_kernel<<<grid_for((int64_t)n * l0.k, 256), 256, 0, s>>>(n, l0.bs, l0.k, l0.B); note_launch();
+        }
         CK(cudaGetLastError());
         h->fine_nnz = nnz;
         trace_mark(h, 0, AMG_PH_INPUT);
@@ -1048,7 +1231,7 @@ ExportSrc export_src(const amg_hierarchy *h, int level, int what)
     case AMG_EX_A_ROWPTR: return rowptr(lv.A, lv.A.n);
     case AMG_EX_A_COL: return arr(lv.A.ci, lv.A.nnz, 4);
     case AMG_EX_A_VAL: return arr(lv.A.v, lv.A.nnz, 8);
-    case AMG_EX_NULLSPACE: return arr(lv.B, lv.A.n, 8);
+    case AMG_EX_NULLSPACE: return arr(lv.B, (int64_t)lv.A.n * lv.k, 8);
     case AMG_EX_COORDS: return arr(lv.coords, (int64_t)lv.A.n * h->dim, 8);
     default: break;
     }
@@ -1060,8 +1243,8 @@ ExportSrc export_src(const amg_hierarchy *h, int level, int what)
     case AMG_EX_ABAR_ROWPTR: return rowptr(lv.Abar, lv.Abar.n);
     case AMG_EX_ABAR_COL: return arr(lv.Abar.ci, lv.Abar.nnz, 4);
     case AMG_EX_ABAR_VAL: return arr(lv.Abar.v, lv.Abar.nnz, 8);
-    case AMG_EX_AGG: return arr(lv.agg, lv.A.n, 4);
-    case AMG_EX_ROOT: return arr(lv.root, lv.A.n, 1);
+    case AMG_EX_AGG: return arr(lv.agg, lv.A.n / lv.bs, 4);
+    case AMG_EX_ROOT: return arr(lv.root, lv.A.n / lv.bs, 1);
     case AMG_EX_P_ROWPTR: return rowptr(lv.P, lv.P.n);
     case AMG_EX_P_COL: return arr(lv.P.ci, lv.P.nnz, 4);
     case AMG_EX_P_VAL: return arr(lv.P.v, lv.P.nnz, 8);

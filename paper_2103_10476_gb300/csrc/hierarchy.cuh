@@ -28,6 +28,8 @@ struct Level {
     float *invdiag_f = nullptr, *Af = nullptr, *Pf = nullptr, *Rf = nullptr;
     void *vf = nullptr, *vx = nullptr, *vx2 = nullptr, *vr = nullptr, *vd = nullptr;   // solve vectors
     SpmvPlan plan_a, plan_p, plan_r;
+    int bs = 1, k = 1;        // unknowns per node; near-null-space vectors (B is n x k)
+    double *Bc = nullptr;     // systems: the coarse near-null space formed with P
 };
 
 }  // namespace amgk
@@ -42,6 +44,7 @@ struct amg_hierarchy {
     cudaStream_t s = nullptr;
     int nlev = 0;
     int dim = 0;                // coordinates per row (0: none given)
+    bool block = false;         // a system of PDEs (block_size > 1 or nullspace_dim > 1)
     Level lev[32];
     std::vector<void *> allocs;
     double *coarse_inv = nullptr;

@@ -411,8 +411,9 @@ cudaError_t multi_alloc(amg_hierarchy *h, MultiWork &w, int K)
     const size_t n0 = (size_t)h->lev[0].A.n * K;
     for (double **v : {&w.b, &w.xs, &w.rs, &w.zb[0], &w.zb[1], &w.p, &w.q, &w.t})
         AMG_CUDA_TRY(al((void **)v, n0 * sizeof(double)));
+    // the products' partials: one slot per block at the most lanes per row (8 rows per block)
     int maxb = kReduceBlocks;
-    for (int L = 0; L < h->nlev; ++L) maxb = std::max(maxb, (h->lev[L].A.n + 127) / 128 + 1);
+    for (int L = 0; L < h->nlev; ++L) maxb = std::max(maxb, (h->lev[L].A.n + kMT / 32 - 1) / (kMT / 32) + 1);
     w.nparts = maxb;
     for (double **v : {&w.partial, &w.pa, &w.pb, &w.rr, &w.tt, &w.bb})
         AMG_CUDA_TRY(al((void **)v, sizeof(double) * (size_t)K * maxb));

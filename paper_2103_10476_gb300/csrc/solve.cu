@@ -560,7 +560,9 @@ cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, con
                                          counter);
 }
 
-int spmv_partials_needed(int n) { return spmv_blocks(n, 2) + 1; }
+// per-block partial sums of a product over n rows: as many as blocks at the most lanes per row
+// (fewest rows per block) any plan chooses, plus one
+int spmv_partials_needed(int n) { return spmv_blocks(n, 32) + 1; }
 
 int sell_slices(int n) { return n > 0 ? (n + kSliceRows - 1) / kSliceRows : 0; }
 

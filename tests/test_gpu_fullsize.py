@@ -3,7 +3,8 @@ right-hand side and solution resident on the device, the solve on torch's curren
 
 stretched64 (262,144 unknowns, 6.86M entries; the five methods the benchmark steps through),
 randcoef128 (2,097,152 unknowns, 55.7M entries; 1Norm + OffLmp, FP64 and mixed) and the
-nonsymmetric convdiff64 (262,144 unknowns; GMRES(30), FP64 and mixed): the whole hierarchy
+nonsymmetric convdiff64 (262,144 unknowns; GMRES(30), FP64 and mixed) and the elasticity
+system (201,720 unknowns, three per node, six rigid-body modes; FP64 and mixed): the whole hierarchy
 against the oracle's (integer structures bit-exact, values within VAL_TOL), PCG or GMRES
 iterations by the rule of the small-size tests, solutions within SOL_TOL, and the
 relative residual ||b - A x|| / ||b|| recomputed here on the host with scipy.
@@ -115,3 +116,32 @@ def test_convdiff64_gmres_matches_oracle_fp64_and_mixed(amg, oracle_lib):
     amg.amg_free(hm)
     assert infom.status == 0 and abs(infom.iters - oinfo.iters) <= 2, (infom.iters, oinfo.iters)
     assert _relres(A, xm, b) <= 1.01 * TOL
+
+
+def test_elasticity40_matches_oracle_fp64_and_mixed(amg, oracle_lib):
+    # the systems line of the benchmark: 3D elasticity, six rigid-body modes
+    A, b, kw = P.workload_elasticity()
+    B = A.meta["rbm"]
+    import torch
+    stream = torch.cuda.current_stream()
+    rp, ci, v = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A.row_ptr, A.col, A.val))
+    Bd = torch.from_numpy(np.ascontiguousarray(B).reshape(-1)).cuda()
+    bd = torch.from_numpy(b).cuda()
+    oh, ost = oracle_lib.setup(A, nullspace=B, **kw)
+    assert ost == 0
+    xo, oinfo, ostat = oh.solve(b, TOL)
+    for prec in (amg.AMG_FP64, amg.AMG_MIXED):
+        h = amg.amg_setup(amg.csr_arg(A.n, rp, ci, v), Bd,
+                          gpu_params(amg, cuda_stream=stream.cuda_stream, precision=prec, **kw))
+        if prec == amg.AMG_FP64:
+            bad = compare_hierarchies(h, oh)
+            assert not bad, bad[:8]
+        xd = torch.zeros_like(bd)
+        info = amg.amg_solve(h, bd, xd, TOL)
+        torch.cuda.synchronize()
+        amg.amg_free(h)
+        x = xd.cpu().numpy()
+        assert info.status == 0 and ostat == 0
+        assert abs(info.iters - oinfo.iters) <= (0 if prec == amg.AMG_FP64 else 1), (prec, info.iters, oinfo.iters)
+        assert _relres(A, x, b) <= 1.01 * TOL
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= (SOL_TOL if prec == amg.AMG_FP64 else 1e-6)
