@@ -673,7 +673,8 @@ def main():
     ap.add_argument("--systems-only", action="store_true", help="only the elasticity line, printed alone")
     ap.add_argument("--no-gmres", action="store_true", help="skip the nonsymmetric (GMRES) line")
     ap.add_argument("--gmres-only", action="store_true", help="only the nonsymmetric (GMRES) line, printed alone")
-    ap.add_argument("--serving", action="store_true", help="also serve the request stream (off by default)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
+    ap.add_argument("--serving-only", action="store_true", help="only the served stream, printed alone")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-fp64", action="store_true", help="serve the stream in FP64 as well as mixed")
@@ -689,6 +690,13 @@ def main():
         torch.cuda.set_device(local)
         from paper_2103_10476_gb300 import amg
         print(json.dumps(run_multi(args, amg, torch)), flush=True)
+        return 0
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2103_10476_gb300 import amg
+        print(json.dumps(run_serving(args, amg, args.serve_seconds,
+                                     ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])), flush=True)
         return 0
     if args.systems_only:
         import torch
@@ -840,7 +848,7 @@ def main():
     multi = None if args.no_multi else run_multi(args, amg, torch)
     gmres = None if args.no_gmres else run_gmres(args, amg, torch)
     systems = None if args.no_systems else run_systems(args, amg, torch)
-    serving = None if not args.serving else run_serving(args, amg, args.serve_seconds,
+    serving = None if args.no_serving else run_serving(args, amg, args.serve_seconds,
                                                         ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
 
     if rank != 0:
