@@ -35,6 +35,7 @@ VARIANT_SETS = {
     "stretched64": [("traditional", 0), ("1norm", 1), ("offlmp", 2), ("sprsfy", 4), ("cnstrnt", 8)],
     "randcoef128": [("1norm+offlmp", 3)],
     "laplace20": [("traditional", 0)],
+    "elasticity40": [("traditional", 0)],     # --once only (the systems line times it otherwise)
 }
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
@@ -55,6 +56,9 @@ def make_workload(name: str):
     elif name == "laplace20":
         A, b, cfg = P.workload_laplace20()
         theta = 0.0
+    elif name == "elasticity40":
+        A, b, cfg = P.workload_elasticity()
+        theta = cfg["theta"]
     else:
         raise SystemExit(f"unknown workload {name}")
     return A, b, theta
@@ -251,6 +255,7 @@ def workload_config(args):
                        "5 methods (traditional, 1Norm, OffLmp, Sprsfy, Cnstrnt) per step",
         "randcoef128": "Q1 FE diffusion, 128^3 interior nodes, coefficient 10^U(-3,3), theta=0.02, 1Norm+OffLmp",
         "laplace20": "Q1 FE Laplacian, 20^3 interior nodes, theta=0",
+        "elasticity40": "3D elasticity, 40^3 hexahedra, 3 unknowns per node, 6 rigid-body modes, theta=0.02",
     }[args.workload]
     return {"workload": args.workload, "description": desc, "precision": args.precision, "tol": TOL,
             "rhs": "uniform[-1,1) SplitMix64", "l2": "flushed (256 MiB write) before every timed step",
@@ -262,6 +267,7 @@ def workload_config(args):
 def run_once(args):
     """One setup + solve (or V-cycles) of one method: a bounded number of kernel launches for
     profiler captures (ncu) of the same code path the benchmark times."""
+    import numpy as np
     import torch
     from paper_2103_10476_gb300 import amg
     A, b, theta = make_workload(args.workload)
@@ -288,8 +294,12 @@ def run_once(args):
             amg.amg_free(ht)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    h = amg.amg_setup(arg, None, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec,
-                                                       spmv_layout=lay))
+    ns, block = None, {}
+    if "rbm" in A.meta:       # a system: three unknowns per node, the six rigid-body modes
+        ns = torch.from_numpy(np.ascontiguousarray(A.meta["rbm"]).reshape(-1)).cuda()
+        block = dict(block_size=3, nullspace_dim=6)
+    h = amg.amg_setup(arg, ns, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec,
+                                                     spmv_layout=lay, **block))
     torch.cuda.synchronize()
     out = {"workload": args.workload, "method": name, "layout": args.layout,
            "setup_ms": 1000 * (time.perf_counter() - t0)}
@@ -728,6 +738,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2103_10476_gb300 import amg
 
+    if args.workload == "elasticity40":
+        raise SystemExit("elasticity40 is timed by the systems line (--systems-only); use it with --once")
     A, b, theta = make_workload(args.workload)
     variants = VARIANT_SETS[args.workload]
     prec = amg.AMG_MIXED if args.precision == "mixed" else amg.AMG_FP64

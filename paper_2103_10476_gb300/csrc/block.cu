@@ -9,8 +9,10 @@
 //     components ascending) factored B_a = Q_a R_a by modified Gram-Schmidt; Pt holds Q_a,
 //     the coarse near-null space is R_a (k unknowns per aggregate on the coarse level);
 //   * P = Pt - omega Dbar^-1 (Abar Pt) with Abar Pt from the generic SpGEMM (Eq. 3).
-// Compiled without FMA contraction: every sum and product is rounded as written, in the
-// order stated, so structures and tentative-prolongator values match a sequential evaluation.
+// Compiled without FMA contraction: every sum and product is rounded as written.  The block
+// norms are summed in the stated order, so the strength decisions match a sequential
+// evaluation bit for bit; the QR's inner products are warp sums in a fixed order (values equal
+// to a sequential evaluation up to rounding).
 #include <climits>
 
 #include "amg_internal.cuh"
@@ -21,54 +23,66 @@ namespace {
 constexpr int kMaxBs = 16;     // unknowns per node at most
 constexpr int kMaxK = 8;       // near-null-space vectors at most
 
-// node I's bs rows merged: calls visit(J, p, end) for each coupled node J in ascending order,
-// with p[r] at row r's first entry of node J (entries of J are contiguous in a sorted row)
-template <typename Visit>
-__device__ __forceinline__ void merge_node_rows(const int *rp, const int *ci, int bs, int I, Visit visit)
+// One warp per node I: lane r < bs holds the cursor of row I bs + r; each step the warp takes
+// the smallest node id J under the cursors, every lane moves past J's entries in its row, and
+// lane 0 emits J (count only when nci is null).  Node ids ascend along a sorted row.
+__device__ __forceinline__ int warp_min_int(int v)
 {
-    int p[kMaxBs], end[kMaxBs];
-    for (int r = 0; r < bs; ++r) {
-        p[r] = rp[I * bs + r];
-        end[r] = rp[I * bs + r + 1];
-    }
-    for (;;) {
-        int J = INT_MAX;
-        for (int r = 0; r < bs; ++r)
-            if (p[r] < end[r]) J = min(J, ci[p[r]] / bs);
-        if (J == INT_MAX) break;
-        visit(J, p, end);
-        for (int r = 0; r < bs; ++r)
-            while (p[r] < end[r] && ci[p[r]] / bs == J) ++p[r];
-    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
-__global__ void node_count_kernel(int nn, const int *rp, const int *ci, int bs, int *cnt)
+__global__ void node_merge_kernel(int nn, const int *rp, const int *ci, int bs, const int *nrp, int *cnt, int *nci)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (I >= nn) return;
+    int p = 0, end = 0;
+    if (lane < bs) {
+        p = rp[I * bs + lane];
+        end = rp[I * bs + lane + 1];
+    }
     int c = 0;
-    merge_node_rows(rp, ci, bs, I, [&](int, const int *, const int *) { ++c; });
-    cnt[I] = c;
+    int out = nci ? nrp[I] : 0;
+    for (;;) {
+        const int head = p < end ? ci[p] / bs : INT_MAX;
+        const int J = warp_min_int(head);
+        if (J == INT_MAX) break;
+        while (p < end && ci[p] / bs == J) ++p;
+        if (nci && lane == 0) nci[out + c] = J;
+        ++c;
+    }
+    if (!nci && lane == 0) cnt[I] = c;
 }
 
-// nci, F_IJ (squares summed over the block's rows in order, each row's entries in order),
-// and F_II per node
-__global__ void node_fill_kernel(int nn, const int *rp, const int *ci, const double *v, int bs, const int *nrp,
-                                 int *nci, double *nF, double *fdiag)
+// one thread per node entry t = (I, J): F_IJ = sqrt of the squares of the block's entries,
+// summed over its rows in order and each row's entries in order (the columns J bs .. J bs +
+// bs - 1 of a sorted row are contiguous: found by binary search); F_II also to fdiag
+__global__ void node_norm_kernel(int nn, int64_t nnz_n, const int *rp, const int *ci, const double *v, int bs,
+                                 const int *nrp, const int *nci, double *nF, double *fdiag)
 {
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    if (I >= nn) return;
-    int t = nrp[I];
-    merge_node_rows(rp, ci, bs, I, [&](int J, const int *p, const int *end) {
-        double acc = 0.0;
-        for (int r = 0; r < bs; ++r)
-            for (int e = p[r]; e < end[r] && ci[e] / bs == J; ++e) acc = acc + v[e] * v[e];
-        const double f = sqrt(acc);
-        nci[t] = J;
-        nF[t] = f;
-        if (J == I) fdiag[I] = f;
-        ++t;
-    });
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nnz_n) return;
+    int lo = 0, hi = nn - 1;                     // node I: the last with nrp[I] <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (nrp[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int I = lo, J = nci[t];
+    const int c0 = J * bs, c1 = c0 + bs;
+    double acc = 0.0;
+    for (int r = 0; r < bs; ++r) {
+        int a = rp[I * bs + r], b = rp[I * bs + r + 1];
+        while (a < b) {                          // first entry with column >= c0
+            const int mid = (a + b) >> 1;
+            if (ci[mid] < c0) a = mid + 1; else b = mid;
+        }
+        for (int e = a; e < rp[I * bs + r + 1] && ci[e] < c1; ++e) acc = acc + v[e] * v[e];
+    }
+    const double f = sqrt(acc);
+    nF[t] = f;
+    if (J == I) fdiag[I] = f;
 }
 
 __global__ void node_strong_kernel(int nn, const int *nrp, const int *nci, const double *nF, const double *fdiag,
@@ -116,12 +130,23 @@ __global__ void block_masks_kernel(int n, const int *rp, const int *ci, int bs, 
     kept[i] = k;
 }
 
-// one thread per aggregate: B_a = Q_a R_a by modified Gram-Schmidt in column order; a column
-// left with norm <= 1e-12 of its norm before the projections marks *bad (rank-deficient)
+// fixed-order warp sum: each lane's partial over its rows t = lane, lane + 32, ... in order,
+// then a butterfly over the lanes (every lane receives the same total)
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// one warp per aggregate: B_a = Q_a R_a by modified Gram-Schmidt in column order, the rows
+// spread over the lanes (lane l owns rows l, l + 32, ...); a column left with norm <= 1e-12 of
+// its norm before the projections marks *bad (rank-deficient)
 __global__ void block_tentative_kernel(int n, int bs, int k, int nagg, const int *mstart, const int *members,
                                        const double *B, double *W, double *Qv, double *Bc, int *bad)
 {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (a >= nagg) return;
     const int m0 = mstart[a], m = (mstart[a + 1] - m0) * bs;
     double *w = W + (size_t)m0 * bs * k;
@@ -129,37 +154,40 @@ __global__ void block_tentative_kernel(int n, int bs, int k, int nagg, const int
     double R[kMaxK * kMaxK];
     for (int j = 0; j < k * k; ++j) R[j] = 0.0;
     for (int j = 0; j < k; ++j)
-        for (int t = 0; t < m; ++t) {
+        for (int t = lane; t < m; t += 32) {
             const int i = members[m0 + t / bs] * bs + t % bs;
             w[(size_t)j * m + t] = B[(size_t)j * n + i];
         }
     for (int j = 0; j < k; ++j) {
         double *wj = w + (size_t)j * m;
         double before = 0.0;
-        for (int t = 0; t < m; ++t) before = before + wj[t] * wj[t];
+        for (int t = lane; t < m; t += 32) before = before + wj[t] * wj[t];
+        before = warp_sum_d(before);
         for (int l = 0; l < j; ++l) {
             const double *wl = w + (size_t)l * m;
             double r = 0.0;
-            for (int t = 0; t < m; ++t) r = r + wl[t] * wj[t];
+            for (int t = lane; t < m; t += 32) r = r + wl[t] * wj[t];
+            r = warp_sum_d(r);
             R[l * k + j] = r;
-            for (int t = 0; t < m; ++t) wj[t] = wj[t] - r * wl[t];
+            for (int t = lane; t < m; t += 32) wj[t] = wj[t] - r * wl[t];
         }
         double s = 0.0;
-        for (int t = 0; t < m; ++t) s = s + wj[t] * wj[t];
+        for (int t = lane; t < m; t += 32) s = s + wj[t] * wj[t];
+        s = warp_sum_d(s);
         const double rjj = sqrt(s);
         if (!(rjj > 1e-12 * sqrt(before))) {
-            atomicAdd(bad, 1);
-            return;
+            if (lane == 0) atomicAdd(bad, 1);
+            return;                              // uniform over the warp
         }
-        for (int t = 0; t < m; ++t) wj[t] = wj[t] / rjj;
+        for (int t = lane; t < m; t += 32) wj[t] = wj[t] / rjj;
         R[j * k + j] = rjj;
     }
-    for (int t = 0; t < m; ++t) {
+    for (int t = lane; t < m; t += 32) {
         const int i = members[m0 + t / bs] * bs + t % bs;
         for (int j = 0; j < k; ++j) Qv[(size_t)i * k + j] = w[(size_t)j * m + t];
     }
-    for (int c = 0; c < k; ++c)
-        for (int j = 0; j < k; ++j) Bc[(size_t)c * nc + (size_t)a * k + j] = R[j * k + c];
+    if (lane < k)
+        for (int j = 0; j < k; ++j) Bc[(size_t)lane * nc + (size_t)a * k + j] = R[j * k + lane];
 }
 
 // Pt: row i holds k entries, columns agg(i/bs) k + j, values Qv[i k + j]
@@ -200,7 +228,7 @@ cudaError_t node_counts(const DevCsr &A, int bs, int *cnt, cudaStream_t s)
 {
     const int nn = A.n / bs;
     if (nn == 0) return cudaSuccess;
-    node_count_kernel<<<grid_for(nn, 128), 128, 0, s>>>(nn, A.rp, A.ci, bs, cnt); note_launch();
+    node_merge_kernel<<<grid_for((int64_t)nn * 32, 256), 256, 0, s>>>(nn, A.rp, A.ci, bs, nullptr, cnt, nullptr); note_launch();
     return cudaGetLastError();
 }
 
@@ -208,7 +236,13 @@ cudaError_t node_fill(const DevCsr &A, int bs, const int *nrp, int *nci, double 
 {
     const int nn = A.n / bs;
     if (nn == 0) return cudaSuccess;
-    node_fill_kernel<<<grid_for(nn, 128), 128, 0, s>>>(nn, A.rp, A.ci, A.v, bs, nrp, nci, nF, fdiag); note_launch();
+    node_merge_kernel<<<grid_for((int64_t)nn * 32, 256), 256, 0, s>>>(nn, A.rp, A.ci, bs, nrp, nullptr, nci); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    int64_t nnz_n = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&nnz_n, nrp + nn, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nnz_n == 0) return cudaSuccess;
+    node_norm_kernel<<<grid_for(nnz_n, 256), 256, 0, s>>>(nn, nnz_n, A.rp, A.ci, A.v, bs, nrp, nci, nF, fdiag); note_launch();
     return cudaGetLastError();
 }
 
@@ -233,7 +267,8 @@ cudaError_t block_tentative(int n, int bs, int k, int nagg, const int *mstart, c
                             double *W, double *Qv, double *Bc, int *bad, cudaStream_t s)
 {
     if (nagg == 0) return cudaSuccess;
-    block_tentative_kernel<<<grid_for(nagg, 64), 64, 0, s>>>(n, bs, k, nagg, mstart, members, B, W, Qv, Bc, bad); note_launch();
+    block_tentative_kernel<<<grid_for((int64_t)nagg * 32, 128), 128, 0, s>>>(n, bs, k, nagg, mstart, members, B, W, Qv,
+                                                                            Bc, bad); note_launch();
     return cudaGetLastError();
 }
 
