@@ -36,6 +36,7 @@ VARIANT_SETS = {
     "randcoef128": [("1norm+offlmp", 3)],
     "laplace20": [("traditional", 0)],
     "elasticity40": [("traditional", 0)],     # --once only (the systems line times it otherwise)
+    "convdiff64": [("1norm+offlmp", 3)],      # --once only (the GMRES line times it otherwise)
 }
 L2_BYTES = 129 * 1024 * 1024
 FALLBACK_HBM_GBS = 6800.0
@@ -59,6 +60,10 @@ def make_workload(name: str):
     elif name == "elasticity40":
         A, b, cfg = P.workload_elasticity()
         theta = cfg["theta"]
+    elif name == "convdiff64":
+        A, b, cfg = P.workload_convdiff64()
+        theta = cfg["theta"]
+        A.meta["krylov"] = (cfg["krylov"], cfg["restart"])
     else:
         raise SystemExit(f"unknown workload {name}")
     return A, b, theta
@@ -256,6 +261,7 @@ def workload_config(args):
         "randcoef128": "Q1 FE diffusion, 128^3 interior nodes, coefficient 10^U(-3,3), theta=0.02, 1Norm+OffLmp",
         "laplace20": "Q1 FE Laplacian, 20^3 interior nodes, theta=0",
         "elasticity40": "3D elasticity, 40^3 hexahedra, 3 unknowns per node, 6 rigid-body modes, theta=0.02",
+        "convdiff64": "convection-diffusion 64^3, theta=0.02, 1Norm+OffLmp, GMRES(30)",
     }[args.workload]
     return {"workload": args.workload, "description": desc, "precision": args.precision, "tol": TOL,
             "rhs": "uniform[-1,1) SplitMix64", "l2": "flushed (256 MiB write) before every timed step",
@@ -298,6 +304,8 @@ def run_once(args):
     if "rbm" in A.meta:       # a system: three unknowns per node, the six rigid-body modes
         ns = torch.from_numpy(np.ascontiguousarray(A.meta["rbm"]).reshape(-1)).cuda()
         block = dict(block_size=3, nullspace_dim=6)
+    if "krylov" in A.meta:    # a nonsymmetric operator: flexible GMRES
+        block = dict(krylov=A.meta["krylov"][0], restart=A.meta["krylov"][1])
     h = amg.amg_setup(arg, ns, amg.amg_params_default(theta=theta, variants=variants[name], precision=prec,
                                                      spmv_layout=lay, **block))
     torch.cuda.synchronize()
@@ -738,8 +746,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2103_10476_gb300 import amg
 
-    if args.workload == "elasticity40":
-        raise SystemExit("elasticity40 is timed by the systems line (--systems-only); use it with --once")
+    if args.workload in ("elasticity40", "convdiff64"):
+        raise SystemExit(f"{args.workload} is timed by its own line (--systems-only, --gmres-only); use it with --once")
     A, b, theta = make_workload(args.workload)
     variants = VARIANT_SETS[args.workload]
     prec = amg.AMG_MIXED if args.precision == "mixed" else amg.AMG_FP64

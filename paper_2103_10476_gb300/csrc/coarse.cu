@@ -393,6 +393,13 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
             newton32_check_kernel<<<1, 1, 0, s>>>(st); note_launch();
             newton_gemm_kernel<float, 1><<<grd, blk, 0, s>>>(n, cur, Rf, nxt, st); note_launch();
             std::swap(cur, nxt);
+            if ((k & 7) == 7 && k + 1 < kGeneral32) {
+                // every 8 steps: stop once converged (the steps after it would only copy)
+                NewtonState now{};
+                AMG_CUDA_TRY(cudaMemcpyAsync(&now, st, sizeof now, cudaMemcpyDeviceToHost, s));
+                AMG_CUDA_TRY(cudaStreamSynchronize(s));
+                if (now.done) break;
+            }
         }
         convert_dense_kernel<float, double><<<cgrid, 256, 0, s>>>(nn, cur, X); note_launch();
         AMG_CUDA_TRY(cudaGetLastError());

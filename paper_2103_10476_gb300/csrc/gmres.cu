@@ -67,16 +67,40 @@ __device__ __forceinline__ double block_sum_g(double v)
     return r;
 }
 
-// partial[i * gridDim + block] = sum over the block's rows of V_i . w, i < nv
+// partial[i * gridDim + block] = sum over the block's rows of V_i . w, i < nv.  Up to kGC basis
+// vectors per pass over w; each vector's sum has the order of a one-vector block sum (thread
+// partials over the grid stride, then lanes by shuffles, then the warps in order)
+constexpr int kGC = 8;
 __global__ void __launch_bounds__(kGT) gs_dots_kernel(int n, const double *V, int nv, const double *w,
                                                       double *partial)
 {
-    for (int i = 0; i < nv; ++i) {
-        const double *vi = V + (size_t)i * n;
-        double acc = 0.0;
-        for (int e = blockIdx.x * kGT + threadIdx.x; e < n; e += gridDim.x * kGT) acc += vi[e] * w[e];
-        const double t = block_sum_g(acc);
-        if (threadIdx.x == 0) partial[(size_t)i * gridDim.x + blockIdx.x] = t;
+    __shared__ double sh[kGC][kGT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = 0; i0 < nv; i0 += kGC) {
+        const int c = min(kGC, nv - i0);
+        double acc[kGC];
+#pragma unroll
+        for (int q = 0; q < kGC; ++q) acc[q] = 0.0;
+        for (int e = blockIdx.x * kGT + threadIdx.x; e < n; e += gridDim.x * kGT) {
+            const double we = w[e];
+#pragma unroll
+            for (int q = 0; q < kGC; ++q)
+                if (q < c) acc[q] += V[(size_t)(i0 + q) * n + e] * we;
+        }
+#pragma unroll
+        for (int q = 0; q < kGC; ++q) {
+            double v = acc[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[q][warp] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < c) {
+            double t = 0.0;
+            for (int k = 0; k < kGT / 32; ++k) t += sh[threadIdx.x][k];
+            partial[(size_t)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
     }
 }
 
