@@ -29,7 +29,7 @@ struct GmresWork {
     int m = 0, n = 0;
     int slot = 0;                     // doubles per step slot: 2 (m+1) projections, then |w|^2
     double *V = nullptr, *Z = nullptr, *w = nullptr;   // V: (m+1) x n, Z: m x n
-    double *partial = nullptr;        // kReduceBlocks x (m+1)
+    double *partial = nullptr;        // kDotBlocks x (m+1)
     double *hd = nullptr;             // device: m step slots, then r.r of the cycle's start
     double *yd = nullptr;             // device copy of y
     double *host = nullptr;           // pinned: m step slots, r.r, then y (m values)
@@ -42,6 +42,7 @@ struct GmresWork {
 namespace {
 
 constexpr int kGT = 256;
+constexpr int kDotBlocks = kReduceBlocks;   // Gram-Schmidt dot products: 2 blocks of 256 per SM
 
 double now_ms_g()
 {
@@ -68,32 +69,64 @@ __device__ __forceinline__ double block_sum_g(double v)
 }
 
 // partial[i * gridDim + block] = sum over the block's rows of V_i . w, i < nv.  Up to kGC basis
-// vectors per pass over w; each vector's sum has the order of a one-vector block sum (thread
-// partials over the grid stride, then lanes by shuffles, then the warps in order)
+// vectors per pass over w.  Each thread accumulates its grid-stride entries in ascending order,
+// kGU strides' loads issued together; the warp then reduces all kGC sums at once by a transposing
+// butterfly (after the exchanges at distances 16, 8 and 4, lane L holds a quarter-warp sum of
+// vector L/4; distances 2 and 1 finish it): 9 FP64 additions a lane instead of 5 per vector, which
+// matters where FP64 issues at a small fraction of the FP32 rate; the block adds its warps in order.
 constexpr int kGC = 8;
+constexpr int kGU = 4;
 __global__ void __launch_bounds__(kGT) gs_dots_kernel(int n, const double *V, int nv, const double *w,
                                                       double *partial)
 {
     __shared__ double sh[kGC][kGT / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const size_t stride = (size_t)gridDim.x * kGT;
     for (int i0 = 0; i0 < nv; i0 += kGC) {
         const int c = min(kGC, nv - i0);
+        const double *Vb = V + (size_t)i0 * n;
         double acc[kGC];
 #pragma unroll
         for (int q = 0; q < kGC; ++q) acc[q] = 0.0;
-        for (int e = blockIdx.x * kGT + threadIdx.x; e < n; e += gridDim.x * kGT) {
-            const double we = w[e];
+        for (size_t e0 = (size_t)blockIdx.x * kGT + threadIdx.x; e0 < (size_t)n; e0 += kGU * stride) {
+            double we[kGU], vv[kGU][kGC];
 #pragma unroll
-            for (int q = 0; q < kGC; ++q)
-                if (q < c) acc[q] += V[(size_t)(i0 + q) * n + e] * we;
+            for (int u = 0; u < kGU; ++u) {
+                const size_t e = e0 + u * stride;
+                const bool in = e < (size_t)n;
+                we[u] = in ? w[e] : 0.0;
+#pragma unroll
+                for (int q = 0; q < kGC; ++q) vv[u][q] = (in && q < c) ? Vb[(size_t)q * n + e] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kGU; ++u)
+                if (e0 + u * stride < (size_t)n) {
+#pragma unroll
+                    for (int q = 0; q < kGC; ++q)
+                        if (q < c) acc[q] += vv[u][q] * we[u];
+                }
+        }
+        const unsigned full = 0xffffffffu;
+        const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+        double r4[4], r2[2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const double keep = b4 ? acc[j + 4] : acc[j], send = b4 ? acc[j] : acc[j + 4];
+            r4[j] = keep + __shfl_xor_sync(full, send, 16);
         }
 #pragma unroll
-        for (int q = 0; q < kGC; ++q) {
-            double v = acc[q];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[q][warp] = v;
+        for (int j = 0; j < 2; ++j) {
+            const double keep = b3 ? r4[j + 2] : r4[j], send = b3 ? r4[j] : r4[j + 2];
+            r2[j] = keep + __shfl_xor_sync(full, send, 8);
         }
+        double r1;
+        {
+            const double keep = b2 ? r2[1] : r2[0], send = b2 ? r2[0] : r2[1];
+            r1 = keep + __shfl_xor_sync(full, send, 4);
+        }
+        r1 += __shfl_xor_sync(full, r1, 2);
+        r1 += __shfl_xor_sync(full, r1, 1);
+        if ((lane & 3) == 0) sh[lane >> 2][warp] = r1;
         __syncthreads();
         if (threadIdx.x < c) {
             double t = 0.0;
@@ -114,22 +147,42 @@ __global__ void __launch_bounds__(kGT) gs_reduce_kernel(const double *partial, i
     if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
-// w -= sum_i h_i V_i (per entry, i ascending)
-__global__ void gs_update_kernel(int n, const double *V, int nv, const double *h, double *w)
+// w -= sum_i h_i V_i (per entry, i ascending); the coefficients staged in shared memory
+constexpr int kMaxBasis = 513;
+__global__ void __launch_bounds__(256) gs_update_kernel(int n, const double *V, int nv, const double *h,
+                                                        double *w)
 {
+    __shared__ double hs[kMaxBasis];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         double t = w[e];
-        for (int i = 0; i < nv; ++i) t = t - h[i] * V[(size_t)i * n + e];
+        int i = 0;
+        for (; i + 4 <= nv; i += 4) {
+            const double a0 = V[(size_t)i * n + e], a1 = V[(size_t)(i + 1) * n + e],
+                         a2 = V[(size_t)(i + 2) * n + e], a3 = V[(size_t)(i + 3) * n + e];
+            t = t - hs[i] * a0;
+            t = t - hs[i + 1] * a1;
+            t = t - hs[i + 2] * a2;
+            t = t - hs[i + 3] * a3;
+        }
+        for (; i < nv; ++i) t = t - hs[i] * V[(size_t)i * n + e];
         w[e] = t;
     }
 }
 
-// v = w / sqrt(*nrm2) (v = 0 when the norm is 0: the step before broke down and the host stops)
-__global__ void scale_norm_kernel(int n, const double *w, const double *nrm2, double *v)
+// v = w * (1 / sqrt(*nrm2)), the reciprocal formed once per block (v = 0 when the norm is 0: the
+// step before broke down and the host stops)
+__global__ void __launch_bounds__(256) scale_norm_kernel(int n, const double *w, const double *nrm2, double *v)
 {
-    const double nrm = sqrt(*nrm2);
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        v[e] = nrm > 0.0 ? w[e] / nrm : 0.0;
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(*nrm2);
+        inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+    __syncthreads();
+    const double r = inv;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) v[e] = w[e] * r;
 }
 
 // x += sum_k y_k Z_k (per entry, k ascending)
@@ -171,7 +224,7 @@ cudaError_t gmres_alloc(amg_hierarchy *h, GmresWork &g, int m)
     AMG_CUDA_TRY(al((void **)&g.V, sizeof(double) * nn * (size_t)(m + 1)));
     AMG_CUDA_TRY(al((void **)&g.Z, sizeof(double) * nn * (size_t)m));
     AMG_CUDA_TRY(al((void **)&g.w, sizeof(double) * nn));
-    AMG_CUDA_TRY(al((void **)&g.partial, sizeof(double) * (size_t)kReduceBlocks * (size_t)(m + 1)));
+    AMG_CUDA_TRY(al((void **)&g.partial, sizeof(double) * (size_t)kDotBlocks * (size_t)(m + 1)));
     AMG_CUDA_TRY(al((void **)&g.hd, sizeof(double) * ((size_t)m * g.slot + 1)));
     AMG_CUDA_TRY(al((void **)&g.yd, sizeof(double) * (size_t)(m + 1)));
     AMG_CUDA_TRY(cudaMallocHost(&g.host, sizeof(double) * ((size_t)m * g.slot + 1 + (size_t)m)));
@@ -196,8 +249,8 @@ cudaError_t step_body(amg_hierarchy *h, GmresWork &W, int j, cudaStream_t st)
     const int nv = j + 1;
     for (int pass = 0; pass < 2; ++pass) {
         double *hp = slot + (size_t)pass * (m + 1);
-        gs_dots_kernel<<<kReduceBlocks, kGT, 0, st>>>(n, W.V, nv, W.w, W.partial); note_launch();
-        gs_reduce_kernel<<<nv, kGT, 0, st>>>(W.partial, kReduceBlocks, hp); note_launch();
+        gs_dots_kernel<<<kDotBlocks, kGT, 0, st>>>(n, W.V, nv, W.w, W.partial); note_launch();
+        gs_reduce_kernel<<<nv, kGT, 0, st>>>(W.partial, kDotBlocks, hp); note_launch();
         gs_update_kernel<<<gp, 256, 0, st>>>(n, W.V, nv, hp, W.w); note_launch();
     }
     AMG_CUDA_TRY(cudaGetLastError());
