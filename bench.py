@@ -165,8 +165,10 @@ def measured_peaks():
 
 # the sources each timed kernel class is compiled from (its kernels, launch code and headers)
 KERNEL_SOURCES = {
-    "vcycle_fine_spmv": ("solve.cu", "tma.cuh"),
-    "pcg_spmv_fp64": ("solve.cu", "tma.cuh"),
+    # api.cu chooses the fine level's layout (CSR tiles or the sliced-ELL copy), hence which
+    # kernel the class runs
+    "vcycle_fine_spmv": ("solve.cu", "tma.cuh", "api.cu"),
+    "pcg_spmv_fp64": ("solve.cu", "tma.cuh", "api.cu"),
     "galerkin_spgemm": ("spgemm.cu",),
 }
 

@@ -72,9 +72,9 @@ enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
  * A sliced-ELL copy (slices of 32 rows, column-major inside a slice, padded to the slice's
  * longest row; one lane per row with coalesced loads) may be kept beside CSR for a level whose
  * rows average at most 40 entries and whose padding stays within an eighth of its entries.
- * SELL: every such level.  AUTO: only those whose FP64 operator (12 bytes per entry) exceeds the
- * L2 cache; smaller ones are read mostly from L2 by the CSR kernel's consecutive products,
- * which is faster there.  CSR: never.  A row is summed in the order of the CSR kernel, so every
+ * SELL: every such level.  AUTO: those whose FP64 operator (12 bytes per entry) exceeds the L2
+ * cache or that have at least 1024 rows per SM (four 256-row sliced blocks per SM); on smaller
+ * levels the sliced kernel leaves most SMs idle and the CSR kernel is faster.  CSR: never.  A row is summed in the order of the CSR kernel, so every
  * layout gives identical results; a copy costs 12 bytes per stored entry (16 with AMG_MIXED)
  * plus its padding. */
 enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_CSR = 1, AMG_LAYOUT_SELL = 2 };

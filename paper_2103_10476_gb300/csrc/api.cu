@@ -630,17 +630,21 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         }
         // sliced-ELL copies of the level operators with short rows (their layout first; the
         // entry counts reach the host with the plans' synchronisation)
-        // An operator that fits in L2 is read mostly from L2 by the CSR kernel's consecutive
-        // products; only larger ones, with short rows, get the copy.
+        // AUTO copies an operator with short rows when it is larger than L2 (the CSR kernel
+        // would stream it from HBM) or has rows enough for four 256-row sliced blocks per SM: one
+        // lane per row issues fewer FP64 instructions than two, but a level with fewer rows
+        // leaves the SMs without warps to cover the latency of its longer rows.
         std::vector<int> sell_levels;
         unsigned long long *tot_host = (unsigned long long *)h->rr_host;
-        int dev = 0, l2 = 0;
+        int dev = 0, l2 = 0, nsm = 0;
         CK(cudaGetDevice(&dev));
         CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         for (int L = 0; L + 1 < h->nlev; ++L) {
             Level &lv = h->lev[L];
             const bool want = h->p.spmv_layout == AMG_LAYOUT_SELL ||
-                              (h->p.spmv_layout == AMG_LAYOUT_AUTO && 12.0 * (double)lv.A.nnz > (double)l2);
+                              (h->p.spmv_layout == AMG_LAYOUT_AUTO &&
+                               (12.0 * (double)lv.A.nnz > (double)l2 || (double)lv.A.n >= 1024.0 * nsm));
             if (!want || lv.plan_a.lpr != 2 || lv.A.n == 0 || (int)sell_levels.size() >= kReduceBlocks) continue;
             const int nsl = sell_slices(lv.A.n);
             int *sw = nullptr, *sp = nullptr;

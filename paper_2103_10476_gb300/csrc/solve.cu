@@ -154,6 +154,39 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             for (int k = b + lane; k < e; k += LPR) sum += v[k] * x[ci[k]];
         }
     }
+    if (MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || MODE == MODE_PROLONG) {
+        // The row's sum and its update are formed by thread r < RPB for row r of the block, every
+        // lane of those warps busy, instead of by the first of each row's LPR lanes: a warp's FP64
+        // instruction takes the FP64 pipe whether one lane in LPR or all lanes are active, and the
+        // update is up to five of them per row.  Same sums: with two lanes, partial 0 + partial 1
+        // as the shuffle gives; with more, the shuffle tree first.
+        __shared__ T ps[kSpmvThreads];
+        if (LPR == 2) {
+            ps[lane * RPB + threadIdx.x / LPR] = sum;
+        } else {
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
+            if (lane == 0) ps[threadIdx.x / LPR] = sum;
+        }
+        __syncthreads();
+        const int rw = r0 + (int)threadIdx.x;
+        if ((int)threadIdx.x < RPB && rw < r1 && tile_ok) {
+            const T sr = LPR == 2 ? ps[threadIdx.x] + ps[RPB + threadIdx.x] : ps[threadIdx.x];
+            if (MODE == MODE_Y) {
+                y[rw] = sr;
+            } else if (MODE == MODE_RESID) {
+                y[rw] = f[rw] - sr;
+            } else if (MODE == MODE_CHEB) {
+                T r = f[rw] - sr;
+                T dn = c1 * d[rw] + c2 * (aux[rw] * r);
+                d[rw] = dn;
+                y[rw] = x[rw] + dn;
+            } else {
+                y[rw] += sr;
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
     double contrib = 0.0, contrib2 = 0.0;
