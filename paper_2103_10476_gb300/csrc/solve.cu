@@ -274,6 +274,16 @@ int pick_lanes(double avg_row) { return pick_lpr(avg_row); }
 
 int spmv_blocks(int n, int lpr) { return n > 0 ? (n + kSpmvThreads / lpr - 1) / (kSpmvThreads / lpr) : 0; }
 
+// Lanes per row of a level operator's products: the row-length rule, then doubled while the grid
+// would hold fewer than two blocks per SM and every lane still keeps four entries or more (a
+// small level with long rows otherwise runs on a fraction of the SMs, latency-bound).
+int pick_lpr_rows(double avg_row, int n)
+{
+    int lpr = pick_lpr(avg_row);
+    while (lpr < 32 && spmv_blocks(n, lpr) < kReduceBlocks && avg_row >= 8.0 * lpr) lpr *= 2;
+    return lpr;
+}
+
 __global__ void span_max_kernel(int n, const int *rp, int rpb, int *out)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,7 +306,7 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         SpmvPlan *pl = plans[k];
         const int n = ns[k];
-        pl->lpr = pick_lpr(n ? (double)nnzs[k] / n : 1.0);
+        pl->lpr = pick_lpr_rows(n ? (double)nnzs[k] / n : 1.0, n);
         pl->cap = 0;
         if (n == 0 || nnzs[k] == 0) continue;
         const int nb = spmv_blocks(n, pl->lpr);
@@ -313,7 +323,7 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
 
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s)
 {
-    plan->lpr = pick_lpr(n ? (double)nnz / n : 1.0);
+    plan->lpr = pick_lpr_rows(n ? (double)nnz / n : 1.0, n);
     plan->cap = 0;
     if (n == 0 || nnz == 0) return cudaSuccess;
     int *d = nullptr, h = 0;
