@@ -474,6 +474,64 @@ def test_constrain_row_invariants_random(oracle_lib):
             assert p0.sum() == 0.0 and not p.any()
 
 
+def _capped_simplex_projection(p0):
+    """The §2.4 row problem solved exactly, independently of Algorithm 3: the Euclidean projection
+    of the row's nonzero entries onto {0 <= x <= 1, sum x = sum p0} (zeros stay zero).  By the
+    KKT conditions x = clip(p0 - tau, 0, 1) for the tau at which the sum matches; the sum is
+    monotone in tau, so bisection finds it."""
+    p0 = np.asarray(p0, dtype=np.float64)
+    nz = p0 != 0.0
+    v = p0[nz]
+    s = v.sum()
+    lo, hi = v.min() - 1.0, v.max()      # sum = |v| at lo, 0 at hi
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.clip(v - mid, 0.0, 1.0).sum() > s:
+            lo = mid
+        else:
+            hi = mid
+    x = np.zeros_like(p0)
+    x[nz] = np.clip(v - 0.5 * (lo + hi), 0.0, 1.0)
+    return x
+
+
+def test_constrain_row_one_sided_is_the_exact_projection(oracle_lib):
+    # rows whose violators all lie on one side (negative entries and none above one, or entries
+    # above one and none negative): Algorithm 3 reaches the minimiser of the §2.4 row problem
+    rng = np.random.default_rng(11)
+    checked = 0
+    for trial in range(600):
+        m = int(rng.integers(2, 12))
+        if trial % 2 == 0:
+            p0 = rng.uniform(-0.6, 1.0, m)          # lower violators only
+        else:
+            p0 = rng.uniform(0.05, 1.9, m)          # upper violators only
+        p0[rng.random(m) < 0.15] = 0.0
+        nnz = int((p0 != 0).sum())
+        s = p0.sum()
+        if nnz == 0 or s <= 0.0 or s > nnz or ((p0 >= 0) & (p0 <= 1)).all():
+            continue
+        p, c = oracle_lib.constrain_row(p0, 0, 1.0)
+        assert c == 0
+        np.testing.assert_allclose(p, _capped_simplex_projection(p0), rtol=0, atol=1e-12)
+        checked += 1
+    assert checked > 250
+
+
+def test_constrain_row_two_sided_follows_algorithm3(oracle_lib):
+    # with violators on both sides one pass pins both and spreads their combined excess evenly;
+    # the exact minimiser lets the negative entry rise instead: (1/15, 1, 7/15, 7/15), distance^2
+    # 1/3 against 0.34.  The method is Algorithm 3 (the oracle and the kernels follow it).
+    p0 = np.array([-0.1, 1.5, 0.3, 0.3])
+    p, c = oracle_lib.constrain_row(p0, 1, 1.0)
+    assert c == 0
+    np.testing.assert_allclose(p, [0.0, 1.0, 0.5, 0.5], rtol=0, atol=1e-15)
+    x = _capped_simplex_projection(p0)
+    np.testing.assert_allclose(x, [1 / 15, 1.0, 7 / 15, 7 / 15], rtol=0, atol=1e-12)
+    assert ((x - p0) ** 2).sum() == pytest.approx(1 / 3, abs=1e-12)
+    assert ((p - p0) ** 2).sum() == pytest.approx(0.34, abs=1e-12)
+
+
 # ------------------------------------------------------------------ §2.5 sparsification
 
 def _two_columns(extra_links):
