@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(kGT) gs_reduce_kernel(const double *partial, i
     if (threadIdx.x == 0) out[blockIdx.x] = t;
 }
 
-// w -= sum_i h_i V_i (per entry, i ascending); the coefficients staged in shared memory
+// w -= sum_i h_i V_i (per entry, i ascending); the coefficients staged in shared memory.  A
+// step has at most restart basis vectors and amg_setup refuses restart above 512.
 constexpr int kMaxBasis = 513;
 __global__ void __launch_bounds__(256) gs_update_kernel(int n, const double *V, int nv, const double *h,
                                                         double *w)
