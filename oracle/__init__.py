@@ -91,6 +91,8 @@ def lib():
         L.oc_lu.argtypes = [C.c_int64, vp, vp]
         L.oc_lu_solve.argtypes = [C.c_int64, vp, vp, vp, vp]
         L.oc_vcycle.argtypes = [vp, vp, vp]
+        L.oc_chebyshev_apply.argtypes = [C.c_int64, vp, vp, vp, vp, C.c_double, C.c_int, C.c_double, C.c_double,
+                                         vp, vp]
         L.oc_free.argtypes = [vp]
         L.oc_nlevels.argtypes = [vp]
         L.oc_level_get.argtypes = [vp, C.c_int, C.c_int, vp, C.POINTER(C.c_int64)]
@@ -254,6 +256,21 @@ def power_lambda(A, D, sweeps: int, stream_seed: int) -> float:
 
 def power_stream_seed(seed: int, level: int, purpose: int) -> int:
     return int(lib().oc_power_stream_seed(seed, level, purpose))
+
+
+def chebyshev_apply(A, lam: float, degree: int, x0=None, f=None, ratio: float = 10.0, boost: float = 1.1):
+    """The V-cycle's smoother on its own: `degree` Chebyshev steps in D^-1 A on
+    [boost*lam/ratio, boost*lam] applied to A x = f from x0 (zero if None); returns (x, status)."""
+    rp, ci, v = _arrs(A)
+    d = np.zeros(A.n)
+    rows = np.repeat(np.arange(A.n), np.diff(rp))
+    on = rows == ci
+    d[rows[on]] = v[on]
+    invd = 1.0 / d
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    x = np.zeros(A.n) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+    st = lib().oc_chebyshev_apply(A.n, _p(rp), _p(ci), _p(v), _p(invd), lam, degree, ratio, boost, _p(f), _p(x))
+    return x, int(st)
 
 
 def cholesky(a: np.ndarray):

@@ -1395,6 +1395,26 @@ static void chebyshev(const struct oc_level *lv, int degree, double ratio, doubl
     }
 }
 
+/* The smoother alone, for its pins: the same routine on an operator given as CSR with
+ * 1/diag(A) and lambda supplied by the caller. */
+int oc_chebyshev_apply(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *invdiag,
+                       double lambda, int degree, double ratio, double boost, const double *f, double *x)
+{
+    if (n < 0 || degree < 1 || !(ratio > 1.0) || !(lambda > 0.0) || !(boost > 0.0)) return OC_ERR_INVALID_ARG;
+    struct oc_level lv;
+    memset(&lv, 0, sizeof(lv));
+    lv.A.n = n; lv.A.nnz = rp[n];
+    lv.A.rp = (int64_t *)rp; lv.A.ci = (int32_t *)ci; lv.A.v = (double *)v;
+    lv.invdiag = (double *)invdiag;
+    lv.lambda_cheb = lambda;
+    double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *d = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!r || !d) { free(r); free(d); return OC_ERR_OOM; }
+    chebyshev(&lv, degree, ratio, boost, f, x, r, d);
+    free(r); free(d);
+    return OC_OK;
+}
+
 /* Algorithm 1 from level L with u holding the initial guess. */
 static void vcycle_level(oc_hier *h, int L, const double *f, double *u)
 {

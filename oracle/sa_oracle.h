@@ -116,6 +116,9 @@ int oc_solve(oc_hier *h, const double *b, double *x, double tol, oc_info *info);
 int oc_pcg_plain(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *b,
                  double *x, double tol, int max_iter, oc_info *info);
 int oc_vcycle(oc_hier *h, const double *f, double *u);
+/* the Chebyshev smoother of the V-cycle on its own (degree m in D^-1 A on [b lambda/ratio, b lambda]) */
+int oc_chebyshev_apply(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const double *invdiag,
+                       double lambda, int degree, double ratio, double boost, const double *f, double *x);
 void oc_free(oc_hier *h);
 
 /* introspection */
