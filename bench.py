@@ -1,18 +1,23 @@
 """Benchmark: SA-AMG hierarchy setup + PCG solve to 1e-8 relative residual on one GB300.
 
-Workload (default): Q1 finite-element Laplacian on a 64^3-node box mesh whose z spacing
-grows by 1.1 per element layer (aspect ratios 1 to ~1:446), strength threshold 0.02, right-
-hand side uniform in [-1, 1) (seed 1); one step = setup + solve for each of the five methods
-{traditional SA, 1Norm, OffLmp, Sprsfy, Cnstrnt} in FP64.  Synthetic inputs stand in for the
-paper's meshes (which are not available).
+Workload (default): Q1 finite-element diffusion on the unit cube with 128^3 interior nodes
+(2,097,152 unknowns, 55,742,968 stored entries), per-element coefficient 10^U(-3,3) (SplitMix64
+seed 2), strength threshold 0.02 with 1Norm + OffLmp, right-hand side uniform in [-1, 1)
+(seed 2); one step = amg_setup + amg_solve (+ amg_free) in FP64, with the mixed form (FP32
+hierarchy values and V-cycle inside FP64 PCG) timed the same way beside it.  Synthetic inputs
+stand in for the paper's coefficient-jump problems (SPE10 is not available).  Other workloads:
+stretched64 (64^3 box, z spacing x1.1 per layer, five methods per step), laplace20.
 
-Prints one JSON line (rank 0): solves/s over the timed steps (inputs resident in HBM), the
-end-to-end number through the C ABI with host buffers, the roofline of the dominant timed
-kernel class, the oracle timed on the host cores, and the SM clocks sampled during the
-timed region.
+Prints one JSON line (rank 0): solves/s over the timed steps (inputs resident in HBM) with the
+setup and solve milliseconds per solve, the end-to-end number through the C ABI with host
+buffers, the roofline of the dominant kernel class (taken from a separate profiled pass),
+the oracle timed on the host cores (one whole solve at full size, in a process of its own)
+and each result's error against the oracle's solution, the SM clocks sampled during the
+timed region, and the side lines (batched, served, several right-hand sides, GMRES,
+systems, the 16-combination study).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload stretched64|randcoef128|laplace20] [--precision fp64|mixed]
+                  [--workload randcoef128|stretched64|laplace20] [--precision fp64|mixed]
 """
 from __future__ import annotations
 
@@ -205,6 +210,63 @@ def ncu_traffic(kclass_name: str, workload: str):
 
 # ------------------------------------------------------------------------------ CPU baseline / reference arm
 
+# workloads whose CPU baseline is one whole oracle solve at full size (minutes of CPU time),
+# run in a spawned process beside the GPU work; its solution also gives each result's error
+ORACLE_FULL = ("randcoef128",)
+
+
+def _oracle_full_child(workload: str, out_prefix: str):
+    """Spawned process: the oracle's setup + solve of the full workload (first method)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    A, b, theta = make_workload(workload)
+    name, v = VARIANT_SETS[workload][0]
+    t0 = time.perf_counter()
+    h, st = oracle.setup(A, theta=theta, variants=v)
+    t1 = time.perf_counter()
+    res = {"status": int(st), "method": name, "setup_s": t1 - t0}
+    if h is not None:
+        x, info, st2 = h.solve(b, TOL)
+        res.update(solve_s=time.perf_counter() - t1, iters=int(info.iters), status=int(st2),
+                   relres=float(info.relres_true), levels=int(info.levels))
+        np.save(out_prefix + ".npy", x)
+    with open(out_prefix + ".json", "w") as f:
+        json.dump(res, f)
+
+
+class OracleFullRun:
+    """The oracle's whole solve of a workload in a spawned process (a fresh interpreter, so
+    it is safe to start after the GPU is in use)."""
+
+    def __init__(self, workload: str):
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="oracle_full_")
+        self.prefix = os.path.join(self.dir, "run")
+        self.proc = mp.get_context("spawn").Process(target=_oracle_full_child, args=(workload, self.prefix),
+                                                    daemon=True)
+        self.proc.start()
+
+    def result(self, timeout_s: float = 1800.0):
+        import numpy as np
+        self.proc.join(timeout_s)
+        if self.proc.is_alive():
+            self.proc.terminate()
+            return {"status": -1, "error": "oracle run exceeded its time limit"}
+        try:
+            res = json.load(open(self.prefix + ".json"))
+        except Exception as e:      # the child failed before writing its result
+            return {"status": -1, "error": f"no result ({e}); exit code {self.proc.exitcode}"}
+        if os.path.exists(self.prefix + ".npy"):
+            res["x"] = np.load(self.prefix + ".npy")
+        return res
+
+
+# the reference arm's bounded sample of the 128^3 workload: whole oracle solves of a smaller
+# cube of the same family (iid coefficients 10^U(-3,3), theta 0.02, 1Norm+OffLmp), each timed
+# and scaled to the full cube by the ratio of stored entries
+SAMPLE_EDGE = {"randcoef128": 48}
+
 def oracle_sample(A, b, theta, variants, budget_s: float):
     """Times the oracle (as it stands) on whole setup+solve runs of the workload's methods,
     cycling through them until about budget_s seconds have passed.  Returns (solves, seconds,
@@ -233,6 +295,8 @@ def oracle_sample(A, b, theta, variants, budget_s: float):
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
+    if args.workload in SAMPLE_EDGE:
+        return run_reference_scaled(args)
     A, b, theta = make_workload(args.workload)
     variants = VARIANT_SETS[args.workload]
     # the oracle keeps no state between runs, so warm-up steps are not run (bounds the wall time)
@@ -262,6 +326,48 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_reference_scaled(args):
+    """Reference arm for a workload whose single solve takes the oracle minutes: every step is
+    one whole oracle setup + solve of a smaller cube of the same family, and its time is
+    scaled to the full workload by the ratio of stored entries (AMG setup and each PCG
+    iteration are linear in them; the iteration count of the sample is reported beside)."""
+    import oracle
+    from paper_2103_10476_gb300 import problems as P
+    oracle.build()
+    edge = int(os.environ.get("REF_SAMPLE_EDGE", SAMPLE_EDGE[args.workload]))
+    As = P.random_coefficient_cube(edge, 2, 3.0)
+    bs = P.rhs_uniform(As.n, 2)
+    full_nnz = (3 * 128 - 2) ** 3
+    scale = full_nnz / As.nnz
+    name, v = VARIANT_SETS[args.workload][0]
+    per, iters = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        h, st = oracle.setup(As, theta=0.02, variants=v)
+        if h is not None:
+            _, info, _ = h.solve(bs, TOL)
+            iters = info.iters
+            del h
+        per.append((time.perf_counter() - t0) * scale)
+    secs = sum(per)
+    value = args.steps / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one whole oracle setup + solve ({name}) of a {edge}^3 cube of the same "
+                                   f"family ({As.n} unknowns, {As.nnz} entries, {iters} PCG iterations), its time "
+                                   f"scaled by {scale:.2f} (the full cube's entries over the sample's); single "
+                                   f"thread, host has {os.cpu_count()} cores; warm-up steps not run (no state)"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "p50_ms": 1000 * statistics.median(per), "p99_ms": 1000 * max(per),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def workload_config(args):
     desc = {
         "stretched64": "Q1 FE Laplacian, 64^3 interior nodes, z spacing x1.1 per layer, theta=0.02; "
@@ -272,7 +378,8 @@ def workload_config(args):
         "convdiff64": "convection-diffusion 64^3, theta=0.02, 1Norm+OffLmp, GMRES(30)",
     }[args.workload]
     return {"workload": args.workload, "description": desc, "precision": args.precision, "tol": TOL,
-            "rhs": "uniform[-1,1) SplitMix64", "l2": "flushed (256 MiB write) before every timed step",
+            "rhs": "uniform[-1,1) SplitMix64", "inputs": "matrix and right-hand side resident in HBM",
+            "l2": "flushed (256 MiB write) before every timed step",
             "parallelism": f"replicas x{args.gpus}"}
 
 
@@ -395,7 +502,7 @@ def run_batched(args, amg, torch):
 
 
 def run_multi(args, amg, torch):
-    """§8(f) row 4: eight right-hand sides of the benchmark's stretched64 system (1Norm) solved
+    """Several right-hand sides of one system: eight right-hand sides of the benchmark's stretched64 system (1Norm) solved
     at once by amg_solve_multi against the same eight solved one after another by amg_solve on
     the same hierarchy; matrix, right-hand sides and solutions resident on the device; solve
     phase only (one setup shared), FP64 and mixed.  Host wall time between device
@@ -444,7 +551,7 @@ def run_multi(args, amg, torch):
 
 
 def run_gmres(args, amg, torch):
-    """§8(f) row 3: the nonsymmetric stand-in for §3's pressure system (convection-diffusion,
+    """Nonsymmetric operators: the stand-in for §3's pressure system (convection-diffusion,
     64^3 interior nodes, 6.86M entries) with the symmetrised strength mask, the general
     coarsest inverse and flexible GMRES(30) to 1e-8, one V-cycle per step; matrix, right-hand
     side and solution resident on the device; one step = amg_setup + amg_solve + amg_free, host
@@ -486,7 +593,7 @@ def run_gmres(args, amg, torch):
 
 
 def run_systems(args, amg, torch):
-    """§8(f) row 2: a system of PDEs, 3D linear elasticity on 40^3 unit hexahedra (face x = 0
+    """A system of PDEs: 3D linear elasticity on 40^3 unit hexahedra (face x = 0
     clamped; 201,720 unknowns, three per node; 15.5M entries) with its six rigid-body modes as
     the near-null space: block strength, node aggregation, QR tentative prolongator; theta
     0.02, PCG to 1e-8; matrix, near-null space and RHS resident on the device; one step =
@@ -671,7 +778,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stretched64", choices=sorted(VARIANT_SETS))
+    ap.add_argument("--workload", default="randcoef128", choices=sorted(VARIANT_SETS))
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision line beside the FP64 one")
@@ -771,81 +878,118 @@ def main():
     arg_d = amg.csr_arg(A.n, rp_d, ci_d, v_d)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def timed(params_list, steps, warmup, profile):
-        """Warm-up, then `steps` timed steps (per-step CUDA events on the launching stream,
-        L2 flushed before each step outside the events).  Returns the step times and details."""
-        per_solve, iters, statuses = [], {}, {}
+    def one_step(params_list, record, evs=None):
+        """Setup + solve (+ free) of every method of the workload; with `evs`, CUDA events on
+        the launching stream before each setup, after it and after the solve."""
+        for k, ((name, _), p) in enumerate(zip(variants, params_list)):
+            if evs is not None:
+                evs[k][0].record(stream)
+            h, st = amg.amg_setup_status(arg_d, None, p)
+            if evs is not None:
+                evs[k][1].record(stream)
+            if h is None:
+                if record is not None:
+                    record["status"][name] = amg.amg_status_string(st)
+                if evs is not None:
+                    evs[k][2].record(stream)
+                continue
+            info = amg.amg_solve(h, b_d, x_d, TOL)
+            amg.amg_free(h)
+            if evs is not None:
+                evs[k][2].record(stream)
+            if record is not None:
+                record["iters"][name] = info.iters
+                record["status"][name] = amg.amg_status_string(info.status)
+                record["relres"][name] = info.relres_true
+                record["levels"][name] = info.levels
 
-        def step(record):
-            for k, ((name, _), p) in enumerate(zip(variants, params_list)):
-                # the kernel-class events are recorded around the first method's launches only
-                # (the fine-level kernels are the same for every method), so that the event
-                # records do not weigh on the other four
-                if record and profile and k == 0:
-                    amg.amg_profile_enable(2)
-                t0 = time.perf_counter()
-                h, st = amg.amg_setup_status(arg_d, None, p)
-                if h is None:
-                    statuses[name] = amg.amg_status_string(st)
-                    if record and profile and k == 0:
-                        amg.amg_profile_enable(0)
-                    continue
-                info = amg.amg_solve(h, b_d, x_d, TOL)
-                amg.amg_free(h)
-                if record and profile and k == 0:
-                    amg.amg_profile_enable(0)
-                if record:
-                    per_solve.append(1000 * (time.perf_counter() - t0))
-                    iters[name] = info.iters
-                    statuses[name] = amg.amg_status_string(info.status)
-
+    def timed(params_list, steps, warmup):
+        """Warm-up, then `steps` timed steps: CUDA events on the launching stream around each
+        step and around each method's setup and solve, L2 flushed before each step (outside
+        the events).  Nothing else is recorded inside the timed region."""
+        rec = {"iters": {}, "status": {}, "relres": {}, "levels": {}}
         for _ in range(warmup):
-            step(False)
+            one_step(params_list, None)
         torch.cuda.synchronize()
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        mk = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        ev0 = [mk() for _ in range(steps)]
+        ev1 = [mk() for _ in range(steps)]
+        per = [[[mk(), mk(), mk()] for _ in variants] for _ in range(steps)]
         launches0 = amg.amg_launch_count()
-        if profile:
-            amg.amg_profile_enable(1)      # reset the totals
-            amg.amg_profile_enable(0)
         barrier(world)
         torch.cuda.synchronize()
         for k in range(steps):
             flush.zero_()
             ev0[k].record(stream)
-            step(True)
+            one_step(params_list, rec if k == steps - 1 else None, per[k])
             ev1[k].record(stream)
         torch.cuda.synchronize()
         barrier(world)
         launches = amg.amg_launch_count() - launches0
-        prof = None
-        if profile:
-            prof = {kc: amg.amg_profile_read(kc) for kc in (amg.KC_PCG_SPMV, amg.KC_VCYCLE_SPMV, amg.KC_SPGEMM)}
         step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(steps)]
-        return step_ms, per_solve, iters, statuses, launches, prof
+        setup_ms = [e[0].elapsed_time(e[1]) for st in per for e in st]
+        solve_ms = [e[1].elapsed_time(e[2]) for st in per for e in st]
+        return step_ms, setup_ms, solve_ms, rec, launches
+
+    def profiled(params_list, steps):
+        """Kernel-class timing (library CUDA events around the first method's fine-level
+        launches) over `steps` extra steps, outside the timed region."""
+        amg.amg_profile_enable(1)      # reset the totals
+        amg.amg_profile_enable(0)
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            for k, ((name, _), p) in enumerate(zip(variants, params_list)):
+                if k == 0:
+                    amg.amg_profile_enable(2)
+                h, st = amg.amg_setup_status(arg_d, None, p)
+                if h is not None:
+                    amg.amg_solve(h, b_d, x_d, TOL)
+                    amg.amg_free(h)
+                if k == 0:
+                    amg.amg_profile_enable(0)
+        torch.cuda.synchronize()
+        return {kc: amg.amg_profile_read(kc) for kc in (amg.KC_PCG_SPMV, amg.KC_VCYCLE_SPMV, amg.KC_SPGEMM)}
+
+    def solution(params_list):
+        """The first method's solution, solved once more after the timed regions (host copy)."""
+        h, st = amg.amg_setup_status(arg_d, None, params_list[0])
+        if h is None:
+            return None
+        x_d.zero_()
+        amg.amg_solve(h, b_d, x_d, TOL)
+        amg.amg_free(h)
+        torch.cuda.synchronize()
+        return x_d.cpu().numpy().copy()
 
     t_wall = time.perf_counter()
     with ClockSampler(local) as clk:
-        step_ms, per_solve_ms, iters, statuses, launches, prof = timed(params, args.steps, args.warmup, True)
+        step_ms, setup_ms, solve_ms, rec, launches = timed(params, args.steps, args.warmup)
     t_wall = time.perf_counter() - t_wall
     total_ms = max_over_ranks(world, sum(step_ms))
     solves_per_step = len(variants)
     value = whole_job_rate(solves_per_step * args.steps, world, total_ms)
 
+    # the oracle's whole solve of the full workload (the CPU baseline) runs in a process of its
+    # own while the rest of the benchmark uses the GPU; its solution gives each result's error
+    oracle_job = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ORACLE_FULL:
+        oracle_job = OracleFullRun(args.workload)
+
     # the other precision, same workload and timing rules (reported beside the headline)
     other = None
+    mparams = None
     if args.precision == "fp64" and not args.no_mixed:
         mparams = [amg.amg_params_default(theta=theta, variants=v, precision=amg.AMG_MIXED,
                                           cuda_stream=stream.cuda_stream) for _, v in variants]
-        msteps = max(2, args.steps // 2)
-        m_ms, m_solve, m_iters, m_status, _, _ = timed(mparams, msteps, 1, False)
+        msteps = max(3, args.steps // 2)
+        m_ms, m_setup, m_solve, m_rec, _ = timed(mparams, msteps, 2)
         m_total = max_over_ranks(world, sum(m_ms))
-        mlat = sorted(m_solve)
         other = {"precision": "mixed (FP32 hierarchy values and V-cycle, FP64 flexible PCG)",
                  "value": whole_job_rate(solves_per_step * msteps, world, m_total), "unit": "solves/s",
-                 "ms_per_step": m_total / msteps, "steps": msteps, "iters": m_iters, "status": m_status,
-                 "p50_ms": mlat[len(mlat) // 2] if mlat else None,
-                 "p99_ms": mlat[min(len(mlat) - 1, int(0.99 * len(mlat)))] if mlat else None}
+                 "ms_per_step": m_total / msteps, "steps": msteps,
+                 "setup_ms_per_solve": statistics.median(m_setup), "solve_ms_per_solve": statistics.median(m_solve),
+                 "iters": m_rec["iters"], "status": m_rec["status"], "relres": m_rec["relres"]}
 
     # end to end through the C ABI with host buffers (host -> device copy of the matrix and the
     # right-hand side inside every step, device -> host copy of the solution)
@@ -855,7 +999,7 @@ def main():
     ci_h = torch.from_numpy(A.col).pin_memory()
     val_h = torch.from_numpy(A.val).pin_memory()
     arg_h = amg.csr_arg(A.n, rp_h, ci_h, val_h)
-    e2e_steps = max(1, args.steps // 2)
+    e2e_steps = max(2, args.steps // 2)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(e2e_steps):
@@ -871,6 +1015,11 @@ def main():
     h2d = solves_per_step * (8 * (A.n + 1) + 12 * A.nnz + 8 * A.n)
     d2h = solves_per_step * 8 * A.n
 
+    # roofline classes from a separate, profiled pass
+    prof = profiled(params, 2)
+    x_fp64 = solution(params) if oracle_job is not None else None
+    x_mixed = solution(mparams) if (oracle_job is not None and mparams is not None) else None
+
     batched = None if args.no_batched else run_batched(args, amg, torch)
     study = None if args.no_study else run_study(args, amg, torch)
     multi = None if args.no_multi else run_multi(args, amg, torch)
@@ -882,7 +1031,7 @@ def main():
     if rank != 0:
         return 0
 
-    # roofline of the dominant timed kernel class
+    # roofline of the dominant kernel class (profiled pass)
     peak, peak_src = measured_peaks()
     names = {amg.KC_PCG_SPMV: "pcg_spmv_fp64", amg.KC_VCYCLE_SPMV: "vcycle_fine_spmv", amg.KC_SPGEMM: "galerkin_spgemm"}
     dom = max(prof, key=lambda k: prof[k][1])
@@ -897,12 +1046,34 @@ def main():
                             for k in prof}}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    errors = None
+    if oracle_job is not None:
+        full = oracle_job.result()
+        if full is not None and full.get("status") == 0:
+            secs = full["setup_s"] + full["solve_s"]
+            cpu = {"value": 1.0 / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one whole setup + solve of the same workload at full size ({A.n} unknowns, "
+                             f"{variants[0][0]}, FP64): setup {full['setup_s']:.1f} s + solve {full['solve_s']:.1f} s "
+                             f"({full['iters']} PCG iterations), single-threaded C oracle in a process of its own "
+                             f"while the GPU side lines ran; host has {os.cpu_count()} cores",
+                   "setup_s": full["setup_s"], "solve_s": full["solve_s"], "iters": full["iters"],
+                   "levels": full["levels"]}
+            xo = full["x"]
+            nxo = float(np.linalg.norm(xo))
+            errors = {"reference": "FP64 oracle solution of the same system (1e-8 relative residual)",
+                      "fp64": float(np.linalg.norm(x_fp64 - xo) / nxo) if x_fp64 is not None else None,
+                      "mixed": float(np.linalg.norm(x_mixed - xo) / nxo) if x_mixed is not None else None,
+                      "oracle_iters": full["iters"]}
+        else:
+            cpu = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                   "sample": f"oracle full run failed: {full}"}
+    elif not args.no_cpu_baseline:
         n_s, secs, done = oracle_sample(A, b, theta, variants, args.cpu_budget)
         cpu = {"value": n_s / secs, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"{n_s} whole setup+solve runs ({', '.join(done)}) of the same workload, single-threaded C "
                          f"oracle, {secs:.1f} s; host has {os.cpu_count()} cores"}
 
+    per_solve_ms = [a_ + b_ for a_, b_ in zip(setup_ms, solve_ms)]
     lat = sorted(per_solve_ms)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -916,7 +1087,10 @@ def main():
         "gpu_launches": launches,
         "p50_ms": lat[len(lat) // 2] if lat else None,
         "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
-        "iters": iters, "status": statuses, "wall_s": t_wall,
+        "setup_ms_per_solve": statistics.median(setup_ms), "solve_ms_per_solve": statistics.median(solve_ms),
+        "iters": rec["iters"], "status": rec["status"], "relres": rec["relres"], "levels": rec["levels"],
+        "wall_s": t_wall,
+        "error_vs_oracle": errors,
         "mixed": other,
         "batched": batched,
         "study": study,

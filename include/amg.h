@@ -240,8 +240,8 @@ amg_status_t amg_vcycle(amg_handle_t h, const double *r, double *z);
 /* Sparse product C = A B on the device (the two-phase hash kernel used for Eq. (2)).
  * A: m x k, B: k x ncolB, both device CSR with sorted columns.  C is allocated by the
  * library (device memory, int64 row pointers); release it with amg_csr_release.
- * Each c_ij is summed over ascending k starting from zero, with every product rounded
- * separately (no fused multiply-add). */
+ * Each c_ij is summed over ascending k starting from zero, each term added by one fused
+ * multiply-add c = fma(a_ik, b_kj, c) (one rounding per term). */
 typedef struct {
     int64_t nrow, ncol, nnz;
     int64_t *row_ptr;
@@ -264,14 +264,18 @@ amg_status_t amg_dcsr_download(const amg_dcsr_t *C, int64_t *row_ptr, int32_t *c
  *   device: C_row_ptr (m + 1 entries), C_col and C_val (capacity entries each).
  *   *nnz_out (host) receives nnz(C).  If it exceeds capacity, nothing is written to C_col or
  *   C_val and AMG_ERR_BUDGET is returned, so the caller can retry with larger arrays.
+ *   Checked before any kernel reads a row: row pointers that do not start at 0, decrease or
+ *   do not end at nnz, column indices outside the matrix, and NULL col/val arrays of a
+ *   matrix with entries give AMG_ERR_INVALID_ARG with nothing written to C.
  * Temporaries live in one 32 MiB array of device memory that is part of the library: every
  * GPU that loads the library holds it until the process exits.  Limits: at most 1,000,000
- * rows in A and in B, and the hash tables of very long rows must fit in what the row arrays
- * leave of the 32 MiB; beyond them the call returns AMG_ERR_UNSUPPORTED (amg_last_error says
- * which).  The first call on a device looks the array up (no allocation); make that first
+ * rows in A and in B, at most 2^31 - 16 entries in C, and the hash tables of very long rows
+ * must fit in what the row arrays leave of the 32 MiB (their sizes are summed in 64 bits);
+ * beyond them the call returns AMG_ERR_UNSUPPORTED (amg_last_error says which).  The first call on a device looks the array up (no allocation); make that first
  * call before any stream capture.  All calls share the array: calls that may overlap on the
  * GPU (different host threads, or streams without ordering between them) race and must be
- * serialised by the caller.  Runs on `cuda_stream` and synchronises it before returning. */
+ * serialised by the caller.  Runs on `cuda_stream` and synchronises it before every return
+ * that follows a launch, whatever the status. */
 amg_status_t amg_spgemm_noalloc(const amg_csr_t *A, int64_t ncolA, const amg_csr_t *B, int64_t ncolB,
                                 void *cuda_stream, int64_t *C_row_ptr, int32_t *C_col, double *C_val,
                                 int64_t capacity, int64_t *nnz_out);

@@ -169,10 +169,10 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
 
 // Allocation-free C = A B on device arrays (int64 row pointers in and out), temporaries in a
 // fixed file-scope device array; see spgemm.cu.
-cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int nB,
-                           int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t *crp64,
-                           int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status, std::string *msg,
-                           cudaStream_t s);
+cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int64_t nnzA,
+                           int nB, int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t nnzB,
+                           int64_t *crp64, int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status,
+                           std::string *msg, cudaStream_t s);
 
 // --------------------------------------------------------------------------------- coarse.cu
 // Dense SPD inverse of the coarsest operator in FP64 (FP32 Cholesky and inverse refined by

@@ -1330,15 +1330,15 @@ amg_status_t amg_spgemm_noalloc(const amg_csr_t *A, int64_t ncolA, const amg_csr
         g_last_error = "amg_spgemm_noalloc: A and B must be device arrays";
         return AMG_ERR_INVALID_ARG;
     }
-    if (A->n < 0 || B->n < 0 || ncolA != B->n || ncolB < 0 || ncolB > 0x7ffffffe || A->nnz > 0x7ffffffe ||
-        B->nnz > 0x7ffffffe || A->n > 0x7ffffffe || B->n > 0x7ffffffe || (A->n > 0 && !A->row_ptr) ||
-        (B->n > 0 && !B->row_ptr))
+    if (A->n < 0 || B->n < 0 || ncolA != B->n || ncolB < 0 || ncolB > 0x7ffffffe || A->nnz < 0 || B->nnz < 0 ||
+        A->nnz > 0x7ffffffe || B->nnz > 0x7ffffffe || A->n > 0x7ffffffe || B->n > 0x7ffffffe || !A->row_ptr ||
+        !B->row_ptr || (A->nnz > 0 && (!A->col || !A->val)) || (B->nnz > 0 && (!B->col || !B->val)))
         return AMG_ERR_INVALID_ARG;
     int code = 0;
     std::string msg;
-    cudaError_t e = spgemm_noalloc((int)A->n, (int)ncolA, A->row_ptr, A->col, A->val, (int)B->n, (int)ncolB,
-                                   B->row_ptr, B->col, B->val, C_row_ptr, C_col, C_val, capacity, nnz_out, &code,
-                                   &msg, (cudaStream_t)stream);
+    cudaError_t e = spgemm_noalloc((int)A->n, (int)ncolA, A->row_ptr, A->col, A->val, A->nnz, (int)B->n, (int)ncolB,
+                                   B->row_ptr, B->col, B->val, B->nnz, C_row_ptr, C_col, C_val, capacity, nnz_out,
+                                   &code, &msg, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e, "amg_spgemm_noalloc");
     if (code) g_last_error = msg;
     switch (code) {

@@ -615,12 +615,56 @@ cudaError_t noalloc_scratch(void **ptr, size_t *bytes)
     return cudaSuccess;
 }
 
+// Input checks of the allocation-free product, run before any kernel walks the rows: *bad
+// counts row pointers that do not start at 0 or do not end at nnz, and column indices
+// outside [0, ncol).
+__global__ void noalloc_ends_kernel(const int64_t *rp, int n, int64_t nnz, int *bad)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (rp[0] != 0 || rp[n] != nnz)) atomicAdd(bad, 1);
+}
+__global__ void noalloc_cols_kernel(const int *ci, int64_t nnz, int ncol, int *bad)
+{
+    int cnt = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        int c = ci[e];
+        cnt += (c < 0 || c >= ncol);
+    }
+    if (cnt) atomicAdd(bad, cnt);
+}
+// 64-bit sum of n non-negative ints (the counts an int32 scan is about to add up)
+__global__ void noalloc_sum64_kernel(const int *v, int n, unsigned long long *out)
+{
+    unsigned long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int x = v[i];
+        acc += x > 0 ? (unsigned long long)x : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFullMask, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+namespace {
+// sum of v[0..n) in 64 bits, read back to the host (synchronises the stream)
+cudaError_t noalloc_sum64(const int *v, int n, unsigned long long *d_sum, unsigned long long *sum, cudaStream_t s)
+{
+    AMG_CUDA_TRY(cudaMemsetAsync(d_sum, 0, sizeof(unsigned long long), s));
+    if (n > 0) {
+        noalloc_sum64_kernel<<<grid_for(n, 256, 1024), 256, 0, s>>>(v, n, d_sum); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
+    AMG_CUDA_TRY(cudaMemcpyAsync(sum, d_sum, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    return cudaStreamSynchronize(s);
+}
+}  // namespace
+
 // status: 0 ok, 1 sizes beyond the scratch limits (msg set), 2 output capacity too small
-// (*nnz_out = required), 3 invalid row pointers, 4 hash overflow; CUDA errors returned as such
-cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int nB,
-                           int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t *crp64,
-                           int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status, std::string *msg,
-                           cudaStream_t s)
+// (*nnz_out = required), 3 invalid row pointers or column indices, 4 hash overflow; CUDA
+// errors returned as such.  Every return after the first launch synchronises the stream.
+cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *aci, const double *av, int64_t nnzA,
+                           int nB, int ncolB, const int64_t *brp64, const int *bci, const double *bv, int64_t nnzB,
+                           int64_t *crp64, int *cci, double *cv, int64_t capacity, int64_t *nnz_out, int *status,
+                           std::string *msg, cudaStream_t s)
 {
     *status = 0;
     *nnz_out = 0;
@@ -637,66 +681,95 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
     int *arp = ar.take<int>((size_t)nA + 1);
     int *brp = ar.take<int>((size_t)nB + 1);
     int *crp = ar.take<int>((size_t)nA + 17);
-    int *work = ar.take<int>((size_t)3 * n + 3 * (kNumBins + 1) + 4);
+    int *work = ar.take<int>((size_t)3 * n + 3 * (kNumBins + 1) + 8);
     int *scan_ws = ar.take<int>(scan_ws_ints(n + 1) + 16);
-    if (!arp || !brp || !crp || !work || !scan_ws) {
+    unsigned long long *d_sum = ar.take<unsigned long long>(1);
+    if (!arp || !brp || !crp || !work || !scan_ws || !d_sum) {
         *status = 1;
         *msg = "amg_spgemm_noalloc: row arrays do not fit in the 32 MiB scratch";
         return cudaSuccess;
     }
+    // from here on kernels may be in flight: every early exit synchronises the stream first
+    auto stop = [&](int code, const char *m) -> cudaError_t {
+        *status = code;
+        *msg = m;
+        return cudaStreamSynchronize(s);
+    };
     int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
     int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
-    int *d_flags = d_binStart + kNumBins + 1;     // [0] bad row pointers, [1] hash overflow
-    AMG_CUDA_TRY(cudaMemsetAsync(d_flags, 0, 2 * sizeof(int), s));
+    int *d_flags = d_binStart + kNumBins + 1;     // [0] bad row pointers, [1] hash overflow, [2] bad columns
+    AMG_CUDA_TRY(cudaMemsetAsync(d_flags, 0, 4 * sizeof(int), s));
     AMG_CUDA_TRY(convert_rowptr_to32(arp64, arp, nA + 1, d_flags, s));
     AMG_CUDA_TRY(convert_rowptr_to32(brp64, brp, nB + 1, d_flags, s));
+    noalloc_ends_kernel<<<1, 32, 0, s>>>(arp64, nA, nnzA, d_flags); note_launch();
+    noalloc_ends_kernel<<<1, 32, 0, s>>>(brp64, nB, nnzB, d_flags); note_launch();
+    if (nnzA > 0) { noalloc_cols_kernel<<<grid_for(nnzA, 256, 1024), 256, 0, s>>>(aci, nnzA, nB, d_flags + 2); note_launch(); }
+    if (nnzB > 0) { noalloc_cols_kernel<<<grid_for(nnzB, 256, 1024), 256, 0, s>>>(bci, nnzB, ncolB, d_flags + 2); note_launch(); }
+    AMG_CUDA_TRY(cudaGetLastError());
+    int hflags[3] = {0, 0, 0};
+    AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflags[0]) return stop(3, "amg_spgemm_noalloc: row pointers must start at 0, never decrease and end at nnz");
+    if (hflags[2]) return stop(3, "amg_spgemm_noalloc: column index outside the matrix");
     DevCsr A, B, C;
     A.n = nA; A.ncol = ncolA; A.rp = arp; A.ci = const_cast<int *>(aci); A.v = const_cast<double *>(av);
     B.n = nB; B.ncol = ncolB; B.rp = brp; B.ci = const_cast<int *>(bci); B.v = const_cast<double *>(bv);
     C.n = nA; C.ncol = ncolB; C.rp = crp; C.ci = cci; C.v = cv;
-    int hflags[2] = {0, 0};
     Bins hb;
     if (n == 0) {
         AMG_CUDA_TRY(cudaMemsetAsync(crp64, 0, sizeof(int64_t), s));
         return cudaStreamSynchronize(s);
     }
+    // the long-row tables of the global bin: sizes summed in 64 bits and checked against what
+    // is left of the scratch before the int32 scan of their offsets (slot_bytes per slot)
+    auto global_tables = [&](int cnt, const int *rows, size_t slot_bytes, int **toff, void **keys,
+                             double **vals) -> cudaError_t {
+        *toff = ar.take<int>((size_t)cnt + 1);
+        int *ws2 = ar.take<int>(scan_ws_ints(cnt + 1) + 16);
+        if (!*toff || !ws2) return stop(1, "amg_spgemm_noalloc: long-row tables do not fit in the scratch");
+        gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, d_tsize, *toff); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        unsigned long long total = 0;
+        AMG_CUDA_TRY(noalloc_sum64(*toff, cnt, d_sum, &total, s));
+        if (total > 0x7fffffffull || total * slot_bytes > ar.size - ar.used)
+            return stop(1, "amg_spgemm_noalloc: long-row tables do not fit in the scratch");
+        AMG_CUDA_TRY(scan_exclusive_ws(*toff, *toff, cnt, ws2, s));
+        *keys = ar.take<int>((size_t)total);
+        if (vals) *vals = ar.take<double>((size_t)total);
+        if (!*keys || (vals && !*vals)) return stop(1, "amg_spgemm_noalloc: long-row tables do not fit in the scratch");
+        return cudaSuccess;
+    };
     // symbolic
     AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
     ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
-    AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s));
-    if (hflags[0]) { *status = 3; *msg = "amg_spgemm_noalloc: row pointers not monotone"; return cudaSuccess; }
     for (int b = 0; b < kGlobalBin; ++b)
         if (hb.count[b]) AMG_CUDA_TRY(symbolic_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, d_flags + 1, s));
     const size_t mark = ar.used;
     if (hb.count[kGlobalBin]) {
         int cnt = hb.count[kGlobalBin];
         const int *rows = d_perm + hb.start[kGlobalBin];
-        int *toff = ar.take<int>((size_t)cnt + 1);
-        int *ws2 = ar.take<int>(scan_ws_ints(cnt + 1) + 16);
-        if (!toff || !ws2) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
-        gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, d_tsize, toff); note_launch();
-        AMG_CUDA_TRY(scan_exclusive_ws(toff, toff, cnt, ws2, s));
-        int total = 0;
-        AMG_CUDA_TRY(cudaMemcpyAsync(&total, toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        int *gkeys = total >= 0 ? ar.take<int>((size_t)total) : nullptr;
-        if (!gkeys) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
-        symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, gkeys, A.rp,
-                                                                               A.ci, B.rp, B.ci, C.rp, d_flags + 1); note_launch();
+        int *toff = nullptr;
+        void *gkeys = nullptr;
+        AMG_CUDA_TRY(global_tables(cnt, rows, sizeof(int), &toff, &gkeys, nullptr));
+        if (*status) return cudaSuccess;
+        symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, (int *)gkeys,
+                                                                               A.rp, A.ci, B.rp, B.ci, C.rp, d_flags + 1); note_launch();
         AMG_CUDA_TRY(cudaGetLastError());
     }
     ar.used = mark;
-    AMG_CUDA_TRY(scan_exclusive_ws(C.rp, C.rp, n, scan_ws, s));
-    int nnz = 0;
-    AMG_CUDA_TRY(cudaMemcpyAsync(&nnz, C.rp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+    // nnz(C) in 64 bits before the int32 scan of the row counts
+    unsigned long long nnz64 = 0;
+    AMG_CUDA_TRY(noalloc_sum64(C.rp, n, d_sum, &nnz64, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hflags[1]) { *status = 4; *msg = "amg_spgemm_noalloc: hash table overflow"; return cudaSuccess; }
-    *nnz_out = nnz;
-    if (nnz > capacity) { *status = 2; *msg = "amg_spgemm_noalloc: output capacity smaller than nnz(C)"; return cudaSuccess; }
-    C.nnz = nnz;
+    if (hflags[1]) return stop(4, "amg_spgemm_noalloc: hash table overflow");
+    *nnz_out = (int64_t)nnz64;
+    if (nnz64 > 0x7ffffff0ull) return stop(1, "amg_spgemm_noalloc: more than 2^31 - 16 entries in C");
+    if ((int64_t)nnz64 > capacity) return stop(2, "amg_spgemm_noalloc: output capacity smaller than nnz(C)");
+    AMG_CUDA_TRY(scan_exclusive_ws(C.rp, C.rp, n, scan_ws, s));
+    C.nnz = (int)nnz64;
     // numeric, binned by the exact row counts
     AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
     exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
@@ -707,20 +780,14 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
     if (hb.count[kGlobalBin]) {
         int cnt = hb.count[kGlobalBin];
         const int *rows = d_perm + hb.start[kGlobalBin];
-        int *toff = ar.take<int>((size_t)cnt + 1);
-        int *ws2 = ar.take<int>(scan_ws_ints(cnt + 1) + 16);
-        if (!toff || !ws2) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
-        gather_tsize_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, d_tsize, toff); note_launch();
-        AMG_CUDA_TRY(scan_exclusive_ws(toff, toff, cnt, ws2, s));
-        int total = 0;
-        AMG_CUDA_TRY(cudaMemcpyAsync(&total, toff + cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        int *gkeys = total >= 0 ? ar.take<int>((size_t)total) : nullptr;
-        double *gvals = total >= 0 ? ar.take<double>((size_t)total) : nullptr;
-        if (!gkeys || !gvals) { *status = 1; *msg = "amg_spgemm_noalloc: long-row tables do not fit in the scratch"; return cudaSuccess; }
-        numeric_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, gkeys, gvals,
-                                                                              A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
-                                                                              C.ci, C.v, d_flags + 1); note_launch();
+        int *toff = nullptr;
+        void *gkeys = nullptr;
+        double *gvals = nullptr;
+        AMG_CUDA_TRY(global_tables(cnt, rows, sizeof(int) + sizeof(double), &toff, &gkeys, &gvals));
+        if (*status) return cudaSuccess;
+        numeric_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(cnt, rows, toff, d_tsize, (int *)gkeys,
+                                                                              gvals, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
+                                                                              C.rp, C.ci, C.v, d_flags + 1); note_launch();
         AMG_CUDA_TRY(cudaGetLastError());
     }
     AMG_CUDA_TRY(convert_rowptr_to64(C.rp, crp64, n + 1, s));

@@ -1,5 +1,5 @@
-"""Pins of the oracle's nonsymmetric path (§8(f) row 3: GMRES outer iteration, as used for
-§3's wind pressure system): dense LU with partial pivoting, flexible GMRES, and the
+"""Pins of the oracle's path for nonsymmetric operators (a GMRES outer iteration, as §3
+uses for the wind pressure system): dense LU with partial pivoting, flexible GMRES, and the
 symmetrised strength mask.
 
 Each test checks against something other than the code under test: numpy's dense solver,

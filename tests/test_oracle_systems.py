@@ -1,5 +1,5 @@
-"""Pins of the elasticity generator and of the oracle's path for systems of PDEs (§8(f) row 2:
-several unknowns per node, a multi-vector near-null space): block strength between nodes, MIS-2
+"""Pins of the elasticity generator and of the oracle's path for systems of PDEs (several
+unknowns per node, a multi-vector near-null space): block strength between nodes, MIS-2
 on the node graph, the QR tentative prolongator, and the whole hierarchy.
 
 Each test checks against something other than the code under test: closed-form energies and the

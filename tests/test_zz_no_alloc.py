@@ -4,8 +4,8 @@
 amg_spgemm_noalloc exists for callers that must not allocate device memory (a process that
 gives all GPU memory to its own pool, or a serving loop with a fixed budget); it keeps every
 temporary in a fixed array inside the library.  Both entry points sum each entry over the
-same ascending inner index with separately rounded products, so the results must agree bit
-for bit -- the same bar as the other SpGEMM parity tests -- on two calls in a row (the shared
+same ascending inner index, each term added by one fused multiply-add, so the results must
+agree bit for bit -- the same bar as the other SpGEMM parity tests -- on two calls in a row (the shared
 array keeps the previous call's contents; nothing may leak from one call into the next).
 This file is collected last, and passes alone in a fresh process as well as after the rest.
 """
@@ -90,5 +90,79 @@ def test_noalloc_spgemm_reports_small_output_and_size_limit(amg):
     assert st == amg.AMG_ERR_UNSUPPORTED and "1,000,000" in amg.amg_last_error()
     # host arrays are refused (this entry point only takes device arrays)
     st, _ = amg.amg_spgemm_noalloc(amg.csr_arg(50, *A), 60, Bd, 70, crp, cci, cv, nnz)
+    assert st == amg.AMG_ERR_INVALID_ARG
+    del keepA, keepB
+
+
+def test_noalloc_spgemm_refuses_long_row_tables_beyond_the_scratch(amg):
+    # one row of A reaches 8 rows of B with 600,000 entries each over 5,000,000 columns: its
+    # hash table (the next power of two above twice 4.8M slots, 4 bytes each) is larger than
+    # the 32 MiB array, so the call must refuse before any long-row kernel runs, leave C's
+    # column and value arrays untouched, and the next call must be exact again
+    import torch
+    ncol = 5_000_000
+    rng = np.random.default_rng(21)
+    per = 600_000
+    brp = np.arange(0, 9 * per, per, dtype=np.int64)
+    bci = np.concatenate([np.sort(rng.choice(ncol, per, replace=False)) for _ in range(8)]).astype(np.int32)
+    bv = rng.uniform(-1, 1, len(bci))
+    arp = np.array([0, 8, 9], dtype=np.int64)
+    aci = np.array(list(range(8)) + [3], dtype=np.int32)
+    av = rng.uniform(-1, 1, 9)
+    Ad, keepA = _device(amg, 2, arp, aci, av)
+    Bd, keepB = _device(amg, 8, brp, bci, bv)
+    crp = torch.full((3,), -7, dtype=torch.int64, device="cuda")
+    cap = 16
+    cci = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    cv = torch.full((cap,), 3.5, dtype=torch.float64, device="cuda")
+    st, _ = amg.amg_spgemm_noalloc(Ad, 8, Bd, ncol, crp, cci, cv, cap)
+    assert st == amg.AMG_ERR_UNSUPPORTED and "do not fit" in amg.amg_last_error()
+    assert (cci.cpu().numpy() == -7).all() and (cv.cpu().numpy() == 3.5).all()
+    del keepA, keepB
+    # a normal product right after: bit for bit the allocating entry point's
+    A = _random_csr(rng, 400, 300, 0.03)
+    B = _random_csr(rng, 300, 500, 0.03)
+    ref = amg.amg_spgemm(amg.csr_arg(400, *A), 300, amg.csr_arg(300, *B), 500)
+    nnz = len(ref[1])
+    Ad, keepA = _device(amg, 400, *A)
+    Bd, keepB = _device(amg, 300, *B)
+    crp = torch.zeros(401, dtype=torch.int64, device="cuda")
+    cci = torch.zeros(nnz, dtype=torch.int32, device="cuda")
+    cv = torch.zeros(nnz, dtype=torch.float64, device="cuda")
+    st, got = amg.amg_spgemm_noalloc(Ad, 300, Bd, 500, crp, cci, cv, nnz)
+    assert st == amg.AMG_OK and got == nnz
+    assert np.array_equal(crp.cpu().numpy(), ref[0]) and np.array_equal(cci.cpu().numpy(), ref[1])
+    assert np.array_equal(cv.cpu().numpy(), ref[2])
+    del keepA, keepB
+
+
+def test_noalloc_spgemm_rejects_bad_row_pointers_and_columns(amg):
+    # checked before any kernel walks a row: a decreasing row pointer, a last row pointer that
+    # is not nnz, and a column index outside B; C is left as it was in each case
+    import torch
+    rng = np.random.default_rng(9)
+    A = _random_csr(rng, 40, 30, 0.2)
+    B = _random_csr(rng, 30, 50, 0.2)
+    Bd, keepB = _device(amg, 30, *B)
+    crp = torch.full((41,), -7, dtype=torch.int64, device="cuda")
+    cci = torch.full((2000,), -7, dtype=torch.int32, device="cuda")
+    cv = torch.full((2000,), 3.5, dtype=torch.float64, device="cuda")
+    bad_rp = A[0].copy()
+    bad_rp[5], bad_rp[6] = bad_rp[6], bad_rp[5] - 1        # decreasing at row 5
+    bad_end = A[0].copy()
+    bad_end[-1] -= 1                                       # ends before nnz
+    bad_col = A[1].copy()
+    bad_col[len(bad_col) // 2] = 30                        # column 30 of a 30-row B
+    for rp, ci in ((bad_rp, A[1]), (bad_end, A[1]), (A[0], bad_col)):
+        Ad, keepA = _device(amg, 40, rp, ci, A[2])
+        Ad.nnz = len(ci)                                   # the entries the arrays hold
+        st, _ = amg.amg_spgemm_noalloc(Ad, 30, Bd, 50, crp, cci, cv, 2000)
+        assert st == amg.AMG_ERR_INVALID_ARG, amg.amg_last_error()
+        assert (cci.cpu().numpy() == -7).all() and (cv.cpu().numpy() == 3.5).all()
+        del keepA
+    # NULL column array with entries: refused on the host
+    Ad, keepA = _device(amg, 40, *A)
+    nullc = amg.amg_csr_t(40, int(A[0][-1]), Ad.row_ptr, None, Ad.val, 1)
+    st, _ = amg.amg_spgemm_noalloc(nullc, 30, Bd, 50, crp, cci, cv, 2000)
     assert st == amg.AMG_ERR_INVALID_ARG
     del keepA, keepB
