@@ -14,6 +14,17 @@
 // If the FP32 factorisation meets a pivot <= 0 (the operator is too ill-conditioned for FP32)
 // or the refinement does not bring E below 1e-6, the inverse is formed directly in FP64 by
 // the same factorisation and inverse kernels in double precision.
+// A large coarsest level (more than kCgMinRows rows, at most one stored entry in eight) is
+// what aggregation leaves when it stalls: no entry is strong any more, so the Jacobi-scaled
+// operator S A S (S = diag(a_ii)^-1/2) is close to the identity (condition numbers 1.1-1.2 on
+// the random-coefficient cubes).  Its inverse is then formed without a dense factorisation,
+// by conjugate gradients on the n columns of S A S X = I at once in FP64 (every column with
+// its own step lengths; one product of the sparse operator with all n columns per step), until
+// every column's residual is below 1e-15; the result is accepted once the true residual
+// max |I - S A S X| is below 1e-13, and scaled back, A^-1 = S X S.  The dense factorisation
+// costs n^3 work however sparse the operator is (a 7,004-row level with 4.5 entries per row
+// took seconds); this costs (nnz + 10 n) n per step.  When CG does not converge within
+// kCgMaxSteps steps, or a column meets a non-positive curvature, the dense path below is taken.
 // A nonsymmetric coarsest operator (GMRES outer iteration) has no Cholesky factor: its
 // inverse starts from X0 = A^T / (||A||_1 ||A||_inf), for which ||I - A X0||_2 < 1 whenever A
 // is nonsingular, and takes Newton-Schulz steps in FP32 until E < 1e-4, then in FP64.
@@ -29,7 +40,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "amg_internal.cuh"
 
@@ -42,6 +55,10 @@ constexpr int kNewtonSteps = 4;              // refinement steps at most (E0 up 
 constexpr int kGeneral32 = 64;               // nonsymmetric operators: FP32 steps from the scaled transpose
 constexpr int kGeneral64 = 8;                //   and FP64 steps after them
 constexpr int kGT = 16;                      // product tile: many blocks, so that every SM's FP64 units work
+constexpr int kCgMinRows = 512;              // the CG path for sparse coarsest levels larger than this
+constexpr int kCgMaxSteps = 240;             // CG steps at most before the dense path is taken
+constexpr int kCgCheck = 4;                  // steps between convergence checks on the host
+constexpr int kCgChunk = 32;                 // rows per partial column sum
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
 {
@@ -304,6 +321,206 @@ __global__ void newton_check_kernel(NewtonState *state)
     state->e_bits = 0ULL;
 }
 
+// ------------------------------------------------------------------------------------ large and sparse: CG
+// s_i = a_ii^-1/2 and sv = s_i a_ij s_j (bad[0] counts rows whose diagonal is missing or not
+// positive: the operator is then not SPD and the dense path reports it)
+__global__ void jacobi_scale_kernel(int n, const int *rp, const int *ci, const double *v, double *sc, int *bad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+        if (ci[e] == i) d = v[e];
+    if (!(d > 0.0)) {
+        atomicAdd(bad, 1);
+        sc[i] = 0.0;
+        return;
+    }
+    sc[i] = 1.0 / sqrt(d);
+}
+__global__ void scale_values_kernel(int n, const int *rp, const int *ci, const double *v, const double *sc, double *sv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) sv[e] = sc[i] * v[e] * sc[ci[e]];
+}
+
+// Every CG kernel works on n x n row-major arrays with thread (column c = blockIdx.x * 256 +
+// threadIdx.x, rows of chunk blockIdx.y); per-chunk partial column sums go to part[chunk][c]
+// and are added in chunk order by cg_reduce_kernel (reproducible).
+// MODE 0: Q = S A S P and part = P .* Q;  MODE 1 (check): part = max |I - S A S P| per column.
+template <int MODE>
+__global__ void __launch_bounds__(256) cg_spmm_kernel(int n, const int *rp, const int *ci, const double *sv,
+                                                       const double *P, double *Q, double *part)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
+    double acc = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        double q = 0.0;
+        for (int e = rp[i]; e < rp[i + 1]; ++e) q = fma(sv[e], P[(size_t)ci[e] * n + c], q);
+        const size_t ic = (size_t)i * n + c;
+        if (MODE == 0) {
+            Q[ic] = q;
+            acc = fma(P[ic], q, acc);
+        } else {
+            acc = fmax(acc, fabs((i == c ? 1.0 : 0.0) - q));
+        }
+    }
+    part[(size_t)blockIdx.y * n + c] = acc;
+}
+
+// per column c: sum (MODE 0: alpha = rr / pq; MODE 1: beta = rr_new / rr, rr = rr_new) or
+// max (MODE 2) of the chunk partials.  flags[0] += 1 for a non-positive curvature p.q;
+// bits[0] = max_c rr (bit patterns of non-negative doubles order as the values).
+template <int MODE>
+__global__ void cg_reduce_kernel(int n, int chunks, const double *part, double *rr, double *coef, int *flags,
+                                 unsigned long long *bits)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    double t = 0.0;
+    for (int k = 0; k < chunks; ++k) {
+        const double x = part[(size_t)k * n + c];
+        t = MODE == 2 ? fmax(t, x) : t + x;
+    }
+    if (MODE == 0) {
+        const double r = rr[c];
+        if (r > 0.0 && !(t > 0.0)) atomicAdd(flags, 1);
+        coef[c] = (r > 0.0 && t > 0.0) ? r / t : 0.0;
+    } else if (MODE == 1) {
+        const double r = rr[c];
+        coef[c] = r > 0.0 ? t / r : 0.0;
+        rr[c] = t;
+        atomicMax(bits, (unsigned long long)__double_as_longlong(t));
+    } else {
+        atomicMax(bits, (unsigned long long)__double_as_longlong(t));
+    }
+}
+
+// X += alpha P, R -= alpha Q, part = R .* R
+__global__ void __launch_bounds__(256) cg_update_kernel(int n, const double *alpha, const double *P, const double *Q,
+                                                         double *X, double *R, double *part)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
+    const double a = alpha[c];
+    double acc = 0.0;
+    for (int i = i0; i < i1; ++i) {
+        const size_t ic = (size_t)i * n + c;
+        X[ic] = fma(a, P[ic], X[ic]);
+        const double r = fma(-a, Q[ic], R[ic]);
+        R[ic] = r;
+        acc = fma(r, r, acc);
+    }
+    part[(size_t)blockIdx.y * n + c] = acc;
+}
+
+// P = R + beta P (FIRST: X = 0, R = P = I)
+template <bool FIRST>
+__global__ void __launch_bounds__(256) cg_direction_kernel(int n, const double *beta, double *X, double *R, double *P)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
+    const double bc = FIRST ? 0.0 : beta[c];
+    for (int i = i0; i < i1; ++i) {
+        const size_t ic = (size_t)i * n + c;
+        if (FIRST) {
+            const double e = (i == c) ? 1.0 : 0.0;
+            X[ic] = 0.0;
+            R[ic] = e;
+            P[ic] = e;
+        } else {
+            P[ic] = fma(bc, P[ic], R[ic]);
+        }
+    }
+}
+
+// inv = S X S
+__global__ void unscale_inverse_kernel(int n, const double *sc, const double *X, double *inv)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
+    for (int i = i0; i < i1; ++i) {
+        const size_t ic = (size_t)i * n + c;
+        inv[ic] = sc[i] * X[ic] * sc[c];
+    }
+}
+
+// The CG path; *taken = false (inv untouched) when the operator does not qualify or CG does
+// not reach the accuracy.  mats: four n^2 doubles (X, R, P, Q); aux: n + nnz + (chunks + 4) n
+// doubles plus 16 bytes of flags.
+cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_doubles, double *inv, bool *taken,
+                       cudaStream_t s)
+{
+    *taken = false;
+    const int n = A.n;
+    const size_t nn = (size_t)n * n;
+    const int chunks = (n + kCgChunk - 1) / kCgChunk;
+    if (n <= kCgMinRows || (size_t)A.nnz * 8 > nn) return cudaSuccess;
+    const size_t need = (size_t)n + 16 + (size_t)A.nnz + 16 + (size_t)(chunks + 4) * n + 16;
+    if (need > aux_doubles) return cudaSuccess;
+    double *X = mats, *R = X + nn, *P = R + nn, *Q = P + nn;
+    double *sc = aux, *sv = sc + n + 16, *part = sv + A.nnz + 16, *rr = part + (size_t)chunks * n;
+    double *coef = rr + n;
+    int *flags = (int *)(coef + n + 16);
+    unsigned long long *bits = (unsigned long long *)(flags + 4);
+    AMG_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int) + 2 * sizeof(unsigned long long), s));
+    jacobi_scale_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, flags); note_launch();
+    scale_values_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, sv); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    int hflag = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hflag) return cudaSuccess;
+    const dim3 blk(256), grd((n + 255) / 256, chunks);
+    const int cgrid = (n + 255) / 256;
+    cg_direction_kernel<true><<<grd, blk, 0, s>>>(n, nullptr, X, R, P); note_launch();
+    std::vector<double> ones((size_t)n, 1.0);
+    AMG_CUDA_TRY(cudaMemcpyAsync(rr, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    bool converged = false;
+    for (int k = 0; k < kCgMaxSteps && !converged; ++k) {
+        if (k > 0) { cg_direction_kernel<false><<<grd, blk, 0, s>>>(n, coef, X, R, P); note_launch(); }
+        cg_spmm_kernel<0><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, P, Q, part); note_launch();
+        cg_reduce_kernel<0><<<cgrid, 256, 0, s>>>(n, chunks, part, rr, coef, flags, bits); note_launch();
+        cg_update_kernel<<<grd, blk, 0, s>>>(n, coef, P, Q, X, R, part); note_launch();
+        AMG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s));
+        cg_reduce_kernel<1><<<cgrid, 256, 0, s>>>(n, chunks, part, rr, coef, flags, bits); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        if ((k + 1) % kCgCheck == 0 || k + 1 == kCgMaxSteps) {
+            unsigned long long hb = 0;
+            AMG_CUDA_TRY(cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaMemcpyAsync(&hb, bits, sizeof hb, cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (hflag) return cudaSuccess;                       // not positive definite
+            double rmax = 0.0;
+            std::memcpy(&rmax, &hb, sizeof rmax);
+            if (!(rmax == rmax)) return cudaSuccess;             // NaN
+            converged = rmax <= 1e-30;                           // every column's ||r|| <= 1e-15
+        }
+    }
+    if (!converged) return cudaSuccess;
+    // the true residual
+    AMG_CUDA_TRY(cudaMemsetAsync(bits + 1, 0, sizeof(unsigned long long), s));
+    cg_spmm_kernel<1><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, X, nullptr, part); note_launch();
+    cg_reduce_kernel<2><<<cgrid, 256, 0, s>>>(n, chunks, part, nullptr, nullptr, nullptr, bits + 1); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    unsigned long long he = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&he, bits + 1, sizeof he, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    double err = 0.0;
+    std::memcpy(&err, &he, sizeof err);
+    if (!(err < 1e-13)) return cudaSuccess;
+    unscale_inverse_kernel<<<grd, blk, 0, s>>>(n, sc, X, inv); note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    *taken = true;
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t factor_and_invert(int n, T *a, T *lt, T *rdiag, T *inv, int *info, cudaStream_t s)
 {
@@ -408,6 +625,17 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
         if (!(err < 1e-6))             // singular, or too ill-conditioned: info = -1 (all bits set)
             return cudaMemsetAsync(info_dev, 0xFF, sizeof(int), s);
         return cudaMemcpyAsync(inv, res, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+    }
+    // a large, sparse operator (aggregation stalled on it): the CG path, in the memory of the
+    // dense matrices (rebuilt if CG gives up)
+    if (n > kCgMinRows && (size_t)A.nnz * 8 <= nn) {
+        bool taken = false;
+        AMG_CUDA_TRY(cg_inverse(A, Ad, (double *)Af, nn, inv, &taken, s));
+        if (taken) return cudaSuccess;
+        AMG_CUDA_TRY(cudaMemsetAsync(Ad, 0, sizeof(double) * nn, s));
+        dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
+        convert_dense_kernel<double, float><<<cgrid, 256, 0, s>>>(nn, Ad, Af); note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
     }
     // stage 1: FP32 factor and inverse (X0 in Y's memory, as floats)
     float *Xf = (float *)Y;
