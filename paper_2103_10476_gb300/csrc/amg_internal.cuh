@@ -186,9 +186,20 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_d
 
 // --------------------------------------------------------------------------------- solve.cu
 // SpMV launch plan of one matrix: lanes per row and the shared-memory tile (entries; 0 = none)
+// Rows far longer than the rest of their operator (a stalled coarse level can hold rows coupled
+// to every other row): each is summed by a whole block of its own (spmv_long_kernel, solve.cu)
+// and skipped by the row-tile kernel, whose lanes would otherwise walk it as one serial chain.
+// The list travels by value in the kernel's parameters (no device memory of its own).
+constexpr int kMaxLongRows = 128;
+struct LongRows {
+    int count = 0;               // rows listed
+    int len = 0x7fffffff;        // rows with more entries than this are long
+    int rows[kMaxLongRows];
+};
 struct SpmvPlan {
     int lpr = 2;
     int cap = 0;
+    LongRows lr;
     // sliced-ELL copy of the matrix read by the solve's products (solve.cu; ns = 0: none).
     // Columns and the layout are shared by the FP64 and FP32 values.
     int ns = 0;

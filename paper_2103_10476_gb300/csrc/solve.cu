@@ -13,6 +13,7 @@
 // to log2(LPR) per row.  The working type T is double (FP64 path) or float (the mixed
 // path's V-cycle); accumulation is in T.  Partial dot products are per block, in a fixed
 // order, so every reduction is bitwise reproducible.
+#include <algorithm>
 #include <mutex>
 
 #include <vector>
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
                                                                  int cap, double *partial, double *result,
-                                                                 unsigned *counter, int *err)
+                                                                 unsigned *counter, int *err, int long_len)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -146,7 +147,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     const int row = r0 + threadIdx.x / LPR;
     const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    if (row < r1 && tile_ok) {
+    // rows longer than long_len were finished by spmv_long_kernel, launched before this kernel
+    const bool is_long = row < r1 && rp[row + 1] - rp[row] > long_len;
+    if (row < r1 && tile_ok && !is_long) {
         const int b = rp[row], e = rp[row + 1];
         if (staged) {
             for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         }
         __syncthreads();
         const int rw = r0 + (int)threadIdx.x;
-        if ((int)threadIdx.x < RPB && rw < r1 && tile_ok) {
+        if ((int)threadIdx.x < RPB && rw < r1 && tile_ok && rp[rw + 1] - rp[rw] <= long_len) {
             const T sr = LPR == 2 ? ps[threadIdx.x] + ps[RPB + threadIdx.x] : ps[threadIdx.x];
             if (MODE == MODE_Y) {
                 y[rw] = sr;
@@ -197,7 +200,18 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         __syncthreads();
         rq = rq_s;
     }
-    if (row < r1 && lane == 0 && tile_ok) {
+    if (row < r1 && lane == 0 && tile_ok && is_long) {
+        // the long row's value is in y already: only its share of the dot products here
+        if (MODE == MODE_DOT) {
+            contrib = (double)x[row] * (double)y[row];
+        } else if (MODE == MODE_SCALEDOT) {
+            contrib = (double)x[row] * (double)y[row];
+        } else if (MODE == MODE_POWER) {
+            const double yi = (double)y[row];
+            contrib = (double)x[row] * yi;
+            contrib2 = yi * yi;
+        }
+    } else if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
         } else if (MODE == MODE_RESID) {
@@ -261,6 +275,70 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     }
 }
 
+// One block per long row (the plan's list, by value): the row's sum by every thread of the
+// block in a fixed order (strided partial sums, a shuffle tree per warp, the warps in order),
+// then the same update as spmv_tile_kernel's for that row.  DOT, SCALEDOT and POWER store the
+// row's y only; spmv_tile_kernel, launched after this kernel, adds the row's share of the dot
+// products in its block's fixed order.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_long_kernel(LongRows lr, const int *__restrict__ rp,
+                                                                 const int *__restrict__ ci,
+                                                                 const T *__restrict__ v, const T *__restrict__ x,
+                                                                 T *y, const T *__restrict__ f,
+                                                                 const T *__restrict__ aux, T *d, T c1, T c2)
+{
+    __shared__ T ws[kSpmvThreads / 32];
+    if ((int)blockIdx.x >= lr.count) return;
+    const int row = lr.rows[blockIdx.x];
+    const int b = rp[row], e = rp[row + 1];
+    T sum = T(0);
+    for (int k = b + (int)threadIdx.x; k < e; k += kSpmvThreads) sum += v[k] * x[ci[k]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    T sr = T(0);
+    for (int w = 0; w < kSpmvThreads / 32; ++w) sr += ws[w];
+    if (MODE == MODE_Y || MODE == MODE_DOT) {
+        y[row] = sr;
+    } else if (MODE == MODE_RESID) {
+        y[row] = f[row] - sr;
+    } else if (MODE == MODE_CHEB) {
+        T r = f[row] - sr;
+        T dn = c1 * d[row] + c2 * (aux[row] * r);
+        d[row] = dn;
+        y[row] = x[row] + dn;
+    } else if (MODE == MODE_PROLONG) {
+        y[row] += sr;
+    } else if (MODE == MODE_SCALEDOT) {
+        y[row] = sr / aux[row];
+    } else {
+        const double rq = 1.0 / __dsqrt_rn((double)f[0]);
+        y[row] = (T)(((double)sr / (double)aux[row]) * rq);
+    }
+}
+
+// rows longer than len: count (cnt[0]) and the first kMaxLongRows of them (order of arrival;
+// sorted on the host)
+__global__ void long_rows_kernel(int n, const int *rp, int len, int *cnt, int *rows)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || rp[i + 1] - rp[i] <= len) return;
+    const int k = atomicAdd(cnt, 1);
+    if (k < kMaxLongRows) rows[k] = i;
+}
+
+// per threshold t = 0..7: rows longer than base << t
+__global__ void long_hist_kernel(int n, const int *rp, int base, int *hist)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int len = rp[i + 1] - rp[i];
+    for (int t = 0; t < 8; ++t)
+        if (len > (base << t)) atomicAdd(&hist[t], 1);
+}
+
 int pick_lpr(double avg_row)
 {
     if (avg_row <= 40.0) return 2;
@@ -284,13 +362,70 @@ int pick_lpr_rows(double avg_row, int n)
     return lpr;
 }
 
-__global__ void span_max_kernel(int n, const int *rp, int rpb, int *out)
+// the largest block range of a plan, over the blocks without a long row (a block holding one is
+// not staged: its range exceeds the tile, and its short rows read global memory)
+__global__ void span_max_kernel(int n, const int *rp, int rpb, int long_len, int *out)
 {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     int r0 = b * rpb;
     if (r0 >= n) return;
     int r1 = min(n, r0 + rpb);
+    for (int r = r0; r < r1; ++r)
+        if (rp[r + 1] - rp[r] > long_len) return;
     atomicMax(out, rp[r1] - rp[r0]);
+}
+
+// The long rows of a plan: more than max(512, 8 x the mean row) entries, the threshold doubled
+// (up to 7 times) until at most kMaxLongRows rows exceed it.  One synchronisation per call.
+// lr.len stays "none" when no row qualifies.
+cudaError_t long_rows_plan(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
+                           const int64_t *nnzs, cudaStream_t s)
+{
+    std::vector<int> base((size_t)count, 0);
+    int *d = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * (size_t)count * (9 + kMaxLongRows), s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * (size_t)count * (9 + kMaxLongRows), s);
+    std::vector<int> h((size_t)count * (9 + kMaxLongRows), 0);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        plans[k]->lr = LongRows();
+        const int n = ns[k];
+        if (n == 0 || nnzs[k] == 0) continue;
+        const double avg = (double)nnzs[k] / n;
+        base[(size_t)k] = (int)std::min(1.0e9, std::max(512.0, 8.0 * avg));
+        long_hist_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, rps[k], base[(size_t)k], d + (size_t)k * (9 + kMaxLongRows));
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    bool any = false;
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int *hist = h.data() + (size_t)k * (9 + kMaxLongRows);
+        int t = 0;
+        while (t < 8 && hist[t] > kMaxLongRows) ++t;
+        if (t == 8 || hist[t] == 0) continue;
+        plans[k]->lr.len = base[(size_t)k] << t;
+        int *slot = d + (size_t)k * (9 + kMaxLongRows);
+        e = cudaMemsetAsync(slot + 8, 0, sizeof(int), s);
+        if (e == cudaSuccess) {
+            long_rows_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], plans[k]->lr.len, slot + 8, slot + 9);
+            note_launch();
+            e = cudaGetLastError();
+        }
+        any = true;
+    }
+    if (any && e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (any && e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    for (int k = 0; any && e == cudaSuccess && k < count; ++k) {
+        if (plans[k]->lr.len == 0x7fffffff) continue;
+        const int *slot = h.data() + (size_t)k * (9 + kMaxLongRows);
+        LongRows &lr = plans[k]->lr;
+        lr.count = std::min(slot[8], kMaxLongRows);
+        std::copy(slot + 9, slot + 9 + lr.count, lr.rows);
+        std::sort(lr.rows, lr.rows + lr.count);
+    }
+    return e;
 }
 
 // Plans of several matrices with one synchronisation: every span kernel is queued first,
@@ -299,6 +434,7 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
                        cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
+    AMG_CUDA_TRY(long_rows_plan(count, plans, rps, ns, nnzs, s));
     int *d = nullptr;
     std::vector<int> h((size_t)count, 0);
     AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * (size_t)count, s));
@@ -310,7 +446,8 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
         pl->cap = 0;
         if (n == 0 || nnzs[k] == 0) continue;
         const int nb = spmv_blocks(n, pl->lpr);
-        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rps[k], kSpmvThreads / pl->lpr, d + k); note_launch();
+        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rps[k], kSpmvThreads / pl->lpr, pl->lr.len, d + k);
+        note_launch();
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, s);
@@ -323,22 +460,11 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
 
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s)
 {
-    plan->lpr = pick_lpr_rows(n ? (double)nnz / n : 1.0, n);
-    plan->cap = 0;
-    if (n == 0 || nnz == 0) return cudaSuccess;
-    int *d = nullptr, h = 0;
-    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int), s));
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), s);
-    const int nb = spmv_blocks(n, plan->lpr);
-    if (e == cudaSuccess) {
-        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rp, kSpmvThreads / plan->lpr, d); note_launch();
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(d, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    plan->cap = h + 8 < kMaxTile ? h + 8 : kMaxTile;
-    return e;
+    SpmvPlan *pls[1] = {plan};
+    const int *rps[1] = {rp};
+    const int ns[1] = {n};
+    const int64_t nz[1] = {nnz};
+    return spmv_plans(1, pls, rps, ns, nz, s);
 }
 
 static int *g_spmv_err = nullptr;   // device error flag of the bounded waits (allocated once)
@@ -527,7 +653,7 @@ cudaError_t sell_fill_t(int n, const int *rp, const int *ci, const T *v, int ns,
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
-                        cudaStream_t s)
+                        cudaStream_t s, int long_len)
 {
     const int smem = tile_bytes<T>(cap);
     // the attribute is set once per instantiation (any thread may get here first)
@@ -539,7 +665,7 @@ cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T
     });
     AMG_CUDA_TRY(cfg_err);
     spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag()); note_launch();
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), long_len); note_launch();
     return cudaGetLastError();
 }
 
@@ -550,18 +676,33 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
 {
     if (n == 0) return cudaSuccess;
     if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr)) &&
-        pl.ns > 0 && pl.lpr == 2) {
+        pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0) {
         const T *sv = sell_values<T>(pl);
         if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s);
     }
+    int long_len = 0x7fffffff;
+    if (pl.lr.count > 0) {
+        spmv_long_kernel<T, MODE><<<pl.lr.count, kSpmvThreads, 0, s>>>(pl.lr, rp, ci, v, x, y, f, aux, d, c1, c2);
+        note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+        long_len = pl.lr.len;
+    }
     switch (pl.lpr) {
-    case 2: return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    case 4: return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
-    case 8: return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+    case 2:
+        return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
+                                       long_len);
+    case 4:
+        return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
+                                       long_len);
+    case 8:
+        return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
+                                       long_len);
     case 16:
-        return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+        return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
+                                        long_len);
     default:
-        return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s);
+        return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
+                                        long_len);
     }
 }
 
