@@ -8,6 +8,7 @@
 //
 // Rows are binned by table size so each launch uses one size: the symbolic phase by an
 // upper bound (min(products, columns)), the numeric phase by the exact count.
+#include <algorithm>
 #include <mutex>
 #include <stdio.h>
 #include <string>
@@ -361,6 +362,330 @@ __global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff,
                 overflow);
 }
 
+// ------------------------------------------------------------------------------------ numeric by chains
+// The numeric phase of the allocating product runs in three passes instead of numeric_row's one:
+//   pattern  C's sorted columns per row and, per entry c_ij, its number of terms (how many
+//            a_ik b_kj reach it) -- integer work only;
+//   place    every product's (a_ik, b_kj) into the chain of its entry, in the row's product
+//            order (k ascending), so chain q holds c_q's terms in the order they are summed;
+//   chain    each lane of a warp sums whole chains, c = fma(a, b, c) from 0 in chain order,
+//            taking the next chain of the warp's range when it finishes one.
+// The sums are numeric_row's, bit for bit; but every FP64 instruction of the chain pass has
+// all 32 lanes busy (until the last chains of a range), where numeric_row issues one FP64
+// instruction per distinct column per batch of 32 products, most of its lanes idle.  Rows of
+// more than 2048 entries count their columns in a dense array in shared memory (one block
+// per row) when B has at most kDenseCols columns, instead of one warp on a global hash table.
+constexpr int kDenseCols = 49152;          // 192 KB of int counters in shared memory
+constexpr int kDenseThreads = 512;
+constexpr int kChainOutputs = 256;         // entries of C per warp of the chain pass
+
+// counts[ncolB] of row i's products per column (block-wide, any order)
+__device__ __forceinline__ void dense_count_row(int i, const int *arp, const int *aci, const int *brp, const int *bci,
+                                                int ncolB, int *cnt)
+{
+    for (int j = threadIdx.x; j < ncolB; j += blockDim.x) cnt[j] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int e = arp[i] + warp; e < arp[i + 1]; e += nw) {
+        const int k = aci[e];
+        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) atomicAdd(&cnt[bci[f]], 1);
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kDenseThreads) dense_symbolic_kernel(int cnt_rows, const int *rows, const int *arp,
+                                                                       const int *aci, const int *brp, const int *bci,
+                                                                       int ncolB, int *ccnt)
+{
+    extern __shared__ int dcnt[];
+    __shared__ int wsum[kDenseThreads / 32];
+    if ((int)blockIdx.x >= cnt_rows) return;
+    const int i = rows[blockIdx.x];
+    dense_count_row(i, arp, aci, brp, bci, ncolB, dcnt);
+    int mine = 0;
+    for (int j = threadIdx.x; j < ncolB; j += blockDim.x) mine += dcnt[j] > 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_down_sync(kFullMask, mine, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+        ccnt[i] = t;
+    }
+}
+
+// columns of row i in ascending order and their term counts, from the dense counters: thread
+// t owns the contiguous column range [t cpt, (t + 1) cpt)
+__global__ void __launch_bounds__(kDenseThreads) dense_pattern_kernel(int cnt_rows, const int *rows, const int *arp,
+                                                                      const int *aci, const int *brp, const int *bci,
+                                                                      int ncolB, const int *crp, int *cci,
+                                                                      int *ccount, int *overflow)
+{
+    extern __shared__ int dcnt[];
+    __shared__ int wsum[kDenseThreads / 32];
+    if ((int)blockIdx.x >= cnt_rows) return;
+    const int i = rows[blockIdx.x];
+    dense_count_row(i, arp, aci, brp, bci, ncolB, dcnt);
+    const int cpt = (ncolB + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int j0 = threadIdx.x * cpt, j1 = min(ncolB, j0 + cpt);
+    int mine = 0;
+    for (int j = j0; j < j1; ++j) mine += dcnt[j] > 0;
+    // exclusive scan of the per-thread counts, threads in order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < warp) before += wsum[w];
+        total += wsum[w];
+    }
+    const int out = crp[i];
+    if (total != crp[i + 1] - out) {
+        if (threadIdx.x == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    int p = out + before + incl - mine;
+    for (int j = j0; j < j1; ++j) {
+        const int c = dcnt[j];
+        if (c > 0) {
+            cci[p] = j;
+            ccount[p] = c;
+            ++p;
+        }
+    }
+}
+
+// hash-table form (one warp per row): columns and their term counts, sorted by column
+__device__ void pattern_row(int i, const int *arp, const int *aci, const int *brp, const int *bci, int *keys, int *cnts,
+                            int S, const int *crp, int *cci, int *ccount, int *overflow)
+{
+    const int lane = threadIdx.x & 31;
+    for (int t = lane; t < S; t += 32) { keys[t] = -1; cnts[t] = 0; }
+    __syncwarp();
+    const int ae = arp[i + 1];
+    for (int eb = arp[i]; eb < ae; eb += 32) {
+        const int e = eb + lane;
+        int len = 0, fb = 0;
+        if (e < ae) {
+            const int k = aci[e];
+            fb = brp[k];
+            len = brp[k + 1] - fb;
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFullMask, incl, 31);
+        const int excl = incl - len;
+        for (int qb = 0; qb < total; qb += 32) {
+            ProductBatch pb = product_at<false>(qb + lane, total, incl, excl, fb, 0.0, bci, nullptr);
+            if (pb.valid) {
+                bool fresh;
+                const int slot = hash_insert(keys, S, pb.j, fresh, overflow);
+                if (slot >= 0) atomicAdd(&cnts[slot], 1);
+            }
+        }
+    }
+    __syncwarp();
+    // compact occupied slots to the front, in slot order
+    int base = 0;
+    for (int t0 = 0; t0 < S; t0 += 32) {
+        const int t = t0 + lane;
+        const int key = keys[t], c = cnts[t];
+        const bool occ = key != -1;
+        const unsigned m = __ballot_sync(kFullMask, occ);
+        __syncwarp();
+        if (occ) {
+            const int p = base + __popc(m & ((1u << lane) - 1u));
+            keys[p] = key;
+            cnts[p] = c;
+        }
+        base += __popc(m);
+        __syncwarp();
+    }
+    const int cnt = base;
+    const int out = crp[i];
+    if (cnt != crp[i + 1] - out) {
+        if (lane == 0) atomicAdd(overflow, 1);
+        return;
+    }
+    if (cnt <= 512) {
+        for (int t = lane; t < cnt; t += 32) {
+            const int key = keys[t];
+            int rank = 0;
+            for (int u = 0; u < cnt; ++u) rank += keys[u] < key;
+            cci[out + rank] = key;
+            ccount[out + rank] = cnts[t];
+        }
+        return;
+    }
+    int P2 = 1;
+    while (P2 < cnt) P2 <<= 1;
+    for (int t = cnt + lane; t < P2; t += 32) { keys[t] = 0x7fffffff; cnts[t] = 0; }
+    __syncwarp();
+    for (int kk = 2; kk <= P2; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < P2; t += 32) {
+                const int ixj = t ^ jj;
+                if (ixj > t) {
+                    const bool asc = (t & kk) == 0;
+                    const int a = keys[t], b = keys[ixj];
+                    if ((a > b) == asc) {
+                        keys[t] = b; keys[ixj] = a;
+                        const int ca = cnts[t];
+                        cnts[t] = cnts[ixj]; cnts[ixj] = ca;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    for (int t = lane; t < cnt; t += 32) {
+        cci[out + t] = keys[t];
+        ccount[out + t] = cnts[t];
+    }
+}
+
+template <int S>
+__global__ void pattern_shared_kernel(int cnt, const int *rows, const int *arp, const int *aci, const int *brp,
+                                      const int *bci, const int *crp, int *cci, int *ccount, int *overflow)
+{
+    extern __shared__ int smem_pat[];
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    const int row_slot = blockIdx.x * warps + w;
+    if (row_slot >= cnt) return;
+    pattern_row(rows[row_slot], arp, aci, brp, bci, smem_pat + 2 * w * S, smem_pat + (2 * w + 1) * S, S, crp, cci,
+                ccount, overflow);
+}
+
+__global__ void pattern_global_kernel(int cnt, const int *rows, const int *toff, const int *tsize, int *gkeys,
+                                      int *gcnts, const int *arp, const int *aci, const int *brp, const int *bci,
+                                      const int *crp, int *cci, int *ccount, int *overflow)
+{
+    const int row_slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row_slot >= cnt) return;
+    const int i = rows[row_slot];
+    pattern_row(i, arp, aci, brp, bci, gkeys + toff[row_slot], gcnts + toff[row_slot], tsize[i], crp, cci, ccount,
+                overflow);
+}
+
+// Every product of row i (warp per row, k ascending, then B's row order) to its chain:
+// position off[q] + (terms of q already placed) for the entry q of its column, found by binary
+// search in the row's sorted columns.  Rows are taken from the end of `rows` first (the bins
+// of the longest rows come last there), so that the longest start first.
+__global__ void place_kernel(int cnt, const int *rows, const int *arp, const int *aci, const double *av, const int *brp,
+                             const int *bci, const double *bv, const int *crp, const int *cci, const int *off, int *run,
+                             double *sa, double *sb)
+{
+    const int slot = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (slot >= cnt) return;
+    const int i = rows[cnt - 1 - slot];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int rb = crp[i], nc = crp[i + 1] - rb;
+    const int *cols = cci + rb;
+    const int ae = arp[i + 1];
+    for (int eb = arp[i]; eb < ae; eb += 32) {
+        const int e = eb + lane;
+        int len = 0, fb = 0;
+        double a = 0.0;
+        if (e < ae) {
+            const int k = aci[e];
+            a = av[e];
+            fb = brp[k];
+            len = brp[k + 1] - fb;
+        }
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFullMask, incl, 31);
+        const int excl = incl - len;
+        for (int qb = 0; qb < total; qb += 32) {
+            ProductBatch pb = product_at<true>(qb + lane, total, incl, excl, fb, a, bci, bv);
+            int q = -1 - lane;
+            if (pb.valid) {
+                int lo = 0, hi = nc;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (cols[mid] < pb.j) lo = mid + 1; else hi = mid;
+                }
+                q = rb + lo;
+            }
+            const unsigned same = __match_any_sync(kFullMask, q);
+            const int rib = __popc(same & lt), grp = __popc(same);
+            const int base = pb.valid ? run[q] : 0;
+            if (pb.valid) {
+                const int pos = off[q] + base + rib;
+                sa[pos] = pb.a;
+                sb[pos] = pb.b;
+            }
+            __syncwarp();
+            if (pb.valid && rib == grp - 1) run[q] = base + grp;
+            __syncwarp();
+        }
+    }
+}
+
+// c_q = sum of its chain, fma from 0 in chain order; warp w owns entries [w K, (w + 1) K), each
+// lane sums one chain at a time and takes the warp's next chain when it finishes
+__global__ void __launch_bounds__(256) chain_kernel(int nnz, const int *off, const double *sa, const double *sb,
+                                                    double *cv)
+{
+    const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int q0 = warp * kChainOutputs;
+    if (q0 >= nnz) return;
+    const int q1 = min(nnz, q0 + kChainOutputs);
+    int q = q0 + lane, next = q0 + 32;
+    int pos = 0, end = 0;
+    double acc = 0.0;
+    if (q < q1) { pos = off[q]; end = off[q + 1]; }
+    for (;;) {
+        const bool act = q < q1;
+        if (!__any_sync(kFullMask, act)) break;
+        if (act) {
+            acc = __fma_rn(sa[pos], sb[pos], acc);
+            ++pos;
+        }
+        const bool fin = act && pos >= end;
+        const unsigned fm = __ballot_sync(kFullMask, fin);
+        if (fin) {
+            cv[q] = acc;
+            acc = 0.0;
+            q = next + __popc(fm & lt);
+            if (q < q1) { pos = off[q]; end = off[q + 1]; }
+        }
+        next += __popc(fm);
+    }
+}
+
+// 64-bit sum of n non-negative ints (a total an int32 scan is about to form)
+__global__ void sum64_kernel(const int *v, int n, unsigned long long *out)
+{
+    unsigned long long acc = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = v[i];
+        acc += x > 0 ? (unsigned long long)x : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFullMask, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
 // ------------------------------------------------------------------------------------ host side
 namespace {
 
@@ -448,6 +773,56 @@ cudaError_t numeric_bin(int b, int cnt, const int *rows, const DevCsr &A, const 
     }
 }
 
+template <int S>
+cudaError_t launch_pattern(int cnt, const int *rows, const DevCsr &A, const DevCsr &B, const int *crp, int *cci,
+                           int *ccount, int *ovf, cudaStream_t s)
+{
+    int warps = kSmemBudget / (S * 8);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    const size_t smem = (size_t)warps * S * 8;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [smem] {
+        attr = cudaFuncSetAttribute(pattern_shared_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)std::max<size_t>(smem, (size_t)kSmemBudget));
+    });
+    AMG_CUDA_TRY(attr);
+    pattern_shared_kernel<S><<<(cnt + warps - 1) / warps, warps * 32, smem, s>>>(cnt, rows, A.rp, A.ci, B.rp, B.ci, crp,
+                                                                                cci, ccount, ovf); note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t pattern_bin(int b, int cnt, const int *rows, const DevCsr &A, const DevCsr &B, const int *crp, int *cci,
+                        int *ccount, int *ovf, cudaStream_t s)
+{
+    switch (b) {
+    case 0: return launch_pattern<32>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 1: return launch_pattern<64>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 2: return launch_pattern<128>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 3: return launch_pattern<256>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 4: return launch_pattern<512>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 5: return launch_pattern<1024>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 6: return launch_pattern<2048>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    case 7: return launch_pattern<4096>(cnt, rows, A, B, crp, cci, ccount, ovf, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t dense_attr()
+{
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(dense_symbolic_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kDenseCols * (int)sizeof(int));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(dense_pattern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kDenseCols * (int)sizeof(int));
+    });
+    return attr;
+}
+
 // table offsets (int) for the rows of the global bin; returns total slots
 cudaError_t global_tables(int cnt, const int *rows, const int *tsize, int **toff, int64_t *total, cudaStream_t s)
 {
@@ -464,6 +839,73 @@ cudaError_t global_tables(int cnt, const int *rows, const int *tsize, int **toff
     AMG_CUDA_TRY(scan_exclusive(*toff, *toff, cnt, s));
     *total = sum;
     return cudaSuccess;
+}
+
+// The numeric phase by chains.  *done = false (nothing written, no error) when the products of
+// the whole row set do not fit the int32 chain offsets; the caller then runs numeric_row.
+cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, const Bins &hb, const int *d_perm,
+                           const int *d_tsize, int *d_ovf, bool *done, cudaStream_t s)
+{
+    *done = false;
+    const int nnz = (int)C.nnz;
+    int *off = nullptr, *run = nullptr, *toff = nullptr, *gkeys = nullptr;
+    unsigned long long *d_sum = nullptr;
+    double *sa = nullptr, *sb = nullptr;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMallocAsync(&off, sizeof(int) * ((size_t)nnz + 1), s))) break;
+        if ((e = cudaMallocAsync(&run, sizeof(int) * (size_t)nnz, s))) break;
+        if ((e = cudaMallocAsync(&d_sum, sizeof(unsigned long long), s))) break;
+        if ((e = cudaMemsetAsync(run, 0, sizeof(int) * (size_t)nnz, s))) break;
+        if ((e = cudaMemsetAsync(d_sum, 0, sizeof(unsigned long long), s))) break;
+        // pattern: C's columns (sorted) and each entry's term count (into off)
+        for (int b = 0; b < kGlobalBin && !e; ++b)
+            if (hb.count[b]) e = pattern_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, C.ci, off, d_ovf, s);
+        if (e) break;
+        if (hb.count[kGlobalBin]) {
+            const int cnt = hb.count[kGlobalBin];
+            const int *rows = d_perm + hb.start[kGlobalBin];
+            if (B.ncol <= kDenseCols) {
+                if ((e = dense_attr())) break;
+                dense_pattern_kernel<<<cnt, kDenseThreads, sizeof(int) * (size_t)B.ncol, s>>>(
+                    cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp, C.ci, off, d_ovf); note_launch();
+                if ((e = cudaGetLastError())) break;
+            } else {
+                int64_t total = 0;
+                if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
+                if ((e = cudaMallocAsync(&gkeys, sizeof(int) * 2 * (size_t)total, s))) break;
+                pattern_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
+                    cnt, rows, toff, d_tsize, gkeys, gkeys + total, A.rp, A.ci, B.rp, B.ci, C.rp, C.ci, off, d_ovf);
+                note_launch();
+                if ((e = cudaGetLastError())) break;
+            }
+        }
+        // the number of products, in 64 bits, before the int32 scan of the term counts
+        sum64_kernel<<<grid_for(nnz, 256, 1024), 256, 0, s>>>(off, nnz, d_sum); note_launch();
+        if ((e = cudaGetLastError())) break;
+        unsigned long long total = 0;
+        if ((e = cudaMemcpyAsync(&total, d_sum, sizeof total, cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaStreamSynchronize(s))) break;
+        if (total > 0x7ffffff0ull) break;                    // too many products: numeric_row instead
+        if ((e = scan_exclusive(off, off, nnz, s))) break;
+        if ((e = cudaMallocAsync(&sa, sizeof(double) * (size_t)(total + 1), s))) break;
+        if ((e = cudaMallocAsync(&sb, sizeof(double) * (size_t)(total + 1), s))) break;
+        place_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, d_perm, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
+                                                                   C.ci, off, run, sa, sb); note_launch();
+        if ((e = cudaGetLastError())) break;
+        const int64_t warps = ((int64_t)nnz + kChainOutputs - 1) / kChainOutputs;
+        chain_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(nnz, off, sa, sb, C.v); note_launch();
+        if ((e = cudaGetLastError())) break;
+        *done = true;
+    } while (0);
+    if (off) cudaFreeAsync(off, s);
+    if (run) cudaFreeAsync(run, s);
+    if (d_sum) cudaFreeAsync(d_sum, s);
+    if (toff) cudaFreeAsync(toff, s);
+    if (gkeys) cudaFreeAsync(gkeys, s);
+    if (sa) cudaFreeAsync(sa, s);
+    if (sb) cudaFreeAsync(sb, s);
+    return e;
 }
 
 }  // namespace
@@ -502,14 +944,22 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if (hb.count[kGlobalBin]) {
             int cnt = hb.count[kGlobalBin];
             const int *rows = d_perm + hb.start[kGlobalBin];
-            int64_t total = 0;
-            if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
-            if ((e = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) break;
-            symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
-                cnt, rows, toff, d_tsize, gkeys, A.rp, A.ci, B.rp, B.ci, C.rp, d_ovf); note_launch();
-            if ((e = cudaGetLastError())) break;
-            cudaFreeAsync(gkeys, s); gkeys = nullptr;
-            cudaFreeAsync(toff, s); toff = nullptr;
+            if (B.ncol <= kDenseCols) {
+                // long rows against few columns: dense counters in shared memory, a block per row
+                if ((e = dense_attr())) break;
+                dense_symbolic_kernel<<<cnt, kDenseThreads, sizeof(int) * (size_t)B.ncol, s>>>(
+                    cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp); note_launch();
+                if ((e = cudaGetLastError())) break;
+            } else {
+                int64_t total = 0;
+                if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
+                if ((e = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) break;
+                symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
+                    cnt, rows, toff, d_tsize, gkeys, A.rp, A.ci, B.rp, B.ci, C.rp, d_ovf); note_launch();
+                if ((e = cudaGetLastError())) break;
+                cudaFreeAsync(gkeys, s); gkeys = nullptr;
+                cudaFreeAsync(toff, s); toff = nullptr;
+            }
         }
         if ((e = scan_exclusive(C.rp, C.rp, n, s))) break;
         int nnz = 0;
@@ -525,10 +975,14 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
         if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
-        for (int b = 0; b < kGlobalBin && !e; ++b)
+        // pattern, chain placement and chain sums (see "numeric by chains" above); numeric_row
+        // when the products exceed the chains' int32 offsets
+        bool chained = false;
+        if (nnz > 0 && (e = numeric_chains(n, A, B, C, hb, d_perm, d_tsize, d_ovf, &chained, s))) break;
+        for (int b = 0; b < kGlobalBin && !e && !chained; ++b)
             if (hb.count[b]) e = numeric_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C, d_ovf, s);
         if (e) break;
-        if (hb.count[kGlobalBin]) {
+        if (hb.count[kGlobalBin] && !chained) {
             int cnt = hb.count[kGlobalBin];
             const int *rows = d_perm + hb.start[kGlobalBin];
             int64_t total = 0;

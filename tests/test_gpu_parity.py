@@ -166,6 +166,30 @@ def test_spgemm_long_rows_use_global_tables(amg, oracle_lib):
     assert np.array_equal(ci, Co.col) and np.array_equal(v, Co.val)
 
 
+@pytest.mark.parametrize("ncol", [20000, 60000], ids=["dense-counters", "hash-tables"])
+def test_spgemm_rows_of_thousands_of_entries(amg, oracle_lib, ncol):
+    # rows of C with thousands of entries: counted in shared memory per block when B has at most
+    # 49,152 columns, in global hash tables beyond; and a short row beside them
+    import scipy.sparse as sp
+    rng = np.random.default_rng(17)
+    Am = sp.random(9, 400, density=0.9, random_state=rng, format="lil")
+    Am[8, :] = 0
+    Am[8, 3] = 1.5
+    Am = Am.tocsr()
+    Am.sort_indices()
+    Bm = sp.random(400, ncol, density=0.05, random_state=rng, format="csr")
+    Bm.sort_indices()
+    from paper_2103_10476_gb300.problems import CSR
+    Ac = CSR(9, Am.indptr.astype(np.int64), Am.indices.astype(np.int32), Am.data.astype(np.float64))
+    Bc = CSR(400, Bm.indptr.astype(np.int64), Bm.indices.astype(np.int32), Bm.data.astype(np.float64))
+    rp, ci, v = amg.amg_spgemm(amg.csr_arg(9, Ac.row_ptr, Ac.col, Ac.val), 400,
+                               amg.csr_arg(400, Bc.row_ptr, Bc.col, Bc.val), ncol)
+    Co = oracle_lib.spgemm(Ac, Bc, ncol)
+    assert np.diff(Co.row_ptr).max() > 2048
+    assert np.array_equal(rp, Co.row_ptr) and np.array_equal(ci, Co.col)
+    assert np.array_equal(v, Co.val)
+
+
 # ---------------------------------------------------------------- degenerate cases
 
 def test_single_level_one_iteration(amg):
