@@ -59,12 +59,14 @@ constexpr int kCgMinRows = 512;              // the CG path for sparse coarsest 
 constexpr int kCgMaxSteps = 240;             // CG steps at most before the dense path is taken
 constexpr int kCgCheck = 4;                  // steps between convergence checks on the host
 constexpr int kCgChunk = 32;                 // rows per partial column sum
+constexpr int kCgLongRow = 128;              // longer rows are summed in segments by blocks of their own
+constexpr int kCgSegment = 256;
 
 __global__ void dense_from_csr_kernel(int n, const int *rp, const int *ci, const double *v, double *a)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) a[(size_t)i * n + ci[e]] = v[e];
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) a[(size_t)i * n + ci[e]] = v[e];
 }
 
 template <typename A, typename B>
@@ -326,11 +328,18 @@ __global__ void newton_check_kernel(NewtonState *state)
 // positive: the operator is then not SPD and the dense path reports it)
 __global__ void jacobi_scale_kernel(int n, const int *rp, const int *ci, const double *v, double *sc, int *bad)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    // a warp per row (rows of thousands of entries occur on stalled levels)
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
     double d = 0.0;
-    for (int e = rp[i]; e < rp[i + 1]; ++e)
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32)
         if (ci[e] == i) d = v[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double t = __shfl_xor_sync(0xffffffffu, d, o);
+        d = d != 0.0 ? d : t;
+    }
+    if (lane != 0) return;
     if (!(d > 0.0)) {
         atomicAdd(bad, 1);
         sc[i] = 0.0;
@@ -340,35 +349,64 @@ __global__ void jacobi_scale_kernel(int n, const int *rp, const int *ci, const d
 }
 __global__ void scale_values_kernel(int n, const int *rp, const int *ci, const double *v, const double *sc, double *sv)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (i >= n) return;
-    for (int e = rp[i]; e < rp[i + 1]; ++e) sv[e] = sc[i] * v[e] * sc[ci[e]];
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) sv[e] = sc[i] * v[e] * sc[ci[e]];
 }
 
 // Every CG kernel works on n x n row-major arrays with thread (column c = blockIdx.x * 256 +
 // threadIdx.x, rows of chunk blockIdx.y); per-chunk partial column sums go to part[chunk][c]
 // and are added in chunk order by cg_reduce_kernel (reproducible).
 // MODE 0: Q = S A S P and part = P .* Q;  MODE 1 (check): part = max |I - S A S P| per column.
+// Rows longer than long_len were summed by cg_long_partial/cg_long_reduce into Q beforehand.
 template <int MODE>
 __global__ void __launch_bounds__(256) cg_spmm_kernel(int n, const int *rp, const int *ci, const double *sv,
-                                                       const double *P, double *Q, double *part)
+                                                       const double *P, double *Q, double *part, int long_len)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
     const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
     double acc = 0.0;
     for (int i = i0; i < i1; ++i) {
-        double q = 0.0;
-        for (int e = rp[i]; e < rp[i + 1]; ++e) q = fma(sv[e], P[(size_t)ci[e] * n + c], q);
         const size_t ic = (size_t)i * n + c;
+        double q = 0.0;
+        if (rp[i + 1] - rp[i] > long_len) {
+            q = Q[ic];
+        } else {
+            for (int e = rp[i]; e < rp[i + 1]; ++e) q = fma(sv[e], P[(size_t)ci[e] * n + c], q);
+        }
         if (MODE == 0) {
-            Q[ic] = q;
+            if (rp[i + 1] - rp[i] <= long_len) Q[ic] = q;
             acc = fma(P[ic], q, acc);
         } else {
             acc = fmax(acc, fabs((i == c ? 1.0 : 0.0) - q));
         }
     }
     part[(size_t)blockIdx.y * n + c] = acc;
+}
+
+// Long rows of S A S: segment s (entries [seg_k0[s], seg_k1[s]) of one long row) times the
+// n columns of P, into part_long[s][c]; then each long row's segments added in order into Q.
+__global__ void __launch_bounds__(256) cg_long_partial_kernel(int n, const int *seg_k0, const int *seg_k1,
+                                                               const int *ci, const double *sv, const double *P,
+                                                               double *part_long)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int sg = blockIdx.y;
+    double q = 0.0;
+    for (int e = seg_k0[sg]; e < seg_k1[sg]; ++e) q = fma(sv[e], P[(size_t)ci[e] * n + c], q);
+    part_long[(size_t)sg * n + c] = q;
+}
+__global__ void __launch_bounds__(256) cg_long_reduce_kernel(int n, const int *long_rows, const int *seg_first,
+                                                              const double *part_long, double *Q)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int r = blockIdx.y;
+    double q = 0.0;
+    for (int sg = seg_first[r]; sg < seg_first[r + 1]; ++sg) q += part_long[(size_t)sg * n + c];
+    Q[(size_t)long_rows[r] * n + c] = q;
 }
 
 // per column c: sum (MODE 0: alpha = rr / pq; MODE 1: beta = rr_new / rr, rr = rr_new) or
@@ -470,13 +508,54 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
     int *flags = (int *)(coef + n + 16);
     unsigned long long *bits = (unsigned long long *)(flags + 4);
     AMG_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int) + 2 * sizeof(unsigned long long), s));
-    jacobi_scale_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, flags); note_launch();
-    scale_values_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, sv); note_launch();
+    jacobi_scale_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, flags); note_launch();
+    scale_values_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, sc, sv); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     int hflag = 0;
+    std::vector<int> hrp((size_t)n + 1);
     AMG_CUDA_TRY(cudaMemcpyAsync(&hflag, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(hrp.data(), A.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     if (hflag) return cudaSuccess;
+    // rows longer than kCgLongRow: summed in segments of kCgSegment entries by blocks of their own
+    std::vector<int> lrows, seg_first(1, 0), seg_k0, seg_k1;
+    for (int i = 0; i < n; ++i) {
+        const int len = hrp[(size_t)i + 1] - hrp[(size_t)i];
+        if (len <= kCgLongRow) continue;
+        lrows.push_back(i);
+        for (int k = hrp[(size_t)i]; k < hrp[(size_t)i + 1]; k += kCgSegment) {
+            seg_k0.push_back(k);
+            seg_k1.push_back(std::min(k + kCgSegment, hrp[(size_t)i + 1]));
+        }
+        seg_first.push_back((int)seg_k0.size());
+    }
+    const int nlong = (int)lrows.size(), nseg = (int)seg_k0.size();
+    const int long_len = nlong ? kCgLongRow : 0x7fffffff;
+    double *part_long = nullptr;
+    int *d_lists = nullptr;
+    if (nlong) {
+        AMG_CUDA_TRY(cudaMallocAsync(&part_long, sizeof(double) * (size_t)nseg * n, s));
+        AMG_CUDA_TRY(cudaMallocAsync(&d_lists, sizeof(int) * (size_t)(2 * nlong + 1 + 2 * nseg), s));
+        std::vector<int> packed;
+        packed.insert(packed.end(), lrows.begin(), lrows.end());
+        packed.insert(packed.end(), seg_first.begin(), seg_first.end());
+        packed.insert(packed.end(), seg_k0.begin(), seg_k0.end());
+        packed.insert(packed.end(), seg_k1.begin(), seg_k1.end());
+        AMG_CUDA_TRY(cudaMemcpyAsync(d_lists, packed.data(), sizeof(int) * packed.size(), cudaMemcpyHostToDevice, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));       // the host vector goes out of scope
+    }
+    const int *d_lrows = d_lists, *d_segfirst = d_lists + nlong, *d_k0 = d_segfirst + nlong + 1, *d_k1 = d_k0 + nseg;
+    struct Release {
+        double *p; int *q; cudaStream_t s;
+        ~Release() { if (p) cudaFreeAsync(p, s); if (q) cudaFreeAsync(q, s); }
+    } release{part_long, d_lists, s};
+    auto long_rows_product = [&](const double *Pm, double *Qm) {
+        if (!nlong) return;
+        cg_long_partial_kernel<<<dim3((n + 255) / 256, nseg), 256, 0, s>>>(n, d_k0, d_k1, A.ci, sv, Pm, part_long);
+        note_launch();
+        cg_long_reduce_kernel<<<dim3((n + 255) / 256, nlong), 256, 0, s>>>(n, d_lrows, d_segfirst, part_long, Qm);
+        note_launch();
+    };
     const dim3 blk(256), grd((n + 255) / 256, chunks);
     const int cgrid = (n + 255) / 256;
     cg_direction_kernel<true><<<grd, blk, 0, s>>>(n, nullptr, X, R, P); note_launch();
@@ -485,7 +564,8 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
     bool converged = false;
     for (int k = 0; k < kCgMaxSteps && !converged; ++k) {
         if (k > 0) { cg_direction_kernel<false><<<grd, blk, 0, s>>>(n, coef, X, R, P); note_launch(); }
-        cg_spmm_kernel<0><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, P, Q, part); note_launch();
+        long_rows_product(P, Q);
+        cg_spmm_kernel<0><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, P, Q, part, long_len); note_launch();
         cg_reduce_kernel<0><<<cgrid, 256, 0, s>>>(n, chunks, part, rr, coef, flags, bits); note_launch();
         cg_update_kernel<<<grd, blk, 0, s>>>(n, coef, P, Q, X, R, part); note_launch();
         AMG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s));
@@ -506,7 +586,8 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
     if (!converged) return cudaSuccess;
     // the true residual
     AMG_CUDA_TRY(cudaMemsetAsync(bits + 1, 0, sizeof(unsigned long long), s));
-    cg_spmm_kernel<1><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, X, nullptr, part); note_launch();
+    long_rows_product(X, Q);
+    cg_spmm_kernel<1><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, X, Q, part, long_len); note_launch();
     cg_reduce_kernel<2><<<cgrid, 256, 0, s>>>(n, chunks, part, nullptr, nullptr, nullptr, bits + 1); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     unsigned long long he = 0;
@@ -589,8 +670,15 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
     float *Af = (float *)(rd + n + 16), *Ltf = Af + nn, *rdf = Ltf + nn;
     NewtonState *st = (NewtonState *)(((uintptr_t)(rdf + n + 16) + 15) & ~(uintptr_t)15);
     const int cgrid = (int)std::min<size_t>((nn + 255) / 256, 4096);
+    // a large, sparse SPD operator (aggregation stalled on it): the CG path first, in the memory
+    // of the dense matrices
+    if (!general && n > kCgMinRows && (size_t)A.nnz * 8 <= nn) {
+        bool taken = false;
+        AMG_CUDA_TRY(cg_inverse(A, Ad, (double *)Af, nn, inv, &taken, s));
+        if (taken) return cudaSuccess;
+    }
     AMG_CUDA_TRY(cudaMemsetAsync(Ad, 0, sizeof(double) * nn, s));
-    dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
+    dense_from_csr_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
     convert_dense_kernel<double, float><<<cgrid, 256, 0, s>>>(nn, Ad, Af); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     if (general) {
@@ -625,17 +713,6 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work_v, double *inv, int *info
         if (!(err < 1e-6))             // singular, or too ill-conditioned: info = -1 (all bits set)
             return cudaMemsetAsync(info_dev, 0xFF, sizeof(int), s);
         return cudaMemcpyAsync(inv, res, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
-    }
-    // a large, sparse operator (aggregation stalled on it): the CG path, in the memory of the
-    // dense matrices (rebuilt if CG gives up)
-    if (n > kCgMinRows && (size_t)A.nnz * 8 <= nn) {
-        bool taken = false;
-        AMG_CUDA_TRY(cg_inverse(A, Ad, (double *)Af, nn, inv, &taken, s));
-        if (taken) return cudaSuccess;
-        AMG_CUDA_TRY(cudaMemsetAsync(Ad, 0, sizeof(double) * nn, s));
-        dense_from_csr_kernel<<<grid_for(n, 128), 128, 0, s>>>(n, A.rp, A.ci, A.v, Ad); note_launch();
-        convert_dense_kernel<double, float><<<cgrid, 256, 0, s>>>(nn, Ad, Af); note_launch();
-        AMG_CUDA_TRY(cudaGetLastError());
     }
     // stage 1: FP32 factor and inverse (X0 in Y's memory, as floats)
     float *Xf = (float *)Y;
