@@ -602,29 +602,75 @@ cudaError_t sprsfy(const DevCsr &A, const uint8_t *strong, const int *agg, const
 enum { LUMP_DIAG = 0, LUMP_KPLUS = 1, LUMP_DIAG_KMINUS = 2, LUMP_KPLUS_NEG = 3, LUMP_SKIPPED = 4,
        LUMP_FALLBACK = 5 };
 
-// One thread per row: every sum runs sequentially in ascending column order (the per-row
-// FP64 work is a handful of additions per stored entry; GB300's FP64 pipe makes redundant
-// per-lane sums expensive).
-__global__ void filter_kernel(int n, const int *rp, const int *ci, const double *v, const uint8_t *removed,
-                              int offlmp, double tau, int onenorm, double sigma, const int *brp, int *bci,
-                              double *bv, double *Dsm, uint8_t *lumpflag, int *zero_diag)
+// Every sum runs sequentially in ascending column order.  Rows of up to kFilterLong entries: one
+// thread per row (the per-row FP64 work is a handful of additions per stored entry, and GB300's
+// FP64 pipe makes redundant per-lane sums expensive).  Longer rows (a stalled coarse level holds
+// rows of thousands): one warp per row, the warp loading 32 entries at a time with coalesced
+// loads and every lane running the same sequential sums on them (shuffled in entry order), so
+// the row no longer waits on one thread's dependent loads; lane 0 writes.  Both take the
+// entries in the same order and give the same bits.
+constexpr int kFilterLong = 256;
+
+// the row's entries, one at a time, from global memory
+struct FilterThreadAccess {
+    const int *ci;
+    const double *v;
+    const uint8_t *removed;
+    __device__ __forceinline__ void load(int e, int &j, double &val, int &rem) const
+    {
+        j = ci[e];
+        val = v[e];
+        rem = removed[e];
+    }
+};
+
+// the row's entries from a chunk of 32 held one per lane, reloaded (by every lane) when entry
+// e leaves it; load() is called with e = b, b + 1, ... by every lane in step
+struct FilterWarpAccess {
+    const int *ci;
+    const double *v;
+    const uint8_t *removed;
+    int e_end;
+    int base = -(1 << 30);
+    int cj = 0, crem = 0;
+    double cv = 0.0;
+    __device__ __forceinline__ void load(int e, int &j, double &val, int &rem)
+    {
+        const int lane = threadIdx.x & 31;
+        if (e < base || e >= base + 32) {
+            base = e;
+            const int idx = e + lane;
+            if (idx < e_end) {
+                cj = ci[idx];
+                cv = v[idx];
+                crem = removed[idx];
+            }
+        }
+        j = __shfl_sync(0xffffffffu, cj, e - base);
+        val = __shfl_sync(0xffffffffu, cv, e - base);
+        rem = __shfl_sync(0xffffffffu, crem, e - base);
+    }
+};
+
+template <typename Acc>
+__device__ __forceinline__ void filter_row(int i, int b, int e_end, Acc &acc, bool writer, int offlmp, double tau,
+                                           int onenorm, double sigma, const int *brp, int *bci, double *bv,
+                                           double *Dsm, uint8_t *lumpflag, int *zero_diag)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int b = rp[i], e_end = rp[i + 1];
     // pass 1: row sums in ascending order
     double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
     int nkp = 0, nkm = 0, has_diag = 0;
     for (int e = b; e < e_end; ++e) {
-        const int j = ci[e];
-        const double val = v[e];
+        int j, rem;
+        double val;
+        acc.load(e, j, val, rem);
         if (j == i) {
             aii = val;
             has_diag = 1;
             continue;
         }
         if (offlmp) offabs = offabs + fabs(val);
-        if (removed[e]) {
+        if (rem) {
             r = r + val;
         } else if (offlmp) {
             if (val > 0.0) { kp = kp + val; ++nkp; }
@@ -677,12 +723,13 @@ __global__ void filter_kernel(int n, const int *rp, const int *ci, const double 
     int out = brp[i];
     double dsum = 0.0, ssum = 0.0;
     for (int e = b; e < e_end; ++e) {
-        const int j = ci[e];
+        int j, rem;
+        double val;
+        acc.load(e, j, val, rem);
         double nv;
         if (j == i) {
             nv = new_diag;
-        } else if (!removed[e]) {
-            const double val = v[e];
+        } else if (!rem) {
             nv = val;
             if (offlmp && flag != LUMP_FALLBACK) {
                 if (val > 0.0) {
@@ -695,14 +742,17 @@ __global__ void filter_kernel(int n, const int *rp, const int *ci, const double 
         } else {
             continue;
         }
-        bci[out] = j;
-        bv[out] = nv;
+        if (writer) {
+            bci[out] = j;
+            bv[out] = nv;
+        }
         ++out;
         if (onenorm) {
             dsum = dsum + fabs(nv);
             ssum = ssum + nv;
         }
     }
+    if (!writer) return;
     lumpflag[i] = (uint8_t)flag;
     double dd;
     if (onenorm) {
@@ -717,14 +767,56 @@ __global__ void filter_kernel(int n, const int *rp, const int *ci, const double 
     Dsm[i] = dd;
 }
 
+__global__ void filter_kernel(int n, const int *rp, const int *ci, const double *v, const uint8_t *removed,
+                              int offlmp, double tau, int onenorm, double sigma, const int *brp, int *bci,
+                              double *bv, double *Dsm, uint8_t *lumpflag, int *zero_diag, int *long_rows,
+                              int *nlong)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = rp[i], e_end = rp[i + 1];
+    if (e_end - b > kFilterLong) {
+        long_rows[atomicAdd(nlong, 1)] = i;
+        return;
+    }
+    FilterThreadAccess acc{ci, v, removed};
+    filter_row(i, b, e_end, acc, true, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag, zero_diag);
+}
+
+__global__ void filter_long_kernel(const int *rp, const int *ci, const double *v, const uint8_t *removed, int offlmp,
+                                   double tau, int onenorm, double sigma, const int *brp, int *bci, double *bv,
+                                   double *Dsm, uint8_t *lumpflag, int *zero_diag, const int *long_rows,
+                                   const int *nlong)
+{
+    const int warps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    for (int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); w < *nlong; w += warps) {
+        const int i = long_rows[w];
+        const int b = rp[i], e_end = rp[i + 1];
+        FilterWarpAccess acc{ci, v, removed, e_end};
+        filter_row(i, b, e_end, acc, lane == 0, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag,
+                   zero_diag);
+    }
+}
+
 cudaError_t filter(const DevCsr &A, const uint8_t *removed, int offlmp, double tau, int onenorm, double sigma,
                    DevCsr &Abar, double *Dsm, uint8_t *lumpflag, int *zero_diag, cudaStream_t s)
 {
     if (A.n == 0) return cudaSuccess;
-    filter_kernel<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rp, A.ci, A.v, removed, offlmp, tau,
-                                                                   onenorm, sigma, Abar.rp, Abar.ci, Abar.v, Dsm,
-                                                                   lumpflag, zero_diag); note_launch();
-    return cudaGetLastError();
+    int *lr = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&lr, sizeof(int) * ((size_t)A.n + 1), s));
+    cudaError_t e = cudaMemsetAsync(lr, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        filter_kernel<<<grid_for(A.n, 128), 128, 0, s>>>(A.n, A.rp, A.ci, A.v, removed, offlmp, tau, onenorm, sigma,
+                                                         Abar.rp, Abar.ci, Abar.v, Dsm, lumpflag, zero_diag, lr + 1,
+                                                         lr); note_launch();
+        filter_long_kernel<<<2 * kReduceBlocks, 128, 0, s>>>(A.rp, A.ci, A.v, removed, offlmp, tau, onenorm, sigma,
+                                                             Abar.rp, Abar.ci, Abar.v, Dsm, lumpflag, zero_diag, lr + 1,
+                                                             lr); note_launch();
+        e = cudaGetLastError();
+    }
+    cudaError_t e2 = cudaFreeAsync(lr, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 // ------------------------------------------------------------------------------------ smoothed prolongator

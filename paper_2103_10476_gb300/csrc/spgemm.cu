@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kDenseThreads) dense_symbolic_kernel(int cnt_r
 __global__ void __launch_bounds__(kDenseThreads) dense_pattern_kernel(int cnt_rows, const int *rows, const int *arp,
                                                                       const int *aci, const int *brp, const int *bci,
                                                                       int ncolB, const int *crp, int *cci,
-                                                                      int *ccount, int *overflow)
+                                                                      int *ccount, int *overflow, int zero_counts)
 {
     extern __shared__ int dcnt[];
     __shared__ int wsum[kDenseThreads / 32];
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kDenseThreads) dense_pattern_kernel(int cnt_ro
         const int c = dcnt[j];
         if (c > 0) {
             cci[p] = j;
-            ccount[p] = c;
+            ccount[p] = zero_counts ? 0 : c;     // zero: the row's values come from dense_direct_kernel
             ++p;
         }
     }
@@ -671,6 +671,118 @@ __global__ void __launch_bounds__(kDenseThreads) place_dense_kernel(int cnt_rows
     place_row(i, arp, aci, av, brp, bci, bv, crp, cci, rank_map, off, run, sa, sb);
 }
 
+// B^T in CSR for dense_direct_kernel (B with at most kDenseCols rows): counts, scan, an unordered
+// scatter (a warp per row of B), then each row of B^T sorted by its (distinct) keys -- by rank
+// counting in a warp when short, by a dense marker array over B's rows in shared memory when long.
+constexpr int kTrShort = 64;
+__global__ void trw_count_kernel(int64_t nnz, const int *ci, int *cnt)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[e]], 1);
+}
+__global__ void trw_scatter_kernel(int n, const int *rp, const int *ci, const double *v, const int *trp, int *fill,
+                                   int *tci, double *tv)
+{
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) {
+        const int c = ci[e];
+        const int p = trp[c] + atomicAdd(&fill[c], 1);
+        tci[p] = i;
+        tv[p] = v[e];
+    }
+}
+__global__ void trw_sort_short_kernel(int nrow, const int *trp, const int *tci, const double *tv, int *oci, double *ov,
+                                      int *long_rows, int *nlong)
+{
+    const int lane = threadIdx.x & 31;
+    const int r = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (r >= nrow) return;
+    const int b = trp[r], m = trp[r + 1] - b;
+    if (m > kTrShort) {
+        if (lane == 0) long_rows[atomicAdd(nlong, 1)] = r;
+        return;
+    }
+    for (int t = lane; t < m; t += 32) {
+        const int key = tci[b + t];
+        int rank = 0;
+        for (int u = 0; u < m; ++u) rank += tci[b + u] < key;
+        oci[b + rank] = key;
+        ov[b + rank] = tv[b + t];
+    }
+}
+__global__ void __launch_bounds__(kDenseThreads) trw_sort_long_kernel(int nkeys, const int *trp, const int *tci,
+                                                                      const double *tv, int *oci, double *ov,
+                                                                      const int *long_rows, const int *nlong)
+{
+    extern __shared__ int where[];
+    __shared__ int wsum[kDenseThreads / 32];
+    for (int w = blockIdx.x; w < *nlong; w += gridDim.x) {
+        const int r = long_rows[w];
+        const int b = trp[r], m = trp[r + 1] - b;
+        for (int k = threadIdx.x; k < nkeys; k += blockDim.x) where[k] = -1;
+        __syncthreads();
+        for (int t = threadIdx.x; t < m; t += blockDim.x) where[tci[b + t]] = t;
+        __syncthreads();
+        // keys in ascending order: thread t owns keys [t kpt, (t + 1) kpt)
+        const int kpt = (nkeys + (int)blockDim.x - 1) / (int)blockDim.x;
+        const int k0 = threadIdx.x * kpt, k1 = min(nkeys, k0 + kpt);
+        int mine = 0;
+        for (int k = k0; k < k1; ++k) mine += where[k] >= 0;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFullMask, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        int p = 0;
+        for (int q = 0; q < warp; ++q) p += wsum[q];
+        p += incl - mine;
+        for (int k = k0; k < k1; ++k) {
+            const int t = where[k];
+            if (t >= 0) {
+                oci[b + p] = k;
+                ov[b + p] = tv[b + t];
+                ++p;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Rows of thousands of entries when B has at most kDenseCols rows and columns: c_ij directly from
+// column j of B (Bt = B^T in CSR: its row j lists the k with b_kj != 0, ascending).  The block
+// maps each k of A's row i to its entry (or -1) in shared memory; each thread walks the columns
+// of some of the row's entries and sums c_ij = fma(a_ik, b_kj, c_ij) over the k of the column
+// that row i holds, ascending -- the order of every other path -- with no staging at all.
+__global__ void __launch_bounds__(kDenseThreads) dense_direct_kernel(int cnt_rows, const int *rows, int nB,
+                                                                     const int *arp, const int *aci, const double *av,
+                                                                     const int *btrp, const int *btci,
+                                                                     const double *btv, const int *crp, const int *cci,
+                                                                     double *cv)
+{
+    extern __shared__ int pos_of_k[];
+    if ((int)blockIdx.x >= cnt_rows) return;
+    const int i = rows[blockIdx.x];
+    for (int k = threadIdx.x; k < nB; k += blockDim.x) pos_of_k[k] = -1;
+    __syncthreads();
+    for (int e = arp[i] + threadIdx.x; e < arp[i + 1]; e += blockDim.x) pos_of_k[aci[e]] = e;
+    __syncthreads();
+    const int rb = crp[i], nc = crp[i + 1] - rb;
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        const int j = cci[rb + t];
+        double acc = 0.0;
+        for (int f = btrp[j]; f < btrp[j + 1]; ++f) {
+            const int e = pos_of_k[btci[f]];
+            if (e >= 0) acc = __fma_rn(av[e], btv[f], acc);
+        }
+        cv[rb + t] = acc;
+    }
+}
+
 // c_q = sum of its chain, fma from 0 in chain order; warp w owns entries [w K, (w + 1) K), each
 // lane sums one chain at a time and takes the warp's next chain when it finishes
 __global__ void __launch_bounds__(256) chain_kernel(int nnz, const int *off, const double *sa, const double *sb,
@@ -689,7 +801,7 @@ __global__ void __launch_bounds__(256) chain_kernel(int nnz, const int *off, con
     for (;;) {
         const bool act = q < q1;
         if (!__any_sync(kFullMask, act)) break;
-        if (act) {
+        if (act && pos < end) {
             acc = __fma_rn(sa[pos], sb[pos], acc);
             ++pos;
         }
@@ -854,6 +966,12 @@ cudaError_t dense_attr()
         if (attr == cudaSuccess)
             attr = cudaFuncSetAttribute(place_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kDenseCols * (int)sizeof(int));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(dense_direct_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kDenseCols * (int)sizeof(int));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(trw_sort_long_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kDenseCols * (int)sizeof(int));
     });
     return attr;
 }
@@ -887,7 +1005,38 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
     unsigned long long *d_sum = nullptr;
     double *sa = nullptr, *sb = nullptr;
     cudaError_t e = cudaSuccess;
+    // the longest rows straight from B's columns when B is small enough for the dense maps
+    const bool direct = hb.count[kGlobalBin] > 0 && B.ncol <= kDenseCols && B.n <= kDenseCols;
+    DevCsr Bt;
+    int *tfill = nullptr, *tci = nullptr;
+    double *tv = nullptr;
     do {
+        if (direct) {
+            Bt.n = B.ncol;
+            Bt.ncol = B.n;
+            Bt.nnz = B.nnz;
+            if ((e = cudaMallocAsync(&Bt.rp, sizeof(int) * ((size_t)B.ncol + 1), s))) break;
+            if ((e = cudaMallocAsync(&Bt.ci, sizeof(int) * ((size_t)B.nnz + 1), s))) break;
+            if ((e = cudaMallocAsync(&Bt.v, sizeof(double) * ((size_t)B.nnz + 1), s))) break;
+            if ((e = cudaMallocAsync(&tfill, sizeof(int) * (2 * (size_t)B.ncol + 2), s))) break;
+            if ((e = cudaMallocAsync(&tci, sizeof(int) * ((size_t)B.nnz + 1), s))) break;
+            if ((e = cudaMallocAsync(&tv, sizeof(double) * ((size_t)B.nnz + 1), s))) break;
+            if ((e = cudaMemsetAsync(Bt.rp, 0, sizeof(int) * ((size_t)B.ncol + 1), s))) break;
+            if ((e = cudaMemsetAsync(tfill, 0, sizeof(int) * (2 * (size_t)B.ncol + 2), s))) break;
+            if ((e = dense_attr())) break;
+            if (B.nnz > 0) {
+                trw_count_kernel<<<grid_for(B.nnz, 256, 8192), 256, 0, s>>>(B.nnz, B.ci, Bt.rp); note_launch();
+            }
+            if ((e = scan_exclusive(Bt.rp, Bt.rp, B.ncol, s))) break;
+            int *nlong = tfill + B.ncol, *lrows = nlong + 1;
+            trw_scatter_kernel<<<grid_for((int64_t)B.n * 32, 256), 256, 0, s>>>(B.n, B.rp, B.ci, B.v, Bt.rp, tfill,
+                                                                                 tci, tv); note_launch();
+            trw_sort_short_kernel<<<grid_for((int64_t)B.ncol * 32, 256), 256, 0, s>>>(B.ncol, Bt.rp, tci, tv, Bt.ci,
+                                                                                     Bt.v, lrows, nlong); note_launch();
+            trw_sort_long_kernel<<<2 * kReduceBlocks, kDenseThreads, sizeof(int) * (size_t)B.n, s>>>(
+                B.n, Bt.rp, tci, tv, Bt.ci, Bt.v, lrows, nlong); note_launch();
+            if ((e = cudaGetLastError())) break;
+        }
         if ((e = cudaMallocAsync(&off, sizeof(int) * ((size_t)nnz + 1), s))) break;
         if ((e = cudaMallocAsync(&run, sizeof(int) * (size_t)nnz, s))) break;
         if ((e = cudaMallocAsync(&d_sum, sizeof(unsigned long long), s))) break;
@@ -903,7 +1052,7 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
             if (B.ncol <= kDenseCols) {
                 if ((e = dense_attr())) break;
                 dense_pattern_kernel<<<cnt, kDenseThreads, sizeof(int) * (size_t)B.ncol, s>>>(
-                    cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp, C.ci, off, d_ovf); note_launch();
+                    cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp, C.ci, off, d_ovf, direct ? 1 : 0); note_launch();
                 if ((e = cudaGetLastError())) break;
             } else {
                 int64_t total = 0;
@@ -928,7 +1077,7 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
         // the rows of the global bin (more than 2048 entries) by place_dense_kernel when their
         // columns fit the dense map; place_kernel takes the rest
         const bool dense_rows = hb.count[kGlobalBin] > 0 && B.ncol <= kDenseCols;
-        if (dense_rows) {
+        if (dense_rows && !direct) {
             place_dense_kernel<<<hb.count[kGlobalBin], kDenseThreads, sizeof(int) * (size_t)B.ncol, s>>>(
                 hb.count[kGlobalBin], d_perm + hb.start[kGlobalBin], A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci,
                 off, run, sa, sb); note_launch();
@@ -942,6 +1091,13 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
         const int64_t warps = ((int64_t)nnz + kChainOutputs - 1) / kChainOutputs;
         chain_kernel<<<grid_for(warps * 32, 256), 256, 0, s>>>(nnz, off, sa, sb, C.v); note_launch();
         if ((e = cudaGetLastError())) break;
+        if (direct) {
+            // after the chains: their empty chains of these rows wrote zeros
+            dense_direct_kernel<<<hb.count[kGlobalBin], kDenseThreads, sizeof(int) * (size_t)B.n, s>>>(
+                hb.count[kGlobalBin], d_perm + hb.start[kGlobalBin], B.n, A.rp, A.ci, A.v, Bt.rp, Bt.ci, Bt.v, C.rp,
+                C.ci, C.v); note_launch();
+            if ((e = cudaGetLastError())) break;
+        }
         *done = true;
     } while (0);
     if (off) cudaFreeAsync(off, s);
@@ -951,6 +1107,12 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
     if (gkeys) cudaFreeAsync(gkeys, s);
     if (sa) cudaFreeAsync(sa, s);
     if (sb) cudaFreeAsync(sb, s);
+    if (Bt.rp) cudaFreeAsync(Bt.rp, s);
+    if (Bt.ci) cudaFreeAsync(Bt.ci, s);
+    if (Bt.v) cudaFreeAsync(Bt.v, s);
+    if (tfill) cudaFreeAsync(tfill, s);
+    if (tci) cudaFreeAsync(tci, s);
+    if (tv) cudaFreeAsync(tv, s);
     return e;
 }
 
