@@ -378,6 +378,46 @@ amg_status_t amg_server_wait(amg_server_t srv, uint64_t ticket, amg_request_info
 amg_status_t amg_server_stats(amg_server_t srv, amg_server_stats_t *stats);
 amg_status_t amg_server_destroy(amg_server_t srv);
 
+/* ---- Requests across several GPUs (no counterpart in the paper, which treats one system).
+ * A router gives each operator a home device the first time it sees it and keeps it, so that
+ * every repeat of the operator reaches the server that holds its hierarchy.  The operator's
+ * key is its content hash (row pointers, columns and values, the server's cache key).  A new
+ * operator goes to the device with the least work assigned so far (ties: the lowest index);
+ * work counts stored entries, nnz(A) x (nrhs + 20) for an operator new to the device (a setup
+ * weighs about twenty solves' matrix passes) and nnz(A) x nrhs for a repeat.  Decisions
+ * depend on the request sequence only (never on timing): processes that see the same
+ * sequence of requests make the same decisions without any exchange, which lets one process
+ * per GPU take its share of a common stream.  Host-side only: no collective, no peer access.
+ *
+ * amg_router_create: ndev devices (1 ... 4096), numbered 0 ... ndev - 1.
+ * amg_router_route: the device of a request for A with nrhs right-hand sides (*device); *key
+ *   (may be NULL) receives the content hash and *repeat (may be NULL) 1 when the operator was
+ *   seen before.  A on the host or the device (device arrays are copied to the host to be
+ *   hashed).  Records the request.  AMG_ERR_CUDA if such a copy fails.
+ * amg_router_attach: device's server for amg_router_submit (owned by the caller, who creates
+ *   it with that device current and destroys it after the router's last use; NULL detaches).
+ * amg_router_submit: routes the request (as amg_router_route) and submits it to the attached
+ *   server of its device; *ticket is the router's ticket, *device (may be NULL) the device.
+ *   AMG_ERR_INVALID_ARG when that device has no server.  A, b, x as for amg_server_submit.
+ * amg_router_poll / amg_router_wait: as amg_server_poll / amg_server_wait for a router ticket;
+ *   *device (may be NULL) receives the device that served it.
+ * amg_router_stats: for one device, the requests routed to it, the operators whose home it is,
+ *   the repeats among those requests and the work assigned (any pointer may be NULL).
+ * amg_router_destroy: releases the router (not the attached servers); tickets not yet
+ *   collected are dropped. */
+typedef struct amg_router *amg_router_t;
+amg_status_t amg_router_create(int ndev, amg_router_t *out);
+amg_status_t amg_router_route(amg_router_t r, const amg_csr_t *A, int nrhs, int *device, uint64_t *key,
+                              int *repeat);
+amg_status_t amg_router_attach(amg_router_t r, int device, amg_server_t srv);
+amg_status_t amg_router_submit(amg_router_t r, const amg_csr_t *A, int nrhs, const double *b, double *x,
+                               uint64_t *ticket, int *device);
+amg_status_t amg_router_poll(amg_router_t r, uint64_t ticket, amg_request_info_t *info, int *device);
+amg_status_t amg_router_wait(amg_router_t r, uint64_t ticket, amg_request_info_t *info, int *device);
+amg_status_t amg_router_stats(amg_router_t r, int device, int64_t *requests, int64_t *operators, int64_t *repeats,
+                              double *work);
+amg_status_t amg_router_destroy(amg_router_t r);
+
 /* Measurement hooks (no counterpart in the paper).
  * amg_launch_count: kernels launched by this library since it was loaded (all threads).
  * amg_profile_enable(1) resets the totals and starts recording CUDA events around the

@@ -130,6 +130,17 @@ def _load():
         "amg_server_wait": (st, [vp, C.c_uint64, C.POINTER(amg_request_info_t)]),
         "amg_server_stats": (st, [vp, C.POINTER(amg_server_stats_t)]),
         "amg_server_destroy": (st, [vp]),
+        "amg_router_create": (st, [C.c_int, C.POINTER(vp)]),
+        "amg_router_route": (st, [vp, C.POINTER(amg_csr_t), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint64),
+                                  C.POINTER(C.c_int)]),
+        "amg_router_attach": (st, [vp, C.c_int, vp]),
+        "amg_router_submit": (st, [vp, C.POINTER(amg_csr_t), C.c_int, vp, vp, C.POINTER(C.c_uint64),
+                                   C.POINTER(C.c_int)]),
+        "amg_router_poll": (st, [vp, C.c_uint64, C.POINTER(amg_request_info_t), C.POINTER(C.c_int)]),
+        "amg_router_wait": (st, [vp, C.c_uint64, C.POINTER(amg_request_info_t), C.POINTER(C.c_int)]),
+        "amg_router_stats": (st, [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_double)]),
+        "amg_router_destroy": (st, [vp]),
         "amg_status_string": (C.c_char_p, [st]),
         "amg_last_error": (C.c_char_p, []),
     }
@@ -433,6 +444,60 @@ def amg_server_stats(srv) -> amg_server_stats_t:
 
 def amg_server_destroy(srv):
     _check(lib.amg_server_destroy(srv), "amg_server_destroy")
+
+
+def amg_router_create(ndev: int):
+    r = C.c_void_p()
+    _check(lib.amg_router_create(ndev, C.byref(r)), "amg_router_create")
+    return r
+
+
+def amg_router_route(r, A: amg_csr_t, nrhs: int):
+    """(device, content key, repeat) of a request for A with nrhs right-hand sides."""
+    d, k, rep = C.c_int(), C.c_uint64(), C.c_int()
+    _check(lib.amg_router_route(r, C.byref(A), nrhs, C.byref(d), C.byref(k), C.byref(rep)), "amg_router_route")
+    return d.value, k.value, bool(rep.value)
+
+
+def amg_router_attach(r, device: int, srv):
+    _check(lib.amg_router_attach(r, device, srv), "amg_router_attach")
+
+
+def amg_router_submit(r, A: amg_csr_t, nrhs: int, b, x):
+    """(router ticket, device); b, x and A's arrays must outlive the request."""
+    t, d = C.c_uint64(), C.c_int()
+    pb, _ = _ptr(b)
+    px, _ = _ptr(x)
+    _check(lib.amg_router_submit(r, C.byref(A), nrhs, pb, px, C.byref(t), C.byref(d)), "amg_router_submit")
+    return t.value, d.value
+
+
+def amg_router_wait(r, ticket: int):
+    """(amg_request_info_t, device that served it)."""
+    info, d = amg_request_info_t(), C.c_int()
+    _check(lib.amg_router_wait(r, ticket, C.byref(info), C.byref(d)), "amg_router_wait")
+    return info, d.value
+
+
+def amg_router_poll(r, ticket: int):
+    """None while pending, else (amg_request_info_t, device)."""
+    info, d = amg_request_info_t(), C.c_int()
+    s = lib.amg_router_poll(r, ticket, C.byref(info), C.byref(d))
+    if s == AMG_PENDING:
+        return None
+    _check(s, "amg_router_poll")
+    return info, d.value
+
+
+def amg_router_stats(r, device: int) -> dict:
+    req, ops, rep, work = C.c_int64(), C.c_int64(), C.c_int64(), C.c_double()
+    _check(lib.amg_router_stats(r, device, C.byref(req), C.byref(ops), C.byref(rep), C.byref(work)),
+           "amg_router_stats")
+    return {"requests": req.value, "operators": ops.value, "repeats": rep.value, "work": work.value}
+
+
+def amg_router_destroy(r):
+    _check(lib.amg_router_destroy(r), "amg_router_destroy")
 
 
 def amg_status_string(s: int) -> str:

@@ -29,6 +29,7 @@ SOURCES = {
     "api.cu": [],
     "batch.cu": [],
     "server.cu": [],
+    "router.cu": [],
 }
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

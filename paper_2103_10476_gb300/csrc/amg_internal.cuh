@@ -163,6 +163,12 @@ cudaError_t block_pt(int n, int bs, int k, const int *agg, const double *Qv, Dev
 cudaError_t block_combine(int n, int bs, int k, const int *agg, const double *Qv, const double *Dsm,
                           const double *omega, DevCsr &AP, cudaStream_t s);
 
+// --------------------------------------------------------------------------------- server.cu
+// 64-bit content hash of an operator (n, nnz, row pointers, columns, values; device arrays are
+// copied to the host first); 0 with *err set when a copy fails.  The server's cache key and the
+// router's (router.cu).
+uint64_t operator_key(const amg_csr_t *A, std::string *err);
+
 // --------------------------------------------------------------------------------- spgemm.cu
 // C = A B, allocating C's arrays with cudaMalloc.  On failure C is left empty.
 cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s);

@@ -23,16 +23,10 @@
 #include "engine.cuh"
 
 namespace amgk {
-namespace {
-
-double now_ms()
-{
-    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
-}
 
 // 64-bit content hash of a byte range: four independent multiply-xorshift lanes over 8-byte
 // words (the tail zero-padded), folded at the end
-void hash_bytes(const void *p, size_t bytes, uint64_t h[4])
+static void hash_bytes(const void *p, size_t bytes, uint64_t h[4])
 {
     const unsigned char *c = (const unsigned char *)p;
     const uint64_t K = 0x9E3779B97F4A7C15ull;
@@ -81,6 +75,13 @@ uint64_t operator_key(const amg_csr_t *A, std::string *err)
     uint64_t k = h[0] ^ (h[1] * 0xC2B2AE3D27D4EB4Full) ^ (h[2] * 0x165667B19E3779F9ull) ^ (h[3] * 0x27D4EB2F165667C5ull);
     k ^= k >> 31;
     return k;
+}
+
+namespace {
+
+double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
 struct Request;

@@ -11,6 +11,8 @@ Tolerances (FP64 path):
     order) in the 20-150 iterations move the iterate within that accuracy, by up to ~1e-9 in
     the slowly converging cases, so SOL_TOL is ten times the PCG tolerance.
 """
+import warnings
+
 import numpy as np
 
 VAL_TOL = 1e-12
@@ -51,7 +53,12 @@ def iterations_agree(oracle_lib, A, kw, b, tol, k_gpu, k_oracle):
     k = min(k_gpu, k_oracle)
     hk, st = oracle_lib.setup(A, max_iter=k, **kw)
     _, info, _ = hk.solve(b, tol)
-    return info.relres_true <= 2.0 * tol
+    ok = info.relres_true <= 2.0 * tol
+    # every use of the exception is reported in the test output
+    warnings.warn(f"borderline PCG stop (n={A.n}): {k_gpu} vs {k_oracle} iterations, relative residual "
+                  f"{info.relres_true:.3e} at {k} iterations against tolerance {tol:.0e}: "
+                  f"{'accepted' if ok else 'rejected'}")
+    return ok
 
 
 def rel_err(a, b):

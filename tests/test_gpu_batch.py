@@ -3,8 +3,9 @@ alone (amg_solve on the same hierarchy) and against the oracle.
 
 Every system of a batch runs its own PCG (own scalars, own stopping test) through shared
 launches, so a batched result must be the result of that system alone: the same iteration
-count (up to the borderline rule of the single-system parity tests, the summation order of
-the dot products differs) and a solution within SOL_TOL.  With lanes per row chosen from the
+count (FP64: exactly, or within two when the stop is borderline by the oracle's own residual,
+the rule of the single-system parity tests, since the summation order of the dot products
+differs; mixed precision: within one) and a solution within SOL_TOL.  With lanes per row chosen from the
 mean row length (no timing), a system's rows are computed by the same lanes in the same order
 wherever the system sits, so reordering the systems of a batch changes nothing, bit for bit.
 """
@@ -56,7 +57,7 @@ def _setup(amg, systems, **kw):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_equals_each_system_alone(amg, precision):
+def test_batch_equals_each_system_alone(amg, oracle_lib, precision):
     systems = _systems()
     hs = _setup(amg, systems, precision=precision, **KW)
     alone = []
@@ -75,7 +76,10 @@ def test_batch_equals_each_system_alone(amg, precision):
     for k, ((A, b), (ia, xa), ib, xb) in enumerate(zip(systems, alone, infos, xs)):
         assert ib.status == 0 and ib.relres_true <= 1e-8, (k, ib.status, ib.relres_true)
         assert ib.levels == ia.levels
-        assert abs(ib.iters - ia.iters) <= (1 if precision else 2), (k, ib.iters, ia.iters)
+        if precision:
+            assert abs(ib.iters - ia.iters) <= 1, (k, ib.iters, ia.iters)
+        else:
+            assert iterations_agree(oracle_lib, A, KW, b, 1e-8, ib.iters, ia.iters), (k, ib.iters, ia.iters)
         assert np.linalg.norm(xb - xa) / np.linalg.norm(xa) <= (1e-6 if precision else SOL_TOL), k
 
 
@@ -161,20 +165,22 @@ def test_empty_batch(amg):
     assert st == 0 and infos == []
 
 
-def test_shared_hierarchy_many_right_hand_sides(amg):
+def test_shared_hierarchy_many_right_hand_sides(amg, oracle_lib):
     # one hierarchy serving several right-hand sides (the batch refers to it, copies nothing)
     systems = _systems()[:2]
     hs = _setup(amg, systems, **KW)
     A0, A1 = systems[0][0], systems[1][0]
     bs = [P.rhs_uniform(A0.n, 11), P.rhs_uniform(A0.n, 12), systems[1][1], P.rhs_uniform(A0.n, 13)]
     handles = [hs[0], hs[0], hs[1], hs[0]]
+    mats = [A0, A0, A1, A0]
     xs = [np.zeros(len(b)) for b in bs]
     st, infos = amg.amg_solve_batch(handles, bs, xs, 1e-8)
     assert st == 0
-    for h, b, x, info in zip(handles, bs, xs, infos):
+    for h, A, b, x, info in zip(handles, mats, bs, xs, infos):
         xa = np.zeros(len(b))
         ia = amg.amg_solve(h, b, xa, 1e-8)
-        assert info.status == 0 and abs(info.iters - ia.iters) <= 2
+        assert info.status == 0
+        assert iterations_agree(oracle_lib, A, KW, b, 1e-8, info.iters, ia.iters), (info.iters, ia.iters)
         assert np.linalg.norm(x - xa) / np.linalg.norm(xa) <= SOL_TOL
     for h in hs:
         amg.amg_free(h)

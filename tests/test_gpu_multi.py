@@ -1,5 +1,5 @@
 """Several right-hand sides of one system at once (amg_solve_multi) against each column solved
-alone with amg_solve on the same hierarchy.
+alone with amg_solve on the same hierarchy, and against the oracle.
 
 Each column runs the arithmetic of amg_solve: the column's share of every sparse product is
 summed by the same lanes in the same order, and every dot product uses the same blocks and
@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2103_10476_gb300 import problems as P
-from tests.gpu_common import gpu_params
+from tests.gpu_common import SOL_TOL, gpu_params, iterations_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,31 @@ def test_multi_equals_each_column_alone(amg, precision, k):
         assert infos[j].iters == ia.iters, (j, infos[j].iters, ia.iters)
         assert np.linalg.norm(X[j] - xa) / np.linalg.norm(xa) <= 1e-12, j
     amg.amg_free(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_columns_match_oracle(amg, oracle_lib, precision):
+    # every column against the oracle's solve of that right-hand side: FP64 iterations by the
+    # borderline rule and solutions within SOL_TOL; mixed within one iteration and 1e-6
+    A = P.random_coefficient_cube(14, 6, 2.0)
+    kw = dict(theta=0.02, variants=3, max_coarse=40)
+    h = _setup(amg, A, precision=precision, **kw)
+    k = 5
+    B = np.stack([P.rhs_uniform(A.n, 500 + j) for j in range(k)])
+    X = np.zeros_like(B)
+    st, infos = amg.amg_solve_multi(h, B, X, 1e-8)
+    amg.amg_free(h)
+    assert st == 0
+    oh, ost = oracle_lib.setup(A, **kw)
+    assert ost == 0
+    for j in range(k):
+        xo, oinfo, _ = oh.solve(B[j], 1e-8)
+        if precision:
+            assert abs(infos[j].iters - oinfo.iters) <= 1, (j, infos[j].iters, oinfo.iters)
+            assert np.linalg.norm(X[j] - xo) / np.linalg.norm(xo) <= 1e-6
+        else:
+            assert iterations_agree(oracle_lib, A, kw, B[j], 1e-8, infos[j].iters, oinfo.iters), j
+            assert np.linalg.norm(X[j] - xo) / np.linalg.norm(xo) <= SOL_TOL
 
 
 def test_multi_zero_column_limit_and_device_arrays(amg):
