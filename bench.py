@@ -498,6 +498,22 @@ def run_batched(args, amg, torch):
         tot = sum(s_["setup_ms"] + s_["solve_ms"] for s_ in steps)
         out[prec_name] = {"value": count * len(steps) / (tot / 1000.0), "unit": "solves/s",
                           "ms_per_step": tot / len(steps), "steps": len(steps), "per_step": steps}
+    if not args.no_plain:
+        # the plain FP64 GPU path on the same systems: amg_setup + amg_solve + amg_free one
+        # system after another (device-resident matrices), no batching
+        p = amg.amg_params_default(theta=0.02, variants=3, precision=amg.AMG_FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = []
+        for arg, b_, x_ in zip(args_d, bs, xs):
+            h = amg.amg_setup(arg, None, p)
+            its.append(amg.amg_solve(h, b_, x_, TOL).iters)
+            amg.amg_free(h)
+        torch.cuda.synchronize()
+        tp = time.perf_counter() - t0
+        out["plain_fp64"] = {"value": count / tp, "unit": "solves/s", "ms": 1e3 * tp,
+                             "iters_mean": sum(its) / len(its),
+                             "how": "amg_setup + amg_solve + amg_free one system at a time, FP64"}
     return out
 
 
@@ -769,6 +785,31 @@ def run_serving(args, amg, seconds: float, precisions):
             "statuses": sorted({amg.amg_status_string(i.status) for i in infos}),
             "hbm_hierarchies_gb": stats.bytes_hierarchies / 2**30,
             "hbm_engine_gb": stats.bytes_engine / 2**30}
+    if not args.no_plain:
+        # the plain FP64 GPU path on the first requests of the same stream, one after another:
+        # amg_setup of the request's operator from its host arrays, amg_solve of each of its
+        # right-hand sides, amg_free (no server, no cache, no batching)
+        k = min(len(reqs), args.plain_requests)
+        p = amg.amg_params_default(theta=0.02, variants=3, precision=amg.AMG_FP64)
+        xs = [np.zeros_like(bs[i]) for i in range(k)]
+        lat = []
+        t0 = time.perf_counter()
+        solves = 0
+        for i in range(k):
+            r = reqs[i]
+            n = mats[r[1]].n
+            ts = time.perf_counter()
+            h = amg.amg_setup(csr[r[1]], None, p)
+            for j in range(r[2]):
+                amg.amg_solve(h, bs[i][j * n:(j + 1) * n], xs[i][j * n:(j + 1) * n], TOL)
+            amg.amg_free(h)
+            solves += r[2]
+            lat.append(1e3 * (time.perf_counter() - ts))
+        tp = time.perf_counter() - t0
+        out["plain_fp64"] = {"solves_per_s": solves / tp, "requests_per_s": k / tp, "requests": k, "solves": solves,
+                             "wall_s": tp, "mean_ms_per_request": sum(lat) / len(lat),
+                             "how": "the first requests of the same stream, one after another: amg_setup from host "
+                                    "arrays + amg_solve per right-hand side + amg_free, FP64, no server or cache"}
     return out
 
 
@@ -808,9 +849,13 @@ def main():
     ap.add_argument("--gmres-only", action="store_true", help="only the nonsymmetric (GMRES) line, printed alone")
     ap.add_argument("--no-serving", action="store_true", help="skip the served request stream")
     ap.add_argument("--serving-only", action="store_true", help="only the served stream, printed alone")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="seconds of arrivals of the served stream")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="seconds of arrivals of the served stream")
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-fp64", action="store_true", help="serve the stream in FP64 as well as mixed")
+    ap.add_argument("--serve-mixed-only", action="store_true", help="serve the stream in mixed precision only")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the plain FP64 one-at-a-time baselines of the batched and served lines")
+    ap.add_argument("--plain-requests", type=int, default=300,
+                    help="requests of the served stream timed through the plain FP64 path")
     args = ap.parse_args()
     world, rank, local = dist_init()
 
@@ -829,7 +874,7 @@ def main():
         torch.cuda.set_device(local)
         from paper_2103_10476_gb300 import amg
         print(json.dumps(run_serving(args, amg, args.serve_seconds,
-                                     ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])), flush=True)
+                                     ["mixed"] if args.serve_mixed_only else ["mixed", "fp64"])), flush=True)
         return 0
     if args.systems_only:
         import torch
@@ -1026,7 +1071,7 @@ def main():
     gmres = None if args.no_gmres else run_gmres(args, amg, torch)
     systems = None if args.no_systems else run_systems(args, amg, torch)
     serving = None if args.no_serving else run_serving(args, amg, args.serve_seconds,
-                                                        ["mixed", "fp64"] if args.serve_fp64 else ["mixed"])
+                                                        ["mixed"] if args.serve_mixed_only else ["mixed", "fp64"])
 
     if rank != 0:
         return 0
