@@ -143,11 +143,126 @@ __global__ void __launch_bounds__(kMT) spmm_tile_kernel(int n, const int *__rest
     }
 }
 
+// The same products on the level's sliced-ELL copy (slices of 32 rows stored column-major, one
+// lane per row: coalesced loads of values and columns), FP64, for Y, RESID, CHEB and DOT: a row's
+// entries 0, 2, 4, ... and 1, 3, 5, ... are summed apart and added at the end, the arithmetic of
+// spmm_tile_kernel with two lanes per row, and DOT rebuilds that kernel's per-128-row partials
+// with its shuffle tree and order of warps: the same bits as the CSR form.
+constexpr int kSliceRowsM = 32;
+template <typename T, int MODE, int K>
+__global__ void __launch_bounds__(kMT) spmm_sell_kernel(int n, const int *__restrict__ sp, const int *__restrict__ sw,
+                                                         const int *__restrict__ sci, const T *__restrict__ sv,
+                                                         const T *__restrict__ x, T *y, const T *__restrict__ f,
+                                                         const T *__restrict__ invd, T *d, T c1, T c2,
+                                                         double *partial, int nparts)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slice = blockIdx.x * (kMT / kSliceRowsM) + warp;
+    const int row = slice * kSliceRowsM + lane;
+    T acc[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) acc[c] = T(0);
+    if (slice * kSliceRowsM < n) {
+        const int base = sp[slice] + lane, w = sw[slice];
+        T s0[K], s1[K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) { s0[c] = T(0); s1[c] = T(0); }
+        int k = 0;
+        for (; k + 1 < w; k += 2) {
+            const T a0 = sv[base + kSliceRowsM * k], a1 = sv[base + kSliceRowsM * (k + 1)];
+            const T *x0 = x + (size_t)sci[base + kSliceRowsM * k] * K;
+            const T *x1 = x + (size_t)sci[base + kSliceRowsM * (k + 1)] * K;
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                s0[c] += a0 * x0[c];
+                s1[c] += a1 * x1[c];
+            }
+        }
+        if (k < w) {
+            const T a0 = sv[base + kSliceRowsM * k];
+            const T *x0 = x + (size_t)sci[base + kSliceRowsM * k] * K;
+#pragma unroll
+            for (int c = 0; c < K; ++c) s0[c] += a0 * x0[c];
+        }
+#pragma unroll
+        for (int c = 0; c < K; ++c) acc[c] = s0[c] + s1[c];
+    }
+    double contrib[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) contrib[c] = 0.0;
+    if (row < n) {
+        const size_t o = (size_t)row * K;
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            if (MODE == MM_Y) {
+                y[o + c] = acc[c];
+            } else if (MODE == MM_RESID) {
+                y[o + c] = f[o + c] - acc[c];
+            } else if (MODE == MM_CHEB) {
+                const T r = f[o + c] - acc[c];
+                const T dn = c1 * d[o + c] + c2 * (invd[row] * r);
+                d[o + c] = dn;
+                y[o + c] = x[o + c] + dn;
+            } else {
+                y[o + c] = acc[c];
+                contrib[c] = (double)x[o + c] * (double)acc[c];
+            }
+        }
+    }
+    if (MODE == MM_DOT) {
+        // CSR block b covers rows 128 b ... 128 b + 127, its warp w rows 16 w ... 16 w + 15 with
+        // row j's term on lane 2 j; this block's rows are CSR blocks 2 blockIdx and 2 blockIdx + 1
+        __shared__ double con[K][kMT];
+        __shared__ double wsum[2][kMT / 32][K];
+#pragma unroll
+        for (int c = 0; c < K; ++c) con[c][threadIdx.x] = contrib[c];
+        __syncthreads();
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+                double v = (lane & 1) ? 0.0 : con[c][128 * hh + 16 * warp + (lane >> 1)];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kAllM, v, o);
+                if (lane == 0) wsum[hh][warp][c] = v;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 * K) {
+            const int hh = threadIdx.x / K, c = threadIdx.x % K;
+            const int part = 2 * blockIdx.x + hh;
+            if (part < nparts) {
+                double t = 0.0;
+                for (int q = 0; q < kMT / 32; ++q) t += wsum[hh][q][c];
+                partial[(size_t)c * nparts + part] = t;
+            }
+        }
+    }
+}
+
+template <typename T>
+const T *sell_values_m(const SpmvPlan &pl);
+template <>
+const double *sell_values_m<double>(const SpmvPlan &pl) { return pl.sv64; }
+template <>
+const float *sell_values_m<float>(const SpmvPlan &pl) { return pl.sv32; }
+
 template <typename T, int MODE, int K>
 cudaError_t spmm(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f,
                  const T *invd, T *d, T c1, T c2, double *partial, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    // FP64 only: with FP32 values the staged CSR tiles below were faster (1.51x against 1.11x
+    // for eight right-hand sides of stretched64 against one at a time)
+    if (sizeof(T) == 8 && MODE != MM_PROLONG && pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 &&
+        sell_values_m<T>(pl)) {
+        const int blocks = (pl.ns + kMT / kSliceRowsM - 1) / (kMT / kSliceRowsM);
+        const int nparts = (n + kMT / 2 - 1) / (kMT / 2);
+        spmm_sell_kernel<T, MODE, K><<<blocks, kMT, 0, s>>>(n, pl.sp, pl.sw, pl.sci, sell_values_m<T>(pl), x, y, f,
+                                                           invd, d, c1, c2, partial, nparts);
+        note_launch();
+        return cudaGetLastError();
+    }
     const int smem = tile_bytes<T>(pl.cap);
     auto go = [&](auto kern, int lpr) -> cudaError_t {
         // the shared-memory limit is raised once per instantiation (no API call inside a capture)

@@ -31,11 +31,15 @@ def _setup(amg, A, **kw):
     return amg.amg_setup(arg, None, gpu_params(amg, **kw))
 
 
+@pytest.mark.parametrize("layout", ["auto", "sell"])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("k", [1, 3, 8])
-def test_multi_equals_each_column_alone(amg, precision, k):
+def test_multi_equals_each_column_alone(amg, precision, k, layout):
+    # layout "sell": every short-row level carries its sliced-ELL copy, which both the single
+    # column's products and the block products then read
     A = P.stretched_box(18, 1.1)
-    h = _setup(amg, A, theta=0.02, variants=3, precision=precision, max_coarse=40)
+    lay = amg.AMG_LAYOUT_SELL if layout == "sell" else amg.AMG_LAYOUT_AUTO
+    h = _setup(amg, A, theta=0.02, variants=3, precision=precision, max_coarse=40, spmv_layout=lay)
     B = np.stack([P.rhs_uniform(A.n, 100 + j) for j in range(k)])
     X = np.zeros_like(B)
     st, infos = amg.amg_solve_multi(h, B, X, 1e-8)
