@@ -58,14 +58,41 @@ cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t 
 // One warp per row.  theta = 0 makes every stored off-diagonal strong (the filtered matrix is
 // then A); otherwise |a_ij| >= theta * sqrt(a_ii * a_jj) with each operation rounded, and a
 // negative product (sqrt = NaN) makes the entry weak.
+// The FP64 test costs a square root (about ten FP64 instructions) per entry, and most entries
+// lie far from the threshold, so the test is first taken without FP64 instructions: the row's
+// and column's diagonals come in FP32 (converted once per row, NaN when outside [1e-18, 1e18]),
+// t32 = theta sqrt(d_i d_j) in FP32 with every operation rounded to nearest (this file is
+// compiled without contraction) lies within 4.5 units of 2^-24 (2.7e-7) of the exact value, and
+// the FP64 threshold within 4e-16 of it.  The bounds hi = t32 (1 + 2e-6) and lo = t32 (1 - 2e-6)
+// (FP32, normal) are turned into the bit patterns of the same values in FP64 by integer
+// arithmetic and compared with |a_ij|'s bit pattern (positive doubles order as their bits):
+// above hi proves the FP64 test true, below lo proves it false.  Entries in between, NaN
+// entries, diagonals outside the range and theta below 1e-6 take the FP64 test itself.  The
+// decisions are the FP64 test's, bit for bit.
+__device__ __forceinline__ unsigned long long f32_to_f64_bits(float x)      // x positive, normal
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned long long e = (unsigned long long)(((u >> 23) & 0xffu) - 127u + 1023u);
+    return (e << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+}
+
+__global__ void diag_f32_kernel(int n, const double *d, float *df)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = d[i];
+    df[i] = (x >= 1e-18 && x <= 1e18) ? (float)x : __int_as_float(0x7fc00000);
+}
+
 __global__ void strength_kernel(int n, const int *rp, const int *ci, const double *v, const double *d,
-                                double theta, uint8_t *strong, uint8_t *removed, int *kept)
+                                const float *df, double theta, float thf, uint8_t *strong, uint8_t *removed,
+                                int *kept)
 {
     const int lane = threadIdx.x & 31;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (i >= n) return;
     const int b = rp[i], e_end = rp[i + 1];
-    const double di = d[i];
+    const float dfi = df[i];
     int nkept = 0;
     for (int base = b; base < e_end; base += 32) {
         int e = base + lane;
@@ -77,9 +104,21 @@ __global__ void strength_kernel(int n, const int *rp, const int *ci, const doubl
                 if (theta == 0.0) {
                     s = true;
                 } else {
-                    double prod = __dmul_rn(di, d[j]);
-                    double thr = __dmul_rn(theta, __dsqrt_rn(prod));
-                    s = fabs(v[e]) >= thr;
+                    const unsigned long long ab =
+                        (unsigned long long)__double_as_longlong(v[e]) & 0x7fffffffffffffffull;
+                    const float t32 = __fmul_rn(thf, __fsqrt_rn(__fmul_rn(dfi, df[j])));
+                    int decided = 0;
+                    if (thf >= 1e-6f && t32 >= 1e-30f && t32 <= 1e30f && ab < 0x7ff0000000000000ull) {
+                        if (ab > f32_to_f64_bits(__fmul_rn(t32, 1.000002f))) decided = 1;
+                        else if (ab < f32_to_f64_bits(__fmul_rn(t32, 0.999998f))) decided = -1;
+                    }
+                    if (decided) {
+                        s = decided > 0;
+                    } else {
+                        const double prod = __dmul_rn(d[i], d[j]);
+                        const double thr = __dmul_rn(theta, __dsqrt_rn(prod));
+                        s = fabs(v[e]) >= thr;
+                    }
                 }
                 rem = !s;
             }
@@ -96,9 +135,15 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
                      int *kept, cudaStream_t s)
 {
     if (A.n == 0) return cudaSuccess;
-    strength_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, theta, strong,
-                                                                     removed, kept); note_launch();
-    return cudaGetLastError();
+    float *df = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&df, sizeof(float) * (size_t)A.n, s));
+    diag_f32_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, d, df); note_launch();
+    strength_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta,
+                                                                     (float)theta, strong, removed, kept);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    cudaError_t e2 = cudaFreeAsync(df, s);
+    return e != cudaSuccess ? e : e2;
 }
 
 // ------------------------------------------------------------------------------------ nonsymmetric operators

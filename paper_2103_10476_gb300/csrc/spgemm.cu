@@ -74,13 +74,14 @@ __device__ __forceinline__ void bin_count_block(int b, bool valid, int *binCount
     if (threadIdx.x < kNumBins && hist[threadIdx.x]) atomicAdd(&binCount[threadIdx.x], hist[threadIdx.x]);
 }
 
+// (ubstats, when given: [0] the most products of a row, [1] all products, warp-reduced first)
 __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
-                          int *tsize)
+                          int *tsize, unsigned long long *ubstats = nullptr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = 0;
+    int64_t ub = 0;
     if (i < n) {
-        int64_t ub = 0;
         for (int e = arp[i]; e < arp[i + 1]; ++e) {
             int k = aci[e];
             ub += brp[k + 1] - brp[k];
@@ -90,6 +91,19 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
         b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
         bin[i] = b;
         tsize[i] = S;
+    }
+    if (ubstats) {
+        unsigned long long mx = (unsigned long long)ub, sm = (unsigned long long)ub;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(kFullMask, mx, o);
+            mx = y > mx ? y : mx;
+            sm += __shfl_xor_sync(kFullMask, sm, o);
+        }
+        if ((threadIdx.x & 31) == 0 && sm) {
+            atomicMax(&ubstats[0], mx);
+            atomicAdd(&ubstats[1], sm);
+        }
     }
     bin_count_block(b, i < n, binCount);
 }
@@ -378,6 +392,8 @@ __global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff,
 constexpr int kDenseCols = 49152;          // 192 KB of int counters in shared memory
 constexpr int kDenseThreads = 512;
 constexpr int kChainOutputs = 256;         // entries of C per warp of the chain pass
+constexpr int kChainProducts = 32768;      // rows with more products take the chain path ...
+constexpr long long kChainTotal = 16 << 20;  // ... when the whole product has at most this many
 
 // counts[ncolB] of row i's products per column (block-wide, any order)
 __device__ __forceinline__ void dense_count_row(int i, const int *arp, const int *aci, const int *brp, const int *bci,
@@ -1136,14 +1152,22 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
     int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
     int *d_ovf = d_binStart + kNumBins + 1;
-    cudaError_t e = cudaSuccess;
+    unsigned long long *d_ubstats = nullptr, h_ubstats[2] = {0, 0};
+    cudaError_t e = cudaMallocAsync(&d_ubstats, 2 * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(work, s);
+        return e;
+    }
     int *gkeys = nullptr, *toff = nullptr;
     double *gvals = nullptr;
     Bins hb;
     do {
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_ovf, 0, sizeof(int), s))) break;
-        ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize); note_launch();
+        if ((e = cudaMemsetAsync(d_ubstats, 0, 2 * sizeof(unsigned long long), s))) break;
+        ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize, d_ubstats);
+        note_launch();
+        if ((e = cudaMemcpyAsync(h_ubstats, d_ubstats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s))) break;
         if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
         // symbolic
         for (int b = 0; b < kGlobalBin && !e; ++b)
@@ -1188,8 +1212,12 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         // single pass stays cheaper than the chains' staging in global memory on short rows (the
         // 128^3 fine level: 4.1 + 3.0 ms against 5.8 + 6.4 ms for A P and R (A P)); numeric_row also
         // when the products exceed the chains' int32 offsets.
+        // Also products with rows of more than kChainProducts products (a stalled level's large
+        // aggregates) when the whole product is small enough for the chains' global staging.
         bool chained = false;
-        if (nnz > 0 && hb.count[kGlobalBin] > 0 &&
+        const bool long_products = h_ubstats[0] > (unsigned long long)kChainProducts &&
+                                   h_ubstats[1] <= (unsigned long long)kChainTotal;
+        if (nnz > 0 && (hb.count[kGlobalBin] > 0 || long_products) &&
             (e = numeric_chains(n, A, B, C, hb, d_perm, d_tsize, d_ovf, &chained, s)))
             break;
         for (int b = 0; b < kGlobalBin && !e && !chained; ++b)
@@ -1213,6 +1241,7 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     if (gkeys) cudaFreeAsync(gkeys, s);
     if (gvals) cudaFreeAsync(gvals, s);
     if (toff) cudaFreeAsync(toff, s);
+    cudaFreeAsync(d_ubstats, s);
     cudaFreeAsync(work, s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
