@@ -359,16 +359,13 @@ __global__ void scale_values_kernel(int n, const int *rp, const int *ci, const d
 // and are added in chunk order by cg_reduce_kernel (reproducible).
 // MODE 0: Q = S A S P and part = P .* Q;  MODE 1 (check): part = max |I - S A S P| per column.
 // Rows longer than long_len were summed by cg_long_partial/cg_long_reduce into Q beforehand.
-// The grid's x walks the row chunks and y the column blocks, so that the blocks resident at any
-// time cover every row of a few column blocks: the rows of P the gathers reach (anywhere in the
-// column range) stay in L2 (7,004 x 256 doubles = 14 MB a column block).
 template <int MODE>
 __global__ void __launch_bounds__(256) cg_spmm_kernel(int n, const int *rp, const int *ci, const double *sv,
                                                        const double *P, double *Q, double *part, int long_len)
 {
-    const int c = blockIdx.y * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n) return;
-    const int i0 = blockIdx.x * kCgChunk, i1 = min(n, i0 + kCgChunk);
+    const int i0 = blockIdx.y * kCgChunk, i1 = min(n, i0 + kCgChunk);
     double acc = 0.0;
     for (int i = i0; i < i1; ++i) {
         const size_t ic = (size_t)i * n + c;
@@ -385,7 +382,7 @@ __global__ void __launch_bounds__(256) cg_spmm_kernel(int n, const int *rp, cons
             acc = fmax(acc, fabs((i == c ? 1.0 : 0.0) - q));
         }
     }
-    part[(size_t)blockIdx.x * n + c] = acc;
+    part[(size_t)blockIdx.y * n + c] = acc;
 }
 
 // Long rows of S A S: segment s (entries [seg_k0[s], seg_k1[s]) of one long row) times the
@@ -559,7 +556,7 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
         cg_long_reduce_kernel<<<dim3((n + 255) / 256, nlong), 256, 0, s>>>(n, d_lrows, d_segfirst, part_long, Qm);
         note_launch();
     };
-    const dim3 blk(256), grd((n + 255) / 256, chunks), grd_rows(chunks, (n + 255) / 256);
+    const dim3 blk(256), grd((n + 255) / 256, chunks);
     const int cgrid = (n + 255) / 256;
     cg_direction_kernel<true><<<grd, blk, 0, s>>>(n, nullptr, X, R, P); note_launch();
     std::vector<double> ones((size_t)n, 1.0);
@@ -568,7 +565,7 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
     for (int k = 0; k < kCgMaxSteps && !converged; ++k) {
         if (k > 0) { cg_direction_kernel<false><<<grd, blk, 0, s>>>(n, coef, X, R, P); note_launch(); }
         long_rows_product(P, Q);
-        cg_spmm_kernel<0><<<grd_rows, blk, 0, s>>>(n, A.rp, A.ci, sv, P, Q, part, long_len); note_launch();
+        cg_spmm_kernel<0><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, P, Q, part, long_len); note_launch();
         cg_reduce_kernel<0><<<cgrid, 256, 0, s>>>(n, chunks, part, rr, coef, flags, bits); note_launch();
         cg_update_kernel<<<grd, blk, 0, s>>>(n, coef, P, Q, X, R, part); note_launch();
         AMG_CUDA_TRY(cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s));
@@ -590,7 +587,7 @@ cudaError_t cg_inverse(const DevCsr &A, double *mats, double *aux, size_t aux_do
     // the true residual
     AMG_CUDA_TRY(cudaMemsetAsync(bits + 1, 0, sizeof(unsigned long long), s));
     long_rows_product(X, Q);
-    cg_spmm_kernel<1><<<grd_rows, blk, 0, s>>>(n, A.rp, A.ci, sv, X, Q, part, long_len); note_launch();
+    cg_spmm_kernel<1><<<grd, blk, 0, s>>>(n, A.rp, A.ci, sv, X, Q, part, long_len); note_launch();
     cg_reduce_kernel<2><<<cgrid, 256, 0, s>>>(n, chunks, part, nullptr, nullptr, nullptr, bits + 1); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     unsigned long long he = 0;
