@@ -78,6 +78,20 @@ enum { AMG_KRYLOV_CG = 0, AMG_KRYLOV_GMRES = 1 };
  * layout gives identical results; a copy costs 12 bytes per stored entry (16 with AMG_MIXED)
  * plus its padding. */
 enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_CSR = 1, AMG_LAYOUT_SELL = 2 };
+/* The coarsest-level solve (§3.1: a direct solver on the coarsest level).  INVERSE: a dense
+ * FP64 inverse of the coarsest operator, applied by one dense product per V-cycle (the exact
+ * solve to rounding).  AUTO (default): the same, except for a coarsest operator of more than 512
+ * rows with at most one stored entry in eight whose Jacobi-scaled spectrum is narrow (what
+ * stalled aggregation leaves): there the V-cycle applies a fixed Chebyshev polynomial in D^-1 A
+ * of the least degree (at most 40) whose error bound on an interval holding that spectrum is
+ * below 1e-16.  The interval comes from 24 Lanczos steps (through Jacobi-preconditioned CG),
+ * widened by a fifth of its width each way, and is accepted only when a check solve of a
+ * pseudo-random right-hand side leaves a relative residual (D^-1 norm) at most 1e-12;
+ * otherwise the inverse is formed.  A fixed polynomial is one linear operator, as the inverse
+ * is, so PCG keeps its fixed preconditioner; the setup forms no n^2 arrays.  The batch engine
+ * and the server form the inverse of such a handle when it joins them.  With AMG_KRYLOV_GMRES
+ * the inverse is always used. */
+enum { AMG_COARSE_AUTO = 0, AMG_COARSE_INVERSE = 1 };
 /* Systems of PDEs (block_size > 1 or nullspace_dim > 1; the paper treats scalar PDEs and leaves
  * systems to future work).  Unknown bs v + c is component c of node v (n a multiple of bs).
  * The near-null space passed to amg_setup is then nullspace_dim vectors of length n, one after
@@ -133,6 +147,7 @@ typedef struct {
     int block_size;      /* systems of PDEs: unknowns per node, interleaved (1: scalar; <= 16)  */
     int nullspace_dim;   /* near-null-space vectors k (1; <= 8); coarse levels have k unknowns  */
                          /*   per aggregate                                                   */
+    int coarse_solve;    /* AMG_COARSE_AUTO (default) or AMG_COARSE_INVERSE                     */
 } amg_params_t;
 
 typedef struct {
@@ -214,6 +229,12 @@ amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms);
 
 /* Number of levels. */
 amg_status_t amg_num_levels(amg_handle_t h, int *levels);
+
+/* The coarsest-level solve the setup chose (params.coarse_solve): *degree = 0 for the dense
+ * inverse, else the Chebyshev degree, with the interval [theta - delta, theta + delta] on the
+ * spectrum of D^-1 A and the relative residual of the setup's check solve (-1 when no check
+ * ran).  Any output pointer may be NULL. */
+amg_status_t amg_coarse_solver(amg_handle_t h, int *degree, double *theta, double *delta, double *check);
 
 /* Size of level l: rows, stored entries of A_l, and the number of aggregates formed on it
  * (0 on the coarsest level). */

@@ -26,6 +26,7 @@ AMG_LAMBDA_ONE, AMG_LAMBDA_POWER = 0, 1
 AMG_STRENGTH_MATRIX, AMG_STRENGTH_DISTANCE = 0, 1
 AMG_KRYLOV_CG, AMG_KRYLOV_GMRES = 0, 1
 AMG_LAYOUT_AUTO, AMG_LAYOUT_CSR, AMG_LAYOUT_SELL = 0, 1, 2
+AMG_COARSE_AUTO, AMG_COARSE_INVERSE = 0, 1
 PHASES = ("input", "strength", "aggregate", "filter", "eigen", "prolong", "galerkin_ap", "galerkin_rap",
           "smoother", "coarse", "prepare")
 EXPORTS = {"A.rp": (0, np.int64), "A.ci": (1, np.int32), "A.v": (2, np.float64), "strong": (3, np.uint8),
@@ -55,7 +56,7 @@ class amg_params_t(C.Structure):
                 ("onenorm_lambda", C.c_int), ("max_iter", C.c_int), ("seed", C.c_uint64),
                 ("lambda_override", C.c_double), ("cuda_stream", C.c_void_p), ("strength", C.c_int),
                 ("trace", C.c_int), ("krylov", C.c_int), ("restart", C.c_int), ("spmv_layout", C.c_int),
-                ("block_size", C.c_int), ("nullspace_dim", C.c_int)]
+                ("block_size", C.c_int), ("nullspace_dim", C.c_int), ("coarse_solve", C.c_int)]
 
 
 class amg_info_t(C.Structure):
@@ -100,6 +101,8 @@ def _load():
         "amg_solve_multi": (st, [vp, C.c_int, vp, vp, C.c_double, C.POINTER(amg_info_t)]),
         "amg_free": (st, [vp]),
         "amg_num_levels": (st, [vp, C.POINTER(C.c_int)]),
+        "amg_coarse_solver": (st, [vp, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
         "amg_setup_trace": (st, [vp, C.c_int, C.POINTER(C.c_double)]),
         "amg_level_info": (st, [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "amg_export_count": (st, [vp, C.c_int, C.c_int, C.POINTER(C.c_int64)]),
@@ -255,6 +258,13 @@ def amg_num_levels(h) -> int:
     n = C.c_int()
     _check(lib.amg_num_levels(h, C.byref(n)), "amg_num_levels")
     return n.value
+
+
+def amg_coarse_solver(h):
+    """(degree, theta, delta, check) of the coarsest-level solve; degree 0: the dense inverse."""
+    d, t, w, c = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+    _check(lib.amg_coarse_solver(h, C.byref(d), C.byref(t), C.byref(w), C.byref(c)), "amg_coarse_solver")
+    return d.value, t.value, w.value, c.value
 
 
 def amg_level_info(h, level: int):

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -212,7 +213,14 @@ struct SpmvPlan {
     const int *sp = nullptr, *sw = nullptr, *sci = nullptr;
     const double *sv64 = nullptr;
     const float *sv32 = nullptr;
+    // rows split off the row tiles for the solve's products (a device list owned by the
+    // hierarchy; split = nullptr: none).  Every row with more than split_len entries is listed:
+    // the first split_long (more than kSplitBlockLen entries) are summed by a block each, the
+    // next split_mid by a warp each.  When present it supersedes lr.
+    const int *split = nullptr;
+    int split_len = 0x7fffffff, split_long = 0, split_mid = 0;
 };
+constexpr int kSplitBlockLen = 1024;
 // sliced ELL (slices of 32 rows): slices of an n-row matrix; widths sw[ns], offsets sp[ns+1]
 // and the entry count in 64 bits (*total64, device; the offsets hold only when it fits an
 // int); then columns and values
@@ -225,6 +233,11 @@ cudaError_t sell_fill_f(int n, const int *rp, const float *v, int ns, const int 
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s);
 cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns, const int64_t *nnzs,
                        cudaStream_t s);
+// The split rows of the solve's plans (above): counts with one synchronisation, then a list per
+// plan with split rows from alloc(&list, entries) (device memory the caller owns).
+cudaError_t spmv_split_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
+                            const int64_t *nnzs, const std::function<cudaError_t(int **, size_t)> &alloc,
+                            cudaStream_t s);
 int spmv_partials_needed(int n);
 int *spmv_error_flag();
 int spmv_take_errors(cudaStream_t s);
@@ -247,6 +260,10 @@ struct SolveCtx {
     LevelView lev[32];
     int coarse_n = 0;
     const double *coarse_inv = nullptr;     // dense n x n FP64
+    // coarse_degree > 0: the coarsest level is solved by coarse_degree Chebyshev steps on
+    // [theta - delta, theta + delta] (its LevelView then holds A, D^-1, x2 and d), not by the inverse
+    int coarse_degree = 0;
+    double coarse_theta = 0.0, coarse_delta = 0.0;
     double *coarse_tmp_in = nullptr, *coarse_tmp_out = nullptr;
     int cheb_degree = 2;
     double cheb_ratio = 10.0;
@@ -255,6 +272,11 @@ struct SolveCtx {
 };
 // z = V-cycle(r) from z = 0 on the finest level (r, z double on the device).
 cudaError_t vcycle(const SolveCtx &c, const double *r, double *z, cudaStream_t s);
+// The coarsest level's Chebyshev solve (solve.cu): *degree = 0 when it does not apply (the
+// spectrum of D^-1 A too wide for a short polynomial, or the check solve's relative residual
+// *check above 1e-12); else the degree and the interval's centre and half-width.
+cudaError_t coarse_cheb_setup(const DevCsr &A, const SpmvPlan &pl, const double *invdiag, int *degree,
+                              double *theta, double *delta, double *check, cudaStream_t s);
 
 // PCG building blocks (FP64, deterministic reductions; scalars live on the device)
 struct PcgScalars {     // device

@@ -540,6 +540,42 @@ done:
     return st;
 }
 
+// Coarsest levels above this many rows (and sparse) may take the Chebyshev solve instead of the
+// dense inverse
+constexpr int kCoarsePolyMinRows = 512;
+
+// The dense inverse of the coarsest operator into h->coarse_inv (coarse.cu: the Cholesky-based
+// inverse, CG on the columns of a large sparse SPD operator, Newton-Schulz for a nonsymmetric
+// one).  Synchronises h->s.
+amg_status_t form_coarse_inverse(amg_hierarchy *h)
+{
+    amg_status_t st = AMG_OK;
+    cudaStream_t s = h->s;
+    const DevCsr &A = h->lev[h->nlev - 1].A;
+    const int nc = A.n;
+    double *inv = nullptr;
+    void *cwork = nullptr;
+    int *info_dev = nullptr;
+    int info = 0;
+    if (nc > 8192) {
+        g_last_error = "coarsest level too large for the dense solve";
+        return AMG_ERR_UNSUPPORTED;
+    }
+    CK(dalloc(h, &inv, (size_t)nc * nc));
+    CK(cudaMallocAsync(&cwork, coarse_work_bytes(nc), s));
+    CK(cudaMallocAsync(&info_dev, sizeof(int), s));
+    CK(coarse_inverse(A, cwork, inv, info_dev, s, h->p.krylov == AMG_KRYLOV_GMRES));
+    CK(cudaMemcpyAsync(&info, info_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (info < 0) { g_last_error = "coarsest operator singular or too ill-conditioned for its inverse"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
+    if (info) { g_last_error = "coarsest operator not positive definite"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
+    h->coarse_inv = inv;
+done:
+    free_async(cwork, s);
+    free_async(info_dev, s);
+    return st;
+}
+
 amg_status_t prepare_solve(amg_hierarchy *h)
 {
     amg_status_t st = AMG_OK;
@@ -589,10 +625,28 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             } else {
                 v.av = lv.A.v; v.pv = lv.P.v; v.rv = lv.R.v; v.invdiag = lv.invdiag;
             }
+        } else if (h->coarse_degree > 0) {
+            // the Chebyshev coarse solve: A, D^-1 and two more vectors of the coarsest level
+            CK(dalloc(h, (char **)&lv.vx2, (size_t)n * ts));
+            CK(dalloc(h, (char **)&lv.vd, (size_t)n * ts));
+            v.x2 = lv.vx2;
+            v.d = lv.vd;
+            v.arp = lv.A.rp; v.aci = lv.A.ci;
+            v.nnz_a = lv.A.nnz;
+            if (mixed) {
+                CK(dalloc(h, &lv.Af, (size_t)lv.A.nnz));
+                CK(convert_d2f(lv.A.v, lv.Af, lv.A.nnz, s));
+                v.av = lv.Af; v.invdiag = lv.invdiag_f;
+            } else {
+                v.av = lv.A.v; v.invdiag = lv.invdiag;
+            }
         }
     }
     c.coarse_n = h->lev[h->nlev - 1].A.n;
     c.coarse_inv = h->coarse_inv;
+    c.coarse_degree = h->coarse_degree;
+    c.coarse_theta = h->coarse_theta;
+    c.coarse_delta = h->coarse_delta;
     // PCG vectors
     CK(dalloc(h, &h->b, (size_t)n0));
     CK(dalloc(h, &h->x, (size_t)n0));
@@ -684,6 +738,28 @@ amg_status_t prepare_solve(amg_hierarchy *h)
                 pa.sv32 = sv32;
             }
         }
+        // rows far longer than their operator's mean leave the row tiles of every solve product
+        {
+            std::vector<SpmvPlan *> sp;
+            std::vector<const int *> srp;
+            std::vector<int> sn;
+            std::vector<int64_t> snz;
+            for (int L = 0; L + 1 < h->nlev; ++L) {
+                Level &lv = h->lev[L];
+                sp.push_back(&lv.plan_a); srp.push_back(lv.A.rp); sn.push_back(lv.A.n); snz.push_back(lv.A.nnz);
+                sp.push_back(&lv.plan_p); srp.push_back(lv.P.rp); sn.push_back(lv.A.n); snz.push_back(lv.P.nnz);
+                sp.push_back(&lv.plan_r); srp.push_back(lv.R.rp); sn.push_back(lv.R.n); snz.push_back(lv.R.nnz);
+            }
+            if (h->nlev == 1 && n0 > 0) {
+                sp.push_back(&h->plan0); srp.push_back(h->lev[0].A.rp); sn.push_back(n0); snz.push_back(h->lev[0].A.nnz);
+            }
+            if (h->coarse_degree > 0) {
+                Level &cl = h->lev[h->nlev - 1];
+                sp.push_back(&cl.plan_a); srp.push_back(cl.A.rp); sn.push_back(cl.A.n); snz.push_back(cl.A.nnz);
+            }
+            CK(spmv_split_rows((int)sp.size(), sp.data(), srp.data(), sn.data(), snz.data(),
+                               [h](int **list, size_t count) { return dalloc(h, list, count); }, s));
+        }
         if (h->nlev > 1) h->plan0 = h->lev[0].plan_a;
         for (int L = 0; L + 1 < h->nlev; ++L) {
             Level &lv = h->lev[L];
@@ -691,6 +767,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             c.lev[L].plan_p = lv.plan_p;
             c.lev[L].plan_r = lv.plan_r;
         }
+        if (h->coarse_degree > 0) c.lev[h->nlev - 1].plan_a = h->lev[h->nlev - 1].plan_a;
     }
     CK(dalloc(h, (char **)&h->sc, sizeof(PcgScalars)));
     CK(dalloc(h, &h->counters, 8));
@@ -785,6 +862,14 @@ __global__ void csr_check_kernel(int n, int ncol, int64_t nnz, const int *rp, co
 
 }  // namespace
 
+amg_status_t amgk::ensure_coarse_inverse(amg_hierarchy *h)
+{
+    if (!h || h->coarse_inv || h->nlev < 1) return AMG_OK;
+    const amg_status_t st = form_coarse_inverse(h);
+    if (st == AMG_OK) h->ctx.coarse_inv = h->coarse_inv;
+    return st;
+}
+
 int amgk::hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail)
 {
     int *bad = nullptr;
@@ -849,6 +934,7 @@ void amg_params_default(amg_params_t *p)
     p->spmv_layout = AMG_LAYOUT_AUTO;
     p->block_size = 1;
     p->nullspace_dim = 1;
+    p->coarse_solve = AMG_COARSE_AUTO;
 }
 
 amg_status_t amg_setup_trace(amg_handle_t h, int level, double *ms)
@@ -948,7 +1034,8 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         p.max_coarse < 1 || p.max_levels < 1 || p.max_iter < 0 || !(p.tau > 0.0) || !(p.sigma < 1.0) ||
         (p.krylov != AMG_KRYLOV_CG && p.krylov != AMG_KRYLOV_GMRES) ||
         (p.krylov == AMG_KRYLOV_GMRES && (p.restart < 1 || p.restart > 512)) ||
-        (p.spmv_layout != AMG_LAYOUT_AUTO && p.spmv_layout != AMG_LAYOUT_CSR && p.spmv_layout != AMG_LAYOUT_SELL)) {
+        (p.spmv_layout != AMG_LAYOUT_AUTO && p.spmv_layout != AMG_LAYOUT_CSR && p.spmv_layout != AMG_LAYOUT_SELL) ||
+        (p.coarse_solve != AMG_COARSE_AUTO && p.coarse_solve != AMG_COARSE_INVERSE)) {
         g_last_error = "parameter out of range";
         return AMG_ERR_INVALID_ARG;
     }
@@ -978,8 +1065,6 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
     int64_t *rp64 = nullptr;
     const int maxL = p.max_levels < 32 ? p.max_levels : 32;
     int L = 0;
-    int coarse_info = 0;
-    double *cwork = nullptr;
     {
         Level &l0 = h->lev[0];
         l0.A.n = n;
@@ -1040,18 +1125,27 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
         if (coarsest) break;
     }
     h->nlev = L + 1;
-    // coarsest level: dense inverse through the Cholesky factor
+    // coarsest level: the Chebyshev solve where it applies, else the dense inverse
     {
         Level &cl = h->lev[L];
         const int nc = cl.A.n;
-        if (nc > 8192) { g_last_error = "coarsest level too large for the dense solve"; st = AMG_ERR_UNSUPPORTED; goto done; }
-        CK(dalloc(h, &h->coarse_inv, (size_t)nc * nc));
-        CK(cudaMallocAsync(&cwork, coarse_work_bytes(nc), s));
-        CK(coarse_inverse(cl.A, cwork, h->coarse_inv, bad, s, p.krylov == AMG_KRYLOV_GMRES));
-        CK(cudaMemcpyAsync(&coarse_info, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (coarse_info < 0) { g_last_error = "coarsest operator singular or too ill-conditioned for its inverse"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
-        if (coarse_info) { g_last_error = "coarsest operator not positive definite"; st = AMG_ERR_COARSE_NOT_SPD; goto done; }
+        if (p.coarse_solve == AMG_COARSE_AUTO && p.krylov != AMG_KRYLOV_GMRES && nc > kCoarsePolyMinRows &&
+            cl.A.nnz * 8 <= (int64_t)nc * nc) {
+            int hzero = 0;
+            CK(dalloc(h, &cl.invdiag, (size_t)nc));
+            if (p.precision == AMG_MIXED) CK(dalloc(h, &cl.invdiag_f, (size_t)nc));
+            CK(cudaMemsetAsync(bad, 0, sizeof(int), s));
+            CK(invert_diag(cl.diag, cl.invdiag, cl.invdiag_f, nc, bad, s));
+            CK(cudaMemcpyAsync(&hzero, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+            CK(spmv_plan(cl.A.rp, nc, cl.A.nnz, &cl.plan_a, s));     // synchronises s
+            if (!hzero)
+                CK(coarse_cheb_setup(cl.A, cl.plan_a, cl.invdiag, &h->coarse_degree, &h->coarse_theta,
+                                     &h->coarse_delta, &h->coarse_check, s));
+        }
+        if (h->coarse_degree == 0) {
+            st = form_coarse_inverse(h);
+            if (st != AMG_OK) goto done;
+        }
         trace_mark(h, L, AMG_PH_COARSE);
     }
     st = prepare_solve(h);
@@ -1067,7 +1161,6 @@ amg_status_t amg_setup_coords(const amg_csr_t *Ain, const double *nullspace, con
 done:
     free_async(bad, s);
     free_async(rp64, s);
-    free_async(cwork, s);
     if (st != AMG_OK) {
         amg_free(h);
         return st;
@@ -1081,6 +1174,16 @@ amg_status_t amg_num_levels(amg_handle_t h, int *levels)
 {
     if (!h || !levels) return AMG_ERR_INVALID_ARG;
     *levels = h->nlev;
+    return AMG_OK;
+}
+
+amg_status_t amg_coarse_solver(amg_handle_t h, int *degree, double *theta, double *delta, double *check)
+{
+    if (!h) return AMG_ERR_INVALID_ARG;
+    if (degree) *degree = h->coarse_degree;
+    if (theta) *theta = h->coarse_theta;
+    if (delta) *delta = h->coarse_delta;
+    if (check) *check = h->coarse_check;
     return AMG_OK;
 }
 

@@ -658,7 +658,7 @@ void Engine::arena_give(std::vector<std::pair<int64_t, int64_t>> &fl, int64_t of
 
 int Engine::add(amg_hierarchy *h)
 {
-    if (!h || h->nlev < 1 || h->nlev > kEngLevels) return -1;
+    if (!h || h->nlev < 1 || h->nlev > kEngLevels || !h->coarse_inv) return -1;
     if ((h->p.precision == AMG_MIXED) != (cfg_.mixed != 0) || h->p.cheb_degree != cfg_.degree) return -1;
     int k = -1;
     for (int i = 0; i < (int)slots_.size(); ++i)
@@ -1365,6 +1365,7 @@ amg_status_t amg_setup_batch(int count, const amg_csr_t *const *A, const double 
             if (!ws) { status[k] = AMG_ERR_CUDA; msg[k] = "stream creation failed"; continue; }
             amg_params_t pk = *p;
             pk.cuda_stream = ws;
+            pk.coarse_solve = AMG_COARSE_INVERSE;      // the engine applies the dense inverse
             amg_handle_t h = nullptr;
             status[k] = amg_setup(A[k], nullspace ? nullspace[k] : nullptr, &pk, &h);
             if (status[k] != AMG_OK) { msg[k] = amg_last_error(); continue; }
@@ -1411,6 +1412,9 @@ amg_status_t amg_batch_create(int count, const amg_handle_t *h, void *cuda_strea
             set_last_error("a hierarchy deeper than the batch engine's level limit");
             return AMG_ERR_UNSUPPORTED;
         }
+        // the engine applies the coarsest level's dense inverse
+        const amg_status_t ci = ensure_coarse_inverse(h[k]);
+        if (ci != AMG_OK) return ci;
     }
     Engine::Config cfg;
     cfg.mixed = count > 0 && h[0]->p.precision == AMG_MIXED;

@@ -48,6 +48,11 @@ struct amg_hierarchy {
     Level lev[32];
     std::vector<void *> allocs;
     double *coarse_inv = nullptr;
+    // the coarsest level's Chebyshev solve (coarse_degree > 0; coarse_inv stays null until the
+    // batch engine or the server needs it): degree, interval centre and half-width, and the
+    // relative residual of the setup's check solve
+    int coarse_degree = 0;
+    double coarse_theta = 0.0, coarse_delta = 0.0, coarse_check = -1.0;
     // solve workspace (FP64, finest level)
     double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *t = nullptr;
     double *z_prev = nullptr;   // previous preconditioned residual (flexible update, mixed precision)
@@ -88,6 +93,10 @@ int hierarchy_check(const amg_hierarchy *h, cudaStream_t s, std::string *detail)
 // with params.trace: synchronise the handle's stream and book the time since the last mark to
 // (level, phase)
 void trace_mark(amg_hierarchy *h, int level, int phase);
+// forms the dense inverse of the coarsest operator of a handle whose V-cycle uses the
+// Chebyshev solve (the batch engine and the server apply inverses); synchronises the handle's
+// stream.  Does nothing when the inverse exists.
+amg_status_t ensure_coarse_inverse(amg_hierarchy *h);
 // releases the host side of amg_solve_multi's work vectors (their device memory is in allocs)
 void multi_release(amg_hierarchy *h);
 // flexible GMRES(params.restart) preconditioned by one V-cycle per step (amg_solve of a handle

@@ -552,7 +552,8 @@ cudaError_t mvcycle_level(const amg_hierarchy *h, MultiWork &w, int L, T **out, 
     T *x = (T *)w.x[L], *x2 = (T *)w.x2[L];
     const T *f = (const T *)w.f[L];
     const int n = lv.A.n;
-    if (L == h->nlev - 1) {
+    const bool coarse_cheb = L == h->nlev - 1 && c.coarse_degree > 0;
+    if (L == h->nlev - 1 && !coarse_cheb) {
         if (n > 0)
             mcoarse_kernel<T, K><<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, h->coarse_inv, f, x); note_launch();
         *out = x;
@@ -561,7 +562,10 @@ cudaError_t mvcycle_level(const amg_hierarchy *h, MultiWork &w, int L, T **out, 
     const T *av = (const T *)vw.av, *invd = (const T *)vw.invdiag;
     T *d = (T *)w.d[L];
     const double lmax = c.cheb_boost * vw.lambda, lmin = lmax / c.cheb_ratio;
-    const ChebC cc{0.5 * (lmax + lmin), 0.5 * (lmax - lmin), (lmax + lmin) / (lmax - lmin)};
+    // the smoother's interval, or the coarsest level's Chebyshev solve (its own interval and degree)
+    const ChebC cc = coarse_cheb ? ChebC{c.coarse_theta, c.coarse_delta, c.coarse_theta / c.coarse_delta}
+                                 : ChebC{0.5 * (lmax + lmin), 0.5 * (lmax - lmin), (lmax + lmin) / (lmax - lmin)};
+    const int degree = coarse_cheb ? c.coarse_degree : c.cheb_degree;
     auto smooth = [&](bool zero, T *fin) -> cudaError_t {
         double rho = 1.0 / cc.sigma1;
         int k0 = 1;
@@ -570,16 +574,16 @@ cudaError_t mvcycle_level(const amg_hierarchy *h, MultiWork &w, int L, T **out, 
                                                                                     x); note_launch();
             AMG_CUDA_TRY(cudaGetLastError());
         } else {
-            T *dst = (fin && c.cheb_degree == 1) ? fin : x2;
+            T *dst = (fin && degree == 1) ? fin : x2;
             AMG_CUDA_TRY((spmm<T, MM_CHEB, K>(vw.plan_a, n, vw.arp, vw.aci, av, x, dst, f, invd, d, (T)0,
                                               (T)(1.0 / cc.theta), nullptr, s)));
             x2 = x;
             x = dst;
         }
-        for (int k = k0; k < c.cheb_degree; ++k) {
+        for (int k = k0; k < degree; ++k) {
             const double rho_new = 1.0 / (2.0 * cc.sigma1 - rho);
             const double c1 = rho_new * rho, c2 = 2.0 * rho_new / cc.delta;
-            T *dst = (fin && k == c.cheb_degree - 1) ? fin : x2;
+            T *dst = (fin && k == degree - 1) ? fin : x2;
             AMG_CUDA_TRY((spmm<T, MM_CHEB, K>(vw.plan_a, n, vw.arp, vw.aci, av, x, dst, f, invd, d, (T)c1, (T)c2,
                                               nullptr, s)));
             x2 = x;
@@ -589,6 +593,10 @@ cudaError_t mvcycle_level(const amg_hierarchy *h, MultiWork &w, int L, T **out, 
         return cudaSuccess;
     };
     AMG_CUDA_TRY(smooth(true, nullptr));
+    if (coarse_cheb) {
+        *out = x;
+        return cudaSuccess;
+    }
     const Level &cl = h->lev[L + 1];
     T *rv = (T *)w.r[L];
     AMG_CUDA_TRY((spmm<T, MM_RESID, K>(vw.plan_a, n, vw.arp, vw.aci, av, x, rv, f, nullptr, nullptr, (T)0, (T)0,

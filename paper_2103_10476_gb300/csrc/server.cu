@@ -262,6 +262,7 @@ void worker_loop(amg_server *S)
         lk.unlock();
         amg_params_t p = S->cfg.params;
         p.cuda_stream = ws;
+        p.coarse_solve = AMG_COARSE_INVERSE;           // the engine applies the dense inverse
         amg_handle_t h = nullptr;
         const double t0 = now_ms();
         const amg_status_t st = amg_setup(&r->A, nullptr, &p, &h);

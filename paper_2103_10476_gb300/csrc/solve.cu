@@ -14,6 +14,7 @@
 // path's V-cycle); accumulation is in T.  Partial dot products are per block, in a fixed
 // order, so every reduction is bitwise reproducible.
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include <vector>
@@ -111,6 +112,107 @@ __device__ __forceinline__ void last_block_total2(const double *partial, int nbl
     }
 }
 
+// The update of one row whose sum sr was formed outside the row tiles (long and split rows).
+// DOT and SCALEDOT store the row's y only (the tile kernel adds its share of the dot products
+// in its block's fixed order); POWER reads q = x . x from f[0].
+template <typename T, int MODE>
+__device__ __forceinline__ void outside_row_update(int row, T sr, const T *x, T *y, const T *f, const T *aux, T *d,
+                                                   T c1, T c2)
+{
+    if (MODE == MODE_Y || MODE == MODE_DOT) {
+        y[row] = sr;
+    } else if (MODE == MODE_RESID) {
+        y[row] = f[row] - sr;
+    } else if (MODE == MODE_CHEB) {
+        T r = f[row] - sr;
+        T dn = c1 * d[row] + c2 * (aux[row] * r);
+        d[row] = dn;
+        y[row] = x[row] + dn;
+    } else if (MODE == MODE_PROLONG) {
+        y[row] += sr;
+    } else if (MODE == MODE_SCALEDOT) {
+        y[row] = sr / aux[row];
+    } else {
+        const double rq = 1.0 / __dsqrt_rn((double)f[0]);
+        y[row] = (T)(((double)sr / (double)aux[row]) * rq);
+    }
+}
+
+// sum of v[k] x[ci[k]] over k = k, k + stride, ... < e in four independent partial sums: four
+// gathers of x in flight per thread (the rows summed outside the row tiles are few and long, and
+// their time is the latency of these loads, not the arithmetic)
+template <typename T>
+__device__ __forceinline__ T strided_sum4(int k, int e, int stride, const int *__restrict__ ci,
+                                          const T *__restrict__ v, const T *x)
+{
+    T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
+    for (; (int64_t)k + 3 * stride < (int64_t)e; k += 4 * stride) {
+        const int c0 = ci[k], c1 = ci[k + stride], c2 = ci[k + 2 * stride], c3 = ci[k + 3 * stride];
+        const T a0 = v[k], a1 = v[k + stride], a2 = v[k + 2 * stride], a3 = v[k + 3 * stride];
+        s0 += a0 * x[c0];
+        s1 += a1 * x[c1];
+        s2 += a2 * x[c2];
+        s3 += a3 * x[c3];
+    }
+    for (; k < e; k += stride) s0 += v[k] * x[ci[k]];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// A row's sum by every thread of the block (four strided partial sums per thread, a shuffle
+// tree per warp, the warps in order); thread 0 applies the update
+template <typename T, int MODE>
+__device__ __forceinline__ void block_row(int row, const int *__restrict__ rp, const int *__restrict__ ci,
+                                          const T *__restrict__ v, const T *x, T *y, const T *f, const T *aux,
+                                          T *d, T c1, T c2)
+{
+    __shared__ T ws[kSpmvThreads / 32];
+    const int b = rp[row], e = rp[row + 1];
+    T sum = strided_sum4<T>(b + (int)threadIdx.x, e, kSpmvThreads, ci, v, x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    T sr = T(0);
+    for (int w = 0; w < kSpmvThreads / 32; ++w) sr += ws[w];
+    outside_row_update<T, MODE>(row, sr, x, y, f, aux, d, c1, c2);
+}
+
+// Block b of a plan's split rows: split rows 0 .. nlong-1 take a block each, the next nmid a
+// warp each (eight to a block; strided partial sums over the lanes, a shuffle tree)
+constexpr int kSplitRowsPerBlock = kSpmvThreads / 32;
+template <typename T, int MODE>
+__device__ __forceinline__ void split_rows_block(int b, const int *__restrict__ split, int nlong, int nmid,
+                                                 const int *__restrict__ rp, const int *__restrict__ ci,
+                                                 const T *__restrict__ v, const T *x, T *y, const T *f,
+                                                 const T *aux, T *d, T c1, T c2)
+{
+    if (b < nlong) {
+        block_row<T, MODE>(split[b], rp, ci, v, x, y, f, aux, d, c1, c2);
+        return;
+    }
+    const int m = (b - nlong) * kSplitRowsPerBlock + (int)(threadIdx.x >> 5);
+    if (m >= nmid) return;
+    const int row = split[nlong + m];
+    const int lane = threadIdx.x & 31;
+    T sum = strided_sum4<T>(rp[row] + lane, rp[row + 1], 32, ci, v, x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+    if (lane == 0) outside_row_update<T, MODE>(row, sum, x, y, f, aux, d, c1, c2);
+}
+
+// the split rows of a product with dot products, summed before its tile kernel
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_split_kernel(const int *__restrict__ split, int nlong, int nmid,
+                                                                  const int *__restrict__ rp,
+                                                                  const int *__restrict__ ci,
+                                                                  const T *__restrict__ v, const T *__restrict__ x,
+                                                                  T *y, const T *__restrict__ f,
+                                                                  const T *__restrict__ aux, T *d, T c1, T c2)
+{
+    split_rows_block<T, MODE>(blockIdx.x, split, nlong, nmid, rp, ci, v, x, y, f, aux, d, c1, c2);
+}
+
 template <typename T, int LPR, int MODE>
 __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const int *__restrict__ rp,
                                                                  const int *__restrict__ ci,
@@ -118,13 +220,26 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
                                                                  int cap, double *partial, double *result,
-                                                                 unsigned *counter, int *err, int long_len)
+                                                                 unsigned *counter, int *err, int long_len,
+                                                                 const int *__restrict__ split, int nlong, int nmid)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     constexpr int RPB = kSpmvThreads / LPR;
     constexpr int VA = 16 / (int)sizeof(T);
-    const int r0 = blockIdx.x * RPB;
+    // the first blocks of an update-only product sum the plan's split rows (nlong + nmid = 0
+    // for the products with dot products, whose split rows a separate launch sums first)
+    int bx = blockIdx.x, nbx = gridDim.x;
+    {
+        const int extra = nlong + (nmid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
+        if (bx < extra) {
+            split_rows_block<T, MODE>(bx, split, nlong, nmid, rp, ci, v, x, y, f, aux, d, c1, c2);
+            return;
+        }
+        bx -= extra;
+        nbx -= extra;
+    }
+    const int r0 = bx * RPB;
     const int r1 = min(n, r0 + RPB);
     const int k0 = rp[r0], k1 = rp[r1];
     const int k0v = k0 & ~(VA - 1), k1v = (k1 + VA - 1) & ~(VA - 1);
@@ -147,13 +262,18 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
     const int row = r0 + threadIdx.x / LPR;
     const int lane = threadIdx.x % LPR;
     T sum = T(0);
-    // rows longer than long_len were finished by spmv_long_kernel, launched before this kernel
+    // rows longer than long_len are summed elsewhere: by spmv_long_kernel or spmv_split_kernel,
+    // launched before this kernel, or by this kernel's first blocks (split rows, above)
     const bool is_long = row < r1 && rp[row + 1] - rp[row] > long_len;
     if (row < r1 && tile_ok && !is_long) {
         const int b = rp[row], e = rp[row + 1];
+        // (unrolled: the gathers of x of four iterations are issued before their additions,
+        // which stay in order)
         if (staged) {
+#pragma unroll 4
             for (int k = b + lane; k < e; k += LPR) sum += sv[k - k0v] * x[sc[k - k0i]];
         } else {
+#pragma unroll 4
             for (int k = b + lane; k < e; k += LPR) sum += v[k] * x[ci[k]];
         }
     }
@@ -255,10 +375,10 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                 t1 += sh1[w];
                 t2 += sh2[w];
             }
-            partial[blockIdx.x] = t1;
-            partial[gridDim.x + blockIdx.x] = t2;
+            partial[bx] = t1;
+            partial[nbx + bx] = t2;
         }
-        last_block_total2(partial, gridDim.x, counter, result, (double *)d, rq);
+        last_block_total2(partial, nbx, counter, result, (double *)d, rq);
     }
     if (MODE == MODE_DOT || MODE == MODE_SCALEDOT) {
         __shared__ double sh[kSpmvThreads / 32];
@@ -269,9 +389,9 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         if (threadIdx.x == 0) {
             double t = 0.0;
             for (int w = 0; w < kSpmvThreads / 32; ++w) t += sh[w];
-            partial[blockIdx.x] = t;
+            partial[bx] = t;
         }
-        if (result) last_block_total(partial, gridDim.x, counter, result);
+        if (result) last_block_total(partial, nbx, counter, result);
     }
 }
 
@@ -287,36 +407,8 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_long_kernel(LongRows lr, co
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2)
 {
-    __shared__ T ws[kSpmvThreads / 32];
     if ((int)blockIdx.x >= lr.count) return;
-    const int row = lr.rows[blockIdx.x];
-    const int b = rp[row], e = rp[row + 1];
-    T sum = T(0);
-    for (int k = b + (int)threadIdx.x; k < e; k += kSpmvThreads) sum += v[k] * x[ci[k]];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x != 0) return;
-    T sr = T(0);
-    for (int w = 0; w < kSpmvThreads / 32; ++w) sr += ws[w];
-    if (MODE == MODE_Y || MODE == MODE_DOT) {
-        y[row] = sr;
-    } else if (MODE == MODE_RESID) {
-        y[row] = f[row] - sr;
-    } else if (MODE == MODE_CHEB) {
-        T r = f[row] - sr;
-        T dn = c1 * d[row] + c2 * (aux[row] * r);
-        d[row] = dn;
-        y[row] = x[row] + dn;
-    } else if (MODE == MODE_PROLONG) {
-        y[row] += sr;
-    } else if (MODE == MODE_SCALEDOT) {
-        y[row] = sr / aux[row];
-    } else {
-        const double rq = 1.0 / __dsqrt_rn((double)f[0]);
-        y[row] = (T)(((double)sr / (double)aux[row]) * rq);
-    }
+    block_row<T, MODE>(lr.rows[blockIdx.x], rp, ci, v, x, y, f, aux, d, c1, c2);
 }
 
 // rows longer than len: count (cnt[0]) and the first kMaxLongRows of them (order of arrival;
@@ -465,6 +557,80 @@ cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStr
     const int ns[1] = {n};
     const int64_t nz[1] = {nnz};
     return spmv_plans(1, pls, rps, ns, nz, s);
+}
+
+// rows with more than len entries: cnt[0] of more than kSplitBlockLen, cnt[1] the others
+__global__ void split_count_kernel(int n, const int *rp, int len, int *cnt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = rp[i + 1] - rp[i];
+    if (l > len) atomicAdd(&cnt[l > kSplitBlockLen ? 0 : 1], 1);
+}
+
+// the same rows into list (the long ones first; order of arrival within each part: a row's
+// sum does not depend on which block or warp forms it)
+__global__ void split_fill_kernel(int n, const int *rp, int len, int nlong, int *cnt, int *list)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int l = rp[i + 1] - rp[i];
+    if (l <= len) return;
+    if (l > kSplitBlockLen)
+        list[atomicAdd(&cnt[0], 1)] = i;
+    else
+        list[nlong + atomicAdd(&cnt[1], 1)] = i;
+}
+
+// A solve plan's row-tile limit: a row of more than 16 entries a lane (and more than 4 x its
+// operator's mean, and more than 32) leaves the tiles, whose lanes would walk it as one serial
+// chain of FP64 additions while the rest of the block waits.
+int split_threshold(int lpr, double avg)
+{
+    const double t = std::max(std::max(32.0, 16.0 * lpr), 4.0 * avg);
+    return t < 1.0e9 ? (int)t : 1000000000;
+}
+
+cudaError_t spmv_split_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
+                            const int64_t *nnzs, const std::function<cudaError_t(int **, size_t)> &alloc,
+                            cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    int *d = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * 4 * (size_t)count, s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * 4 * (size_t)count, s);
+    std::vector<int> len((size_t)count, 0x7fffffff);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        SpmvPlan *pl = plans[k];
+        pl->split = nullptr;
+        pl->split_len = 0x7fffffff;
+        pl->split_long = pl->split_mid = 0;
+        if (ns[k] == 0 || nnzs[k] == 0) continue;
+        len[(size_t)k] = split_threshold(pl->lpr, (double)nnzs[k] / ns[k]);
+        split_count_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], d + 4 * k);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    std::vector<int> h((size_t)count * 4, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int nl = h[(size_t)4 * k], nm = h[(size_t)4 * k + 1];
+        if (nl + nm == 0) continue;
+        int *list = nullptr;
+        e = alloc(&list, (size_t)nl + (size_t)nm);
+        if (e != cudaSuccess) break;
+        split_fill_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], nl, d + 4 * k + 2, list);
+        note_launch();
+        e = cudaGetLastError();
+        SpmvPlan *pl = plans[k];
+        pl->split = list;
+        pl->split_len = len[(size_t)k];
+        pl->split_long = nl;
+        pl->split_mid = nm;
+    }
+    cudaFreeAsync(d, s);
+    return e;
 }
 
 static int *g_spmv_err = nullptr;   // device error flag of the bounded waits (allocated once)
@@ -653,8 +819,9 @@ cudaError_t sell_fill_t(int n, const int *rp, const int *ci, const T *v, int ns,
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
-                        cudaStream_t s, int long_len)
+                        cudaStream_t s, int long_len, const int *split, int nlong, int nmid)
 {
+    const int extra = nlong + (nmid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
     const int smem = tile_bytes<T>(cap);
     // the attribute is set once per instantiation (any thread may get here first)
     static std::once_flag configured;
@@ -664,8 +831,9 @@ cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T
                                        tile_bytes<T>(kMaxTile));
     });
     AMG_CUDA_TRY(cfg_err);
-    spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR), kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), long_len); note_launch();
+    spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR) + extra, kSpmvThreads, smem, s>>>(
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), long_len, split, nlong,
+        nmid); note_launch();
     return cudaGetLastError();
 }
 
@@ -676,12 +844,28 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
 {
     if (n == 0) return cudaSuccess;
     if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr)) &&
-        pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0) {
+        pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 && pl.split == nullptr) {
         const T *sv = sell_values<T>(pl);
         if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s);
     }
     int long_len = 0x7fffffff;
-    if (pl.lr.count > 0) {
+    const int *split = nullptr;
+    int nlong = 0, nmid = 0;
+    if (pl.split) {
+        long_len = pl.split_len;
+        if (MODE == MODE_DOT || MODE == MODE_SCALEDOT || MODE == MODE_POWER) {
+            // the tile kernel's dot products read the split rows' y: they go first
+            const int blocks = pl.split_long + (pl.split_mid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
+            spmv_split_kernel<T, MODE><<<blocks, kSpmvThreads, 0, s>>>(pl.split, pl.split_long, pl.split_mid, rp, ci,
+                                                                       v, x, y, f, aux, d, c1, c2);
+            note_launch();
+            AMG_CUDA_TRY(cudaGetLastError());
+        } else {
+            split = pl.split;
+            nlong = pl.split_long;
+            nmid = pl.split_mid;
+        }
+    } else if (pl.lr.count > 0) {
         spmv_long_kernel<T, MODE><<<pl.lr.count, kSpmvThreads, 0, s>>>(pl.lr, rp, ci, v, x, y, f, aux, d, c1, c2);
         note_launch();
         AMG_CUDA_TRY(cudaGetLastError());
@@ -690,19 +874,19 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
     switch (pl.lpr) {
     case 2:
         return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len);
+                                       long_len, split, nlong, nmid);
     case 4:
         return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len);
+                                       long_len, split, nlong, nmid);
     case 8:
         return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len);
+                                       long_len, split, nlong, nmid);
     case 16:
         return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                        long_len);
+                                        long_len, split, nlong, nmid);
     default:
         return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                        long_len);
+                                        long_len, split, nlong, nmid);
     }
 }
 
@@ -941,6 +1125,238 @@ __global__ void t2d_kernel(int n, const T *in, double *out)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (double)in[i];
 }
 
+// ------------------------------------------------------------------------------------ coarse polynomial solve
+// A large, sparse coarsest operator whose Jacobi-scaled form is well conditioned (what stalled
+// aggregation leaves: 7,004 rows with scaled condition number 1.2 on the 128^3 random-
+// coefficient cube) is solved in every V-cycle by a Chebyshev iteration of fixed degree m on an
+// interval [lo, hi] holding the spectrum of D^-1 A, instead of a product with a dense inverse.
+// m steps from x = 0 apply a fixed polynomial in D^-1 A, so the coarse solve stays one linear
+// operator (as the exact inverse is); m is the least degree whose bound 2 rho^m on the error,
+// rho = (sqrt(hi/lo) - 1) / (sqrt(hi/lo) + 1), is below kCoarseChebTol.
+//
+// The interval: m_L steps of Jacobi-preconditioned CG on A x = b for a pseudo-random b are m_L
+// steps of the Lanczos process on D^-1 A (the tridiagonal matrix follows from the CG
+// coefficients alpha_j = rz_j / pq_j and beta_j = rz_{j+1} / rz_j).  Its extreme eigenvalues
+// lie inside the spectrum; widened by a fifth of their distance each way they bound it, and a
+// solve of a second pseudo-random right-hand side checks the result.
+constexpr int kLanczosSteps = 24;
+constexpr int kCoarseChebMax = 40;
+constexpr double kCoarseChebTol = 1e-16;
+
+__device__ __forceinline__ double coarse_rand(int i, uint64_t stream)
+{
+    uint64_t z = stream + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-52 - 1.0;       // uniform in [-1, 1)
+}
+
+// b pseudo-random (stream); r = b, p = D^-1 b, *rz0 = r . D^-1 r (fixed-order two-stage sum)
+__global__ void __launch_bounds__(kReduceThreads) lz_start_kernel(int n, uint64_t stream, const double *invdiag,
+                                                                  double *r, double *p, double *partial,
+                                                                  unsigned *counter, double *rz0)
+{
+    double acc = 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += gridDim.x * kReduceThreads) {
+        const double b = coarse_rand(i, stream);
+        const double z = invdiag[i] * b;
+        r[i] = b;
+        p[i] = z;
+        acc += b * z;
+    }
+    const double t = block_sum_all(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    last_block_total(partial, gridDim.x, counter, rz0);
+}
+
+// CG step j after q = A p, pq[j] = p . q: r -= alpha q, rz[j + 1] = r . D^-1 r
+__global__ void __launch_bounds__(kReduceThreads) lz_update_kernel(int n, const double *invdiag, double *r,
+                                                                   const double *q, double *rz, const double *pq,
+                                                                   int j, double *partial, unsigned *counter)
+{
+    const double a = (pq[j] > 0.0 && rz[j] > 0.0) ? rz[j] / pq[j] : 0.0;
+    double acc = 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += gridDim.x * kReduceThreads) {
+        const double ri = r[i] - a * q[i];
+        r[i] = ri;
+        acc += ri * (invdiag[i] * ri);
+    }
+    const double t = block_sum_all(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    last_block_total(partial, gridDim.x, counter, rz + j + 1);
+}
+
+// p = D^-1 r + beta p, beta = rz[j + 1] / rz[j]
+__global__ void __launch_bounds__(kReduceThreads) lz_direction_kernel(int n, const double *invdiag, const double *r,
+                                                                      double *p, const double *rz, int j)
+{
+    const double b = rz[j] > 0.0 ? rz[j + 1] / rz[j] : 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += gridDim.x * kReduceThreads)
+        p[i] = invdiag[i] * r[i] + b * p[i];
+}
+
+// out[0] = r . D^-1 r, out[1] = f . D^-1 f (the check's residual and right-hand side norms)
+__global__ void __launch_bounds__(kReduceThreads) dnorm2_kernel(int n, const double *invdiag, const double *r,
+                                                                const double *f, double *partial, unsigned *counter,
+                                                                double *out)
+{
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += gridDim.x * kReduceThreads) {
+        a += r[i] * (invdiag[i] * r[i]);
+        b += f[i] * (invdiag[i] * f[i]);
+    }
+    const double ta = block_sum_all(a);
+    if (threadIdx.x == 0) partial[blockIdx.x] = ta;
+    const double tb = block_sum_all(b);
+    if (threadIdx.x == 0) partial[gridDim.x + blockIdx.x] = tb;
+    last_block_total2(partial, gridDim.x, counter, out, out + 1, 1.0);
+}
+
+__global__ void rand_fill_kernel(int n, uint64_t stream, double *f)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) f[i] = coarse_rand(i, stream);
+}
+
+// Sturm count: eigenvalues of the symmetric tridiagonal (a diagonal, b off-diagonal) below t
+static int sturm_below(const std::vector<double> &a, const std::vector<double> &b, double t)
+{
+    int count = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double off = i ? b[i - 1] * b[i - 1] : 0.0;
+        q = (a[i] - t) - (i ? off / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0.0) ++count;
+    }
+    return count;
+}
+
+// the k-th smallest eigenvalue (k = 0 .. size-1) by bisection inside the Gershgorin bounds
+static double tridiag_eig(const std::vector<double> &a, const std::vector<double> &b, int k)
+{
+    double lo = 1e300, hi = -1e300;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double rad = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - rad);
+        hi = std::max(hi, a[i] + rad);
+    }
+    for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (sturm_below(a, b, mid) > k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// x = p_m(D^-1 A) D^-1 f: m Chebyshev steps on [theta - delta, theta + delta] from x = 0; x2
+// and d are work vectors.  Returns the buffer holding the result (x or x2).
+template <typename T>
+T *coarse_cheb_apply(const SpmvPlan &pl, int n, const int *rp, const int *ci, const T *v, const T *invdiag,
+                     const T *f, T *x, T *x2, T *d, double theta, double delta, int degree, cudaStream_t s,
+                     cudaError_t *err)
+{
+    const double sigma1 = theta / delta;
+    double rho = 1.0 / sigma1;
+    cheb_first_zero_kernel<T><<<grid_for(n, 256, 8192), 256, 0, s>>>(n, f, invdiag, (T)(1.0 / theta), d, x);
+    note_launch();
+    *err = cudaGetLastError();
+    for (int k = 1; k < degree && *err == cudaSuccess; ++k) {
+        const double rho_new = 1.0 / (2.0 * sigma1 - rho);
+        const double c1 = rho_new * rho, c2 = 2.0 * rho_new / delta;
+        *err = spmv_mode<T, MODE_CHEB>(pl, n, rp, ci, v, x, x2, f, invdiag, d, (T)c1, (T)c2, nullptr, s);
+        T *t = x; x = x2; x2 = t;
+        rho = rho_new;
+    }
+    return x;
+}
+
+cudaError_t coarse_cheb_setup(const DevCsr &A, const SpmvPlan &pl, const double *invdiag, int *degree,
+                              double *theta, double *delta, double *check, cudaStream_t s)
+{
+    *degree = 0;
+    *check = -1.0;
+    const int n = A.n;
+    if (n == 0) return cudaSuccess;
+    const int np = std::max(spmv_partials_needed(n), 2 * kReduceBlocks);
+    const size_t vec = (size_t)n + 16;
+    double *w = nullptr;
+    const size_t total = 5 * vec + (size_t)np + 2 * kLanczosSteps + 8;
+    AMG_CUDA_TRY(cudaMallocAsync(&w, sizeof(double) * total + 64, s));
+    struct Release {
+        double *p; cudaStream_t s;
+        ~Release() { cudaFreeAsync(p, s); }
+    } release{w, s};
+    double *r = w, *p = r + vec, *q = p + vec, *x2 = q + vec, *d = x2 + vec, *partial = d + vec;
+    double *rz = partial + np, *pq = rz + kLanczosSteps + 1, *out = pq + kLanczosSteps;
+    unsigned *counter = (unsigned *)(out + 4);
+    AMG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(unsigned), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(rz, 0, sizeof(double) * (2 * kLanczosSteps + 1), s));
+    lz_start_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, 0x243F6A8885A308D3ULL, invdiag, r, p, partial,
+                                                             counter, rz);
+    note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    for (int j = 0; j < kLanczosSteps; ++j) {
+        AMG_CUDA_TRY(spmv_dot(A, pl, p, q, partial, pq + j, counter, s));
+        lz_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, invdiag, r, q, rz, pq, j, partial, counter);
+        note_launch();
+        lz_direction_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, invdiag, r, p, rz, j);
+        note_launch();
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<double> h(2 * kLanczosSteps + 1);
+    AMG_CUDA_TRY(cudaMemcpyAsync(h.data(), rz, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    const double *hrz = h.data(), *hpq = h.data() + kLanczosSteps + 1;
+    if (!(hrz[0] > 0.0) || !std::isfinite(hrz[0])) return cudaSuccess;
+    // the steps before the residual fell to 1e-13 of its start (later coefficients are noise)
+    int J = 0;
+    while (J < kLanczosSteps && hpq[J] > 0.0 && std::isfinite(hpq[J]) && hrz[J] > 1e-26 * hrz[0]) ++J;
+    if (J == 0) return cudaSuccess;
+    std::vector<double> a((size_t)J), b((size_t)(J > 1 ? J - 1 : 0));
+    for (int j = 0; j < J; ++j) {
+        const double alpha = hrz[j] / hpq[j];
+        a[(size_t)j] = 1.0 / alpha;
+        if (j > 0) {
+            const double alpha_prev = hrz[j - 1] / hpq[j - 1], beta_prev = hrz[j] / hrz[j - 1];
+            a[(size_t)j] += beta_prev / alpha_prev;
+            b[(size_t)j - 1] = std::sqrt(beta_prev) / alpha_prev;
+        }
+    }
+    const double tmin = tridiag_eig(a, b, 0), tmax = tridiag_eig(a, b, J - 1);
+    if (!(tmin > 0.0) || !(tmax >= tmin) || !std::isfinite(tmax)) return cudaSuccess;
+    const double margin = 0.2 * (tmax - tmin) + 1e-3 * tmax;
+    const double lo = tmin - margin, hi = tmax + margin;
+    if (!(lo > 0.0)) return cudaSuccess;
+    const double sk = std::sqrt(hi / lo), rho = (sk - 1.0) / (sk + 1.0);
+    int m = rho > 0.0 ? (int)std::ceil(std::log(kCoarseChebTol / 2.0) / std::log(rho)) : 1;
+    m = std::max(m, 2);
+    if (m > kCoarseChebMax) return cudaSuccess;
+    // the check: a solve of another pseudo-random right-hand side, its residual in the D^-1 norm
+    double *f = p;
+    rand_fill_kernel<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, 0x13198A2E03707344ULL, f);
+    note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    cudaError_t e = cudaSuccess;
+    double *x = coarse_cheb_apply<double>(pl, n, A.rp, A.ci, A.v, invdiag, f, q, x2, d, 0.5 * (hi + lo),
+                                          0.5 * (hi - lo), m, s, &e);
+    AMG_CUDA_TRY(e);
+    AMG_CUDA_TRY(residual_d(A, pl, f, x, r, s));
+    dnorm2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, invdiag, r, f, partial, counter, out);
+    note_launch();
+    AMG_CUDA_TRY(cudaGetLastError());
+    double hn[2] = {0.0, 0.0};
+    AMG_CUDA_TRY(cudaMemcpyAsync(hn, out, sizeof hn, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!(hn[1] > 0.0)) return cudaSuccess;
+    *check = std::sqrt(hn[0] / hn[1]);
+    if (!(*check <= 1e-12)) return cudaSuccess;
+    *degree = m;
+    *theta = 0.5 * (hi + lo);
+    *delta = 0.5 * (hi - lo);
+    return cudaSuccess;
+}
+
 namespace {
 
 struct ChebCoef {
@@ -1011,6 +1427,13 @@ cudaError_t vcycle_level(const SolveCtx &c, int L, T **out, cudaStream_t s, T *f
     const LevelView &lv = c.lev[L];
     T *x = (T *)lv.x, *x2 = (T *)lv.x2;
     if (L == c.nlev - 1) {
+        if (c.coarse_degree > 0 && lv.n > 0) {
+            cudaError_t e = cudaSuccess;
+            *out = coarse_cheb_apply<T>(lv.plan_a, lv.n, lv.arp, lv.aci, (const T *)lv.av, (const T *)lv.invdiag,
+                                        (const T *)lv.f, x, x2, (T *)lv.d, c.coarse_theta, c.coarse_delta,
+                                        c.coarse_degree, s, &e);
+            return e;
+        }
         if (lv.n > 0)
             coarse_gemv_kernel<T><<<grid_for((int64_t)lv.n * 32, 128), 128, 0, s>>>(lv.n, c.coarse_inv,
                                                                                   (const T *)lv.f, x); note_launch();
