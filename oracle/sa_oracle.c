@@ -5,7 +5,8 @@
  * (arXiv:2103.10476).
  *
  * TEST INFRASTRUCTURE ONLY: the reference the CUDA path is checked against.  It is slow on
- * purpose (single thread, dense accumulators, sequential sums in ascending index order) and
+ * purpose (single thread, dense accumulators, sequential sums in ascending index order, by
+ * segments of 256 positions in rows longer than that) and
  * shares nothing with the CUDA library.  The product path never calls it.
  *
  * Where the paper is silent or ambiguous the reading taken is stated at the point of use
@@ -379,12 +380,50 @@ out:
     return st;
 }
 
+/* Sums along one stored row.  Reading (the paper fixes no summation order): position t of the
+ * row (0-based; every stored entry has a position, whether or not it is a term of the sum) lies
+ * in segment t / OC_SEG.  A row of at most OC_SEG positions is summed left to right from 0.  In
+ * a longer row each segment's terms are summed left to right from 0, then the sums of all the
+ * row's segments (0 for one without terms) are added left to right.  Used for the filtered
+ * matrix's sums (r_i, kappa+, kappa-, the dominance sum) and the 1Norm sums of Eq. (9)-(10). */
+#define OC_SEG 256
+typedef struct {
+    double tot, seg;
+    int64_t cur;          /* the segment being summed */
+} rowsum;
+
+static void rs_init(rowsum *s) { s->tot = 0.0; s->seg = 0.0; s->cur = 0; }
+
+/* closes the segments before segment q */
+static void rs_to(rowsum *s, int64_t q)
+{
+    while (s->cur < q) {
+        s->tot = s->cur == 0 ? s->seg : s->tot + s->seg;
+        s->seg = 0.0;
+        ++s->cur;
+    }
+}
+
+static void rs_add(rowsum *s, int64_t t, double x)
+{
+    rs_to(s, t / OC_SEG);
+    s->seg = s->seg + x;
+}
+
+/* the sum over a row of len positions */
+static double rs_value(rowsum *s, int64_t len)
+{
+    rs_to(s, len > 0 ? (len - 1) / OC_SEG : 0);
+    return s->cur == 0 ? s->seg : s->tot + s->seg;
+}
+
 static double ddom(const double *val, const int32_t *col, int64_t len, int64_t i, double aii)
 {
-    double s = 0.0;
+    rowsum s;
+    rs_init(&s);
     for (int64_t t = 0; t < len; ++t)
-        if (col[t] != i) s += fabs(val[t]);
-    return s / fabs(aii);
+        if (col[t] != i) rs_add(&s, t, fabs(val[t]));
+    return rs_value(&s, len) / fabs(aii);
 }
 
 /* Algorithm 2 (Lump_AvoidSmallDiag) for one row.  val/col: the stored row of A (length
@@ -412,9 +451,11 @@ static int offlmp_row(int64_t i, const int32_t *col, const double *val, const ui
     for (int64_t t = 0; t < len; ++t) { out[t] = val[t]; if (col[t] == i) di = t; }
     double aii = di >= 0 ? val[di] : 0.0;
     /* r_i: sum of the removed entries */
-    double r = 0.0;
+    rowsum rs;
+    rs_init(&rs);
     for (int64_t t = 0; t < len; ++t)
-        if (rem[t] && col[t] != i) r += val[t];
+        if (rem[t] && col[t] != i) rs_add(&rs, t, val[t]);
+    double r = rs_value(&rs, len);
     if (!(aii > 0.0)) {                    /* reading: fallback to Eq. (6) */
         if (di >= 0) out[di] = aii + r;
         return OC_LUMP_FALLBACK;
@@ -425,13 +466,16 @@ static int offlmp_row(int64_t i, const int32_t *col, const double *val, const ui
         return OC_LUMP_DIAG;
     }
     /* kept positive / negative off-diagonals K+, K- and their sums */
-    double kp = 0.0, km = 0.0;
+    rowsum sp, sm;
+    rs_init(&sp);
+    rs_init(&sm);
     int64_t nkp = 0, nkm = 0;
     for (int64_t t = 0; t < len; ++t) {
         if (col[t] == i || rem[t]) continue;
-        if (val[t] > 0.0) { kp += val[t]; ++nkp; }
-        else if (val[t] < 0.0) { km += val[t]; ++nkm; }
+        if (val[t] > 0.0) { rs_add(&sp, t, val[t]); ++nkp; }
+        else if (val[t] < 0.0) { rs_add(&sm, t, val[t]); ++nkm; }
     }
+    double kp = rs_value(&sp, len), km = rs_value(&sm, len);
     /* |r_i| <= kappa+: K+ absorbs all of it and stays non-negative */
     if (fabs(r) <= kp) {
         double delta = r / kp;
@@ -477,7 +521,8 @@ static int offlmp_row(int64_t i, const int32_t *col, const double *val, const ui
 /* Filtered matrix.  Its pattern is the diagonal plus every stored off-diagonal not in the
  * removal set (removed = weak, plus the §2.5 pruned links); entries that lumping sets to
  * zero stay stored (patterns are symbolic).  offlmp = 0: Eq. (6), the removed entries are
- * summed in ascending column order and added to a_ii; offlmp = 1: Algorithm 2. */
+ * summed in ascending column order (by segments in rows of more than OC_SEG entries, rowsum
+ * above) and added to a_ii; offlmp = 1: Algorithm 2. */
 int oc_filter(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, const uint8_t *removed,
               int offlmp, double tau, oc_csr **out, uint8_t *rowflag)
 {
@@ -498,14 +543,15 @@ int oc_filter(int64_t n, const int64_t *rp, const int32_t *ci, const double *v, 
         if (offlmp) {
             flag = offlmp_row(i, ci + b, v + b, removed + b, len, tau, tmp);
         } else {
-            double r = 0.0;
+            rowsum rs;
+            rs_init(&rs);
             int64_t di = -1;
             for (int64_t t = 0; t < len; ++t) {
                 tmp[t] = v[b + t];
                 if (ci[b + t] == i) di = t;
-                else if (removed[b + t]) r += v[b + t];
+                else if (removed[b + t]) rs_add(&rs, t, v[b + t]);
             }
-            if (di >= 0) tmp[di] = v[b + di] + r;
+            if (di >= 0) tmp[di] = v[b + di] + rs_value(&rs, len);
         }
         if (rowflag) rowflag[i] = (uint8_t)flag;
         for (int64_t t = 0; t < len; ++t) {
@@ -762,7 +808,11 @@ int oc_constrain_row(int64_t m, double *p, int64_t ptent_pos, double ptent_val)
 /* C = A B by rows (Gustavson): for each i, for k ascending in row i of A, for j in row k of B,
  * acc[j] = fma(a_ik, b_kj, acc[j]) (one rounding per term).  Every reachable (i, j) is stored,
  * whatever its value; columns are sorted.  Each c_ij is therefore accumulated in ascending k
- * starting from 0. */
+ * starting from 0.
+ * Reading for a row of A of more than OC_SEG stored entries (the same segments as rowsum
+ * above): the row's positions fall in segments of OC_SEG; each c_ij is accumulated as above
+ * over the terms of each segment separately (ascending k from 0), and the segment sums of
+ * every segment of the row (0 for a segment without a term for j) are added in segment order. */
 int oc_spgemm(const oc_csr *A, const oc_csr *B, int64_t ncolB, oc_csr **out)
 {
     int64_t n = A->n;
@@ -790,16 +840,42 @@ int oc_spgemm(const oc_csr *A, const oc_csr *B, int64_t ncolB, oc_csr **out)
     c->v = (double *)malloc((size_t)(c->nnz > 0 ? c->nnz : 1) * sizeof(double));
     for (int64_t j = 0; j < ncolB; ++j) mark[j] = -1;
     /* numeric */
+    double *tot = (double *)malloc((size_t)(ncolB > 0 ? ncolB : 1) * sizeof(double));
+    if (!tot) return OC_ERR_OOM;
     for (int64_t i = 0; i < n; ++i) {
         int64_t cnt = 0;
-        for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e) {
-            int64_t k = A->ci[e];
-            double a = A->v[e];
-            for (int64_t f = B->rp[k]; f < B->rp[k + 1]; ++f) {
-                int64_t j = B->ci[f];
-                if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols[cnt++] = (int32_t)j; }
-                acc[j] = fma(a, B->v[f], acc[j]);
+        const int64_t len = A->rp[i + 1] - A->rp[i];
+        if (len <= OC_SEG) {
+            for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e) {
+                int64_t k = A->ci[e];
+                double a = A->v[e];
+                for (int64_t f = B->rp[k]; f < B->rp[k + 1]; ++f) {
+                    int64_t j = B->ci[f];
+                    if (mark[j] != i) { mark[j] = i; acc[j] = 0.0; cols[cnt++] = (int32_t)j; }
+                    acc[j] = fma(a, B->v[f], acc[j]);
+                }
             }
+        } else {
+            /* the row's columns first, then one segment at a time */
+            for (int64_t e = A->rp[i]; e < A->rp[i + 1]; ++e)
+                for (int64_t f = B->rp[A->ci[e]]; f < B->rp[A->ci[e] + 1]; ++f) {
+                    int64_t j = B->ci[f];
+                    if (mark[j] != i) { mark[j] = i; cols[cnt++] = (int32_t)j; }
+                }
+            for (int64_t q = 0; q * OC_SEG < len; ++q) {
+                for (int64_t t = 0; t < cnt; ++t) acc[cols[t]] = 0.0;
+                const int64_t e0 = A->rp[i] + q * OC_SEG;
+                const int64_t e1 = e0 + OC_SEG < A->rp[i + 1] ? e0 + OC_SEG : A->rp[i + 1];
+                for (int64_t e = e0; e < e1; ++e) {
+                    int64_t k = A->ci[e];
+                    double a = A->v[e];
+                    for (int64_t f = B->rp[k]; f < B->rp[k + 1]; ++f)
+                        acc[B->ci[f]] = fma(a, B->v[f], acc[B->ci[f]]);
+                }
+                for (int64_t t = 0; t < cnt; ++t)
+                    tot[cols[t]] = q == 0 ? acc[cols[t]] : tot[cols[t]] + acc[cols[t]];
+            }
+            for (int64_t t = 0; t < cnt; ++t) acc[cols[t]] = tot[cols[t]];
         }
         qsort(cols, (size_t)cnt, sizeof(int32_t), cmp_i32);
         for (int64_t t = 0; t < cnt; ++t) {
@@ -807,7 +883,7 @@ int oc_spgemm(const oc_csr *A, const oc_csr *B, int64_t ncolB, oc_csr **out)
             c->v[rp[i] + t] = acc[cols[t]];
         }
     }
-    free(acc); free(mark); free(cols);
+    free(acc); free(mark); free(cols); free(tot);
     *out = c;
     return OC_OK;
 }
@@ -1068,11 +1144,15 @@ static int build_prolongator(oc_hier *h, int L, int stop_if_not_coarsened)
          * which is 2 s_i for sigma = 1/3; an all-zero row gets 1 */
         double f = (p->sigma == 1.0 / 3.0) ? 2.0 : 4.0 / (3.0 * (1.0 - p->sigma));
         for (int64_t i = 0; i < n; ++i) {
-            double d = 0.0, s = 0.0;
-            for (int64_t e = lv->Abar.rp[i]; e < lv->Abar.rp[i + 1]; ++e) {
-                d = d + fabs(lv->Abar.v[e]);
-                s = s + lv->Abar.v[e];
+            const int64_t b = lv->Abar.rp[i], len = lv->Abar.rp[i + 1] - b;
+            rowsum rd, rsum;
+            rs_init(&rd);
+            rs_init(&rsum);
+            for (int64_t e = b; e < b + len; ++e) {
+                rs_add(&rd, e - b, fabs(lv->Abar.v[e]));
+                rs_add(&rsum, e - b, lv->Abar.v[e]);
             }
+            double d = rs_value(&rd, len), s = rs_value(&rsum, len);
             if (d == 0.0) d = 1.0;
             if (d < f * s) d = f * s;
             lv->Dsm[i] = d;

@@ -213,6 +213,7 @@ struct SpmvPlan {
     const int *sp = nullptr, *sw = nullptr, *sci = nullptr;
     const double *sv64 = nullptr;
     const float *sv32 = nullptr;
+    size_t sell_entries = 0;     // stored entries of the copy, padding included
     // rows split off the row tiles for the solve's products (a device list owned by the
     // hierarchy; split = nullptr: none).  Every row with more than split_len entries is listed:
     // the first split_long (more than kSplitBlockLen entries) are summed by a block each, the
@@ -286,7 +287,7 @@ cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, doubl
                      double *result, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
                             double *partial, double *result, unsigned *counter, cudaStream_t s);
-cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, const double *xx,
+cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *invD, const double *x, const double *xx,
                        double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
 cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,

@@ -149,6 +149,54 @@ void amgk::trace_mark(amg_hierarchy *h, int level, int phase)
 namespace {
 
 // one level of the hierarchy; *coarsest = 1 if the level cannot be coarsened further
+// Whether a level operator gets a sliced-ELL copy for its products (params.spmv_layout): AUTO
+// copies an operator with short rows when it is larger than L2 (the CSR kernel would stream it
+// from HBM) or has rows enough for four 256-row sliced blocks per SM: one lane per row issues
+// fewer FP64 instructions than two, but a level with fewer rows leaves the SMs without warps to
+// cover the latency of its longer rows.
+bool sell_wanted(const amg_hierarchy *h, const Level &lv, int l2, int nsm)
+{
+    const bool want = h->p.spmv_layout == AMG_LAYOUT_SELL ||
+                      (h->p.spmv_layout == AMG_LAYOUT_AUTO &&
+                       (12.0 * (double)lv.A.nnz > (double)l2 || (double)lv.A.n >= 1024.0 * nsm));
+    return want && lv.plan_a.lpr == 2 && lv.A.n > 0 && lv.plan_a.sci == nullptr;
+}
+
+// The finest level's sliced-ELL copy (FP64 values) during setup, so that its power method reads
+// it too; no copy when the offsets would overflow or the padding exceeds an eighth of the
+// entries.  Synchronises s.
+cudaError_t sell_build_fine(amg_hierarchy *h, Level &lv, cudaStream_t s)
+{
+    int dev = 0, l2 = 0, nsm = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (!sell_wanted(h, lv, l2, nsm)) return cudaSuccess;
+    const int nsl = sell_slices(lv.A.n);
+    int *sw = nullptr, *sp = nullptr, *sci = nullptr;
+    unsigned long long *t64 = nullptr, tot = 0;
+    double *sv64 = nullptr;
+    AMG_CUDA_TRY(dalloc(h, &sw, (size_t)nsl));
+    AMG_CUDA_TRY(dalloc(h, &sp, (size_t)nsl + 1));
+    AMG_CUDA_TRY(dalloc(h, &t64, 1));
+    AMG_CUDA_TRY(sell_layout(lv.A.n, lv.A.rp, sw, sp, t64, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(&tot, t64, sizeof tot, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (tot > (unsigned long long)INT32_MAX - 64 || tot > (unsigned long long)lv.A.nnz + (unsigned long long)lv.A.nnz / 8)
+        return cudaSuccess;
+    AMG_CUDA_TRY(dalloc(h, &sci, (size_t)tot));
+    AMG_CUDA_TRY(dalloc(h, &sv64, (size_t)tot));
+    SpmvPlan &pa = lv.plan_a;
+    pa.ns = nsl;
+    pa.sw = sw;
+    pa.sp = sp;
+    AMG_CUDA_TRY(sell_fill_d(lv.A.n, lv.A.rp, lv.A.ci, lv.A.v, pa.ns, pa.sp, pa.sw, sci, sv64, s));
+    pa.sci = sci;
+    pa.sv64 = sv64;
+    pa.sell_entries = (size_t)tot;
+    return cudaSuccess;
+}
+
 amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
 {
     amg_status_t st = AMG_OK;
@@ -491,7 +539,9 @@ galerkin:
         CK(e);
         trace_mark(h, L, AMG_PH_GALERKIN_RAP);
     }
-    // Chebyshev smoother: lambda_max(D^-1 A_L) and D^-1
+    // Chebyshev smoother: lambda_max(D^-1 A_L) and D^-1 (the finest level's power method on
+    // its sliced-ELL copy, made here rather than with the other levels' copies)
+    if (L == 0) CK(sell_build_fine(h, lv, s));
     CK(dalloc(h, &lv.invdiag, (size_t)n));
     if (p.precision == AMG_MIXED) CK(dalloc(h, &lv.invdiag_f, (size_t)n));
     CK(invert_diag(lv.diag, lv.invdiag, lv.invdiag_f, n, flags + 3, s));
@@ -682,12 +732,9 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         if (h->nlev == 1 && n0 > 0) {
             pls.push_back(&h->plan0); rps.push_back(h->lev[0].A.rp); ns.push_back(n0); nz.push_back(h->lev[0].A.nnz);
         }
-        // sliced-ELL copies of the level operators with short rows (their layout first; the
-        // entry counts reach the host with the plans' synchronisation)
-        // AUTO copies an operator with short rows when it is larger than L2 (the CSR kernel
-        // would stream it from HBM) or has rows enough for four 256-row sliced blocks per SM: one
-        // lane per row issues fewer FP64 instructions than two, but a level with fewer rows
-        // leaves the SMs without warps to cover the latency of its longer rows.
+        // sliced-ELL copies of the level operators with short rows (sell_wanted; their layout
+        // first; the entry counts reach the host with the plans' synchronisation).  The finest
+        // level's FP64 copy exists already (sell_build_fine).
         std::vector<int> sell_levels;
         unsigned long long *tot_host = (unsigned long long *)h->rr_host;
         int dev = 0, l2 = 0, nsm = 0;
@@ -696,10 +743,7 @@ amg_status_t prepare_solve(amg_hierarchy *h)
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         for (int L = 0; L + 1 < h->nlev; ++L) {
             Level &lv = h->lev[L];
-            const bool want = h->p.spmv_layout == AMG_LAYOUT_SELL ||
-                              (h->p.spmv_layout == AMG_LAYOUT_AUTO &&
-                               (12.0 * (double)lv.A.nnz > (double)l2 || (double)lv.A.n >= 1024.0 * nsm));
-            if (!want || lv.plan_a.lpr != 2 || lv.A.n == 0 || (int)sell_levels.size() >= kReduceBlocks) continue;
+            if (!sell_wanted(h, lv, l2, nsm) || (int)sell_levels.size() >= kReduceBlocks) continue;
             const int nsl = sell_slices(lv.A.n);
             int *sw = nullptr, *sp = nullptr;
             unsigned long long *t64 = nullptr;
@@ -731,12 +775,23 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             CK(sell_fill_d(lv.A.n, lv.A.rp, lv.A.ci, lv.A.v, pa.ns, pa.sp, pa.sw, sci, sv64, s));
             pa.sci = sci;
             pa.sv64 = sv64;
+            pa.sell_entries = total;
             if (mixed) {
                 float *sv32 = nullptr;
                 CK(dalloc(h, &sv32, total));
                 CK(sell_fill_f(lv.A.n, lv.A.rp, lv.Af, pa.ns, pa.sp, pa.sw, sv32, s));
                 pa.sv32 = sv32;
             }
+        }
+        // the FP32 values of a copy made during setup (the finest level's)
+        for (int L = 0; mixed && L + 1 < h->nlev; ++L) {
+            Level &lv = h->lev[L];
+            SpmvPlan &pa = lv.plan_a;
+            if (!pa.sci || pa.sv32) continue;
+            float *sv32 = nullptr;
+            CK(dalloc(h, &sv32, pa.sell_entries));
+            CK(sell_fill_f(lv.A.n, lv.A.rp, lv.Af, pa.ns, pa.sp, pa.sw, sv32, s));
+            pa.sv32 = sv32;
         }
         // rows far longer than their operator's mean leave the row tiles of every solve product
         {

@@ -647,158 +647,85 @@ cudaError_t sprsfy(const DevCsr &A, const uint8_t *strong, const int *agg, const
 enum { LUMP_DIAG = 0, LUMP_KPLUS = 1, LUMP_DIAG_KMINUS = 2, LUMP_KPLUS_NEG = 3, LUMP_SKIPPED = 4,
        LUMP_FALLBACK = 5 };
 
-// Every sum runs sequentially in ascending column order.  Rows of up to kFilterLong entries: one
-// thread per row (the per-row FP64 work is a handful of additions per stored entry, and GB300's
-// FP64 pipe makes redundant per-lane sums expensive).  Longer rows (a stalled coarse level holds
-// rows of thousands): one warp per row, the warp loading 32 entries at a time with coalesced
-// loads and every lane running the same sequential sums on them (shuffled in entry order), so
-// the row no longer waits on one thread's dependent loads; lane 0 writes.  Both take the
-// entries in the same order and give the same bits.
+// Every sum runs in ascending column order: left to right from 0 over a row of at most
+// kFilterLong stored positions, one thread per row (the per-row FP64 work is a handful of
+// additions per stored entry, and GB300's FP64 pipe makes redundant per-lane sums expensive).
+// A longer row (a stalled coarse level holds rows of thousands) is summed by segments of
+// kFilterLong positions, each left to right from 0, the segment sums then added left to right
+// (the oracle's reading for long rows): one warp per row, lane q summing segment q, so the row's
+// time is one segment's chain of dependent additions instead of the whole row's.
 constexpr int kFilterLong = 256;
 
-// the row's entries, one at a time, from global memory
-struct FilterThreadAccess {
-    const int *ci;
-    const double *v;
-    const uint8_t *removed;
-    __device__ __forceinline__ void load(int e, int &j, double &val, int &rem) const
-    {
-        j = ci[e];
-        val = v[e];
-        rem = removed[e];
-    }
-};
-
-// the row's entries from a chunk of 32 held one per lane, reloaded (by every lane) when entry
-// e leaves it; load() is called with e = b, b + 1, ... by every lane in step
-struct FilterWarpAccess {
-    const int *ci;
-    const double *v;
-    const uint8_t *removed;
-    int e_end;
-    int base = -(1 << 30);
-    int cj = 0, crem = 0;
-    double cv = 0.0;
-    __device__ __forceinline__ void load(int e, int &j, double &val, int &rem)
-    {
-        const int lane = threadIdx.x & 31;
-        if (e < base || e >= base + 32) {
-            base = e;
-            const int idx = e + lane;
-            if (idx < e_end) {
-                cj = ci[idx];
-                cv = v[idx];
-                crem = removed[idx];
-            }
-        }
-        j = __shfl_sync(0xffffffffu, cj, e - base);
-        val = __shfl_sync(0xffffffffu, cv, e - base);
-        rem = __shfl_sync(0xffffffffu, crem, e - base);
-    }
-};
-
-template <typename Acc>
-__device__ __forceinline__ void filter_row(int i, int b, int e_end, Acc &acc, bool writer, int offlmp, double tau,
-                                           int onenorm, double sigma, const int *brp, int *bci, double *bv,
-                                           double *Dsm, uint8_t *lumpflag, int *zero_diag)
-{
-    // pass 1: row sums in ascending order
-    double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
-    int nkp = 0, nkm = 0, has_diag = 0;
-    for (int e = b; e < e_end; ++e) {
-        int j, rem;
-        double val;
-        acc.load(e, j, val, rem);
-        if (j == i) {
-            aii = val;
-            has_diag = 1;
-            continue;
-        }
-        if (offlmp) offabs = offabs + fabs(val);
-        if (rem) {
-            r = r + val;
-        } else if (offlmp) {
-            if (val > 0.0) { kp = kp + val; ++nkp; }
-            else if (val < 0.0) { km = km + val; ++nkm; }
-        }
-    }
-    // the row's outcome
+// The row's outcome from its sums (Eq. 6, or Algorithm 2 with offlmp)
+struct FilterOutcome {
     int flag = LUMP_DIAG;
-    double new_diag = aii + r;     // Eq. (6)
-    double fplus = 1.0, fminus = 1.0;
+    double new_diag = 0.0, fplus = 1.0, fminus = 1.0;
     bool zero_plus = false;
-    if (offlmp) {
-        if (!(aii > 0.0)) {
-            flag = LUMP_FALLBACK;
-        } else if (r >= 0.0) {
-            flag = LUMP_DIAG;
-        } else if (fabs(r) <= kp) {
-            flag = LUMP_KPLUS;
-            new_diag = aii;
-            fplus = 1.0 + r / kp;
-        } else if (nkm == 0) {
-            new_diag = aii;
-            if (nkp > 0) {
-                flag = LUMP_KPLUS_NEG;
-                fplus = 1.0 + r / kp;
-            } else {
-                flag = LUMP_SKIPPED;
-            }
+};
+
+__device__ __forceinline__ FilterOutcome filter_outcome(double aii, double r, double kp, double km, double offabs,
+                                                        int nkp, int nkm, int offlmp, double tau)
+{
+    FilterOutcome o;
+    o.new_diag = aii + r;     // Eq. (6)
+    if (!offlmp) return o;
+    if (!(aii > 0.0)) {
+        o.flag = LUMP_FALLBACK;
+    } else if (r >= 0.0) {
+        o.flag = LUMP_DIAG;
+    } else if (fabs(r) <= kp) {
+        o.flag = LUMP_KPLUS;
+        o.new_diag = aii;
+        o.fplus = 1.0 + r / kp;
+    } else if (nkm == 0) {
+        o.new_diag = aii;
+        if (nkp > 0) {
+            o.flag = LUMP_KPLUS_NEG;
+            o.fplus = 1.0 + r / kp;
         } else {
-            flag = LUMP_DIAG_KMINUS;
-            zero_plus = true;
-            double rhat = r + kp;
-            double t_bound = tau * (offabs / fabs(aii));
-            double N = -km - rhat;
-            double mag = -rhat;
-            double rstar;
-            if (N <= aii) {
-                rstar = mag;
-            } else if (N <= t_bound * aii) {
-                double rmax = (t_bound * aii - N) / (t_bound - 1.0);
-                rstar = rmax < mag ? rmax : mag;
-            } else {
-                rstar = 0.0;
-            }
-            new_diag = aii - rstar;
-            fminus = 1.0 + (rhat + rstar) / km;
+            o.flag = LUMP_SKIPPED;
+        }
+    } else {
+        o.flag = LUMP_DIAG_KMINUS;
+        o.zero_plus = true;
+        double rhat = r + kp;
+        double t_bound = tau * (offabs / fabs(aii));
+        double N = -km - rhat;
+        double mag = -rhat;
+        double rstar;
+        if (N <= aii) {
+            rstar = mag;
+        } else if (N <= t_bound * aii) {
+            double rmax = (t_bound * aii - N) / (t_bound - 1.0);
+            rstar = rmax < mag ? rmax : mag;
+        } else {
+            rstar = 0.0;
+        }
+        o.new_diag = aii - rstar;
+        o.fminus = 1.0 + (rhat + rstar) / km;
+    }
+    return o;
+}
+
+// a kept entry's new value (j != i)
+__device__ __forceinline__ double filter_kept_value(double val, const FilterOutcome &o, int offlmp)
+{
+    double nv = val;
+    if (offlmp && o.flag != LUMP_FALLBACK) {
+        if (val > 0.0) {
+            if (o.zero_plus) nv = 0.0;
+            else if (o.flag == LUMP_KPLUS || o.flag == LUMP_KPLUS_NEG) nv = val * o.fplus;
+        } else if (val < 0.0 && o.flag == LUMP_DIAG_KMINUS) {
+            nv = val * o.fminus;
         }
     }
-    // pass 2: the kept entries, and the 1-norm sums over them in ascending order
-    int out = brp[i];
-    double dsum = 0.0, ssum = 0.0;
-    for (int e = b; e < e_end; ++e) {
-        int j, rem;
-        double val;
-        acc.load(e, j, val, rem);
-        double nv;
-        if (j == i) {
-            nv = new_diag;
-        } else if (!rem) {
-            nv = val;
-            if (offlmp && flag != LUMP_FALLBACK) {
-                if (val > 0.0) {
-                    if (zero_plus) nv = 0.0;
-                    else if (flag == LUMP_KPLUS || flag == LUMP_KPLUS_NEG) nv = val * fplus;
-                } else if (val < 0.0 && flag == LUMP_DIAG_KMINUS) {
-                    nv = val * fminus;
-                }
-            }
-        } else {
-            continue;
-        }
-        if (writer) {
-            bci[out] = j;
-            bv[out] = nv;
-        }
-        ++out;
-        if (onenorm) {
-            dsum = dsum + fabs(nv);
-            ssum = ssum + nv;
-        }
-    }
-    if (!writer) return;
-    lumpflag[i] = (uint8_t)flag;
+    return nv;
+}
+
+// the smoothing diagonal from the row's sums
+__device__ __forceinline__ double filter_dsm(int onenorm, double sigma, double dsum, double ssum, int has_diag,
+                                             double new_diag, int *zero_diag)
+{
     double dd;
     if (onenorm) {
         double f = (sigma == 1.0 / 3.0) ? 2.0 : 4.0 / (3.0 * (1.0 - sigma));
@@ -809,7 +736,169 @@ __device__ __forceinline__ void filter_row(int i, int b, int e_end, Acc &acc, bo
         dd = has_diag ? new_diag : 0.0;
         if (dd == 0.0) atomicAdd(zero_diag, 1);
     }
-    Dsm[i] = dd;
+    return dd;
+}
+
+__device__ __forceinline__ void filter_row(int i, int b, int e_end, const int *ci, const double *v,
+                                           const uint8_t *removed, int offlmp, double tau, int onenorm, double sigma,
+                                           const int *brp, int *bci, double *bv, double *Dsm, uint8_t *lumpflag,
+                                           int *zero_diag)
+{
+    // pass 1: row sums in ascending order
+    double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
+    int nkp = 0, nkm = 0, has_diag = 0;
+    for (int e = b; e < e_end; ++e) {
+        const int j = ci[e];
+        const double val = v[e];
+        if (j == i) {
+            aii = val;
+            has_diag = 1;
+            continue;
+        }
+        if (offlmp) offabs = offabs + fabs(val);
+        if (removed[e]) {
+            r = r + val;
+        } else if (offlmp) {
+            if (val > 0.0) { kp = kp + val; ++nkp; }
+            else if (val < 0.0) { km = km + val; ++nkm; }
+        }
+    }
+    const FilterOutcome o = filter_outcome(aii, r, kp, km, offabs, nkp, nkm, offlmp, tau);
+    // pass 2: the kept entries, and the 1-norm sums over them in ascending order
+    int out = brp[i];
+    double dsum = 0.0, ssum = 0.0;
+    for (int e = b; e < e_end; ++e) {
+        const int j = ci[e];
+        double nv;
+        if (j == i) nv = o.new_diag;
+        else if (!removed[e]) nv = filter_kept_value(v[e], o, offlmp);
+        else continue;
+        bci[out] = j;
+        bv[out] = nv;
+        ++out;
+        if (onenorm) {
+            dsum = dsum + fabs(nv);
+            ssum = ssum + nv;
+        }
+    }
+    lumpflag[i] = (uint8_t)o.flag;
+    Dsm[i] = filter_dsm(onenorm, sigma, dsum, ssum, has_diag, o.new_diag, zero_diag);
+}
+
+// Row i of more than kFilterLong entries, by one warp: segment q (positions q kFilterLong ..
+// (q + 1) kFilterLong - 1 of A's row in pass 1, of Abar's row for the 1-norm sums) on lane
+// q mod 32; every lane folds the segment sums of each group of 32 in segment order (shuffles),
+// so all lanes hold the row's sums.
+__device__ void filter_long_row(int i, int b, int e_end, const int *ci, const double *v, const uint8_t *removed,
+                                int offlmp, double tau, int onenorm, double sigma, const int *brp, int *bci,
+                                double *bv, double *Dsm, uint8_t *lumpflag, int *zero_diag)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nseg = (e_end - b + kFilterLong - 1) / kFilterLong;
+    double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
+    int nkp = 0, nkm = 0, has_diag = 0;
+    for (int q0 = 0; q0 < nseg; q0 += 32) {
+        const int q = q0 + lane;
+        double sr = 0.0, skp = 0.0, skm = 0.0, soff = 0.0, da = 0.0;
+        int cp = 0, cm = 0, hd = 0;
+        if (q < nseg) {
+            const int e0 = b + q * kFilterLong, e1 = min(e_end, e0 + kFilterLong);
+            for (int e = e0; e < e1; ++e) {
+                const int j = ci[e];
+                const double val = v[e];
+                if (j == i) {
+                    da = val;
+                    hd = 1;
+                    continue;
+                }
+                if (offlmp) soff = soff + fabs(val);
+                if (removed[e]) {
+                    sr = sr + val;
+                } else if (offlmp) {
+                    if (val > 0.0) { skp = skp + val; ++cp; }
+                    else if (val < 0.0) { skm = skm + val; ++cm; }
+                }
+            }
+        }
+        const int last = min(32, nseg - q0);
+        for (int t = 0; t < last; ++t) {
+            const double a1 = __shfl_sync(full, sr, t), a2 = __shfl_sync(full, skp, t);
+            const double a3 = __shfl_sync(full, skm, t), a4 = __shfl_sync(full, soff, t);
+            if (q0 + t == 0) {
+                r = a1; kp = a2; km = a3; offabs = a4;
+            } else {
+                r = r + a1; kp = kp + a2; km = km + a3; offabs = offabs + a4;
+            }
+        }
+        nkp += __reduce_add_sync(full, cp);
+        nkm += __reduce_add_sync(full, cm);
+        const unsigned dm = __ballot_sync(full, hd);
+        if (dm) {
+            aii = __shfl_sync(full, da, __ffs(dm) - 1);
+            has_diag = 1;
+        }
+    }
+    const FilterOutcome o = filter_outcome(aii, r, kp, km, offabs, nkp, nkm, offlmp, tau);
+    // pass 2: each lane writes the kept entries of its segments at their places in Abar's row
+    int base = brp[i];
+    for (int q0 = 0; q0 < nseg; q0 += 32) {
+        const int q = q0 + lane;
+        const int e0 = b + q * kFilterLong, e1 = q < nseg ? min(e_end, e0 + kFilterLong) : e0;
+        int kept = 0;
+        for (int e = e0; e < e1; ++e) kept += (ci[e] == i || !removed[e]);
+        int incl = kept;
+#pragma unroll
+        for (int o2 = 1; o2 < 32; o2 <<= 1) {
+            const int y = __shfl_up_sync(full, incl, o2);
+            if (lane >= o2) incl += y;
+        }
+        int out = base + incl - kept;
+        for (int e = e0; e < e1; ++e) {
+            const int j = ci[e];
+            double nv;
+            if (j == i) nv = o.new_diag;
+            else if (!removed[e]) nv = filter_kept_value(v[e], o, offlmp);
+            else continue;
+            bci[out] = j;
+            bv[out] = nv;
+            ++out;
+        }
+        base += __shfl_sync(full, incl, 31);
+    }
+    // the 1-norm sums over Abar's row, by segments of its positions
+    double dsum = 0.0, ssum = 0.0;
+    if (onenorm) {
+        __threadfence_block();
+        __syncwarp();
+        const int ab = brp[i], ae = base;
+        const int nseg2 = (ae - ab + kFilterLong - 1) / kFilterLong;
+        for (int q0 = 0; q0 < nseg2; q0 += 32) {
+            const int q = q0 + lane;
+            double sd = 0.0, ss = 0.0;
+            if (q < nseg2) {
+                const int e0 = ab + q * kFilterLong, e1 = min(ae, e0 + kFilterLong);
+                for (int e = e0; e < e1; ++e) {
+                    const double nv = bv[e];
+                    sd = sd + fabs(nv);
+                    ss = ss + nv;
+                }
+            }
+            const int last = min(32, nseg2 - q0);
+            for (int t = 0; t < last; ++t) {
+                const double a1 = __shfl_sync(full, sd, t), a2 = __shfl_sync(full, ss, t);
+                if (q0 + t == 0) {
+                    dsum = a1; ssum = a2;
+                } else {
+                    dsum = dsum + a1; ssum = ssum + a2;
+                }
+            }
+        }
+    }
+    if (lane == 0) {
+        lumpflag[i] = (uint8_t)o.flag;
+        Dsm[i] = filter_dsm(onenorm, sigma, dsum, ssum, has_diag, o.new_diag, zero_diag);
+    }
 }
 
 __global__ void filter_kernel(int n, const int *rp, const int *ci, const double *v, const uint8_t *removed,
@@ -824,8 +913,7 @@ __global__ void filter_kernel(int n, const int *rp, const int *ci, const double 
         long_rows[atomicAdd(nlong, 1)] = i;
         return;
     }
-    FilterThreadAccess acc{ci, v, removed};
-    filter_row(i, b, e_end, acc, true, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag, zero_diag);
+    filter_row(i, b, e_end, ci, v, removed, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag, zero_diag);
 }
 
 __global__ void filter_long_kernel(const int *rp, const int *ci, const double *v, const uint8_t *removed, int offlmp,
@@ -834,13 +922,10 @@ __global__ void filter_long_kernel(const int *rp, const int *ci, const double *v
                                    const int *nlong)
 {
     const int warps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
-    const int lane = threadIdx.x & 31;
     for (int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); w < *nlong; w += warps) {
         const int i = long_rows[w];
-        const int b = rp[i], e_end = rp[i + 1];
-        FilterWarpAccess acc{ci, v, removed, e_end};
-        filter_row(i, b, e_end, acc, lane == 0, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag,
-                   zero_diag);
+        filter_long_row(i, rp[i], rp[i + 1], ci, v, removed, offlmp, tau, onenorm, sigma, brp, bci, bv, Dsm, lumpflag,
+                        zero_diag);
     }
 }
 
@@ -1154,6 +1239,8 @@ cudaError_t transpose_fill(const DevCsr &P, DevCsr &R, int *fill, cudaStream_t s
 // ------------------------------------------------------------------------------------ power method
 // x0_i = 2 u_i - 1, u_i the i-th output of the SplitMix64 stream started at stream_seed;
 // x = x0 / ||x0||; each sweep y = D^-1 A x, lambda = x . y; between sweeps x = y / ||y||.
+// (The sweeps multiply by 1/D_i where the oracle divides by D_i: the estimate agrees to
+// rounding.)
 uint64_t power_stream_seed(uint64_t seed, int level, int purpose)
 {
     return seed ^ ((uint64_t)(level + 1) << 48) ^ ((uint64_t)purpose << 56);
@@ -1168,11 +1255,26 @@ __global__ void power_init_kernel(int n, uint64_t s0, double *x)
     x[i] = 2.0 * u - 1.0;
 }
 
+__global__ void reciprocal_kernel(int n, const double *D, double *inv)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) inv[i] = 1.0 / D[i];
+}
+
 cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D, int sweeps, uint64_t stream_seed,
                          double *x, double *y, double *partial, double *scal, double *lambda_dev, cudaStream_t s)
 {
     const int n = A.n;
     if (n == 0) return cudaMemsetAsync(lambda_dev, 0, sizeof(double), s);
+    // D^-1 once (the sweeps multiply by it: an FP64 division per row and sweep is a long
+    // instruction sequence on this GPU)
+    double *invD = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&invD, sizeof(double) * (size_t)n, s));
+    struct Release {
+        double *p; cudaStream_t s;
+        ~Release() { cudaFreeAsync(p, s); }
+    } release{invD, s};
+    reciprocal_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, D, invD); note_launch();
     // x0 and x0 . x0; each sweep then works on the unnormalised iterate and its squared norm
     // (scal[3], scal[4] alternate), which equals normalising before every sweep
     power_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, stream_seed, x); note_launch();
@@ -1183,7 +1285,7 @@ cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D,
     AMG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(double), s));
     double *a = x, *b = y;
     for (int k = 0; k < sweeps; ++k) {
-        AMG_CUDA_TRY(spmv_power(A, plan, D, a, scal + 3 + (k & 1), b, scal + 4 - (k & 1), partial, lambda_dev,
+        AMG_CUDA_TRY(spmv_power(A, plan, invD, a, scal + 3 + (k & 1), b, scal + 4 - (k & 1), partial, lambda_dev,
                                 counter, s));
         std::swap(a, b);
     }

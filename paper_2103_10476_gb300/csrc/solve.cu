@@ -35,8 +35,8 @@ enum SpmvMode {
     MODE_PROLONG = 3,    // y += A x
     MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
     MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
-    MODE_POWER = 6,      // power-method sweep on an unnormalised x with q = f[0] = x . x:
-                         // y = (A x) / D / sqrt(q); result[0] = (x . y) / sqrt(q); d[0] = y . y
+    MODE_POWER = 6,      // power-method sweep on an unnormalised x with q = f[0] = x . x, aux = D^-1:
+                         // y = (D^-1 A x) / sqrt(q); result[0] = (x . y) / sqrt(q); d[0] = y . y
 };
 
 
@@ -71,16 +71,17 @@ __device__ __forceinline__ void last_block_total(const double *partial, int nblo
 }
 
 // Two fixed-order sums at once (partial[0, nblocks) and partial[nblocks, 2 nblocks)); the last
-// block stores *r1 = scale * (first total) and *r2 = second total.
+// block to arrive (of narrive; nblocks when not given) stores *r1 = scale * (first total) and
+// *r2 = second total.
 __device__ __forceinline__ void last_block_total2(const double *partial, int nblocks, unsigned *counter, double *r1,
-                                                  double *r2, double scale)
+                                                  double *r2, double scale, int narrive = -1)
 {
     __shared__ bool last;
     __shared__ double w1[32], w2[32];
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(counter, 1u) == (unsigned)nblocks - 1u;
+        last = atomicAdd(counter, 1u) == (unsigned)(narrive < 0 ? nblocks : narrive) - 1u;
     }
     __syncthreads();
     if (!last) return;
@@ -134,7 +135,7 @@ __device__ __forceinline__ void outside_row_update(int row, T sr, const T *x, T 
         y[row] = sr / aux[row];
     } else {
         const double rq = 1.0 / __dsqrt_rn((double)f[0]);
-        y[row] = (T)(((double)sr / (double)aux[row]) * rq);
+        y[row] = (T)(((double)sr * (double)aux[row]) * rq);
     }
 }
 
@@ -310,27 +311,65 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         }
         return;
     }
-#pragma unroll
-    for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
-    double contrib = 0.0, contrib2 = 0.0;
-    double rq = 0.0;                // MODE_POWER: 1 / sqrt(x . x), formed once per block (a
-    if (MODE == MODE_POWER) {       // square root and a division are long FP64 sequences)
+    if (MODE == MODE_POWER) {
+        // As for the update modes: row r's update by thread r < RPB (full warps; y_i takes three
+        // FP64 products), D^-1 from aux, 1 / sqrt(x . x) formed once per block (a square root
+        // and a division are long FP64 sequences); then the block's two dot-product partials.
+        __shared__ double pps[kSpmvThreads];
         __shared__ double rq_s;
+        if (LPR == 2) {
+            pps[lane * RPB + threadIdx.x / LPR] = (double)sum;
+        } else {
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
+            if (lane == 0) pps[threadIdx.x / LPR] = (double)sum;
+        }
         if (threadIdx.x == 0) rq_s = 1.0 / __dsqrt_rn((double)f[0]);
         __syncthreads();
-        rq = rq_s;
-    }
-    if (row < r1 && lane == 0 && tile_ok && is_long) {
-        // the long row's value is in y already: only its share of the dot products here
-        if (MODE == MODE_DOT) {
-            contrib = (double)x[row] * (double)y[row];
-        } else if (MODE == MODE_SCALEDOT) {
-            contrib = (double)x[row] * (double)y[row];
-        } else if (MODE == MODE_POWER) {
-            const double yi = (double)y[row];
-            contrib = (double)x[row] * yi;
-            contrib2 = yi * yi;
+        const double rq = rq_s;
+        double c1v = 0.0, c2v = 0.0;
+        const int rw = r0 + (int)threadIdx.x;
+        if ((int)threadIdx.x < RPB && rw < r1 && tile_ok) {
+            double yi;
+            if (rp[rw + 1] - rp[rw] > long_len) {
+                yi = (double)y[rw];                 // summed outside the tiles, in y already
+            } else {
+                const double sr = LPR == 2 ? pps[threadIdx.x] + pps[RPB + threadIdx.x] : pps[threadIdx.x];
+                yi = (sr * (double)aux[rw]) * rq;
+                y[rw] = (T)yi;
+            }
+            c1v = (double)x[rw] * yi;
+            c2v = yi * yi;
         }
+        __shared__ double sp1[kSpmvThreads / 32], sp2[kSpmvThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c1v += __shfl_down_sync(kAll, c1v, o);
+            c2v += __shfl_down_sync(kAll, c2v, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sp1[threadIdx.x >> 5] = c1v;
+            sp2[threadIdx.x >> 5] = c2v;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int w = 0; w < kSpmvThreads / 32; ++w) {
+                t1 += sp1[w];
+                t2 += sp2[w];
+            }
+            partial[bx] = t1;
+            partial[nbx + bx] = t2;
+        }
+        last_block_total2(partial, nbx, counter, result, (double *)d, rq);
+        return;
+    }
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
+    double contrib = 0.0;
+    if (row < r1 && lane == 0 && tile_ok && is_long) {
+        // the long row's value is in y already: only its share of the dot product here
+        contrib = (double)x[row] * (double)y[row];
     } else if (row < r1 && lane == 0 && tile_ok) {
         if (MODE == MODE_Y) {
             y[row] = sum;
@@ -350,35 +389,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             T yi = sum / aux[row];
             y[row] = yi;
             contrib = (double)x[row] * (double)yi;
-        } else {
-            const double yi = ((double)sum / (double)aux[row]) * rq;
-            y[row] = (T)yi;
-            contrib = (double)x[row] * yi;
-            contrib2 = yi * yi;
         }
-    }
-    if (MODE == MODE_POWER) {
-        __shared__ double sh1[kSpmvThreads / 32], sh2[kSpmvThreads / 32];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            contrib += __shfl_down_sync(kAll, contrib, o);
-            contrib2 += __shfl_down_sync(kAll, contrib2, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            sh1[threadIdx.x >> 5] = contrib;
-            sh2[threadIdx.x >> 5] = contrib2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t1 = 0.0, t2 = 0.0;
-            for (int w = 0; w < kSpmvThreads / 32; ++w) {
-                t1 += sh1[w];
-                t2 += sh2[w];
-            }
-            partial[bx] = t1;
-            partial[nbx + bx] = t2;
-        }
-        last_block_total2(partial, nbx, counter, result, (double *)d, rq);
     }
     if (MODE == MODE_DOT || MODE == MODE_SCALEDOT) {
         __shared__ double sh[kSpmvThreads / 32];
@@ -686,9 +697,10 @@ __device__ __forceinline__ int ld_stream(const int *p)
     return v;
 }
 
-// MODE_Y, MODE_RESID, MODE_CHEB and MODE_DOT (partials only) as in spmv_tile_kernel.  MODE_DOT
-// writes the partials of the two-lanes-per-row CSR kernel: one per 128 rows (nparts), each
-// summed by the same shuffle tree and the same order of warps.
+// MODE_Y, MODE_RESID, MODE_CHEB, MODE_DOT (partials only) and MODE_POWER as in
+// spmv_tile_kernel.  MODE_DOT and MODE_POWER write the partials of the two-lanes-per-row CSR
+// kernel: one per 128 rows (nparts), each summed by the same shuffle tree and the same order of
+// warps; MODE_POWER then completes its two sums as the CSR kernel does (result, counter).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const int *__restrict__ sp,
                                                                  const int *__restrict__ sw,
@@ -696,9 +708,17 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
                                                                  const T *__restrict__ sv, const T *__restrict__ x,
                                                                  T *y, const T *__restrict__ f,
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
-                                                                 double *partial, int nparts)
+                                                                 double *partial, int nparts, double *result,
+                                                                 unsigned *counter)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double rq = 0.0;
+    if (MODE == MODE_POWER) {
+        __shared__ double rq_s;
+        if (threadIdx.x == 0) rq_s = 1.0 / __dsqrt_rn((double)f[0]);
+        __syncthreads();
+        rq = rq_s;
+    }
     const int slice = blockIdx.x * (kSellThreads / kSliceRows) + warp;
     const int row = slice * kSliceRows + lane;
     T sum = T(0);
@@ -716,7 +736,7 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
         if (k < w) s0 += ld_stream(vv + kSliceRows * k) * x[ld_stream(cc + kSliceRows * k)];
         sum = s0 + s1;
     }
-    double contrib = 0.0;
+    double contrib = 0.0, contrib2 = 0.0;
     if (row < n) {
         if (MODE == MODE_Y) {
             y[row] = sum;
@@ -727,10 +747,48 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
             T dn = c1 * d[row] + c2 * (aux[row] * r);
             d[row] = dn;
             y[row] = x[row] + dn;
+        } else if (MODE == MODE_POWER) {
+            const double yi = ((double)sum * (double)aux[row]) * rq;
+            y[row] = (T)yi;
+            contrib = (double)x[row] * yi;
+            contrib2 = yi * yi;
         } else {
             y[row] = sum;
             contrib = (double)x[row] * (double)sum;
         }
+    }
+    if (MODE == MODE_POWER) {
+        // CSR block b = rows 128 b .. 128 b + 127 = this block's warps 4 hh .. 4 hh + 3 (rows of
+        // the CSR block's warp w' on its lanes, in order); the CSR block's warps 4-7 hold zeros
+        __shared__ double q1[kSellThreads / 32], q2[kSellThreads / 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            contrib += __shfl_down_sync(kAll, contrib, o);
+            contrib2 += __shfl_down_sync(kAll, contrib2, o);
+        }
+        if (lane == 0) {
+            q1[warp] = contrib;
+            q2[warp] = contrib2;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int part = 2 * blockIdx.x + threadIdx.x;
+            if (part < nparts) {
+                double t1 = 0.0, t2 = 0.0;
+                for (int w = 0; w < 4; ++w) {
+                    t1 += q1[4 * threadIdx.x + w];
+                    t2 += q2[4 * threadIdx.x + w];
+                }
+                for (int w = 4; w < kSpmvThreads / 32; ++w) {
+                    t1 += 0.0;
+                    t2 += 0.0;
+                }
+                partial[part] = t1;
+                partial[nparts + part] = t2;
+            }
+        }
+        last_block_total2(partial, nparts, counter, result, (double *)d, rq, (int)gridDim.x);
+        return;
     }
     if (MODE == MODE_DOT) {
         // CSR block b covers rows 128 b .. 128 b + 127, its warp w rows 16 w .. 16 w + 15 with
@@ -798,11 +856,13 @@ const float *sell_values<float>(const SpmvPlan &pl) { return pl.sv32; }
 
 template <typename T, int MODE>
 cudaError_t launch_sell(const SpmvPlan &pl, int n, const T *sv, const T *x, T *y, const T *f, const T *aux, T *d,
-                        T c1, T c2, double *partial, cudaStream_t s)
+                        T c1, T c2, double *partial, cudaStream_t s, double *result = nullptr,
+                        unsigned *counter = nullptr)
 {
     const int blocks = (pl.ns + kSellThreads / kSliceRows - 1) / (kSellThreads / kSliceRows);
     spmv_sell_kernel<T, MODE><<<blocks, kSellThreads, 0, s>>>(n, pl.sp, pl.sw, pl.sci, sv, x, y, f, aux, d, c1, c2,
-                                                              partial, spmv_blocks(n, 2)); note_launch();
+                                                              partial, spmv_blocks(n, 2), result, counter);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -843,10 +903,11 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
                       double *result = nullptr, unsigned *counter = nullptr)
 {
     if (n == 0) return cudaSuccess;
-    if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr)) &&
+    if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr) ||
+         MODE == MODE_POWER) &&
         pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 && pl.split == nullptr) {
         const T *sv = sell_values<T>(pl);
-        if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s);
+        if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s, result, counter);
     }
     int long_len = 0x7fffffff;
     const int *split = nullptr;
@@ -918,13 +979,13 @@ cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D
                                             s, result, counter);
 }
 
-// one sweep of the power method on D^-1 A from the unnormalised x with *xx = x . x:
-// y = (D^-1 A x) / sqrt(xx), *lambda = (x . y) / sqrt(xx) (the Rayleigh quotient of the unit
-// vector), *yy = y . y.  partial holds 2 x the plan's blocks.
-cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, const double *xx,
+// one sweep of the power method on D^-1 A (invD = D^-1) from the unnormalised x with
+// *xx = x . x: y = (D^-1 A x) / sqrt(xx), *lambda = (x . y) / sqrt(xx) (the Rayleigh quotient of
+// the unit vector), *yy = y . y.  partial holds 2 x the plan's blocks.
+cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *invD, const double *x, const double *xx,
                        double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s)
 {
-    return spmv_mode<double, MODE_POWER>(pl, A.n, A.rp, A.ci, A.v, x, y, xx, D, yy, 0.0, 0.0, partial, s, lambda,
+    return spmv_mode<double, MODE_POWER>(pl, A.n, A.rp, A.ci, A.v, x, y, xx, invD, yy, 0.0, 0.0, partial, s, lambda,
                                          counter);
 }
 

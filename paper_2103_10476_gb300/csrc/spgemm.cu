@@ -9,6 +9,7 @@
 // Rows are binned by table size so each launch uses one size: the symbolic phase by an
 // upper bound (min(products, columns)), the numeric phase by the exact count.
 #include <algorithm>
+#include <functional>
 #include <mutex>
 #include <stdio.h>
 #include <string>
@@ -23,8 +24,10 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kMinTable = 32;
 constexpr int kMaxSharedSym = 8192;     // symbolic: 4 bytes per slot
 constexpr int kMaxSharedNum = 4096;     // numeric: 12 bytes per slot
-constexpr int kNumBins = 10;            // 32 .. 8192 and the global bin
-constexpr int kGlobalBin = kNumBins - 1;
+constexpr int kNumBins = 11;            // 32 .. 8192, the global bin and the segmented rows
+constexpr int kGlobalBin = 9;
+constexpr int kSegBin = 10;             // numeric phase: rows of A of more than kSegLen entries
+constexpr int kSegLen = 256;
 constexpr int kSmemBudget = 96 * 1024;
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
@@ -108,16 +111,26 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
     bin_count_block(b, i < n, binCount);
 }
 
-__global__ void exact_bin_kernel(int n, const int *crp, int *bin, int *binCount, int *tsize)
+// numeric bins by the exact row counts; rows of A with more than kSegLen entries go to kSegBin
+// (*segmax: the longest of them)
+__global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin, int *binCount, int *tsize,
+                                 int *segmax)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = 0;
     if (i < n) {
-        int64_t cnt = crp[i + 1] - crp[i];
-        int S = table_for(cnt);
-        b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
+        const int alen = arp[i + 1] - arp[i];
+        if (alen > kSegLen) {
+            b = kSegBin;
+            tsize[i] = 0;
+            atomicMax(segmax, alen);
+        } else {
+            int64_t cnt = crp[i + 1] - crp[i];
+            int S = table_for(cnt);
+            b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
+            tsize[i] = S;
+        }
         bin[i] = b;
-        tsize[i] = S;
     }
     bin_count_block(b, i < n, binCount);
 }
@@ -833,6 +846,189 @@ __global__ void __launch_bounds__(256) chain_kernel(int nnz, const int *off, con
     }
 }
 
+// ------------------------------------------------------------------------------------ segmented rows
+// Rows of A with more than kSegLen stored entries (stalled coarse levels hold rows of thousands)
+// follow the segmented reading of the sums: the row's positions fall in segments of kSegLen;
+// c_ij is summed with fma over each segment's terms in ascending k from 0, and the sums of all
+// the row's segments (0 where a segment has no term for j) are added in segment order.  The
+// segments are independent, so a block per (row, segment) forms its segment's sums: the
+// segment's rows of B staged in shared memory, then one k after another (a barrier per k) into
+// an accumulator over B's columns in shared memory (over the row's entries in a scratch slice,
+// found by binary search, when B has more than kSegCols columns); the sums go to a scratch
+// array, and one pass adds each entry's segment sums in order.  The row's columns come from a
+// flag array over B's columns, one block per row.
+constexpr int kSegCols = 8192;          // B columns of the shared accumulator (64 KB)
+constexpr int kSegStage = 6144;         // staged entries of B per pass (72 KB)
+constexpr int kSegThreads = 512;
+
+// size[r] = segments x entries of segmented row r (its scratch slice)
+__global__ void seg_size_kernel(int cnt, const int *rows, const int *arp, const int *crp, int *size)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= cnt) return;
+    const int i = rows[r];
+    const int nseg = (arp[i + 1] - arp[i] + kSegLen - 1) / kSegLen;
+    size[r] = nseg * (crp[i + 1] - crp[i]);
+}
+
+// C's sorted columns of segmented row r = blockIdx.x (flags over B's columns: shared memory, or
+// the block's slice of gflags); *ovf += 1 when the count differs from the symbolic phase's
+__global__ void __launch_bounds__(kSegThreads) seg_pattern_kernel(int cnt, const int *rows, const int *arp,
+                                                                   const int *aci, const int *brp, const int *bci,
+                                                                   int ncolB, const int *crp, int *cci, int *ovf,
+                                                                   int *gflags)
+{
+    extern __shared__ int seg_flag_s[];
+    __shared__ int wsum[kSegThreads / 32];
+    __shared__ int base_s;
+    if ((int)blockIdx.x >= cnt) return;
+    int *flag = gflags ? gflags + (size_t)blockIdx.x * (size_t)ncolB : seg_flag_s;
+    const int i = rows[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = threadIdx.x; j < ncolB; j += blockDim.x) flag[j] = 0;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    for (int e = arp[i] + warp; e < arp[i + 1]; e += nw) {
+        const int k = aci[e];
+        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) flag[bci[f]] = 1;
+    }
+    __syncthreads();
+    const int out0 = crp[i], nc = crp[i + 1] - out0;
+    for (int j0 = 0; j0 < ncolB; j0 += blockDim.x) {
+        const int j = j0 + (int)threadIdx.x;
+        const int fl = j < ncolB ? flag[j] : 0;
+        const unsigned m = __ballot_sync(kFullMask, fl);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int p = base_s + __popc(m & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) p += wsum[w];
+        if (fl && p < nc) cci[out0 + p] = j;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < nw; ++w) t += wsum[w];
+            base_s += t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && base_s != nc) atomicAdd(ovf, 1);
+}
+
+// position of column j among the n sorted columns c (present by construction)
+__device__ __forceinline__ int seg_find(const int *c, int n, int j)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (c[mid] < j) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// segment q = blockIdx.y of segmented row r = blockIdx.x: S[soff[r] + q nc + t] = the sum over
+// the segment's terms of entry t, fma in ascending k from 0 (DENSE: accumulator over B's
+// columns in shared memory; else in the scratch slice itself, positions by binary search)
+template <bool DENSE>
+__global__ void __launch_bounds__(kSegThreads) seg_numeric_kernel(int cnt, const int *rows, const int *arp,
+                                                                   const int *aci, const double *av, const int *brp,
+                                                                   const int *bci, const double *bv, const int *crp,
+                                                                   const int *cci, const int *soff, double *S)
+{
+    extern __shared__ __align__(16) unsigned char seg_num_s[];
+    __shared__ int sk[kSegLen], spre[kSegLen + 1];
+    __shared__ double sa[kSegLen];
+    __shared__ int chunk_end;
+    const int r = blockIdx.x, q = blockIdx.y;
+    if (r >= cnt) return;
+    const int i = rows[r];
+    const int a0 = arp[i], alen = arp[i + 1] - a0;
+    const int nseg = (alen + kSegLen - 1) / kSegLen;
+    const int out0 = crp[i], nc = crp[i + 1] - out0;
+    if (q >= nseg || nc == 0) return;
+    double *slice = S + soff[r] + (size_t)q * (size_t)nc;
+    double *acc = DENSE ? (double *)seg_num_s : slice;
+    int *scol = (int *)(seg_num_s + (DENSE ? sizeof(double) * kSegCols : 0));
+    double *sval = (double *)(scol + kSegStage);
+    const int *rc = cci + out0;
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        if (DENSE) acc[rc[t]] = 0.0;
+        else acc[t] = 0.0;
+    }
+    const int m = min(kSegLen, alen - q * kSegLen);
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        const int k = aci[a0 + q * kSegLen + t];
+        sk[t] = k;
+        sa[t] = av[a0 + q * kSegLen + t];
+        spre[t + 1] = brp[k + 1] - brp[k];
+    }
+    if (threadIdx.x == 0) spre[0] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int t = 0; t < m; ++t) spre[t + 1] += spre[t];
+    __syncthreads();
+    int kk = 0;
+    while (kk < m) {
+        // the next k's whose rows of B fit the stage together (at least one)
+        if (threadIdx.x == 0) {
+            int ke = kk + 1;
+            while (ke < m && spre[ke + 1] - spre[kk] <= kSegStage) ++ke;
+            chunk_end = ke;
+        }
+        __syncthreads();
+        const int ke = chunk_end;
+        const int base = spre[kk], total = spre[ke] - base;
+        const bool staged = total <= kSegStage;
+        if (staged) {
+            for (int p = threadIdx.x; p < total; p += blockDim.x) {
+                // the k of staged entry p: the last t in [kk, ke) with spre[t] - base <= p
+                int lo = kk, hi = ke - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (spre[mid] - base <= p) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int f = brp[sk[lo]] + (p - (spre[lo] - base));
+                scol[p] = bci[f];
+                sval[p] = bv[f];
+            }
+            __syncthreads();
+        }
+        for (int t = kk; t < ke; ++t) {
+            const double a = sa[t];
+            const int len = spre[t + 1] - spre[t];
+            const int fb = brp[sk[t]];
+            for (int u = threadIdx.x; u < len; u += blockDim.x) {
+                const int j = staged ? scol[spre[t] - base + u] : bci[fb + u];
+                const double b = staged ? sval[spre[t] - base + u] : bv[fb + u];
+                const int pos = DENSE ? j : seg_find(rc, nc, j);
+                acc[pos] = __fma_rn(a, b, acc[pos]);
+            }
+            __syncthreads();
+        }
+        kk = ke;
+    }
+    if (DENSE)
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) slice[t] = acc[rc[t]];
+}
+
+// C's values of segmented row r = blockIdx.x: each entry's segment sums added in order
+__global__ void seg_combine_kernel(int cnt, const int *rows, const int *arp, const int *crp, const int *soff,
+                                   const double *S, double *cv)
+{
+    const int r = blockIdx.x;
+    if (r >= cnt) return;
+    const int i = rows[r];
+    const int nseg = (arp[i + 1] - arp[i] + kSegLen - 1) / kSegLen;
+    const int out0 = crp[i], nc = crp[i + 1] - out0;
+    const double *sl = S + soff[r];
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+        double c = sl[t];
+        for (int q = 1; q < nseg; ++q) c = c + sl[(size_t)q * nc + t];
+        cv[out0 + t] = c;
+    }
+}
+
 // 64-bit sum of n non-negative ints (a total an int32 scan is about to form)
 __global__ void sum64_kernel(const int *v, int n, unsigned long long *out)
 {
@@ -1054,6 +1250,8 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
             if ((e = cudaGetLastError())) break;
         }
         if ((e = cudaMallocAsync(&off, sizeof(int) * ((size_t)nnz + 1), s))) break;
+        // zero: the segmented rows' entries get no terms here (their own path fills them)
+        if ((e = cudaMemsetAsync(off, 0, sizeof(int) * ((size_t)nnz + 1), s))) break;
         if ((e = cudaMallocAsync(&run, sizeof(int) * (size_t)nnz, s))) break;
         if ((e = cudaMallocAsync(&d_sum, sizeof(unsigned long long), s))) break;
         if ((e = cudaMemsetAsync(run, 0, sizeof(int) * (size_t)nnz, s))) break;
@@ -1099,9 +1297,11 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
                 off, run, sa, sb); note_launch();
             if ((e = cudaGetLastError())) break;
         }
-        place_kernel<<<grid_for((int64_t)n * 32, 128), 128, 0, s>>>(n, d_perm, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp,
-                                                                   C.ci, off, run, sa, sb,
-                                                                   dense_rows ? kMaxSharedNum / 2 : 0x7fffffff);
+        // every row but the segmented ones (the last of the bins' order)
+        const int nplace = n - hb.count[kSegBin];
+        place_kernel<<<grid_for((int64_t)nplace * 32, 128), 128, 0, s>>>(nplace, d_perm, A.rp, A.ci, A.v, B.rp, B.ci,
+                                                                        B.v, C.rp, C.ci, off, run, sa, sb,
+                                                                        dense_rows ? kMaxSharedNum / 2 : 0x7fffffff);
         note_launch();
         if ((e = cudaGetLastError())) break;
         const int64_t warps = ((int64_t)nnz + kChainOutputs - 1) / kChainOutputs;
@@ -1132,6 +1332,89 @@ cudaError_t numeric_chains(int n, const DevCsr &A, const DevCsr &B, DevCsr &C, c
     return e;
 }
 
+cudaError_t seg_attr()
+{
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(seg_pattern_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kDenseCols * (int)sizeof(int));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(seg_numeric_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(sizeof(double) * kSegCols + 12 * kSegStage));
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(seg_numeric_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        12 * kSegStage);
+    });
+    return attr;
+}
+
+// Device scratch for the segmented rows: take(bytes) gives memory (nullptr when there is none
+// left), give(p) returns it.
+struct SegScratch {
+    std::function<void *(size_t)> take;
+    std::function<void(void *)> give;
+};
+
+// C's columns and values of the rows of A with more than kSegLen entries (rows[0, cnt), the
+// longest segmax entries).  *no_room: the scratch could not hold the segment sums (C untouched).
+cudaError_t numeric_segmented(const DevCsr &A, const DevCsr &B, DevCsr &C, const int *rows, int cnt, int segmax,
+                              int *d_ovf, const SegScratch &sc, bool *no_room, cudaStream_t s)
+{
+    *no_room = false;
+    if (cnt == 0) return cudaSuccess;
+    if ((segmax + kSegLen - 1) / kSegLen > 65535) {     // segments beyond the grid's y extent
+        *no_room = true;
+        return cudaSuccess;
+    }
+    AMG_CUDA_TRY(seg_attr());
+    int *soff = nullptr, *gflags = nullptr, *ws = nullptr;
+    unsigned long long *d_sum = nullptr;
+    double *S = nullptr;
+    cudaError_t e = cudaSuccess;
+    do {
+        soff = (int *)sc.take(sizeof(int) * ((size_t)cnt + 1));
+        d_sum = (unsigned long long *)sc.take(sizeof(unsigned long long));
+        if (!soff || !d_sum) { *no_room = true; break; }
+        if ((e = cudaMemsetAsync(d_sum, 0, sizeof(unsigned long long), s))) break;
+        seg_size_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, rows, A.rp, C.rp, soff); note_launch();
+        sum64_kernel<<<grid_for(cnt, 256, 1024), 256, 0, s>>>(soff, cnt, d_sum); note_launch();
+        if ((e = cudaGetLastError())) break;
+        unsigned long long total = 0;
+        if ((e = cudaMemcpyAsync(&total, d_sum, sizeof total, cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaStreamSynchronize(s))) break;
+        if (total > 0x7ffffff0ull) { *no_room = true; break; }
+        ws = (int *)sc.take(sizeof(int) * (scan_ws_ints(cnt + 1) + 16));
+        if (!ws) { *no_room = true; break; }
+        if ((e = scan_exclusive_ws(soff, soff, cnt, ws, s))) break;
+        S = (double *)sc.take(sizeof(double) * ((size_t)total + 1));
+        if (!S) { *no_room = true; break; }
+        if (B.ncol > kDenseCols) {
+            gflags = (int *)sc.take(sizeof(int) * (size_t)B.ncol * (size_t)cnt);
+            if (!gflags) { *no_room = true; break; }
+        }
+        const size_t psmem = gflags ? 0 : sizeof(int) * (size_t)B.ncol;
+        seg_pattern_kernel<<<cnt, kSegThreads, psmem, s>>>(cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp, C.ci, d_ovf,
+                                                            gflags); note_launch();
+        const dim3 grid(cnt, (segmax + kSegLen - 1) / kSegLen);
+        if (B.ncol <= kSegCols) {
+            seg_numeric_kernel<true><<<grid, kSegThreads, sizeof(double) * kSegCols + 12 * kSegStage, s>>>(
+                cnt, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, soff, S); note_launch();
+        } else {
+            seg_numeric_kernel<false><<<grid, kSegThreads, 12 * kSegStage, s>>>(
+                cnt, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, soff, S); note_launch();
+        }
+        seg_combine_kernel<<<cnt, 256, 0, s>>>(cnt, rows, A.rp, C.rp, soff, S, C.v); note_launch();
+        e = cudaGetLastError();
+    } while (0);
+    if (ws) sc.give(ws);
+    if (gflags) sc.give(gflags);
+    if (S) sc.give(S);
+    if (d_sum) sc.give(d_sum);
+    if (soff) sc.give(soff);
+    return e;
+}
+
 }  // namespace
 
 cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_host, cudaStream_t s)
@@ -1146,12 +1429,12 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         AMG_CUDA_TRY(cudaMemsetAsync(C.rp, 0, sizeof(int), s));
         return cudaSuccess;
     }
-    int *work = nullptr;   // bin[n] tsize[n] perm[n] binCount binFill binStart overflow
-    const size_t nwork = (size_t)3 * n + 3 * (kNumBins + 1) + 1;
+    int *work = nullptr;   // bin[n] tsize[n] perm[n] binCount binFill binStart overflow segmax
+    const size_t nwork = (size_t)3 * n + 3 * (kNumBins + 1) + 2;
     AMG_CUDA_TRY(cudaMallocAsync(&work, sizeof(int) * nwork, s));
     int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
     int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
-    int *d_ovf = d_binStart + kNumBins + 1;
+    int *d_ovf = d_binStart + kNumBins + 1, *d_segmax = d_ovf + 1;
     unsigned long long *d_ubstats = nullptr, h_ubstats[2] = {0, 0};
     cudaError_t e = cudaMallocAsync(&d_ubstats, 2 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
@@ -1203,9 +1486,13 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         // 16 elements of padding: bulk copies of row ranges widen to 16-byte boundaries
         if ((e = cudaMallocAsync(&C.ci, sizeof(int) * ((size_t)nnz + 16), s))) break;
         if ((e = cudaMallocAsync(&C.v, sizeof(double) * ((size_t)nnz + 16), s))) break;
-        // numeric, binned by the exact row counts
+        // numeric, binned by the exact row counts (rows of A of more than kSegLen entries apart)
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
-        exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
+        if ((e = cudaMemsetAsync(d_segmax, 0, sizeof(int), s))) break;
+        exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_segmax);
+        note_launch();
+        int h_segmax = 0;
+        if ((e = cudaMemcpyAsync(&h_segmax, d_segmax, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
         if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
         // Products with rows of more than 2048 entries (stalled coarse levels): pattern, chain
         // placement and chain sums (see "numeric by chains" above).  Otherwise numeric_row, whose
@@ -1233,6 +1520,23 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
             numeric_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
                 cnt, rows, toff, d_tsize, gkeys, gvals, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, C.v, d_ovf); note_launch();
             if ((e = cudaGetLastError())) break;
+        }
+        if (hb.count[kSegBin]) {
+            SegScratch sc;
+            sc.take = [s](size_t bytes) -> void * {
+                void *p = nullptr;
+                return cudaMallocAsync(&p, bytes, s) == cudaSuccess ? p : nullptr;
+            };
+            sc.give = [s](void *p) { cudaFreeAsync(p, s); };
+            bool no_room = false;
+            if ((e = numeric_segmented(A, B, C, d_perm + hb.start[kSegBin], hb.count[kSegBin], h_segmax, d_ovf, sc,
+                                       &no_room, s)))
+                break;
+            if (no_room) {
+                cudaGetLastError();
+                e = cudaErrorMemoryAllocation;
+                break;
+            }
         }
         if ((e = cudaMemcpyAsync(overflow_host, d_ovf, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
         if ((e = cudaStreamSynchronize(s))) break;
@@ -1466,10 +1770,15 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
     if ((int64_t)nnz64 > capacity) return stop(2, "amg_spgemm_noalloc: output capacity smaller than nnz(C)");
     AMG_CUDA_TRY(scan_exclusive_ws(C.rp, C.rp, n, scan_ws, s));
     C.nnz = (int)nnz64;
-    // numeric, binned by the exact row counts
+    // numeric, binned by the exact row counts (rows of A of more than kSegLen entries apart;
+    // d_flags[3] holds the longest of them)
     AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
-    exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_bin, d_binCount, d_tsize); note_launch();
+    AMG_CUDA_TRY(cudaMemsetAsync(d_flags + 3, 0, sizeof(int), s));
+    exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_flags + 3);
+    note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
+    int h_segmax = 0;
+    AMG_CUDA_TRY(cudaMemcpyAsync(&h_segmax, d_flags + 3, sizeof(int), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s));
     for (int b = 0; b < kGlobalBin; ++b)
         if (hb.count[b]) AMG_CUDA_TRY(numeric_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C, d_flags + 1, s));
@@ -1485,6 +1794,15 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
                                                                               gvals, A.rp, A.ci, A.v, B.rp, B.ci, B.v,
                                                                               C.rp, C.ci, C.v, d_flags + 1); note_launch();
         AMG_CUDA_TRY(cudaGetLastError());
+    }
+    if (hb.count[kSegBin]) {
+        SegScratch sc;
+        sc.take = [&ar](size_t bytes) -> void * { return ar.take<unsigned char>(bytes); };
+        sc.give = [](void *) {};
+        bool no_room = false;
+        AMG_CUDA_TRY(numeric_segmented(A, B, C, d_perm + hb.start[kSegBin], hb.count[kSegBin], h_segmax, d_flags + 1,
+                                       sc, &no_room, s));
+        if (no_room) return stop(1, "amg_spgemm_noalloc: the segment sums of long rows do not fit in the scratch");
     }
     AMG_CUDA_TRY(convert_rowptr_to64(C.rp, crp64, n + 1, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(hflags, d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
