@@ -111,22 +111,23 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
     bin_count_block(b, i < n, binCount);
 }
 
-// numeric bins by the exact row counts; rows of A with more than kSegLen entries go to kSegBin
-// (*segmax: the longest of them)
+// numeric bins by the exact row counts.  kSegBin takes the rows of A with more than kSegLen
+// entries and, with seg_wide (B narrow enough for the segment kernels' dense accumulator), the
+// rows too long for a shared-memory table as well (*segmax: the longest row of A among them).
 __global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin, int *binCount, int *tsize,
-                                 int *segmax)
+                                 int *segmax, int seg_wide)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = 0;
     if (i < n) {
         const int alen = arp[i + 1] - arp[i];
-        if (alen > kSegLen) {
+        const int64_t cnt = crp[i + 1] - crp[i];
+        const int S = table_for(cnt);
+        if (alen > kSegLen || (seg_wide && S > kMaxSharedNum)) {
             b = kSegBin;
             tsize[i] = 0;
             atomicMax(segmax, alen);
         } else {
-            int64_t cnt = crp[i + 1] - crp[i];
-            int S = table_for(cnt);
             b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
             tsize[i] = S;
         }
@@ -856,7 +857,10 @@ __global__ void __launch_bounds__(256) chain_kernel(int nnz, const int *off, con
 // an accumulator over B's columns in shared memory (over the row's entries in a scratch slice,
 // found by binary search, when B has more than kSegCols columns); the sums go to a scratch
 // array, and one pass adds each entry's segment sums in order.  The row's columns come from a
-// flag array over B's columns, one block per row.
+// flag array over B's columns, one block per row.  When B has at most kSegCols columns, the rows
+// of C too long for a shared-memory hash table (rows of A of at most kSegLen entries: a single
+// segment, the plain ascending-k sums) take this path as well: a k at a time into the dense
+// accumulator instead of a global hash table or a walk of every column of B.
 constexpr int kSegCols = 8192;          // B columns of the shared accumulator (64 KB)
 constexpr int kSegStage = 6144;         // staged entries of B per pass (72 KB)
 constexpr int kSegThreads = 512;
@@ -1396,7 +1400,7 @@ cudaError_t numeric_segmented(const DevCsr &A, const DevCsr &B, DevCsr &C, const
         const size_t psmem = gflags ? 0 : sizeof(int) * (size_t)B.ncol;
         seg_pattern_kernel<<<cnt, kSegThreads, psmem, s>>>(cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp, C.ci, d_ovf,
                                                             gflags); note_launch();
-        const dim3 grid(cnt, (segmax + kSegLen - 1) / kSegLen);
+        const dim3 grid(cnt, std::max(1, (segmax + kSegLen - 1) / kSegLen));
         if (B.ncol <= kSegCols) {
             seg_numeric_kernel<true><<<grid, kSegThreads, sizeof(double) * kSegCols + 12 * kSegStage, s>>>(
                 cnt, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, soff, S); note_launch();
@@ -1489,7 +1493,8 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         // numeric, binned by the exact row counts (rows of A of more than kSegLen entries apart)
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_segmax, 0, sizeof(int), s))) break;
-        exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_segmax);
+        exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_segmax,
+                                                          B.ncol <= kSegCols ? 1 : 0);
         note_launch();
         int h_segmax = 0;
         if ((e = cudaMemcpyAsync(&h_segmax, d_segmax, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
@@ -1774,7 +1779,8 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
     // d_flags[3] holds the longest of them)
     AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
     AMG_CUDA_TRY(cudaMemsetAsync(d_flags + 3, 0, sizeof(int), s));
-    exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_flags + 3);
+    exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_flags + 3,
+                                                      B.ncol <= kSegCols ? 1 : 0);
     note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     int h_segmax = 0;
