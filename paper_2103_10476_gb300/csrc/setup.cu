@@ -338,8 +338,11 @@ __global__ void mis_decide_kernel(int n, const int *grp, const int *gci, const u
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
     const bool valid = i < n;
     int und = 0;
-    unsigned long long m = (valid && sub == 0) ? t1[i] : 0ULL;
-    if (valid) {
+    // a decided vertex (root or out) never changes again: no need for its neighbourhood
+    const unsigned long long own0 = valid ? t0[i] : 0ULL;
+    const bool open = valid && (own0 >> 62) == 1ULL;
+    unsigned long long m = (open && sub == 0) ? t1[i] : 0ULL;
+    if (open) {
         for (int e = grp[i] + sub; e < grp[i + 1]; e += 8) {
             unsigned long long t = t1[gci[e]];
             m = t > m ? t : m;
@@ -350,13 +353,11 @@ __global__ void mis_decide_kernel(int n, const int *grp, const int *gci, const u
         unsigned long long t = __shfl_down_sync(kFull, m, o, 8);
         m = t > m ? t : m;
     }
-    if (valid && sub == 0) {
-        unsigned long long own = t0[i];
-        if ((own >> 62) == 1ULL) {
-            if (m == own) t0[i] = kStRoot | (own & kPrioMask);
-            else if ((m >> 62) == 2ULL) t0[i] = own & kPrioMask;
-            else und = 1;
-        }
+    if (open && sub == 0) {
+        const unsigned long long own = own0;
+        if (m == own) t0[i] = kStRoot | (own & kPrioMask);
+        else if ((m >> 62) == 2ULL) t0[i] = own & kPrioMask;
+        else und = 1;
     }
     // block-level count of still-undecided vertices
     __shared__ int cnt;

@@ -77,20 +77,42 @@ __device__ __forceinline__ void bin_count_block(int b, bool valid, int *binCount
     if (threadIdx.x < kNumBins && hist[threadIdx.x]) atomicAdd(&binCount[threadIdx.x], hist[threadIdx.x]);
 }
 
-// (ubstats, when given: [0] the most products of a row, [1] all products, warp-reduced first)
+// Row i's product count (an upper bound of its entries), one thread per row; a row of more than
+// 64 entries (stalled levels hold rows of thousands) is counted by its whole warp instead, the
+// warp taking its long rows one after another.  (ubstats, when given: [0] the most products of a
+// row, [1] all products, warp-reduced first.)
 __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
                           int *tsize, unsigned long long *ubstats = nullptr)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int b = 0;
-    int64_t ub = 0;
-    if (i < n) {
-        for (int e = arp[i]; e < arp[i + 1]; ++e) {
-            int k = aci[e];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const bool valid = i < n;
+    const int r0 = valid ? arp[i] : 0, r1 = valid ? arp[i + 1] : 0;
+    const bool longrow = r1 - r0 > 64;
+    long long ub = 0;
+    if (valid && !longrow)
+        for (int e = r0; e < r1; ++e) {
+            const int k = aci[e];
             ub += brp[k + 1] - brp[k];
         }
-        int64_t need = ub < ncolB ? ub : ncolB;
-        int S = table_for(need);
+    unsigned m = __ballot_sync(kFullMask, longrow);
+    while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int sb = __shfl_sync(kFullMask, r0, src), se = __shfl_sync(kFullMask, r1, src);
+        long long part = 0;
+        for (int e = sb + lane; e < se; e += 32) {
+            const int k = aci[e];
+            part += brp[k + 1] - brp[k];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFullMask, part, o);
+        if (lane == src) ub = part;
+    }
+    int b = 0;
+    if (valid) {
+        const int64_t need = ub < ncolB ? ub : ncolB;
+        const int S = table_for(need);
         b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
         bin[i] = b;
         tsize[i] = S;
@@ -103,12 +125,12 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
             mx = y > mx ? y : mx;
             sm += __shfl_xor_sync(kFullMask, sm, o);
         }
-        if ((threadIdx.x & 31) == 0 && sm) {
+        if (lane == 0 && sm) {
             atomicMax(&ubstats[0], mx);
             atomicAdd(&ubstats[1], sm);
         }
     }
-    bin_count_block(b, i < n, binCount);
+    bin_count_block(b, valid, binCount);
 }
 
 // numeric bins by the exact row counts.  kSegBin takes the rows of A with more than kSegLen
@@ -404,10 +426,44 @@ __global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff,
 // more than 2048 entries count their columns in a dense array in shared memory (one block
 // per row) when B has at most kDenseCols columns, instead of one warp on a global hash table.
 constexpr int kDenseCols = 49152;          // 192 KB of int counters in shared memory
-constexpr int kDenseThreads = 512;
 constexpr int kChainOutputs = 256;         // entries of C per warp of the chain pass
 constexpr int kChainProducts = 32768;      // rows with more products take the chain path ...
 constexpr long long kChainTotal = 16 << 20;  // ... when the whole product has at most this many
+
+// visit(j) for the column of every product of row i, block-wide, in no particular order: one
+// thread per entry of A's row walks a row of B of up to 32 entries; the longer rows of B (a
+// stalled level's dense rows) are deferred to whole warps, so no thread walks a long chain of
+// dependent loads alone.  blockDim.x <= kDenseThreads.
+constexpr int kDenseThreads = 512;
+template <typename F>
+__device__ __forceinline__ void row_products(int i, const int *arp, const int *aci, const int *brp, const int *bci,
+                                             F visit)
+{
+    __shared__ int dk[kDenseThreads];
+    __shared__ int nd;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ae = arp[i + 1];
+    for (int e0 = arp[i]; e0 < ae; e0 += blockDim.x) {
+        if (threadIdx.x == 0) nd = 0;
+        __syncthreads();
+        const int e = e0 + (int)threadIdx.x;
+        if (e < ae) {
+            const int k = aci[e];
+            const int b0 = brp[k], b1 = brp[k + 1];
+            if (b1 - b0 <= 32) {
+                for (int f = b0; f < b1; ++f) visit(bci[f]);
+            } else {
+                dk[atomicAdd(&nd, 1)] = k;
+            }
+        }
+        __syncthreads();
+        for (int d = warp; d < nd; d += nw) {
+            const int k = dk[d];
+            for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) visit(bci[f]);
+        }
+        __syncthreads();
+    }
+}
 
 // counts[ncolB] of row i's products per column (block-wide, any order)
 __device__ __forceinline__ void dense_count_row(int i, const int *arp, const int *aci, const int *brp, const int *bci,
@@ -415,12 +471,7 @@ __device__ __forceinline__ void dense_count_row(int i, const int *arp, const int
 {
     for (int j = threadIdx.x; j < ncolB; j += blockDim.x) cnt[j] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int e = arp[i] + warp; e < arp[i + 1]; e += nw) {
-        const int k = aci[e];
-        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) atomicAdd(&cnt[bci[f]], 1);
-    }
-    __syncthreads();
+    row_products(i, arp, aci, brp, bci, [cnt](int j) { atomicAdd(&cnt[j], 1); });
 }
 
 __global__ void __launch_bounds__(kDenseThreads) dense_symbolic_kernel(int cnt_rows, const int *rows, const int *arp,
@@ -892,11 +943,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_pattern_kernel(int cnt, const
     for (int j = threadIdx.x; j < ncolB; j += blockDim.x) flag[j] = 0;
     if (threadIdx.x == 0) base_s = 0;
     __syncthreads();
-    for (int e = arp[i] + warp; e < arp[i + 1]; e += nw) {
-        const int k = aci[e];
-        for (int f = brp[k] + lane; f < brp[k + 1]; f += 32) flag[bci[f]] = 1;
-    }
-    __syncthreads();
+    row_products(i, arp, aci, brp, bci, [flag](int j) { flag[j] = 1; });
     const int out0 = crp[i], nc = crp[i + 1] - out0;
     for (int j0 = 0; j0 < ncolB; j0 += blockDim.x) {
         const int j = j0 + (int)threadIdx.x;
@@ -1746,7 +1793,8 @@ cudaError_t spgemm_noalloc(int nA, int ncolA, const int64_t *arp64, const int *a
     };
     // symbolic
     AMG_CUDA_TRY(cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s));
-    ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize); note_launch();
+    ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize);
+    note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     AMG_CUDA_TRY(make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s));
     for (int b = 0; b < kGlobalBin; ++b)
