@@ -198,6 +198,20 @@ cudaError_t coarse_inverse(const DevCsr &A, void *work, double *inv, int *info_d
 // and skipped by the row-tile kernel, whose lanes would otherwise walk it as one serial chain.
 // The list travels by value in the kernel's parameters (no device memory of its own).
 constexpr int kMaxLongRows = 128;
+// Rows split off the row tiles of the solve's products, as the kernels take them (by value).
+// rows lists first the rows of more than kSegRowLen entries, summed in segments of kSegRowLen
+// entries by a block each (the last block of a row to finish adds the segments' sums in order),
+// then the rows of more than kBlockRowLen entries (a block each), then the rest (a warp each).
+constexpr int kSegRowLen = 1024;
+constexpr int kBlockRowLen = 128;
+struct SplitRows {
+    const int *rows = nullptr;
+    int nseg_rows = 0, nblock = 0, nwarp = 0;
+    int nsegb = 0;               // segment blocks of the segmented rows
+    const int *seg = nullptr;    // per segment block: row, first entry, end, its row's first segment block, count
+    double *part = nullptr;      // per segment block: its sum
+    unsigned *tick = nullptr;    // per segmented row (at its first segment block): blocks finished
+};
 struct LongRows {
     int count = 0;               // rows listed
     int len = 0x7fffffff;        // rows with more entries than this are long
@@ -214,14 +228,12 @@ struct SpmvPlan {
     const double *sv64 = nullptr;
     const float *sv32 = nullptr;
     size_t sell_entries = 0;     // stored entries of the copy, padding included
-    // rows split off the row tiles for the solve's products (a device list owned by the
-    // hierarchy; split = nullptr: none).  Every row with more than split_len entries is listed:
-    // the first split_long (more than kSplitBlockLen entries) are summed by a block each, the
-    // next split_mid by a warp each.  When present it supersedes lr.
-    const int *split = nullptr;
-    int split_len = 0x7fffffff, split_long = 0, split_mid = 0;
+    // rows split off the row tiles for the solve's products (device arrays owned by the
+    // hierarchy; sr.rows = nullptr: none): every row with more than split_len entries.  When
+    // present it supersedes lr.
+    SplitRows sr;
+    int split_len = 0x7fffffff;
 };
-constexpr int kSplitBlockLen = 1024;
 // sliced ELL (slices of 32 rows): slices of an n-row matrix; widths sw[ns], offsets sp[ns+1]
 // and the entry count in 64 bits (*total64, device; the offsets hold only when it fits an
 // int); then columns and values

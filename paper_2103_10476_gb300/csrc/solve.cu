@@ -179,22 +179,51 @@ __device__ __forceinline__ void block_row(int row, const int *__restrict__ rp, c
     outside_row_update<T, MODE>(row, sr, x, y, f, aux, d, c1, c2);
 }
 
-// Block b of a plan's split rows: split rows 0 .. nlong-1 take a block each, the next nmid a
-// warp each (eight to a block; strided partial sums over the lanes, a shuffle tree)
+// Block b of a plan's split rows (SplitRows): the segment blocks first (a segment's sum by the
+// whole block; the row's last segment block to finish, by an arrival ticket, adds the row's
+// segment sums in segment order and applies the update, then resets the ticket), then a block
+// per row of the block rows, then the warp rows eight to a block.
 constexpr int kSplitRowsPerBlock = kSpmvThreads / 32;
-template <typename T, int MODE>
-__device__ __forceinline__ void split_rows_block(int b, const int *__restrict__ split, int nlong, int nmid,
-                                                 const int *__restrict__ rp, const int *__restrict__ ci,
-                                                 const T *__restrict__ v, const T *x, T *y, const T *f,
-                                                 const T *aux, T *d, T c1, T c2)
+__host__ __device__ __forceinline__ int split_blocks(const SplitRows &sr)
 {
-    if (b < nlong) {
-        block_row<T, MODE>(split[b], rp, ci, v, x, y, f, aux, d, c1, c2);
+    return sr.nsegb + sr.nblock + (sr.nwarp + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
+}
+template <typename T, int MODE>
+__device__ __forceinline__ void split_rows_block(int b, const SplitRows &sr, const int *__restrict__ rp,
+                                                 const int *__restrict__ ci, const T *__restrict__ v, const T *x,
+                                                 T *y, const T *f, const T *aux, T *d, T c1, T c2)
+{
+    if (b < sr.nsegb) {
+        __shared__ T ws[kSpmvThreads / 32];
+        const int *g = sr.seg + 5 * b;
+        const int row = g[0], k0 = g[1], k1 = g[2], first = g[3], nseg = g[4];
+        T sum = strided_sum4<T>(k0 + (int)threadIdx.x, k1, kSpmvThreads, ci, v, x);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x != 0) return;
+        T t = T(0);
+        for (int w = 0; w < kSpmvThreads / 32; ++w) t += ws[w];
+        sr.part[b] = (double)t;
+        __threadfence();
+        if (atomicAdd(&sr.tick[first], 1u) != (unsigned)nseg - 1u) return;
+        __threadfence();
+        double acc = 0.0;
+        for (int q = 0; q < nseg; ++q) acc += ((volatile const double *)sr.part)[first + q];
+        sr.tick[first] = 0u;
+        outside_row_update<T, MODE>(row, (T)acc, x, y, f, aux, d, c1, c2);
         return;
     }
-    const int m = (b - nlong) * kSplitRowsPerBlock + (int)(threadIdx.x >> 5);
-    if (m >= nmid) return;
-    const int row = split[nlong + m];
+    b -= sr.nsegb;
+    if (b < sr.nblock) {
+        block_row<T, MODE>(sr.rows[sr.nseg_rows + b], rp, ci, v, x, y, f, aux, d, c1, c2);
+        return;
+    }
+    b -= sr.nblock;
+    const int m = b * kSplitRowsPerBlock + (int)(threadIdx.x >> 5);
+    if (m >= sr.nwarp) return;
+    const int row = sr.rows[sr.nseg_rows + sr.nblock + m];
     const int lane = threadIdx.x & 31;
     T sum = strided_sum4<T>(rp[row] + lane, rp[row + 1], 32, ci, v, x);
 #pragma unroll
@@ -204,14 +233,13 @@ __device__ __forceinline__ void split_rows_block(int b, const int *__restrict__ 
 
 // the split rows of a product with dot products, summed before its tile kernel
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kSpmvThreads) spmv_split_kernel(const int *__restrict__ split, int nlong, int nmid,
-                                                                  const int *__restrict__ rp,
+__global__ void __launch_bounds__(kSpmvThreads) spmv_split_kernel(SplitRows sr, const int *__restrict__ rp,
                                                                   const int *__restrict__ ci,
                                                                   const T *__restrict__ v, const T *__restrict__ x,
                                                                   T *y, const T *__restrict__ f,
                                                                   const T *__restrict__ aux, T *d, T c1, T c2)
 {
-    split_rows_block<T, MODE>(blockIdx.x, split, nlong, nmid, rp, ci, v, x, y, f, aux, d, c1, c2);
+    split_rows_block<T, MODE>(blockIdx.x, sr, rp, ci, v, x, y, f, aux, d, c1, c2);
 }
 
 template <typename T, int LPR, int MODE>
@@ -222,19 +250,19 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                                                                  const T *__restrict__ aux, T *d, T c1, T c2,
                                                                  int cap, double *partial, double *result,
                                                                  unsigned *counter, int *err, int long_len,
-                                                                 const int *__restrict__ split, int nlong, int nmid)
+                                                                 SplitRows sr)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     constexpr int RPB = kSpmvThreads / LPR;
     constexpr int VA = 16 / (int)sizeof(T);
-    // the first blocks of an update-only product sum the plan's split rows (nlong + nmid = 0
-    // for the products with dot products, whose split rows a separate launch sums first)
+    // the first blocks of an update-only product sum the plan's split rows (none given to the
+    // products with dot products, whose split rows a separate launch sums first)
     int bx = blockIdx.x, nbx = gridDim.x;
     {
-        const int extra = nlong + (nmid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
+        const int extra = split_blocks(sr);
         if (bx < extra) {
-            split_rows_block<T, MODE>(bx, split, nlong, nmid, rp, ci, v, x, y, f, aux, d, c1, c2);
+            split_rows_block<T, MODE>(bx, sr, rp, ci, v, x, y, f, aux, d, c1, c2);
             return;
         }
         bx -= extra;
@@ -570,27 +598,43 @@ cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStr
     return spmv_plans(1, pls, rps, ns, nz, s);
 }
 
-// rows with more than len entries: cnt[0] of more than kSplitBlockLen, cnt[1] the others
+// rows with more than len entries, by class: cnt[0] more than kSegRowLen entries, cnt[1] more
+// than kBlockRowLen, cnt[2] the others
+__device__ __forceinline__ int split_class(int l) { return l > kSegRowLen ? 0 : l > kBlockRowLen ? 1 : 2; }
 __global__ void split_count_kernel(int n, const int *rp, int len, int *cnt)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int l = rp[i + 1] - rp[i];
-    if (l > len) atomicAdd(&cnt[l > kSplitBlockLen ? 0 : 1], 1);
+    if (l > len) atomicAdd(&cnt[split_class(l)], 1);
 }
 
-// the same rows into list (the long ones first; order of arrival within each part: a row's
-// sum does not depend on which block or warp forms it)
-__global__ void split_fill_kernel(int n, const int *rp, int len, int nlong, int *cnt, int *list)
+// the same rows into list, class after class (order of arrival within a class: a row's sum does
+// not depend on which block or warp forms it)
+__global__ void split_fill_kernel(int n, const int *rp, int len, int n0, int n1, int *cnt, int *list)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int l = rp[i + 1] - rp[i];
     if (l <= len) return;
-    if (l > kSplitBlockLen)
-        list[atomicAdd(&cnt[0], 1)] = i;
-    else
-        list[nlong + atomicAdd(&cnt[1], 1)] = i;
+    const int c = split_class(l);
+    list[(c == 0 ? 0 : c == 1 ? n0 : n0 + n1) + atomicAdd(&cnt[c], 1)] = i;
+}
+
+// segment block b's row: entry 0 of its table row holds the row's index in the list
+__global__ void split_seg_rows_kernel(int nsegb, const int *list, int *seg)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nsegb) seg[5 * b] = list[seg[5 * b]];
+}
+
+// first and end entry of each of the m listed rows
+__global__ void split_ranges_kernel(int m, const int *list, const int *rp, int *out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    out[2 * t] = rp[list[t]];
+    out[2 * t + 1] = rp[list[t] + 1];
 }
 
 // A solve plan's row-tile limit: a row of more than 16 entries a lane (and more than 4 x its
@@ -602,44 +646,124 @@ int split_threshold(int lpr, double avg)
     return t < 1.0e9 ? (int)t : 1000000000;
 }
 
+// Per plan, one allocation of ints: the segment sums (2 ints each, first: 8-byte aligned), the
+// tickets, the segment table (5 ints each), the row list.
 cudaError_t spmv_split_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
                             const int64_t *nnzs, const std::function<cudaError_t(int **, size_t)> &alloc,
                             cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
+    constexpr int W = 8;     // counter ints per plan: 3 to count, 3 to fill
     int *d = nullptr;
-    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * 4 * (size_t)count, s));
-    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * 4 * (size_t)count, s);
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * W * (size_t)count, s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * W * (size_t)count, s);
     std::vector<int> len((size_t)count, 0x7fffffff);
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         SpmvPlan *pl = plans[k];
-        pl->split = nullptr;
+        pl->sr = SplitRows();
         pl->split_len = 0x7fffffff;
-        pl->split_long = pl->split_mid = 0;
         if (ns[k] == 0 || nnzs[k] == 0) continue;
         len[(size_t)k] = split_threshold(pl->lpr, (double)nnzs[k] / ns[k]);
-        split_count_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], d + 4 * k);
+        split_count_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], d + W * k);
         note_launch();
         e = cudaGetLastError();
     }
-    std::vector<int> h((size_t)count * 4, 0);
+    std::vector<int> h((size_t)count * W, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    for (int k = 0; k < count && e == cudaSuccess; ++k) {
-        const int nl = h[(size_t)4 * k], nm = h[(size_t)4 * k + 1];
-        if (nl + nm == 0) continue;
-        int *list = nullptr;
-        e = alloc(&list, (size_t)nl + (size_t)nm);
-        if (e != cudaSuccess) break;
-        split_fill_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], nl, d + 4 * k + 2, list);
-        note_launch();
-        e = cudaGetLastError();
-        SpmvPlan *pl = plans[k];
-        pl->split = list;
-        pl->split_len = len[(size_t)k];
-        pl->split_long = nl;
-        pl->split_mid = nm;
+    // the row lists, and the ranges of the rows to be segmented
+    std::vector<int *> base((size_t)count, nullptr);
+    std::vector<size_t> rng_off((size_t)count, 0);
+    size_t rng_total = 0;
+    for (int k = 0; k < count; ++k) {
+        rng_off[(size_t)k] = rng_total;
+        rng_total += 2 * (size_t)h[(size_t)W * k];
     }
+    int *rng = nullptr;
+    if (e == cudaSuccess && rng_total) e = cudaMallocAsync(&rng, sizeof(int) * rng_total, s);
+    std::vector<int *> lists((size_t)count, nullptr);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int n0 = h[(size_t)W * k], n1 = h[(size_t)W * k + 1], n2 = h[(size_t)W * k + 2];
+        if (n0 + n1 + n2 == 0) continue;
+        e = cudaMallocAsync(&lists[(size_t)k], sizeof(int) * ((size_t)n0 + n1 + n2), s);
+        if (e != cudaSuccess) break;
+        split_fill_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], len[(size_t)k], n0, n1, d + W * k + 3,
+                                                               lists[(size_t)k]);
+        note_launch();
+        if (n0) {
+            split_ranges_kernel<<<grid_for(n0, 256), 256, 0, s>>>(n0, lists[(size_t)k], rps[k],
+                                                                  rng + rng_off[(size_t)k]);
+            note_launch();
+        }
+        e = cudaGetLastError();
+    }
+    std::vector<int> hr(rng_total);
+    if (e == cudaSuccess && rng_total)
+        e = cudaMemcpyAsync(hr.data(), rng, sizeof(int) * rng_total, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // per plan: the segment table on the host, then one allocation for everything
+    std::vector<std::vector<int>> tables((size_t)count);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int n0 = h[(size_t)W * k], n1 = h[(size_t)W * k + 1], n2 = h[(size_t)W * k + 2];
+        const int nl = n0 + n1 + n2;
+        if (nl == 0) continue;
+        std::vector<int> &seg = tables[(size_t)k];
+        for (int t = 0; t < n0; ++t) {
+            const int k0 = hr[rng_off[(size_t)k] + 2 * t], k1 = hr[rng_off[(size_t)k] + 2 * t + 1];
+            const int first = (int)(seg.size() / 5), nseg = (k1 - k0 + kSegRowLen - 1) / kSegRowLen;
+            for (int q = 0; q < nseg; ++q) {
+                seg.push_back(-1);                          // the row, from the device list below
+                seg.push_back(k0 + q * kSegRowLen);
+                seg.push_back(std::min(k1, k0 + (q + 1) * kSegRowLen));
+                seg.push_back(first);
+                seg.push_back(nseg);
+            }
+        }
+        const size_t nsegb = seg.size() / 5;
+        int *buf = nullptr;
+        e = alloc(&buf, 2 * nsegb + nsegb + 5 * nsegb + (size_t)nl);
+        if (e != cudaSuccess) break;
+        SplitRows &sr = plans[k]->sr;
+        sr.part = (double *)buf;
+        sr.tick = (unsigned *)(buf + 2 * nsegb);
+        int *dseg = buf + 3 * nsegb;       // filled below, once each segment's row is known
+        int *drows = dseg + 5 * nsegb;
+        sr.seg = dseg;
+        sr.rows = drows;
+        sr.nseg_rows = n0;
+        sr.nblock = n1;
+        sr.nwarp = n2;
+        sr.nsegb = (int)nsegb;
+        plans[k]->split_len = len[(size_t)k];
+        if (nsegb) e = cudaMemsetAsync(sr.tick, 0, sizeof(unsigned) * nsegb, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(drows, lists[(size_t)k], sizeof(int) * (size_t)nl, cudaMemcpyDeviceToDevice, s);
+        // each segment's row: the segmented rows in list order
+        if (e == cudaSuccess && nsegb) {
+            int t = 0;
+            for (size_t b = 0; b < nsegb; ++b) {
+                if (b > 0 && seg[5 * b + 3] != seg[5 * (b - 1) + 3]) ++t;
+                seg[5 * b] = t;            // index into the list for now
+            }
+        }
+    }
+    // the row of each segment block from the list (a device gather: the list order is the
+    // device's), then the tables
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        SplitRows &sr = plans[k]->sr;
+        if (!sr.nsegb) continue;
+        e = cudaMemcpyAsync((void *)sr.seg, tables[(size_t)k].data(), sizeof(int) * tables[(size_t)k].size(),
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            split_seg_rows_kernel<<<grid_for(sr.nsegb, 256), 256, 0, s>>>(sr.nsegb, sr.rows, (int *)sr.seg);
+            note_launch();
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);       // the host tables go out of scope
+    for (int *p : lists)
+        if (p) cudaFreeAsync(p, s);
+    if (rng) cudaFreeAsync(rng, s);
     cudaFreeAsync(d, s);
     return e;
 }
@@ -879,9 +1003,9 @@ cudaError_t sell_fill_t(int n, const int *rp, const int *ci, const T *v, int ns,
 template <typename T, int LPR, int MODE>
 cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T *x, T *y, const T *f, const T *aux,
                         T *d, T c1, T c2, int cap, double *partial, double *result, unsigned *counter,
-                        cudaStream_t s, int long_len, const int *split, int nlong, int nmid)
+                        cudaStream_t s, int long_len, const SplitRows &sr)
 {
-    const int extra = nlong + (nmid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
+    const int extra = split_blocks(sr);
     const int smem = tile_bytes<T>(cap);
     // the attribute is set once per instantiation (any thread may get here first)
     static std::once_flag configured;
@@ -892,8 +1016,8 @@ cudaError_t launch_tile(int n, const int *rp, const int *ci, const T *v, const T
     });
     AMG_CUDA_TRY(cfg_err);
     spmv_tile_kernel<T, LPR, MODE><<<spmv_blocks(n, LPR) + extra, kSpmvThreads, smem, s>>>(
-        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), long_len, split, nlong,
-        nmid); note_launch();
+        n, rp, ci, v, x, y, f, aux, d, c1, c2, cap, partial, result, counter, spmv_error_flag(), long_len, sr);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -905,26 +1029,22 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
     if (n == 0) return cudaSuccess;
     if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || (MODE == MODE_DOT && result == nullptr) ||
          MODE == MODE_POWER) &&
-        pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 && pl.split == nullptr) {
+        pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 && pl.sr.rows == nullptr) {
         const T *sv = sell_values<T>(pl);
         if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s, result, counter);
     }
     int long_len = 0x7fffffff;
-    const int *split = nullptr;
-    int nlong = 0, nmid = 0;
-    if (pl.split) {
+    SplitRows sr;
+    if (pl.sr.rows) {
         long_len = pl.split_len;
         if (MODE == MODE_DOT || MODE == MODE_SCALEDOT || MODE == MODE_POWER) {
             // the tile kernel's dot products read the split rows' y: they go first
-            const int blocks = pl.split_long + (pl.split_mid + kSplitRowsPerBlock - 1) / kSplitRowsPerBlock;
-            spmv_split_kernel<T, MODE><<<blocks, kSpmvThreads, 0, s>>>(pl.split, pl.split_long, pl.split_mid, rp, ci,
-                                                                       v, x, y, f, aux, d, c1, c2);
+            spmv_split_kernel<T, MODE><<<split_blocks(pl.sr), kSpmvThreads, 0, s>>>(pl.sr, rp, ci, v, x, y, f, aux, d,
+                                                                                    c1, c2);
             note_launch();
             AMG_CUDA_TRY(cudaGetLastError());
         } else {
-            split = pl.split;
-            nlong = pl.split_long;
-            nmid = pl.split_mid;
+            sr = pl.sr;
         }
     } else if (pl.lr.count > 0) {
         spmv_long_kernel<T, MODE><<<pl.lr.count, kSpmvThreads, 0, s>>>(pl.lr, rp, ci, v, x, y, f, aux, d, c1, c2);
@@ -935,19 +1055,19 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
     switch (pl.lpr) {
     case 2:
         return launch_tile<T, 2, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len, split, nlong, nmid);
+                                       long_len, sr);
     case 4:
         return launch_tile<T, 4, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len, split, nlong, nmid);
+                                       long_len, sr);
     case 8:
         return launch_tile<T, 8, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                       long_len, split, nlong, nmid);
+                                       long_len, sr);
     case 16:
         return launch_tile<T, 16, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                        long_len, split, nlong, nmid);
+                                        long_len, sr);
     default:
         return launch_tile<T, 32, MODE>(n, rp, ci, v, x, y, f, aux, d, c1, c2, pl.cap, partial, result, counter, s,
-                                        long_len, split, nlong, nmid);
+                                        long_len, sr);
     }
 }
 
