@@ -233,6 +233,7 @@ struct SpmvPlan {
     // present it supersedes lr.
     SplitRows sr;
     int split_len = 0x7fffffff;
+    int rowk = 0;                // short rows: one thread per row (spmv_rows_kernel)
 };
 // sliced ELL (slices of 32 rows): slices of an n-row matrix; widths sw[ns], offsets sp[ns+1]
 // and the entry count in 64 bits (*total64, device; the offsets hold only when it fits an
@@ -246,6 +247,9 @@ cudaError_t sell_fill_f(int n, const int *rp, const float *v, int ns, const int 
 cudaError_t spmv_plan(const int *rp, int n, int64_t nnz, SpmvPlan *plan, cudaStream_t s);
 cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns, const int64_t *nnzs,
                        cudaStream_t s);
+// Marks the solve's plans of short rows for the thread-per-row kernel (one synchronisation)
+cudaError_t spmv_short_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
+                            const int64_t *nnzs, cudaStream_t s);
 // The split rows of the solve's plans (above): counts with one synchronisation, then a list per
 // plan with split rows from alloc(&list, entries) (device memory the caller owns).
 cudaError_t spmv_split_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,

@@ -814,6 +814,16 @@ amg_status_t prepare_solve(amg_hierarchy *h)
             }
             CK(spmv_split_rows((int)sp.size(), sp.data(), srp.data(), sn.data(), snz.data(),
                                [h](int **list, size_t count) { return dalloc(h, list, count); }, s));
+            // the prolongators' short rows: a thread per row (the products with P only)
+            std::vector<SpmvPlan *> pp;
+            std::vector<const int *> prp;
+            std::vector<int> pn;
+            std::vector<int64_t> pnz;
+            for (int L = 0; L + 1 < h->nlev; ++L) {
+                Level &lv = h->lev[L];
+                pp.push_back(&lv.plan_p); prp.push_back(lv.P.rp); pn.push_back(lv.A.n); pnz.push_back(lv.P.nnz);
+            }
+            CK(spmv_short_rows((int)pp.size(), pp.data(), prp.data(), pn.data(), pnz.data(), s));
         }
         if (h->nlev > 1) h->plan0 = h->lev[0].plan_a;
         for (int L = 0; L + 1 < h->nlev; ++L) {

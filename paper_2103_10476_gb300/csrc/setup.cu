@@ -1256,6 +1256,9 @@ __global__ void power_init_kernel(int n, uint64_t s0, double *x)
     x[i] = 2.0 * u - 1.0;
 }
 
+// q[1] = 1 / sqrt(q[0])
+__global__ void rsqrt_slot_kernel(double *q) { q[1] = 1.0 / __dsqrt_rn(q[0]); }
+
 __global__ void reciprocal_kernel(int n, const double *D, double *inv)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1276,18 +1279,20 @@ cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D,
         ~Release() { cudaFreeAsync(p, s); }
     } release{invD, s};
     reciprocal_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, D, invD); note_launch();
-    // x0 and x0 . x0; each sweep then works on the unnormalised iterate and its squared norm
-    // (scal[3], scal[4] alternate), which equals normalising before every sweep
+    // x0 and x0 . x0; each sweep then works on the unnormalised iterate, its squared norm and
+    // the reciprocal of its norm (scal[3..4] and scal[5..6] alternate), which equals
+    // normalising before every sweep
     power_init_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, stream_seed, x); note_launch();
     AMG_CUDA_TRY(cudaGetLastError());
     AMG_CUDA_TRY(dot(x, x, n, partial, scal + 3, s));
+    rsqrt_slot_kernel<<<1, 1, 0, s>>>(scal + 3); note_launch();
     // ticket counter of the SpMV's fixed-order reduction (scal[7], zero)
     unsigned *counter = reinterpret_cast<unsigned *>(scal + 7);
     AMG_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(double), s));
     double *a = x, *b = y;
     for (int k = 0; k < sweeps; ++k) {
-        AMG_CUDA_TRY(spmv_power(A, plan, invD, a, scal + 3 + (k & 1), b, scal + 4 - (k & 1), partial, lambda_dev,
-                                counter, s));
+        AMG_CUDA_TRY(spmv_power(A, plan, invD, a, scal + 3 + 2 * (k & 1), b, scal + 5 - 2 * (k & 1), partial,
+                                lambda_dev, counter, s));
         std::swap(a, b);
     }
     return cudaGetLastError();

@@ -35,8 +35,9 @@ enum SpmvMode {
     MODE_PROLONG = 3,    // y += A x
     MODE_DOT = 4,        // y = A x; partial[block] = sum of x_i y_i
     MODE_SCALEDOT = 5,   // y = (A x) / D; partial[block] = sum of x_i y_i
-    MODE_POWER = 6,      // power-method sweep on an unnormalised x with q = f[0] = x . x, aux = D^-1:
-                         // y = (D^-1 A x) / sqrt(q); result[0] = (x . y) / sqrt(q); d[0] = y . y
+    MODE_POWER = 6,      // power-method sweep on an unnormalised x with f[0] = x . x, f[1] = 1 / sqrt(x . x),
+                         // aux = D^-1: y = (D^-1 A x) f[1]; result[0] = (x . y) f[1]; d[0] = y . y and
+                         // d[1] = 1 / sqrt(y . y) (the next sweep's f)
 };
 
 
@@ -74,7 +75,7 @@ __device__ __forceinline__ void last_block_total(const double *partial, int nblo
 // block to arrive (of narrive; nblocks when not given) stores *r1 = scale * (first total) and
 // *r2 = second total.
 __device__ __forceinline__ void last_block_total2(const double *partial, int nblocks, unsigned *counter, double *r1,
-                                                  double *r2, double scale, int narrive = -1)
+                                                  double *r2, double scale, int narrive = -1, bool r2_rsqrt = false)
 {
     __shared__ bool last;
     __shared__ double w1[32], w2[32];
@@ -109,6 +110,7 @@ __device__ __forceinline__ void last_block_total2(const double *partial, int nbl
         }
         *r1 = scale * t1;
         *r2 = t2;
+        if (r2_rsqrt) r2[1] = 1.0 / __dsqrt_rn(t2);    // the next sweep's 1 / ||y||
         *counter = 0u;
     }
 }
@@ -134,7 +136,7 @@ __device__ __forceinline__ void outside_row_update(int row, T sr, const T *x, T 
     } else if (MODE == MODE_SCALEDOT) {
         y[row] = sr / aux[row];
     } else {
-        const double rq = 1.0 / __dsqrt_rn((double)f[0]);
+        const double rq = (double)f[1];
         y[row] = (T)(((double)sr * (double)aux[row]) * rq);
     }
 }
@@ -240,6 +242,49 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_split_kernel(SplitRows sr, 
                                                                   const T *__restrict__ aux, T *d, T c1, T c2)
 {
     split_rows_block<T, MODE>(blockIdx.x, sr, rp, ci, v, x, y, f, aux, d, c1, c2);
+}
+
+// Short rows (a prolongator's: a few entries each) by one thread per row, without staging: the
+// rows of a warp are contiguous in memory, so their loads are as coalesced as the tile's.  The
+// arithmetic of the two-lanes-per-row tile kernel (even and odd entries summed apart, then
+// added), so both give the same bits.  Update modes only.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kSpmvThreads) spmv_rows_kernel(int n, const int *__restrict__ rp,
+                                                                 const int *__restrict__ ci,
+                                                                 const T *__restrict__ v, const T *__restrict__ x,
+                                                                 T *y, const T *__restrict__ f,
+                                                                 const T *__restrict__ aux, T *d, T c1, T c2)
+{
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    const int b = rp[row], e = rp[row + 1];
+    T s0 = T(0), s1 = T(0);
+    int k = b;
+    for (; k + 1 < e; k += 2) {
+        s0 += v[k] * x[ci[k]];
+        s1 += v[k + 1] * x[ci[k + 1]];
+    }
+    if (k < e) s0 += v[k] * x[ci[k]];
+    const T sr = s0 + s1;
+    if (MODE == MODE_Y) {
+        y[row] = sr;
+    } else if (MODE == MODE_RESID) {
+        y[row] = f[row] - sr;
+    } else if (MODE == MODE_CHEB) {
+        T r = f[row] - sr;
+        T dn = c1 * d[row] + c2 * (aux[row] * r);
+        d[row] = dn;
+        y[row] = x[row] + dn;
+    } else {
+        y[row] += sr;
+    }
+}
+
+// the longest row of each of count matrices into out[k]
+__global__ void max_row_kernel(int n, const int *rp, int *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, rp[i + 1] - rp[i]);
 }
 
 template <typename T, int LPR, int MODE>
@@ -352,7 +397,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
             if (lane == 0) pps[threadIdx.x / LPR] = (double)sum;
         }
-        if (threadIdx.x == 0) rq_s = 1.0 / __dsqrt_rn((double)f[0]);
+        if (threadIdx.x == 0) rq_s = (double)f[1];
         __syncthreads();
         const double rq = rq_s;
         double c1v = 0.0, c2v = 0.0;
@@ -389,7 +434,7 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             partial[bx] = t1;
             partial[nbx + bx] = t2;
         }
-        last_block_total2(partial, nbx, counter, result, (double *)d, rq);
+        last_block_total2(partial, nbx, counter, result, (double *)d, rq, -1, true);
         return;
     }
 #pragma unroll
@@ -768,6 +813,32 @@ cudaError_t spmv_split_rows(int count, SpmvPlan *const *plans, const int *const 
     return e;
 }
 
+// Plans of short rows (two lanes per row in the tiles, at most 8 entries a row on average and
+// 16 at most) take spmv_rows_kernel: one synchronisation for all.
+cudaError_t spmv_short_rows(int count, SpmvPlan *const *plans, const int *const *rps, const int *ns,
+                            const int64_t *nnzs, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    int *d = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&d, sizeof(int) * (size_t)count, s));
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int) * (size_t)count, s);
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        plans[k]->rowk = 0;
+        if (ns[k] == 0 || plans[k]->lpr != 2 || nnzs[k] > 8 * (int64_t)ns[k]) continue;
+        max_row_kernel<<<grid_for(ns[k], 256), 256, 0, s>>>(ns[k], rps[k], d + k);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    std::vector<int> h((size_t)count, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), d, sizeof(int) * (size_t)count, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d, s);
+    for (int k = 0; k < count && e == cudaSuccess; ++k)
+        if (ns[k] > 0 && plans[k]->lpr == 2 && nnzs[k] <= 8 * (int64_t)ns[k] && h[(size_t)k] <= 16)
+            plans[k]->rowk = 1;
+    return e;
+}
+
 static int *g_spmv_err = nullptr;   // device error flag of the bounded waits (allocated once)
 static std::once_flag g_spmv_err_once;
 
@@ -836,13 +907,7 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
                                                                  unsigned *counter)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double rq = 0.0;
-    if (MODE == MODE_POWER) {
-        __shared__ double rq_s;
-        if (threadIdx.x == 0) rq_s = 1.0 / __dsqrt_rn((double)f[0]);
-        __syncthreads();
-        rq = rq_s;
-    }
+    const double rq = MODE == MODE_POWER ? (double)f[1] : 0.0;
     const int slice = blockIdx.x * (kSellThreads / kSliceRows) + warp;
     const int row = slice * kSliceRows + lane;
     T sum = T(0);
@@ -911,7 +976,7 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
                 partial[nparts + part] = t2;
             }
         }
-        last_block_total2(partial, nparts, counter, result, (double *)d, rq, (int)gridDim.x);
+        last_block_total2(partial, nparts, counter, result, (double *)d, rq, (int)gridDim.x, true);
         return;
     }
     if (MODE == MODE_DOT) {
@@ -1033,6 +1098,13 @@ cudaError_t spmv_mode(const SpmvPlan &pl, int n, const int *rp, const int *ci, c
         const T *sv = sell_values<T>(pl);
         if (sv) return launch_sell<T, MODE>(pl, n, sv, x, y, f, aux, d, c1, c2, partial, s, result, counter);
     }
+    if ((MODE == MODE_Y || MODE == MODE_RESID || MODE == MODE_CHEB || MODE == MODE_PROLONG) && pl.rowk &&
+        pl.sr.rows == nullptr && pl.lr.count == 0) {
+        spmv_rows_kernel<T, MODE><<<(n + kSpmvThreads - 1) / kSpmvThreads, kSpmvThreads, 0, s>>>(n, rp, ci, v, x, y,
+                                                                                              f, aux, d, c1, c2);
+        note_launch();
+        return cudaGetLastError();
+    }
     int long_len = 0x7fffffff;
     SplitRows sr;
     if (pl.sr.rows) {
@@ -1100,8 +1172,9 @@ cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D
 }
 
 // one sweep of the power method on D^-1 A (invD = D^-1) from the unnormalised x with
-// *xx = x . x: y = (D^-1 A x) / sqrt(xx), *lambda = (x . y) / sqrt(xx) (the Rayleigh quotient of
-// the unit vector), *yy = y . y.  partial holds 2 x the plan's blocks.
+// xx[0] = x . x and xx[1] = 1 / sqrt(x . x): y = (D^-1 A x) xx[1], *lambda = (x . y) xx[1] (the
+// Rayleigh quotient of the unit vector), yy[0] = y . y, yy[1] = 1 / sqrt(y . y).  partial holds
+// 2 x the plan's blocks.
 cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *invD, const double *x, const double *xx,
                        double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s)
 {
@@ -1180,8 +1253,12 @@ __device__ __forceinline__ double sum_partials_all(const double *partial, int co
 
 // alpha = rz / (p . q); x += alpha p; r -= alpha q; partial sums of r . r (read back by the
 // host for the stopping test)
-__global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x, double *r, const double *p,
-                                                                const double *q, PcgScalars *sc,
+// (the vector loops below are unrolled with their arrays marked unaliased, so a thread's loads of
+// several iterations are in flight at once; the sums still add in iteration order)
+__global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *__restrict__ x,
+                                                                double *__restrict__ r,
+                                                                const double *__restrict__ p,
+                                                                const double *__restrict__ q, PcgScalars *sc,
                                                                 const double *pq_partial, int pq_count,
                                                                 double *rr_partial)
 {
@@ -1193,6 +1270,7 @@ __global__ void __launch_bounds__(kReduceThreads) pcg_xr_kernel(int n, double *x
     // reads only rz_next, so the write races with nothing
     if (blockIdx.x == 0 && threadIdx.x == 0) { sc->alpha = alpha; sc->rz = sc->rz_next; }
     double acc = 0.0;
+#pragma unroll 4
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
         x[i] += alpha * p[i];
         double ri = r[i] - alpha * q[i];
@@ -1211,11 +1289,13 @@ cudaError_t pcg_update_xr(int n, double *x, double *r, const double *p, const do
 }
 
 // r . z (and r . z_prev for the flexible form) into scalars, fixed-order two-stage sums
-__global__ void __launch_bounds__(kReduceThreads) dot_rz_kernel(int n, const double *r, const double *z,
-                                                                const double *zp, double *pa, double *pb,
-                                                                PcgScalars *sc, unsigned *counters)
+__global__ void __launch_bounds__(kReduceThreads) dot_rz_kernel(int n, const double *__restrict__ r,
+                                                                const double *__restrict__ z,
+                                                                const double *__restrict__ zp, double *pa,
+                                                                double *pb, PcgScalars *sc, unsigned *counters)
 {
     double a = 0.0, b = 0.0;
+#pragma unroll 4
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads) {
         const double ri = r[i];
         a += ri * z[i];
@@ -1233,11 +1313,13 @@ __global__ void __launch_bounds__(kReduceThreads) dot_rz_kernel(int n, const dou
 
 // beta = rz_new / rz (flexible: (rz_new - rz_cross) / rz); p = z + beta p.  rz_new goes to
 // rz_next, which the next alpha reads (no block overwrites what another still reads).
-__global__ void __launch_bounds__(kReduceThreads) pcg_p_kernel(int n, double *p, const double *z, PcgScalars *sc,
+__global__ void __launch_bounds__(kReduceThreads) pcg_p_kernel(int n, double *__restrict__ p,
+                                                               const double *__restrict__ z, PcgScalars *sc,
                                                                int flexible)
 {
     const double rz_new = sc->rz_new;
     const double beta = (flexible ? rz_new - sc->rz_cross : rz_new) / sc->rz;
+#pragma unroll 4
     for (int i = blockIdx.x * kReduceThreads + threadIdx.x; i < n; i += kReduceBlocks * kReduceThreads)
         p[i] = z[i] + beta * p[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) { sc->beta = beta; sc->rz_next = rz_new; }
