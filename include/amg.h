@@ -84,7 +84,7 @@ enum { AMG_LAYOUT_AUTO = 0, AMG_LAYOUT_CSR = 1, AMG_LAYOUT_SELL = 2 };
  * rows with at most one stored entry in eight whose Jacobi-scaled spectrum is narrow (what
  * stalled aggregation leaves): there the V-cycle applies a fixed Chebyshev polynomial in D^-1 A
  * of the least degree (at most 40) whose error bound on an interval holding that spectrum is
- * below 1e-16.  The interval comes from 24 Lanczos steps (through Jacobi-preconditioned CG),
+ * below 1e-16.  The interval comes from 16 Lanczos steps (through Jacobi-preconditioned CG),
  * widened by a fifth of its width each way, and is accepted only when a check solve of a
  * pseudo-random right-hand side leaves a relative residual (D^-1 norm) at most 1e-12;
  * otherwise the inverse is formed.  A fixed polynomial is one linear operator, as the inverse

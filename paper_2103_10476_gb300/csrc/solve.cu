@@ -540,15 +540,18 @@ int pick_lpr_rows(double avg_row, int n)
 
 // the largest block range of a plan, over the blocks without a long row (a block holding one is
 // not staged: its range exceeds the tile, and its short rows read global memory)
+// (a warp per block range, its lanes over the range's rows)
 __global__ void span_max_kernel(int n, const int *rp, int rpb, int long_len, int *out)
 {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    int r0 = b * rpb;
-    if (r0 >= n) return;
-    int r1 = min(n, r0 + rpb);
-    for (int r = r0; r < r1; ++r)
-        if (rp[r + 1] - rp[r] > long_len) return;
-    atomicMax(out, rp[r1] - rp[r0]);
+    const int lane = threadIdx.x & 31;
+    const int b = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int r0 = b * rpb;
+    if (r0 >= n) return;             // the whole warp: r0 is the same for its lanes
+    const int r1 = min(n, r0 + rpb);
+    bool has_long = false;
+    for (int r = r0 + lane; r < r1; r += 32) has_long |= rp[r + 1] - rp[r] > long_len;
+    if (__any_sync(kAll, has_long)) return;
+    if (lane == 0) atomicMax(out, rp[r1] - rp[r0]);
 }
 
 // The long rows of a plan: more than max(512, 8 x the mean row) entries, the threshold doubled
@@ -622,7 +625,8 @@ cudaError_t spmv_plans(int count, SpmvPlan *const *plans, const int *const *rps,
         pl->cap = 0;
         if (n == 0 || nnzs[k] == 0) continue;
         const int nb = spmv_blocks(n, pl->lpr);
-        span_max_kernel<<<grid_for(nb, 256), 256, 0, s>>>(n, rps[k], kSpmvThreads / pl->lpr, pl->lr.len, d + k);
+        span_max_kernel<<<grid_for((int64_t)nb * 32, 256), 256, 0, s>>>(n, rps[k], kSpmvThreads / pl->lpr,
+                                                                          pl->lr.len, d + k);
         note_launch();
         e = cudaGetLastError();
     }
@@ -1397,12 +1401,12 @@ __global__ void t2d_kernel(int n, const T *in, double *out)
 // operator (as the exact inverse is); m is the least degree whose bound 2 rho^m on the error,
 // rho = (sqrt(hi/lo) - 1) / (sqrt(hi/lo) + 1), is below kCoarseChebTol.
 //
-// The interval: m_L steps of Jacobi-preconditioned CG on A x = b for a pseudo-random b are m_L
+// The interval: m_L = 16 steps of Jacobi-preconditioned CG on A x = b for a pseudo-random b are m_L
 // steps of the Lanczos process on D^-1 A (the tridiagonal matrix follows from the CG
 // coefficients alpha_j = rz_j / pq_j and beta_j = rz_{j+1} / rz_j).  Its extreme eigenvalues
 // lie inside the spectrum; widened by a fifth of their distance each way they bound it, and a
 // solve of a second pseudo-random right-hand side checks the result.
-constexpr int kLanczosSteps = 24;
+constexpr int kLanczosSteps = 16;
 constexpr int kCoarseChebMax = 40;
 constexpr double kCoarseChebTol = 1e-16;
 

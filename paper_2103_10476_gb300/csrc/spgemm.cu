@@ -28,6 +28,8 @@ constexpr int kNumBins = 11;            // 32 .. 8192, the global bin and the se
 constexpr int kGlobalBin = 9;
 constexpr int kSegBin = 10;             // numeric phase: rows of A of more than kSegLen entries
 constexpr int kSegLen = 256;
+constexpr int kChainProducts = 32768;      // rows with more products take the chain path (B wide) or
+                                           // the segment kernels (B narrow) ...
 constexpr int kSmemBudget = 96 * 1024;
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
@@ -137,7 +139,7 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
 // entries and, with seg_wide (B narrow enough for the segment kernels' dense accumulator), the
 // rows too long for a shared-memory table as well (*segmax: the longest row of A among them).
 __global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin, int *binCount, int *tsize,
-                                 int *segmax, int seg_wide)
+                                 int *segmax, int seg_wide, const int *aci = nullptr, const int *brp = nullptr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int b = 0;
@@ -145,7 +147,14 @@ __global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin
         const int alen = arp[i + 1] - arp[i];
         const int64_t cnt = crp[i + 1] - crp[i];
         const int S = table_for(cnt);
-        if (alen > kSegLen || (seg_wide && S > kMaxSharedNum)) {
+        // (with aci and brp: also the rows of more than kChainProducts products)
+        bool many = false;
+        if (seg_wide && aci && alen <= kSegLen) {
+            int64_t prod = 0;
+            for (int e = arp[i]; e < arp[i + 1]; ++e) prod += brp[aci[e] + 1] - brp[aci[e]];
+            many = prod > kChainProducts;
+        }
+        if (alen > kSegLen || (seg_wide && (S > kMaxSharedNum || many))) {
             b = kSegBin;
             tsize[i] = 0;
             atomicMax(segmax, alen);
@@ -427,7 +436,6 @@ __global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff,
 // per row) when B has at most kDenseCols columns, instead of one warp on a global hash table.
 constexpr int kDenseCols = 49152;          // 192 KB of int counters in shared memory
 constexpr int kChainOutputs = 256;         // entries of C per warp of the chain pass
-constexpr int kChainProducts = 32768;      // rows with more products take the chain path ...
 constexpr long long kChainTotal = 16 << 20;  // ... when the whole product has at most this many
 
 // visit(j) for the column of every product of row i, block-wide, in no particular order: one
@@ -1540,8 +1548,11 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         // numeric, binned by the exact row counts (rows of A of more than kSegLen entries apart)
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_segmax, 0, sizeof(int), s))) break;
+        const bool seg_wide = B.ncol <= kSegCols;
+        const bool heavy_rows = h_ubstats[0] > (unsigned long long)kChainProducts;
+        const bool long_products = heavy_rows && h_ubstats[1] <= (unsigned long long)kChainTotal;
         exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_segmax,
-                                                          B.ncol <= kSegCols ? 1 : 0);
+                                                          seg_wide ? 1 : 0, heavy_rows ? A.ci : nullptr, B.rp);
         note_launch();
         int h_segmax = 0;
         if ((e = cudaMemcpyAsync(&h_segmax, d_segmax, sizeof(int), cudaMemcpyDeviceToHost, s))) break;
@@ -1552,11 +1563,10 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         // 128^3 fine level: 4.1 + 3.0 ms against 5.8 + 6.4 ms for A P and R (A P)); numeric_row also
         // when the products exceed the chains' int32 offsets.
         // Also products with rows of more than kChainProducts products (a stalled level's large
-        // aggregates) when the whole product is small enough for the chains' global staging.
+        // aggregates) when the whole product is small enough for the chains' global staging and B
+        // is too wide for the segment kernels, which otherwise take those rows (kSegBin).
         bool chained = false;
-        const bool long_products = h_ubstats[0] > (unsigned long long)kChainProducts &&
-                                   h_ubstats[1] <= (unsigned long long)kChainTotal;
-        if (nnz > 0 && (hb.count[kGlobalBin] > 0 || long_products) &&
+        if (nnz > 0 && (hb.count[kGlobalBin] > 0 || (long_products && !seg_wide)) &&
             (e = numeric_chains(n, A, B, C, hb, d_perm, d_tsize, d_ovf, &chained, s)))
             break;
         for (int b = 0; b < kGlobalBin && !e && !chained; ++b)
