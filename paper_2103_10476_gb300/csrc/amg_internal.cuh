@@ -304,7 +304,8 @@ cudaError_t spmv_dot(const DevCsr &A, const SpmvPlan &pl, const double *p, doubl
 cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D, const double *x, double *y,
                             double *partial, double *result, unsigned *counter, cudaStream_t s);
 cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *invD, const double *x, const double *xx,
-                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s);
+                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s,
+                       bool with_lambda = true);
 cudaError_t spmv_d(const DevCsr &A, const SpmvPlan &pl, const double *x, double *y, cudaStream_t s);
 cudaError_t residual_d(const DevCsr &A, const SpmvPlan &pl, const double *b, const double *x, double *r,
                        cudaStream_t s);

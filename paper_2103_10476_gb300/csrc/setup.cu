@@ -1292,7 +1292,7 @@ cudaError_t power_lambda(const DevCsr &A, const SpmvPlan &plan, const double *D,
     double *a = x, *b = y;
     for (int k = 0; k < sweeps; ++k) {
         AMG_CUDA_TRY(spmv_power(A, plan, invD, a, scal + 3 + 2 * (k & 1), b, scal + 5 - 2 * (k & 1), partial,
-                                lambda_dev, counter, s));
+                                lambda_dev, counter, s, k + 1 == sweeps));
         std::swap(a, b);
     }
     return cudaGetLastError();

@@ -415,13 +415,15 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             c2v = yi * yi;
         }
         __shared__ double sp1[kSpmvThreads / 32], sp2[kSpmvThreads / 32];
+        // x . y only when asked (c1 != 0: the last sweep's, the estimate); y . y every sweep
+        if (c1 != T(0)) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c1v += __shfl_down_sync(kAll, c1v, o);
-            c2v += __shfl_down_sync(kAll, c2v, o);
+            for (int o = 16; o > 0; o >>= 1) c1v += __shfl_down_sync(kAll, c1v, o);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c2v += __shfl_down_sync(kAll, c2v, o);
         if ((threadIdx.x & 31) == 0) {
-            sp1[threadIdx.x >> 5] = c1v;
+            sp1[threadIdx.x >> 5] = c1 != T(0) ? c1v : 0.0;
             sp2[threadIdx.x >> 5] = c2v;
         }
         __syncthreads();
@@ -954,13 +956,14 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
         // CSR block b = rows 128 b .. 128 b + 127 = this block's warps 4 hh .. 4 hh + 3 (rows of
         // the CSR block's warp w' on its lanes, in order); the CSR block's warps 4-7 hold zeros
         __shared__ double q1[kSellThreads / 32], q2[kSellThreads / 32];
+        if (c1 != T(0)) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            contrib += __shfl_down_sync(kAll, contrib, o);
-            contrib2 += __shfl_down_sync(kAll, contrib2, o);
+            for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(kAll, contrib, o);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) contrib2 += __shfl_down_sync(kAll, contrib2, o);
         if (lane == 0) {
-            q1[warp] = contrib;
+            q1[warp] = c1 != T(0) ? contrib : 0.0;
             q2[warp] = contrib2;
         }
         __syncthreads();
@@ -1177,13 +1180,14 @@ cudaError_t spmv_scaled_dot(const DevCsr &A, const SpmvPlan &pl, const double *D
 
 // one sweep of the power method on D^-1 A (invD = D^-1) from the unnormalised x with
 // xx[0] = x . x and xx[1] = 1 / sqrt(x . x): y = (D^-1 A x) xx[1], *lambda = (x . y) xx[1] (the
-// Rayleigh quotient of the unit vector), yy[0] = y . y, yy[1] = 1 / sqrt(y . y).  partial holds
-// 2 x the plan's blocks.
+// Rayleigh quotient of the unit vector; only with_lambda, else 0), yy[0] = y . y,
+// yy[1] = 1 / sqrt(y . y).  partial holds 2 x the plan's blocks.
 cudaError_t spmv_power(const DevCsr &A, const SpmvPlan &pl, const double *invD, const double *x, const double *xx,
-                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s)
+                       double *y, double *yy, double *partial, double *lambda, unsigned *counter, cudaStream_t s,
+                       bool with_lambda)
 {
-    return spmv_mode<double, MODE_POWER>(pl, A.n, A.rp, A.ci, A.v, x, y, xx, invD, yy, 0.0, 0.0, partial, s, lambda,
-                                         counter);
+    return spmv_mode<double, MODE_POWER>(pl, A.n, A.rp, A.ci, A.v, x, y, xx, invD, yy, with_lambda ? 1.0 : 0.0, 0.0,
+                                         partial, s, lambda, counter);
 }
 
 // per-block partial sums of a product over n rows: as many as blocks at the most lanes per row

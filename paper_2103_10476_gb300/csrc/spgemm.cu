@@ -28,8 +28,8 @@ constexpr int kNumBins = 11;            // 32 .. 8192, the global bin and the se
 constexpr int kGlobalBin = 9;
 constexpr int kSegBin = 10;             // numeric phase: rows of A of more than kSegLen entries
 constexpr int kSegLen = 256;
-constexpr int kChainProducts = 32768;      // rows with more products take the chain path (B wide) or
-                                           // the segment kernels (B narrow) ...
+constexpr int kChainProducts = 32768;      // rows with more products take the chain path (B wide) ...
+constexpr int kSegProducts = 4096;         // ... or with more than these, the segment kernels (B narrow)
 constexpr int kSmemBudget = 96 * 1024;
 
 __device__ __forceinline__ unsigned hash_col(int j) { return (unsigned)j * 2654435761u; }
@@ -147,12 +147,13 @@ __global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin
         const int alen = arp[i + 1] - arp[i];
         const int64_t cnt = crp[i + 1] - crp[i];
         const int S = table_for(cnt);
-        // (with aci and brp: also the rows of more than kChainProducts products)
+        // (with aci and brp: also the rows of more than kSegProducts products, which a warp on a
+        // hash table would walk 32 products at a time)
         bool many = false;
         if (seg_wide && aci && alen <= kSegLen) {
             int64_t prod = 0;
             for (int e = arp[i]; e < arp[i + 1]; ++e) prod += brp[aci[e] + 1] - brp[aci[e]];
-            many = prod > kChainProducts;
+            many = prod > kSegProducts;
         }
         if (alen > kSegLen || (seg_wide && (S > kMaxSharedNum || many))) {
             b = kSegBin;
@@ -1549,8 +1550,9 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_segmax, 0, sizeof(int), s))) break;
         const bool seg_wide = B.ncol <= kSegCols;
-        const bool heavy_rows = h_ubstats[0] > (unsigned long long)kChainProducts;
-        const bool long_products = heavy_rows && h_ubstats[1] <= (unsigned long long)kChainTotal;
+        const bool heavy_rows = h_ubstats[0] > (unsigned long long)kSegProducts;
+        const bool long_products = h_ubstats[0] > (unsigned long long)kChainProducts &&
+                                   h_ubstats[1] <= (unsigned long long)kChainTotal;
         exact_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, A.rp, d_bin, d_binCount, d_tsize, d_segmax,
                                                           seg_wide ? 1 : 0, heavy_rows ? A.ci : nullptr, B.rp);
         note_launch();
