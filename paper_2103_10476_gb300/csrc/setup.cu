@@ -84,51 +84,67 @@ __global__ void diag_f32_kernel(int n, const double *d, float *df)
     df[i] = (x >= 1e-18 && x <= 1e18) ? (float)x : __int_as_float(0x7fc00000);
 }
 
-__global__ void strength_kernel(int n, const int *rp, const int *ci, const double *v, const double *d,
-                                const float *df, double theta, float thf, uint8_t *strong, uint8_t *removed,
-                                int *kept)
+// Eq. 7 for entry e = (i, j), j != i: the FP32 bounds decide it unless |a_ij| is within a
+// relative 2e-6 of the FP32 threshold (compared as bit patterns: FP64-pipe work avoided); then
+// the literal FP64 test, every operation rounded (the oracle's arithmetic, R1)
+__device__ __forceinline__ bool strong_entry(double vij, const double *d, int i, int j, float dfi, float dfj,
+                                             double theta, float thf)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    const int b = rp[i], e_end = rp[i + 1];
-    const float dfi = df[i];
-    int nkept = 0;
-    for (int base = b; base < e_end; base += 32) {
-        int e = base + lane;
-        bool rem = false;
-        if (e < e_end) {
-            int j = ci[e];
-            bool s = false;
-            if (j != i) {
-                if (theta == 0.0) {
-                    s = true;
-                } else {
-                    const unsigned long long ab =
-                        (unsigned long long)__double_as_longlong(v[e]) & 0x7fffffffffffffffull;
-                    const float t32 = __fmul_rn(thf, __fsqrt_rn(__fmul_rn(dfi, df[j])));
-                    int decided = 0;
-                    if (thf >= 1e-6f && t32 >= 1e-30f && t32 <= 1e30f && ab < 0x7ff0000000000000ull) {
-                        if (ab > f32_to_f64_bits(__fmul_rn(t32, 1.000002f))) decided = 1;
-                        else if (ab < f32_to_f64_bits(__fmul_rn(t32, 0.999998f))) decided = -1;
-                    }
-                    if (decided) {
-                        s = decided > 0;
-                    } else {
-                        const double prod = __dmul_rn(d[i], d[j]);
-                        const double thr = __dmul_rn(theta, __dsqrt_rn(prod));
-                        s = fabs(v[e]) >= thr;
-                    }
-                }
-                rem = !s;
-            }
-            strong[e] = s ? 1 : 0;
-            removed[e] = rem ? 1 : 0;
-        }
-        unsigned keep = __ballot_sync(kFull, e < e_end && !rem);
-        nkept += __popc(keep);
+    if (theta == 0.0) return true;
+    const unsigned long long ab = (unsigned long long)__double_as_longlong(vij) & 0x7fffffffffffffffull;
+    const float t32 = __fmul_rn(thf, __fsqrt_rn(__fmul_rn(dfi, dfj)));
+    if (thf >= 1e-6f && t32 >= 1e-30f && t32 <= 1e30f && ab < 0x7ff0000000000000ull) {
+        if (ab > f32_to_f64_bits(__fmul_rn(t32, 1.000002f))) return true;
+        if (ab < f32_to_f64_bits(__fmul_rn(t32, 0.999998f))) return false;
     }
-    if (lane == 0) kept[i] = nkept;
+    const double prod = __dmul_rn(d[i], d[j]);
+    const double thr = __dmul_rn(theta, __dsqrt_rn(prod));
+    return fabs(vij) >= thr;
+}
+
+// A block per kStrRows consecutive rows: its threads stride over the rows' entries (contiguous),
+// each entry's row found by binary search in the block's row pointers (shared memory), so loads
+// and the flag stores are coalesced however long or short the rows; kept counts per row by
+// shared-memory atomics.
+constexpr int kStrRows = 256;
+__global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, const int *ci, const double *v,
+                                                       const double *d, const float *df, double theta, float thf,
+                                                       uint8_t *strong, uint8_t *removed, int *kept)
+{
+    __shared__ int srp[kStrRows + 1];
+    __shared__ float sdf[kStrRows];
+    __shared__ int skept[kStrRows];
+    const int r0 = blockIdx.x * kStrRows;
+    if (r0 >= n) return;
+    const int nr = min(n - r0, kStrRows);
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        sdf[t] = df[r0 + t];
+        skept[t] = 0;
+    }
+    __syncthreads();
+    const int k0 = srp[0], k1 = srp[nr];
+    for (int e = k0 + (int)threadIdx.x; e < k1; e += blockDim.x) {
+        // the row of e: the last t with srp[t] <= e (an empty row shares its start with the next)
+        int lo = 0, hi = nr - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (srp[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const int i = r0 + lo;
+        const int j = ci[e];
+        bool st = false, rem = false;
+        if (j != i) {
+            st = strong_entry(v[e], d, i, j, sdf[lo], df[j], theta, thf);
+            rem = !st;
+        }
+        strong[e] = st ? 1 : 0;
+        removed[e] = rem ? 1 : 0;
+        if (!rem) atomicAdd(&skept[lo], 1);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) kept[r0 + t] = skept[t];
 }
 
 cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
@@ -138,8 +154,8 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
     float *df = nullptr;
     AMG_CUDA_TRY(cudaMallocAsync(&df, sizeof(float) * (size_t)A.n, s));
     diag_f32_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, d, df); note_launch();
-    strength_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta,
-                                                                     (float)theta, strong, removed, kept);
+    strength_kernel<<<(A.n + kStrRows - 1) / kStrRows, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta,
+                                                                    (float)theta, strong, removed, kept);
     note_launch();
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(df, s);
