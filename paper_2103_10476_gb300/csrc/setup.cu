@@ -7,6 +7,7 @@
 // of the same formulas bit for bit (decisions taken on them are then identical too).
 #include <math.h>
 
+#include <algorithm>
 #include <utility>
 
 #include "amg_internal.cuh"
@@ -102,21 +103,30 @@ __device__ __forceinline__ bool strong_entry(double vij, const double *d, int i,
     return fabs(vij) >= thr;
 }
 
-// A block per kStrRows consecutive rows: its threads stride over the rows' entries (contiguous),
+// A block per tile of consecutive rows (tile_rows: about kStrEntries entries, at most kStrRows
+// rows): its threads stride over the rows' entries (contiguous),
 // each entry's row found by binary search in the block's row pointers (shared memory), so loads
 // and the flag stores are coalesced however long or short the rows; kept counts per row by
 // shared-memory atomics.
-constexpr int kStrRows = 256;
+constexpr int kStrRows = 256;         // rows of a tile at most
+constexpr int kStrEntries = 4096;     // entries a tile aims at (16 a thread)
+
+// rows per tile for a matrix of n rows and nnz entries
+int tile_rows(int n, int64_t nnz)
+{
+    const double avg = n > 0 ? (double)nnz / n : 1.0;
+    return std::max(1, std::min(kStrRows, (int)(kStrEntries / std::max(avg, 1.0))));
+}
 __global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, const int *ci, const double *v,
                                                        const double *d, const float *df, double theta, float thf,
-                                                       uint8_t *strong, uint8_t *removed, int *kept)
+                                                       uint8_t *strong, uint8_t *removed, int *kept, int rpb)
 {
     __shared__ int srp[kStrRows + 1];
     __shared__ float sdf[kStrRows];
     __shared__ int skept[kStrRows];
-    const int r0 = blockIdx.x * kStrRows;
+    const int r0 = blockIdx.x * rpb;
     if (r0 >= n) return;
-    const int nr = min(n - r0, kStrRows);
+    const int nr = min(n - r0, rpb);
     for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t];
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
         sdf[t] = df[r0 + t];
@@ -154,8 +164,9 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
     float *df = nullptr;
     AMG_CUDA_TRY(cudaMallocAsync(&df, sizeof(float) * (size_t)A.n, s));
     diag_f32_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, d, df); note_launch();
-    strength_kernel<<<(A.n + kStrRows - 1) / kStrRows, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta,
-                                                                    (float)theta, strong, removed, kept);
+    const int rpb = tile_rows(A.n, A.nnz);
+    strength_kernel<<<(A.n + rpb - 1) / rpb, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta, (float)theta, strong,
+                                                          removed, kept, rpb);
     note_launch();
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(df, s);
@@ -265,45 +276,93 @@ cudaError_t coarse_coords(int nagg, const int *mstart, const int *members, const
 }
 
 // ------------------------------------------------------------------------------------ strong graph
-__global__ void sg_count_kernel(int n, const int *rp, const uint8_t *strong, int *cnt)
+// Row tiles as in strength_kernel: a block per tile of rows, threads strided over the rows'
+// entries (coalesced however short the rows), each entry's row by binary search in the block's
+// row pointers in shared memory.
+__device__ __forceinline__ int tile_row(int e, const int *srp, int nr)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    int c = 0;
-    for (int e = rp[i] + lane; e < rp[i + 1]; e += 32) c += strong[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kFull, c, o);
-    if (lane == 0) cnt[i] = c;
+    int lo = 0, hi = nr - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (srp[mid] <= e) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void sg_fill_kernel(int n, const int *rp, const int *ci, const uint8_t *strong, const int *grp,
-                               int *gci)
+// cnt[i] = strong entries of row i
+__global__ void __launch_bounds__(256) sg_count_kernel(int n, const int *rp, const uint8_t *strong, int *cnt, int rpb)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= n) return;
-    int out = grp[i];
-    for (int base = rp[i]; base < rp[i + 1]; base += 32) {
-        int e = base + lane;
-        bool s = e < rp[i + 1] && strong[e];
-        unsigned m = __ballot_sync(kFull, s);
-        if (s) gci[out + __popc(m & ((1u << lane) - 1u))] = ci[e];
-        out += __popc(m);
+    __shared__ int srp[kStrRows + 1];
+    __shared__ int sc[kStrRows];
+    const int r0 = blockIdx.x * rpb;
+    if (r0 >= n) return;
+    const int nr = min(n - r0, rpb);
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) sc[t] = 0;
+    __syncthreads();
+    for (int e = srp[0] + (int)threadIdx.x; e < srp[nr]; e += blockDim.x)
+        if (strong[e]) atomicAdd(&sc[tile_row(e, srp, nr)], 1);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) cnt[r0 + t] = sc[t];
+}
+
+// gci[grp[i] ...]: row i's strong columns in ascending order.  The block's entries go 256 at a
+// time; a block-wide scan of their strong flags gives each its rank among the strong entries of
+// the block so far, and the rank of its row's first entry (recorded when that entry's chunk was
+// scanned) turns it into the rank within the row.
+__global__ void __launch_bounds__(256) sg_fill_kernel(int n, const int *rp, const int *ci, const uint8_t *strong,
+                                                      const int *grp, int *gci, int rpb)
+{
+    __shared__ int srp[kStrRows + 1];
+    __shared__ int rowbase[kStrRows];
+    __shared__ int wsum[8];
+    __shared__ int chunk_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * rpb;
+    if (r0 >= n) return;
+    const int nr = min(n - r0, rpb);
+    for (int t = threadIdx.x; t <= nr; t += blockDim.x) srp[t] = rp[r0 + t];
+    if (threadIdx.x == 0) chunk_base = 0;
+    __syncthreads();
+    const int k0 = srp[0], k1 = srp[nr];
+    for (int c0 = k0; c0 < k1; c0 += blockDim.x) {
+        const int e = c0 + (int)threadIdx.x;
+        const bool valid = e < k1;
+        const int lo = valid ? tile_row(e, srp, nr) : 0;
+        const bool st = valid && strong[e];
+        const unsigned m = __ballot_sync(0xffffffffu, st);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int rank = chunk_base + __popc(m & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) rank += wsum[w];
+        // the first entry of a row records the block's strong count before it
+        if (valid && e == srp[lo]) rowbase[lo] = rank;
+        __syncthreads();
+        if (st) gci[grp[r0 + lo] + rank - rowbase[lo]] = ci[e];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < 8; ++w) t += wsum[w];
+            chunk_base += t;
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t strong_graph_counts(const DevCsr &A, const uint8_t *strong, int *cnt, cudaStream_t s)
 {
     if (A.n == 0) return cudaSuccess;
-    sg_count_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, strong, cnt); note_launch();
+    const int rpb = tile_rows(A.n, A.nnz);
+    sg_count_kernel<<<(A.n + rpb - 1) / rpb, 256, 0, s>>>(A.n, A.rp, strong, cnt, rpb); note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t strong_graph_fill(const DevCsr &A, const uint8_t *strong, const int *grp, int *gci, cudaStream_t s)
 {
     if (A.n == 0) return cudaSuccess;
-    sg_fill_kernel<<<grid_for((int64_t)A.n * 32, 256), 256, 0, s>>>(A.n, A.rp, A.ci, strong, grp, gci); note_launch();
+    const int rpb = tile_rows(A.n, A.nnz);
+    sg_fill_kernel<<<(A.n + rpb - 1) / rpb, 256, 0, s>>>(A.n, A.rp, A.ci, strong, grp, gci, rpb); note_launch();
     return cudaGetLastError();
 }
 
@@ -325,13 +384,14 @@ __global__ void mis_init_kernel(int n, uint64_t seed, int level, unsigned long l
     if (i < n) t0[i] = kStUndec | agg_priority(seed, level, i);
 }
 
-// one sub-warp of 8 lanes per vertex (no early exit: the shuffles use the full warp)
+// one sub-warp of 8 lanes per vertex (no early exit: the shuffles use the full warp).  Only the
+// vertices flagged in act: the ones an undecided vertex reads (itself and its neighbours).
 __global__ void mis_max_kernel(int n, const int *grp, const int *gci, const unsigned long long *in,
-                               unsigned long long *out)
+                               unsigned long long *out, const uint8_t *act)
 {
     const int sub = threadIdx.x & 7;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
-    const bool valid = i < n;
+    const bool valid = i < n && act[i];
     unsigned long long m = (valid && sub == 0) ? in[i] : 0ULL;
     if (valid) {
         for (int e = grp[i] + sub; e < grp[i + 1]; e += 8) {
@@ -347,8 +407,10 @@ __global__ void mis_max_kernel(int n, const int *grp, const int *gci, const unsi
     if (valid && sub == 0) out[i] = m;
 }
 
+// (a vertex still undecided flags itself and its neighbours in act_next: the next round's max
+// is needed there only)
 __global__ void mis_decide_kernel(int n, const int *grp, const int *gci, const unsigned long long *t1,
-                                  unsigned long long *t0, int *undecided)
+                                  unsigned long long *t0, int *undecided, uint8_t *act_next)
 {
     const int sub = threadIdx.x & 7;
     const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 3;
@@ -374,6 +436,11 @@ __global__ void mis_decide_kernel(int n, const int *grp, const int *gci, const u
         if (m == own) t0[i] = kStRoot | (own & kPrioMask);
         else if ((m >> 62) == 2ULL) t0[i] = own & kPrioMask;
         else und = 1;
+    }
+    const int still = __shfl_sync(kFull, und, 0, 8);
+    if (still) {
+        if (sub == 0) act_next[i] = 1;
+        for (int e = grp[i] + sub; e < grp[i + 1]; e += 8) act_next[gci[e]] = 1;
     }
     // block-level count of still-undecided vertices
     __shared__ int cnt;
@@ -454,13 +521,25 @@ cudaError_t aggregate_mis2(int n, const int *grp, const int *gci, uint64_t seed,
     AMG_CUDA_TRY(cudaGetLastError());
     // rounds go in pairs between looks at the undecided count (a round after the last decision
     // changes nothing), which halves the host round trips
+    // which vertices need the next round's max (every vertex in the first round)
+    uint8_t *act = nullptr;
+    AMG_CUDA_TRY(cudaMallocAsync(&act, 2 * (size_t)n, s));
+    struct Release {
+        uint8_t *p; cudaStream_t s;
+        ~Release() { cudaFreeAsync(p, s); }
+    } release{act, s};
+    uint8_t *act_cur = act, *act_next = act + n;
+    AMG_CUDA_TRY(cudaMemsetAsync(act_cur, 1, (size_t)n, s));
     int h_und = 1, rounds = 0;
     while (h_und > 0) {
         if (rounds >= 10000) return cudaErrorLaunchFailure;   // cannot happen: each round decides >= 1 vertex
         for (int q = 0; q < 2; ++q) {
             if (q == 1) AMG_CUDA_TRY(cudaMemsetAsync(w.counter, 0, sizeof(int), s));
-            mis_max_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t0, w.t1); note_launch();
-            mis_decide_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t1, w.t0, w.counter); note_launch();
+            AMG_CUDA_TRY(cudaMemsetAsync(act_next, 0, (size_t)n, s));
+            mis_max_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t0, w.t1, act_cur); note_launch();
+            mis_decide_kernel<<<grid_for((int64_t)n * 8, tb), tb, 0, s>>>(n, grp, gci, w.t1, w.t0, w.counter,
+                                                                          act_next); note_launch();
+            std::swap(act_cur, act_next);
         }
         AMG_CUDA_TRY(cudaGetLastError());
         AMG_CUDA_TRY(cudaMemcpyAsync(&h_und, w.counter, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -673,6 +752,21 @@ enum { LUMP_DIAG = 0, LUMP_KPLUS = 1, LUMP_DIAG_KMINUS = 2, LUMP_KPLUS_NEG = 3, 
 // time is one segment's chain of dependent additions instead of the whole row's.
 constexpr int kFilterLong = 256;
 
+// x > 0 and x < 0 decided on the bit pattern with integer instructions instead of FP64
+// comparisons (GB300's FP64 pipe is the filter's bound); the same answers for every double,
+// zeros, infinities and NaN included
+__device__ __forceinline__ bool dpos(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dneg(double x)
+{
+    const long long b = __double_as_longlong(x);
+    const long long m = b & 0x7fffffffffffffffLL;
+    return b < 0 && m != 0 && m <= 0x7ff0000000000000LL;
+}
+
 // The row's outcome from its sums (Eq. 6, or Algorithm 2 with offlmp)
 struct FilterOutcome {
     int flag = LUMP_DIAG;
@@ -729,10 +823,10 @@ __device__ __forceinline__ double filter_kept_value(double val, const FilterOutc
 {
     double nv = val;
     if (offlmp && o.flag != LUMP_FALLBACK) {
-        if (val > 0.0) {
+        if (dpos(val)) {
             if (o.zero_plus) nv = 0.0;
             else if (o.flag == LUMP_KPLUS || o.flag == LUMP_KPLUS_NEG) nv = val * o.fplus;
-        } else if (val < 0.0 && o.flag == LUMP_DIAG_KMINUS) {
+        } else if (dneg(val) && o.flag == LUMP_DIAG_KMINUS) {
             nv = val * o.fminus;
         }
     }
@@ -776,8 +870,8 @@ __device__ __forceinline__ void filter_row(int i, int b, int e_end, const int *c
         if (removed[e]) {
             r = r + val;
         } else if (offlmp) {
-            if (val > 0.0) { kp = kp + val; ++nkp; }
-            else if (val < 0.0) { km = km + val; ++nkm; }
+            if (dpos(val)) { kp = kp + val; ++nkp; }
+            else if (dneg(val)) { km = km + val; ++nkm; }
         }
     }
     const FilterOutcome o = filter_outcome(aii, r, kp, km, offabs, nkp, nkm, offlmp, tau);
@@ -821,6 +915,8 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
         int cp = 0, cm = 0, hd = 0;
         if (q < nseg) {
             const int e0 = b + q * kFilterLong, e1 = min(e_end, e0 + kFilterLong);
+            // (unrolled: a lane's loads of eight entries in flight at once; the sums stay in order)
+#pragma unroll 8
             for (int e = e0; e < e1; ++e) {
                 const int j = ci[e];
                 const double val = v[e];
@@ -833,8 +929,8 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
                 if (removed[e]) {
                     sr = sr + val;
                 } else if (offlmp) {
-                    if (val > 0.0) { skp = skp + val; ++cp; }
-                    else if (val < 0.0) { skm = skm + val; ++cm; }
+                    if (dpos(val)) { skp = skp + val; ++cp; }
+                    else if (dneg(val)) { skm = skm + val; ++cm; }
                 }
             }
         }
@@ -863,6 +959,7 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
         const int q = q0 + lane;
         const int e0 = b + q * kFilterLong, e1 = q < nseg ? min(e_end, e0 + kFilterLong) : e0;
         int kept = 0;
+#pragma unroll 8
         for (int e = e0; e < e1; ++e) kept += (ci[e] == i || !removed[e]);
         int incl = kept;
 #pragma unroll
@@ -871,6 +968,7 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
             if (lane >= o2) incl += y;
         }
         int out = base + incl - kept;
+#pragma unroll 8
         for (int e = e0; e < e1; ++e) {
             const int j = ci[e];
             double nv;
@@ -895,6 +993,7 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
             double sd = 0.0, ss = 0.0;
             if (q < nseg2) {
                 const int e0 = ab + q * kFilterLong, e1 = min(ae, e0 + kFilterLong);
+#pragma unroll 8
                 for (int e = e0; e < e1; ++e) {
                     const double nv = bv[e];
                     sd = sd + fabs(nv);
