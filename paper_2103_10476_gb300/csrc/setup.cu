@@ -111,11 +111,14 @@ __device__ __forceinline__ bool strong_entry(double vij, const double *d, int i,
 constexpr int kStrRows = 256;         // rows of a tile at most
 constexpr int kStrEntries = 4096;     // entries a tile aims at (16 a thread)
 
-// rows per tile for a matrix of n rows and nnz entries
+// rows per tile for a matrix of n rows and nnz entries (and at least kStrBlocks tiles: the
+// stalled coarse levels' few thousand rows would otherwise fill a fifth of the multiprocessors)
+constexpr int kStrBlocks = 608;
 int tile_rows(int n, int64_t nnz)
 {
     const double avg = n > 0 ? (double)nnz / n : 1.0;
-    return std::max(1, std::min(kStrRows, (int)(kStrEntries / std::max(avg, 1.0))));
+    const int spread = (int)(((int64_t)n + kStrBlocks - 1) / kStrBlocks);
+    return std::max(1, std::min(std::min(kStrRows, spread), (int)(kStrEntries / std::max(avg, 1.0))));
 }
 __global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, const int *ci, const double *v,
                                                        const double *d, const float *df, double theta, float thf,
@@ -858,6 +861,8 @@ __device__ __forceinline__ void filter_row(int i, int b, int e_end, const int *c
     // pass 1: row sums in ascending order
     double r = 0.0, kp = 0.0, km = 0.0, offabs = 0.0, aii = 0.0;
     int nkp = 0, nkm = 0, has_diag = 0;
+    // (unrolled: eight entries' loads in flight at once; the sums stay in order)
+#pragma unroll 8
     for (int e = b; e < e_end; ++e) {
         const int j = ci[e];
         const double val = v[e];
@@ -878,6 +883,7 @@ __device__ __forceinline__ void filter_row(int i, int b, int e_end, const int *c
     // pass 2: the kept entries, and the 1-norm sums over them in ascending order
     int out = brp[i];
     double dsum = 0.0, ssum = 0.0;
+#pragma unroll 8
     for (int e = b; e < e_end; ++e) {
         const int j = ci[e];
         double nv;

@@ -9,6 +9,7 @@
 // Rows are binned by table size so each launch uses one size: the symbolic phase by an
 // upper bound (min(products, columns)), the numeric phase by the exact count.
 #include <algorithm>
+#include <climits>
 #include <functional>
 #include <mutex>
 #include <stdio.h>
@@ -83,8 +84,10 @@ __device__ __forceinline__ void bin_count_block(int b, bool valid, int *binCount
 // 64 entries (stalled levels hold rows of thousands) is counted by its whole warp instead, the
 // warp taking its long rows one after another.  (ubstats, when given: [0] the most products of a
 // row, [1] all products, warp-reduced first.)
+// dense_above: rows of more products go to the global bin (whose symbolic kernel is then a
+// block per row with dense counters over B's columns; B narrow enough for them)
 __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
-                          int *tsize, unsigned long long *ubstats = nullptr)
+                          int *tsize, unsigned long long *ubstats = nullptr, long long dense_above = LLONG_MAX)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -115,7 +118,7 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
     if (valid) {
         const int64_t need = ub < ncolB ? ub : ncolB;
         const int S = table_for(need);
-        b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
+        b = S > kMaxSharedSym || ub > dense_above ? kGlobalBin : bin_of_table(S);
         bin[i] = b;
         tsize[i] = S;
     }
@@ -289,9 +292,61 @@ __global__ void symbolic_global_kernel(int cnt, const int *rows, const int *toff
 }
 
 // ------------------------------------------------------------------------------------ numeric
+// The row's entries of C from the occupied slots of its table, in ascending column order: each
+// column's rank is the number of occupied columns below it, read from a bitmap over B's columns
+// (bm: `words` words, then as many exclusive prefix counts of the words).  Two passes over the
+// table instead of a compaction and a sort.  Returns false (and counts an overflow) when the
+// number of columns differs from the symbolic phase's.
+__device__ bool emit_by_bitmap(const int *keys, const double *vals, int S, unsigned *bm, int words, int out, int nc,
+                               int *cci, double *cv, int *overflow)
+{
+    const int lane = threadIdx.x & 31;
+    int *pre = reinterpret_cast<int *>(bm + words);
+    for (int w = lane; w < words; w += 32) bm[w] = 0u;
+    __syncwarp();
+    for (int t = lane; t < S; t += 32) {
+        const int key = keys[t];
+        if (key != -1) atomicOr(&bm[key >> 5], 1u << (key & 31));
+    }
+    __syncwarp();
+    const int per = (words + 31) >> 5;
+    const int w0 = lane * per, w1 = min(words, w0 + per);
+    int c = 0;
+    for (int w = w0; w < w1; ++w) c += __popc(bm[w]);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
+    }
+    int run = incl - c;
+    for (int w = w0; w < w1; ++w) {
+        pre[w] = run;
+        run += __popc(bm[w]);
+    }
+    const int total = __shfl_sync(kFullMask, incl, 31);
+    __syncwarp();
+    if (total != nc) {
+        if (lane == 0) atomicAdd(overflow, 1);
+        return false;
+    }
+    for (int t = lane; t < S; t += 32) {
+        const int key = keys[t];
+        if (key != -1) {
+            const int w = key >> 5;
+            const int rank = pre[w] + __popc(bm[w] & ((1u << (key & 31)) - 1u));
+            cci[out + rank] = key;
+            cv[out + rank] = vals[t];
+        }
+    }
+    return true;
+}
+
+// bm: nullptr, or the warp's bitmap over B's columns (words words + words prefix counts), which
+// then orders the row's entries (emit_by_bitmap)
 __device__ void numeric_row(int i, const int *arp, const int *aci, const double *av, const int *brp, const int *bci,
                             const double *bv, int *keys, double *vals, int S, const int *crp, int *cci, double *cv,
-                            int *overflow)
+                            int *overflow, unsigned *bm = nullptr, int words = 0)
 {
     const int lane = threadIdx.x & 31;
     for (int t = lane; t < S; t += 32) { keys[t] = -1; vals[t] = 0.0; }
@@ -333,6 +388,10 @@ __device__ void numeric_row(int i, const int *arp, const int *aci, const double 
                 __syncwarp();
             }
         }
+    }
+    if (bm) {
+        emit_by_bitmap(keys, vals, S, bm, words, crp[i], crp[i + 1] - crp[i], cci, cv, overflow);
+        return;
     }
     // compact occupied slots to the front, in slot order
     int base = 0;
@@ -395,19 +454,23 @@ __device__ void numeric_row(int i, const int *arp, const int *aci, const double 
     }
 }
 
+// words > 0: each warp also holds a bitmap of `words` words over B's columns (and their prefix
+// counts) after the tables, which orders its rows' entries
 template <int S>
 __global__ void numeric_shared_kernel(int cnt, const int *rows, const int *arp, const int *aci, const double *av,
                                       const int *brp, const int *bci, const double *bv, const int *crp, int *cci,
-                                      double *cv, int *overflow)
+                                      double *cv, int *overflow, int words)
 {
     extern __shared__ double smem_num[];
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     double *vals = smem_num + w * S;
     int *keys = reinterpret_cast<int *>(smem_num + warps * S) + w * S;
+    unsigned *bm = words > 0 ? reinterpret_cast<unsigned *>(smem_num + warps * S) + warps * S + 2 * w * words
+                             : nullptr;
     const int row_slot = blockIdx.x * warps + w;
     if (row_slot >= cnt) return;
-    numeric_row(rows[row_slot], arp, aci, av, brp, bci, bv, keys, vals, S, crp, cci, cv, overflow);
+    numeric_row(rows[row_slot], arp, aci, av, brp, bci, bv, keys, vals, S, crp, cci, cv, overflow, bm, words);
 }
 
 __global__ void numeric_global_kernel(int cnt, const int *rows, const int *toff, const int *tsize, int *gkeys,
@@ -444,6 +507,7 @@ constexpr long long kChainTotal = 16 << 20;  // ... when the whole product has a
 // stalled level's dense rows) are deferred to whole warps, so no thread walks a long chain of
 // dependent loads alone.  blockDim.x <= kDenseThreads.
 constexpr int kDenseThreads = 512;
+constexpr long long kDenseSymProducts = 2048;   // symbolic: rows of more products by dense counters
 template <typename F>
 __device__ __forceinline__ void row_products(int i, const int *arp, const int *aci, const int *brp, const int *bci,
                                              F visit)
@@ -986,9 +1050,48 @@ __device__ __forceinline__ int seg_find(const int *c, int n, int j)
     return lo;
 }
 
+// exclusive prefix sum of one int per thread over a block of kSegThreads threads
+__device__ __forceinline__ int seg_block_scan(int v, int *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFullMask, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int x = lane < kSegThreads / 32 ? wsum[lane] : 0;
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFullMask, xi, o);
+            if (lane >= o) xi += y;
+        }
+        if (lane < kSegThreads / 32) wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    return incl - v + wsum[warp];
+}
+
+// dynamic shared memory of seg_numeric_kernel: the dense accumulator (DENSE), then the staged
+// columns (int), values (double), bucket lists (uint16) and k indices (uint8) of kSegStage entries
+constexpr size_t kSegStageBytes = (size_t)kSegStage * (4 + 8 + 2 + 1);
+constexpr size_t seg_numeric_smem(bool dense) { return (dense ? sizeof(double) * kSegCols : 0) + kSegStageBytes; }
+
 // segment q = blockIdx.y of segmented row r = blockIdx.x: S[soff[r] + q nc + t] = the sum over
 // the segment's terms of entry t, fma in ascending k from 0 (DENSE: accumulator over B's
-// columns in shared memory; else in the scratch slice itself, positions by binary search)
+// columns in shared memory; else in the scratch slice itself, positions by binary search).
+// The segment's k's go in chunks whose rows of B fit the stage together.  A staged chunk's
+// products fall in kSegThreads buckets by their accumulator position; each thread sorts its
+// bucket by product index (products are staged in ascending k, and a row of B holds a column
+// once, so this is ascending k within every position) and applies its fma's in that order:
+// the sums of a per-k sweep with a barrier after every k, without the barriers.  Chunks of k's
+// with many terms each keep the per-k sweep (a few barriers, and buckets of one position's many
+// terms would be long serial sorts).  A k whose row of B alone exceeds the stage is swept
+// straight from global memory (its columns are distinct).
 template <bool DENSE>
 __global__ void __launch_bounds__(kSegThreads) seg_numeric_kernel(int cnt, const int *rows, const int *arp,
                                                                    const int *aci, const double *av, const int *brp,
@@ -998,6 +1101,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_numeric_kernel(int cnt, const
     extern __shared__ __align__(16) unsigned char seg_num_s[];
     __shared__ int sk[kSegLen], spre[kSegLen + 1];
     __shared__ double sa[kSegLen];
+    __shared__ int bfill[kSegThreads], wsum[kSegThreads / 32];
     __shared__ int chunk_end;
     const int r = blockIdx.x, q = blockIdx.y;
     if (r >= cnt) return;
@@ -1010,27 +1114,30 @@ __global__ void __launch_bounds__(kSegThreads) seg_numeric_kernel(int cnt, const
     double *acc = DENSE ? (double *)seg_num_s : slice;
     int *scol = (int *)(seg_num_s + (DENSE ? sizeof(double) * kSegCols : 0));
     double *sval = (double *)(scol + kSegStage);
+    unsigned short *bucket = (unsigned short *)(sval + kSegStage);
+    unsigned char *st = (unsigned char *)(bucket + kSegStage);
     const int *rc = cci + out0;
-    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    const int tid = threadIdx.x;
+    for (int t = tid; t < nc; t += blockDim.x) {
         if (DENSE) acc[rc[t]] = 0.0;
         else acc[t] = 0.0;
     }
     const int m = min(kSegLen, alen - q * kSegLen);
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    for (int t = tid; t < m; t += blockDim.x) {
         const int k = aci[a0 + q * kSegLen + t];
         sk[t] = k;
         sa[t] = av[a0 + q * kSegLen + t];
         spre[t + 1] = brp[k + 1] - brp[k];
     }
-    if (threadIdx.x == 0) spre[0] = 0;
+    if (tid == 0) spre[0] = 0;
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (tid == 0)
         for (int t = 0; t < m; ++t) spre[t + 1] += spre[t];
     __syncthreads();
     int kk = 0;
     while (kk < m) {
         // the next k's whose rows of B fit the stage together (at least one)
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             int ke = kk + 1;
             while (ke < m && spre[ke + 1] - spre[kk] <= kSegStage) ++ke;
             chunk_end = ke;
@@ -1038,41 +1145,86 @@ __global__ void __launch_bounds__(kSegThreads) seg_numeric_kernel(int cnt, const
         __syncthreads();
         const int ke = chunk_end;
         const int base = spre[kk], total = spre[ke] - base;
-        const bool staged = total <= kSegStage;
-        if (staged) {
-            for (int p = threadIdx.x; p < total; p += blockDim.x) {
-                // the k of staged entry p: the last t in [kk, ke) with spre[t] - base <= p
-                int lo = kk, hi = ke - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (spre[mid] - base <= p) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int f = brp[sk[lo]] + (p - (spre[lo] - base));
-                scol[p] = bci[f];
-                sval[p] = bv[f];
-            }
-            __syncthreads();
-        }
-        for (int t = kk; t < ke; ++t) {
-            const double a = sa[t];
-            const int len = spre[t + 1] - spre[t];
-            const int fb = brp[sk[t]];
-            for (int u = threadIdx.x; u < len; u += blockDim.x) {
-                const int j = staged ? scol[spre[t] - base + u] : bci[fb + u];
-                const double b = staged ? sval[spre[t] - base + u] : bv[fb + u];
+        if (total > kSegStage) {
+            // one k (ke == kk + 1): its columns are distinct, every term at once
+            const double a = sa[kk];
+            const int fb = brp[sk[kk]];
+            for (int u = tid; u < total; u += blockDim.x) {
+                const int j = bci[fb + u];
                 const int pos = DENSE ? j : seg_find(rc, nc, j);
-                acc[pos] = __fma_rn(a, b, acc[pos]);
+                acc[pos] = __fma_rn(a, bv[fb + u], acc[pos]);
             }
             __syncthreads();
+            kk = ke;
+            continue;
         }
+        // buckets when the chunk's k's average fewer than 16 terms (a barrier per k would leave
+        // most threads idle); else one k after another, a barrier after each
+        const bool bucketed = total < 16 * (ke - kk);
+        if (bucketed) bfill[tid] = 0;
+        __syncthreads();
+        for (int p = tid; p < total; p += blockDim.x) {
+            // the k of staged entry p: the last t in [kk, ke) with spre[t] - base <= p
+            int lo = kk, hi = ke - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (spre[mid] - base <= p) lo = mid;
+                else hi = mid - 1;
+            }
+            const int f = brp[sk[lo]] + (p - (spre[lo] - base));
+            const int j = bci[f];
+            const int pos = DENSE ? j : seg_find(rc, nc, j);
+            scol[p] = pos;
+            sval[p] = bv[f];
+            st[p] = (unsigned char)lo;
+            if (bucketed) atomicAdd(&bfill[pos & (kSegThreads - 1)], 1);
+        }
+        __syncthreads();
+        if (!bucketed) {
+            for (int t = kk; t < ke; ++t) {
+                const double a = sa[t];
+                const int p0 = spre[t] - base, len = spre[t + 1] - spre[t];
+                for (int u = tid; u < len; u += blockDim.x) {
+                    const int pos = scol[p0 + u];
+                    acc[pos] = __fma_rn(a, sval[p0 + u], acc[pos]);
+                }
+                __syncthreads();
+            }
+            kk = ke;
+            continue;
+        }
+        const int mine = bfill[tid];
+        const int b0 = seg_block_scan(mine, wsum);
+        bfill[tid] = b0;
+        __syncthreads();
+        for (int p = tid; p < total; p += blockDim.x)
+            bucket[atomicAdd(&bfill[scol[p] & (kSegThreads - 1)], 1)] = (unsigned short)p;
+        __syncthreads();
+        // this thread's bucket: insertion sort by product index, then its fma's in that order
+        unsigned short *bk = bucket + b0;
+        for (int x = 1; x < mine; ++x) {
+            const unsigned short v = bk[x];
+            int y = x - 1;
+            while (y >= 0 && bk[y] > v) {
+                bk[y + 1] = bk[y];
+                --y;
+            }
+            bk[y + 1] = v;
+        }
+        for (int x = 0; x < mine; ++x) {
+            const int p = bk[x];
+            const int pos = scol[p];
+            acc[pos] = __fma_rn(sa[st[p]], sval[p], acc[pos]);
+        }
+        __syncthreads();
         kk = ke;
     }
     if (DENSE)
-        for (int t = threadIdx.x; t < nc; t += blockDim.x) slice[t] = acc[rc[t]];
+        for (int t = tid; t < nc; t += blockDim.x) slice[t] = acc[rc[t]];
 }
 
-// C's values of segmented row r = blockIdx.x: each entry's segment sums added in order
+// C's values of segmented row r = blockIdx.x: each entry's segment sums added in order (the
+// row's entries strided over the blockIdx.y blocks of the row)
 __global__ void seg_combine_kernel(int cnt, const int *rows, const int *arp, const int *crp, const int *soff,
                                    const double *S, double *cv)
 {
@@ -1082,7 +1234,7 @@ __global__ void seg_combine_kernel(int cnt, const int *rows, const int *arp, con
     const int nseg = (arp[i + 1] - arp[i] + kSegLen - 1) / kSegLen;
     const int out0 = crp[i], nc = crp[i + 1] - out0;
     const double *sl = S + soff[r];
-    for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < nc; t += gridDim.y * blockDim.x) {
         double c = sl[t];
         for (int q = 1; q < nseg; ++q) c = c + sl[(size_t)q * nc + t];
         cv[out0 + t] = c;
@@ -1141,6 +1293,13 @@ cudaError_t launch_symbolic(int cnt, const int *rows, const DevCsr &A, const Dev
     return cudaGetLastError();
 }
 
+// Rows of more than 256 entries of C (tables of 1024 slots and up) order their entries by a
+// bitmap over B's columns when B has at most kBitmapCols columns: a warp's sort of 512-2048
+// entries (rank counting or a bitonic network, thousands of dependent shared-memory steps) was
+// the long pole of the stalled coarse levels' Galerkin products.
+constexpr int kBitmapCols = 8192;       // 2 KB a warp: two blocks of 1024-slot tables still fit an SM
+constexpr int kBitmapMinTable = 1024;
+
 template <int S>
 cudaError_t launch_numeric(int cnt, const int *rows, const DevCsr &A, const DevCsr &B, DevCsr &C, int *ovf,
                            cudaStream_t s)
@@ -1148,11 +1307,13 @@ cudaError_t launch_numeric(int cnt, const int *rows, const DevCsr &A, const DevC
     int warps = kSmemBudget / (S * 12);
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
-    size_t smem = (size_t)warps * S * 12;
+    const int words = S >= kBitmapMinTable && B.ncol <= kBitmapCols ? (B.ncol + 31) / 32 : 0;
+    size_t smem = (size_t)warps * ((size_t)S * 12 + (size_t)words * 8);
     AMG_CUDA_TRY(cudaFuncSetAttribute(numeric_shared_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     numeric_shared_kernel<S><<<(cnt + warps - 1) / warps, warps * 32, smem, s>>>(cnt, rows, A.rp, A.ci, A.v, B.rp,
-                                                                                B.ci, B.v, C.rp, C.ci, C.v, ovf); note_launch();
+                                                                                B.ci, B.v, C.rp, C.ci, C.v, ovf,
+                                                                                words); note_launch();
     return cudaGetLastError();
 }
 
@@ -1401,10 +1562,10 @@ cudaError_t seg_attr()
                                     kDenseCols * (int)sizeof(int));
         if (attr == cudaSuccess)
             attr = cudaFuncSetAttribute(seg_numeric_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(sizeof(double) * kSegCols + 12 * kSegStage));
+                                        (int)seg_numeric_smem(true));
         if (attr == cudaSuccess)
             attr = cudaFuncSetAttribute(seg_numeric_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        12 * kSegStage);
+                                        (int)seg_numeric_smem(false));
     });
     return attr;
 }
@@ -1458,13 +1619,15 @@ cudaError_t numeric_segmented(const DevCsr &A, const DevCsr &B, DevCsr &C, const
                                                             gflags); note_launch();
         const dim3 grid(cnt, std::max(1, (segmax + kSegLen - 1) / kSegLen));
         if (B.ncol <= kSegCols) {
-            seg_numeric_kernel<true><<<grid, kSegThreads, sizeof(double) * kSegCols + 12 * kSegStage, s>>>(
+            seg_numeric_kernel<true><<<grid, kSegThreads, seg_numeric_smem(true), s>>>(
                 cnt, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, soff, S); note_launch();
         } else {
-            seg_numeric_kernel<false><<<grid, kSegThreads, 12 * kSegStage, s>>>(
+            seg_numeric_kernel<false><<<grid, kSegThreads, seg_numeric_smem(false), s>>>(
                 cnt, rows, A.rp, A.ci, A.v, B.rp, B.ci, B.v, C.rp, C.ci, soff, S); note_launch();
         }
-        seg_combine_kernel<<<cnt, 256, 0, s>>>(cnt, rows, A.rp, C.rp, soff, S, C.v); note_launch();
+        // about four blocks a multiprocessor over all the rows' entries
+        const dim3 cgrid(cnt, std::max(1, std::min(32, 608 / cnt)));
+        seg_combine_kernel<<<cgrid, 128, 0, s>>>(cnt, rows, A.rp, C.rp, soff, S, C.v); note_launch();
         e = cudaGetLastError();
     } while (0);
     if (ws) sc.give(ws);
@@ -1508,7 +1671,11 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_ovf, 0, sizeof(int), s))) break;
         if ((e = cudaMemsetAsync(d_ubstats, 0, 2 * sizeof(unsigned long long), s))) break;
-        ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize, d_ubstats);
+        // rows of many products: one warp walks a hash table 32 products at a time (thousands
+        // of dependent steps on a stalled level's few long rows); a block with dense counters
+        // takes them when B is narrow enough
+        ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize, d_ubstats,
+                                                    B.ncol <= kDenseCols ? kDenseSymProducts : LLONG_MAX);
         note_launch();
         if ((e = cudaMemcpyAsync(h_ubstats, d_ubstats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s))) break;
         if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
