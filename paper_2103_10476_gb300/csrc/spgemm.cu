@@ -25,6 +25,9 @@ constexpr unsigned kFullMask = 0xffffffffu;
 constexpr int kMinTable = 32;
 constexpr int kMaxSharedSym = 8192;     // symbolic: 4 bytes per slot
 constexpr int kMaxSharedNum = 4096;     // numeric: 12 bytes per slot
+constexpr int kCapTable = 1024;         // symbolic: the first table of a row whose bound asks more
+constexpr int kCapRows = 32768;         // ... in products of at least this many rows (a second round
+                                        // costs a host round trip that small products do not repay)
 constexpr int kNumBins = 11;            // 32 .. 8192, the global bin and the segmented rows
 constexpr int kGlobalBin = 9;
 constexpr int kSegBin = 10;             // numeric phase: rows of A of more than kSegLen entries
@@ -86,8 +89,12 @@ __device__ __forceinline__ void bin_count_block(int b, bool valid, int *binCount
 // row, [1] all products, warp-reduced first.)
 // dense_above: rows of more products go to the global bin (whose symbolic kernel is then a
 // block per row with dense counters over B's columns; B narrow enough for them)
+// cap_table > 0: a row whose bound asks for a larger table goes to the bin of cap_table slots
+// first (tsize keeps the bound's size; ubstats[2] counts such rows): the symbolic phase counts
+// it there unless it holds more than cap_table / 2 columns, and sends it back to its own bin then
 __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp, int ncolB, int *bin, int *binCount,
-                          int *tsize, unsigned long long *ubstats = nullptr, long long dense_above = LLONG_MAX)
+                          int *tsize, unsigned long long *ubstats = nullptr, long long dense_above = LLONG_MAX,
+                          int cap_table = 0)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -115,12 +122,24 @@ __global__ void ub_kernel(int n, const int *arp, const int *aci, const int *brp,
         if (lane == src) ub = part;
     }
     int b = 0;
+    bool capped = false;
     if (valid) {
         const int64_t need = ub < ncolB ? ub : ncolB;
         const int S = table_for(need);
-        b = S > kMaxSharedSym || ub > dense_above ? kGlobalBin : bin_of_table(S);
+        if (ub > dense_above) {
+            b = kGlobalBin;
+        } else if (cap_table > 0 && S > cap_table) {
+            b = bin_of_table(cap_table);
+            capped = true;
+        } else {
+            b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
+        }
         bin[i] = b;
         tsize[i] = S;
+    }
+    if (ubstats && cap_table > 0) {
+        const unsigned cm = __ballot_sync(kFullMask, capped);
+        if (lane == 0 && cm) atomicAdd(&ubstats[2], (unsigned long long)__popc(cm));
     }
     if (ubstats) {
         unsigned long long mx = (unsigned long long)ub, sm = (unsigned long long)ub;
@@ -165,6 +184,22 @@ __global__ void exact_bin_kernel(int n, const int *crp, const int *arp, int *bin
         } else {
             b = S > kMaxSharedNum ? kGlobalBin : bin_of_table(S);
             tsize[i] = S;
+        }
+        bin[i] = b;
+    }
+    bin_count_block(b, i < n, binCount);
+}
+
+// The symbolic phase's second round: a capped row that stopped (count -1) to the bin of its
+// own table size; every other row to kSegBin, which the symbolic phase does not run
+__global__ void retry_bin_kernel(int n, const int *ccnt, const int *tsize, int *bin, int *binCount)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = kSegBin;
+    if (i < n) {
+        if (ccnt[i] < 0) {
+            const int S = tsize[i];
+            b = S > kMaxSharedSym ? kGlobalBin : bin_of_table(S);
         }
         bin[i] = b;
     }
@@ -231,13 +266,15 @@ __device__ __forceinline__ ProductBatch product_at(int q, int total, int incl, i
     return pb;
 }
 
+// capped: the row's bound asked for a larger table; it stops, with ccnt[i] = -1, once it holds
+// more than S / 2 columns (a batch adds at most 32, so the table never fills)
 __device__ void symbolic_row(int i, const int *arp, const int *aci, const int *brp, const int *bci, int *keys, int S,
-                             int *ccnt, int *overflow)
+                             int *ccnt, int *overflow, bool capped = false)
 {
     const int lane = threadIdx.x & 31;
     for (int t = lane; t < S; t += 32) keys[t] = -1;
     __syncwarp();
-    int mine = 0;
+    int mine = 0, held = 0;
     const int ae = arp[i + 1];
     for (int eb = arp[i]; eb < ae; eb += 32) {
         const int e = eb + lane;
@@ -257,10 +294,18 @@ __device__ void symbolic_row(int i, const int *arp, const int *aci, const int *b
         const int excl = incl - len;
         for (int qb = 0; qb < total; qb += 32) {
             ProductBatch pb = product_at<false>(qb + lane, total, incl, excl, fb, 0.0, bci, nullptr);
+            bool fresh = false;
             if (pb.valid) {
-                bool fresh;
                 hash_insert(keys, S, pb.j, fresh, overflow);
                 mine += fresh;
+            }
+            if (capped) {
+                held += __popc(__ballot_sync(kFullMask, fresh));
+                if (held > S / 2) {
+                    if (lane == 0) ccnt[i] = -1;
+                    __syncwarp();
+                    return;
+                }
             }
         }
     }
@@ -270,15 +315,17 @@ __device__ void symbolic_row(int i, const int *arp, const int *aci, const int *b
     __syncwarp();
 }
 
+// tsize (when given): the rows' own table sizes; a row of a larger one is capped here
 template <int S>
 __global__ void symbolic_shared_kernel(int cnt, const int *rows, const int *arp, const int *aci, const int *brp,
-                                       const int *bci, int *ccnt, int *overflow)
+                                       const int *bci, int *ccnt, int *overflow, const int *tsize)
 {
     extern __shared__ int smem_keys[];
     const int w = threadIdx.x >> 5;
     const int row_slot = blockIdx.x * (blockDim.x >> 5) + w;
     if (row_slot >= cnt) return;
-    symbolic_row(rows[row_slot], arp, aci, brp, bci, smem_keys + w * S, S, ccnt, overflow);
+    const int i = rows[row_slot];
+    symbolic_row(i, arp, aci, brp, bci, smem_keys + w * S, S, ccnt, overflow, tsize && tsize[i] > S);
 }
 
 __global__ void symbolic_global_kernel(int cnt, const int *rows, const int *toff, const int *tsize, int *gkeys,
@@ -1280,7 +1327,7 @@ cudaError_t make_bins(int n, int *d_bin, int *d_binCount, int *d_binFill, int *d
 
 template <int S>
 cudaError_t launch_symbolic(int cnt, const int *rows, const DevCsr &A, const DevCsr &B, int *ccnt, int *ovf,
-                            cudaStream_t s)
+                            const int *tsize, cudaStream_t s)
 {
     int warps = kSmemBudget / (S * 4);
     if (warps > 8) warps = 8;
@@ -1289,7 +1336,7 @@ cudaError_t launch_symbolic(int cnt, const int *rows, const DevCsr &A, const Dev
     AMG_CUDA_TRY(cudaFuncSetAttribute(symbolic_shared_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
     symbolic_shared_kernel<S><<<(cnt + warps - 1) / warps, warps * 32, smem, s>>>(cnt, rows, A.rp, A.ci, B.rp, B.ci,
-                                                                                 ccnt, ovf); note_launch();
+                                                                                 ccnt, ovf, tsize); note_launch();
     return cudaGetLastError();
 }
 
@@ -1318,18 +1365,18 @@ cudaError_t launch_numeric(int cnt, const int *rows, const DevCsr &A, const DevC
 }
 
 cudaError_t symbolic_bin(int b, int cnt, const int *rows, const DevCsr &A, const DevCsr &B, int *ccnt, int *ovf,
-                         cudaStream_t s)
+                         cudaStream_t s, const int *tsize = nullptr)
 {
     switch (b) {
-    case 0: return launch_symbolic<32>(cnt, rows, A, B, ccnt, ovf, s);
-    case 1: return launch_symbolic<64>(cnt, rows, A, B, ccnt, ovf, s);
-    case 2: return launch_symbolic<128>(cnt, rows, A, B, ccnt, ovf, s);
-    case 3: return launch_symbolic<256>(cnt, rows, A, B, ccnt, ovf, s);
-    case 4: return launch_symbolic<512>(cnt, rows, A, B, ccnt, ovf, s);
-    case 5: return launch_symbolic<1024>(cnt, rows, A, B, ccnt, ovf, s);
-    case 6: return launch_symbolic<2048>(cnt, rows, A, B, ccnt, ovf, s);
-    case 7: return launch_symbolic<4096>(cnt, rows, A, B, ccnt, ovf, s);
-    case 8: return launch_symbolic<8192>(cnt, rows, A, B, ccnt, ovf, s);
+    case 0: return launch_symbolic<32>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 1: return launch_symbolic<64>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 2: return launch_symbolic<128>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 3: return launch_symbolic<256>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 4: return launch_symbolic<512>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 5: return launch_symbolic<1024>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 6: return launch_symbolic<2048>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 7: return launch_symbolic<4096>(cnt, rows, A, B, ccnt, ovf, tsize, s);
+    case 8: return launch_symbolic<8192>(cnt, rows, A, B, ccnt, ovf, tsize, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1658,8 +1705,8 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     int *d_bin = work, *d_tsize = work + n, *d_perm = work + 2 * n;
     int *d_binCount = work + 3 * n, *d_binFill = d_binCount + kNumBins + 1, *d_binStart = d_binFill + kNumBins + 1;
     int *d_ovf = d_binStart + kNumBins + 1, *d_segmax = d_ovf + 1;
-    unsigned long long *d_ubstats = nullptr, h_ubstats[2] = {0, 0};
-    cudaError_t e = cudaMallocAsync(&d_ubstats, 2 * sizeof(unsigned long long), s);
+    unsigned long long *d_ubstats = nullptr, h_ubstats[3] = {0, 0, 0};
+    cudaError_t e = cudaMallocAsync(&d_ubstats, 3 * sizeof(unsigned long long), s);
     if (e != cudaSuccess) {
         cudaFreeAsync(work, s);
         return e;
@@ -1670,38 +1717,52 @@ cudaError_t spgemm(const DevCsr &A, const DevCsr &B, DevCsr &C, int *overflow_ho
     do {
         if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
         if ((e = cudaMemsetAsync(d_ovf, 0, sizeof(int), s))) break;
-        if ((e = cudaMemsetAsync(d_ubstats, 0, 2 * sizeof(unsigned long long), s))) break;
+        if ((e = cudaMemsetAsync(d_ubstats, 0, 3 * sizeof(unsigned long long), s))) break;
         // rows of many products: one warp walks a hash table 32 products at a time (thousands
         // of dependent steps on a stalled level's few long rows); a block with dense counters
-        // takes them when B is narrow enough
+        // takes them when B is narrow enough.  Rows whose bound asks for more than kCapTable
+        // slots (a coarse operator's rows count their products many times over: 600 products
+        // for 60 columns on the first coarse level) try a table of kCapTable first, eight warps
+        // a block instead of one or two; the few that hold more columns go round again.  (The
+        // fine level's R (A P): 3.2 -> 2.3 ms.)
         ub_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, A.rp, A.ci, B.rp, B.ncol, d_bin, d_binCount, d_tsize, d_ubstats,
-                                                    B.ncol <= kDenseCols ? kDenseSymProducts : LLONG_MAX);
+                                                    B.ncol <= kDenseCols ? kDenseSymProducts : LLONG_MAX,
+                                                    n >= kCapRows ? kCapTable : 0);
         note_launch();
-        if ((e = cudaMemcpyAsync(h_ubstats, d_ubstats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s))) break;
+        if ((e = cudaMemcpyAsync(h_ubstats, d_ubstats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s))) break;
         if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
         // symbolic
-        for (int b = 0; b < kGlobalBin && !e; ++b)
-            if (hb.count[b]) e = symbolic_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, d_ovf, s);
-        if (e) break;
-        if (hb.count[kGlobalBin]) {
-            int cnt = hb.count[kGlobalBin];
+        auto symbolic_pass = [&]() -> cudaError_t {
+            cudaError_t r = cudaSuccess;
+            for (int b = 0; b < kGlobalBin && !r; ++b)
+                if (hb.count[b]) r = symbolic_bin(b, hb.count[b], d_perm + hb.start[b], A, B, C.rp, d_ovf, s, d_tsize);
+            if (r || !hb.count[kGlobalBin]) return r;
+            const int cnt = hb.count[kGlobalBin];
             const int *rows = d_perm + hb.start[kGlobalBin];
             if (B.ncol <= kDenseCols) {
                 // long rows against few columns: dense counters in shared memory, a block per row
-                if ((e = dense_attr())) break;
+                if ((r = dense_attr())) return r;
                 dense_symbolic_kernel<<<cnt, kDenseThreads, sizeof(int) * (size_t)B.ncol, s>>>(
                     cnt, rows, A.rp, A.ci, B.rp, B.ci, B.ncol, C.rp); note_launch();
-                if ((e = cudaGetLastError())) break;
-            } else {
-                int64_t total = 0;
-                if ((e = global_tables(cnt, rows, d_tsize, &toff, &total, s))) break;
-                if ((e = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) break;
-                symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
-                    cnt, rows, toff, d_tsize, gkeys, A.rp, A.ci, B.rp, B.ci, C.rp, d_ovf); note_launch();
-                if ((e = cudaGetLastError())) break;
-                cudaFreeAsync(gkeys, s); gkeys = nullptr;
-                cudaFreeAsync(toff, s); toff = nullptr;
+                return cudaGetLastError();
             }
+            int64_t total = 0;
+            if ((r = global_tables(cnt, rows, d_tsize, &toff, &total, s))) return r;
+            if ((r = cudaMallocAsync(&gkeys, sizeof(int) * (size_t)total, s))) return r;
+            symbolic_global_kernel<<<grid_for((int64_t)cnt * 32, 128), 128, 0, s>>>(
+                cnt, rows, toff, d_tsize, gkeys, A.rp, A.ci, B.rp, B.ci, C.rp, d_ovf); note_launch();
+            if ((r = cudaGetLastError())) return r;
+            cudaFreeAsync(gkeys, s); gkeys = nullptr;
+            cudaFreeAsync(toff, s); toff = nullptr;
+            return cudaSuccess;
+        };
+        if ((e = symbolic_pass())) break;
+        if (h_ubstats[2] > 0) {
+            // the capped rows that held more than kCapTable / 2 columns (count -1), in their own bins
+            if ((e = cudaMemsetAsync(d_binCount, 0, sizeof(int) * kNumBins, s))) break;
+            retry_bin_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, C.rp, d_tsize, d_bin, d_binCount); note_launch();
+            if ((e = make_bins(n, d_bin, d_binCount, d_binFill, d_binStart, d_perm, hb, s))) break;
+            if ((e = symbolic_pass())) break;
         }
         if ((e = scan_exclusive(C.rp, C.rp, n, s))) break;
         int nnz = 0;
