@@ -89,8 +89,9 @@ cudaError_t dot_partial(const double *x, const double *y, int n, double *partial
 // Index of each row's diagonal entry (-1 if absent) and its value.
 cudaError_t diag_extract(const DevCsr &A, int *diagpos, double *d, cudaStream_t s);
 // Eq. (7): strong[e], removed[e] (= weak off-diagonal) and kept-entry counts per row.
+// strong_cnt (optional): each row's count of strong entries (the strong graph's row lengths)
 cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
-                     int *kept, cudaStream_t s);
+                     int *kept, cudaStream_t s, int *strong_cnt = nullptr);
 // nonsymmetric operators: strong[e] = own[e] or own[transpose of e]; removed and kept follow
 cudaError_t symmetrize_strength(const DevCsr &A, const uint8_t *own, uint8_t *strong, uint8_t *removed, int *kept,
                                 cudaStream_t s);

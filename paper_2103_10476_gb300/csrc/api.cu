@@ -369,26 +369,27 @@ amg_status_t build_level(amg_hierarchy *h, int L, int *coarsest)
         trace_mark(h, L, AMG_PH_PROLONG);
         goto galerkin;
     }
-    // Eq. (7), on A or (§3.1) on the distance Laplacian of the level's coordinates
+    // Eq. (7), on A or (§3.1) on the distance Laplacian of the level's coordinates; the strong
+    // graph's row lengths come with it unless the nonsymmetric case changes the strong set
+    CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(n + 1), s));
     if (p.strength == AMG_STRENGTH_DISTANCE) {
         CK(cudaMallocAsync(&lvals, sizeof(double) * (size_t)(A.nnz > 0 ? A.nnz : 1), s));
         CK(cudaMallocAsync(&ldiag, sizeof(double) * (size_t)(n > 0 ? n : 1), s));
         CK(distance_laplacian(A, lv.coords, h->dim, lvals, ldiag, flags + 4, s));
         DevCsr Ld = A;
         Ld.v = lvals;
-        CK(strength(Ld, ldiag, p.theta, lv.strong, lv.removed, kept, s));
+        CK(strength(Ld, ldiag, p.theta, lv.strong, lv.removed, kept, s, grp));
     } else {
-        CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s));
+        CK(strength(A, lv.diag, p.theta, lv.strong, lv.removed, kept, s, grp));
     }
     if (p.krylov == AMG_KRYLOV_GMRES) {
         // nonsymmetric operator: i-j strong when either direction passes Eq. (7)
         CK(cudaMallocAsync(&own_mask, (size_t)(A.nnz > 0 ? A.nnz : 1), s));
         CK(cudaMemcpyAsync(own_mask, lv.strong, (size_t)A.nnz, cudaMemcpyDeviceToDevice, s));
         CK(symmetrize_strength(A, own_mask, lv.strong, lv.removed, kept, s));
+        CK(strong_graph_counts(A, lv.strong, grp, s));
     }
     // strong graph
-    CK(cudaMallocAsync(&grp, sizeof(int) * (size_t)(n + 1), s));
-    CK(strong_graph_counts(A, lv.strong, grp, s));
     CK(scan_exclusive(grp, grp, n, s));
     CK(cudaMemcpyAsync(&nnz_g, grp + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

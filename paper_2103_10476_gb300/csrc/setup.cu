@@ -120,13 +120,15 @@ int tile_rows(int n, int64_t nnz)
     const int spread = (int)(((int64_t)n + kStrBlocks - 1) / kStrBlocks);
     return std::max(1, std::min(std::min(kStrRows, spread), (int)(kStrEntries / std::max(avg, 1.0))));
 }
+// (scnt, when given: each row's count of strong entries, the strong graph's row lengths)
 __global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, const int *ci, const double *v,
                                                        const double *d, const float *df, double theta, float thf,
-                                                       uint8_t *strong, uint8_t *removed, int *kept, int rpb)
+                                                       uint8_t *strong, uint8_t *removed, int *kept, int rpb,
+                                                       int *scnt)
 {
     __shared__ int srp[kStrRows + 1];
     __shared__ float sdf[kStrRows];
-    __shared__ int skept[kStrRows];
+    __shared__ int skept[kStrRows], sstr[kStrRows];
     const int r0 = blockIdx.x * rpb;
     if (r0 >= n) return;
     const int nr = min(n - r0, rpb);
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, con
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
         sdf[t] = df[r0 + t];
         skept[t] = 0;
+        sstr[t] = 0;
     }
     __syncthreads();
     const int k0 = srp[0], k1 = srp[nr];
@@ -155,13 +158,17 @@ __global__ void __launch_bounds__(256) strength_kernel(int n, const int *rp, con
         strong[e] = st ? 1 : 0;
         removed[e] = rem ? 1 : 0;
         if (!rem) atomicAdd(&skept[lo], 1);
+        if (st) atomicAdd(&sstr[lo], 1);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) kept[r0 + t] = skept[t];
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        kept[r0 + t] = skept[t];
+        if (scnt) scnt[r0 + t] = sstr[t];
+    }
 }
 
 cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *strong, uint8_t *removed,
-                     int *kept, cudaStream_t s)
+                     int *kept, cudaStream_t s, int *strong_cnt)
 {
     if (A.n == 0) return cudaSuccess;
     float *df = nullptr;
@@ -169,7 +176,7 @@ cudaError_t strength(const DevCsr &A, const double *d, double theta, uint8_t *st
     diag_f32_kernel<<<grid_for(A.n, 256), 256, 0, s>>>(A.n, d, df); note_launch();
     const int rpb = tile_rows(A.n, A.nnz);
     strength_kernel<<<(A.n + rpb - 1) / rpb, 256, 0, s>>>(A.n, A.rp, A.ci, A.v, d, df, theta, (float)theta, strong,
-                                                          removed, kept, rpb);
+                                                          removed, kept, rpb, strong_cnt);
     note_launch();
     cudaError_t e = cudaGetLastError();
     cudaError_t e2 = cudaFreeAsync(df, s);
@@ -310,10 +317,11 @@ __global__ void __launch_bounds__(256) sg_count_kernel(int n, const int *rp, con
     for (int t = threadIdx.x; t < nr; t += blockDim.x) cnt[r0 + t] = sc[t];
 }
 
-// gci[grp[i] ...]: row i's strong columns in ascending order.  The block's entries go 256 at a
-// time; a block-wide scan of their strong flags gives each its rank among the strong entries of
-// the block so far, and the rank of its row's first entry (recorded when that entry's chunk was
-// scanned) turns it into the rank within the row.
+// gci[grp[i] ...]: row i's strong columns in ascending order.  The block's entries go in chunks
+// of four a thread (consecutive); a block-wide scan of the threads' strong counts gives each
+// entry its rank among the strong entries of the block so far, and the rank of its row's first
+// entry (recorded when that entry's chunk was scanned) turns it into the rank within the row.
+constexpr int kFillPer = 4;
 __global__ void __launch_bounds__(256) sg_fill_kernel(int n, const int *rp, const int *ci, const uint8_t *strong,
                                                       const int *grp, int *gci, int rpb)
 {
@@ -329,20 +337,51 @@ __global__ void __launch_bounds__(256) sg_fill_kernel(int n, const int *rp, cons
     if (threadIdx.x == 0) chunk_base = 0;
     __syncthreads();
     const int k0 = srp[0], k1 = srp[nr];
-    for (int c0 = k0; c0 < k1; c0 += blockDim.x) {
-        const int e = c0 + (int)threadIdx.x;
-        const bool valid = e < k1;
-        const int lo = valid ? tile_row(e, srp, nr) : 0;
-        const bool st = valid && strong[e];
-        const unsigned m = __ballot_sync(0xffffffffu, st);
-        if (lane == 0) wsum[warp] = __popc(m);
+    for (int c0 = k0; c0 < k1; c0 += kFillPer * (int)blockDim.x) {
+        const int e0 = c0 + kFillPer * (int)threadIdx.x;
+        int lo = e0 < k1 ? tile_row(e0, srp, nr) : 0;
+        bool st[kFillPer];
+        int rows_of[kFillPer], mine = 0;
+#pragma unroll
+        for (int u = 0; u < kFillPer; ++u) {
+            const int e = e0 + u;
+            st[u] = false;
+            rows_of[u] = lo;
+            if (e < k1) {
+                while (srp[lo + 1] <= e) ++lo;     // rows advance with e (empty rows skipped)
+                rows_of[u] = lo;
+                st[u] = strong[e] != 0;
+            }
+            mine += st[u];
+        }
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
         __syncthreads();
-        int rank = chunk_base + __popc(m & ((1u << lane) - 1u));
+        int rank = chunk_base + incl - mine;
         for (int w = 0; w < warp; ++w) rank += wsum[w];
         // the first entry of a row records the block's strong count before it
-        if (valid && e == srp[lo]) rowbase[lo] = rank;
+        {
+            int r = rank;
+#pragma unroll
+            for (int u = 0; u < kFillPer; ++u) {
+                const int e = e0 + u;
+                if (e < k1 && e == srp[rows_of[u]]) rowbase[rows_of[u]] = r;
+                r += st[u];
+            }
+        }
         __syncthreads();
-        if (st) gci[grp[r0 + lo] + rank - rowbase[lo]] = ci[e];
+#pragma unroll
+        for (int u = 0; u < kFillPer; ++u) {
+            if (st[u]) {
+                gci[grp[r0 + rows_of[u]] + rank - rowbase[rows_of[u]]] = ci[e0 + u];
+                ++rank;
+            }
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             int t = 0;
