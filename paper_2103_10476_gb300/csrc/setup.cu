@@ -860,19 +860,31 @@ __device__ __forceinline__ FilterOutcome filter_outcome(double aii, double r, do
     return o;
 }
 
-// a kept entry's new value (j != i)
+// a kept entry's new value (j != i): the factor chosen first, then one multiply (the lanes of a
+// warp take different sign branches; one FP64 instruction instead of one per branch)
 __device__ __forceinline__ double filter_kept_value(double val, const FilterOutcome &o, int offlmp)
 {
-    double nv = val;
-    if (offlmp && o.flag != LUMP_FALLBACK) {
-        if (dpos(val)) {
-            if (o.zero_plus) nv = 0.0;
-            else if (o.flag == LUMP_KPLUS || o.flag == LUMP_KPLUS_NEG) nv = val * o.fplus;
-        } else if (dneg(val) && o.flag == LUMP_DIAG_KMINUS) {
-            nv = val * o.fminus;
-        }
-    }
-    return nv;
+    if (!offlmp || o.flag == LUMP_FALLBACK) return val;
+    const bool pos = dpos(val);
+    const bool scale_p = pos && !o.zero_plus && (o.flag == LUMP_KPLUS || o.flag == LUMP_KPLUS_NEG);
+    const bool scale_m = !pos && o.flag == LUMP_DIAG_KMINUS && dneg(val);
+    const double prod = val * (scale_p ? o.fplus : o.fminus);
+    return pos && o.zero_plus ? 0.0 : (scale_p || scale_m) ? prod : val;
+}
+
+// Adds val to the one of r (removed entries), kp (kept positive) and km (kept negative) that
+// takes it, through a single FP64 addition on the selected sum
+__device__ __forceinline__ void filter_accumulate(double val, bool rem, int offlmp, double &r, double &kp, double &km,
+                                                  int &nkp, int &nkm)
+{
+    const bool p = !rem && offlmp && dpos(val);
+    const bool m = !rem && offlmp && !p && dneg(val);
+    const double nx = (rem ? r : p ? kp : km) + val;
+    r = rem ? nx : r;
+    kp = p ? nx : kp;
+    km = m ? nx : km;
+    nkp += p;
+    nkm += m;
 }
 
 // the smoothing diagonal from the row's sums
@@ -911,12 +923,7 @@ __device__ __forceinline__ void filter_row(int i, int b, int e_end, const int *c
             continue;
         }
         if (offlmp) offabs = offabs + fabs(val);
-        if (removed[e]) {
-            r = r + val;
-        } else if (offlmp) {
-            if (dpos(val)) { kp = kp + val; ++nkp; }
-            else if (dneg(val)) { km = km + val; ++nkm; }
-        }
+        filter_accumulate(val, removed[e] != 0, offlmp, r, kp, km, nkp, nkm);
     }
     const FilterOutcome o = filter_outcome(aii, r, kp, km, offabs, nkp, nkm, offlmp, tau);
     // pass 2: the kept entries, and the 1-norm sums over them in ascending order
@@ -971,12 +978,7 @@ __device__ void filter_long_row(int i, int b, int e_end, const int *ci, const do
                     continue;
                 }
                 if (offlmp) soff = soff + fabs(val);
-                if (removed[e]) {
-                    sr = sr + val;
-                } else if (offlmp) {
-                    if (dpos(val)) { skp = skp + val; ++cp; }
-                    else if (dneg(val)) { skm = skm + val; ++cm; }
-                }
+                filter_accumulate(val, removed[e] != 0, offlmp, sr, skp, skm, cp, cm);
             }
         }
         const int last = min(32, nseg - q0);

@@ -41,6 +41,27 @@ enum SpmvMode {
 };
 
 
+// partial[i] over i = threadIdx.x, + blockDim.x, ... < n, added in that order from 0; the loads
+// of four steps are issued before their additions (thousands of partials: the last block's
+// tail).  L2 loads: the other blocks' partials are visible there after their fences and the
+// ticket.
+__device__ __forceinline__ double ordered_strided_sum(const double *p, int n)
+{
+    const int bd = (int)blockDim.x;
+    double acc = 0.0;
+    int i = (int)threadIdx.x;
+    for (; i + 3 * bd < n; i += 4 * bd) {
+        const double v0 = __ldcg(p + i), v1 = __ldcg(p + i + bd), v2 = __ldcg(p + i + 2 * bd),
+                     v3 = __ldcg(p + i + 3 * bd);
+        acc += v0;
+        acc += v1;
+        acc += v2;
+        acc += v3;
+    }
+    for (; i < n; i += bd) acc += __ldcg(p + i);
+    return acc;
+}
+
 // Fixed-order completion of a two-stage sum: the block that arrives last (atomic ticket)
 // adds every block's partial in index order -- the same order whichever block is last -- and
 // stores the total; it then returns the ticket counter to zero for the next launch.
@@ -57,8 +78,7 @@ __device__ __forceinline__ void last_block_total(const double *partial, int nblo
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += ((volatile const double *)partial)[i];
+    double acc = ordered_strided_sum(partial, nblocks);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kAll, acc, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = acc;
@@ -87,11 +107,7 @@ __device__ __forceinline__ void last_block_total2(const double *partial, int nbl
     __syncthreads();
     if (!last) return;
     __threadfence();
-    double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
-        a += ((volatile const double *)partial)[i];
-        b += ((volatile const double *)partial)[nblocks + i];
-    }
+    double a = ordered_strided_sum(partial, nblocks), b = ordered_strided_sum(partial + nblocks, nblocks);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(kAll, a, o);
