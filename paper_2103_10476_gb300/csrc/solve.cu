@@ -427,26 +427,33 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
                 yi = (sr * (double)aux[rw]) * rq;
                 y[rw] = (T)yi;
             }
-            c1v = (double)x[rw] * yi;
+            if (c1 != T(0)) c1v = (double)x[rw] * yi;
             c2v = yi * yi;
         }
-        __shared__ double sp1[kSpmvThreads / 32], sp2[kSpmvThreads / 32];
-        // x . y only when asked (c1 != 0: the last sweep's, the estimate); y . y every sweep
-        if (c1 != T(0)) {
+        // Only the first kActive warps hold rows' updates (the rest hold zeros, whose sums would
+        // add exact zeros to sums that start from +0 and so never become -0): their trees alone,
+        // each FP64 step a full pipe slot on GB300 whatever the lanes hold
+        constexpr int kActive = (RPB + 31) / 32;
+        __shared__ double sp1[kActive], sp2[kActive];
+        const int wp = (int)threadIdx.x >> 5;
+        if (wp < kActive) {
+            // x . y only when asked (c1 != 0: the last sweep's, the estimate); y . y every sweep
+            if (c1 != T(0)) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) c1v += __shfl_down_sync(kAll, c1v, o);
-        }
+                for (int o = 16; o > 0; o >>= 1) c1v += __shfl_down_sync(kAll, c1v, o);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c2v += __shfl_down_sync(kAll, c2v, o);
-        if ((threadIdx.x & 31) == 0) {
-            sp1[threadIdx.x >> 5] = c1 != T(0) ? c1v : 0.0;
-            sp2[threadIdx.x >> 5] = c2v;
+            for (int o = 16; o > 0; o >>= 1) c2v += __shfl_down_sync(kAll, c2v, o);
+            if ((threadIdx.x & 31) == 0) {
+                sp1[wp] = c1 != T(0) ? c1v : 0.0;
+                sp2[wp] = c2v;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             double t1 = 0.0, t2 = 0.0;
-            for (int w = 0; w < kSpmvThreads / 32; ++w) {
-                t1 += sp1[w];
+            for (int w = 0; w < kActive; ++w) {
+                if (c1 != T(0)) t1 += sp1[w];
                 t2 += sp2[w];
             }
             partial[bx] = t1;
@@ -969,7 +976,7 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
         } else if (MODE == MODE_POWER) {
             const double yi = ((double)sum * (double)aux[row]) * rq;
             y[row] = (T)yi;
-            contrib = (double)x[row] * yi;
+            if (c1 != T(0)) contrib = (double)x[row] * yi;
             contrib2 = yi * yi;
         } else {
             y[row] = sum;
@@ -978,7 +985,8 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
     }
     if (MODE == MODE_POWER) {
         // CSR block b = rows 128 b .. 128 b + 127 = this block's warps 4 hh .. 4 hh + 3 (rows of
-        // the CSR block's warp w' on its lanes, in order); the CSR block's warps 4-7 hold zeros
+        // the CSR block's warp w' on its lanes, in order); the CSR block's warps 4-7 hold zeros,
+        // which it does not add
         __shared__ double q1[kSellThreads / 32], q2[kSellThreads / 32];
         if (c1 != T(0)) {
 #pragma unroll
@@ -996,12 +1004,8 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
             if (part < nparts) {
                 double t1 = 0.0, t2 = 0.0;
                 for (int w = 0; w < 4; ++w) {
-                    t1 += q1[4 * threadIdx.x + w];
+                    if (c1 != T(0)) t1 += q1[4 * threadIdx.x + w];
                     t2 += q2[4 * threadIdx.x + w];
-                }
-                for (int w = 4; w < kSpmvThreads / 32; ++w) {
-                    t1 += 0.0;
-                    t2 += 0.0;
                 }
                 partial[part] = t1;
                 partial[nparts + part] = t2;
