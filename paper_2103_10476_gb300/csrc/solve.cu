@@ -400,6 +400,46 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
         }
         return;
     }
+    if (MODE == MODE_DOT) {
+        // As for the update modes: row r's y and x_r y_r by thread r < RPB, then the dot
+        // product's trees over those warps only (a row a lane; the other warps would hold zeros)
+        __shared__ T pd[kSpmvThreads];
+        if (LPR == 2) {
+            pd[lane * RPB + threadIdx.x / LPR] = sum;
+        } else {
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(kAll, sum, o, LPR);
+            if (lane == 0) pd[threadIdx.x / LPR] = sum;
+        }
+        __syncthreads();
+        constexpr int kActive = (RPB + 31) / 32;
+        __shared__ double sd[kActive];
+        const int rw = r0 + (int)threadIdx.x;
+        double c = 0.0;
+        if ((int)threadIdx.x < RPB && rw < r1 && tile_ok) {
+            if (rp[rw + 1] - rp[rw] > long_len) {
+                c = (double)x[rw] * (double)y[rw];     // summed outside the tiles, in y already
+            } else {
+                const T sr = LPR == 2 ? pd[threadIdx.x] + pd[RPB + threadIdx.x] : pd[threadIdx.x];
+                y[rw] = sr;
+                c = (double)x[rw] * (double)sr;
+            }
+        }
+        const int wp = (int)threadIdx.x >> 5;
+        if (wp < kActive) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(kAll, c, o);
+            if ((threadIdx.x & 31) == 0) sd[wp] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kActive; ++w) t += sd[w];
+            partial[bx] = t;
+        }
+        if (result) last_block_total(partial, nbx, counter, result);
+        return;
+    }
     if (MODE == MODE_POWER) {
         // As for the update modes: row r's update by thread r < RPB (full warps; y_i takes three
         // FP64 products), D^-1 from aux, 1 / sqrt(x . x) formed once per block (a square root
@@ -480,16 +520,13 @@ __global__ void __launch_bounds__(kSpmvThreads) spmv_tile_kernel(int n, const in
             y[row] = x[row] + dn;
         } else if (MODE == MODE_PROLONG) {
             y[row] += sum;
-        } else if (MODE == MODE_DOT) {
-            y[row] = sum;
-            contrib = (double)x[row] * (double)sum;
         } else if (MODE == MODE_SCALEDOT) {
             T yi = sum / aux[row];
             y[row] = yi;
             contrib = (double)x[row] * (double)yi;
         }
     }
-    if (MODE == MODE_DOT || MODE == MODE_SCALEDOT) {
+    if (MODE == MODE_SCALEDOT) {
         __shared__ double sh[kSpmvThreads / 32];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(kAll, contrib, o);
@@ -1015,25 +1052,18 @@ __global__ void __launch_bounds__(kSellThreads) spmv_sell_kernel(int n, const in
         return;
     }
     if (MODE == MODE_DOT) {
-        // CSR block b covers rows 128 b .. 128 b + 127, its warp w rows 16 w .. 16 w + 15 with
-        // row j's term on lane 2 j; this block's rows are CSR blocks 2 blockIdx and 2 blockIdx + 1
-        __shared__ double con[kSellThreads];
-        __shared__ double wsum[2][kSellThreads / 32];
-        con[threadIdx.x] = contrib;
-        __syncthreads();
+        // CSR block b = rows 128 b .. 128 b + 127 = this block's warps 4 hh .. 4 hh + 3, row r of
+        // a CSR warp on lane r of the same warp here: the same trees, the same partials
+        __shared__ double qd[kSellThreads / 32];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            double v = (lane & 1) ? 0.0 : con[128 * hh + 16 * warp + (lane >> 1)];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kAll, v, o);
-            if (lane == 0) wsum[hh][warp] = v;
-        }
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(kAll, contrib, o);
+        if (lane == 0) qd[warp] = contrib;
         __syncthreads();
         if (threadIdx.x < 2) {
             const int part = 2 * blockIdx.x + threadIdx.x;
             if (part < nparts) {
                 double t = 0.0;
-                for (int w = 0; w < kSellThreads / 32; ++w) t += wsum[threadIdx.x][w];
+                for (int w = 0; w < 4; ++w) t += qd[4 * threadIdx.x + w];
                 partial[part] = t;
             }
         }
