@@ -190,6 +190,63 @@ def test_spgemm_rows_of_thousands_of_entries(amg, oracle_lib, ncol):
     assert np.array_equal(v, Co.val)
 
 
+def _structured_product(rng, m, ncol):
+    """A (m rows) and B (3000 rows, ncol columns) whose rows reach every branch of the product on
+    at least 32,768 rows: bounds above 1,024 slots that hold more than 512 columns (the second
+    symbolic round) and that hold 40 (kept from the first), rows of more than 2,048 products (dense
+    counters when B is narrow enough), rows of A of more than 256 entries with one term a k (the
+    segment kernels' buckets) and with eight (their per-k sweep), and short rows around them."""
+    import scipy.sparse as sp
+    from paper_2103_10476_gb300.problems import CSR
+    brows = []
+    for k in range(3000):
+        if k < 2000:
+            cols = rng.choice(ncol, 8, replace=False)
+        elif k < 2500:
+            cols = rng.choice(40, 10, replace=False)
+        else:
+            cols = rng.choice(ncol, 1, replace=False)
+        brows.append(np.sort(cols))
+    arows = []
+    for i in range(m):
+        if i < 50:
+            ks = rng.choice(2000, 150, replace=False)
+        elif i < 100:
+            ks = 2000 + rng.choice(500, 100, replace=False)
+        elif i < 110:
+            ks = 2500 + rng.choice(500, 400, replace=False)
+        elif i < 115:
+            ks = rng.choice(2000, 300, replace=False)
+        else:
+            ks = rng.choice(3000, 3, replace=False)
+        arows.append(np.sort(ks))
+
+    def csr(rows, n):
+        rp = np.zeros(len(rows) + 1, dtype=np.int64)
+        rp[1:] = np.cumsum([len(r) for r in rows])
+        ci = np.concatenate(rows).astype(np.int32)
+        v = rng.standard_normal(len(ci))
+        return CSR(len(rows), rp, ci, v)
+    return csr(arows, m), csr(brows, 3000)
+
+
+@pytest.mark.parametrize("ncol", [40000, 6000], ids=["wide-B", "narrow-B"])
+def test_spgemm_capped_tables_and_segments(amg, oracle_lib, ncol):
+    # B of 40,000 columns: the capped first round and its retry, dense counters, the segment
+    # kernels' binary-search accumulator; B of 6,000: the bitmap order of long rows of C and
+    # the segment kernels' dense accumulator -- every result bit-exact against the oracle
+    rng = np.random.default_rng(23 + ncol)
+    m = 40000
+    Ac, Bc = _structured_product(rng, m, ncol)
+    rp, ci, v = amg.amg_spgemm(amg.csr_arg(m, Ac.row_ptr, Ac.col, Ac.val), 3000,
+                               amg.csr_arg(3000, Bc.row_ptr, Bc.col, Bc.val), ncol)
+    Co = oracle_lib.spgemm(Ac, Bc, ncol)
+    lens = np.diff(Co.row_ptr)
+    assert lens[:50].min() > 512 and lens[50:100].max() <= 40 and lens[110:115].min() > 1024
+    assert np.array_equal(rp, Co.row_ptr) and np.array_equal(ci, Co.col)
+    assert np.array_equal(v, Co.val)
+
+
 # ---------------------------------------------------------------- degenerate cases
 
 def test_single_level_one_iteration(amg):
