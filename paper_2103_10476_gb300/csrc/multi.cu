@@ -253,7 +253,7 @@ cudaError_t spmm(const SpmvPlan &pl, int n, const int *rp, const int *ci, const 
 {
     if (n == 0) return cudaSuccess;
     // FP64 only: with FP32 values the staged CSR tiles below were faster (1.51x against 1.11x
-    // for eight right-hand sides of stretched64 against one at a time)
+    // for eight right-hand sides of the 64^3 stretched cube against one at a time)
     if (sizeof(T) == 8 && MODE != MM_PROLONG && pl.ns > 0 && pl.lpr == 2 && pl.lr.count == 0 &&
         sell_values_m<T>(pl)) {
         const int blocks = (pl.ns + kMT / kSliceRowsM - 1) / (kMT / kSliceRowsM);

@@ -578,8 +578,8 @@ __global__ void long_hist_kernel(int n, const int *rp, int base, int *hist)
 }
 
 // Lanes per row of a product from its mean row length.  Rows of 40-80 entries take 8 lanes, not
-// 4: on randcoef128's first coarse level (58.6 a row) the shorter chains of dependent gathers
-// beat the extra shuffle level (solve 23.5 → 22.9 ms).
+// 4: on the first coarse level of the 128^3 random-coefficient cube (58.6 a row) the shorter
+// chains of dependent gathers beat the extra shuffle level (solve 23.5 → 22.9 ms).
 int pick_lpr(double avg_row)
 {
     if (avg_row <= 40.0) return 2;
