@@ -247,6 +247,48 @@ def test_spgemm_capped_tables_and_segments(amg, oracle_lib, ncol):
     assert np.array_equal(v, Co.val)
 
 
+def test_spgemm_capped_tables_at_their_boundary(amg, oracle_lib):
+    # 33,000 rows (capped first tables on): rows whose product bounds ask for 2,048 slots and
+    # that hold exactly 512 columns (kept from the first round) or 513 (the second round), empty
+    # rows of A between them, and empty rows of B inside the heavy rows' sums
+    from paper_2103_10476_gb300.problems import CSR
+    rng = np.random.default_rng(41)
+    m, k, ncol = 33000, 1100, 30000
+    brows = [np.array([], dtype=np.int64) if j % 11 == 0 else np.sort(rng.choice(ncol, 2, replace=False))
+             for j in range(k)]
+    brows[1] = np.arange(512)            # row 0 of A: 512 columns from B's row 1 ...
+    brows[2] = np.arange(513)            # ... row 2 of A: 513 from B's row 2
+    arows = []
+    for i in range(m):
+        if i == 0:
+            ks = np.array([1] + list(range(1000, 1100)))          # bound 512 + 100 x 4 = 912
+        elif i == 2:
+            ks = np.array([2] + list(range(1000, 1100)))
+        elif i % 7 == 3:
+            ks = np.array([], dtype=np.int64)
+        else:
+            ks = np.sort(rng.choice(k, 3, replace=False))
+        arows.append(ks)
+    # rows 0 and 2 take their extra columns only inside 0..511 / 0..512: B's rows 1000-1099
+    # point there, so the distinct counts stay 512 and 513
+    for j in range(1000, 1100):
+        brows[j] = np.sort(rng.choice(512, 4, replace=False))
+
+    def csr(rows, n):
+        rp = np.zeros(n + 1, dtype=np.int64)
+        rp[1:] = np.cumsum([len(r) for r in rows])
+        ci = (np.concatenate(rows) if rp[-1] else np.zeros(0)).astype(np.int32)
+        return CSR(n, rp, ci, rng.standard_normal(len(ci)))
+    Ac, Bc = csr(arows, m), csr(brows, k)
+    rp, ci, v = amg.amg_spgemm(amg.csr_arg(m, Ac.row_ptr, Ac.col, Ac.val), k,
+                               amg.csr_arg(k, Bc.row_ptr, Bc.col, Bc.val), ncol)
+    Co = oracle_lib.spgemm(Ac, Bc, ncol)
+    lens = np.diff(Co.row_ptr)
+    assert lens[0] == 512 and lens[2] == 513 and lens[3] == 0
+    assert np.array_equal(rp, Co.row_ptr) and np.array_equal(ci, Co.col)
+    assert np.array_equal(v, Co.val)
+
+
 # ---------------------------------------------------------------- degenerate cases
 
 def test_single_level_one_iteration(amg):
